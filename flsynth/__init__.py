@@ -1,0 +1,201 @@
+"""Seeded synthetic inputs for the facility-location path (graphs, masks, costs).
+
+Shared by the CPU oracle's tests, the CUDA path's tests and the benchmark.  It
+holds none of the method's arithmetic: it only draws graphs and per-vertex
+inputs from a counter-based hash (see ``synth.c``), so the same call gives the
+same arrays on every machine and thread count.
+
+Workload recipes (the paper's social/web graphs and its synthetic R-MAT family,
+Section 5 and Table 1, stood in for by seeded R-MAT and Erdos-Renyi graphs):
+
+* ``er10k``  -- G(n=10^4, M=4*10^4), every vertex client and facility, cost 20.0,
+  sketch k=16.
+* ``rmat20`` -- R-MAT scale 20, 16*2^20 draws, (a,b,c,d)=(.57,.19,.19,.05),
+  seeded relabelling, symmetrised and deduplicated; all vertices clients and
+  facilities; costs log-uniform in [5, 500]; k=32.
+* ``rmat26`` -- the same recipe at scale 26; clients Bernoulli(0.5), facilities
+  Bernoulli(0.1) independently, facility costs log-uniform in [10, 10^4], other
+  vertices +inf; k=16.
+* ``rmatS`` for other scales (tests): the rmat20 recipe at scale S.
+
+Seeds: graph seed 42 + config number (er10k=1, rmat20=2, rmat26=3, rmat23=5),
+sketch seed 1, mask/cost seed 7, query seed 11.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "synth.c")
+_LIB_PATH = os.path.join(_HERE, "libflsynth.so")
+_lock = threading.Lock()
+_lib = None
+
+SKETCH_SEED = 1
+MASK_SEED = 7
+QUERY_SEED = 11
+
+
+def build(force: bool = False) -> str:
+    """Compile ``synth.c`` into ``libflsynth.so`` (gcc, OpenMP)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp"
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            i64, u64, u32, vp = ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p
+            lib.syn_er.restype = i64
+            lib.syn_er.argtypes = [i64, i64, u64, vp, vp]
+            lib.syn_rmat.restype = i64
+            lib.syn_rmat.argtypes = [ctypes.c_int, i64, u32, u32, u32, u64, vp, vp]
+            lib.syn_bernoulli.restype = None
+            lib.syn_bernoulli.argtypes = [i64, u64, u32, vp]
+            lib.syn_loguniform.restype = None
+            lib.syn_loguniform.argtypes = [i64, u64, ctypes.c_double, ctypes.c_double, vp, vp]
+            lib.syn_uniform.restype = None
+            lib.syn_uniform.argtypes = [i64, u64, ctypes.c_double, ctypes.c_double, vp]
+            lib.syn_hash.restype = None
+            lib.syn_hash.argtypes = [i64, u64, vp]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def er(n: int, M: int, seed: int):
+    """Erdos-Renyi G(n, M) as symmetric CSR (rowp int64[n+1], cols int32[2M])."""
+    lib = _load()
+    rowp = np.zeros(n + 1, np.int64)
+    cols = np.zeros(max(2 * M, 1), np.int32)
+    nnz = lib.syn_er(n, M, seed, _ptr(rowp), _ptr(cols))
+    if nnz < 0:
+        raise ValueError(f"syn_er failed for n={n} M={M}")
+    return rowp, cols[:nnz].copy()
+
+
+def rmat(scale: int, edgefactor: int, seed: int, a=0.57, b=0.19, c=0.19):
+    """R-MAT graph with 2^scale vertices and edgefactor*2^scale draws, as CSR."""
+    lib = _load()
+    n = 1 << scale
+    ndraws = edgefactor * n
+    ta = int(a * 65536)
+    tb = int((a + b) * 65536)
+    tc = int((a + b + c) * 65536)
+    rowp = np.zeros(n + 1, np.int64)
+    cols = np.empty(max(2 * ndraws, 1), np.int32)
+    nnz = lib.syn_rmat(scale, ndraws, ta, tb, tc, seed, _ptr(rowp), _ptr(cols))
+    if nnz < 0:
+        raise ValueError(f"syn_rmat failed for scale={scale}")
+    out = cols[:nnz]
+    if nnz < len(cols) // 2:
+        out = out.copy()
+    return rowp, out
+
+
+def bernoulli(n: int, seed: int, p: float) -> np.ndarray:
+    lib = _load()
+    m = np.zeros(n, np.uint8)
+    lib.syn_bernoulli(n, seed, min(int(p * 4294967296.0), 0xFFFFFFFF), _ptr(m))
+    return m
+
+
+def loguniform(n: int, seed: int, lo: float, hi: float, facility_mask=None) -> np.ndarray:
+    lib = _load()
+    out = np.zeros(n, np.float64)
+    fm = None if facility_mask is None else np.ascontiguousarray(facility_mask, np.uint8)
+    lib.syn_loguniform(n, seed, lo, hi, None if fm is None else _ptr(fm), _ptr(out))
+    return out
+
+
+def uniform(m: int, seed: int, lo: float, hi: float) -> np.ndarray:
+    lib = _load()
+    out = np.zeros(m, np.float64)
+    lib.syn_uniform(m, seed, lo, hi, _ptr(out))
+    return out
+
+
+def hashes(m: int, seed: int) -> np.ndarray:
+    lib = _load()
+    out = np.zeros(m, np.uint64)
+    lib.syn_hash(m, seed, _ptr(out))
+    return out
+
+
+@dataclasses.dataclass
+class Workload:
+    """One facility-location instance: CSR graph + per-vertex inputs."""
+    name: str
+    n: int
+    rowp: np.ndarray          # int64[n+1]
+    cols: np.ndarray          # int32[nnz]
+    k: int                    # bottom-k sketch size
+    seed: int                 # rank seed
+    cost: np.ndarray          # float64[n], +inf = not a facility
+    client: np.ndarray        # uint8[n], 1 = client
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowp[-1])
+
+
+def from_csr(name, rowp, cols, k, seed, cost, client) -> Workload:
+    n = len(rowp) - 1
+    return Workload(name, n, np.ascontiguousarray(rowp, np.int64),
+                    np.ascontiguousarray(cols, np.int32), k, seed,
+                    np.ascontiguousarray(cost, np.float64),
+                    np.ascontiguousarray(client, np.uint8))
+
+
+def config(name: str) -> Workload:
+    """Build one of the named workloads (see module docstring)."""
+    if name == "er10k":
+        n = 10_000
+        rowp, cols = er(n, 40_000, 42 + 1)
+        return from_csr(name, rowp, cols, 16, SKETCH_SEED,
+                        np.full(n, 20.0), np.ones(n, np.uint8))
+    if name.startswith("rmat"):
+        scale = int(name[4:])
+        rowp, cols = rmat(scale, 16, 42 + {20: 2, 26: 3, 23: 5}.get(scale, scale))
+        n = 1 << scale
+        if scale == 26:
+            client = bernoulli(n, MASK_SEED, 0.5)
+            fac = bernoulli(n, MASK_SEED + 1, 0.1)
+            cost = loguniform(n, MASK_SEED + 2, 10.0, 1.0e4, fac)
+            return from_csr(name, rowp, cols, 16, SKETCH_SEED, cost, client)
+        k = 32
+        cost = loguniform(n, MASK_SEED, 5.0, 500.0)
+        return from_csr(name, rowp, cols, k, SKETCH_SEED, cost, np.ones(n, np.uint8))
+    raise KeyError(name)
+
+
+def small_er(n: int, avg_deg: float, seed: int, k: int = 16, cost: float = 20.0,
+             client_p: float = 1.0, fac_p: float = 1.0) -> Workload:
+    """Small ER instance for tests (optionally with random client/facility subsets)."""
+    M = int(round(n * avg_deg / 2))
+    M = min(M, n * (n - 1) // 2)
+    rowp, cols = er(n, M, seed)
+    client = np.ones(n, np.uint8) if client_p >= 1.0 else bernoulli(n, seed + 1000, client_p)
+    fac = np.ones(n, np.uint8) if fac_p >= 1.0 else bernoulli(n, seed + 2000, fac_p)
+    c = np.where(fac > 0, cost, np.inf)
+    return from_csr(f"er{n}", rowp, cols, k, SKETCH_SEED, c, client)

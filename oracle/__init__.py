@@ -1,0 +1,247 @@
+"""CPU oracle for the facility-location hot path -- TEST INFRASTRUCTURE.
+
+A plain, slow implementation of the paper's definitions in C (``fl_oracle.c``),
+loaded through ctypes.  Only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package; the library under
+``paper_1503_03635_gb300`` never does, and the two share no code.
+
+Each wrapper names the passage of the paper it follows (see ``fl_oracle.c``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fl_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libfloracle.so")
+_lock = threading.Lock()
+_lib = None
+
+i64, u64, i32, dbl, vp = (ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32,
+                          ctypes.c_double, ctypes.c_void_p)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, OpenMP, no FP contraction, no fast-math)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp"
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            lib.orc_splitmix64_next.restype = u64
+            lib.orc_splitmix64_next.argtypes = [ctypes.POINTER(u64)]
+            lib.orc_rank.restype = u64
+            lib.orc_rank.argtypes = [u64, i64]
+            lib.orc_priority.restype = u64
+            lib.orc_priority.argtypes = [u64, i64]
+            lib.orc_graph_create.restype = vp
+            lib.orc_graph_create.argtypes = [i64, vp, vp]
+            lib.orc_graph_destroy.restype = None
+            lib.orc_graph_destroy.argtypes = [vp]
+            lib.orc_build_sketches.restype = ctypes.c_int
+            lib.orc_build_sketches.argtypes = [vp, ctypes.c_int, u64]
+            for name in ("orc_hops", "orc_edge_merges", "orc_ads_groups", "orc_ads_entries"):
+                getattr(lib, name).restype = i64
+                getattr(lib, name).argtypes = [vp]
+            lib.orc_export_sketch.restype = ctypes.c_int
+            lib.orc_export_sketch.argtypes = [vp, vp, vp]
+            lib.orc_export_ads.restype = ctypes.c_int
+            lib.orc_export_ads.argtypes = [vp] + [vp] * 8
+            lib.orc_vertex_ads.restype = i64
+            lib.orc_vertex_ads.argtypes = [vp, ctypes.c_int, u64, i64, i64,
+                                           vp, vp, vp, vp, vp, vp, ctypes.POINTER(i64)]
+            lib.orc_compute_radii.restype = ctypes.c_int
+            lib.orc_compute_radii.argtypes = [vp, vp, vp, vp]
+            lib.orc_hip_estimate.restype = dbl
+            lib.orc_hip_estimate.argtypes = [vp, i64, i64, vp]
+            lib.orc_open_facilities.restype = ctypes.c_int
+            lib.orc_open_facilities.argtypes = [vp, vp, vp, u64, vp, ctypes.POINTER(i64)]
+            lib.orc_assign.restype = ctypes.c_int
+            lib.orc_assign.argtypes = [vp, vp, vp, vp]
+            lib.orc_objective.restype = ctypes.c_int
+            lib.orc_objective.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(dbl),
+                                          ctypes.POINTER(i64), ctypes.POINTER(i64)]
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def splitmix64_outputs(state: int, count: int) -> list[int]:
+    """The first `count` outputs of SplitMix64 from `state` (Steele et al. 2014)."""
+    lib = _load()
+    s = u64(state)
+    return [int(lib.orc_splitmix64_next(ctypes.byref(s))) for _ in range(count)]
+
+
+def rank(seed: int, v: int) -> int:
+    """r(v): the hash of vertex v used by the bottom-k sketches (Algorithm 1)."""
+    return int(_load().orc_rank(seed, v))
+
+
+def ranks(seed: int, n: int) -> np.ndarray:
+    lib = _load()
+    return np.array([lib.orc_rank(seed, v) for v in range(n)], np.uint64)
+
+
+def priority(seed: int, f: int) -> int:
+    """pi(f): the random facility ID of the greedy MIS (Section 3.3)."""
+    return int(_load().orc_priority(seed, f))
+
+
+class Graph:
+    """An oracle graph (copies the CSR) with its sketch/ADS state."""
+
+    def __init__(self, rowp: np.ndarray, cols: np.ndarray):
+        self._lib = _load()
+        self.rowp = np.ascontiguousarray(rowp, np.int64)
+        self.cols = np.ascontiguousarray(cols, np.int32)
+        self.n = len(self.rowp) - 1
+        self._h = self._lib.orc_graph_create(self.n, _p(self.rowp), _p(self.cols))
+        if not self._h:
+            raise MemoryError("orc_graph_create failed")
+        self.k = None
+        self.seed = None
+
+    def close(self):
+        if self._h:
+            self._lib.orc_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- phase (i): Section 2.3, Algorithms 1-2 ---------------------------
+    def build_sketches(self, k: int, seed: int) -> None:
+        rc = self._lib.orc_build_sketches(self._h, k, seed)
+        if rc != 0:
+            raise RuntimeError(f"orc_build_sketches rc={rc}")
+        self.k, self.seed = k, seed
+
+    @property
+    def hops(self) -> int:
+        return int(self._lib.orc_hops(self._h))
+
+    @property
+    def edge_merges(self) -> int:
+        return int(self._lib.orc_edge_merges(self._h))
+
+    def sketch(self):
+        S = np.zeros((self.n, self.k), np.uint64)
+        cnt = np.zeros(self.n, np.int32)
+        self._lib.orc_export_sketch(self._h, _p(S), _p(cnt))
+        return S, cnt
+
+    def ads(self) -> dict:
+        ng = int(self._lib.orc_ads_groups(self._h))
+        ne = int(self._lib.orc_ads_entries(self._h))
+        out = dict(gofs=np.zeros(self.n + 1, np.int64), eofs=np.zeros(self.n + 1, np.int64),
+                   ghop=np.zeros(ng, np.int32), gcnt=np.zeros(ng, np.int32),
+                   gcounted=np.zeros(ng, np.int32), gwt=np.zeros(ng, np.float64),
+                   eid=np.zeros(ne, np.int32), erank=np.zeros(ne, np.uint64))
+        self._lib.orc_export_ads(self._h, _p(out["gofs"]), _p(out["eofs"]), _p(out["ghop"]),
+                                 _p(out["gcnt"]), _p(out["gcounted"]), _p(out["gwt"]),
+                                 _p(out["eid"]), _p(out["erank"]))
+        return out
+
+    def vertex_ads(self, k: int, seed: int, v: int, cap: int = 1 << 16) -> dict:
+        """Algorithm 1 run for the single vertex v (sequential BFS order)."""
+        ids = np.zeros(cap, np.int32)
+        rk = np.zeros(cap, np.uint64)
+        gh = np.zeros(cap, np.int32)
+        gn = np.zeros(cap, np.int32)
+        gc = np.zeros(cap, np.int32)
+        gw = np.zeros(cap, np.float64)
+        ng = i64(0)
+        ne = self._lib.orc_vertex_ads(self._h, k, seed, v, cap, _p(ids), _p(rk), _p(gh),
+                                      _p(gn), _p(gc), _p(gw), ctypes.byref(ng))
+        if ne < 0:
+            raise RuntimeError("orc_vertex_ads failed (capacity)")
+        g = ng.value
+        return dict(eid=ids[:ne].copy(), erank=rk[:ne].copy(), ghop=gh[:g].copy(),
+                    gcnt=gn[:g].copy(), gcounted=gc[:g].copy(), gwt=gw[:g].copy())
+
+    def hip_estimate(self, v: int, h: int, client=None) -> float:
+        c = None if client is None else np.ascontiguousarray(client, np.uint8)
+        return float(self._lib.orc_hip_estimate(self._h, v, h, None if c is None else _p(c)))
+
+    # -- phase (ii): Eq. 1 at epsilon -> 0 -------------------------------
+    def radii(self, cost: np.ndarray, client: np.ndarray) -> np.ndarray:
+        cost = np.ascontiguousarray(cost, np.float64)
+        client = np.ascontiguousarray(client, np.uint8)
+        r = np.zeros(self.n, np.float64)
+        rc = self._lib.orc_compute_radii(self._h, _p(cost), _p(client), _p(r))
+        if rc != 0:
+            raise RuntimeError(f"orc_compute_radii rc={rc}")
+        return r
+
+    # -- phase (iii): lexicographically-first MIS (Section 3.3) -----------
+    def open_facilities(self, r: np.ndarray, client: np.ndarray, seed: int):
+        r = np.ascontiguousarray(r, np.float64)
+        client = np.ascontiguousarray(client, np.uint8)
+        op = np.zeros(self.n, np.uint8)
+        nopen = i64(0)
+        rc = self._lib.orc_open_facilities(self._h, _p(r), _p(client), seed, _p(op),
+                                           ctypes.byref(nopen))
+        if rc != 0:
+            raise RuntimeError(f"orc_open_facilities rc={rc}")
+        return op, int(nopen.value)
+
+    # -- assignment + objective (Section 3.1) ----------------------------
+    def assign(self, open_: np.ndarray):
+        op = np.ascontiguousarray(open_, np.uint8)
+        a = np.zeros(self.n, np.int32)
+        d = np.zeros(self.n, np.int32)
+        rc = self._lib.orc_assign(self._h, _p(op), _p(a), _p(d))
+        if rc != 0:
+            raise RuntimeError(f"orc_assign rc={rc}")
+        return a, d
+
+
+def objective(open_, cost, client, dist):
+    lib = _load()
+    op = np.ascontiguousarray(open_, np.uint8)
+    cost = np.ascontiguousarray(cost, np.float64)
+    client = np.ascontiguousarray(client, np.uint8)
+    dist = np.ascontiguousarray(dist, np.int32)
+    obj, ds, un = dbl(0), i64(0), i64(0)
+    lib.orc_objective(len(op), _p(op), _p(cost), _p(client), _p(dist),
+                      ctypes.byref(obj), ctypes.byref(ds), ctypes.byref(un))
+    return float(obj.value), int(ds.value), int(un.value)
+
+
+def solve(rowp, cols, k, seed, cost, client) -> dict:
+    """The whole path on the CPU: sketches, radii, MIS, assignment, objective."""
+    g = Graph(rowp, cols)
+    g.build_sketches(k, seed)
+    r = g.radii(cost, client)
+    op, nopen = g.open_facilities(r, client, seed)
+    a, d = g.assign(op)
+    obj, ds, un = objective(op, cost, client, d)
+    S, cnt = g.sketch()
+    out = dict(graph=g, hops=g.hops, edge_merges=g.edge_merges, S=S, Scnt=cnt,
+               ads=g.ads(), radii=r, open=op, n_open=nopen, assign=a, dist=d,
+               objective=obj, dist_sum=ds, n_unserved=un)
+    return out

@@ -1,0 +1,664 @@
+/*
+ * fl_oracle.c -- TEST INFRASTRUCTURE.  A plain, slow CPU oracle for the
+ * data-parallel hot path of scalable graph facility location (Garimella,
+ * De Francisci Morales, Gionis, Sozio: "Scalable Facility Location for
+ * Massive Graphs on Pregel-like Systems").  Only the test suite, the smoke
+ * check and the benchmark's CPU-baseline leg may load or run this code; the
+ * product path never does.  It shares no code with the CUDA library.
+ *
+ * Every routine follows the paper's definitions step by step, in the
+ * paper's order, with no blocking or fusion.  Readings taken where the
+ * paper is silent (all cited at the routine):
+ *   - ranks r(u) are SplitMix64 outputs (Steele, Lea, Flood 2014);
+ *   - within one hop, vertices at equal distance are presented to the
+ *     bottom-k sketch in ascending rank (so hop-synchronous propagation and
+ *     Algorithm 1 build the same ADS);
+ *   - HIP weights condition on all ranks except the entry's own, with all
+ *     vertices at one distance treated together (weight 2^64 / t, t the
+ *     k-th smallest rank of the ball, counting the k-1 smallest only);
+ *   - radius r_f is the root of the epsilon->0, all-unfrozen form of Eq. 1;
+ *   - facility selection is the lexicographically-first MIS of the
+ *     conflict graph under the key (r_f, pi_f).
+ *
+ * Floating point: every FP64 operation is a single IEEE-754 operation in
+ * the order written (build with -ffp-contract=off, no fast-math).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 3
+#define ORC_ESTATE 2
+
+/* ---------------------------------------------------------------------- */
+/* Ranks: SplitMix64 (Steele, Lea, Flood, OOPSLA 2014).                    */
+/* The paper only says r(u) is a hash of u (Section 2.3, Algorithm 1).     */
+/* ---------------------------------------------------------------------- */
+
+#define SM_GAMMA 0x9e3779b97f4a7c15ULL
+
+/* One SplitMix64 step: advance the state by the golden-gamma increment
+   and return the mixed state. */
+uint64_t orc_splitmix64_next(uint64_t* state) {
+    *state += SM_GAMMA;
+    uint64_t z = *state;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+/* r(v): the (v+1)-th output of SplitMix64 started from state `seed`. */
+uint64_t orc_rank(uint64_t seed, int64_t v) {
+    uint64_t state = seed + (uint64_t)v * SM_GAMMA;
+    return orc_splitmix64_next(&state);
+}
+
+/* pi(f): MIS priority (Section 3.3 draws a random ID per facility).  The
+   (f+1)-th output of a second SplitMix64 stream whose starting state is
+   the first SplitMix64 output for `seed`.  Injective in f, like r. */
+uint64_t orc_priority(uint64_t seed, int64_t f) {
+    uint64_t s = seed;
+    uint64_t stream = orc_splitmix64_next(&s);
+    uint64_t state = stream + (uint64_t)f * SM_GAMMA;
+    return orc_splitmix64_next(&state);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Graph handle                                                            */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t hop;      /* distance d(v, u) of the entries */
+    int32_t cnt;      /* entries in this group */
+    int32_t counted;  /* leading entries that carry the weight */
+    double wt;        /* HIP adjusted weight of each counted entry */
+    int64_t first;    /* index of the first entry in the entry arrays */
+} orc_group;
+
+typedef struct {
+    int64_t n;
+    int64_t* rowp;
+    int32_t* cols;
+    /* sketch state */
+    int k;
+    uint64_t seed;
+    int built;
+    uint64_t* S;      /* n*k final bottom-k sketch (ascending ranks) */
+    int32_t* Scnt;    /* n */
+    int64_t hops;     /* last hop at which some sketch changed */
+    int64_t edge_merges;
+    /* ADS, vertex-major: groups of v are gofs[v]..gofs[v+1], entries of v
+       are eofs[v]..eofs[v+1]; within v ordered by hop, then by rank */
+    int64_t* gofs;
+    int64_t* eofs;
+    orc_group* grp;
+    int32_t* ent_id;
+    uint64_t* ent_rank;
+    int64_t ngroups, nentries;
+} orc_graph;
+
+static void orc_clear_ads(orc_graph* g) {
+    free(g->S); free(g->Scnt); free(g->gofs); free(g->eofs);
+    free(g->grp); free(g->ent_id); free(g->ent_rank);
+    g->S = NULL; g->Scnt = NULL; g->gofs = NULL; g->eofs = NULL;
+    g->grp = NULL; g->ent_id = NULL; g->ent_rank = NULL;
+    g->built = 0;
+}
+
+orc_graph* orc_graph_create(int64_t n, const int64_t* rowp, const int32_t* cols) {
+    if (n < 0 || !rowp) return NULL;
+    orc_graph* g = (orc_graph*)calloc(1, sizeof(orc_graph));
+    if (!g) return NULL;
+    g->n = n;
+    int64_t nnz = rowp[n];
+    g->rowp = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
+    g->cols = (int32_t*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    if (!g->rowp || !g->cols) { free(g->rowp); free(g->cols); free(g); return NULL; }
+    memcpy(g->rowp, rowp, ((size_t)n + 1) * sizeof(int64_t));
+    if (nnz > 0) memcpy(g->cols, cols, (size_t)nnz * sizeof(int32_t));
+    return g;
+}
+
+void orc_graph_destroy(orc_graph* g) {
+    if (!g) return;
+    orc_clear_ads(g);
+    free(g->rowp); free(g->cols);
+    free(g);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Bottom-k insertion (Algorithm 1 / Algorithm 2 inner step).              */
+/* ---------------------------------------------------------------------- */
+
+/* Insert rank x into the ascending list L (length *len, capacity k) if the
+   list has fewer than k entries or x is below its k-th entry, and x is not
+   already present.  This is the reading of the test "r(u) < max_r(BKMH)"
+   of Algorithms 1 and 2 for a list that is not yet full. */
+static void bottomk_insert(uint64_t* L, int32_t* len, int k, uint64_t x) {
+    int32_t m = *len;
+    if (m == k && x >= L[k - 1]) return;
+    int32_t pos = 0;
+    while (pos < m && L[pos] < x) ++pos;
+    if (pos < m && L[pos] == x) return;          /* already present */
+    int32_t last = (m < k) ? m : k - 1;          /* drop the old k-th if full */
+    for (int32_t i = last; i > pos; --i) L[i] = L[i - 1];
+    L[pos] = x;
+    if (m < k) *len = m + 1;
+}
+
+typedef struct { uint64_t rank; int32_t id; } rank_id;
+
+static int rank_id_cmp(const void* a, const void* b) {
+    uint64_t x = ((const rank_id*)a)->rank, y = ((const rank_id*)b)->rank;
+    return (x > y) - (x < y);
+}
+
+/* ---------------------------------------------------------------------- */
+/* HIP weight of the entries that join a sketch at one distance.           */
+/* ---------------------------------------------------------------------- */
+
+/* Given S_h(v) = bottom-k of the ball of radius h (length len), an entry w
+   at distance h that is at position i of S_h(v) is counted by the HIP
+   estimator iff len < k or i < k-1; its inclusion probability conditioned
+   on all other ranks is then 1 (len < k) or t / 2^64 with t = S_h(v)[k-1]
+   (the (k-1)-th smallest rank of the ball without w).  The adjusted weight
+   is the inverse (Cohen 2014, HIP; cited in Section 2.3). */
+static double hip_weight(const uint64_t* Sh, int32_t len, int k) {
+    if (len < k) return 1.0;
+    return 18446744073709551616.0 / (double)Sh[k - 1];
+}
+
+/* ---------------------------------------------------------------------- */
+/* Phase (i): sketches and ADS by hop-synchronous propagation.             */
+/* Section 2.3, Algorithm 2 (unweighted: no CleanUp is needed because one  */
+/* superstep delivers exactly the vertices of one distance).               */
+/* ---------------------------------------------------------------------- */
+
+typedef struct { int32_t v; int32_t hop; int64_t at; int32_t cnt; } hop_rec;
+
+int orc_build_sketches(orc_graph* g, int k, uint64_t seed) {
+    if (!g || k < 2 || k > 64) return ORC_EINVAL;
+    orc_clear_ads(g);
+    const int64_t n = g->n;
+    g->k = k;
+    g->seed = seed;
+    g->hops = 0;
+    g->edge_merges = 0;
+
+    uint64_t* S = (uint64_t*)malloc((size_t)(n > 0 ? n : 1) * k * sizeof(uint64_t));
+    int32_t* Scnt = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    uint64_t* Dprev = (uint64_t*)malloc((size_t)(n > 0 ? n : 1) * k * sizeof(uint64_t));
+    int32_t* Dprev_cnt = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    uint64_t* Dcur = (uint64_t*)malloc((size_t)(n > 0 ? n : 1) * k * sizeof(uint64_t));
+    int32_t* Dcur_cnt = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    double* Dcur_wt = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    int32_t* Dcur_counted = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    /* hop-major record of every (v, hop) group, appended in (hop, v) order */
+    int64_t rec_cap = n + 16, rec_n = 0;
+    hop_rec* rec = (hop_rec*)malloc((size_t)rec_cap * sizeof(hop_rec));
+    double* rec_wt = (double*)malloc((size_t)rec_cap * sizeof(double));
+    int32_t* rec_counted = (int32_t*)malloc((size_t)rec_cap * sizeof(int32_t));
+    int64_t ent_cap = n + 16, ent_n = 0;
+    uint64_t* ent = (uint64_t*)malloc((size_t)ent_cap * sizeof(uint64_t));
+    if (!S || !Scnt || !Dprev || !Dprev_cnt || !Dcur || !Dcur_cnt || !Dcur_wt ||
+        !Dcur_counted || !rec || !rec_wt || !rec_counted || !ent) {
+        free(S); free(Scnt); free(Dprev); free(Dprev_cnt); free(Dcur); free(Dcur_cnt);
+        free(Dcur_wt); free(Dcur_counted); free(rec); free(rec_wt); free(rec_counted); free(ent);
+        return ORC_ENOMEM;
+    }
+
+    /* hop 0: every vertex knows itself (distance 0) */
+    for (int64_t v = 0; v < n; ++v) {
+        uint64_t r = orc_rank(seed, v);
+        S[v * k] = r;
+        Scnt[v] = 1;
+        Dprev[v * k] = r;
+        Dprev_cnt[v] = 1;
+        rec[rec_n].v = (int32_t)v; rec[rec_n].hop = 0; rec[rec_n].at = ent_n; rec[rec_n].cnt = 1;
+        rec_wt[rec_n] = hip_weight(&S[v * k], 1, k);
+        rec_counted[rec_n] = 1;
+        ++rec_n;
+        ent[ent_n++] = r;
+    }
+
+    int64_t merges = 0;
+    for (int64_t h = 1;; ++h) {
+        int64_t changed = 0;
+        /* every vertex merges the entries its neighbours added at hop h-1 */
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : changed, merges)
+        for (int64_t v = 0; v < n; ++v) {
+            uint64_t old[64];
+            int32_t oldn = Scnt[v];
+            memcpy(old, &S[v * k], (size_t)oldn * sizeof(uint64_t));
+            uint64_t* L = &S[v * k];
+            int32_t len = oldn;
+            for (int64_t e = g->rowp[v]; e < g->rowp[v + 1]; ++e) {
+                int32_t u = g->cols[e];
+                if (Dprev_cnt[u] == 0) continue;
+                ++merges;
+                for (int32_t i = 0; i < Dprev_cnt[u]; ++i)
+                    bottomk_insert(L, &len, k, Dprev[(int64_t)u * k + i]);
+            }
+            Scnt[v] = len;
+            /* new entries: in the new sketch but not in the old one */
+            int32_t dn = 0, counted = 0, oi = 0;
+            for (int32_t i = 0; i < len; ++i) {
+                while (oi < oldn && old[oi] < L[i]) ++oi;
+                if (oi < oldn && old[oi] == L[i]) continue;
+                Dcur[v * k + dn] = L[i];
+                if (len < k || i < k - 1) ++counted;
+                ++dn;
+            }
+            Dcur_cnt[v] = dn;
+            Dcur_counted[v] = counted;
+            Dcur_wt[v] = hip_weight(L, len, k);
+            if (dn) ++changed;
+        }
+        if (!changed) { g->hops = h - 1; break; }
+        /* append this hop's groups in vertex order */
+        for (int64_t v = 0; v < n; ++v) {
+            if (!Dcur_cnt[v]) continue;
+            if (rec_n == rec_cap) {
+                rec_cap *= 2;
+                rec = (hop_rec*)realloc(rec, (size_t)rec_cap * sizeof(hop_rec));
+                rec_wt = (double*)realloc(rec_wt, (size_t)rec_cap * sizeof(double));
+                rec_counted = (int32_t*)realloc(rec_counted, (size_t)rec_cap * sizeof(int32_t));
+                if (!rec || !rec_wt || !rec_counted) return ORC_ENOMEM;
+            }
+            while (ent_n + Dcur_cnt[v] > ent_cap) {
+                ent_cap *= 2;
+                ent = (uint64_t*)realloc(ent, (size_t)ent_cap * sizeof(uint64_t));
+                if (!ent) return ORC_ENOMEM;
+            }
+            rec[rec_n].v = (int32_t)v; rec[rec_n].hop = (int32_t)h;
+            rec[rec_n].at = ent_n; rec[rec_n].cnt = Dcur_cnt[v];
+            rec_wt[rec_n] = Dcur_wt[v];
+            rec_counted[rec_n] = Dcur_counted[v];
+            ++rec_n;
+            memcpy(&ent[ent_n], &Dcur[v * k], (size_t)Dcur_cnt[v] * sizeof(uint64_t));
+            ent_n += Dcur_cnt[v];
+        }
+        uint64_t* t = Dprev; Dprev = Dcur; Dcur = t;
+        int32_t* tc = Dprev_cnt; Dprev_cnt = Dcur_cnt; Dcur_cnt = tc;
+    }
+    g->edge_merges = merges;
+
+    /* vertex-major ADS: stable counting sort of the records by vertex */
+    g->gofs = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    g->eofs = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    g->grp = (orc_group*)malloc((size_t)(rec_n > 0 ? rec_n : 1) * sizeof(orc_group));
+    g->ent_id = (int32_t*)malloc((size_t)(ent_n > 0 ? ent_n : 1) * sizeof(int32_t));
+    g->ent_rank = (uint64_t*)malloc((size_t)(ent_n > 0 ? ent_n : 1) * sizeof(uint64_t));
+    int64_t* gcur = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
+    int64_t* ecur = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
+    if (!g->gofs || !g->eofs || !g->grp || !g->ent_id || !g->ent_rank || !gcur || !ecur)
+        return ORC_ENOMEM;
+    for (int64_t i = 0; i < rec_n; ++i) {
+        g->gofs[rec[i].v + 1] += 1;
+        g->eofs[rec[i].v + 1] += rec[i].cnt;
+    }
+    for (int64_t v = 0; v < n; ++v) { g->gofs[v + 1] += g->gofs[v]; g->eofs[v + 1] += g->eofs[v]; }
+    memcpy(gcur, g->gofs, ((size_t)n + 1) * sizeof(int64_t));
+    memcpy(ecur, g->eofs, ((size_t)n + 1) * sizeof(int64_t));
+    /* rank -> vertex id: ranks of distinct vertices are distinct (SplitMix64
+       outputs of distinct counters), so a table sorted by rank maps each
+       entry's rank back to its vertex */
+    rank_id* tab = (rank_id*)malloc((size_t)(n > 0 ? n : 1) * sizeof(rank_id));
+    if (!tab) return ORC_ENOMEM;
+    for (int64_t v = 0; v < n; ++v) { tab[v].rank = orc_rank(seed, v); tab[v].id = (int32_t)v; }
+    qsort(tab, (size_t)n, sizeof(rank_id), rank_id_cmp);
+    for (int64_t i = 0; i < rec_n; ++i) {
+        int64_t v = rec[i].v;
+        int64_t gi = gcur[v]++;
+        int64_t ei = ecur[v];
+        ecur[v] += rec[i].cnt;
+        g->grp[gi].hop = rec[i].hop;
+        g->grp[gi].cnt = rec[i].cnt;
+        g->grp[gi].counted = rec_counted[i];
+        g->grp[gi].wt = rec_wt[i];
+        g->grp[gi].first = ei;
+        memcpy(&g->ent_rank[ei], &ent[rec[i].at], (size_t)rec[i].cnt * sizeof(uint64_t));
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t e2 = 0; e2 < ent_n; ++e2) {
+        uint64_t x = g->ent_rank[e2];
+        int64_t lo = 0, hi = n - 1;
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (tab[mid].rank < x) lo = mid + 1; else hi = mid;
+        }
+        g->ent_id[e2] = tab[lo].id;
+    }
+    free(tab);
+    free(gcur); free(ecur);
+    g->ngroups = rec_n;
+    g->nentries = ent_n;
+    g->S = S;
+    g->Scnt = Scnt;
+    g->built = 1;
+    free(Dprev); free(Dprev_cnt); free(Dcur); free(Dcur_cnt); free(Dcur_wt); free(Dcur_counted);
+    free(rec); free(rec_wt); free(rec_counted); free(ent);
+    return ORC_OK;
+}
+
+int64_t orc_hops(const orc_graph* g) { return g && g->built ? g->hops : -1; }
+int64_t orc_edge_merges(const orc_graph* g) { return g && g->built ? g->edge_merges : -1; }
+int64_t orc_ads_groups(const orc_graph* g) { return g && g->built ? g->ngroups : -1; }
+int64_t orc_ads_entries(const orc_graph* g) { return g && g->built ? g->nentries : -1; }
+
+/* Final sketches: S[v*k + i] for i < cnt[v], UINT64_MAX padding after. */
+int orc_export_sketch(const orc_graph* g, uint64_t* S, int32_t* cnt) {
+    if (!g || !g->built) return ORC_ESTATE;
+    for (int64_t v = 0; v < g->n; ++v) {
+        cnt[v] = g->Scnt[v];
+        for (int i = 0; i < g->k; ++i)
+            S[v * g->k + i] = i < g->Scnt[v] ? g->S[v * g->k + i] : UINT64_MAX;
+    }
+    return ORC_OK;
+}
+
+/* ADS export, vertex-major.  gofs/eofs: n+1 offsets; per group: hop, cnt,
+   counted, weight; per entry: vertex id and rank. */
+int orc_export_ads(const orc_graph* g, int64_t* gofs, int64_t* eofs, int32_t* ghop,
+                   int32_t* gcnt, int32_t* gcounted, double* gwt,
+                   int32_t* eid, uint64_t* erank) {
+    if (!g || !g->built) return ORC_ESTATE;
+    memcpy(gofs, g->gofs, ((size_t)g->n + 1) * sizeof(int64_t));
+    memcpy(eofs, g->eofs, ((size_t)g->n + 1) * sizeof(int64_t));
+    for (int64_t i = 0; i < g->ngroups; ++i) {
+        ghop[i] = g->grp[i].hop;
+        gcnt[i] = g->grp[i].cnt;
+        gcounted[i] = g->grp[i].counted;
+        gwt[i] = g->grp[i].wt;
+    }
+    if (eid) memcpy(eid, g->ent_id, (size_t)g->nentries * sizeof(int32_t));
+    if (erank) memcpy(erank, g->ent_rank, (size_t)g->nentries * sizeof(uint64_t));
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Algorithm 1 for one vertex (sampled checks on large graphs).            */
+/* ---------------------------------------------------------------------- */
+
+/* Sequential ADS of vertex v (Algorithm 1): list vertices by increasing
+   distance from v (equal distances in ascending rank), insert u when the
+   bottom-k list has fewer than k entries or r(u) is below its k-th entry.
+   Output arrays are sized by the caller: hop/id/rank capacity `cap`
+   entries, group weight/counted capacity `cap`.  Returns the number of
+   entries (or -1 when cap is too small / no memory).  Groups: per distance
+   with at least one entry, gw[] = weight, gc[] = counted, gh[] = distance,
+   gn[] = entry count; *ngroups set. */
+int64_t orc_vertex_ads(const orc_graph* g, int k, uint64_t seed, int64_t v, int64_t cap,
+                       int32_t* ids, uint64_t* ranks, int32_t* gh, int32_t* gn,
+                       int32_t* gc, double* gw, int64_t* ngroups) {
+    const int64_t n = g->n;
+    int32_t* dist = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    int32_t* q = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    rank_id* lvl = (rank_id*)malloc((size_t)n * sizeof(rank_id));
+    if (!dist || !q || !lvl) { free(dist); free(q); free(lvl); return -1; }
+    for (int64_t i = 0; i < n; ++i) dist[i] = -1;
+    uint64_t B[64];
+    int32_t blen = 0;
+    int64_t ne = 0, ng = 0;
+    int64_t qh = 0, qt = 0;
+    dist[v] = 0;
+    q[qt++] = (int32_t)v;
+    int32_t d = 0;
+    while (qh < qt) {
+        /* one distance level: q[qh..level_end) */
+        int64_t level_end = qt;
+        int64_t m = 0;
+        for (int64_t i = qh; i < level_end; ++i) { lvl[m].id = q[i]; lvl[m].rank = orc_rank(seed, q[i]); ++m; }
+        qsort(lvl, (size_t)m, sizeof(rank_id), rank_id_cmp);   /* ascending rank */
+        int64_t first = ne;
+        for (int64_t i = 0; i < m; ++i) {
+            uint64_t r = lvl[i].rank;
+            if (blen < k || r < B[k - 1]) {
+                if (ne >= cap) { free(dist); free(q); free(lvl); return -1; }
+                ids[ne] = lvl[i].id;
+                ranks[ne] = r;
+                ++ne;
+                bottomk_insert(B, &blen, k, r);
+            }
+        }
+        if (ne > first) {
+            /* weight from the finished level (the ball of radius d) */
+            int32_t counted = 0;
+            for (int64_t e = first; e < ne; ++e) {
+                int32_t pos = 0;
+                while (B[pos] != ranks[e]) ++pos;
+                if (blen < k || pos < k - 1) ++counted;
+            }
+            gh[ng] = d; gn[ng] = (int32_t)(ne - first); gc[ng] = counted;
+            gw[ng] = hip_weight(B, blen, k);
+            ++ng;
+        }
+        /* expand the next level */
+        for (int64_t i = qh; i < level_end; ++i) {
+            int32_t x = q[i];
+            for (int64_t e = g->rowp[x]; e < g->rowp[x + 1]; ++e) {
+                int32_t u = g->cols[e];
+                if (dist[u] < 0) { dist[u] = d + 1; q[qt++] = u; }
+            }
+        }
+        qh = level_end;
+        ++d;
+    }
+    *ngroups = ng;
+    free(dist); free(q); free(lvl);
+    return ne;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Phase (ii): per-facility radius.                                        */
+/* Eq. 1 (Section 3) with all clients unfrozen and alpha(c) = alpha, as in */
+/* Section 3.2 before Eq. 2, taken at epsilon -> 0: the served-client      */
+/* slack sum_c max{0, r - d(c,f)} equals the opening cost c(f).  Client    */
+/* counts per distance come from predicated HIP queries on the ADS         */
+/* (Section 3.4, "How to estimate the number of unfrozen clients?").       */
+/* ---------------------------------------------------------------------- */
+
+/* Radius of one facility from its ADS groups (hop ascending).  W_h = the
+   HIP-estimated number of clients at distance h; N_j = sum_{h<=j} W_h;
+   G_0 = 0, G_{j+1} = G_j + N_j (so g(r) = G_j + N_j (r - j) on [j, j+1]).
+   L = hop of the last group.  r = j + (c - G_j)/N_j for the smallest
+   j < L with G_{j+1} >= c; otherwise r = L + (c - G_L)/N_L if N_L > 0,
+   else +inf.  Non-facilities (cost +inf) get +inf. */
+static double radius_one(const orc_graph* g, int64_t f, double cost, const uint8_t* client) {
+    if (!(cost < INFINITY)) return INFINITY;
+    int64_t g0 = g->gofs[f], g1 = g->gofs[f + 1];
+    if (g1 == g0) return INFINITY;
+    int64_t L = g->grp[g1 - 1].hop;
+    double N = 0.0, G = 0.0;
+    int64_t gi = g0;
+    for (int64_t j = 0; j <= L; ++j) {
+        double W = 0.0;
+        if (gi < g1 && g->grp[gi].hop == j) {
+            const orc_group* gr = &g->grp[gi];
+            int64_t clients = 0;
+            for (int32_t i = 0; i < gr->counted; ++i)
+                if (client[g->ent_id[gr->first + i]]) ++clients;
+            W = (double)clients * gr->wt;
+            ++gi;
+        }
+        N = N + W;
+        if (j < L) {
+            double Gn = G + N;
+            if (Gn >= cost) return (double)j + (cost - G) / N;
+            G = Gn;
+        }
+    }
+    if (N > 0.0) return (double)L + (cost - G) / N;
+    return INFINITY;
+}
+
+int orc_compute_radii(const orc_graph* g, const double* cost, const uint8_t* client, double* r) {
+    if (!g || !g->built) return ORC_ESTATE;
+#pragma omp parallel for schedule(dynamic, 1024)
+    for (int64_t f = 0; f < g->n; ++f) r[f] = radius_one(g, f, cost[f], client);
+    return ORC_OK;
+}
+
+/* HIP estimate of the number of clients within distance h of v (the
+   predicated neighbourhood query of Section 2.3): sum of counted client
+   weights over groups with hop <= h.  Summed group by group in hop order:
+   each group adds (#counted clients) * weight. */
+double orc_hip_estimate(const orc_graph* g, int64_t v, int64_t h, const uint8_t* client) {
+    if (!g || !g->built) return NAN;
+    double N = 0.0;
+    for (int64_t gi = g->gofs[v]; gi < g->gofs[v + 1]; ++gi) {
+        const orc_group* gr = &g->grp[gi];
+        if (gr->hop > h) break;
+        int64_t clients = 0;
+        for (int32_t i = 0; i < gr->counted; ++i)
+            if (!client || client[g->ent_id[gr->first + i]]) ++clients;
+        N = N + (double)clients * gr->wt;
+    }
+    return N;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Phase (iii): facility selection = lexicographically-first MIS of H-bar. */
+/* Section 3.3 (Algorithm 3 lines building H-bar; Algorithm 6; the greedy  */
+/* MIS of Blelloch, Fineman, Shun returns the lexicographically-first MIS  */
+/* for its priority order).  Candidate facilities: r_f finite.  Ball(f) =  */
+/* clients c with d(c,f) <= floor(r_f).  f ~ g iff their balls share a     */
+/* client.  Key(f) = (r_f, pi_f).                                          */
+/* ---------------------------------------------------------------------- */
+
+typedef struct { double r; uint64_t pi; int32_t f; } cand_t;
+
+static int cand_cmp(const void* a, const void* b) {
+    const cand_t* x = (const cand_t*)a;
+    const cand_t* y = (const cand_t*)b;
+    if (x->r < y->r) return -1;
+    if (x->r > y->r) return 1;
+    if (x->pi < y->pi) return -1;
+    if (x->pi > y->pi) return 1;
+    return 0;
+}
+
+/* Sequential greedy in key order: f joins S iff no client of Ball(f) is
+   already claimed; then it claims all of Ball(f).  open[f] = 1 for S. */
+int orc_open_facilities(const orc_graph* g, const double* r, const uint8_t* client,
+                        uint64_t seed, uint8_t* open, int64_t* n_open) {
+    if (!g) return ORC_EINVAL;
+    const int64_t n = g->n;
+    int64_t m = 0;
+    for (int64_t f = 0; f < n; ++f) if (r[f] < INFINITY) ++m;
+    cand_t* c = (cand_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(cand_t));
+    uint8_t* claimed = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+    int32_t* dist = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t* q = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t* ball = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!c || !claimed || !dist || !q || !ball) {
+        free(c); free(claimed); free(dist); free(q); free(ball);
+        return ORC_ENOMEM;
+    }
+    m = 0;
+    for (int64_t f = 0; f < n; ++f)
+        if (r[f] < INFINITY) { c[m].r = r[f]; c[m].pi = orc_priority(seed, f); c[m].f = (int32_t)f; ++m; }
+    qsort(c, (size_t)m, sizeof(cand_t), cand_cmp);
+    for (int64_t v = 0; v < n; ++v) { dist[v] = -1; open[v] = 0; }
+    int64_t opened = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        int32_t f = c[i].f;
+        double fl = floor(c[i].r);
+        int64_t B = fl > 2147483647.0 ? 2147483647 : (int64_t)fl;
+        /* BFS from f to depth B; stop at the first claimed client */
+        int64_t qh = 0, qt = 0, nb = 0;
+        int conflict = 0;
+        dist[f] = 0;
+        q[qt++] = f;
+        while (qh < qt && !conflict) {
+            int32_t x = q[qh++];
+            if (client[x]) {
+                if (claimed[x]) { conflict = 1; break; }
+                ball[nb++] = x;
+            }
+            if (dist[x] == B) continue;
+            for (int64_t e = g->rowp[x]; e < g->rowp[x + 1]; ++e) {
+                int32_t u = g->cols[e];
+                if (dist[u] < 0) { dist[u] = dist[x] + 1; q[qt++] = u; }
+            }
+        }
+        for (int64_t j = 0; j < qt; ++j) dist[q[j]] = -1;
+        if (conflict) continue;
+        open[f] = 1;
+        ++opened;
+        for (int64_t j = 0; j < nb; ++j) claimed[ball[j]] = 1;
+    }
+    *n_open = opened;
+    free(c); free(claimed); free(dist); free(q); free(ball);
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Assignment: every vertex to its nearest open facility (ties: smallest  */
+/* facility id); Section 3.1 objective d(c,S) = min_{f in S} d(c,f), and  */
+/* Algorithm 3's fallback of connecting a client to its nearest facility. */
+/* Level-synchronous multi-source BFS; unreachable vertices get -1.       */
+/* ---------------------------------------------------------------------- */
+
+int orc_assign(const orc_graph* g, const uint8_t* open, int32_t* assign, int32_t* dist) {
+    if (!g) return ORC_EINVAL;
+    const int64_t n = g->n;
+    int32_t* cur = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t* nxt = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!cur || !nxt) { free(cur); free(nxt); return ORC_ENOMEM; }
+    int64_t nc = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        dist[v] = -1;
+        assign[v] = -1;
+        if (open[v]) { dist[v] = 0; assign[v] = (int32_t)v; cur[nc++] = (int32_t)v; }
+    }
+    int32_t L = 0;
+    while (nc > 0) {
+        int64_t nn = 0;
+        for (int64_t i = 0; i < nc; ++i) {
+            int32_t x = cur[i];
+            for (int64_t e = g->rowp[x]; e < g->rowp[x + 1]; ++e) {
+                int32_t u = g->cols[e];
+                if (dist[u] < 0) {
+                    dist[u] = L + 1;
+                    assign[u] = assign[x];
+                    nxt[nn++] = u;
+                } else if (dist[u] == L + 1 && assign[x] < assign[u]) {
+                    assign[u] = assign[x];
+                }
+            }
+        }
+        int32_t* t = cur; cur = nxt; nxt = t;
+        nc = nn;
+        ++L;
+    }
+    free(cur); free(nxt);
+    return ORC_OK;
+}
+
+/* Objective (Section 3.1): sum_{f in S} c(f) + sum_{c in C} d(c, S).
+   Opening costs are added in ascending facility id; distances of served
+   clients are summed exactly in int64 and added once; clients with no
+   open facility in their component are counted in *n_unserved and left
+   out of the sum. */
+int orc_objective(int64_t n, const uint8_t* open, const double* cost, const uint8_t* client,
+                  const int32_t* dist, double* obj, int64_t* dist_sum, int64_t* n_unserved) {
+    double open_cost = 0.0;
+    int64_t ds = 0, un = 0;
+    for (int64_t v = 0; v < n; ++v)
+        if (open[v]) open_cost = open_cost + cost[v];
+    for (int64_t v = 0; v < n; ++v) {
+        if (!client[v]) continue;
+        if (dist[v] < 0) ++un; else ds += dist[v];
+    }
+    *obj = open_cost + (double)ds;
+    *dist_sum = ds;
+    *n_unserved = un;
+    return ORC_OK;
+}

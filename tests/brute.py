@@ -1,0 +1,171 @@
+"""Brute-force definitions for tiny graphs (test helpers, pure Python).
+
+Everything here is computed from first principles on a materialised
+all-pairs distance table, independently of the oracle's propagation code:
+
+* balls and bottom-k sketches of balls (Section 2.3: the ADS is the union of
+  the min-hash sketches of the l closest vertices, for every l);
+* the ADS by definition, with HIP weights from the definition of the
+  conditional inclusion probability (Cohen 2014, cited in Section 2.3);
+* the exact root of the epsilon->0 opening condition (Eq. 1) from exact
+  client distances, in rational arithmetic;
+* the conflict graph H-bar (Algorithm 3) and its lexicographically-first MIS;
+* nearest-open-facility assignment and the objective (Section 3.1).
+"""
+from __future__ import annotations
+
+from collections import deque
+from fractions import Fraction
+
+import numpy as np
+
+TWO64 = float(2 ** 64)
+
+
+def csr_from_edges(n: int, edges) -> tuple[np.ndarray, np.ndarray]:
+    adj = [set() for _ in range(n)]
+    for a, b in edges:
+        if a != b:
+            adj[a].add(b)
+            adj[b].add(a)
+    rowp = np.zeros(n + 1, np.int64)
+    cols = []
+    for v in range(n):
+        nb = sorted(adj[v])
+        cols.extend(nb)
+        rowp[v + 1] = rowp[v] + len(nb)
+    return rowp, np.array(cols, np.int32)
+
+
+def adjacency(rowp, cols):
+    n = len(rowp) - 1
+    return [list(cols[rowp[v]:rowp[v + 1]]) for v in range(n)]
+
+
+def apsp(rowp, cols) -> np.ndarray:
+    """All-pairs hop distances by one BFS per vertex; -1 = unreachable."""
+    adj = adjacency(rowp, cols)
+    n = len(adj)
+    D = np.full((n, n), -1, np.int64)
+    for s in range(n):
+        D[s, s] = 0
+        q = deque([s])
+        while q:
+            x = q.popleft()
+            for u in adj[x]:
+                if D[s, u] < 0:
+                    D[s, u] = D[s, x] + 1
+                    q.append(u)
+    return D
+
+
+def ball(D, v, h):
+    return [w for w in range(D.shape[0]) if 0 <= D[v, w] <= h]
+
+
+def bottom_k(values, k):
+    return sorted(values)[:k]
+
+
+def sketch_at(D, rk, k, v, h):
+    """S_h(v): the k smallest ranks of the ball of radius h around v."""
+    return bottom_k([int(rk[w]) for w in ball(D, v, h)], k)
+
+
+def max_ecc(D):
+    return int(D.max()) if D.size else 0
+
+
+def ads_by_definition(D, rk, k):
+    """ADS(v) = {(w, d(v,w)) : r(w) is among the k smallest ranks of the ball
+    of radius d(v,w)}; each entry carries `counted` (it is among the k-1
+    smallest, or the ball has fewer than k vertices) and its HIP weight:
+    1 / Pr[w counted | all other ranks] = 2^64 / t, where t is the (k-1)-th
+    smallest rank of the ball without w (weight 1 when that ball has fewer
+    than k-1 vertices).  Returned per vertex as a list of
+    (hop, sorted [(rank, id, counted, weight)])."""
+    n = D.shape[0]
+    out = []
+    for v in range(n):
+        groups = []
+        hmax = int(D[v].max())
+        for h in range(hmax + 1):
+            B = ball(D, v, h)
+            ranks_B = sorted(int(rk[w]) for w in B)
+            entries = []
+            for w in B:
+                if D[v, w] != h:
+                    continue
+                r = int(rk[w])
+                if r not in ranks_B[:k]:
+                    continue
+                others = sorted(int(rk[x]) for x in B if x != w)
+                counted = len(ranks_B) < k or r in ranks_B[:k - 1]
+                if len(others) < k - 1:
+                    wt = 1.0
+                else:
+                    wt = TWO64 / float(others[k - 2])
+                entries.append((r, w, counted, wt))
+            if entries:
+                groups.append((h, sorted(entries)))
+        out.append(groups)
+    return out
+
+
+def exact_radius(dists, cost):
+    """Root r >= 0 of sum_c max(0, r - d_c) = cost (exact, Fraction)."""
+    ds = sorted(int(d) for d in dists)
+    if not ds:
+        return None
+    cost = Fraction(cost)
+    # on [ds[i], ds[i+1]] the slope is i+1 and g(ds[i]) = sum_{j<i} (ds[i]-ds[j])
+    for i in range(len(ds)):
+        g_i = sum(Fraction(ds[i] - ds[j]) for j in range(i))
+        hi = ds[i + 1] if i + 1 < len(ds) else None
+        g_hi = None if hi is None else g_i + (i + 1) * (hi - ds[i])
+        if hi is None or g_hi >= cost:
+            return ds[i] + (cost - g_i) / (i + 1)
+    return None
+
+
+def conflict_graph(D, r, client):
+    """H-bar on candidates (finite r): f ~ g iff some client is within
+    floor(r_f) of f and within floor(r_g) of g."""
+    n = D.shape[0]
+    cand = [f for f in range(n) if np.isfinite(r[f])]
+    balls = {}
+    for f in cand:
+        B = int(np.floor(r[f]))
+        balls[f] = {c for c in range(n) if client[c] and 0 <= D[f, c] <= B}
+    adj = {f: set() for f in cand}
+    for i, f in enumerate(cand):
+        for g in cand[i + 1:]:
+            if balls[f] & balls[g]:
+                adj[f].add(g)
+                adj[g].add(f)
+    return cand, balls, adj
+
+
+def lfmis(cand, adj, key):
+    """Lexicographically-first MIS: scan in key order, take f unless a
+    neighbour was already taken."""
+    S = set()
+    for f in sorted(cand, key=key):
+        if not (adj[f] & S):
+            S.add(f)
+    return S
+
+
+def nearest_assignment(D, open_set):
+    n = D.shape[0]
+    a = np.full(n, -1, np.int64)
+    d = np.full(n, -1, np.int64)
+    for v in range(n):
+        best = None
+        for f in sorted(open_set):
+            if D[v, f] >= 0 and (best is None or D[v, f] < best):
+                best = D[v, f]
+                a[v] = f
+        if best is not None:
+            d[v] = best
+    return a, d
