@@ -1,0 +1,191 @@
+/*
+ * fl.h -- C ABI of the GB300 graph facility-location library (libflgpu.so).
+ *
+ * The library computes, on one GPU, the data-parallel hot path of the
+ * facility-location method of Garimella, De Francisci Morales, Gionis and
+ * Sozio ("Scalable Facility Location for Massive Graphs on Pregel-like
+ * Systems"):
+ *   (i)   bottom-k min-hash sketches and all-distances sketches (ADS) with HIP
+ *         weights, by hop-synchronous propagation (Section 2.3, Alg. 1-2);
+ *   (ii)  per-facility opening radii from predicated HIP estimates of client
+ *         counts (Eq. 1 at epsilon -> 0, Section 3.2 and 3.4);
+ *   (iii) facility selection as the lexicographically-first maximal
+ *         independent set of the conflict graph H-bar under key (r_f, pi_f)
+ *         (Alg. 3 and Section 3.3, Alg. 6);
+ *   then each client's nearest open facility and the objective (Section 3.1).
+ *
+ * Conventions for every entry point:
+ *   - Return value: FL_OK (0) or one of the FL_E* codes below; no exception
+ *     or signal crosses the ABI.  fl_last_error() gives the message of the
+ *     most recent failure on the calling thread.
+ *   - Pointers are host or device memory as the call's `mem_kind` says
+ *     (FL_MEM_HOST or FL_MEM_DEVICE); device pointers must belong to the
+ *     current CUDA device.  The caller keeps ownership of every array it
+ *     passes; the library copies inputs before returning and writes outputs
+ *     into caller arrays.  Handles own all device memory they allocate.
+ *   - Work is issued on the stream given to fl_graph_create (NULL = legacy
+ *     default stream).  Calls return after their results are complete
+ *     (outputs are valid on return for both memory kinds).
+ *   - Handles are thread-compatible: use one handle from one thread at a
+ *     time.  A graph may serve many solves created from it, one at a time.
+ *   - Vertex ids are int32 in [0, n); row offsets are int64 (graphs with
+ *     more than 2^31 directed edges are supported).
+ *   - The graph must be undirected: the CSR must be symmetric (u in N(v) iff
+ *     v in N(u)), as in the paper's undirected setting (Section 2.1).
+ */
+#ifndef FL_H
+#define FL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define FL_OK 0
+#define FL_EINVAL 1   /* bad argument: null handle, bad CSR, unsupported k, bad cost */
+#define FL_ESTATE 2   /* called out of order (e.g. radii before sketches) */
+#define FL_ENOMEM 3   /* device or host allocation failed */
+#define FL_ECUDA 4    /* a CUDA runtime call or kernel failed */
+#define FL_ETIMEOUT 5 /* a bounded device-side loop hit its iteration limit */
+
+/* Memory kinds of pointer arguments. */
+#define FL_MEM_HOST 0
+#define FL_MEM_DEVICE 1
+
+typedef struct fl_graph fl_graph; /* device CSR + sketches + ADS of one graph */
+typedef struct fl_solve fl_solve; /* one instance: costs, clients, radii, open set, assignment */
+
+/*
+ * fl_graph_create -- upload a graph (Section 2.1: G = (V, E), unweighted).
+ *   n        number of vertices, 1 <= n <= 2^31 - 1.
+ *   row_off  int64[n+1] CSR row offsets, row_off[0] = 0, non-decreasing,
+ *            row_off[n] = nnz.
+ *   cols     int32[nnz] neighbour ids in [0, n); must be symmetric.
+ *   nnz      number of directed CSR entries (2 x undirected edges).
+ *   mem_kind FL_MEM_HOST or FL_MEM_DEVICE for row_off and cols.
+ *   stream   cudaStream_t on which all work of this graph and its solves runs.
+ *   out      receives the new handle.
+ * The CSR is validated on the device (offsets monotone, ids in range);
+ * violations return FL_EINVAL.  Self-loops and duplicates are tolerated.
+ */
+int fl_graph_create(int64_t n, const int64_t* row_off, const int32_t* cols, int64_t nnz,
+                    int mem_kind, void* stream, fl_graph** out);
+
+/* fl_graph_destroy -- free the handle and all its device memory (NULL ok). */
+int fl_graph_destroy(fl_graph* g);
+
+/*
+ * fl_build_sketches -- phase (i): per-vertex bottom-k sketches and the ADS.
+ * Section 2.3 (Alg. 1 sequential, Alg. 2 vertex program): hop h merges into
+ * each vertex the sketch entries its neighbours gained at hop h-1 and keeps
+ * the k smallest ranks; it stops when no sketch changes.  Ranks are
+ * r(v) = SplitMix64 output v+1 from state `seed`.  Every entry that joins
+ * S_h(v) is an ADS entry (v, u, h); its HIP weight is 1 when S_h(v) holds
+ * fewer than k ranks, else entries at positions < k-1 weigh
+ * 2^64 / S_h(v)[k-1] and the entry at position k-1 weighs 0.
+ *   k     sketch size, 2 <= k <= 32.
+ *   seed  rank seed.
+ * Returns FL_EINVAL if k is unsupported or a vertex's rank would equal
+ * UINT64_MAX (the empty-slot sentinel; probability n / 2^64).
+ * Rebuilding with other (k, seed) replaces the previous sketches and
+ * invalidates solves created before (they return FL_ESTATE).
+ */
+int fl_build_sketches(fl_graph* g, int k, uint64_t seed);
+
+/*
+ * fl_sketch_stats -- counters of the last build (any pointer may be NULL).
+ *   hops         last hop at which some sketch changed (H*).
+ *   edge_merges  sum over processed hops h of the CSR entries (v, u) whose
+ *                u gained entries at hop h-1 (the unit of work of Alg. 2).
+ *   ads_entries  total ADS entries; ads_groups: total (vertex, hop) groups.
+ */
+int fl_sketch_stats(const fl_graph* g, int64_t* hops, int64_t* edge_merges,
+                    int64_t* ads_entries, int64_t* ads_groups);
+
+/*
+ * fl_export_sketches -- copy the final sketches out.
+ *   S    uint64[n*k]: S[v*k + i] = i-th smallest rank of v's component, or
+ *        UINT64_MAX past cnt[v];  cnt int32[n] (either may be NULL).
+ */
+int fl_export_sketches(fl_graph* g, uint64_t* S, int32_t* cnt, int mem_kind);
+
+/*
+ * fl_export_ads -- copy the ADS out, vertex-major (groups of v ordered by hop,
+ * entries of a group by ascending rank).  Sizes from fl_sketch_stats.
+ *   gofs, eofs     int64[n+1] group / entry offsets per vertex.
+ *   ghop, gcnt     int32[groups] distance and entry count of each group.
+ *   gcounted       int32[groups] leading entries that carry the weight.
+ *   gwt            double[groups] HIP weight of each counted entry.
+ *   eid            int32[entries] vertex id of each entry.
+ * Any pointer may be NULL (that array is skipped).
+ */
+int fl_export_ads(fl_graph* g, int64_t* gofs, int64_t* eofs, int32_t* ghop, int32_t* gcnt,
+                  int32_t* gcounted, double* gwt, int32_t* eid, int mem_kind);
+
+/* fl_solve_create / fl_solve_destroy -- one facility-location instance on a
+   graph whose sketches are built (else FL_ESTATE). */
+int fl_solve_create(fl_graph* g, fl_solve** out);
+int fl_solve_destroy(fl_solve* s);
+
+/*
+ * fl_compute_radii -- phase (ii): opening radius of every facility.
+ * Eq. 1 with all clients unfrozen and alpha(c) = r (Section 3.2), at
+ * epsilon -> 0: r_f solves sum_h W_h max(0, r - h) = c(f), where W_h is the
+ * HIP estimate of the clients at distance h of f, read off f's ADS with the
+ * client predicate (Section 3.4).  In FP64 with a fixed operation order.
+ *   open_cost   double[n]; +INFINITY = not a facility; facilities need a
+ *               finite cost > 0 (else FL_EINVAL).
+ *   client_mask uint8[n]; nonzero = client.
+ *   mem_kind    memory kind of open_cost, client_mask and radii_out.
+ *   radii_out   double[n] or NULL; +INFINITY for non-facilities and for
+ *               facilities that reach no client.
+ */
+int fl_compute_radii(fl_solve* s, const double* open_cost, const uint8_t* client_mask,
+                     int mem_kind, double* radii_out);
+
+/*
+ * fl_open_facilities -- phase (iii): the lexicographically-first maximal
+ * independent set S of H-bar (Section 3.3, Alg. 6 with the greedy MIS of
+ * Blelloch, Fineman and Shun).  Candidates: facilities with finite r_f.
+ * Ball(f) = clients within floor(r_f) hops of f; f, g conflict iff their
+ * balls share a client.  Keys (r_f, pi_f), pi_f = SplitMix64 output f+1 from
+ * the state given by the first output for the sketch seed.
+ *   open_out  uint8[n] or NULL (1 = open).   n_open  receives |S| (or NULL).
+ * Needs fl_compute_radii first (else FL_ESTATE).
+ */
+int fl_open_facilities(fl_solve* s, uint8_t* open_out, int64_t* n_open, int mem_kind);
+
+/*
+ * fl_assign_clients -- nearest open facility of every vertex (Section 3.1,
+ * d(c, S) = min over open f of d(c, f)); ties go to the smallest facility id.
+ *   assign_out int32[n] or NULL (-1 = no open facility in the component).
+ *   dist_out   int32[n] or NULL (hop distance, -1 when unassigned).
+ */
+int fl_assign_clients(fl_solve* s, int32_t* assign_out, int32_t* dist_out, int mem_kind);
+
+/*
+ * fl_objective -- sum_{f in S} c(f) + sum_{c in C} d(c, S) (Section 3.1).
+ * Clients without an open facility in their component are left out of the
+ * sum and counted in n_unserved.  obj is FP64; dist_sum is exact.
+ */
+int fl_objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserved);
+
+/* fl_solve_stats -- counters of the last MIS: rounds of the greedy MIS and
+   the number of candidates (any pointer may be NULL). */
+int fl_solve_stats(const fl_solve* s, int64_t* mis_rounds, int64_t* candidates);
+
+/* fl_status_str -- static text for a status code. */
+const char* fl_status_str(int status);
+
+/* fl_last_error -- copy the calling thread's last error message into buf
+   (NUL-terminated, truncated to len); returns the last status code. */
+int fl_last_error(char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FL_H */

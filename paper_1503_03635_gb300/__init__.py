@@ -1,0 +1,247 @@
+"""Python binding of libflgpu (GB300 graph facility location).
+
+Argument marshalling over the C ABI of ``include/fl.h`` only: every step of the
+path runs in the library's CUDA kernels.  Arrays may be NumPy arrays (host
+memory) or CUDA ``torch.Tensor`` objects (device memory); PyTorch provides
+device memory and streams.  If the library cannot be loaded this module raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lock = threading.Lock()
+_lib = None
+
+FL_OK, FL_EINVAL, FL_ESTATE, FL_ENOMEM, FL_ECUDA, FL_ETIMEOUT = range(6)
+FL_MEM_HOST, FL_MEM_DEVICE = 0, 1
+
+EXPORTS = ("fl_graph_create", "fl_graph_destroy", "fl_build_sketches", "fl_sketch_stats",
+           "fl_export_sketches", "fl_export_ads", "fl_solve_create", "fl_solve_destroy",
+           "fl_compute_radii", "fl_open_facilities", "fl_assign_clients", "fl_objective",
+           "fl_solve_stats", "fl_status_str", "fl_last_error")
+
+
+class FLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[{status}] {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libflgpu.so (building it when missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise OSError(f"libflgpu.so not found at {_build.LIB}; run build()")
+        lib = ctypes.CDLL(_build.LIB)
+        i64, u64, vp, ci = ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
+        P64 = ctypes.POINTER(i64)
+        sig = {
+            "fl_graph_create": ([i64, vp, vp, i64, ci, vp, ctypes.POINTER(vp)], ci),
+            "fl_graph_destroy": ([vp], ci),
+            "fl_build_sketches": ([vp, ci, u64], ci),
+            "fl_sketch_stats": ([vp, P64, P64, P64, P64], ci),
+            "fl_export_sketches": ([vp, vp, vp, ci], ci),
+            "fl_export_ads": ([vp, vp, vp, vp, vp, vp, vp, vp, ci], ci),
+            "fl_solve_create": ([vp, ctypes.POINTER(vp)], ci),
+            "fl_solve_destroy": ([vp], ci),
+            "fl_compute_radii": ([vp, vp, vp, ci, vp], ci),
+            "fl_open_facilities": ([vp, vp, P64, ci], ci),
+            "fl_assign_clients": ([vp, vp, vp, ci], ci),
+            "fl_objective": ([vp, ctypes.POINTER(ctypes.c_double), P64, P64], ci),
+            "fl_solve_stats": ([vp, P64, P64], ci),
+            "fl_status_str": ([ci], ctypes.c_char_p),
+            "fl_last_error": ([ctypes.c_char_p, ctypes.c_size_t], ci),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != FL_OK:
+        lib = load(False)
+        buf = ctypes.create_string_buffer(1024)
+        lib.fl_last_error(buf, 1024)
+        raise FLError(rc, f"{lib.fl_status_str(rc).decode()}: {buf.value.decode(errors='replace')}")
+
+
+def _arg(a, dtype=None):
+    """(pointer, mem_kind, keepalive) for a NumPy array or a CUDA tensor; None -> NULL."""
+    if a is None:
+        return None, None, None
+    if isinstance(a, np.ndarray):
+        if dtype is not None and a.dtype != dtype:
+            raise TypeError(f"expected {np.dtype(dtype)}, got {a.dtype}")
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data_as(ctypes.c_void_p), FL_MEM_HOST, a
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        kind = FL_MEM_DEVICE if a.is_cuda else FL_MEM_HOST
+        return ctypes.c_void_p(a.data_ptr()), kind, a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _kind(*kinds):
+    ks = {k for k in kinds if k is not None}
+    if len(ks) > 1:
+        raise ValueError("all arrays of one call must live in the same memory (host or device)")
+    return ks.pop() if ks else FL_MEM_HOST
+
+
+class Graph:
+    """fl_graph: a CSR graph on the device with its sketches and ADS."""
+
+    def __init__(self, rowp, cols, stream=None):
+        self._lib = load()
+        p_r, k_r, _ = _arg(rowp, np.int64)
+        p_c, k_c, _ = _arg(cols, np.int32)
+        kind = _kind(k_r, k_c)
+        self.n = int(len(rowp) - 1)
+        self.nnz = int(len(cols))
+        st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
+        h = ctypes.c_void_p()
+        _check(self._lib.fl_graph_create(self.n, p_r, p_c, self.nnz, kind, st, ctypes.byref(h)))
+        self._h = h
+        self.k = None
+        self.seed = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fl_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_sketches(self, k: int, seed: int):
+        _check(self._lib.fl_build_sketches(self._h, k, seed))
+        self.k, self.seed = k, seed
+
+    def stats(self) -> dict:
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(self._lib.fl_sketch_stats(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(hops=v[0].value, edge_merges=v[1].value, ads_entries=v[2].value, ads_groups=v[3].value)
+
+    def export_sketches(self):
+        S = np.zeros((self.n, self.k), np.uint64)
+        cnt = np.zeros(self.n, np.int32)
+        _check(self._lib.fl_export_sketches(self._h, _arg(S)[0], _arg(cnt)[0], FL_MEM_HOST))
+        return S, cnt
+
+    def export_ads(self) -> dict:
+        st = self.stats()
+        ng, ne = st["ads_groups"], st["ads_entries"]
+        out = dict(gofs=np.zeros(self.n + 1, np.int64), eofs=np.zeros(self.n + 1, np.int64),
+                   ghop=np.zeros(ng, np.int32), gcnt=np.zeros(ng, np.int32),
+                   gcounted=np.zeros(ng, np.int32), gwt=np.zeros(ng, np.float64),
+                   eid=np.zeros(ne, np.int32))
+        _check(self._lib.fl_export_ads(self._h, *[_arg(out[k])[0] for k in
+                                                  ("gofs", "eofs", "ghop", "gcnt", "gcounted", "gwt", "eid")],
+                                       FL_MEM_HOST))
+        return out
+
+
+class Solve:
+    """fl_solve: one facility-location instance on a built graph."""
+
+    def __init__(self, graph: Graph):
+        self._lib = load()
+        self.graph = graph
+        h = ctypes.c_void_p()
+        _check(self._lib.fl_solve_create(graph.handle, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fl_solve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def compute_radii(self, cost, client, radii_out=None):
+        """Phase (ii).  Returns radii_out (allocated on the host when None)."""
+        p_c, k_c, _ = _arg(cost, np.float64)
+        p_m, k_m, _ = _arg(client, np.uint8)
+        if radii_out is None and k_c != FL_MEM_DEVICE:
+            radii_out = np.zeros(self.graph.n, np.float64)
+        p_r, k_r, _ = _arg(radii_out)
+        _check(self._lib.fl_compute_radii(self._h, p_c, p_m, _kind(k_c, k_m, k_r), p_r))
+        return radii_out
+
+    def open_facilities(self, open_out=None):
+        """Phase (iii).  Returns (open mask, number opened)."""
+        if open_out is None:
+            open_out = np.zeros(self.graph.n, np.uint8)
+        p, k, _ = _arg(open_out)
+        nopen = ctypes.c_int64()
+        _check(self._lib.fl_open_facilities(self._h, p, ctypes.byref(nopen), k))
+        return open_out, nopen.value
+
+    def assign_clients(self, assign_out=None, dist_out=None):
+        if assign_out is None and dist_out is None:
+            assign_out = np.zeros(self.graph.n, np.int32)
+            dist_out = np.zeros(self.graph.n, np.int32)
+        pa, ka, _ = _arg(assign_out)
+        pd, kd, _ = _arg(dist_out)
+        _check(self._lib.fl_assign_clients(self._h, pa, pd, _kind(ka, kd)))
+        return assign_out, dist_out
+
+    def objective(self):
+        obj, ds, un = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        _check(self._lib.fl_objective(self._h, ctypes.byref(obj), ctypes.byref(ds), ctypes.byref(un)))
+        return obj.value, ds.value, un.value
+
+    def stats(self) -> dict:
+        r, c = ctypes.c_int64(), ctypes.c_int64()
+        _check(self._lib.fl_solve_stats(self._h, ctypes.byref(r), ctypes.byref(c)))
+        return dict(mis_rounds=r.value, candidates=c.value)
+
+
+def solve(rowp, cols, k, seed, cost, client, stream=None) -> dict:
+    """The whole path through the C ABI with host arrays; returns every output."""
+    g = Graph(rowp, cols, stream)
+    g.build_sketches(k, seed)
+    s = Solve(g)
+    r = s.compute_radii(cost, client)
+    op, nopen = s.open_facilities()
+    a, d = s.assign_clients()
+    obj, ds, un = s.objective()
+    return dict(graph=g, solve=s, stats=g.stats(), radii=r, open=op, n_open=nopen, assign=a, dist=d,
+                objective=obj, dist_sum=ds, n_unserved=un, mis=s.stats())

@@ -1,0 +1,287 @@
+// fl_capi.cu -- the extern "C" entry points declared in include/fl.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fl_internal.cuh"
+
+namespace fl {
+int last_error(char* buf, size_t len);
+}
+
+using namespace fl;
+
+namespace {
+
+cudaMemcpyKind kind_in(int mem_kind) {
+    return mem_kind == FL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+cudaMemcpyKind kind_out(int mem_kind) {
+    return mem_kind == FL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+bool bad_kind(int mem_kind) { return mem_kind != FL_MEM_HOST && mem_kind != FL_MEM_DEVICE; }
+
+int copy_out(void* dst, const void* src, size_t bytes, int mem_kind, cudaStream_t st) {
+    if (!dst || bytes == 0) return FL_OK;
+    FL_CUDA(cudaMemcpyAsync(dst, src, bytes, kind_out(mem_kind), st));
+    return FL_OK;
+}
+
+void destroy_graph(fl_graph* g) {
+    DBuf* bufs[] = {&g->rowp, &g->cols, &g->deg_list, &g->S, &g->Scnt, &g->D[0], &g->D[1], &g->Dcnt[0],
+                    &g->Dcnt[1], &g->frontier[0], &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent,
+                    &g->stg_grp, &g->stg_wt, &g->gofs, &g->eofs, &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub,
+                    &g->ctr, &g->scratch};
+    for (DBuf* b : bufs) dfree(*b);
+    if (g->h_ctr) cudaFreeHost(g->h_ctr);
+    delete g;
+}
+
+void destroy_solve(fl_solve* s) {
+    DBuf* bufs[] = {&s->cost, &s->client, &s->radii, &s->ord, &s->fac_by_ord, &s->bcap, &s->state, &s->claimed,
+                    &s->X, &s->stamp, &s->mval, &s->fr[0], &s->fr[1], &s->frval, &s->touched, &s->ulist,
+                    &s->ubuck, &s->bcount, &s->open, &s->assign, &s->dist};
+    for (DBuf* b : bufs) dfree(*b);
+    delete s;
+}
+
+int check_solve(fl_solve* s) {
+    if (!s || !s->g) FL_FAIL(FL_EINVAL, "null solve handle");
+    if (!s->g->built || s->generation != s->g->generation)
+        FL_FAIL(FL_ESTATE, "the graph's sketches were rebuilt after this solve was created");
+    return FL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fl_status_str(int status) {
+    switch (status) {
+        case FL_OK: return "ok";
+        case FL_EINVAL: return "invalid argument";
+        case FL_ESTATE: return "call out of order";
+        case FL_ENOMEM: return "out of memory";
+        case FL_ECUDA: return "CUDA error";
+        case FL_ETIMEOUT: return "iteration limit reached";
+        default: return "unknown status";
+    }
+}
+
+int fl_last_error(char* buf, size_t len) { return fl::last_error(buf, len); }
+
+int fl_graph_create(int64_t n, const int64_t* row_off, const int32_t* cols, int64_t nnz, int mem_kind,
+                    void* stream, fl_graph** out) {
+    if (!out) FL_FAIL(FL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 2147483647LL) FL_FAIL(FL_EINVAL, "n must be in [1, 2^31-1]");
+    if (nnz < 0 || !row_off || (nnz > 0 && !cols)) FL_FAIL(FL_EINVAL, "bad CSR arrays");
+    if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    fl_graph* g = new (std::nothrow) fl_graph();
+    if (!g) FL_FAIL(FL_ENOMEM, "host allocation failed");
+    g->n = n;
+    g->nnz = nnz;
+    g->stream = static_cast<cudaStream_t>(stream);
+    int rc = FL_OK;
+    do {
+        cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&g->h_ctr), sizeof(Counters));
+        if (e != cudaSuccess) { rc = status_of(e, "cudaMallocHost", __FILE__, __LINE__); break; }
+        if ((rc = dalloc(g->ctr, sizeof(Counters)))) break;
+        if ((rc = dalloc(g->rowp, (size_t)(n + 1) * 8))) break;
+        if ((rc = dalloc(g->cols, (size_t)(nnz > 0 ? nnz : 1) * 4))) break;
+        e = cudaMemcpyAsync(g->rowp.p, row_off, (size_t)(n + 1) * 8, kind_in(mem_kind), g->stream);
+        if (e == cudaSuccess && nnz > 0)
+            e = cudaMemcpyAsync(g->cols.p, cols, (size_t)nnz * 4, kind_in(mem_kind), g->stream);
+        if (e != cudaSuccess) { rc = status_of(e, "CSR upload", __FILE__, __LINE__); break; }
+        if ((rc = validate_csr(g))) break;
+        if ((rc = build_nonisolated_list(g))) break;
+    } while (0);
+    if (rc != FL_OK) {
+        destroy_graph(g);
+        return rc;
+    }
+    *out = g;
+    return FL_OK;
+}
+
+int fl_graph_destroy(fl_graph* g) {
+    if (!g) return FL_OK;
+    cudaStreamSynchronize(g->stream);
+    destroy_graph(g);
+    return FL_OK;
+}
+
+int fl_build_sketches(fl_graph* g, int k, uint64_t seed) {
+    if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    if (k < 2 || k > 32) FL_FAIL(FL_EINVAL, "k must be in [2, 32]");
+    return build_sketches(g, k, seed);
+}
+
+int fl_sketch_stats(const fl_graph* g, int64_t* hops, int64_t* edge_merges, int64_t* ads_entries,
+                    int64_t* ads_groups) {
+    if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    if (!g->built) FL_FAIL(FL_ESTATE, "sketches not built");
+    if (hops) *hops = g->hops;
+    if (edge_merges) *edge_merges = g->edge_merges;
+    if (ads_entries) *ads_entries = g->n_entries;
+    if (ads_groups) *ads_groups = g->n_groups;
+    return FL_OK;
+}
+
+__global__ void k_export_sketch(const uint64_t* __restrict__ S, const uint8_t* __restrict__ Scnt, int64_t n,
+                                int32_t* __restrict__ cnt) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) cnt[v] = Scnt[v];
+}
+
+__global__ void k_unpack_ginfo(const uint32_t* __restrict__ ginfo, int64_t m, int32_t* __restrict__ hop,
+                               int32_t* __restrict__ cnt, int32_t* __restrict__ counted) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        uint32_t x = ginfo[i];
+        if (hop) hop[i] = (int32_t)(x & 0xffffu);
+        if (cnt) cnt[i] = (int32_t)((x >> 16) & 0xffu);
+        if (counted) counted[i] = (int32_t)(x >> 24);
+    }
+}
+
+int fl_export_sketches(fl_graph* g, uint64_t* S, int32_t* cnt, int mem_kind) {
+    if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    if (!g->built) FL_FAIL(FL_ESTATE, "sketches not built");
+    if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    cudaStream_t st = g->stream;
+    FL_TRY(copy_out(S, g->S.p, (size_t)g->n * g->k * 8, mem_kind, st));
+    if (cnt) {
+        DBuf tmp;
+        FL_TRY(dalloc(tmp, (size_t)g->n * 4));
+        k_export_sketch<<<152 * 4, 256, 0, st>>>(g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->n,
+                                                 tmp.as<int32_t>());
+        int rc = copy_out(cnt, tmp.p, (size_t)g->n * 4, mem_kind, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        dfree(tmp);
+        if (rc) return rc;
+        if (e != cudaSuccess) return status_of(e, "export sketches", __FILE__, __LINE__);
+    }
+    FL_CUDA(cudaStreamSynchronize(st));
+    return FL_OK;
+}
+
+int fl_export_ads(fl_graph* g, int64_t* gofs, int64_t* eofs, int32_t* ghop, int32_t* gcnt, int32_t* gcounted,
+                  double* gwt, int32_t* eid, int mem_kind) {
+    if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    if (!g->built) FL_FAIL(FL_ESTATE, "sketches not built");
+    if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    cudaStream_t st = g->stream;
+    FL_TRY(copy_out(gofs, g->gofs.p, (size_t)(g->n + 1) * 8, mem_kind, st));
+    FL_TRY(copy_out(eofs, g->eofs.p, (size_t)(g->n + 1) * 8, mem_kind, st));
+    FL_TRY(copy_out(gwt, g->gwt.p, (size_t)g->n_groups * 8, mem_kind, st));
+    FL_TRY(copy_out(eid, g->eid.p, (size_t)g->n_entries * 4, mem_kind, st));
+    if (ghop || gcnt || gcounted) {
+        DBuf tmp;
+        const size_t m = (size_t)g->n_groups;
+        FL_TRY(dalloc(tmp, m * 12 + 16));
+        int32_t* h = tmp.as<int32_t>();
+        k_unpack_ginfo<<<152 * 4, 256, 0, st>>>(g->ginfo.as<uint32_t>(), (int64_t)m, h, h + m, h + 2 * m);
+        int rc = copy_out(ghop, h, m * 4, mem_kind, st);
+        if (!rc) rc = copy_out(gcnt, h + m, m * 4, mem_kind, st);
+        if (!rc) rc = copy_out(gcounted, h + 2 * m, m * 4, mem_kind, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        dfree(tmp);
+        if (rc) return rc;
+        if (e != cudaSuccess) return status_of(e, "export ADS", __FILE__, __LINE__);
+    }
+    FL_CUDA(cudaStreamSynchronize(st));
+    return FL_OK;
+}
+
+int fl_solve_create(fl_graph* g, fl_solve** out) {
+    if (!out) FL_FAIL(FL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    if (!g->built) FL_FAIL(FL_ESTATE, "build the sketches before creating a solve");
+    fl_solve* s = new (std::nothrow) fl_solve();
+    if (!s) FL_FAIL(FL_ENOMEM, "host allocation failed");
+    s->g = g;
+    s->generation = g->generation;
+    int rc = dalloc(s->cost, (size_t)g->n * 8);
+    if (!rc) rc = dalloc(s->client, (size_t)g->n);
+    if (!rc) rc = dalloc(s->radii, (size_t)g->n * 8);
+    if (rc) {
+        destroy_solve(s);
+        return rc;
+    }
+    *out = s;
+    return FL_OK;
+}
+
+int fl_solve_destroy(fl_solve* s) {
+    if (!s) return FL_OK;
+    if (s->g) cudaStreamSynchronize(s->g->stream);
+    destroy_solve(s);
+    return FL_OK;
+}
+
+int fl_compute_radii(fl_solve* s, const double* open_cost, const uint8_t* client_mask, int mem_kind,
+                     double* radii_out) {
+    FL_TRY(check_solve(s));
+    if (!open_cost || !client_mask) FL_FAIL(FL_EINVAL, "open_cost and client_mask are required");
+    if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    fl_graph* g = s->g;
+    cudaStream_t st = g->stream;
+    s->have_radii = s->have_open = s->have_assign = 0;
+    FL_CUDA(cudaMemcpyAsync(s->cost.p, open_cost, (size_t)g->n * 8, kind_in(mem_kind), st));
+    FL_CUDA(cudaMemcpyAsync(s->client.p, client_mask, (size_t)g->n, kind_in(mem_kind), st));
+    FL_TRY(compute_radii(s));
+    FL_TRY(copy_out(radii_out, s->radii.p, (size_t)g->n * 8, mem_kind, st));
+    FL_CUDA(cudaStreamSynchronize(st));
+    s->have_radii = 1;
+    return FL_OK;
+}
+
+int fl_open_facilities(fl_solve* s, uint8_t* open_out, int64_t* n_open, int mem_kind) {
+    FL_TRY(check_solve(s));
+    if (!s->have_radii) FL_FAIL(FL_ESTATE, "compute radii first");
+    if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    s->have_open = s->have_assign = 0;
+    FL_TRY(open_facilities(s));
+    FL_TRY(copy_out(open_out, s->open.p, (size_t)s->g->n, mem_kind, s->g->stream));
+    FL_CUDA(cudaStreamSynchronize(s->g->stream));
+    if (n_open) *n_open = s->n_open;
+    s->have_open = 1;
+    return FL_OK;
+}
+
+int fl_assign_clients(fl_solve* s, int32_t* assign_out, int32_t* dist_out, int mem_kind) {
+    FL_TRY(check_solve(s));
+    if (!s->have_open) FL_FAIL(FL_ESTATE, "open facilities first");
+    if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    FL_TRY(assign_clients(s));
+    FL_TRY(copy_out(assign_out, s->assign.p, (size_t)s->g->n * 4, mem_kind, s->g->stream));
+    FL_TRY(copy_out(dist_out, s->dist.p, (size_t)s->g->n * 4, mem_kind, s->g->stream));
+    FL_CUDA(cudaStreamSynchronize(s->g->stream));
+    s->have_assign = 1;
+    return FL_OK;
+}
+
+int fl_objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserved) {
+    FL_TRY(check_solve(s));
+    if (!s->have_assign) FL_FAIL(FL_ESTATE, "assign clients first");
+    double o = 0.0;
+    int64_t ds = 0, un = 0;
+    FL_TRY(objective(s, &o, &ds, &un));
+    if (obj) *obj = o;
+    if (dist_sum) *dist_sum = ds;
+    if (n_unserved) *n_unserved = un;
+    return FL_OK;
+}
+
+int fl_solve_stats(const fl_solve* s, int64_t* mis_rounds, int64_t* candidates) {
+    if (!s) FL_FAIL(FL_EINVAL, "null solve handle");
+    if (mis_rounds) *mis_rounds = s->mis_rounds;
+    if (candidates) *candidates = s->n_cand;
+    return FL_OK;
+}
+
+}  // extern "C"

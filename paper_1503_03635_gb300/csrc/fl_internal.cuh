@@ -1,0 +1,287 @@
+// fl_internal.cuh -- shared internals of libflgpu (handles, errors, warp primitives).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/fl.h"
+
+namespace fl {
+
+// ----------------------------------------------------------------- errors
+
+void set_error(int status, const std::string& msg);
+int status_of(cudaError_t e, const char* what, const char* file, int line);
+
+#define FL_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t e__ = (call);                                                  \
+        if (e__ != cudaSuccess) return ::fl::status_of(e__, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define FL_TRY(expr)                 \
+    do {                             \
+        int s__ = (expr);            \
+        if (s__ != FL_OK) return s__; \
+    } while (0)
+
+#define FL_FAIL(code, msg)               \
+    do {                                 \
+        ::fl::set_error((code), (msg));  \
+        return (code);                   \
+    } while (0)
+
+// ----------------------------------------------------------------- device buffers
+
+struct DBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+int dalloc(DBuf& b, size_t bytes);            // free + allocate (no copy)
+int dgrow(DBuf& b, size_t bytes, size_t keep, cudaStream_t st);  // grow keeping `keep` bytes
+void dfree(DBuf& b);
+
+// ----------------------------------------------------------------- constants
+
+constexpr uint64_t kGamma = 0x9e3779b97f4a7c15ULL;   // SplitMix64 increment
+constexpr uint64_t kMul1 = 0xbf58476d1ce4e5b9ULL;
+constexpr uint64_t kMul2 = 0x94d049bb133111ebULL;
+constexpr uint64_t kEmpty = ~0ULL;                   // empty sketch slot
+
+__host__ __device__ constexpr uint64_t inv_odd(uint64_t a) {
+    // Newton iteration for the inverse of an odd number mod 2^64
+    uint64_t x = a;
+    for (int i = 0; i < 6; ++i) x *= 2 - a * x;
+    return x;
+}
+
+// SplitMix64 finaliser and its inverse (each step is a bijection on 64 bits).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * kMul1;
+    z = (z ^ (z >> 27)) * kMul2;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t unmix64(uint64_t y) {
+    y = y ^ (y >> 31) ^ (y >> 62);
+    y *= inv_odd(kMul2);
+    y = y ^ (y >> 27) ^ (y >> 54);
+    y *= inv_odd(kMul1);
+    return y ^ (y >> 30) ^ (y >> 60);
+}
+// r(v): SplitMix64 output v+1 from state `seed`.
+__host__ __device__ __forceinline__ uint64_t vertex_rank(uint64_t seed, int64_t v) {
+    return mix64(seed + (uint64_t)(v + 1) * kGamma);
+}
+// the vertex whose rank is x (ranks are a bijection of the counter)
+__host__ __device__ __forceinline__ int64_t rank_vertex(uint64_t seed, uint64_t x) {
+    return (int64_t)((unmix64(x) - seed) * inv_odd(kGamma) - 1);
+}
+// pi(f): SplitMix64 output f+1 from the state given by the first output for `seed`.
+__host__ __device__ __forceinline__ uint64_t facility_priority(uint64_t seed, int64_t f) {
+    uint64_t stream = mix64(seed + kGamma);
+    return mix64(stream + (uint64_t)(f + 1) * kGamma);
+}
+
+// ----------------------------------------------------------------- warp primitives
+// A "lane list" holds up to 32 uint64 values, one per lane, ascending by lane,
+// padded with kEmpty.
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < b ? b : a; }
+
+// Bitonic sort of one value per lane, ascending across lanes.
+__device__ __forceinline__ uint64_t warp_sort(uint64_t x) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            uint64_t y = __shfl_xor_sync(kFull, x, j);
+            bool up = (lane & k) == 0 || k == 32;
+            bool low = (lane & j) == 0;
+            x = (low == up) ? umin64(x, y) : umax64(x, y);
+        }
+    }
+    return x;
+}
+
+// The 32 smallest of two ascending lane lists, ascending (bitonic merge).
+__device__ __forceinline__ uint64_t warp_merge_low(uint64_t a, uint64_t b) {
+    const int lane = lane_id();
+    uint64_t br = __shfl_sync(kFull, b, 31 - lane);
+    uint64_t c = umin64(a, br);
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+        uint64_t y = __shfl_xor_sync(kFull, c, j);
+        c = (lane & j) ? umax64(c, y) : umin64(c, y);
+    }
+    return c;
+}
+
+// Number of entries of ascending lane list L that are < x (0..32).
+__device__ __forceinline__ int warp_lower_bound(uint64_t L, uint64_t x) {
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        uint64_t y = __shfl_sync(kFull, L, pos + s - 1);
+        if (y < x) pos += s;
+    }
+    uint64_t last = __shfl_sync(kFull, L, 31);
+    if (pos == 31 && last < x) pos = 32;
+    return pos;
+}
+
+// Is x one of the entries of ascending lane list L?
+__device__ __forceinline__ bool warp_member(uint64_t L, uint64_t x) {
+    int pos = warp_lower_bound(L, x);
+    uint64_t y = __shfl_sync(kFull, L, pos & 31);
+    return pos < 32 && y == x;
+}
+
+// Position of the n-th (0-based) set bit of m (m must have > n set bits).
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        unsigned low = m & ((1u << s) - 1u);
+        int c = __popc(low);
+        if (n >= c) {
+            n -= c;
+            m >>= s;
+            pos += s;
+        } else {
+            m = low;
+        }
+    }
+    return pos;
+}
+
+// Gather the values of lanes in `keep` to lanes 0..popc(keep)-1 (order kept),
+// the rest get `fill`.
+__device__ __forceinline__ uint64_t warp_compact(uint64_t x, unsigned keep, uint64_t fill) {
+    const int lane = lane_id();
+    int total = __popc(keep);
+    int src = lane < total ? nth_set_bit(keep, lane) : 0;
+    uint64_t y = __shfl_sync(kFull, x, src);
+    return lane < total ? y : fill;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int x) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        int y = __shfl_up_sync(kFull, x, s);
+        if (lane >= s) x += y;
+    }
+    return x;
+}
+
+// Warp-aggregated append: every lane with `pred` gets a distinct slot index
+// from `counter` (one atomic per warp); lanes without it get -1.  All 32
+// lanes must call it.
+__device__ __forceinline__ long long warp_append(bool pred, unsigned long long* counter) {
+    const int lane = lane_id();
+    unsigned m = __ballot_sync(kFull, pred);
+    if (!m) return -1;
+    int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    return pred ? (long long)(base + __popc(m & ((1u << lane) - 1u))) : -1LL;
+}
+
+// ----------------------------------------------------------------- device counters
+
+// Small block of device counters read back by the host between launches.
+struct Counters {
+    unsigned long long frontier;     // vertices appended to the next frontier
+    unsigned long long active;       // vertices in the active list of a hop
+    unsigned long long stg_entries;  // ADS staging entries used
+    unsigned long long stg_groups;   // ADS staging groups used
+    unsigned long long merges;       // edge-merges of the next hop (sum of deg of frontier)
+    unsigned long long error;        // nonzero: a kernel detected a bad input
+    unsigned long long aux0, aux1, aux2, aux3;
+};
+
+// ----------------------------------------------------------------- handles
+
+}  // namespace fl
+
+struct fl_graph {
+    int64_t n = 0, nnz = 0;
+    cudaStream_t stream = nullptr;
+    fl::DBuf rowp, cols;           // int64[n+1], int32[nnz]
+    fl::DBuf deg_list;             // int32[n]: non-isolated vertices (static active list)
+    int64_t n_nonisolated = 0;
+    // sketches
+    int k = 0;
+    uint64_t seed = 0;
+    int built = 0;
+    uint64_t generation = 0;       // bumped by every build
+    fl::DBuf S, Scnt;              // uint64[n*k], uint8[n]
+    fl::DBuf D[2], Dcnt[2];        // hop deltas (ranks), counts
+    fl::DBuf frontier[2];          // int32[n]
+    fl::DBuf stamp;                // uint32[n]
+    fl::DBuf vg, ve;               // int32[n] per-vertex running group / entry counts
+    fl::DBuf stg_ent;              // int32 staging entries
+    fl::DBuf stg_grp;              // staging group records
+    fl::DBuf stg_wt;               // double staging weights
+    size_t stg_ent_cap = 0, stg_grp_cap = 0;
+    // ADS (vertex-major)
+    fl::DBuf gofs, eofs;           // int64[n+1]
+    fl::DBuf ginfo, gwt, eid;      // uint32[G], double[G], int32[E]
+    int64_t hops = 0, edge_merges = 0, n_entries = 0, n_groups = 0;
+    // per-vertex eccentricity upper bound (caps ball radii; balls unchanged)
+    fl::DBuf ecc_ub;               // int32[n]
+    // counters + scratch
+    fl::DBuf ctr;                  // Counters
+    fl::Counters* h_ctr = nullptr; // pinned host mirror
+    fl::DBuf scratch;              // general scratch (scans, sorts)
+};
+
+struct fl_solve {
+    fl_graph* g = nullptr;
+    uint64_t generation = 0;
+    int have_radii = 0, have_open = 0, have_assign = 0;
+    fl::DBuf cost, client;         // double[n], uint8[n]
+    fl::DBuf radii;                // double[n]
+    fl::DBuf ord, fac_by_ord, bcap, state, claimed;  // MIS state
+    fl::DBuf X, stamp, mval, fr[2], frval, touched, ulist, ubuck, bcount;
+    fl::DBuf open;                 // uint8[n]
+    fl::DBuf assign, dist;         // int32[n]
+    int64_t n_cand = 0, n_open = 0, mis_rounds = 0;
+};
+
+namespace fl {
+
+// ----------------------------------------------------------------- kernel launchers
+// (implemented in the .cu files; all run on g->stream)
+
+int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st, DBuf& tmp);
+int scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st, DBuf& tmp);
+int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaStream_t st, DBuf& tmp);
+
+int validate_csr(fl_graph* g);
+int build_nonisolated_list(fl_graph* g);
+int build_sketches(fl_graph* g, int k, uint64_t seed);
+int compute_ecc_bound(fl_graph* g);
+
+int compute_radii(fl_solve* s);
+int open_facilities(fl_solve* s);
+int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, int32_t* dist,
+          DBuf& X, DBuf& stampb, DBuf* fr, DBuf& frval);
+int assign_clients(fl_solve* s);
+int objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserved);
+
+int read_counters(fl_graph* g);
+
+}  // namespace fl

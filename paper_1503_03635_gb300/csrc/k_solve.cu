@@ -1,0 +1,641 @@
+// k_solve.cu -- phases (ii) and (iii) plus assignment and objective:
+//   radius solve (Eq. 1 at epsilon -> 0 from predicated HIP estimates),
+//   key ordinals (r_f, pi_f), greedy-MIS rounds on the implicit conflict
+//   graph H-bar (Section 3.3, Algorithm 6), nearest-open-facility BFS and
+//   the objective (Section 3.1).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "fl_internal.cuh"
+
+namespace fl {
+
+static int grid_for(int64_t items, int per_block) {
+    int64_t b = (items + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+// ------------------------------------------------------------------ frontier propagation
+// A frontier is a list of vertices with a device-side count.  One round:
+// snapshot (copy each frontier vertex's value, so a round moves values exactly
+// one hop), then push: for every edge (v, u), X[u] = min(X[u], val(v) + add);
+// u joins the next frontier the first time it decreases in the round.
+
+__global__ void k_snapshot(const int32_t* __restrict__ fr, const unsigned long long* __restrict__ n_fr,
+                           const unsigned long long* __restrict__ X, unsigned long long* __restrict__ frval,
+                           unsigned long long* __restrict__ reset_next,
+                           uint32_t* __restrict__ tstamp, uint32_t tval, int32_t* __restrict__ touched,
+                           unsigned long long* __restrict__ n_touched) {
+    const int64_t n = (int64_t)*n_fr;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *reset_next = 0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        int64_t i = base + lane_id();
+        bool fresh = false;
+        int32_t v = 0;
+        if (i < n) {
+            v = fr[i];
+            frval[i] = X[v];
+            if (tstamp) fresh = atomicExch(&tstamp[v], tval) != tval;
+        }
+        if (tstamp) {
+            long long at = warp_append(fresh, n_touched);
+            if (at >= 0) touched[at] = v;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_push(const int32_t* __restrict__ fr, const unsigned long long* __restrict__ frval,
+                                              const unsigned long long* __restrict__ n_fr,
+                                              const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
+                                              unsigned long long add, unsigned long long* __restrict__ X,
+                                              uint32_t* __restrict__ stamp, uint32_t sv, int32_t* __restrict__ fr_next,
+                                              unsigned long long* __restrict__ n_next) {
+    const int lane = lane_id();
+    const int64_t n = (int64_t)*n_fr;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; w < n; w += warps) {
+        const int32_t v = fr[w];
+        const unsigned long long val = frval[w] + add;
+        const int64_t beg = rowp[v], end = rowp[v + 1];
+        for (int64_t cb = beg; cb < end; cb += 32) {
+            int64_t e = cb + lane;
+            bool fresh = false;
+            int32_t u = 0;
+            if (e < end) {
+                u = cols[e];
+                if (val < X[u]) {
+                    unsigned long long old = atomicMin(&X[u], val);
+                    if (val < old) fresh = atomicExch(&stamp[u], sv) != sv;
+                }
+            }
+            long long at = warp_append(fresh, n_next);
+            if (at >= 0) fr_next[at] = u;
+        }
+    }
+}
+
+// Seeds: X[s] = min(X[s], val(s)); s joins the frontier when it decreases.
+__global__ void k_inject(const int32_t* __restrict__ src, int64_t n_src, const unsigned long long* __restrict__ base_val,
+                         unsigned long long hi, const uint32_t* __restrict__ lo_of, unsigned long long* __restrict__ X,
+                         uint32_t* __restrict__ stamp, uint32_t sv, int32_t* __restrict__ fr,
+                         unsigned long long* __restrict__ n_fr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_src; base += stride) {
+        int64_t i = base + lane_id();
+        bool fresh = false;
+        int32_t s = 0;
+        if (i < n_src) {
+            s = src[i];
+            unsigned long long val = (hi << 32) | (lo_of ? lo_of[s] : (uint32_t)s);
+            unsigned long long old = atomicMin(&X[s], val);
+            if (val < old) fresh = atomicExch(&stamp[s], sv) != sv;
+        }
+        long long at = warp_append(fresh, n_fr);
+        if (at >= 0) fr[at] = s;
+    }
+}
+
+// ------------------------------------------------------------------ multi-source BFS
+// Level-synchronous BFS from a source list; X[v] = (dist << 32) | label, and
+// atomicMin keeps the smallest label among the sources at the smallest
+// distance.  label/dist = -1 where no source is reachable.
+
+__global__ void k_unpack_bfs(const unsigned long long* __restrict__ X, int64_t n, int32_t* __restrict__ label,
+                             int32_t* __restrict__ dist) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        unsigned long long x = X[v];
+        bool none = x == ~0ULL;
+        if (label) label[v] = none ? -1 : (int32_t)(x & 0xffffffffULL);
+        if (dist) dist[v] = none ? -1 : (int32_t)(x >> 32);
+    }
+}
+
+int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, int32_t* dist, DBuf& X,
+          DBuf& stampb, DBuf* fr, DBuf& frval) {
+    const int64_t n = g->n;
+    cudaStream_t st = g->stream;
+    FL_TRY(dalloc(X, (size_t)n * 8));
+    FL_TRY(dalloc(stampb, (size_t)n * 4));
+    FL_TRY(dalloc(fr[0], (size_t)n * 4));
+    FL_TRY(dalloc(fr[1], (size_t)n * 4));
+    FL_TRY(dalloc(frval, (size_t)n * 8 + 64));
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(frval.as<char>() + (size_t)n * 8);
+    FL_CUDA(cudaMemsetAsync(X.p, 0xff, (size_t)n * 8, st));
+    FL_CUDA(cudaMemsetAsync(stampb.p, 0, (size_t)n * 4, st));
+    FL_CUDA(cudaMemsetAsync(cnt, 0, 64, st));
+    if (n_src > 0) {
+        k_inject<<<grid_for(n_src, 256), 256, 0, st>>>(src_list, n_src, nullptr, 0ULL, nullptr,
+                                                      X.as<unsigned long long>(), stampb.as<uint32_t>(), 1u,
+                                                      fr[0].as<int32_t>(), &cnt[0]);
+        FL_CUDA(cudaGetLastError());
+    }
+    int cur = 0;
+    int64_t n_cur = n_src;
+    uint32_t level = 0;
+    while (n_cur > 0) {
+        k_snapshot<<<grid_for(n_cur, 256), 256, 0, st>>>(fr[cur].as<int32_t>(), &cnt[cur],
+                                                        X.as<unsigned long long>(), frval.as<unsigned long long>(),
+                                                        &cnt[cur ^ 1], nullptr, 0, nullptr, nullptr);
+        k_push<<<grid_for(n_cur, 8), 256, 0, st>>>(fr[cur].as<int32_t>(), frval.as<unsigned long long>(), &cnt[cur],
+                                                  g->rowp.as<int64_t>(), g->cols.as<int32_t>(), 1ULL << 32,
+                                                  X.as<unsigned long long>(), stampb.as<uint32_t>(), level + 2,
+                                                  fr[cur ^ 1].as<int32_t>(), &cnt[cur ^ 1]);
+        FL_CUDA(cudaGetLastError());
+        unsigned long long nn = 0;
+        FL_CUDA(cudaMemcpyAsync(&nn, &cnt[cur ^ 1], 8, cudaMemcpyDeviceToHost, st));
+        FL_CUDA(cudaStreamSynchronize(st));
+        n_cur = (int64_t)nn;
+        cur ^= 1;
+        ++level;
+    }
+    k_unpack_bfs<<<grid_for(n, 256), 256, 0, st>>>(X.as<unsigned long long>(), n, label, dist);
+    FL_CUDA(cudaGetLastError());
+    return FL_OK;
+}
+
+// ------------------------------------------------------------------ radius (phase ii)
+
+__global__ void k_check_costs(const double* __restrict__ cost, int64_t n, Counters* ctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        double c = cost[v];
+        bool ok = (c > 0.0 && c < INFINITY) || c == INFINITY;  // rejects NaN, <= 0, -inf
+        if (!ok) atomicOr(&ctr->error, 1ULL);
+    }
+}
+
+// Warp per facility.  W_h = (#counted client entries of the hop-h group) x
+// weight; N_j = N_{j-1} + W_j; G_{j+1} = G_j + N_j; r = j + (c - G_j) / N_j at
+// the first j < L with G_{j+1} >= c, else L + (c - G_L) / N_L (L = last hop
+// of the ADS of f), +inf if N_L = 0.  Every operation is one IEEE-754 op in
+// this order (no contraction).
+__global__ void __launch_bounds__(256) k_radius(int64_t n, const double* __restrict__ cost,
+                                                const uint8_t* __restrict__ client,
+                                                const int64_t* __restrict__ gofs, const int64_t* __restrict__ eofs,
+                                                const uint32_t* __restrict__ ginfo, const double* __restrict__ gwt,
+                                                const int32_t* __restrict__ eid, double* __restrict__ r_out) {
+    const int lane = lane_id();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t f = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; f < n; f += warps) {
+        const double c = cost[f];
+        double res = INFINITY;
+        if (c < INFINITY) {
+            const int64_t g0 = gofs[f], g1 = gofs[f + 1];
+            const int L = (int)(ginfo[g1 - 1] & 0xffffu);
+            int64_t e = eofs[f];
+            double N = 0.0, G = 0.0;
+            int j = 0;
+            bool done = false;
+            for (int64_t gi = g0; gi < g1 && !done; ++gi) {
+                const uint32_t info = ginfo[gi];
+                const int hop = (int)(info & 0xffffu);
+                const int cnt = (int)((info >> 16) & 0xffu);
+                const int counted = (int)(info >> 24);
+                for (; j < hop; ++j) {  // hops without new entries: W_j = 0
+                    if (j < L) {
+                        double Gn = __dadd_rn(G, N);
+                        if (Gn >= c) {
+                            res = __dadd_rn((double)j, __ddiv_rn(__dsub_rn(c, G), N));
+                            done = true;
+                            break;
+                        }
+                        G = Gn;
+                    }
+                }
+                if (done) break;
+                bool is_client = lane < counted && client[eid[e + lane]] != 0;
+                int clients = __popc(__ballot_sync(kFull, is_client));
+                double W = __dmul_rn((double)clients, gwt[gi]);
+                N = __dadd_rn(N, W);
+                if (j < L) {
+                    double Gn = __dadd_rn(G, N);
+                    if (Gn >= c) {
+                        res = __dadd_rn((double)j, __ddiv_rn(__dsub_rn(c, G), N));
+                        done = true;
+                        break;
+                    }
+                    G = Gn;
+                }
+                ++j;
+                e += cnt;
+            }
+            if (!done) res = N > 0.0 ? __dadd_rn((double)L, __ddiv_rn(__dsub_rn(c, G), N)) : INFINITY;
+        }
+        if (lane == 0) r_out[f] = res;
+    }
+}
+
+int compute_radii(fl_solve* s) {
+    fl_graph* g = s->g;
+    cudaStream_t st = g->stream;
+    FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st));
+    k_check_costs<<<grid_for(g->n, 256), 256, 0, st>>>(s->cost.as<double>(), g->n, g->ctr.as<Counters>());
+    FL_CUDA(cudaGetLastError());
+    FL_TRY(read_counters(g));
+    if (g->h_ctr->error) FL_FAIL(FL_EINVAL, "open_cost must be finite and > 0 for facilities, +inf otherwise");
+    k_radius<<<grid_for(g->n, 8), 256, 0, st>>>(g->n, s->cost.as<double>(), s->client.as<uint8_t>(),
+                                               g->gofs.as<int64_t>(), g->eofs.as<int64_t>(), g->ginfo.as<uint32_t>(),
+                                               g->gwt.as<double>(), g->eid.as<int32_t>(), s->radii.as<double>());
+    FL_CUDA(cudaGetLastError());
+    return FL_OK;
+}
+
+// ------------------------------------------------------------------ keys (r_f, pi_f)
+
+__global__ void k_candidates(const double* __restrict__ r, int64_t n, uint64_t seed, uint64_t* __restrict__ hi,
+                             uint64_t* __restrict__ lo, uint32_t* __restrict__ val, uint8_t* __restrict__ state,
+                             Counters* ctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        int64_t f = base + lane_id();
+        bool cand = false;
+        double rf = 0.0;
+        if (f < n) {
+            rf = r[f];
+            cand = rf < INFINITY;
+            state[f] = cand ? 0 : 3;
+        }
+        long long at = warp_append(cand, &ctr->aux0);
+        if (at >= 0) {
+            hi[at] = (uint64_t)__double_as_longlong(rf);  // r >= 0: bit order = numeric order
+            lo[at] = facility_priority(seed, f);
+            val[at] = (uint32_t)f;
+        }
+    }
+}
+
+__global__ void k_ordinals(const uint32_t* __restrict__ sorted_f, int64_t m, const double* __restrict__ r,
+                           const int32_t* __restrict__ ecc_ub, uint32_t* __restrict__ ord,
+                           int32_t* __restrict__ fac_by_ord, int32_t* __restrict__ bcap, int32_t* __restrict__ ulist,
+                           unsigned long long* __restrict__ bmax) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        int32_t f = (int32_t)sorted_f[i];
+        ord[f] = (uint32_t)i;
+        fac_by_ord[i] = f;
+        ulist[i] = f;
+        // ball radius floor(r_f), capped by an eccentricity bound (same ball)
+        double fl = floor(r[f]);
+        int32_t cap = ecc_ub[f];
+        int32_t b = fl >= (double)cap ? cap : (int32_t)fl;
+        bcap[f] = b;
+        atomicMax(bmax, (unsigned long long)b);
+    }
+}
+
+// ------------------------------------------------------------------ MIS rounds (phase iii)
+
+__global__ void k_bucket_count(const int32_t* __restrict__ ulist, int64_t n_u, const int32_t* __restrict__ bcap,
+                               int32_t* __restrict__ bcount, unsigned long long* __restrict__ tmax) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_u; i += stride) {
+        int32_t b = bcap[ulist[i]];
+        atomicAdd(&bcount[b], 1);
+        atomicMax(tmax, (unsigned long long)b);
+    }
+}
+
+__global__ void k_bucket_scatter(const int32_t* __restrict__ ulist, int64_t n_u, const int32_t* __restrict__ bcap,
+                                 int32_t* __restrict__ cursor, int32_t* __restrict__ ubuck) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_u; i += stride) {
+        int32_t f = ulist[i];
+        ubuck[atomicAdd(&cursor[bcap[f]], 1)] = f;
+    }
+}
+
+// Gather seeds: every client covered in this round's cover sweep starts with
+// 0 if already claimed, else 1 + (smallest key of an undecided facility
+// covering it); mval keeps that smallest key for the claim step.
+__global__ void k_gather_seed(const int32_t* __restrict__ touched, const unsigned long long* __restrict__ n_touched,
+                              const uint8_t* __restrict__ client, const uint8_t* __restrict__ claimed,
+                              unsigned long long hi, unsigned long long* __restrict__ X, uint32_t* __restrict__ mval,
+                              uint32_t* __restrict__ stamp, uint32_t sv, int32_t* __restrict__ fr,
+                              unsigned long long* __restrict__ n_fr) {
+    const int64_t n = (int64_t)*n_touched;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        int64_t i = base + lane_id();
+        bool seed = false;
+        int32_t v = 0;
+        if (i < n) {
+            v = touched[i];
+            if (client[v]) {
+                uint32_t m = (uint32_t)(X[v] & 0xffffffffULL);
+                mval[v] = m;
+                X[v] = (hi << 32) | (claimed[v] ? 0ULL : (unsigned long long)m + 1ULL);
+                stamp[v] = sv;
+                seed = true;
+            }
+        }
+        long long at = warp_append(seed, n_fr);
+        if (at >= 0) fr[at] = v;
+    }
+}
+
+// Facilities whose ball radius is b read the minimum over their ball after
+// b gather rounds: 0 -> a client of the ball is claimed (dead); own key + 1
+// -> smallest key among all conflicting undecided facilities (joins S).
+__global__ void k_decide(const int32_t* __restrict__ fl, int64_t m, const unsigned long long* __restrict__ X,
+                         unsigned long long hi, const uint32_t* __restrict__ ord, uint8_t* __restrict__ state,
+                         Counters* ctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        int32_t f = fl[i];
+        unsigned long long x = X[f];
+        if ((x >> 32) != hi) {
+            atomicOr(&ctr->error, 8ULL);  // a candidate's ball holds no client (cannot happen)
+            continue;
+        }
+        uint32_t lo = (uint32_t)(x & 0xffffffffULL);
+        if (lo == 0) state[f] = 2;
+        else if (lo == ord[f] + 1u) state[f] = 1;
+    }
+}
+
+__global__ void k_claim(const int32_t* __restrict__ touched, const unsigned long long* __restrict__ n_touched,
+                        const uint8_t* __restrict__ client, uint8_t* __restrict__ claimed,
+                        const uint32_t* __restrict__ mval, const int32_t* __restrict__ fac_by_ord,
+                        const uint8_t* __restrict__ state) {
+    const int64_t n = (int64_t)*n_touched;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        int32_t v = touched[i];
+        if (client[v] && !claimed[v] && state[fac_by_ord[mval[v]]] == 1) claimed[v] = 1;
+    }
+}
+
+__global__ void k_compact_undecided(const int32_t* __restrict__ ulist, int64_t n_u, const uint8_t* __restrict__ state,
+                                    int32_t* __restrict__ out, unsigned long long* __restrict__ n_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_u; base += stride) {
+        int64_t i = base + lane_id();
+        int32_t f = i < n_u ? ulist[i] : 0;
+        bool keep = i < n_u && state[f] == 0;
+        long long at = warp_append(keep, n_out);
+        if (at >= 0) out[at] = f;
+    }
+}
+
+__global__ void k_open_list(const uint8_t* __restrict__ state, int64_t n, uint8_t* __restrict__ open,
+                            int32_t* __restrict__ list, unsigned long long* __restrict__ n_list) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        int64_t v = base + lane_id();
+        bool is_open = v < n && state[v] == 1;
+        if (v < n) open[v] = is_open ? 1 : 0;
+        long long at = warp_append(is_open, n_list);
+        if (at >= 0) list[at] = (int32_t)v;
+    }
+}
+
+int open_facilities(fl_solve* s) {
+    fl_graph* g = s->g;
+    const int64_t n = g->n;
+    cudaStream_t st = g->stream;
+    // -------- keys: candidates sorted by (r_f, pi_f) -> ordinals
+    FL_TRY(dalloc(s->ord, (size_t)n * 4));
+    FL_TRY(dalloc(s->fac_by_ord, (size_t)n * 4));
+    FL_TRY(dalloc(s->bcap, (size_t)n * 4));
+    FL_TRY(dalloc(s->state, (size_t)n));
+    FL_TRY(dalloc(s->claimed, (size_t)n));
+    FL_TRY(dalloc(s->X, (size_t)n * 8));
+    FL_TRY(dalloc(s->stamp, (size_t)n * 4 * 2));  // frontier stamps + touched stamps
+    FL_TRY(dalloc(s->mval, (size_t)n * 4));
+    FL_TRY(dalloc(s->fr[0], (size_t)n * 4));
+    FL_TRY(dalloc(s->fr[1], (size_t)n * 4));
+    FL_TRY(dalloc(s->frval, (size_t)n * 8 + 64));
+    FL_TRY(dalloc(s->touched, (size_t)n * 4));
+    FL_TRY(dalloc(s->ulist, (size_t)n * 4 * 2));
+    FL_TRY(dalloc(s->ubuck, (size_t)n * 4));
+    FL_TRY(dalloc(s->open, (size_t)n));
+    uint32_t* tstamp = s->stamp.as<uint32_t>() + n;
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(s->frval.as<char>() + (size_t)n * 8);
+    // cnt[0], cnt[1]: frontier counts; cnt[2]: touched; cnt[3]: undecided; cnt[4]: T max
+    DBuf hi, lo, val;
+    auto free_keys = [&]() { dfree(hi); dfree(lo); dfree(val); };
+    int rc = FL_OK;
+    if ((rc = dalloc(hi, (size_t)n * 8)) || (rc = dalloc(lo, (size_t)n * 8)) || (rc = dalloc(val, (size_t)n * 4))) {
+        free_keys();
+        return rc;
+    }
+    FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st));
+    k_candidates<<<grid_for(n, 256), 256, 0, st>>>(s->radii.as<double>(), n, g->seed, hi.as<uint64_t>(),
+                                                   lo.as<uint64_t>(), val.as<uint32_t>(), s->state.as<uint8_t>(),
+                                                   g->ctr.as<Counters>());
+    rc = read_counters(g);
+    if (rc) { free_keys(); return rc; }
+    const int64_t m = (int64_t)g->h_ctr->aux0;
+    s->n_cand = m;
+    rc = sort_pairs_u128(hi.as<uint64_t>(), lo.as<uint64_t>(), val.as<uint32_t>(), m, st, g->scratch);
+    if (rc) { free_keys(); return rc; }
+    int32_t* ulist[2] = {s->ulist.as<int32_t>(), s->ulist.as<int32_t>() + n};
+    FL_CUDA(cudaMemsetAsync(cnt, 0, 64, st));
+    if (m > 0) {
+        k_ordinals<<<grid_for(m, 256), 256, 0, st>>>(val.as<uint32_t>(), m, s->radii.as<double>(),
+                                                     g->ecc_ub.as<int32_t>(), s->ord.as<uint32_t>(),
+                                                     s->fac_by_ord.as<int32_t>(), s->bcap.as<int32_t>(), ulist[0],
+                                                     &cnt[4]);
+    }
+    free_keys();
+    FL_CUDA(cudaGetLastError());
+    unsigned long long bmax = 0;
+    FL_CUDA(cudaMemcpyAsync(&bmax, &cnt[4], 8, cudaMemcpyDeviceToHost, st));
+    FL_CUDA(cudaMemsetAsync(s->claimed.p, 0, (size_t)n, st));
+    FL_CUDA(cudaMemsetAsync(s->X.p, 0xff, (size_t)n * 8, st));
+    FL_CUDA(cudaMemsetAsync(s->stamp.p, 0, (size_t)n * 8, st));
+    FL_CUDA(cudaStreamSynchronize(st));
+    DBuf bcount_d;
+    FL_TRY(dalloc(bcount_d, (bmax + 2) * 4 * 2));
+    int32_t* bcount = bcount_d.as<int32_t>();
+    int32_t* cursor = bcount + (bmax + 2);
+    std::vector<int32_t> hcount(bmax + 2), hoff(bmax + 2);
+
+    unsigned long long* X = s->X.as<unsigned long long>();
+    uint32_t* stamp = s->stamp.as<uint32_t>();
+    int32_t* fr[2] = {s->fr[0].as<int32_t>(), s->fr[1].as<int32_t>()};
+    unsigned long long* frval = s->frval.as<unsigned long long>();
+    uint32_t epoch = 0;
+    uint32_t sv = 0;  // frontier stamp values, unique per round
+    int64_t n_u = m;
+    int cu = 0;
+    int64_t rounds = 0;
+    while (n_u > 0) {
+        if (++rounds > m + 1) {
+            dfree(bcount_d);
+            FL_FAIL(FL_ETIMEOUT, "greedy MIS did not converge");
+        }
+        // bucket the undecided facilities by ball radius
+        FL_CUDA(cudaMemsetAsync(bcount, 0, (bmax + 1) * 4, st));
+        FL_CUDA(cudaMemsetAsync(&cnt[4], 0, 8, st));
+        k_bucket_count<<<grid_for(n_u, 256), 256, 0, st>>>(ulist[cu], n_u, s->bcap.as<int32_t>(), bcount, &cnt[4]);
+        FL_CUDA(cudaGetLastError());
+        unsigned long long T64 = 0;
+        FL_CUDA(cudaMemcpyAsync(&T64, &cnt[4], 8, cudaMemcpyDeviceToHost, st));
+        FL_CUDA(cudaMemcpyAsync(hcount.data(), bcount, (bmax + 1) * 4, cudaMemcpyDeviceToHost, st));
+        FL_CUDA(cudaStreamSynchronize(st));
+        const int T = (int)T64;
+        int32_t acc = 0;
+        for (int b = 0; b <= T; ++b) { hoff[b] = acc; acc += hcount[b]; }
+        FL_CUDA(cudaMemcpyAsync(cursor, hoff.data(), (T + 1) * 4, cudaMemcpyHostToDevice, st));
+        k_bucket_scatter<<<grid_for(n_u, 256), 256, 0, st>>>(ulist[cu], n_u, s->bcap.as<int32_t>(), cursor,
+                                                            s->ubuck.as<int32_t>());
+        FL_CUDA(cudaGetLastError());
+        const int32_t* ub = s->ubuck.as<int32_t>();
+
+        // ---- cover: X[c] = smallest key of an undecided f with d(c, f) <= B_f.
+        // Facility f starts at time T - B_f; all waves stop at time T.
+        ++epoch;
+        const unsigned long long hi_c = 0xffffffffULL - epoch;
+        FL_CUDA(cudaMemsetAsync(cnt, 0, 24, st));  // both frontiers + touched
+        int c = 0;
+        const uint32_t sv0 = sv;
+        for (int t = 0; t <= T; ++t) {
+            const int b = T - t;
+            if (hcount[b] > 0)
+                k_inject<<<grid_for(hcount[b], 256), 256, 0, st>>>(ub + hoff[b], hcount[b], nullptr, hi_c,
+                                                                  s->ord.as<uint32_t>(), X, stamp, sv0 + 1 + t, fr[c],
+                                                                  &cnt[c]);
+            k_snapshot<<<152 * 2, 256, 0, st>>>(fr[c], &cnt[c], X, frval, &cnt[c ^ 1], tstamp, epoch,
+                                                s->touched.as<int32_t>(), &cnt[2]);
+            if (t < T)
+                k_push<<<152 * 8, 256, 0, st>>>(fr[c], frval, &cnt[c], g->rowp.as<int64_t>(), g->cols.as<int32_t>(),
+                                                0ULL, X, stamp, sv0 + 2 + t, fr[c ^ 1], &cnt[c ^ 1]);
+            c ^= 1;
+        }
+        FL_CUDA(cudaGetLastError());
+        sv = sv0 + T + 2;
+
+        // ---- gather: min over Ball(f) of (claimed ? 0 : cover + 1), read at radius B_f
+        ++epoch;
+        const unsigned long long hi_g = 0xffffffffULL - epoch;
+        FL_CUDA(cudaMemsetAsync(cnt, 0, 16, st));
+        c = 0;
+        const uint32_t sg0 = ++sv;
+        k_gather_seed<<<152 * 2, 256, 0, st>>>(s->touched.as<int32_t>(), &cnt[2], s->client.as<uint8_t>(),
+                                               s->claimed.as<uint8_t>(), hi_g, X, s->mval.as<uint32_t>(), stamp, sg0,
+                                               fr[c], &cnt[c]);
+        if (hcount[0] > 0)
+            k_decide<<<grid_for(hcount[0], 256), 256, 0, st>>>(ub + hoff[0], hcount[0], X, hi_g,
+                                                               s->ord.as<uint32_t>(), s->state.as<uint8_t>(),
+                                                               g->ctr.as<Counters>());
+        for (int b = 1; b <= T; ++b) {
+            k_snapshot<<<152 * 2, 256, 0, st>>>(fr[c], &cnt[c], X, frval, &cnt[c ^ 1], nullptr, 0, nullptr, nullptr);
+            k_push<<<152 * 8, 256, 0, st>>>(fr[c], frval, &cnt[c], g->rowp.as<int64_t>(), g->cols.as<int32_t>(), 0ULL,
+                                            X, stamp, sg0 + b, fr[c ^ 1], &cnt[c ^ 1]);
+            c ^= 1;
+            if (hcount[b] > 0)
+                k_decide<<<grid_for(hcount[b], 256), 256, 0, st>>>(ub + hoff[b], hcount[b], X, hi_g,
+                                                                   s->ord.as<uint32_t>(), s->state.as<uint8_t>(),
+                                                                   g->ctr.as<Counters>());
+        }
+        sv = sg0 + T + 1;
+        FL_CUDA(cudaGetLastError());
+
+        // ---- claim the balls of this round's winners; keep the undecided
+        k_claim<<<152 * 4, 256, 0, st>>>(s->touched.as<int32_t>(), &cnt[2], s->client.as<uint8_t>(),
+                                         s->claimed.as<uint8_t>(), s->mval.as<uint32_t>(),
+                                         s->fac_by_ord.as<int32_t>(), s->state.as<uint8_t>());
+        FL_CUDA(cudaMemsetAsync(&cnt[3], 0, 8, st));
+        k_compact_undecided<<<grid_for(n_u, 256), 256, 0, st>>>(ulist[cu], n_u, s->state.as<uint8_t>(),
+                                                               ulist[cu ^ 1], &cnt[3]);
+        FL_CUDA(cudaGetLastError());
+        unsigned long long nu = 0;
+        FL_CUDA(cudaMemcpyAsync(&nu, &cnt[3], 8, cudaMemcpyDeviceToHost, st));
+        FL_TRY(read_counters(g));
+        if (g->h_ctr->error) {
+            dfree(bcount_d);
+            FL_FAIL(FL_ECUDA, "greedy MIS: inconsistent gather state");
+        }
+        n_u = (int64_t)nu;
+        cu ^= 1;
+    }
+    dfree(bcount_d);
+    s->mis_rounds = rounds;
+    // open set
+    FL_CUDA(cudaMemsetAsync(&cnt[5], 0, 8, st));
+    k_open_list<<<grid_for(n, 256), 256, 0, st>>>(s->state.as<uint8_t>(), n, s->open.as<uint8_t>(),
+                                                  s->ulist.as<int32_t>(), &cnt[5]);
+    FL_CUDA(cudaGetLastError());
+    unsigned long long no = 0;
+    FL_CUDA(cudaMemcpyAsync(&no, &cnt[5], 8, cudaMemcpyDeviceToHost, st));
+    FL_CUDA(cudaStreamSynchronize(st));
+    s->n_open = (int64_t)no;
+    return FL_OK;
+}
+
+// ------------------------------------------------------------------ assignment + objective
+
+int assign_clients(fl_solve* s) {
+    fl_graph* g = s->g;
+    FL_TRY(dalloc(s->assign, (size_t)g->n * 4));
+    FL_TRY(dalloc(s->dist, (size_t)g->n * 4));
+    // the open list was left in ulist by open_facilities
+    return msbfs(g, s->ulist.as<int32_t>(), s->n_open, s->assign.as<int32_t>(), s->dist.as<int32_t>(), s->X,
+                 s->stamp, s->fr, s->frval);
+}
+
+constexpr int kObjBlocks = 152 * 4;
+
+__global__ void k_objective(int64_t n, const uint8_t* __restrict__ open, const double* __restrict__ cost,
+                            const uint8_t* __restrict__ client, const int32_t* __restrict__ dist,
+                            double* __restrict__ partial, unsigned long long* __restrict__ sums) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    unsigned long long ds = 0, un = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        if (open[v]) acc += cost[v];
+        if (client[v]) {
+            int32_t d = dist[v];
+            if (d < 0) ++un; else ds += (unsigned long long)d;
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s2 = 128; s2 > 0; s2 >>= 1) {
+        if ((int)threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+    if (ds) atomicAdd(&sums[0], ds);
+    if (un) atomicAdd(&sums[1], un);
+}
+
+int objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserved) {
+    fl_graph* g = s->g;
+    cudaStream_t st = g->stream;
+    DBuf tmp;
+    FL_TRY(dalloc(tmp, kObjBlocks * 8 + 64));
+    double* partial = tmp.as<double>();
+    unsigned long long* sums = reinterpret_cast<unsigned long long*>(partial + kObjBlocks);
+    int rc = FL_OK;
+    std::vector<double> hp(kObjBlocks);
+    unsigned long long hs[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(sums, 0, 16, st);
+    if (e == cudaSuccess) {
+        k_objective<<<kObjBlocks, 256, 0, st>>>(g->n, s->open.as<uint8_t>(), s->cost.as<double>(),
+                                                s->client.as<uint8_t>(), s->dist.as<int32_t>(), partial, sums);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), partial, kObjBlocks * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs, sums, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = status_of(e, "objective", __FILE__, __LINE__);
+    dfree(tmp);
+    if (rc) return rc;
+    double open_cost = 0.0;
+    for (int b = 0; b < kObjBlocks; ++b) open_cost += hp[b];
+    *obj = open_cost + (double)hs[0];
+    *dist_sum = (int64_t)hs[0];
+    *n_unserved = (int64_t)hs[1];
+    return FL_OK;
+}
+
+}  // namespace fl

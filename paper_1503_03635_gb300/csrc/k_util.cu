@@ -1,0 +1,356 @@
+// k_util.cu -- errors, device buffers, scans, radix sort, CSR checks.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fl_internal.cuh"
+
+namespace fl {
+
+// ----------------------------------------------------------------- errors
+
+static thread_local std::string t_err;
+static thread_local int t_status = FL_OK;
+
+void set_error(int status, const std::string& msg) {
+    t_status = status;
+    t_err = msg;
+}
+
+int status_of(cudaError_t e, const char* what, const char* file, int line) {
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    int st = (e == cudaErrorMemoryAllocation) ? FL_ENOMEM : FL_ECUDA;
+    set_error(st, buf);
+    return st;
+}
+
+int last_error(char* buf, size_t len) {
+    if (buf && len) {
+        size_t m = t_err.size() < len - 1 ? t_err.size() : len - 1;
+        std::memcpy(buf, t_err.data(), m);
+        buf[m] = 0;
+    }
+    return t_status;
+}
+
+// ----------------------------------------------------------------- buffers
+
+int dalloc(DBuf& b, size_t bytes) {
+    if (b.p && b.bytes >= bytes) return FL_OK;
+    dfree(b);
+    if (bytes == 0) bytes = 16;
+    FL_CUDA(cudaMalloc(&b.p, bytes));
+    b.bytes = bytes;
+    return FL_OK;
+}
+
+int dgrow(DBuf& b, size_t bytes, size_t keep, cudaStream_t st) {
+    if (b.p && b.bytes >= bytes) return FL_OK;
+    DBuf nb;
+    FL_CUDA(cudaMalloc(&nb.p, bytes));
+    nb.bytes = bytes;
+    if (b.p && keep) {
+        cudaError_t e = cudaMemcpyAsync(nb.p, b.p, keep, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            cudaFree(nb.p);
+            return status_of(e, "dgrow copy", __FILE__, __LINE__);
+        }
+    }
+    dfree(b);
+    b = nb;
+    return FL_OK;
+}
+
+void dfree(DBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// ----------------------------------------------------------------- scan
+// Exclusive prefix sum with int64 output: tiles of 2048 items (256 threads x
+// 8 consecutive items), reduce -> scan of tile sums (recursive) -> tile scan.
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <class T>
+__device__ __forceinline__ T block_excl_scan(T x, T* warp_tot, T* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T incl = x;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        T y = __shfl_up_sync(kFull, incl, s);
+        if (lane >= s) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : T(0);
+        T wi = w;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            T y = __shfl_up_sync(kFull, wi, s);
+            if (lane >= s) wi += y;
+        }
+        if (lane < (int)(blockDim.x >> 5)) warp_tot[lane] = wi - w;
+        if (lane == 31) *total = wi;
+    }
+    __syncthreads();
+    T r = incl - x + warp_tot[warp];
+    __syncthreads();
+    return r;
+}
+
+template <class Tin>
+__global__ void k_tile_sums(const Tin* __restrict__ in, int64_t n, int64_t* __restrict__ sums) {
+    __shared__ int64_t wt[32];
+    __shared__ int64_t tot;
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) s += (int64_t)in[base + i];
+    block_excl_scan<int64_t>(s, wt, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+template <class Tin>
+__global__ void k_tile_scan(const Tin* __restrict__ in, int64_t n, const int64_t* __restrict__ offs,
+                            int64_t* __restrict__ out) {
+    __shared__ int64_t wt[32];
+    __shared__ int64_t tot;
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (base + i < n) ? (int64_t)in[base + i] : 0;
+        s += v[i];
+    }
+    int64_t run = block_excl_scan<int64_t>(s, wt, &tot) + (offs ? offs[blockIdx.x] : 0);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+}
+
+static size_t scan_tmp_bytes(int64_t n) {
+    size_t b = 0;
+    while (n > kScanTile) {
+        n = (n + kScanTile - 1) / kScanTile;
+        b += 2 * (size_t)n * sizeof(int64_t) + 256;
+    }
+    return b + 256;
+}
+
+template <class Tin>
+static int scan_rec(const Tin* in, int64_t* out, int64_t n, cudaStream_t st, char* tmp) {
+    if (n <= 0) return FL_OK;
+    int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        k_tile_scan<Tin><<<1, kScanThreads, 0, st>>>(in, n, nullptr, out);
+        FL_CUDA(cudaGetLastError());
+        return FL_OK;
+    }
+    int64_t* sums = reinterpret_cast<int64_t*>(tmp);
+    int64_t* offs = sums + tiles;
+    char* next = reinterpret_cast<char*>(offs + tiles);
+    next += (256 - (reinterpret_cast<uintptr_t>(next) & 255)) & 255;
+    k_tile_sums<Tin><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, sums);
+    FL_CUDA(cudaGetLastError());
+    FL_TRY(scan_rec<int64_t>(sums, offs, tiles, st, next));
+    k_tile_scan<Tin><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, offs, out);
+    FL_CUDA(cudaGetLastError());
+    return FL_OK;
+}
+
+int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st, DBuf& tmp) {
+    FL_TRY(dalloc(tmp, scan_tmp_bytes(n)));
+    return scan_rec<int64_t>(in, out, n, st, tmp.as<char>());
+}
+
+int scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st, DBuf& tmp) {
+    FL_TRY(dalloc(tmp, scan_tmp_bytes(n)));
+    return scan_rec<int32_t>(in, out, n, st, tmp.as<char>());
+}
+
+// ----------------------------------------------------------------- radix sort
+// Stable LSD radix sort of (hi, lo) 128-bit keys with a uint32 payload,
+// 4-bit digits (32 passes, lo word first).  Per pass: per-tile digit
+// histogram -> exclusive scan in digit-major order -> stable scatter, where
+// each thread owns 8 consecutive items and per-digit offsets come from a
+// block scan of 16 packed 16-bit counters (4 x uint64 words).
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+__global__ void k_digit_hist(const uint64_t* __restrict__ key, int64_t n, int shift, int nblocks,
+                             int32_t* __restrict__ hist) {
+    __shared__ int32_t h[16];
+    if (threadIdx.x < 16) h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)threadIdx.x * kSortItems;
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i)
+        if (base + i < n) atomicAdd(&h[(key[base + i] >> shift) & 15], 1);
+    __syncthreads();
+    if (threadIdx.x < 16) hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_digit_scatter(const uint64_t* __restrict__ key, const uint64_t* __restrict__ hi_in,
+                                const uint64_t* __restrict__ lo_in, const uint32_t* __restrict__ val_in,
+                                int64_t n, int shift, int nblocks, const int64_t* __restrict__ offs,
+                                uint64_t* __restrict__ hi_out, uint64_t* __restrict__ lo_out,
+                                uint32_t* __restrict__ val_out) {
+    __shared__ uint64_t wt[4][32];
+    __shared__ uint64_t tot[4];
+    int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)threadIdx.x * kSortItems;
+    int dig[kSortItems];
+    uint64_t cnt[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        dig[i] = (base + i < n) ? (int)((key[base + i] >> shift) & 15) : -1;
+        if (dig[i] >= 0) cnt[dig[i] >> 2] += 1ULL << (16 * (dig[i] & 3));
+    }
+    uint64_t ex[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) ex[w] = block_excl_scan<uint64_t>(cnt[w], wt[w], &tot[w]);
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        int d = dig[i];
+        if (d < 0) continue;
+        int w = d >> 2, sh = 16 * (d & 3);
+        int64_t local = (int64_t)((ex[w] >> sh) & 0xffff);
+        ex[w] += 1ULL << sh;
+        int64_t pos = offs[(int64_t)d * nblocks + blockIdx.x] + local;
+        hi_out[pos] = hi_in[base + i];
+        lo_out[pos] = lo_in[base + i];
+        val_out[pos] = val_in[base + i];
+    }
+}
+
+int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaStream_t st, DBuf& tmp) {
+    if (n <= 1) return FL_OK;
+    int nblocks = (int)((n + kSortTile - 1) / kSortTile);
+    int64_t hn = 16LL * nblocks;
+    size_t need = (size_t)n * (8 + 8 + 4) + 256 * 8 + (size_t)hn * (4 + 8) + scan_tmp_bytes(hn);
+    FL_TRY(dalloc(tmp, need));
+    char* p = tmp.as<char>();
+    auto take = [&](size_t bytes) {
+        char* r = p;
+        p += (bytes + 255) & ~size_t(255);
+        return r;
+    };
+    uint64_t* hi2 = reinterpret_cast<uint64_t*>(take((size_t)n * 8));
+    uint64_t* lo2 = reinterpret_cast<uint64_t*>(take((size_t)n * 8));
+    uint32_t* val2 = reinterpret_cast<uint32_t*>(take((size_t)n * 4));
+    int32_t* hist = reinterpret_cast<int32_t*>(take((size_t)hn * 4));
+    int64_t* offs = reinterpret_cast<int64_t*>(take((size_t)hn * 8));
+    char* stmp = take(scan_tmp_bytes(hn));
+    uint64_t *ahi = hi, *alo = lo, *bhi = hi2, *blo = lo2;
+    uint32_t *aval = val, *bval = val2;
+    for (int pass = 0; pass < 32; ++pass) {
+        const uint64_t* key = pass < 16 ? alo : ahi;
+        int shift = 4 * (pass & 15);
+        k_digit_hist<<<nblocks, kSortThreads, 0, st>>>(key, n, shift, nblocks, hist);
+        FL_CUDA(cudaGetLastError());
+        FL_TRY(scan_rec<int32_t>(hist, offs, hn, st, stmp));
+        k_digit_scatter<<<nblocks, kSortThreads, 0, st>>>(key, ahi, alo, aval, n, shift, nblocks, offs,
+                                                          bhi, blo, bval);
+        FL_CUDA(cudaGetLastError());
+        std::swap(ahi, bhi);
+        std::swap(alo, blo);
+        std::swap(aval, bval);
+    }
+    // 32 passes: the result is back in the caller's arrays
+    return FL_OK;
+}
+
+// ----------------------------------------------------------------- CSR checks
+
+__global__ void k_validate_csr(const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
+                               int64_t n, int64_t nnz, Counters* ctr) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (rowp[i] > rowp[i + 1] || rowp[i] < 0) atomicOr(&ctr->error, 1ULL);
+    }
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+        int32_t c = cols[e];
+        if (c < 0 || c >= n) atomicOr(&ctr->error, 2ULL);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (rowp[0] != 0 || rowp[n] != nnz) atomicOr(&ctr->error, 4ULL);
+    }
+}
+
+int read_counters(fl_graph* g) {
+    FL_CUDA(cudaMemcpyAsync(g->h_ctr, g->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, g->stream));
+    FL_CUDA(cudaStreamSynchronize(g->stream));
+    return FL_OK;
+}
+
+int validate_csr(fl_graph* g) {
+    FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), g->stream));
+    k_validate_csr<<<152 * 8, 256, 0, g->stream>>>(g->rowp.as<int64_t>(), g->cols.as<int32_t>(), g->n,
+                                                    g->nnz, g->ctr.as<Counters>());
+    FL_CUDA(cudaGetLastError());
+    FL_TRY(read_counters(g));
+    if (g->h_ctr->error) {
+        char buf[160];
+        std::snprintf(buf, sizeof(buf), "invalid CSR (flags 0x%llx: 1=offsets decrease, 2=id out of range, "
+                      "4=row_off[0]!=0 or row_off[n]!=nnz)", (unsigned long long)g->h_ctr->error);
+        FL_FAIL(FL_EINVAL, buf);
+    }
+    return FL_OK;
+}
+
+// Ascending list of vertices with at least one neighbour.
+__global__ void k_flag_nonisolated(const int64_t* __restrict__ rowp, int64_t n, int32_t* __restrict__ flag) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        flag[v] = rowp[v + 1] > rowp[v] ? 1 : 0;
+}
+
+__global__ void k_scatter_flagged(const int32_t* __restrict__ flag, const int64_t* __restrict__ pos, int64_t n,
+                                  int32_t* __restrict__ out) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        if (flag[v]) out[pos[v]] = (int32_t)v;
+}
+
+int build_nonisolated_list(fl_graph* g) {
+    const int64_t n = g->n;
+    DBuf flag, pos;
+    int rc = dalloc(flag, (size_t)n * 4);
+    if (rc == FL_OK) rc = dalloc(pos, (size_t)(n + 1) * 8);
+    if (rc == FL_OK) rc = dalloc(g->deg_list, (size_t)n * 4);
+    if (rc == FL_OK) {
+        k_flag_nonisolated<<<152 * 8, 256, 0, g->stream>>>(g->rowp.as<int64_t>(), n, flag.as<int32_t>());
+        rc = scan_exclusive_i32_to_i64(flag.as<int32_t>(), pos.as<int64_t>(), n, g->stream, g->scratch);
+    }
+    if (rc == FL_OK) {
+        k_scatter_flagged<<<152 * 8, 256, 0, g->stream>>>(flag.as<int32_t>(), pos.as<int64_t>(), n,
+                                                          g->deg_list.as<int32_t>());
+        int64_t last_pos = 0;
+        int32_t last_flag = 0;
+        cudaError_t e = cudaMemcpyAsync(&last_pos, pos.as<int64_t>() + n - 1, 8, cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&last_flag, flag.as<int32_t>() + n - 1, 4, cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) rc = status_of(e, "nonisolated list", __FILE__, __LINE__);
+        g->n_nonisolated = last_pos + last_flag;
+    }
+    dfree(flag);
+    dfree(pos);
+    return rc;
+}
+
+}  // namespace fl
