@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(256) k_merge_hop(
         const uint64_t old = lane < k ? S[(int64_t)v * k + lane] : kEmpty;
         uint64_t sk = old;
         int cnt_old = Scnt[v];
-        uint64_t tau = cnt_old == k ? __shfl_sync(kFull, sk, k - 1) : kEmpty;
+        const uint64_t kth_old = __shfl_sync(kFull, sk, k - 1);
+        uint64_t tau = cnt_old == k ? kth_old : kEmpty;
         uint64_t buf = kEmpty;
         int nbuf = 0;
         for (int64_t cb = beg; cb < end; cb += 32) {
@@ -146,7 +147,8 @@ __global__ void __launch_bounds__(256) k_merge_hop(
         if (nbuf) sk = merge_candidates(sk, buf, k);
         // outputs
         const bool valid = lane < k && sk != kEmpty;
-        const bool is_new = valid && !warp_member(old, sk);
+        const bool was_there = warp_member(old, sk);  // every lane takes part in the shuffles
+        const bool is_new = valid && !was_there;
         const unsigned newm = __ballot_sync(kFull, is_new);
         const int dcnt = __popc(newm);
         const int cnt_new = __popc(__ballot_sync(kFull, valid));
