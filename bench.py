@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 facility-location hot path (one JSON line on rank 0).
+
+A step is one pass of the whole path over one instance: bottom-k sketches and
+ADS (phase i), radii (phase ii), key sort and greedy-MIS facility selection
+(phase iii), assignment BFS and objective.  Inputs are resident in HBM when the
+timed region starts (they are larger than L2 for the default workload).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl gpu|reference]
+
+Metric: sketch edge-merges per second (an edge-merge is one CSR entry (v, u)
+processed at a hop whose u gained sketch entries at the previous hop), whole
+job over all ranks.  Under torchrun each rank solves its own replica of the
+workload (the method has no exchange step on one GPU per instance), so the
+scaling is weak.  `--impl reference` times the CPU oracle on a bounded sample
+of the same workload (the first hops of its sketch build) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import flsynth  # noqa: E402
+
+METRIC = "sketch edge-merges/sec and HBM GB/s (% peak); solves/sec batched vs plain; p50/p99"
+UNIT = "edge-merges/s"
+DEFAULT_WORKLOAD = "rmat26"
+# bounded oracle samples (hops of its sketch build) per workload: ~10-30 s of CPU work
+CPU_SAMPLE_HOPS = {"er10k": 64, "rmat20": 64, "rmat26": 1}
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash(path):
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    p = os.path.join(PROFILE_DIR, "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(kernel, {}).get(workload)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_1503_03635_gb300", "csrc", e["source"])
+    if not os.path.exists(src) or source_hash(src) != e["source_sha256_16"]:
+        return None
+    return e["dram_bytes_per_launch"]
+
+
+class Clocks:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for ln in fh:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_sample(w, hops, steps=1):
+    """Time the CPU oracle's sketch build for `hops` hops of the same workload."""
+    import oracle
+
+    g = oracle.Graph(w.rowp, w.cols)
+    times, merges = [], 0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        g.build_sketches(w.k, w.seed, max_hops=hops)
+        times.append(time.perf_counter() - t0)
+        merges = g.edge_merges
+        done_hops = g.hops
+    g.close()
+    t = statistics.median(times)
+    return {"value": merges / t, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"oracle sketch build (phase i), first {min(hops, done_hops)} hop(s) on the full "
+                      f"{w.name} graph: {merges} edge-merges in {t:.2f} s"}
+
+
+def workload_config(w):
+    return {"workload": w.name, "n": w.n, "nnz": w.nnz, "k": w.k, "rank_seed": w.seed,
+            "clients": int(w.client.sum()), "facilities": int(np.isfinite(w.cost).sum()),
+            "l2": "inputs larger than L2 (no flush)" if (w.nnz * 4 + w.n * 8) > 129e6 else
+                  "inputs smaller than L2",
+            "parallelism": "replicas (one instance per GPU)"}
+
+
+def run_reference(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    w = flsynth.config(args.workload)
+    hops = CPU_SAMPLE_HOPS.get(args.workload, 1)
+    import oracle
+
+    g = oracle.Graph(w.rowp, w.cols)
+    for _ in range(args.warmup):
+        g.build_sketches(w.k, w.seed, max_hops=hops)
+    times = []
+    merges = 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        g.build_sketches(w.k, w.seed, max_hops=hops)
+        times.append(time.perf_counter() - t0)
+        merges = g.edge_merges
+    total = sum(times)
+    value = merges * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": workload_config(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"oracle sketch build, first {hops} hop(s) of {w.name} per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_1503_03635_gb300 as fl
+
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    fl.load()
+    w = flsynth.config(args.workload)
+    stream = torch.cuda.Stream(device=dev)
+
+    # ---------------- device-resident inputs and outputs
+    rowp_d = torch.from_numpy(w.rowp).to(dev)
+    cols_d = torch.from_numpy(w.cols).to(dev)
+    cost_d = torch.from_numpy(w.cost).to(dev)
+    client_d = torch.from_numpy(w.client).to(dev)
+    radii_d = torch.empty(w.n, dtype=torch.float64, device=dev)
+    open_d = torch.empty(w.n, dtype=torch.uint8, device=dev)
+    assign_d = torch.empty(w.n, dtype=torch.int32, device=dev)
+    dist_d = torch.empty(w.n, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    g = fl.Graph(rowp_d, cols_d, stream=stream)
+    info = {}
+
+    def step():
+        g.build_sketches(w.k, w.seed)
+        s = fl.Solve(g)
+        s.compute_radii(cost_d, client_d, radii_d)
+        _, nopen = s.open_facilities(open_d)
+        s.assign_clients(assign_d, dist_d)
+        obj = s.objective()
+        info["n_open"] = nopen
+        info["objective"] = obj[0]
+        info["mis"] = s.stats()
+        s.close()
+
+    for _ in range(args.warmup):
+        step()
+    stats = g.stats()
+
+    # ---------------- timed region (device-resident inputs)
+    g.profile(True)
+    g.profile_reset()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    torch.cuda.synchronize()
+    prof = {name: g.profile_query(name) for name in fl.PROF_CLASSES}
+    launches = g.profile_query(-1)["launches"]
+    g.profile(False)
+    merges_step = stats["edge_merges"]
+    value = world * merges_step * args.steps / (ms / 1e3)
+
+    # ---------------- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        rowp_h = torch.from_numpy(w.rowp).pin_memory()
+        cols_h = torch.from_numpy(w.cols).pin_memory()
+        cost_h = torch.from_numpy(w.cost).pin_memory()
+        client_h = torch.from_numpy(w.client).pin_memory()
+        open_h = torch.empty(w.n, dtype=torch.uint8).pin_memory()
+        assign_h = torch.empty(w.n, dtype=torch.int32).pin_memory()
+        dist_h = torch.empty(w.n, dtype=torch.int32).pin_memory()
+        g.close()
+        times = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g2 = fl.Graph(rowp_h, cols_h, stream=stream)      # H2D of the CSR
+            g2.build_sketches(w.k, w.seed)
+            s2 = fl.Solve(g2)
+            s2.compute_radii(cost_h, client_h)                  # H2D of costs and mask
+            s2.open_facilities(open_h)                          # D2H of the open set
+            s2.assign_clients(assign_h, dist_h)                 # D2H of assignment and distance
+            s2.objective()
+            s2.close()
+            g2.close()
+            dt = time.perf_counter() - t0
+            if i > 0:  # the first pass warms allocations
+                times.append(dt)
+        t_e2e = sum(times) / len(times)
+        if dist:
+            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * merges_step / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(w.rowp.nbytes + w.cols.nbytes + w.cost.nbytes + w.client.nbytes),
+               "d2h_bytes_per_step": int(open_h.numel() + 4 * assign_h.numel() + 4 * dist_h.numel()),
+               "ms_per_step": 1e3 * t_e2e, "steps": len(times)}
+    else:
+        g.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # ---------------- roofline of the dominant kernel (the sketch merge)
+    peak, peak_kind = measured_peaks()
+    mp = prof["sketch_merge"]
+    achieved = mp["alg_bytes"] / (mp["ms"] / 1e3) / 1e9 if mp["ms"] > 0 else None
+    per_launch_bytes = mp["alg_bytes"] / mp["launches"] if mp["launches"] else None
+    traffic = ncu_traffic("k_merge_hop", w.name)
+    roofline = {"kernel": "k_merge_hop", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "peak_kind": f"{peak_kind} copy bandwidth", "alg_bytes_per_launch": per_launch_bytes,
+                "launches": mp["launches"], "kernel_ms": mp["ms"],
+                "share_of_step": mp["ms"] / ms if ms > 0 else None}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_sample(w, CPU_SAMPLE_HOPS.get(w.name, 1))
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": workload_config(w),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "solves_per_sec": world * args.steps / (ms / 1e3),
+            "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
+            "hops": stats["hops"], "edge_merges_per_step": merges_step, "ads_entries": stats["ads_entries"],
+            "n_open": info.get("n_open"), "objective": info.get("objective"),
+            "mis_rounds": info.get("mis", {}).get("mis_rounds")}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    help="er10k, rmat20, rmat26 (the named workloads) or rmatS for the rmat20 recipe at scale S")
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

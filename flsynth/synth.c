@@ -79,7 +79,8 @@ static int64_t build_csr(int64_t n, int64_t m, const int32_t* src, const int32_t
                          int64_t* rowp, int32_t* cols) {
     int64_t* deg = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
     int64_t* cur = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
-    if (!deg || !cur) { free(deg); free(cur); return -1; }
+    int32_t* tmp = (int32_t*)malloc((size_t)(2 * m > 0 ? 2 * m : 1) * sizeof(int32_t));
+    if (!deg || !cur || !tmp) { free(deg); free(cur); free(tmp); return -1; }
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < m; ++i) {
         int32_t s = src[i], d = dst[i];
@@ -96,32 +97,30 @@ static int64_t build_csr(int64_t n, int64_t m, const int32_t* src, const int32_t
         int32_t s = src[i], d = dst[i];
         if (s == d) continue;
         int64_t p = __atomic_fetch_add(&cur[s], 1, __ATOMIC_RELAXED);
-        cols[p] = d;
+        tmp[p] = d;
         p = __atomic_fetch_add(&cur[d], 1, __ATOMIC_RELAXED);
-        cols[p] = s;
+        tmp[p] = s;
     }
     /* sort + dedupe each row in place; cur[v] becomes the deduped length */
 #pragma omp parallel for schedule(dynamic, 4096)
     for (int64_t v = 0; v < n; ++v) {
         int64_t b = deg[v], len = deg[v + 1] - deg[v];
-        sort_row(cols + b, len);
+        sort_row(tmp + b, len);
         int64_t w = 0;
         for (int64_t i = 0; i < len; ++i)
-            if (w == 0 || cols[b + i] != cols[b + w - 1]) cols[b + w++] = cols[b + i];
+            if (w == 0 || tmp[b + i] != tmp[b + w - 1]) tmp[b + w++] = tmp[b + i];
         cur[v] = w;
     }
-    /* compact rows to the front, in increasing row order (every row only
-       moves left, so no row is overwritten before it is moved) */
-    int64_t total = 0;
-    for (int64_t v = 0; v < n; ++v) {
-        int64_t b = deg[v], w = cur[v];
-        if (total != b) memmove(cols + total, cols + b, (size_t)w * sizeof(int32_t));
-        rowp[v] = total;
-        total += w;
-    }
-    rowp[n] = total;
+    /* row offsets of the deduplicated rows, then copy the rows out */
+    rowp[0] = 0;
+    for (int64_t v = 0; v < n; ++v) rowp[v + 1] = rowp[v] + cur[v];
+#pragma omp parallel for schedule(dynamic, 4096)
+    for (int64_t v = 0; v < n; ++v)
+        memcpy(cols + rowp[v], tmp + deg[v], (size_t)cur[v] * sizeof(int32_t));
+    int64_t total = rowp[n];
     free(deg);
     free(cur);
+    free(tmp);
     return total;
 }
 

@@ -177,6 +177,38 @@ int fl_objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserve
    the number of candidates (any pointer may be NULL). */
 int fl_solve_stats(const fl_solve* s, int64_t* mis_rounds, int64_t* candidates);
 
+/*
+ * Profiling (launch accounting and kernel timing of a graph and its solves).
+ * The paper reports per-phase running times (Section 5); these calls give the
+ * same split on the GPU.  Every kernel launch is counted per class; when
+ * timing is on, each launch is bracketed by CUDA events on the graph's stream
+ * and the elapsed times are summed when the API call that issued it returns.
+ * Classes: FL_PROF_SKETCH_MERGE (the hop merge kernel), FL_PROF_SKETCH_EXPAND
+ * (frontier expansion), FL_PROF_SKETCH_OTHER (rank init, ADS compaction,
+ * eccentricity bound), FL_PROF_RADIUS, FL_PROF_KEYS (candidate sort),
+ * FL_PROF_MIS, FL_PROF_BFS (assignment), FL_PROF_OTHER; -1 = all classes.
+ * alg_bytes is filled for FL_PROF_SKETCH_MERGE: per hop, 8 B per merging
+ * vertex (row offsets) + 4 B per edge-merge (column) + 8 B per neighbour
+ * delta rank read + 16k B per merging vertex (own sketch read and write) +
+ * 12 B per new ADS entry.
+ */
+#define FL_PROF_SKETCH_MERGE 0
+#define FL_PROF_SKETCH_EXPAND 1
+#define FL_PROF_SKETCH_OTHER 2
+#define FL_PROF_RADIUS 3
+#define FL_PROF_KEYS 4
+#define FL_PROF_MIS 5
+#define FL_PROF_BFS 6
+#define FL_PROF_OTHER 7
+
+/* fl_profile_enable -- turn CUDA-event timing of launches on (1) or off (0). */
+int fl_profile_enable(fl_graph* g, int on);
+/* fl_profile_reset -- zero all counters and times (synchronises the stream). */
+int fl_profile_reset(fl_graph* g);
+/* fl_profile_query -- launches, summed kernel milliseconds and algorithmic
+   bytes of one class (or all, kernel_class = -1); any pointer may be NULL. */
+int fl_profile_query(const fl_graph* g, int kernel_class, int64_t* launches, double* ms, double* alg_bytes);
+
 /* fl_status_str -- static text for a status code. */
 const char* fl_status_str(int status);
 

@@ -57,6 +57,10 @@ def _load():
             lib.orc_graph_destroy.argtypes = [vp]
             lib.orc_build_sketches.restype = ctypes.c_int
             lib.orc_build_sketches.argtypes = [vp, ctypes.c_int, u64]
+            lib.orc_build_sketches_hops.restype = ctypes.c_int
+            lib.orc_build_sketches_hops.argtypes = [vp, ctypes.c_int, u64, i64]
+            lib.orc_threads.restype = ctypes.c_int
+            lib.orc_threads.argtypes = []
             for name in ("orc_hops", "orc_edge_merges", "orc_ads_groups", "orc_ads_entries"):
                 getattr(lib, name).restype = i64
                 getattr(lib, name).argtypes = [vp]
@@ -91,6 +95,11 @@ def splitmix64_outputs(state: int, count: int) -> list[int]:
     lib = _load()
     s = u64(state)
     return [int(lib.orc_splitmix64_next(ctypes.byref(s))) for _ in range(count)]
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's parallel loops use."""
+    return int(_load().orc_threads())
 
 
 def rank(seed: int, v: int) -> int:
@@ -134,8 +143,12 @@ class Graph:
             pass
 
     # -- phase (i): Section 2.3, Algorithms 1-2 ---------------------------
-    def build_sketches(self, k: int, seed: int) -> None:
-        rc = self._lib.orc_build_sketches(self._h, k, seed)
+    def build_sketches(self, k: int, seed: int, max_hops: int | None = None) -> None:
+        """Phase (i); with max_hops, stop after that many hops (a bounded sample)."""
+        if max_hops is None:
+            rc = self._lib.orc_build_sketches(self._h, k, seed)
+        else:
+            rc = self._lib.orc_build_sketches_hops(self._h, k, seed, max_hops)
         if rc != 0:
             raise RuntimeError(f"orc_build_sketches rc={rc}")
         self.k, self.seed = k, seed

@@ -182,7 +182,18 @@ static double hip_weight(const uint64_t* Sh, int32_t len, int k) {
 
 typedef struct { int32_t v; int32_t hop; int64_t at; int32_t cnt; } hop_rec;
 
-int orc_build_sketches(orc_graph* g, int k, uint64_t seed) {
+/* Threads the OpenMP loops of this oracle use. */
+int orc_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Hop-synchronous build; stops after `max_hops` hops (a bounded sample of
+   the build for timing) or at the fixed point, whichever comes first. */
+int orc_build_sketches_hops(orc_graph* g, int k, uint64_t seed, int64_t max_hops) {
     if (!g || k < 2 || k > 64) return ORC_EINVAL;
     orc_clear_ads(g);
     const int64_t n = g->n;
@@ -261,6 +272,7 @@ int orc_build_sketches(orc_graph* g, int k, uint64_t seed) {
             if (dn) ++changed;
         }
         if (!changed) { g->hops = h - 1; break; }
+        if (h >= max_hops) { g->hops = h; }
         /* append this hop's groups in vertex order */
         for (int64_t v = 0; v < n; ++v) {
             if (!Dcur_cnt[v]) continue;
@@ -286,6 +298,7 @@ int orc_build_sketches(orc_graph* g, int k, uint64_t seed) {
         }
         uint64_t* t = Dprev; Dprev = Dcur; Dcur = t;
         int32_t* tc = Dprev_cnt; Dprev_cnt = Dcur_cnt; Dcur_cnt = tc;
+        if (h >= max_hops) break;
     }
     g->edge_merges = merges;
 
@@ -345,6 +358,10 @@ int orc_build_sketches(orc_graph* g, int k, uint64_t seed) {
     free(Dprev); free(Dprev_cnt); free(Dcur); free(Dcur_cnt); free(Dcur_wt); free(Dcur_counted);
     free(rec); free(rec_wt); free(rec_counted); free(ent);
     return ORC_OK;
+}
+
+int orc_build_sketches(orc_graph* g, int k, uint64_t seed) {
+    return orc_build_sketches_hops(g, k, seed, INT64_MAX);
 }
 
 int64_t orc_hops(const orc_graph* g) { return g && g->built ? g->hops : -1; }

@@ -26,7 +26,11 @@ FL_MEM_HOST, FL_MEM_DEVICE = 0, 1
 EXPORTS = ("fl_graph_create", "fl_graph_destroy", "fl_build_sketches", "fl_sketch_stats",
            "fl_export_sketches", "fl_export_ads", "fl_solve_create", "fl_solve_destroy",
            "fl_compute_radii", "fl_open_facilities", "fl_assign_clients", "fl_objective",
-           "fl_solve_stats", "fl_status_str", "fl_last_error")
+           "fl_solve_stats", "fl_status_str", "fl_last_error", "fl_profile_enable", "fl_profile_reset",
+           "fl_profile_query")
+
+PROF_CLASSES = {"sketch_merge": 0, "sketch_expand": 1, "sketch_other": 2, "radius": 3, "keys": 4,
+                "mis": 5, "bfs": 6, "other": 7}
 
 
 class FLError(RuntimeError):
@@ -68,6 +72,9 @@ def load(build_if_missing: bool = True):
             "fl_solve_stats": ([vp, P64, P64], ci),
             "fl_status_str": ([ci], ctypes.c_char_p),
             "fl_last_error": ([ctypes.c_char_p, ctypes.c_size_t], ci),
+            "fl_profile_enable": ([vp, ci], ci),
+            "fl_profile_reset": ([vp], ci),
+            "fl_profile_query": ([vp, ci, P64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -154,6 +161,19 @@ class Graph:
         v = [ctypes.c_int64() for _ in range(4)]
         _check(self._lib.fl_sketch_stats(self._h, *[ctypes.byref(x) for x in v]))
         return dict(hops=v[0].value, edge_merges=v[1].value, ads_entries=v[2].value, ads_groups=v[3].value)
+
+    def profile(self, on: bool = True):
+        _check(self._lib.fl_profile_enable(self._h, 1 if on else 0))
+
+    def profile_reset(self):
+        _check(self._lib.fl_profile_reset(self._h))
+
+    def profile_query(self, kernel_class=-1) -> dict:
+        """Launches, kernel milliseconds and algorithmic bytes of one class (name or id)."""
+        c = PROF_CLASSES[kernel_class] if isinstance(kernel_class, str) else int(kernel_class)
+        l, ms, b = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        _check(self._lib.fl_profile_query(self._h, c, ctypes.byref(l), ctypes.byref(ms), ctypes.byref(b)))
+        return dict(launches=l.value, ms=ms.value, alg_bytes=b.value)
 
     def export_sketches(self):
         S = np.zeros((self.n, self.k), np.uint64)

@@ -35,6 +35,7 @@ void destroy_graph(fl_graph* g) {
                     &g->stg_grp, &g->stg_wt, &g->gofs, &g->eofs, &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub,
                     &g->ctr, &g->scratch};
     for (DBuf* b : bufs) dfree(*b);
+    for (cudaEvent_t e : g->prof.ev) cudaEventDestroy(e);
     if (g->h_ctr) cudaFreeHost(g->h_ctr);
     delete g;
 }
@@ -46,6 +47,21 @@ void destroy_solve(fl_solve* s) {
     for (DBuf* b : bufs) dfree(*b);
     delete s;
 }
+
+// Routes the launch accounting of the kernels of one API call to the
+// handle's profiler; when kernel timing is on, drains the recorded events
+// (after a stream sync) when the call returns.
+struct ProfScope {
+    fl_graph* g;
+    explicit ProfScope(fl_graph* gg) : g(gg) { set_current_prof(g ? &g->prof : nullptr, g ? g->stream : nullptr); }
+    ~ProfScope() {
+        if (g && g->prof.on && g->prof.used) {
+            cudaStreamSynchronize(g->stream);
+            prof_drain(&g->prof);
+        }
+        set_current_prof(nullptr, nullptr);
+    }
+};
 
 int check_solve(fl_solve* s) {
     if (!s || !s->g) FL_FAIL(FL_EINVAL, "null solve handle");
@@ -81,6 +97,7 @@ int fl_graph_create(int64_t n, const int64_t* row_off, const int32_t* cols, int6
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
     fl_graph* g = new (std::nothrow) fl_graph();
     if (!g) FL_FAIL(FL_ENOMEM, "host allocation failed");
+    ProfScope ps(nullptr);
     g->n = n;
     g->nnz = nnz;
     g->stream = static_cast<cudaStream_t>(stream);
@@ -95,6 +112,7 @@ int fl_graph_create(int64_t n, const int64_t* row_off, const int32_t* cols, int6
         if (e == cudaSuccess && nnz > 0)
             e = cudaMemcpyAsync(g->cols.p, cols, (size_t)nnz * 4, kind_in(mem_kind), g->stream);
         if (e != cudaSuccess) { rc = status_of(e, "CSR upload", __FILE__, __LINE__); break; }
+        set_current_prof(&g->prof, g->stream);
         if ((rc = validate_csr(g))) break;
         if ((rc = build_nonisolated_list(g))) break;
     } while (0);
@@ -116,6 +134,7 @@ int fl_graph_destroy(fl_graph* g) {
 int fl_build_sketches(fl_graph* g, int k, uint64_t seed) {
     if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
     if (k < 2 || k > 32) FL_FAIL(FL_EINVAL, "k must be in [2, 32]");
+    ProfScope ps(g);
     return build_sketches(g, k, seed);
 }
 
@@ -151,13 +170,14 @@ int fl_export_sketches(fl_graph* g, uint64_t* S, int32_t* cnt, int mem_kind) {
     if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
     if (!g->built) FL_FAIL(FL_ESTATE, "sketches not built");
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    ProfScope ps(g);
     cudaStream_t st = g->stream;
     FL_TRY(copy_out(S, g->S.p, (size_t)g->n * g->k * 8, mem_kind, st));
     if (cnt) {
         DBuf tmp;
         FL_TRY(dalloc(tmp, (size_t)g->n * 4));
-        k_export_sketch<<<152 * 4, 256, 0, st>>>(g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->n,
-                                                 tmp.as<int32_t>());
+        FL_LAUNCH(kProfOther, k_export_sketch<<<152 * 4, 256, 0, st>>>(g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->n,
+                                                 tmp.as<int32_t>()));
         int rc = copy_out(cnt, tmp.p, (size_t)g->n * 4, mem_kind, st);
         cudaError_t e = cudaStreamSynchronize(st);
         dfree(tmp);
@@ -173,6 +193,7 @@ int fl_export_ads(fl_graph* g, int64_t* gofs, int64_t* eofs, int32_t* ghop, int3
     if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
     if (!g->built) FL_FAIL(FL_ESTATE, "sketches not built");
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    ProfScope ps(g);
     cudaStream_t st = g->stream;
     FL_TRY(copy_out(gofs, g->gofs.p, (size_t)(g->n + 1) * 8, mem_kind, st));
     FL_TRY(copy_out(eofs, g->eofs.p, (size_t)(g->n + 1) * 8, mem_kind, st));
@@ -183,7 +204,7 @@ int fl_export_ads(fl_graph* g, int64_t* gofs, int64_t* eofs, int32_t* ghop, int3
         const size_t m = (size_t)g->n_groups;
         FL_TRY(dalloc(tmp, m * 12 + 16));
         int32_t* h = tmp.as<int32_t>();
-        k_unpack_ginfo<<<152 * 4, 256, 0, st>>>(g->ginfo.as<uint32_t>(), (int64_t)m, h, h + m, h + 2 * m);
+        FL_LAUNCH(kProfOther, k_unpack_ginfo<<<152 * 4, 256, 0, st>>>(g->ginfo.as<uint32_t>(), (int64_t)m, h, h + m, h + 2 * m));
         int rc = copy_out(ghop, h, m * 4, mem_kind, st);
         if (!rc) rc = copy_out(gcnt, h + m, m * 4, mem_kind, st);
         if (!rc) rc = copy_out(gcounted, h + 2 * m, m * 4, mem_kind, st);
@@ -229,6 +250,7 @@ int fl_compute_radii(fl_solve* s, const double* open_cost, const uint8_t* client
     if (!open_cost || !client_mask) FL_FAIL(FL_EINVAL, "open_cost and client_mask are required");
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
     fl_graph* g = s->g;
+    ProfScope ps(g);
     cudaStream_t st = g->stream;
     s->have_radii = s->have_open = s->have_assign = 0;
     FL_CUDA(cudaMemcpyAsync(s->cost.p, open_cost, (size_t)g->n * 8, kind_in(mem_kind), st));
@@ -245,6 +267,7 @@ int fl_open_facilities(fl_solve* s, uint8_t* open_out, int64_t* n_open, int mem_
     if (!s->have_radii) FL_FAIL(FL_ESTATE, "compute radii first");
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
     s->have_open = s->have_assign = 0;
+    ProfScope ps(s->g);
     FL_TRY(open_facilities(s));
     FL_TRY(copy_out(open_out, s->open.p, (size_t)s->g->n, mem_kind, s->g->stream));
     FL_CUDA(cudaStreamSynchronize(s->g->stream));
@@ -257,6 +280,7 @@ int fl_assign_clients(fl_solve* s, int32_t* assign_out, int32_t* dist_out, int m
     FL_TRY(check_solve(s));
     if (!s->have_open) FL_FAIL(FL_ESTATE, "open facilities first");
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    ProfScope ps(s->g);
     FL_TRY(assign_clients(s));
     FL_TRY(copy_out(assign_out, s->assign.p, (size_t)s->g->n * 4, mem_kind, s->g->stream));
     FL_TRY(copy_out(dist_out, s->dist.p, (size_t)s->g->n * 4, mem_kind, s->g->stream));
@@ -270,10 +294,46 @@ int fl_objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserve
     if (!s->have_assign) FL_FAIL(FL_ESTATE, "assign clients first");
     double o = 0.0;
     int64_t ds = 0, un = 0;
+    ProfScope ps(s->g);
     FL_TRY(objective(s, &o, &ds, &un));
     if (obj) *obj = o;
     if (dist_sum) *dist_sum = ds;
     if (n_unserved) *n_unserved = un;
+    return FL_OK;
+}
+
+int fl_profile_enable(fl_graph* g, int on) {
+    if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    g->prof.on = on ? 1 : 0;
+    return FL_OK;
+}
+
+int fl_profile_reset(fl_graph* g) {
+    if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    FL_CUDA(cudaStreamSynchronize(g->stream));
+    g->prof.used = 0;
+    for (int i = 0; i < kProfClasses; ++i) {
+        g->prof.launches[i] = 0;
+        g->prof.ms[i] = 0.0;
+        g->prof.bytes[i] = 0.0;
+    }
+    return FL_OK;
+}
+
+int fl_profile_query(const fl_graph* g, int kernel_class, int64_t* launches, double* ms, double* alg_bytes) {
+    if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    if (kernel_class < -1 || kernel_class >= kProfClasses) FL_FAIL(FL_EINVAL, "bad kernel class");
+    int64_t l = 0;
+    double t = 0.0, b = 0.0;
+    for (int i = 0; i < kProfClasses; ++i) {
+        if (kernel_class != -1 && i != kernel_class) continue;
+        l += g->prof.launches[i];
+        t += g->prof.ms[i];
+        b += g->prof.bytes[i];
+    }
+    if (launches) *launches = l;
+    if (ms) *ms = t;
+    if (alg_bytes) *alg_bytes = b;
     return FL_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/fl.h"
 
@@ -209,8 +210,50 @@ struct Counters {
     unsigned long long stg_groups;   // ADS staging groups used
     unsigned long long merges;       // edge-merges of the next hop (sum of deg of frontier)
     unsigned long long error;        // nonzero: a kernel detected a bad input
-    unsigned long long aux0, aux1, aux2, aux3;
+    unsigned long long aux0;         // general purpose
+    unsigned long long cand_reads;   // merge: neighbour-delta ranks read (sum of |D_{h-1}(u)| over frontier edges)
+    unsigned long long merging;      // merge: vertices with at least one frontier neighbour
+    unsigned long long aux3;
 };
+
+// ----------------------------------------------------------------- profiling
+// Kernel classes for launch counts and CUDA-event timings.
+enum ProfClass {
+    kProfSketchMerge = 0,  // k_merge_hop
+    kProfSketchExpand = 1, // k_expand
+    kProfSketchOther = 2,  // rank init, ADS compaction, scans, eccentricity bound
+    kProfRadius = 3,
+    kProfKeys = 4,         // candidates, radix sort, ordinals
+    kProfMis = 5,          // greedy-MIS rounds
+    kProfBfs = 6,          // assignment BFS
+    kProfOther = 7,        // validation, exports, objective
+    kProfClasses = 8
+};
+
+struct Prof {
+    int on = 0;
+    int64_t launches[kProfClasses] = {};
+    double ms[kProfClasses] = {};
+    double bytes[kProfClasses] = {};
+    std::vector<cudaEvent_t> ev;   // pool of (start, stop) pairs
+    std::vector<int> cls;          // class of each recorded pair
+    size_t used = 0;
+};
+
+// The profiler of the handle whose API call is running on this thread.
+Prof* current_prof();
+void set_current_prof(Prof* p, cudaStream_t st);
+int prof_begin(int cls);           // counts the launch; records a start event when on
+void prof_end(int slot);           // records the stop event
+int prof_drain(Prof* p);           // after a stream sync: accumulate elapsed times
+
+// Launch a kernel statement and account it to a class.
+#define FL_LAUNCH(cls, ...)                      \
+    do {                                         \
+        int slot__ = ::fl::prof_begin(cls);      \
+        __VA_ARGS__;                             \
+        ::fl::prof_end(slot__);                  \
+    } while (0)
 
 // ----------------------------------------------------------------- handles
 
@@ -246,6 +289,7 @@ struct fl_graph {
     fl::DBuf ctr;                  // Counters
     fl::Counters* h_ctr = nullptr; // pinned host mirror
     fl::DBuf scratch;              // general scratch (scans, sorts)
+    fl::Prof prof;                 // launch counts and kernel timings
 };
 
 struct fl_solve {
@@ -266,9 +310,12 @@ namespace fl {
 // ----------------------------------------------------------------- kernel launchers
 // (implemented in the .cu files; all run on g->stream)
 
-int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st, DBuf& tmp);
-int scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st, DBuf& tmp);
-int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaStream_t st, DBuf& tmp);
+int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st, DBuf& tmp,
+                       int cls = kProfSketchOther);
+int scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st, DBuf& tmp,
+                              int cls = kProfSketchOther);
+int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaStream_t st, DBuf& tmp,
+                    int cls = kProfKeys);
 
 int validate_csr(fl_graph* g);
 int build_nonisolated_list(fl_graph* g);
@@ -278,7 +325,7 @@ int compute_ecc_bound(fl_graph* g);
 int compute_radii(fl_solve* s);
 int open_facilities(fl_solve* s);
 int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, int32_t* dist,
-          DBuf& X, DBuf& stampb, DBuf* fr, DBuf& frval);
+          DBuf& X, DBuf& stampb, DBuf* fr, DBuf& frval, int cls);
 int assign_clients(fl_solve* s);
 int objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserved);
 

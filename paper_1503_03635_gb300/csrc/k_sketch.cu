@@ -93,10 +93,12 @@ __global__ void __launch_bounds__(256) k_merge_hop(
     const int lane = lane_id();
     const int64_t n_active = n_active_ptr ? (int64_t)*n_active_ptr : n_active_host;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long cand_reads = 0, merging = 0;  // algorithmic-traffic counters of this warp
     for (int64_t w = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; w < n_active; w += warps) {
         const int32_t v = active[w];
         const int64_t beg = rowp[v], end = rowp[v + 1];
         const uint64_t old = lane < k ? S[(int64_t)v * k + lane] : kEmpty;
+        int vtotal = 0;
         uint64_t sk = old;
         int cnt_old = Scnt[v];
         const uint64_t kth_old = __shfl_sync(kFull, sk, k - 1);
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(256) k_merge_hop(
             int c = e < end ? (int)Dcp[u] : 0;
             int incl = warp_incl_scan(c);
             int total = __shfl_sync(kFull, incl, 31);
+            vtotal += total;
             for (int off = 0; off < total; off += 32) {
                 int t = off + lane;
                 // neighbour slot j holding flattened candidate t: #lanes with incl <= t
@@ -145,6 +148,8 @@ __global__ void __launch_bounds__(256) k_merge_hop(
             }
         }
         if (nbuf) sk = merge_candidates(sk, buf, k);
+        cand_reads += (unsigned long long)vtotal;
+        merging += vtotal > 0 ? 1ULL : 0ULL;
         // outputs
         const bool valid = lane < k && sk != kEmpty;
         const bool was_there = warp_member(old, sk);  // every lane takes part in the shuffles
@@ -182,6 +187,10 @@ __global__ void __launch_bounds__(256) k_merge_hop(
         }
         eat = __shfl_sync(kFull, eat, 0);
         if (lane < dcnt) stg_ent[eat + lane] = (int32_t)rank_vertex(seed, dv);
+    }
+    if (lane == 0 && merging) {
+        atomicAdd(&ctr->cand_reads, cand_reads);
+        atomicAdd(&ctr->merging, merging);
     }
 }
 
@@ -271,10 +280,10 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     FL_CUDA(cudaMemsetAsync(g->D[1].p, 0xff, nk * 8, st));
     FL_CUDA(cudaMemsetAsync(g->stamp.p, 0, (size_t)n * 4, st));
     FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st));
-    k_rank_init<<<grid_for(n, 256), 256, 0, st>>>(n, k, seed, g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(),
+    FL_LAUNCH(kProfSketchOther, k_rank_init<<<grid_for(n, 256), 256, 0, st>>>(n, k, seed, g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(),
                                                    g->D[0].as<uint64_t>(), g->Dcnt[0].as<uint8_t>(),
                                                    g->stg_ent.as<int32_t>(), g->stg_grp.as<StgGroup>(),
-                                                   g->vg.as<int32_t>(), g->ve.as<int32_t>(), g->ctr.as<Counters>());
+                                                   g->vg.as<int32_t>(), g->ve.as<int32_t>(), g->ctr.as<Counters>()));
     FL_CUDA(cudaGetLastError());
     FL_TRY(read_counters(g));
     if (g->h_ctr->error) {
@@ -292,6 +301,8 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     for (;; ++hop) {
         if (hop > kMaxHops) { rc = FL_ETIMEOUT; set_error(rc, "more than 65535 hops"); break; }
         total_merges += next_merges;
+        const int64_t hop_merges = next_merges;
+        const int64_t ent_before = used_ent;
         const int pin = (hop - 1) & 1, pout = hop & 1;
         const int32_t* act_list;
         int64_t n_act;
@@ -306,10 +317,10 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
             act_list = g->deg_list.as<int32_t>();
             n_act = g->n_nonisolated;
         } else {
-            k_expand<<<grid_for(n_front, 8), 256, 0, st>>>(g->frontier[pin].as<int32_t>(), n_front,
+            FL_LAUNCH(kProfSketchExpand, k_expand<<<grid_for(n_front, 8), 256, 0, st>>>(g->frontier[pin].as<int32_t>(), n_front,
                                                           g->rowp.as<int64_t>(), g->cols.as<int32_t>(),
                                                           g->stamp.as<uint32_t>(), (uint32_t)hop,
-                                                          act.as<int32_t>(), g->ctr.as<Counters>());
+                                                          act.as<int32_t>(), g->ctr.as<Counters>()));
             FL_CUDA(cudaGetLastError());
             FL_TRY(read_counters(g));
             act_list = act.as<int32_t>();
@@ -328,12 +339,12 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
         }
         FL_CUDA(cudaMemsetAsync(g->Dcnt[pout].p, 0, (size_t)n, st));
         if (n_act > 0) {
-            k_merge_hop<<<grid_for(n_act, 8), 256, 0, st>>>(
+            FL_LAUNCH(kProfSketchMerge, k_merge_hop<<<grid_for(n_act, 8), 256, 0, st>>>(
                 act_list, nullptr, n_act, g->rowp.as<int64_t>(), g->cols.as<int32_t>(), k, seed, hop,
                 g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[pin].as<uint64_t>(), g->Dcnt[pin].as<uint8_t>(),
                 g->D[pout].as<uint64_t>(), g->Dcnt[pout].as<uint8_t>(), g->frontier[pout].as<int32_t>(),
                 g->vg.as<int32_t>(), g->ve.as<int32_t>(), g->stg_ent.as<int32_t>(), g->stg_grp.as<StgGroup>(),
-                g->ctr.as<Counters>());
+                g->ctr.as<Counters>()));
             FL_CUDA(cudaGetLastError());
         }
         FL_TRY(read_counters(g));
@@ -343,6 +354,14 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
         used_grp = (int64_t)g->h_ctr->stg_groups;
         init.stg_entries = (unsigned long long)used_ent;
         init.stg_groups = (unsigned long long)used_grp;
+        // algorithmic bytes of this hop's merge: active row offsets (8 B), frontier
+        // columns (4 B per edge-merge), neighbour deltas (8 B per rank), own sketch
+        // read + write (16k B per merging vertex), new ADS entries (id + weight, 12 B)
+        {
+            const double A = (double)g->h_ctr->merging, SD = (double)g->h_ctr->cand_reads;
+            g->prof.bytes[kProfSketchMerge] += 8.0 * A + 4.0 * (double)hop_merges + 8.0 * SD + 16.0 * k * A +
+                                               12.0 * (double)(used_ent - ent_before);
+        }
         if (n_front == 0) break;
     }
     dfree(act);
@@ -362,10 +381,10 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     FL_TRY(scan_exclusive_i32_to_i64(g->ve.as<int32_t>(), g->eofs.as<int64_t>(), n, st, g->scratch));
     FL_CUDA(cudaMemcpyAsync(g->gofs.as<int64_t>() + n, &g->n_groups, 8, cudaMemcpyHostToDevice, st));
     FL_CUDA(cudaMemcpyAsync(g->eofs.as<int64_t>() + n, &g->n_entries, 8, cudaMemcpyHostToDevice, st));
-    k_ads_scatter<<<grid_for(used_grp, 256), 256, 0, st>>>(g->stg_grp.as<StgGroup>(), used_grp,
+    FL_LAUNCH(kProfSketchOther, k_ads_scatter<<<grid_for(used_grp, 256), 256, 0, st>>>(g->stg_grp.as<StgGroup>(), used_grp,
                                                           g->stg_ent.as<int32_t>(), g->gofs.as<int64_t>(),
                                                           g->eofs.as<int64_t>(), g->ginfo.as<uint32_t>(),
-                                                          g->gwt.as<double>(), g->eid.as<int32_t>());
+                                                          g->gwt.as<double>(), g->eid.as<int32_t>()));
     FL_CUDA(cudaGetLastError());
     FL_CUDA(cudaStreamSynchronize(st));
     FL_TRY(compute_ecc_bound(g));
@@ -427,17 +446,17 @@ int compute_ecc_bound(fl_graph* g) {
         cudaError_t e = cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(eccr.p, 0, (size_t)n * 4, st);
         if (e != cudaSuccess) { rc = status_of(e, "ecc init", __FILE__, __LINE__); break; }
-        k_roots<<<grid_for(n, 256), 256, 0, st>>>(g->S.as<uint64_t>(), g->k, g->seed, n, root_of.as<int32_t>(),
-                                                  roots.as<int32_t>(), g->ctr.as<Counters>());
+        FL_LAUNCH(kProfSketchOther, k_roots<<<grid_for(n, 256), 256, 0, st>>>(g->S.as<uint64_t>(), g->k, g->seed, n, root_of.as<int32_t>(),
+                                                  roots.as<int32_t>(), g->ctr.as<Counters>()));
         if ((rc = read_counters(g))) break;
         int64_t n_roots = (int64_t)g->h_ctr->aux0;
         if ((rc = msbfs(g, roots.as<int32_t>(), n_roots, label.as<int32_t>(), dist.as<int32_t>(), X, stampb,
-                        fr, frval)))
+                        fr, frval, kProfSketchOther)))
             break;
-        k_ecc_max<<<grid_for(n, 256), 256, 0, st>>>(label.as<int32_t>(), dist.as<int32_t>(), n,
-                                                    eccr.as<int32_t>());
-        k_ecc_ub<<<grid_for(n, 256), 256, 0, st>>>(label.as<int32_t>(), dist.as<int32_t>(), eccr.as<int32_t>(),
-                                                   n, g->ecc_ub.as<int32_t>());
+        FL_LAUNCH(kProfSketchOther, k_ecc_max<<<grid_for(n, 256), 256, 0, st>>>(label.as<int32_t>(), dist.as<int32_t>(), n,
+                                                    eccr.as<int32_t>()));
+        FL_LAUNCH(kProfSketchOther, k_ecc_ub<<<grid_for(n, 256), 256, 0, st>>>(label.as<int32_t>(), dist.as<int32_t>(), eccr.as<int32_t>(),
+                                                   n, g->ecc_ub.as<int32_t>()));
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { rc = status_of(e, "ecc bound", __FILE__, __LINE__); break; }
     } while (0);

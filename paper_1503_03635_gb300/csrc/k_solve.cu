@@ -117,7 +117,7 @@ __global__ void k_unpack_bfs(const unsigned long long* __restrict__ X, int64_t n
 }
 
 int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, int32_t* dist, DBuf& X,
-          DBuf& stampb, DBuf* fr, DBuf& frval) {
+          DBuf& stampb, DBuf* fr, DBuf& frval, int cls) {
     const int64_t n = g->n;
     cudaStream_t st = g->stream;
     FL_TRY(dalloc(X, (size_t)n * 8));
@@ -130,22 +130,22 @@ int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, i
     FL_CUDA(cudaMemsetAsync(stampb.p, 0, (size_t)n * 4, st));
     FL_CUDA(cudaMemsetAsync(cnt, 0, 64, st));
     if (n_src > 0) {
-        k_inject<<<grid_for(n_src, 256), 256, 0, st>>>(src_list, n_src, nullptr, 0ULL, nullptr,
+        FL_LAUNCH(cls, k_inject<<<grid_for(n_src, 256), 256, 0, st>>>(src_list, n_src, nullptr, 0ULL, nullptr,
                                                       X.as<unsigned long long>(), stampb.as<uint32_t>(), 1u,
-                                                      fr[0].as<int32_t>(), &cnt[0]);
+                                                      fr[0].as<int32_t>(), &cnt[0]));
         FL_CUDA(cudaGetLastError());
     }
     int cur = 0;
     int64_t n_cur = n_src;
     uint32_t level = 0;
     while (n_cur > 0) {
-        k_snapshot<<<grid_for(n_cur, 256), 256, 0, st>>>(fr[cur].as<int32_t>(), &cnt[cur],
+        FL_LAUNCH(cls, k_snapshot<<<grid_for(n_cur, 256), 256, 0, st>>>(fr[cur].as<int32_t>(), &cnt[cur],
                                                         X.as<unsigned long long>(), frval.as<unsigned long long>(),
-                                                        &cnt[cur ^ 1], nullptr, 0, nullptr, nullptr);
-        k_push<<<grid_for(n_cur, 8), 256, 0, st>>>(fr[cur].as<int32_t>(), frval.as<unsigned long long>(), &cnt[cur],
+                                                        &cnt[cur ^ 1], nullptr, 0, nullptr, nullptr));
+        FL_LAUNCH(cls, k_push<<<grid_for(n_cur, 8), 256, 0, st>>>(fr[cur].as<int32_t>(), frval.as<unsigned long long>(), &cnt[cur],
                                                   g->rowp.as<int64_t>(), g->cols.as<int32_t>(), 1ULL << 32,
                                                   X.as<unsigned long long>(), stampb.as<uint32_t>(), level + 2,
-                                                  fr[cur ^ 1].as<int32_t>(), &cnt[cur ^ 1]);
+                                                  fr[cur ^ 1].as<int32_t>(), &cnt[cur ^ 1]));
         FL_CUDA(cudaGetLastError());
         unsigned long long nn = 0;
         FL_CUDA(cudaMemcpyAsync(&nn, &cnt[cur ^ 1], 8, cudaMemcpyDeviceToHost, st));
@@ -154,7 +154,7 @@ int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, i
         cur ^= 1;
         ++level;
     }
-    k_unpack_bfs<<<grid_for(n, 256), 256, 0, st>>>(X.as<unsigned long long>(), n, label, dist);
+    FL_LAUNCH(cls, k_unpack_bfs<<<grid_for(n, 256), 256, 0, st>>>(X.as<unsigned long long>(), n, label, dist));
     FL_CUDA(cudaGetLastError());
     return FL_OK;
 }
@@ -235,13 +235,13 @@ int compute_radii(fl_solve* s) {
     fl_graph* g = s->g;
     cudaStream_t st = g->stream;
     FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st));
-    k_check_costs<<<grid_for(g->n, 256), 256, 0, st>>>(s->cost.as<double>(), g->n, g->ctr.as<Counters>());
+    FL_LAUNCH(kProfRadius, k_check_costs<<<grid_for(g->n, 256), 256, 0, st>>>(s->cost.as<double>(), g->n, g->ctr.as<Counters>()));
     FL_CUDA(cudaGetLastError());
     FL_TRY(read_counters(g));
     if (g->h_ctr->error) FL_FAIL(FL_EINVAL, "open_cost must be finite and > 0 for facilities, +inf otherwise");
-    k_radius<<<grid_for(g->n, 8), 256, 0, st>>>(g->n, s->cost.as<double>(), s->client.as<uint8_t>(),
+    FL_LAUNCH(kProfRadius, k_radius<<<grid_for(g->n, 8), 256, 0, st>>>(g->n, s->cost.as<double>(), s->client.as<uint8_t>(),
                                                g->gofs.as<int64_t>(), g->eofs.as<int64_t>(), g->ginfo.as<uint32_t>(),
-                                               g->gwt.as<double>(), g->eid.as<int32_t>(), s->radii.as<double>());
+                                               g->gwt.as<double>(), g->eid.as<int32_t>(), s->radii.as<double>()));
     FL_CUDA(cudaGetLastError());
     return FL_OK;
 }
@@ -426,9 +426,9 @@ int open_facilities(fl_solve* s) {
         return rc;
     }
     FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st));
-    k_candidates<<<grid_for(n, 256), 256, 0, st>>>(s->radii.as<double>(), n, g->seed, hi.as<uint64_t>(),
+    FL_LAUNCH(kProfKeys, k_candidates<<<grid_for(n, 256), 256, 0, st>>>(s->radii.as<double>(), n, g->seed, hi.as<uint64_t>(),
                                                    lo.as<uint64_t>(), val.as<uint32_t>(), s->state.as<uint8_t>(),
-                                                   g->ctr.as<Counters>());
+                                                   g->ctr.as<Counters>()));
     rc = read_counters(g);
     if (rc) { free_keys(); return rc; }
     const int64_t m = (int64_t)g->h_ctr->aux0;
@@ -438,10 +438,10 @@ int open_facilities(fl_solve* s) {
     int32_t* ulist[2] = {s->ulist.as<int32_t>(), s->ulist.as<int32_t>() + n};
     FL_CUDA(cudaMemsetAsync(cnt, 0, 64, st));
     if (m > 0) {
-        k_ordinals<<<grid_for(m, 256), 256, 0, st>>>(val.as<uint32_t>(), m, s->radii.as<double>(),
+        FL_LAUNCH(kProfKeys, k_ordinals<<<grid_for(m, 256), 256, 0, st>>>(val.as<uint32_t>(), m, s->radii.as<double>(),
                                                      g->ecc_ub.as<int32_t>(), s->ord.as<uint32_t>(),
                                                      s->fac_by_ord.as<int32_t>(), s->bcap.as<int32_t>(), ulist[0],
-                                                     &cnt[4]);
+                                                     &cnt[4]));
     }
     free_keys();
     FL_CUDA(cudaGetLastError());
@@ -474,7 +474,7 @@ int open_facilities(fl_solve* s) {
         // bucket the undecided facilities by ball radius
         FL_CUDA(cudaMemsetAsync(bcount, 0, (bmax + 1) * 4, st));
         FL_CUDA(cudaMemsetAsync(&cnt[4], 0, 8, st));
-        k_bucket_count<<<grid_for(n_u, 256), 256, 0, st>>>(ulist[cu], n_u, s->bcap.as<int32_t>(), bcount, &cnt[4]);
+        FL_LAUNCH(kProfMis, k_bucket_count<<<grid_for(n_u, 256), 256, 0, st>>>(ulist[cu], n_u, s->bcap.as<int32_t>(), bcount, &cnt[4]));
         FL_CUDA(cudaGetLastError());
         unsigned long long T64 = 0;
         FL_CUDA(cudaMemcpyAsync(&T64, &cnt[4], 8, cudaMemcpyDeviceToHost, st));
@@ -484,8 +484,8 @@ int open_facilities(fl_solve* s) {
         int32_t acc = 0;
         for (int b = 0; b <= T; ++b) { hoff[b] = acc; acc += hcount[b]; }
         FL_CUDA(cudaMemcpyAsync(cursor, hoff.data(), (T + 1) * 4, cudaMemcpyHostToDevice, st));
-        k_bucket_scatter<<<grid_for(n_u, 256), 256, 0, st>>>(ulist[cu], n_u, s->bcap.as<int32_t>(), cursor,
-                                                            s->ubuck.as<int32_t>());
+        FL_LAUNCH(kProfMis, k_bucket_scatter<<<grid_for(n_u, 256), 256, 0, st>>>(ulist[cu], n_u, s->bcap.as<int32_t>(), cursor,
+                                                            s->ubuck.as<int32_t>()));
         FL_CUDA(cudaGetLastError());
         const int32_t* ub = s->ubuck.as<int32_t>();
 
@@ -499,14 +499,14 @@ int open_facilities(fl_solve* s) {
         for (int t = 0; t <= T; ++t) {
             const int b = T - t;
             if (hcount[b] > 0)
-                k_inject<<<grid_for(hcount[b], 256), 256, 0, st>>>(ub + hoff[b], hcount[b], nullptr, hi_c,
+                FL_LAUNCH(kProfMis, k_inject<<<grid_for(hcount[b], 256), 256, 0, st>>>(ub + hoff[b], hcount[b], nullptr, hi_c,
                                                                   s->ord.as<uint32_t>(), X, stamp, sv0 + 1 + t, fr[c],
-                                                                  &cnt[c]);
-            k_snapshot<<<152 * 2, 256, 0, st>>>(fr[c], &cnt[c], X, frval, &cnt[c ^ 1], tstamp, epoch,
-                                                s->touched.as<int32_t>(), &cnt[2]);
+                                                                  &cnt[c]));
+            FL_LAUNCH(kProfMis, k_snapshot<<<152 * 2, 256, 0, st>>>(fr[c], &cnt[c], X, frval, &cnt[c ^ 1], tstamp, epoch,
+                                                s->touched.as<int32_t>(), &cnt[2]));
             if (t < T)
-                k_push<<<152 * 8, 256, 0, st>>>(fr[c], frval, &cnt[c], g->rowp.as<int64_t>(), g->cols.as<int32_t>(),
-                                                0ULL, X, stamp, sv0 + 2 + t, fr[c ^ 1], &cnt[c ^ 1]);
+                FL_LAUNCH(kProfMis, k_push<<<152 * 8, 256, 0, st>>>(fr[c], frval, &cnt[c], g->rowp.as<int64_t>(), g->cols.as<int32_t>(),
+                                                0ULL, X, stamp, sv0 + 2 + t, fr[c ^ 1], &cnt[c ^ 1]));
             c ^= 1;
         }
         FL_CUDA(cudaGetLastError());
@@ -518,33 +518,33 @@ int open_facilities(fl_solve* s) {
         FL_CUDA(cudaMemsetAsync(cnt, 0, 16, st));
         c = 0;
         const uint32_t sg0 = ++sv;
-        k_gather_seed<<<152 * 2, 256, 0, st>>>(s->touched.as<int32_t>(), &cnt[2], s->client.as<uint8_t>(),
+        FL_LAUNCH(kProfMis, k_gather_seed<<<152 * 2, 256, 0, st>>>(s->touched.as<int32_t>(), &cnt[2], s->client.as<uint8_t>(),
                                                s->claimed.as<uint8_t>(), hi_g, X, s->mval.as<uint32_t>(), stamp, sg0,
-                                               fr[c], &cnt[c]);
+                                               fr[c], &cnt[c]));
         if (hcount[0] > 0)
-            k_decide<<<grid_for(hcount[0], 256), 256, 0, st>>>(ub + hoff[0], hcount[0], X, hi_g,
+            FL_LAUNCH(kProfMis, k_decide<<<grid_for(hcount[0], 256), 256, 0, st>>>(ub + hoff[0], hcount[0], X, hi_g,
                                                                s->ord.as<uint32_t>(), s->state.as<uint8_t>(),
-                                                               g->ctr.as<Counters>());
+                                                               g->ctr.as<Counters>()));
         for (int b = 1; b <= T; ++b) {
-            k_snapshot<<<152 * 2, 256, 0, st>>>(fr[c], &cnt[c], X, frval, &cnt[c ^ 1], nullptr, 0, nullptr, nullptr);
-            k_push<<<152 * 8, 256, 0, st>>>(fr[c], frval, &cnt[c], g->rowp.as<int64_t>(), g->cols.as<int32_t>(), 0ULL,
-                                            X, stamp, sg0 + b, fr[c ^ 1], &cnt[c ^ 1]);
+            FL_LAUNCH(kProfMis, k_snapshot<<<152 * 2, 256, 0, st>>>(fr[c], &cnt[c], X, frval, &cnt[c ^ 1], nullptr, 0, nullptr, nullptr));
+            FL_LAUNCH(kProfMis, k_push<<<152 * 8, 256, 0, st>>>(fr[c], frval, &cnt[c], g->rowp.as<int64_t>(), g->cols.as<int32_t>(), 0ULL,
+                                            X, stamp, sg0 + b, fr[c ^ 1], &cnt[c ^ 1]));
             c ^= 1;
             if (hcount[b] > 0)
-                k_decide<<<grid_for(hcount[b], 256), 256, 0, st>>>(ub + hoff[b], hcount[b], X, hi_g,
+                FL_LAUNCH(kProfMis, k_decide<<<grid_for(hcount[b], 256), 256, 0, st>>>(ub + hoff[b], hcount[b], X, hi_g,
                                                                    s->ord.as<uint32_t>(), s->state.as<uint8_t>(),
-                                                                   g->ctr.as<Counters>());
+                                                                   g->ctr.as<Counters>()));
         }
         sv = sg0 + T + 1;
         FL_CUDA(cudaGetLastError());
 
         // ---- claim the balls of this round's winners; keep the undecided
-        k_claim<<<152 * 4, 256, 0, st>>>(s->touched.as<int32_t>(), &cnt[2], s->client.as<uint8_t>(),
+        FL_LAUNCH(kProfMis, k_claim<<<152 * 4, 256, 0, st>>>(s->touched.as<int32_t>(), &cnt[2], s->client.as<uint8_t>(),
                                          s->claimed.as<uint8_t>(), s->mval.as<uint32_t>(),
-                                         s->fac_by_ord.as<int32_t>(), s->state.as<uint8_t>());
+                                         s->fac_by_ord.as<int32_t>(), s->state.as<uint8_t>()));
         FL_CUDA(cudaMemsetAsync(&cnt[3], 0, 8, st));
-        k_compact_undecided<<<grid_for(n_u, 256), 256, 0, st>>>(ulist[cu], n_u, s->state.as<uint8_t>(),
-                                                               ulist[cu ^ 1], &cnt[3]);
+        FL_LAUNCH(kProfMis, k_compact_undecided<<<grid_for(n_u, 256), 256, 0, st>>>(ulist[cu], n_u, s->state.as<uint8_t>(),
+                                                               ulist[cu ^ 1], &cnt[3]));
         FL_CUDA(cudaGetLastError());
         unsigned long long nu = 0;
         FL_CUDA(cudaMemcpyAsync(&nu, &cnt[3], 8, cudaMemcpyDeviceToHost, st));
@@ -560,8 +560,8 @@ int open_facilities(fl_solve* s) {
     s->mis_rounds = rounds;
     // open set
     FL_CUDA(cudaMemsetAsync(&cnt[5], 0, 8, st));
-    k_open_list<<<grid_for(n, 256), 256, 0, st>>>(s->state.as<uint8_t>(), n, s->open.as<uint8_t>(),
-                                                  s->ulist.as<int32_t>(), &cnt[5]);
+    FL_LAUNCH(kProfMis, k_open_list<<<grid_for(n, 256), 256, 0, st>>>(s->state.as<uint8_t>(), n, s->open.as<uint8_t>(),
+                                                  s->ulist.as<int32_t>(), &cnt[5]));
     FL_CUDA(cudaGetLastError());
     unsigned long long no = 0;
     FL_CUDA(cudaMemcpyAsync(&no, &cnt[5], 8, cudaMemcpyDeviceToHost, st));
@@ -578,7 +578,7 @@ int assign_clients(fl_solve* s) {
     FL_TRY(dalloc(s->dist, (size_t)g->n * 4));
     // the open list was left in ulist by open_facilities
     return msbfs(g, s->ulist.as<int32_t>(), s->n_open, s->assign.as<int32_t>(), s->dist.as<int32_t>(), s->X,
-                 s->stamp, s->fr, s->frval);
+                 s->stamp, s->fr, s->frval, kProfBfs);
 }
 
 constexpr int kObjBlocks = 152 * 4;
@@ -620,8 +620,8 @@ int objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserved) 
     unsigned long long hs[2] = {0, 0};
     cudaError_t e = cudaMemsetAsync(sums, 0, 16, st);
     if (e == cudaSuccess) {
-        k_objective<<<kObjBlocks, 256, 0, st>>>(g->n, s->open.as<uint8_t>(), s->cost.as<double>(),
-                                                s->client.as<uint8_t>(), s->dist.as<int32_t>(), partial, sums);
+        FL_LAUNCH(kProfOther, k_objective<<<kObjBlocks, 256, 0, st>>>(g->n, s->open.as<uint8_t>(), s->cost.as<double>(),
+                                                s->client.as<uint8_t>(), s->dist.as<int32_t>(), partial, sums));
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), partial, kObjBlocks * 8, cudaMemcpyDeviceToHost, st);

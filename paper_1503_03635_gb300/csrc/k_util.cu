@@ -36,6 +36,57 @@ int last_error(char* buf, size_t len) {
     return t_status;
 }
 
+// ----------------------------------------------------------------- profiling
+
+static thread_local Prof* t_prof = nullptr;
+static thread_local cudaStream_t t_stream = nullptr;
+
+Prof* current_prof() { return t_prof; }
+void set_current_prof(Prof* p, cudaStream_t st) {
+    t_prof = p;
+    t_stream = st;
+}
+
+int prof_begin(int cls) {
+    Prof* p = t_prof;
+    if (!p) return -1;
+    p->launches[cls] += 1;
+    if (!p->on) return -1;
+    if (p->used * 2 + 2 > p->ev.size()) {
+        for (int i = 0; i < 64; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            p->ev.push_back(e);
+        }
+    }
+    size_t slot = p->used++;
+    if (p->cls.size() < p->used) p->cls.resize(p->used);
+    p->cls[slot] = cls;
+    cudaEventRecord(p->ev[2 * slot], t_stream);
+    return (int)slot;
+}
+
+void prof_end(int slot) {
+    Prof* p = t_prof;
+    if (!p || slot < 0) return;
+    cudaEventRecord(p->ev[2 * slot + 1], t_stream);
+}
+
+int prof_drain(Prof* p) {
+    if (!p || !p->used) return FL_OK;
+    for (size_t i = 0; i < p->used; ++i) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, p->ev[2 * i], p->ev[2 * i + 1]);
+        if (e != cudaSuccess) {
+            p->used = 0;
+            return status_of(e, "cudaEventElapsedTime", __FILE__, __LINE__);
+        }
+        p->ms[p->cls[i]] += ms;
+    }
+    p->used = 0;
+    return FL_OK;
+}
+
 // ----------------------------------------------------------------- buffers
 
 int dalloc(DBuf& b, size_t bytes) {
@@ -151,11 +202,11 @@ static size_t scan_tmp_bytes(int64_t n) {
 }
 
 template <class Tin>
-static int scan_rec(const Tin* in, int64_t* out, int64_t n, cudaStream_t st, char* tmp) {
+static int scan_rec(const Tin* in, int64_t* out, int64_t n, cudaStream_t st, char* tmp, int cls) {
     if (n <= 0) return FL_OK;
     int64_t tiles = (n + kScanTile - 1) / kScanTile;
     if (tiles == 1) {
-        k_tile_scan<Tin><<<1, kScanThreads, 0, st>>>(in, n, nullptr, out);
+        FL_LAUNCH(cls, k_tile_scan<Tin><<<1, kScanThreads, 0, st>>>(in, n, nullptr, out));
         FL_CUDA(cudaGetLastError());
         return FL_OK;
     }
@@ -163,22 +214,23 @@ static int scan_rec(const Tin* in, int64_t* out, int64_t n, cudaStream_t st, cha
     int64_t* offs = sums + tiles;
     char* next = reinterpret_cast<char*>(offs + tiles);
     next += (256 - (reinterpret_cast<uintptr_t>(next) & 255)) & 255;
-    k_tile_sums<Tin><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, sums);
+    FL_LAUNCH(cls, k_tile_sums<Tin><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, sums));
     FL_CUDA(cudaGetLastError());
-    FL_TRY(scan_rec<int64_t>(sums, offs, tiles, st, next));
-    k_tile_scan<Tin><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, offs, out);
+    FL_TRY(scan_rec<int64_t>(sums, offs, tiles, st, next, cls));
+    FL_LAUNCH(cls, k_tile_scan<Tin><<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, offs, out));
     FL_CUDA(cudaGetLastError());
     return FL_OK;
 }
 
-int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st, DBuf& tmp) {
+int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st, DBuf& tmp, int cls) {
     FL_TRY(dalloc(tmp, scan_tmp_bytes(n)));
-    return scan_rec<int64_t>(in, out, n, st, tmp.as<char>());
+    return scan_rec<int64_t>(in, out, n, st, tmp.as<char>(), cls);
 }
 
-int scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st, DBuf& tmp) {
+int scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st, DBuf& tmp,
+                              int cls) {
     FL_TRY(dalloc(tmp, scan_tmp_bytes(n)));
-    return scan_rec<int32_t>(in, out, n, st, tmp.as<char>());
+    return scan_rec<int32_t>(in, out, n, st, tmp.as<char>(), cls);
 }
 
 // ----------------------------------------------------------------- radix sort
@@ -237,7 +289,7 @@ __global__ void k_digit_scatter(const uint64_t* __restrict__ key, const uint64_t
     }
 }
 
-int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaStream_t st, DBuf& tmp) {
+int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaStream_t st, DBuf& tmp, int cls) {
     if (n <= 1) return FL_OK;
     int nblocks = (int)((n + kSortTile - 1) / kSortTile);
     int64_t hn = 16LL * nblocks;
@@ -260,11 +312,11 @@ int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaSt
     for (int pass = 0; pass < 32; ++pass) {
         const uint64_t* key = pass < 16 ? alo : ahi;
         int shift = 4 * (pass & 15);
-        k_digit_hist<<<nblocks, kSortThreads, 0, st>>>(key, n, shift, nblocks, hist);
+        FL_LAUNCH(cls, k_digit_hist<<<nblocks, kSortThreads, 0, st>>>(key, n, shift, nblocks, hist));
         FL_CUDA(cudaGetLastError());
-        FL_TRY(scan_rec<int32_t>(hist, offs, hn, st, stmp));
-        k_digit_scatter<<<nblocks, kSortThreads, 0, st>>>(key, ahi, alo, aval, n, shift, nblocks, offs,
-                                                          bhi, blo, bval);
+        FL_TRY(scan_rec<int32_t>(hist, offs, hn, st, stmp, cls));
+        FL_LAUNCH(cls, k_digit_scatter<<<nblocks, kSortThreads, 0, st>>>(key, ahi, alo, aval, n, shift, nblocks, offs,
+                                                          bhi, blo, bval));
         FL_CUDA(cudaGetLastError());
         std::swap(ahi, bhi);
         std::swap(alo, blo);
@@ -299,8 +351,8 @@ int read_counters(fl_graph* g) {
 
 int validate_csr(fl_graph* g) {
     FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), g->stream));
-    k_validate_csr<<<152 * 8, 256, 0, g->stream>>>(g->rowp.as<int64_t>(), g->cols.as<int32_t>(), g->n,
-                                                    g->nnz, g->ctr.as<Counters>());
+    FL_LAUNCH(kProfOther, k_validate_csr<<<152 * 8, 256, 0, g->stream>>>(g->rowp.as<int64_t>(), g->cols.as<int32_t>(), g->n,
+                                                    g->nnz, g->ctr.as<Counters>()));
     FL_CUDA(cudaGetLastError());
     FL_TRY(read_counters(g));
     if (g->h_ctr->error) {
@@ -333,12 +385,12 @@ int build_nonisolated_list(fl_graph* g) {
     if (rc == FL_OK) rc = dalloc(pos, (size_t)(n + 1) * 8);
     if (rc == FL_OK) rc = dalloc(g->deg_list, (size_t)n * 4);
     if (rc == FL_OK) {
-        k_flag_nonisolated<<<152 * 8, 256, 0, g->stream>>>(g->rowp.as<int64_t>(), n, flag.as<int32_t>());
-        rc = scan_exclusive_i32_to_i64(flag.as<int32_t>(), pos.as<int64_t>(), n, g->stream, g->scratch);
+        FL_LAUNCH(kProfOther, k_flag_nonisolated<<<152 * 8, 256, 0, g->stream>>>(g->rowp.as<int64_t>(), n, flag.as<int32_t>()));
+        rc = scan_exclusive_i32_to_i64(flag.as<int32_t>(), pos.as<int64_t>(), n, g->stream, g->scratch, kProfOther);
     }
     if (rc == FL_OK) {
-        k_scatter_flagged<<<152 * 8, 256, 0, g->stream>>>(flag.as<int32_t>(), pos.as<int64_t>(), n,
-                                                          g->deg_list.as<int32_t>());
+        FL_LAUNCH(kProfOther, k_scatter_flagged<<<152 * 8, 256, 0, g->stream>>>(flag.as<int32_t>(), pos.as<int64_t>(), n,
+                                                          g->deg_list.as<int32_t>()));
         int64_t last_pos = 0;
         int32_t last_flag = 0;
         cudaError_t e = cudaMemcpyAsync(&last_pos, pos.as<int64_t>() + n - 1, 8, cudaMemcpyDeviceToHost, g->stream);
