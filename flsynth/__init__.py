@@ -16,7 +16,8 @@ Section 5 and Table 1, stood in for by seeded R-MAT and Erdos-Renyi graphs):
 * ``rmat26`` -- the same recipe at scale 26; clients Bernoulli(0.5), facilities
   Bernoulli(0.1) independently, facility costs log-uniform in [10, 10^4], other
   vertices +inf; k=16.
-* ``rmatS`` for other scales (tests): the rmat20 recipe at scale S.
+* ``rmatS`` for other scales (tests): the rmat20 recipe at scale S;
+  ``rmat26sS``: the rmat26 recipe at scale S (profiling at a smaller footprint).
 
 Seeds: graph seed 42 + config number (er10k=1, rmat20=2, rmat26=3, rmat23=5),
 sketch seed 1, mask/cost seed 7, query seed 11.
@@ -175,10 +176,12 @@ def config(name: str) -> Workload:
         return from_csr(name, rowp, cols, 16, SKETCH_SEED,
                         np.full(n, 20.0), np.ones(n, np.uint8))
     if name.startswith("rmat"):
-        scale = int(name[4:])
+        # "rmat26sS": the rmat26 recipe (masks, costs, k) at scale S
+        c3 = name.startswith("rmat26s")
+        scale = int(name[7:]) if c3 else int(name[4:])
         rowp, cols = rmat(scale, 16, 42 + {20: 2, 26: 3, 23: 5}.get(scale, scale))
         n = 1 << scale
-        if scale == 26:
+        if scale == 26 or c3:
             client = bernoulli(n, MASK_SEED, 0.5)
             fac = bernoulli(n, MASK_SEED + 1, 0.1)
             cost = loguniform(n, MASK_SEED + 2, 10.0, 1.0e4, fac)
