@@ -30,10 +30,10 @@ int copy_out(void* dst, const void* src, size_t bytes, int mem_kind, cudaStream_
 }
 
 void destroy_graph(fl_graph* g) {
-    DBuf* bufs[] = {&g->rowp, &g->cols, &g->deg_list, &g->S, &g->Scnt, &g->D[0], &g->D[1], &g->Dcnt[0],
-                    &g->Dcnt[1], &g->frontier[0], &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent,
-                    &g->stg_grp, &g->stg_wt, &g->gofs, &g->eofs, &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub,
-                    &g->ctr, &g->scratch};
+    DBuf* bufs[] = {&g->rowp, &g->cols, &g->low_list, &g->hub_list, &g->hub_seg, &g->seg_hub, &g->part,
+                    &g->S, &g->Scnt, &g->D[0], &g->D[1], &g->Dcnt[0], &g->Dcnt[1], &g->frontier[0],
+                    &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent, &g->stg_grp, &g->gofs, &g->eofs,
+                    &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub, &g->ctr, &g->scratch};
     for (DBuf* b : bufs) dfree(*b);
     for (cudaEvent_t e : g->prof.ev) cudaEventDestroy(e);
     if (g->h_ctr) cudaFreeHost(g->h_ctr);
@@ -114,7 +114,6 @@ int fl_graph_create(int64_t n, const int64_t* row_off, const int32_t* cols, int6
         if (e != cudaSuccess) { rc = status_of(e, "CSR upload", __FILE__, __LINE__); break; }
         set_current_prof(&g->prof, g->stream);
         if ((rc = validate_csr(g))) break;
-        if ((rc = build_nonisolated_list(g))) break;
     } while (0);
     if (rc != FL_OK) {
         destroy_graph(g);

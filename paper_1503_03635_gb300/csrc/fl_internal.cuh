@@ -200,6 +200,87 @@ __device__ __forceinline__ long long warp_append(bool pred, unsigned long long* 
     return pred ? (long long)(base + __popc(m & ((1u << lane) - 1u))) : -1LL;
 }
 
+// ----------------------------------------------------------------- group primitives
+// A group is G consecutive lanes of a warp (G = 16 or 32) that works on one
+// vertex; a G-lane list holds up to G uint64 values, one per lane, ascending,
+// padded with kEmpty.  All sync intrinsics use the group's own lane mask, so
+// the two half-warp groups of a warp may diverge.
+
+template <int G>
+struct Grp {
+    unsigned mask;
+    int l;      // lane within the group
+    int shift;  // position of the group's bits in a warp ballot
+    __device__ __forceinline__ Grp() {
+        const int lane = lane_id();
+        l = lane & (G - 1);
+        shift = (G == 32) ? 0 : (lane & 16);
+        mask = (G == 32) ? kFull : (0xffffu << shift);
+    }
+    __device__ __forceinline__ unsigned ballot(bool p) const {
+        unsigned b = __ballot_sync(mask, p);
+        return (G == 32) ? b : ((b >> shift) & 0xffffu);
+    }
+    template <class T>
+    __device__ __forceinline__ T shfl(T x, int src) const { return __shfl_sync(mask, x, src, G); }
+    template <class T>
+    __device__ __forceinline__ T shfl_xor(T x, int m) const { return __shfl_xor_sync(mask, x, m, G); }
+    template <class T>
+    __device__ __forceinline__ T shfl_up(T x, int d) const { return __shfl_up_sync(mask, x, d, G); }
+};
+
+// Bitonic sort of a G-lane list (ascending).
+template <int G>
+__device__ __forceinline__ uint64_t grp_sort(const Grp<G>& g, uint64_t x) {
+#pragma unroll
+    for (int k = 2; k <= G; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            uint64_t y = g.shfl_xor(x, j);
+            bool up = (g.l & k) == 0 || k == G;
+            bool low = (g.l & j) == 0;
+            x = (low == up) ? umin64(x, y) : umax64(x, y);
+        }
+    }
+    return x;
+}
+
+// The G smallest of two ascending G-lane lists, ascending.
+template <int G>
+__device__ __forceinline__ uint64_t grp_merge_low(const Grp<G>& g, uint64_t a, uint64_t b) {
+    uint64_t c = umin64(a, g.shfl(b, G - 1 - g.l));
+#pragma unroll
+    for (int j = G / 2; j > 0; j >>= 1) {
+        uint64_t y = g.shfl_xor(c, j);
+        c = (g.l & j) ? umax64(c, y) : umin64(c, y);
+    }
+    return c;
+}
+
+// Is x an entry of the ascending G-lane list L?  (every lane of the group calls)
+template <int G>
+__device__ __forceinline__ bool grp_member(const Grp<G>& g, uint64_t L, uint64_t x) {
+    int pos = 0;
+#pragma unroll
+    for (int s = G / 2; s > 0; s >>= 1) {
+        uint64_t y = g.shfl(L, pos + s - 1);
+        if (y < x) pos += s;
+    }
+    uint64_t last = g.shfl(L, G - 1);
+    if (pos == G - 1 && last < x) pos = G;
+    uint64_t y = g.shfl(L, pos & (G - 1));
+    return pos < G && y == x;
+}
+
+// Gather the lanes in `keep` (group-relative bits) to lanes 0.., order kept.
+template <int G>
+__device__ __forceinline__ uint64_t grp_compact(const Grp<G>& g, uint64_t x, unsigned keep, uint64_t fill) {
+    int total = __popc(keep);
+    int src = g.l < total ? nth_set_bit(keep, g.l) : 0;
+    uint64_t y = g.shfl(x, src);
+    return g.l < total ? y : fill;
+}
+
 // ----------------------------------------------------------------- device counters
 
 // Small block of device counters read back by the host between launches.
@@ -263,8 +344,13 @@ struct fl_graph {
     int64_t n = 0, nnz = 0;
     cudaStream_t stream = nullptr;
     fl::DBuf rowp, cols;           // int64[n+1], int32[nnz]
-    fl::DBuf deg_list;             // int32[n]: non-isolated vertices (static active list)
-    int64_t n_nonisolated = 0;
+    // static work lists: non-hub non-isolated vertices, hubs, hub segments
+    int lists_ready = 0;
+    fl::DBuf low_list, hub_list;   // int32[n_low], int32[n_hubs]
+    fl::DBuf hub_seg;              // int64[n_hubs+1]: first segment of each hub
+    fl::DBuf seg_hub;              // int32[n_seg]: hub of each segment
+    int64_t n_low = 0, n_hubs = 0, n_seg = 0;
+    fl::DBuf part;                 // uint64[n_seg*k]: partial bottom-k of each hub segment (scratch)
     // sketches
     int k = 0;
     uint64_t seed = 0;
@@ -275,10 +361,10 @@ struct fl_graph {
     fl::DBuf frontier[2];          // int32[n]
     fl::DBuf stamp;                // uint32[n]
     fl::DBuf vg, ve;               // int32[n] per-vertex running group / entry counts
-    fl::DBuf stg_ent;              // int32 staging entries
-    fl::DBuf stg_grp;              // staging group records
-    fl::DBuf stg_wt;               // double staging weights
-    size_t stg_ent_cap = 0, stg_grp_cap = 0;
+    fl::DBuf stg_ent;              // int32 staging entries (k per slot)
+    fl::DBuf stg_grp;              // staging group records (one per slot)
+    size_t stg_grp_cap = 0;        // slots
+    int stg_k = 0;
     // ADS (vertex-major)
     fl::DBuf gofs, eofs;           // int64[n+1]
     fl::DBuf ginfo, gwt, eid;      // uint32[G], double[G], int32[E]
@@ -318,7 +404,7 @@ int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaSt
                     int cls = kProfKeys);
 
 int validate_csr(fl_graph* g);
-int build_nonisolated_list(fl_graph* g);
+int build_work_lists(fl_graph* g);
 int build_sketches(fl_graph* g, int k, uint64_t seed);
 int compute_ecc_bound(fl_graph* g);
 

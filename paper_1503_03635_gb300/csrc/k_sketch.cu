@@ -7,8 +7,17 @@
 //   Scnt[v]           number of ranks in S[v]
 //   D[p][v*k + i]     entries v gained at the previous / current hop (ranks)
 //   Dcnt[p][v]        their number (0 = v is not in the frontier)
-//   staging           per hop, one group record per vertex that changed and
-//                     its entry ids; compacted to a vertex-major ADS at the end
+//   staging           one group slot per work item of every hop (v, hop, HIP
+//                     weight, counts) and k entry slots; compacted into the
+//                     vertex-major ADS after the last hop
+//
+// Work decomposition of one hop.  A group of G lanes (G = 16 when k <= 16,
+// else 32) owns one vertex: lane i holds S[v][i].  Non-hub vertices are
+// processed directly (k_hop_vertices).  Hubs (degree > kHubDeg) are cut into
+// segments of kSeg edges; each segment yields a partial bottom-k of its
+// candidates in scratch (k_hop_hub_segments), and one group per hub merges
+// the partials into the hub's sketch (k_hop_hubs).  Bottom-k of a union is the
+// bottom-k of the union of bottom-k's, so the split does not change results.
 #include <algorithm>
 #include <cstdio>
 #include <vector>
@@ -18,12 +27,11 @@
 namespace fl {
 
 struct StgGroup {
-    int64_t at;     // first entry in the staging entry array
     double wt;      // HIP weight of the counted entries
     int32_t v;      // vertex
     int32_t gidx;   // index of this group among v's groups
     int32_t eidx;   // index of its first entry among v's entries
-    uint32_t info;  // hop | cnt << 16 | counted << 24
+    uint32_t info;  // hop | cnt << 16 | counted << 24; 0 = empty slot
 };
 
 __host__ __device__ __forceinline__ uint32_t pack_info(int hop, int cnt, int counted) {
@@ -31,6 +39,13 @@ __host__ __device__ __forceinline__ uint32_t pack_info(int hop, int cnt, int cou
 }
 
 constexpr int kMaxHops = 65535;
+constexpr int kHubDeg = 2048;  // vertices with more neighbours are split into segments
+constexpr int kSeg = 2048;     // edges per hub segment
+
+// Per-group counters accumulated in registers and flushed once per group.
+struct HopCounters {
+    unsigned long long front = 0, merges = 0, cand = 0, merging = 0;
+};
 
 // ------------------------------------------------------------------ hop 0
 
@@ -46,9 +61,8 @@ __global__ void k_rank_init(int64_t n, int k, uint64_t seed, uint64_t* __restric
         Scnt[v] = 1;
         D0[v * k] = r;
         Dcnt0[v] = 1;
-        stg_ent[v] = (int32_t)v;
+        stg_ent[v * k] = (int32_t)v;
         StgGroup gr;
-        gr.at = v;
         gr.wt = 1.0;  // a one-vertex ball: fewer than k ranks (k >= 2)
         gr.v = (int32_t)v;
         gr.gidx = 0;
@@ -60,141 +74,289 @@ __global__ void k_rank_init(int64_t n, int k, uint64_t seed, uint64_t* __restric
     }
 }
 
-// ------------------------------------------------------------------ one hop
+// ------------------------------------------------------------------ group sketch updates
 
-// Merge a buffer of candidate ranks (one per lane, unsorted, kEmpty = none)
-// into the ascending sketch list `sk` (k valid slots), keeping the k smallest
-// distinct ranks.  Returns the new list; lanes >= k hold kEmpty.
-__device__ __forceinline__ uint64_t merge_candidates(uint64_t sk, uint64_t buf, int k) {
-    const int lane = lane_id();
-    buf = warp_sort(buf);
-    uint64_t prev = __shfl_up_sync(kFull, buf, 1);
-    bool dup = lane > 0 && prev == buf;
-    bool in_sk = warp_member(sk, buf);
-    unsigned keep = __ballot_sync(kFull, buf != kEmpty && !dup && !in_sk);
-    if (!keep) return sk;
-    buf = warp_compact(buf, keep, kEmpty);
-    uint64_t m = warp_merge_low(sk, buf);
-    return lane < k ? m : kEmpty;
+// Running sketch of one group: list `sk` (k valid lanes), its size `cnt` and
+// the filter `tau` (= sk[k-1] when full, else `tau_base`: kEmpty for a
+// vertex's own sketch, the vertex's old k-th rank for a hub partial).
+template <int G>
+struct Sketch {
+    uint64_t sk;
+    int cnt;
+    uint64_t tau;
+    uint64_t tau_base;
+    __device__ __forceinline__ void retau(const Grp<G>& g, int k) {
+        uint64_t kth = g.shfl(sk, k - 1);
+        tau = cnt == k ? kth : tau_base;
+    }
+};
+
+// Insert one rank x (uniform over the group, x < tau) unless present.
+template <int G>
+__device__ __forceinline__ void insert_one(const Grp<G>& g, int k, uint64_t x, Sketch<G>& s) {
+    if (g.ballot(s.sk == x)) return;
+    int p = __popc(g.ballot(s.sk < x));
+    uint64_t up = g.shfl_up(s.sk, 1);
+    s.sk = (g.l > p) ? up : ((g.l == p) ? x : s.sk);
+    if (g.l >= k) s.sk = kEmpty;
+    if (s.cnt < k) ++s.cnt;
+    s.retau(g, k);
 }
 
-// Warp per active vertex v: S_h(v) = bottom-k(S_{h-1}(v) U union_{u in N(v)} D_{h-1}(u)).
-// Candidates of up to 32 neighbours are flattened into waves of 32 loads;
-// only ranks below the current k-th rank are kept in a per-lane buffer that
-// is merged when full.  Then the new entries D_h(v) = S_h(v) \ S_{h-1}(v) are
-// written for the next hop and staged as the hop-h ADS group of v.
-__global__ void __launch_bounds__(256) k_merge_hop(
-    const int32_t* __restrict__ active, const unsigned long long* __restrict__ n_active_ptr, int64_t n_active_host,
-    const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols, int k, uint64_t seed, int hop,
-    uint64_t* __restrict__ S, uint8_t* __restrict__ Scnt, const uint64_t* __restrict__ Dp,
-    const uint8_t* __restrict__ Dcp, uint64_t* __restrict__ Dc, uint8_t* __restrict__ Dcc,
-    int32_t* __restrict__ fr_next, int32_t* __restrict__ vg, int32_t* __restrict__ ve,
-    int32_t* __restrict__ stg_ent, StgGroup* __restrict__ stg_grp, Counters* ctr) {
-    const int lane = lane_id();
-    const int64_t n_active = n_active_ptr ? (int64_t)*n_active_ptr : n_active_host;
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long cand_reads = 0, merging = 0;  // algorithmic-traffic counters of this warp
-    for (int64_t w = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; w < n_active; w += warps) {
-        const int32_t v = active[w];
-        const int64_t beg = rowp[v], end = rowp[v + 1];
-        const uint64_t old = lane < k ? S[(int64_t)v * k + lane] : kEmpty;
-        int vtotal = 0;
-        uint64_t sk = old;
-        int cnt_old = Scnt[v];
-        const uint64_t kth_old = __shfl_sync(kFull, sk, k - 1);
-        uint64_t tau = cnt_old == k ? kth_old : kEmpty;
-        uint64_t buf = kEmpty;
-        int nbuf = 0;
-        for (int64_t cb = beg; cb < end; cb += 32) {
-            int64_t e = cb + lane;
-            int32_t u = e < end ? cols[e] : 0;
-            int c = e < end ? (int)Dcp[u] : 0;
-            int incl = warp_incl_scan(c);
-            int total = __shfl_sync(kFull, incl, 31);
-            vtotal += total;
-            for (int off = 0; off < total; off += 32) {
-                int t = off + lane;
-                // neighbour slot j holding flattened candidate t: #lanes with incl <= t
-                int j = 0;
-#pragma unroll
-                for (int s = 16; s > 0; s >>= 1) {
-                    int y = __shfl_sync(kFull, incl, j + s - 1);
-                    if (y <= t) j += s;
+// Merge a batch of candidates (one per lane, kEmpty = none; unsorted, may
+// repeat or already be in the sketch) keeping the k smallest distinct ranks.
+template <int G>
+__device__ __forceinline__ void merge_batch(const Grp<G>& g, int k, uint64_t buf, Sketch<G>& s) {
+    buf = grp_sort(g, buf);
+    uint64_t prev = g.shfl_up(buf, 1);
+    bool dup = g.l > 0 && prev == buf;
+    bool in_sk = grp_member(g, s.sk, buf);
+    unsigned keep = g.ballot(buf != kEmpty && !dup && !in_sk);
+    if (!keep) return;
+    buf = grp_compact(g, buf, keep, kEmpty);
+    uint64_t m = grp_merge_low(g, s.sk, buf);
+    s.sk = g.l < k ? m : kEmpty;
+    s.cnt = __popc(g.ballot(s.sk != kEmpty));
+    s.retau(g, k);
+}
+
+// Merge an ascending list of distinct candidates (lanes 0.., kEmpty after)
+// into the sketch: drop the ones already present, then one bitonic merge.
+template <int G>
+__device__ __forceinline__ void merge_sorted(const Grp<G>& g, int k, uint64_t x, Sketch<G>& s) {
+    const bool in_sk = grp_member(g, s.sk, x);
+    const unsigned have = g.ballot(x != kEmpty);
+    const unsigned keep = g.ballot(x != kEmpty && !in_sk);
+    if (!keep) return;
+    if (keep != have) x = grp_compact(g, x, keep, kEmpty);
+    const uint64_t m = grp_merge_low(g, s.sk, x);
+    s.sk = g.l < k ? m : kEmpty;
+    s.cnt = __popc(g.ballot(s.sk != kEmpty));
+    s.retau(g, k);
+}
+
+// Absorb one batch of candidates: filter by tau, then insert one by one when
+// few survive, else merge the whole batch.
+template <int G>
+__device__ __forceinline__ void absorb(const Grp<G>& g, int k, uint64_t x, Sketch<G>& s) {
+    unsigned m = g.ballot(x < s.tau);
+    if (!m) return;
+    if (__popc(m) <= 2) {
+        while (m) {
+            int j = __ffs(m) - 1;
+            m &= m - 1;
+            uint64_t xj = g.shfl(x, j);
+            if (xj < s.tau) insert_one(g, k, xj, s);
+        }
+    } else {
+        merge_batch(g, k, x < s.tau ? x : kEmpty, s);
+    }
+}
+
+// Absorb the candidates of CSR entries [e0, e1): at hop 1 the neighbours' own
+// ranks (recomputed from their ids), later the entries each neighbour gained
+// at the previous hop.  Lane j of the group owns neighbour j of a chunk of G
+// neighbours and loads the first (smallest) entry of its list: G independent
+// loads that also filter whole lists.  Each neighbour whose smallest entry is
+// below the filter then has its list loaded across the group; the entries
+// below the filter form an ascending prefix, absorbed by 1-2 insertions or one
+// bitonic merge.
+template <int G>
+__device__ __forceinline__ void gather_range(const Grp<G>& g, int k, int hop, uint64_t seed,
+                                             const int32_t* __restrict__ cols, int64_t e0, int64_t e1,
+                                             const uint8_t* __restrict__ Dcp, const uint64_t* __restrict__ Dp,
+                                             Sketch<G>& s, unsigned long long& cand) {
+    for (int64_t cb = e0; cb < e1; cb += G) {
+        const int64_t e = cb + g.l;
+        const bool in = e < e1;
+        const int32_t u = in ? __ldg(&cols[e]) : 0;
+        if (hop == 1) {
+            absorb(g, k, in ? vertex_rank(seed, u) : kEmpty, s);
+            continue;
+        }
+        const int c = in ? (int)__ldg(&Dcp[u]) : 0;
+        const uint64_t first = c > 0 ? __ldg(&Dp[(int64_t)u * k]) : kEmpty;
+        cand += c > 0 ? 1ULL : 0ULL;
+        unsigned live = g.ballot(first < s.tau);
+        while (live) {
+            const int j = __ffs(live) - 1;
+            live &= live - 1;
+            const int cj = g.shfl(c, j);
+            const uint64_t fj = g.shfl(first, j);
+            if (!(fj < s.tau)) continue;  // the filter tightened since the first loads
+            if (cj == 1) {
+                insert_one(g, k, fj, s);
+                continue;
+            }
+            const int uj = g.shfl(u, j);
+            uint64_t x = (g.l > 0 && g.l < cj) ? __ldg(&Dp[(int64_t)uj * k + g.l]) : kEmpty;
+            cand += (g.l > 0 && g.l < cj) ? 1ULL : 0ULL;
+            if (g.l == 0) x = fj;
+            const unsigned pm = g.ballot(x < s.tau);  // an ascending prefix of the list
+            if (__popc(pm) <= 2) {
+                insert_one(g, k, fj, s);
+                if (pm & 2u) {
+                    const uint64_t x1 = g.shfl(x, 1);
+                    if (x1 < s.tau) insert_one(g, k, x1, s);
                 }
-                j = j > 31 ? 31 : j;
-                int uj = __shfl_sync(kFull, u, j);
-                int ij = __shfl_sync(kFull, incl, j) - __shfl_sync(kFull, c, j);
-                uint64_t x = t < total ? Dp[(int64_t)uj * k + (t - ij)] : kEmpty;
-                bool ok = x < tau;
-                unsigned vm = __ballot_sync(kFull, ok);
-                int nv = __popc(vm);
-                if (nv == 0) continue;
-                if (nbuf + nv > 32) {
-                    sk = merge_candidates(sk, buf, k);
-                    tau = __shfl_sync(kFull, sk, k - 1);
-                    buf = kEmpty;
-                    nbuf = 0;
-                    ok = x < tau;
-                    vm = __ballot_sync(kFull, ok);
-                    nv = __popc(vm);
-                    if (nv == 0) continue;
-                }
-                // append the kept candidates at buffer slots nbuf .. nbuf+nv-1
-                int p = lane - nbuf;
-                int src = (p >= 0 && p < nv) ? nth_set_bit(vm, p) : 0;
-                uint64_t y = __shfl_sync(kFull, x, src);
-                if (p >= 0 && p < nv) buf = y;
-                nbuf += nv;
+            } else {
+                merge_sorted(g, k, x < s.tau ? x : kEmpty, s);
             }
         }
-        if (nbuf) sk = merge_candidates(sk, buf, k);
-        cand_reads += (unsigned long long)vtotal;
-        merging += vtotal > 0 ? 1ULL : 0ULL;
-        // outputs
-        const bool valid = lane < k && sk != kEmpty;
-        const bool was_there = warp_member(old, sk);  // every lane takes part in the shuffles
-        const bool is_new = valid && !was_there;
-        const unsigned newm = __ballot_sync(kFull, is_new);
-        const int dcnt = __popc(newm);
-        const int cnt_new = __popc(__ballot_sync(kFull, valid));
-        if (dcnt == 0) continue;  // sketch unchanged (and Dc count is already 0)
-        if (lane < k) S[(int64_t)v * k + lane] = sk;
-        const uint64_t dv = warp_compact(sk, newm, kEmpty);
-        if (lane < dcnt) Dc[(int64_t)v * k + lane] = dv;
-        const int counted = cnt_new < k ? dcnt : __popc(newm & ((1u << (k - 1)) - 1u));
-        const uint64_t kth = __shfl_sync(kFull, sk, k - 1);
-        int64_t eat = 0;
-        if (lane == 0) {
-            Scnt[v] = (uint8_t)cnt_new;
-            Dcc[v] = (uint8_t)dcnt;
-            unsigned long long fp = atomicAdd(&ctr->frontier, 1ULL);
-            fr_next[fp] = v;
-            atomicAdd(&ctr->merges, (unsigned long long)(end - beg));
-            eat = (int64_t)atomicAdd(&ctr->stg_entries, (unsigned long long)dcnt);
-            unsigned long long gat = atomicAdd(&ctr->stg_groups, 1ULL);
-            StgGroup gr;
-            gr.at = eat;
-            // HIP weight: 1 while the ball has fewer than k vertices, else
-            // 1 / Pr[rank < k-th] = 2^64 / S_h(v)[k-1] (single IEEE division)
-            gr.wt = cnt_new < k ? 1.0 : __ddiv_rn(18446744073709551616.0, __ull2double_rn(kth));
-            gr.v = v;
-            gr.gidx = vg[v];
-            gr.eidx = ve[v];
-            gr.info = pack_info(hop, dcnt, counted);
-            vg[v] = gr.gidx + 1;
-            ve[v] = gr.eidx + dcnt;
-            stg_grp[gat] = gr;
-        }
-        eat = __shfl_sync(kFull, eat, 0);
-        if (lane < dcnt) stg_ent[eat + lane] = (int32_t)rank_vertex(seed, dv);
-    }
-    if (lane == 0 && merging) {
-        atomicAdd(&ctr->cand_reads, cand_reads);
-        atomicAdd(&ctr->merging, merging);
     }
 }
 
-// Sparse hops: the active set is N(frontier).  Warp per frontier vertex;
+// Write the results of vertex v after its merge: new sketch, the entries it
+// gained (for the next hop) and its staged ADS group in work slot `slot`.
+template <int G>
+__device__ __forceinline__ void finish_vertex(const Grp<G>& g, int k, uint64_t seed, int hop, int32_t v,
+                                              int64_t deg, uint64_t old, const Sketch<G>& s, int64_t slot,
+                                              uint64_t* __restrict__ S, uint8_t* __restrict__ Scnt,
+                                              uint64_t* __restrict__ Dc, uint8_t* __restrict__ Dcc,
+                                              int32_t* __restrict__ vg, int32_t* __restrict__ ve,
+                                              int32_t* __restrict__ stg_ent, StgGroup* __restrict__ stg_grp,
+                                              HopCounters& hc) {
+    const bool valid = g.l < k && s.sk != kEmpty;
+    const bool was_there = grp_member(g, old, s.sk);
+    const unsigned newm = g.ballot(valid && !was_there);
+    const int dcnt = __popc(newm);
+    if (dcnt == 0) {
+        if (g.l == 0) stg_grp[slot].info = 0;  // empty slot
+        return;
+    }
+    const int cnt_new = __popc(g.ballot(valid));
+    if (g.l < k) S[(int64_t)v * k + g.l] = s.sk;
+    const uint64_t dv = grp_compact(g, s.sk, newm, kEmpty);
+    if (g.l < dcnt) {
+        Dc[(int64_t)v * k + g.l] = dv;
+        stg_ent[slot * k + g.l] = (int32_t)rank_vertex(seed, dv);
+    }
+    const uint64_t kth = g.shfl(s.sk, k - 1);
+    if (g.l == 0) {
+        const int counted = cnt_new < k ? dcnt : __popc(newm & ((1u << (k - 1)) - 1u));
+        Scnt[v] = (uint8_t)cnt_new;
+        Dcc[v] = (uint8_t)dcnt;
+        StgGroup gr;
+        // HIP weight: 1 while the ball has fewer than k vertices, else
+        // 1 / Pr[rank < k-th] = 2^64 / S_h(v)[k-1] (one IEEE division)
+        gr.wt = cnt_new < k ? 1.0 : __ddiv_rn(18446744073709551616.0, __ull2double_rn(kth));
+        gr.v = v;
+        gr.gidx = vg[v];
+        gr.eidx = ve[v];
+        gr.info = pack_info(hop, dcnt, counted);
+        vg[v] = gr.gidx + 1;
+        ve[v] = gr.eidx + dcnt;
+        stg_grp[slot] = gr;
+        hc.front += 1;
+        hc.merges += (unsigned long long)deg;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void flush_counters(const Grp<G>& g, HopCounters hc, Counters* ctr) {
+    // candidate reads are counted per lane; the other counters by lane 0
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) hc.cand += g.shfl_xor(hc.cand, o);
+    if (g.l == 0) {
+        if (hc.front) atomicAdd(&ctr->frontier, hc.front);
+        if (hc.merges) atomicAdd(&ctr->merges, hc.merges);
+        if (hc.cand) atomicAdd(&ctr->cand_reads, hc.cand);
+        if (hc.merging) atomicAdd(&ctr->merging, hc.merging);
+    }
+}
+
+// ------------------------------------------------------------------ hop kernels
+
+// Non-hub vertices: S_h(v) = bottom-k(S_{h-1}(v) U union_{u in N(v)} D_{h-1}(u)).
+template <int G>
+__global__ void __launch_bounds__(256) k_hop_vertices(
+    const int32_t* __restrict__ list, int64_t n_list, const int64_t* __restrict__ rowp,
+    const int32_t* __restrict__ cols, int k, uint64_t seed, int hop, uint64_t* __restrict__ S,
+    uint8_t* __restrict__ Scnt, const uint64_t* __restrict__ Dp, const uint8_t* __restrict__ Dcp,
+    uint64_t* __restrict__ Dc, uint8_t* __restrict__ Dcc, int32_t* __restrict__ vg, int32_t* __restrict__ ve,
+    int32_t* __restrict__ stg_ent, StgGroup* __restrict__ stg_grp, Counters* ctr) {
+    const Grp<G> g;
+    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+    HopCounters hc;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; i < n_list; i += groups) {
+        const int32_t v = list[i];
+        const int64_t beg = rowp[v], end = rowp[v + 1];
+        const uint64_t old = g.l < k ? S[(int64_t)v * k + g.l] : kEmpty;
+        Sketch<G> s;
+        s.sk = old;
+        s.cnt = Scnt[v];
+        s.tau_base = kEmpty;
+        s.retau(g, k);
+        const unsigned long long cand0 = hc.cand;
+        gather_range(g, k, hop, seed, cols, beg, end, Dcp, Dp, s, hc.cand);
+        const bool merged = hop == 1 || g.ballot(hc.cand != cand0) != 0;
+        if (g.l == 0 && merged) hc.merging += 1;
+        finish_vertex(g, k, seed, hop, v, end - beg, old, s, i, S, Scnt, Dc, Dcc, vg, ve, stg_ent, stg_grp, hc);
+    }
+    flush_counters(g, hc, ctr);
+}
+
+// Hub segments: partial bottom-k of the candidates of one segment, filtered by
+// the hub's old k-th rank, written to part[seg * k ..].
+template <int G>
+__global__ void __launch_bounds__(256) k_hop_hub_segments(
+    const int32_t* __restrict__ hubs, const int64_t* __restrict__ hub_seg, const int32_t* __restrict__ seg_hub,
+    int64_t n_seg, const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols, int k, uint64_t seed,
+    int hop, const uint64_t* __restrict__ S, const uint8_t* __restrict__ Scnt, const uint64_t* __restrict__ Dp,
+    const uint8_t* __restrict__ Dcp, uint64_t* __restrict__ part, Counters* ctr) {
+    const Grp<G> g;
+    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+    HopCounters hc;
+    for (int64_t sidx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; sidx < n_seg; sidx += groups) {
+        const int32_t h = seg_hub[sidx];
+        const int32_t v = hubs[h];
+        const int64_t e0 = rowp[v] + (sidx - hub_seg[h]) * kSeg;
+        const int64_t e1 = min(e0 + (int64_t)kSeg, rowp[v + 1]);
+        const uint64_t kth_old = S[(int64_t)v * k + k - 1];
+        Sketch<G> s;
+        s.sk = kEmpty;
+        s.cnt = 0;
+        s.tau_base = Scnt[v] == k ? kth_old : kEmpty;
+        s.tau = s.tau_base;
+        gather_range(g, k, hop, seed, cols, e0, e1, Dcp, Dp, s, hc.cand);
+        if (g.l < k) part[sidx * k + g.l] = s.sk;
+    }
+    flush_counters(g, hc, ctr);
+}
+
+// Hubs: merge the partial lists of all segments into the hub's sketch.
+template <int G>
+__global__ void __launch_bounds__(256) k_hop_hubs(
+    const int32_t* __restrict__ hubs, int64_t n_hubs, const int64_t* __restrict__ hub_seg,
+    const uint64_t* __restrict__ part, const int64_t* __restrict__ rowp, int k, uint64_t seed, int hop,
+    int64_t slot0, uint64_t* __restrict__ S, uint8_t* __restrict__ Scnt, uint64_t* __restrict__ Dc,
+    uint8_t* __restrict__ Dcc, int32_t* __restrict__ vg, int32_t* __restrict__ ve, int32_t* __restrict__ stg_ent,
+    StgGroup* __restrict__ stg_grp, Counters* ctr) {
+    const Grp<G> g;
+    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+    HopCounters hc;
+    for (int64_t h = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; h < n_hubs; h += groups) {
+        const int32_t v = hubs[h];
+        const uint64_t old = g.l < k ? S[(int64_t)v * k + g.l] : kEmpty;
+        Sketch<G> s;
+        s.sk = old;
+        s.cnt = Scnt[v];
+        s.tau_base = kEmpty;
+        s.retau(g, k);
+        bool any = false;
+        for (int64_t sidx = hub_seg[h]; sidx < hub_seg[h + 1]; ++sidx) {
+            const uint64_t x = g.l < k ? part[sidx * k + g.l] : kEmpty;
+            any |= g.ballot(x != kEmpty) != 0;
+            absorb(g, k, x, s);
+        }
+        if (g.l == 0 && any) hc.merging += 1;
+        finish_vertex(g, k, seed, hop, v, rowp[v + 1] - rowp[v], old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve,
+                      stg_ent, stg_grp, hc);
+    }
+    flush_counters(g, hc, ctr);
+}
+
+// Sparse hops: the non-hub part of N(frontier).  Warp per frontier vertex;
 // each neighbour is appended once (stamp = hop).
 __global__ void k_expand(const int32_t* __restrict__ fr, int64_t n_fr, const int64_t* __restrict__ rowp,
                          const int32_t* __restrict__ cols, uint32_t* __restrict__ stamp, uint32_t hop,
@@ -210,43 +372,173 @@ __global__ void k_expand(const int32_t* __restrict__ fr, int64_t n_fr, const int
             int32_t v = 0;
             if (e < end) {
                 v = cols[e];
-                fresh = atomicExch(&stamp[v], hop) != hop;
+                if (rowp[v + 1] - rowp[v] <= kHubDeg) fresh = atomicExch(&stamp[v], hop) != hop;
             }
-            unsigned m = __ballot_sync(kFull, fresh);
-            if (!m) continue;
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(&ctr->active, (unsigned long long)__popc(m));
-            base = __shfl_sync(kFull, base, 0);
-            if (fresh) act[base + __popc(m & ((1u << lane) - 1u))] = v;
+            long long at = warp_append(fresh, &ctr->active);
+            if (at >= 0) act[at] = v;
         }
+    }
+}
+
+// Vertices of a work list that gained entries this hop (the next frontier).
+__global__ void k_collect_frontier(const int32_t* __restrict__ list, int64_t n, const uint8_t* __restrict__ Dcc,
+                                   int32_t* __restrict__ fr, unsigned long long* __restrict__ n_fr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        int64_t i = base + lane_id();
+        int32_t v = i < n ? list[i] : 0;
+        bool in = i < n && Dcc[v] > 0;
+        long long at = warp_append(in, n_fr);
+        if (at >= 0) fr[at] = v;
     }
 }
 
 // ------------------------------------------------------------------ ADS compaction
 
-__global__ void k_ads_scatter(const StgGroup* __restrict__ stg_grp, int64_t n_groups,
+__global__ void k_ads_scatter(const StgGroup* __restrict__ stg_grp, int64_t n_slots, int64_t slot_base, int k,
                               const int32_t* __restrict__ stg_ent, const int64_t* __restrict__ gofs,
                               const int64_t* __restrict__ eofs, uint32_t* __restrict__ ginfo,
                               double* __restrict__ gwt, int32_t* __restrict__ eid) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_groups; i += stride) {
-        StgGroup gr = stg_grp[i];
-        int64_t dg = gofs[gr.v] + gr.gidx;
-        int64_t de = eofs[gr.v] + gr.eidx;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += stride) {
+        const StgGroup gr = stg_grp[slot_base + i];
+        if (gr.info == 0) continue;
+        const int64_t dg = gofs[gr.v] + gr.gidx;
+        const int64_t de = eofs[gr.v] + gr.eidx;
         ginfo[dg] = gr.info;
         gwt[dg] = gr.wt;
-        int cnt = (int)((gr.info >> 16) & 0xff);
-        for (int j = 0; j < cnt; ++j) eid[de + j] = stg_ent[gr.at + j];
+        const int cnt = (int)((gr.info >> 16) & 0xff);
+        const int32_t* src = stg_ent + (slot_base + i) * k;
+        for (int j = 0; j < cnt; ++j) eid[de + j] = src[j];
     }
 }
 
-// ------------------------------------------------------------------ driver
+// ------------------------------------------------------------------ graph work lists
+
+__global__ void k_flag_degree(const int64_t* __restrict__ rowp, int64_t n, int32_t* __restrict__ low,
+                              int32_t* __restrict__ hub, int32_t* __restrict__ nseg) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t d = rowp[v + 1] - rowp[v];
+        low[v] = (d > 0 && d <= kHubDeg) ? 1 : 0;
+        hub[v] = d > kHubDeg ? 1 : 0;
+        nseg[v] = d > kHubDeg ? (int32_t)((d + kSeg - 1) / kSeg) : 0;
+    }
+}
+
+__global__ void k_scatter_lists(const int32_t* __restrict__ low, const int32_t* __restrict__ hub,
+                                const int64_t* __restrict__ low_pos, const int64_t* __restrict__ hub_pos,
+                                const int64_t* __restrict__ seg_pos, int64_t n, int32_t* __restrict__ low_list,
+                                int32_t* __restrict__ hub_list, int64_t* __restrict__ hub_seg) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        if (low[v]) low_list[low_pos[v]] = (int32_t)v;
+        if (hub[v]) {
+            hub_list[hub_pos[v]] = (int32_t)v;
+            hub_seg[hub_pos[v]] = seg_pos[v];
+        }
+    }
+}
+
+__global__ void k_seg_owner(const int64_t* __restrict__ hub_seg, int64_t n_hubs, int32_t* __restrict__ seg_hub) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < n_hubs; h += stride)
+        for (int64_t s = hub_seg[h]; s < hub_seg[h + 1]; ++s) seg_hub[s] = (int32_t)h;
+}
 
 static int grid_for(int64_t items, int per_block) {
     int64_t b = (items + per_block - 1) / per_block;
     if (b < 1) b = 1;
     if (b > 152 * 32) b = 152 * 32;
     return (int)b;
+}
+
+// Last element of an exclusive scan plus the last input = the total.
+static int scan_total(const int64_t* pos, const int32_t* flag, int64_t n, cudaStream_t st, int64_t* total) {
+    int64_t p = 0;
+    int32_t f = 0;
+    FL_CUDA(cudaMemcpyAsync(&p, pos + n - 1, 8, cudaMemcpyDeviceToHost, st));
+    FL_CUDA(cudaMemcpyAsync(&f, flag + n - 1, 4, cudaMemcpyDeviceToHost, st));
+    FL_CUDA(cudaStreamSynchronize(st));
+    *total = p + f;
+    return FL_OK;
+}
+
+// Static work lists of a graph: non-hub non-isolated vertices, hubs and the
+// segment table of the hubs.
+int build_work_lists(fl_graph* g) {
+    const int64_t n = g->n;
+    cudaStream_t st = g->stream;
+    DBuf low, hub, nseg, low_pos, hub_pos, seg_pos;
+    int rc = FL_OK;
+    do {
+        if ((rc = dalloc(low, (size_t)n * 4)) || (rc = dalloc(hub, (size_t)n * 4)) ||
+            (rc = dalloc(nseg, (size_t)n * 4)) || (rc = dalloc(low_pos, (size_t)n * 8)) ||
+            (rc = dalloc(hub_pos, (size_t)n * 8)) || (rc = dalloc(seg_pos, (size_t)n * 8)))
+            break;
+        FL_LAUNCH(kProfOther, k_flag_degree<<<grid_for(n, 256), 256, 0, st>>>(
+                                  g->rowp.as<int64_t>(), n, low.as<int32_t>(), hub.as<int32_t>(), nseg.as<int32_t>()));
+        if ((rc = scan_exclusive_i32_to_i64(low.as<int32_t>(), low_pos.as<int64_t>(), n, st, g->scratch, kProfOther)) ||
+            (rc = scan_exclusive_i32_to_i64(hub.as<int32_t>(), hub_pos.as<int64_t>(), n, st, g->scratch, kProfOther)) ||
+            (rc = scan_exclusive_i32_to_i64(nseg.as<int32_t>(), seg_pos.as<int64_t>(), n, st, g->scratch, kProfOther)))
+            break;
+        if ((rc = scan_total(low_pos.as<int64_t>(), low.as<int32_t>(), n, st, &g->n_low)) ||
+            (rc = scan_total(hub_pos.as<int64_t>(), hub.as<int32_t>(), n, st, &g->n_hubs)) ||
+            (rc = scan_total(seg_pos.as<int64_t>(), nseg.as<int32_t>(), n, st, &g->n_seg)))
+            break;
+        if ((rc = dalloc(g->low_list, (size_t)std::max<int64_t>(g->n_low, 1) * 4)) ||
+            (rc = dalloc(g->hub_list, (size_t)std::max<int64_t>(g->n_hubs, 1) * 4)) ||
+            (rc = dalloc(g->hub_seg, (size_t)(g->n_hubs + 1) * 8)) ||
+            (rc = dalloc(g->seg_hub, (size_t)std::max<int64_t>(g->n_seg, 1) * 4)))
+            break;
+        FL_LAUNCH(kProfOther, k_scatter_lists<<<grid_for(n, 256), 256, 0, st>>>(
+                                  low.as<int32_t>(), hub.as<int32_t>(), low_pos.as<int64_t>(), hub_pos.as<int64_t>(),
+                                  seg_pos.as<int64_t>(), n, g->low_list.as<int32_t>(), g->hub_list.as<int32_t>(),
+                                  g->hub_seg.as<int64_t>()));
+        cudaError_t e = cudaMemcpyAsync(g->hub_seg.as<int64_t>() + g->n_hubs, &g->n_seg, 8, cudaMemcpyHostToDevice, st);
+        if (e) { rc = status_of(e, "work lists", __FILE__, __LINE__); break; }
+        if (g->n_hubs > 0)
+            FL_LAUNCH(kProfOther, k_seg_owner<<<grid_for(g->n_hubs, 256), 256, 0, st>>>(
+                                      g->hub_seg.as<int64_t>(), g->n_hubs, g->seg_hub.as<int32_t>()));
+        e = cudaStreamSynchronize(st);
+        if (e) { rc = status_of(e, "work lists", __FILE__, __LINE__); break; }
+    } while (0);
+    dfree(low); dfree(hub); dfree(nseg); dfree(low_pos); dfree(hub_pos); dfree(seg_pos);
+    return rc;
+}
+
+// ------------------------------------------------------------------ driver
+
+template <int G>
+static int launch_hop(fl_graph* g, int hop, const int32_t* list, int64_t n_list, int pin, int pout,
+                      int64_t slot_base) {
+    cudaStream_t st = g->stream;
+    const int k = g->k;
+    const int per_block = 256 / G;
+    StgGroup* grp = g->stg_grp.as<StgGroup>() + slot_base;
+    int32_t* ent = g->stg_ent.as<int32_t>() + slot_base * k;
+    if (n_list > 0)
+        FL_LAUNCH(kProfSketchMerge, k_hop_vertices<G><<<grid_for(n_list, per_block), 256, 0, st>>>(
+                                        list, n_list, g->rowp.as<int64_t>(), g->cols.as<int32_t>(), k, g->seed, hop,
+                                        g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[pin].as<uint64_t>(),
+                                        g->Dcnt[pin].as<uint8_t>(), g->D[pout].as<uint64_t>(),
+                                        g->Dcnt[pout].as<uint8_t>(), g->vg.as<int32_t>(), g->ve.as<int32_t>(), ent,
+                                        grp, g->ctr.as<Counters>()));
+    if (g->n_hubs > 0) {
+        FL_LAUNCH(kProfSketchMerge, k_hop_hub_segments<G><<<grid_for(g->n_seg, per_block), 256, 0, st>>>(
+                                        g->hub_list.as<int32_t>(), g->hub_seg.as<int64_t>(), g->seg_hub.as<int32_t>(),
+                                        g->n_seg, g->rowp.as<int64_t>(), g->cols.as<int32_t>(), k, g->seed, hop,
+                                        g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[pin].as<uint64_t>(),
+                                        g->Dcnt[pin].as<uint8_t>(), g->part.as<uint64_t>(), g->ctr.as<Counters>()));
+        FL_LAUNCH(kProfSketchMerge, k_hop_hubs<G><<<grid_for(g->n_hubs, per_block), 256, 0, st>>>(
+                                        g->hub_list.as<int32_t>(), g->n_hubs, g->hub_seg.as<int64_t>(),
+                                        g->part.as<uint64_t>(), g->rowp.as<int64_t>(), k, g->seed, hop, n_list,
+                                        g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[pout].as<uint64_t>(),
+                                        g->Dcnt[pout].as<uint8_t>(), g->vg.as<int32_t>(), g->ve.as<int32_t>(), ent,
+                                        grp, g->ctr.as<Counters>()));
+    }
+    FL_CUDA(cudaGetLastError());
+    return FL_OK;
 }
 
 int build_sketches(fl_graph* g, int k, uint64_t seed) {
@@ -256,6 +548,10 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     ++g->generation;
     g->k = k;
     g->seed = seed;
+    if (!g->lists_ready) {
+        FL_TRY(build_work_lists(g));
+        g->lists_ready = 1;
+    }
     const size_t nk = (size_t)n * k;
     FL_TRY(dalloc(g->S, nk * 8));
     FL_TRY(dalloc(g->Scnt, (size_t)n));
@@ -267,124 +563,132 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     FL_TRY(dalloc(g->stamp, (size_t)n * 4));
     FL_TRY(dalloc(g->vg, (size_t)n * 4));
     FL_TRY(dalloc(g->ve, (size_t)n * 4));
-    // staging starts at ~4 entries per vertex and grows when a hop might not fit
-    size_t ent_cap = std::max<size_t>((size_t)n * 4, 1024);
-    size_t grp_cap = std::max<size_t>((size_t)n * 2, 1024);
-    if (g->stg_ent_cap < ent_cap) { FL_TRY(dalloc(g->stg_ent, ent_cap * 4)); g->stg_ent_cap = ent_cap; }
-    if (g->stg_grp_cap < grp_cap) { FL_TRY(dalloc(g->stg_grp, grp_cap * sizeof(StgGroup))); g->stg_grp_cap = grp_cap; }
+    FL_TRY(dalloc(g->part, (size_t)std::max<int64_t>(g->n_seg, 1) * k * 8));
+    // staging: slots 0..n-1 for hop 0, then one slot per work item of each hop
+    const int64_t per_dense = g->n_low + g->n_hubs;
+    size_t slot_cap = (size_t)n + (size_t)per_dense * 8 + 1024;
+    if (g->stg_grp_cap < slot_cap || g->stg_k != k) {
+        slot_cap = std::max(slot_cap, g->stg_grp_cap);
+        FL_TRY(dalloc(g->stg_grp, slot_cap * sizeof(StgGroup)));
+        FL_TRY(dalloc(g->stg_ent, slot_cap * k * 4));
+        g->stg_grp_cap = slot_cap;
+        g->stg_k = k;
+    }
     DBuf act;  // active list of sparse hops
     FL_TRY(dalloc(act, (size_t)n * 4));
 
     FL_CUDA(cudaMemsetAsync(g->S.p, 0xff, nk * 8, st));
-    FL_CUDA(cudaMemsetAsync(g->D[0].p, 0xff, nk * 8, st));
-    FL_CUDA(cudaMemsetAsync(g->D[1].p, 0xff, nk * 8, st));
     FL_CUDA(cudaMemsetAsync(g->stamp.p, 0, (size_t)n * 4, st));
     FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st));
-    FL_LAUNCH(kProfSketchOther, k_rank_init<<<grid_for(n, 256), 256, 0, st>>>(n, k, seed, g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(),
-                                                   g->D[0].as<uint64_t>(), g->Dcnt[0].as<uint8_t>(),
-                                                   g->stg_ent.as<int32_t>(), g->stg_grp.as<StgGroup>(),
-                                                   g->vg.as<int32_t>(), g->ve.as<int32_t>(), g->ctr.as<Counters>()));
+    FL_LAUNCH(kProfSketchOther, k_rank_init<<<grid_for(n, 256), 256, 0, st>>>(
+                                    n, k, seed, g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[0].as<uint64_t>(),
+                                    g->Dcnt[0].as<uint8_t>(), g->stg_ent.as<int32_t>(), g->stg_grp.as<StgGroup>(),
+                                    g->vg.as<int32_t>(), g->ve.as<int32_t>(), g->ctr.as<Counters>()));
     FL_CUDA(cudaGetLastError());
     FL_TRY(read_counters(g));
     if (g->h_ctr->error) {
         dfree(act);
         FL_FAIL(FL_EINVAL, "a vertex rank equals the reserved empty-slot value; choose another seed");
     }
-    Counters init{};
-    init.stg_entries = (unsigned long long)n;
-    init.stg_groups = (unsigned long long)n;
-    int64_t n_front = n;                // hop 0: every vertex gained its own rank
+    std::vector<std::pair<int64_t, int64_t>> regions;  // (slot base, slots) of each hop
+    regions.push_back({0, n});
+    int64_t used_slots = n;
+    int64_t n_front = n;  // hop 0: every vertex gained its own rank
+    bool fr_list_ready = false;
     int64_t total_merges = 0, next_merges = g->nnz;
-    int64_t used_ent = n, used_grp = n;
     int hop = 1;
     int rc = FL_OK;
     for (;; ++hop) {
         if (hop > kMaxHops) { rc = FL_ETIMEOUT; set_error(rc, "more than 65535 hops"); break; }
         total_merges += next_merges;
         const int64_t hop_merges = next_merges;
-        const int64_t ent_before = used_ent;
         const int pin = (hop - 1) & 1, pout = hop & 1;
-        const int32_t* act_list;
-        int64_t n_act;
+        const int32_t* list;
+        int64_t n_list;
         // dense hops run every non-isolated vertex; sparse hops expand the frontier
-        bool dense = n_front * 16 >= g->n_nonisolated;
-        init.frontier = 0;
-        init.active = 0;
-        init.merges = 0;
-        init.error = 0;
+        const bool dense = !fr_list_ready;
+        Counters init{};
         FL_CUDA(cudaMemcpyAsync(g->ctr.p, &init, sizeof(Counters), cudaMemcpyHostToDevice, st));
         if (dense) {
-            act_list = g->deg_list.as<int32_t>();
-            n_act = g->n_nonisolated;
+            list = g->low_list.as<int32_t>();
+            n_list = g->n_low;
         } else {
-            FL_LAUNCH(kProfSketchExpand, k_expand<<<grid_for(n_front, 8), 256, 0, st>>>(g->frontier[pin].as<int32_t>(), n_front,
-                                                          g->rowp.as<int64_t>(), g->cols.as<int32_t>(),
-                                                          g->stamp.as<uint32_t>(), (uint32_t)hop,
-                                                          act.as<int32_t>(), g->ctr.as<Counters>()));
+            FL_LAUNCH(kProfSketchExpand, k_expand<<<grid_for(n_front, 8), 256, 0, st>>>(
+                                             g->frontier[pin].as<int32_t>(), n_front, g->rowp.as<int64_t>(),
+                                             g->cols.as<int32_t>(), g->stamp.as<uint32_t>(), (uint32_t)hop,
+                                             act.as<int32_t>(), g->ctr.as<Counters>()));
             FL_CUDA(cudaGetLastError());
             FL_TRY(read_counters(g));
-            act_list = act.as<int32_t>();
-            n_act = (int64_t)g->h_ctr->active;
+            list = act.as<int32_t>();
+            n_list = (int64_t)g->h_ctr->active;
         }
-        // staging room for the worst case of this hop (k entries per active vertex)
-        if ((size_t)(used_ent + n_act * k) > g->stg_ent_cap) {
-            size_t cap = std::max<size_t>((size_t)(used_ent + n_act * k), g->stg_ent_cap * 3 / 2);
-            FL_TRY(dgrow(g->stg_ent, cap * 4, (size_t)used_ent * 4, st));
-            g->stg_ent_cap = cap;
-        }
-        if ((size_t)(used_grp + n_act) > g->stg_grp_cap) {
-            size_t cap = std::max<size_t>((size_t)(used_grp + n_act), g->stg_grp_cap * 3 / 2);
-            FL_TRY(dgrow(g->stg_grp, cap * sizeof(StgGroup), (size_t)used_grp * sizeof(StgGroup), st));
+        const int64_t slots = n_list + g->n_hubs;
+        if ((size_t)(used_slots + slots) > g->stg_grp_cap) {
+            size_t cap = std::max<size_t>((size_t)(used_slots + slots), g->stg_grp_cap * 3 / 2);
+            FL_TRY(dgrow(g->stg_grp, cap * sizeof(StgGroup), (size_t)used_slots * sizeof(StgGroup), st));
+            FL_TRY(dgrow(g->stg_ent, cap * k * 4, (size_t)used_slots * k * 4, st));
             g->stg_grp_cap = cap;
         }
         FL_CUDA(cudaMemsetAsync(g->Dcnt[pout].p, 0, (size_t)n, st));
-        if (n_act > 0) {
-            FL_LAUNCH(kProfSketchMerge, k_merge_hop<<<grid_for(n_act, 8), 256, 0, st>>>(
-                act_list, nullptr, n_act, g->rowp.as<int64_t>(), g->cols.as<int32_t>(), k, seed, hop,
-                g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[pin].as<uint64_t>(), g->Dcnt[pin].as<uint8_t>(),
-                g->D[pout].as<uint64_t>(), g->Dcnt[pout].as<uint8_t>(), g->frontier[pout].as<int32_t>(),
-                g->vg.as<int32_t>(), g->ve.as<int32_t>(), g->stg_ent.as<int32_t>(), g->stg_grp.as<StgGroup>(),
-                g->ctr.as<Counters>()));
-            FL_CUDA(cudaGetLastError());
-        }
+        if (k <= 16)
+            FL_TRY(launch_hop<16>(g, hop, list, n_list, pin, pout, used_slots));
+        else
+            FL_TRY(launch_hop<32>(g, hop, list, n_list, pin, pout, used_slots));
+        regions.push_back({used_slots, slots});
+        used_slots += slots;
         FL_TRY(read_counters(g));
         n_front = (int64_t)g->h_ctr->frontier;
         next_merges = (int64_t)g->h_ctr->merges;
-        used_ent = (int64_t)g->h_ctr->stg_entries;
-        used_grp = (int64_t)g->h_ctr->stg_groups;
-        init.stg_entries = (unsigned long long)used_ent;
-        init.stg_groups = (unsigned long long)used_grp;
-        // algorithmic bytes of this hop's merge: active row offsets (8 B), frontier
-        // columns (4 B per edge-merge), neighbour deltas (8 B per rank), own sketch
-        // read + write (16k B per merging vertex), new ADS entries (id + weight, 12 B)
+        // algorithmic bytes of this hop's merge: row offsets of each merging
+        // vertex (8 B), frontier columns (4 B per edge-merge), neighbour delta
+        // ranks read (8 B each), own sketch read + write (16k B per merging
+        // vertex); the ADS entries (12 B each) are added after the last hop
         {
             const double A = (double)g->h_ctr->merging, SD = (double)g->h_ctr->cand_reads;
-            g->prof.bytes[kProfSketchMerge] += 8.0 * A + 4.0 * (double)hop_merges + 8.0 * SD + 16.0 * k * A +
-                                               12.0 * (double)(used_ent - ent_before);
+            g->prof.bytes[kProfSketchMerge] += 8.0 * A + 4.0 * (double)hop_merges + 8.0 * SD + 16.0 * k * A;
         }
         if (n_front == 0) break;
+        // a small frontier makes the next hop sparse: collect its list
+        fr_list_ready = false;
+        if (n_front * 16 < g->n_low + g->n_hubs) {
+            FL_CUDA(cudaMemsetAsync(&g->ctr.as<Counters>()->aux0, 0, 8, st));
+            if (n_list > 0)
+                FL_LAUNCH(kProfSketchExpand, k_collect_frontier<<<grid_for(n_list, 256), 256, 0, st>>>(
+                                                 list, n_list, g->Dcnt[pout].as<uint8_t>(),
+                                                 g->frontier[pout].as<int32_t>(), &g->ctr.as<Counters>()->aux0));
+            if (g->n_hubs > 0)
+                FL_LAUNCH(kProfSketchExpand, k_collect_frontier<<<grid_for(g->n_hubs, 256), 256, 0, st>>>(
+                                                 g->hub_list.as<int32_t>(), g->n_hubs, g->Dcnt[pout].as<uint8_t>(),
+                                                 g->frontier[pout].as<int32_t>(), &g->ctr.as<Counters>()->aux0));
+            FL_CUDA(cudaGetLastError());
+            FL_TRY(read_counters(g));
+            fr_list_ready = true;
+        }
     }
     dfree(act);
     if (rc != FL_OK) return rc;
     g->hops = hop - 1;
     g->edge_merges = total_merges;
-    g->n_entries = used_ent;
-    g->n_groups = used_grp;
 
     // vertex-major ADS
     FL_TRY(dalloc(g->gofs, (size_t)(n + 1) * 8));
     FL_TRY(dalloc(g->eofs, (size_t)(n + 1) * 8));
-    FL_TRY(dalloc(g->ginfo, (size_t)used_grp * 4));
-    FL_TRY(dalloc(g->gwt, (size_t)used_grp * 8));
-    FL_TRY(dalloc(g->eid, (size_t)used_ent * 4));
     FL_TRY(scan_exclusive_i32_to_i64(g->vg.as<int32_t>(), g->gofs.as<int64_t>(), n, st, g->scratch));
     FL_TRY(scan_exclusive_i32_to_i64(g->ve.as<int32_t>(), g->eofs.as<int64_t>(), n, st, g->scratch));
+    FL_TRY(scan_total(g->gofs.as<int64_t>(), g->vg.as<int32_t>(), n, st, &g->n_groups));
+    FL_TRY(scan_total(g->eofs.as<int64_t>(), g->ve.as<int32_t>(), n, st, &g->n_entries));
+    g->prof.bytes[kProfSketchMerge] += 12.0 * (double)(g->n_entries - n);
+    FL_TRY(dalloc(g->ginfo, (size_t)std::max<int64_t>(g->n_groups, 1) * 4));
+    FL_TRY(dalloc(g->gwt, (size_t)std::max<int64_t>(g->n_groups, 1) * 8));
+    FL_TRY(dalloc(g->eid, (size_t)std::max<int64_t>(g->n_entries, 1) * 4));
     FL_CUDA(cudaMemcpyAsync(g->gofs.as<int64_t>() + n, &g->n_groups, 8, cudaMemcpyHostToDevice, st));
     FL_CUDA(cudaMemcpyAsync(g->eofs.as<int64_t>() + n, &g->n_entries, 8, cudaMemcpyHostToDevice, st));
-    FL_LAUNCH(kProfSketchOther, k_ads_scatter<<<grid_for(used_grp, 256), 256, 0, st>>>(g->stg_grp.as<StgGroup>(), used_grp,
-                                                          g->stg_ent.as<int32_t>(), g->gofs.as<int64_t>(),
-                                                          g->eofs.as<int64_t>(), g->ginfo.as<uint32_t>(),
-                                                          g->gwt.as<double>(), g->eid.as<int32_t>()));
+    for (const auto& r : regions)
+        if (r.second > 0)
+            FL_LAUNCH(kProfSketchOther, k_ads_scatter<<<grid_for(r.second, 256), 256, 0, st>>>(
+                                            g->stg_grp.as<StgGroup>(), r.second, r.first, k, g->stg_ent.as<int32_t>(),
+                                            g->gofs.as<int64_t>(), g->eofs.as<int64_t>(), g->ginfo.as<uint32_t>(),
+                                            g->gwt.as<double>(), g->eid.as<int32_t>()));
     FL_CUDA(cudaGetLastError());
     FL_CUDA(cudaStreamSynchronize(st));
     FL_TRY(compute_ecc_bound(g));
@@ -398,16 +702,12 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
 // and ecc(root), and ecc(v) <= d(v, root) + ecc(root).
 
 __global__ void k_roots(const uint64_t* __restrict__ S, int k, uint64_t seed, int64_t n,
-                        int32_t* __restrict__ root_of, int32_t* __restrict__ roots, Counters* ctr) {
+                        int32_t* __restrict__ roots, Counters* ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
         int64_t v = base + lane_id();
         bool is_root = false;
-        if (v < n) {
-            int32_t r = (int32_t)rank_vertex(seed, S[v * k]);
-            root_of[v] = r;
-            is_root = r == v;
-        }
+        if (v < n) is_root = rank_vertex(seed, S[v * k]) == v;
         long long at = warp_append(is_root, &ctr->aux0);
         if (at >= 0) roots[at] = (int32_t)v;
     }
@@ -417,7 +717,7 @@ __global__ void k_ecc_max(const int32_t* __restrict__ label, const int32_t* __re
                           int32_t* __restrict__ eccr) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-        atomicMax(&eccr[label[v]], dist[v]);
+        if (dist[v] > 0) atomicMax(&eccr[label[v]], dist[v]);
 }
 
 __global__ void k_ecc_ub(const int32_t* __restrict__ label, const int32_t* __restrict__ dist,
@@ -430,14 +730,9 @@ __global__ void k_ecc_ub(const int32_t* __restrict__ label, const int32_t* __res
 int compute_ecc_bound(fl_graph* g) {
     const int64_t n = g->n;
     cudaStream_t st = g->stream;
-    DBuf root_of, roots, label, dist, eccr, X, stampb, fr[2], frval;
-    auto cleanup = [&]() {
-        dfree(root_of); dfree(roots); dfree(label); dfree(dist); dfree(eccr);
-        dfree(X); dfree(stampb); dfree(fr[0]); dfree(fr[1]); dfree(frval);
-    };
+    DBuf roots, label, dist, eccr, X, stampb, fr[2], frval;
     int rc = FL_OK;
     do {
-        if ((rc = dalloc(root_of, (size_t)n * 4))) break;
         if ((rc = dalloc(roots, (size_t)n * 4))) break;
         if ((rc = dalloc(label, (size_t)n * 4))) break;
         if ((rc = dalloc(dist, (size_t)n * 4))) break;
@@ -446,21 +741,25 @@ int compute_ecc_bound(fl_graph* g) {
         cudaError_t e = cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(eccr.p, 0, (size_t)n * 4, st);
         if (e != cudaSuccess) { rc = status_of(e, "ecc init", __FILE__, __LINE__); break; }
-        FL_LAUNCH(kProfSketchOther, k_roots<<<grid_for(n, 256), 256, 0, st>>>(g->S.as<uint64_t>(), g->k, g->seed, n, root_of.as<int32_t>(),
-                                                  roots.as<int32_t>(), g->ctr.as<Counters>()));
+        FL_LAUNCH(kProfSketchOther, k_roots<<<grid_for(n, 256), 256, 0, st>>>(
+                                        g->S.as<uint64_t>(), g->k, g->seed, n, roots.as<int32_t>(),
+                                        g->ctr.as<Counters>()));
         if ((rc = read_counters(g))) break;
         int64_t n_roots = (int64_t)g->h_ctr->aux0;
         if ((rc = msbfs(g, roots.as<int32_t>(), n_roots, label.as<int32_t>(), dist.as<int32_t>(), X, stampb,
                         fr, frval, kProfSketchOther)))
             break;
-        FL_LAUNCH(kProfSketchOther, k_ecc_max<<<grid_for(n, 256), 256, 0, st>>>(label.as<int32_t>(), dist.as<int32_t>(), n,
-                                                    eccr.as<int32_t>()));
-        FL_LAUNCH(kProfSketchOther, k_ecc_ub<<<grid_for(n, 256), 256, 0, st>>>(label.as<int32_t>(), dist.as<int32_t>(), eccr.as<int32_t>(),
-                                                   n, g->ecc_ub.as<int32_t>()));
+        FL_LAUNCH(kProfSketchOther, k_ecc_max<<<grid_for(n, 256), 256, 0, st>>>(label.as<int32_t>(),
+                                                                                dist.as<int32_t>(), n,
+                                                                                eccr.as<int32_t>()));
+        FL_LAUNCH(kProfSketchOther, k_ecc_ub<<<grid_for(n, 256), 256, 0, st>>>(
+                                        label.as<int32_t>(), dist.as<int32_t>(), eccr.as<int32_t>(), n,
+                                        g->ecc_ub.as<int32_t>()));
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { rc = status_of(e, "ecc bound", __FILE__, __LINE__); break; }
     } while (0);
-    cleanup();
+    dfree(roots); dfree(label); dfree(dist); dfree(eccr);
+    dfree(X); dfree(stampb); dfree(fr[0]); dfree(fr[1]); dfree(frval);
     return rc;
 }
 

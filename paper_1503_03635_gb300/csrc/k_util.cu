@@ -364,45 +364,4 @@ int validate_csr(fl_graph* g) {
     return FL_OK;
 }
 
-// Ascending list of vertices with at least one neighbour.
-__global__ void k_flag_nonisolated(const int64_t* __restrict__ rowp, int64_t n, int32_t* __restrict__ flag) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-        flag[v] = rowp[v + 1] > rowp[v] ? 1 : 0;
-}
-
-__global__ void k_scatter_flagged(const int32_t* __restrict__ flag, const int64_t* __restrict__ pos, int64_t n,
-                                  int32_t* __restrict__ out) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-        if (flag[v]) out[pos[v]] = (int32_t)v;
-}
-
-int build_nonisolated_list(fl_graph* g) {
-    const int64_t n = g->n;
-    DBuf flag, pos;
-    int rc = dalloc(flag, (size_t)n * 4);
-    if (rc == FL_OK) rc = dalloc(pos, (size_t)(n + 1) * 8);
-    if (rc == FL_OK) rc = dalloc(g->deg_list, (size_t)n * 4);
-    if (rc == FL_OK) {
-        FL_LAUNCH(kProfOther, k_flag_nonisolated<<<152 * 8, 256, 0, g->stream>>>(g->rowp.as<int64_t>(), n, flag.as<int32_t>()));
-        rc = scan_exclusive_i32_to_i64(flag.as<int32_t>(), pos.as<int64_t>(), n, g->stream, g->scratch, kProfOther);
-    }
-    if (rc == FL_OK) {
-        FL_LAUNCH(kProfOther, k_scatter_flagged<<<152 * 8, 256, 0, g->stream>>>(flag.as<int32_t>(), pos.as<int64_t>(), n,
-                                                          g->deg_list.as<int32_t>()));
-        int64_t last_pos = 0;
-        int32_t last_flag = 0;
-        cudaError_t e = cudaMemcpyAsync(&last_pos, pos.as<int64_t>() + n - 1, 8, cudaMemcpyDeviceToHost, g->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(&last_flag, flag.as<int32_t>() + n - 1, 4, cudaMemcpyDeviceToHost, g->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-        if (e != cudaSuccess) rc = status_of(e, "nonisolated list", __FILE__, __LINE__);
-        g->n_nonisolated = last_pos + last_flag;
-    }
-    dfree(flag);
-    dfree(pos);
-    return rc;
-}
-
 }  // namespace fl
