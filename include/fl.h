@@ -209,6 +209,30 @@ int fl_profile_reset(fl_graph* g);
    bytes of one class (or all, kernel_class = -1); any pointer may be NULL. */
 int fl_profile_query(const fl_graph* g, int kernel_class, int64_t* launches, double* ms, double* alg_bytes);
 
+/*
+ * fl_assign_nearest_noalloc -- nearest open facility of every vertex without
+ * any device allocation.  (The paper has no counterpart: this is a deployment
+ * variant of fl_assign_clients for callers that cannot let a library call
+ * cudaMalloc -- applications that reserve the whole device for their own
+ * memory pool, and latency-critical loops that cannot take an allocation's
+ * implicit synchronisation.)
+ *   n, row_off, cols, nnz   CSR as for fl_graph_create, in DEVICE memory;
+ *                           1 <= n <= 1048576 (the fixed scratch), else
+ *                           FL_EINVAL; the CSR is validated (FL_EINVAL).
+ *   open                    uint8[n] device memory, nonzero = open facility.
+ *   assign_out, dist_out    int32[n] device memory (either may be NULL):
+ *                           smallest-id nearest open facility and its hop
+ *                           distance, -1 where none is reachable.
+ *   stream                  cudaStream_t for all work; returns after it ends.
+ * Scratch (about 28 MB) is one fixed device array of the library, held by
+ * every GPU that loads it until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) and
+ * should come before any stream capture.  All calls share the array and each
+ * clears what must start at zero; calls that overlap on the GPU race.
+ */
+int fl_assign_nearest_noalloc(int64_t n, const int64_t* row_off, const int32_t* cols, int64_t nnz,
+                              const uint8_t* open, int32_t* assign_out, int32_t* dist_out, void* stream);
+
 /* fl_status_str -- static text for a status code. */
 const char* fl_status_str(int status);
 

@@ -27,7 +27,7 @@ EXPORTS = ("fl_graph_create", "fl_graph_destroy", "fl_build_sketches", "fl_sketc
            "fl_export_sketches", "fl_export_ads", "fl_solve_create", "fl_solve_destroy",
            "fl_compute_radii", "fl_open_facilities", "fl_assign_clients", "fl_objective",
            "fl_solve_stats", "fl_status_str", "fl_last_error", "fl_profile_enable", "fl_profile_reset",
-           "fl_profile_query")
+           "fl_profile_query", "fl_assign_nearest_noalloc")
 
 PROF_CLASSES = {"sketch_merge": 0, "sketch_expand": 1, "sketch_other": 2, "radius": 3, "keys": 4,
                 "mis": 5, "bfs": 6, "other": 7}
@@ -75,6 +75,7 @@ def load(build_if_missing: bool = True):
             "fl_profile_enable": ([vp, ci], ci),
             "fl_profile_reset": ([vp], ci),
             "fl_profile_query": ([vp, ci, P64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ci),
+            "fl_assign_nearest_noalloc": ([i64, vp, vp, i64, vp, vp, vp, vp], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -252,6 +253,23 @@ class Solve:
         r, c = ctypes.c_int64(), ctypes.c_int64()
         _check(self._lib.fl_solve_stats(self._h, ctypes.byref(r), ctypes.byref(c)))
         return dict(mis_rounds=r.value, candidates=c.value)
+
+
+def assign_nearest_noalloc(rowp, cols, open_mask, assign_out, dist_out, stream=None):
+    """fl_assign_nearest_noalloc: nearest open facility with no device allocation.
+
+    For callers that cannot let the library allocate device memory; all arrays are
+    CUDA tensors the caller owns (row offsets int64, columns int32, open mask uint8,
+    outputs int32).  Graphs up to 2^20 vertices; calls that overlap on the GPU race.
+    """
+    lib = load()
+    args = [_arg(a) for a in (rowp, cols, open_mask, assign_out, dist_out)]
+    if any(kind != FL_MEM_DEVICE for _, kind, _ in args if kind is not None):
+        raise ValueError("fl_assign_nearest_noalloc takes device memory only")
+    st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
+    _check(lib.fl_assign_nearest_noalloc(len(rowp) - 1, args[0][0], args[1][0], len(cols), args[2][0],
+                                         args[3][0], args[4][0], st))
+    return assign_out, dist_out
 
 
 def solve(rowp, cols, k, seed, cost, client, stream=None) -> dict:
