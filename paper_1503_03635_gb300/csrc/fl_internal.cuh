@@ -412,6 +412,27 @@ int compute_radii(fl_solve* s);
 int open_facilities(fl_solve* s);
 int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, int32_t* dist,
           DBuf& X, DBuf& stampb, DBuf* fr, DBuf& frval, int cls);
+
+// State of a sequence of synchronous min-propagation rounds (k_relax.cu).
+struct Relax {
+    unsigned long long* X[2] = {nullptr, nullptr};  // value buffers; X[cur] is current
+    int cur = 0;
+    int32_t* fr[2] = {nullptr, nullptr};            // frontier lists; fr[fc] is current
+    int fc = 0;
+    unsigned long long* frval = nullptr;            // snapshot of frontier values
+    uint32_t* stamp = nullptr;                      // frontier stamps / changed flags
+    unsigned long long* cnt = nullptr;              // device: [0], [1] list sizes, [2] changed count
+    unsigned long long* h_cnt = nullptr;            // pinned host word
+    int64_t n_front = 0;                            // host copy of the frontier size
+    bool list_valid = true;                         // fr[fc] lists the frontier
+    uint32_t sv_prev = 0;                           // stamp of the current frontier
+    unsigned long long limit = ~0ULL;               // values >= limit are ignored by pulls
+    int dense_div = 8;                              // pull when frontier * dense_div >= vertices
+};
+int relax_round(fl_graph* g, Relax& r, unsigned long long add, uint32_t sv, int cls);
+int relax_prepare_list(fl_graph* g, Relax& r, int cls);
+int relax_collect_epoch(fl_graph* g, const unsigned long long* X, unsigned long long hi, int32_t* out,
+                        unsigned long long* n_out, int cls);
 int assign_clients(fl_solve* s);
 int objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserved);
 

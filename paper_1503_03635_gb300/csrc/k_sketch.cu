@@ -717,7 +717,7 @@ __global__ void k_ecc_max(const int32_t* __restrict__ label, const int32_t* __re
                           int32_t* __restrict__ eccr) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-        if (dist[v] > 0) atomicMax(&eccr[label[v]], dist[v]);
+        if (dist[v] > 0 && eccr[label[v]] < dist[v]) atomicMax(&eccr[label[v]], dist[v]);
 }
 
 __global__ void k_ecc_ub(const int32_t* __restrict__ label, const int32_t* __restrict__ dist,

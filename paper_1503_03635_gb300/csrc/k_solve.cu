@@ -120,41 +120,34 @@ int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, i
           DBuf& stampb, DBuf* fr, DBuf& frval, int cls) {
     const int64_t n = g->n;
     cudaStream_t st = g->stream;
-    FL_TRY(dalloc(X, (size_t)n * 8));
+    FL_TRY(dalloc(X, (size_t)n * 16));
     FL_TRY(dalloc(stampb, (size_t)n * 4));
     FL_TRY(dalloc(fr[0], (size_t)n * 4));
     FL_TRY(dalloc(fr[1], (size_t)n * 4));
     FL_TRY(dalloc(frval, (size_t)n * 8 + 64));
-    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(frval.as<char>() + (size_t)n * 8);
-    FL_CUDA(cudaMemsetAsync(X.p, 0xff, (size_t)n * 8, st));
-    FL_CUDA(cudaMemsetAsync(stampb.p, 0, (size_t)n * 4, st));
-    FL_CUDA(cudaMemsetAsync(cnt, 0, 64, st));
+    Relax r;
+    r.X[0] = X.as<unsigned long long>();
+    r.X[1] = r.X[0] + n;
+    r.fr[0] = fr[0].as<int32_t>();
+    r.fr[1] = fr[1].as<int32_t>();
+    r.frval = frval.as<unsigned long long>();
+    r.stamp = stampb.as<uint32_t>();
+    r.cnt = reinterpret_cast<unsigned long long*>(frval.as<char>() + (size_t)n * 8);
+    r.h_cnt = &g->h_ctr->aux3;
+    r.limit = ~0ULL;
+    r.dense_div = 2;  // a BFS pushes each edge once; pull only for very large levels
+    FL_CUDA(cudaMemsetAsync(r.X[0], 0xff, (size_t)n * 8, st));
+    FL_CUDA(cudaMemsetAsync(r.stamp, 0, (size_t)n * 4, st));
+    FL_CUDA(cudaMemsetAsync(r.cnt, 0, 64, st));
     if (n_src > 0) {
-        FL_LAUNCH(cls, k_inject<<<grid_for(n_src, 256), 256, 0, st>>>(src_list, n_src, nullptr, 0ULL, nullptr,
-                                                      X.as<unsigned long long>(), stampb.as<uint32_t>(), 1u,
-                                                      fr[0].as<int32_t>(), &cnt[0]));
+        FL_LAUNCH(cls, k_inject<<<grid_for(n_src, 256), 256, 0, st>>>(src_list, n_src, nullptr, 0ULL, nullptr, r.X[0],
+                                                                      r.stamp, 1u, r.fr[0], &r.cnt[0]));
         FL_CUDA(cudaGetLastError());
     }
-    int cur = 0;
-    int64_t n_cur = n_src;
-    uint32_t level = 0;
-    while (n_cur > 0) {
-        FL_LAUNCH(cls, k_snapshot<<<grid_for(n_cur, 256), 256, 0, st>>>(fr[cur].as<int32_t>(), &cnt[cur],
-                                                        X.as<unsigned long long>(), frval.as<unsigned long long>(),
-                                                        &cnt[cur ^ 1], nullptr, 0, nullptr, nullptr));
-        FL_LAUNCH(cls, k_push<<<grid_for(n_cur, 8), 256, 0, st>>>(fr[cur].as<int32_t>(), frval.as<unsigned long long>(), &cnt[cur],
-                                                  g->rowp.as<int64_t>(), g->cols.as<int32_t>(), 1ULL << 32,
-                                                  X.as<unsigned long long>(), stampb.as<uint32_t>(), level + 2,
-                                                  fr[cur ^ 1].as<int32_t>(), &cnt[cur ^ 1]));
-        FL_CUDA(cudaGetLastError());
-        unsigned long long nn = 0;
-        FL_CUDA(cudaMemcpyAsync(&nn, &cnt[cur ^ 1], 8, cudaMemcpyDeviceToHost, st));
-        FL_CUDA(cudaStreamSynchronize(st));
-        n_cur = (int64_t)nn;
-        cur ^= 1;
-        ++level;
-    }
-    FL_LAUNCH(cls, k_unpack_bfs<<<grid_for(n, 256), 256, 0, st>>>(X.as<unsigned long long>(), n, label, dist));
+    r.n_front = n_src;
+    r.sv_prev = 1;
+    for (uint32_t level = 0; r.n_front > 0; ++level) FL_TRY(relax_round(g, r, 1ULL << 32, level + 2, cls));
+    FL_LAUNCH(cls, k_unpack_bfs<<<grid_for(n, 256), 256, 0, st>>>(r.X[r.cur], n, label, dist));
     FL_CUDA(cudaGetLastError());
     return FL_OK;
 }
@@ -405,8 +398,8 @@ int open_facilities(fl_solve* s) {
     FL_TRY(dalloc(s->bcap, (size_t)n * 4));
     FL_TRY(dalloc(s->state, (size_t)n));
     FL_TRY(dalloc(s->claimed, (size_t)n));
-    FL_TRY(dalloc(s->X, (size_t)n * 8));
-    FL_TRY(dalloc(s->stamp, (size_t)n * 4 * 2));  // frontier stamps + touched stamps
+    FL_TRY(dalloc(s->X, (size_t)n * 16));          // two value buffers
+    FL_TRY(dalloc(s->stamp, (size_t)n * 4));
     FL_TRY(dalloc(s->mval, (size_t)n * 4));
     FL_TRY(dalloc(s->fr[0], (size_t)n * 4));
     FL_TRY(dalloc(s->fr[1], (size_t)n * 4));
@@ -415,9 +408,9 @@ int open_facilities(fl_solve* s) {
     FL_TRY(dalloc(s->ulist, (size_t)n * 4 * 2));
     FL_TRY(dalloc(s->ubuck, (size_t)n * 4));
     FL_TRY(dalloc(s->open, (size_t)n));
-    uint32_t* tstamp = s->stamp.as<uint32_t>() + n;
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(s->frval.as<char>() + (size_t)n * 8);
-    // cnt[0], cnt[1]: frontier counts; cnt[2]: touched; cnt[3]: undecided; cnt[4]: T max
+    // cnt[0], cnt[1]: frontier counts; cnt[2]: changed count (dense rounds);
+    // cnt[3]: undecided; cnt[4]: T max; cnt[5]: open list; cnt[6]: touched
     DBuf hi, lo, val;
     auto free_keys = [&]() { dfree(hi); dfree(lo); dfree(val); };
     int rc = FL_OK;
@@ -448,8 +441,8 @@ int open_facilities(fl_solve* s) {
     unsigned long long bmax = 0;
     FL_CUDA(cudaMemcpyAsync(&bmax, &cnt[4], 8, cudaMemcpyDeviceToHost, st));
     FL_CUDA(cudaMemsetAsync(s->claimed.p, 0, (size_t)n, st));
-    FL_CUDA(cudaMemsetAsync(s->X.p, 0xff, (size_t)n * 8, st));
-    FL_CUDA(cudaMemsetAsync(s->stamp.p, 0, (size_t)n * 8, st));
+    FL_CUDA(cudaMemsetAsync(s->X.p, 0xff, (size_t)n * 16, st));
+    FL_CUDA(cudaMemsetAsync(s->stamp.p, 0, (size_t)n * 4, st));
     FL_CUDA(cudaStreamSynchronize(st));
     DBuf bcount_d;
     FL_TRY(dalloc(bcount_d, (bmax + 2) * 4 * 2));
@@ -457,10 +450,16 @@ int open_facilities(fl_solve* s) {
     int32_t* cursor = bcount + (bmax + 2);
     std::vector<int32_t> hcount(bmax + 2), hoff(bmax + 2);
 
-    unsigned long long* X = s->X.as<unsigned long long>();
-    uint32_t* stamp = s->stamp.as<uint32_t>();
-    int32_t* fr[2] = {s->fr[0].as<int32_t>(), s->fr[1].as<int32_t>()};
-    unsigned long long* frval = s->frval.as<unsigned long long>();
+    Relax r;
+    r.X[0] = s->X.as<unsigned long long>();
+    r.X[1] = r.X[0] + n;
+    r.fr[0] = s->fr[0].as<int32_t>();
+    r.fr[1] = s->fr[1].as<int32_t>();
+    r.frval = s->frval.as<unsigned long long>();
+    r.stamp = s->stamp.as<uint32_t>();
+    r.cnt = cnt;
+    r.h_cnt = &g->h_ctr->aux3;
+    int32_t* touched = s->touched.as<int32_t>();
     uint32_t epoch = 0;
     uint32_t sv = 0;  // frontier stamp values, unique per round
     int64_t n_u = m;
@@ -474,7 +473,8 @@ int open_facilities(fl_solve* s) {
         // bucket the undecided facilities by ball radius
         FL_CUDA(cudaMemsetAsync(bcount, 0, (bmax + 1) * 4, st));
         FL_CUDA(cudaMemsetAsync(&cnt[4], 0, 8, st));
-        FL_LAUNCH(kProfMis, k_bucket_count<<<grid_for(n_u, 256), 256, 0, st>>>(ulist[cu], n_u, s->bcap.as<int32_t>(), bcount, &cnt[4]));
+        FL_LAUNCH(kProfMis, k_bucket_count<<<grid_for(n_u, 256), 256, 0, st>>>(ulist[cu], n_u, s->bcap.as<int32_t>(),
+                                                                               bcount, &cnt[4]));
         FL_CUDA(cudaGetLastError());
         unsigned long long T64 = 0;
         FL_CUDA(cudaMemcpyAsync(&T64, &cnt[4], 8, cudaMemcpyDeviceToHost, st));
@@ -484,8 +484,8 @@ int open_facilities(fl_solve* s) {
         int32_t acc = 0;
         for (int b = 0; b <= T; ++b) { hoff[b] = acc; acc += hcount[b]; }
         FL_CUDA(cudaMemcpyAsync(cursor, hoff.data(), (T + 1) * 4, cudaMemcpyHostToDevice, st));
-        FL_LAUNCH(kProfMis, k_bucket_scatter<<<grid_for(n_u, 256), 256, 0, st>>>(ulist[cu], n_u, s->bcap.as<int32_t>(), cursor,
-                                                            s->ubuck.as<int32_t>()));
+        FL_LAUNCH(kProfMis, k_bucket_scatter<<<grid_for(n_u, 256), 256, 0, st>>>(
+                                ulist[cu], n_u, s->bcap.as<int32_t>(), cursor, s->ubuck.as<int32_t>()));
         FL_CUDA(cudaGetLastError());
         const int32_t* ub = s->ubuck.as<int32_t>();
 
@@ -493,53 +493,63 @@ int open_facilities(fl_solve* s) {
         // Facility f starts at time T - B_f; all waves stop at time T.
         ++epoch;
         const unsigned long long hi_c = 0xffffffffULL - epoch;
-        FL_CUDA(cudaMemsetAsync(cnt, 0, 24, st));  // both frontiers + touched
-        int c = 0;
+        r.limit = (hi_c + 1) << 32;
+        FL_CUDA(cudaMemsetAsync(cnt, 0, 24, st));
+        r.n_front = 0;
+        r.list_valid = true;
         const uint32_t sv0 = sv;
+        r.sv_prev = sv0 + 1;
         for (int t = 0; t <= T; ++t) {
             const int b = T - t;
-            if (hcount[b] > 0)
-                FL_LAUNCH(kProfMis, k_inject<<<grid_for(hcount[b], 256), 256, 0, st>>>(ub + hoff[b], hcount[b], nullptr, hi_c,
-                                                                  s->ord.as<uint32_t>(), X, stamp, sv0 + 1 + t, fr[c],
-                                                                  &cnt[c]));
-            FL_LAUNCH(kProfMis, k_snapshot<<<152 * 2, 256, 0, st>>>(fr[c], &cnt[c], X, frval, &cnt[c ^ 1], tstamp, epoch,
-                                                s->touched.as<int32_t>(), &cnt[2]));
-            if (t < T)
-                FL_LAUNCH(kProfMis, k_push<<<152 * 8, 256, 0, st>>>(fr[c], frval, &cnt[c], g->rowp.as<int64_t>(), g->cols.as<int32_t>(),
-                                                0ULL, X, stamp, sv0 + 2 + t, fr[c ^ 1], &cnt[c ^ 1]));
-            c ^= 1;
+            if (hcount[b] > 0) {
+                FL_TRY(relax_prepare_list(g, r, kProfMis));
+                FL_LAUNCH(kProfMis, k_inject<<<grid_for(hcount[b], 256), 256, 0, st>>>(
+                                        ub + hoff[b], hcount[b], nullptr, hi_c, s->ord.as<uint32_t>(), r.X[r.cur],
+                                        r.stamp, sv0 + 1 + t, r.fr[r.fc], &r.cnt[r.fc]));
+                FL_CUDA(cudaGetLastError());
+                r.n_front += hcount[b];
+            }
+            if (t < T && r.n_front > 0) FL_TRY(relax_round(g, r, 0ULL, sv0 + 2 + t, kProfMis));
+            else if (t < T) r.sv_prev = sv0 + 2 + t;
         }
-        FL_CUDA(cudaGetLastError());
         sv = sv0 + T + 2;
+        // every vertex the cover reached (its value carries this sweep's epoch)
+        FL_TRY(relax_collect_epoch(g, r.X[r.cur], hi_c, touched, &cnt[6], kProfMis));
 
         // ---- gather: min over Ball(f) of (claimed ? 0 : cover + 1), read at radius B_f
         ++epoch;
         const unsigned long long hi_g = 0xffffffffULL - epoch;
-        FL_CUDA(cudaMemsetAsync(cnt, 0, 16, st));
-        c = 0;
+        r.limit = (hi_g + 1) << 32;
+        FL_CUDA(cudaMemsetAsync(cnt, 0, 24, st));
+        r.fc = 0;
         const uint32_t sg0 = ++sv;
-        FL_LAUNCH(kProfMis, k_gather_seed<<<152 * 2, 256, 0, st>>>(s->touched.as<int32_t>(), &cnt[2], s->client.as<uint8_t>(),
-                                               s->claimed.as<uint8_t>(), hi_g, X, s->mval.as<uint32_t>(), stamp, sg0,
-                                               fr[c], &cnt[c]));
+        FL_LAUNCH(kProfMis, k_gather_seed<<<152 * 2, 256, 0, st>>>(touched, &cnt[6], s->client.as<uint8_t>(),
+                                                                   s->claimed.as<uint8_t>(), hi_g, r.X[r.cur],
+                                                                   s->mval.as<uint32_t>(), r.stamp, sg0, r.fr[0],
+                                                                   &r.cnt[0]));
+        FL_CUDA(cudaGetLastError());
+        FL_CUDA(cudaMemcpyAsync(r.h_cnt, &r.cnt[0], 8, cudaMemcpyDeviceToHost, st));
+        FL_CUDA(cudaStreamSynchronize(st));
+        r.n_front = (int64_t)*r.h_cnt;
+        r.list_valid = true;
+        r.sv_prev = sg0;
         if (hcount[0] > 0)
-            FL_LAUNCH(kProfMis, k_decide<<<grid_for(hcount[0], 256), 256, 0, st>>>(ub + hoff[0], hcount[0], X, hi_g,
-                                                               s->ord.as<uint32_t>(), s->state.as<uint8_t>(),
-                                                               g->ctr.as<Counters>()));
+            FL_LAUNCH(kProfMis, k_decide<<<grid_for(hcount[0], 256), 256, 0, st>>>(
+                                    ub + hoff[0], hcount[0], r.X[r.cur], hi_g, s->ord.as<uint32_t>(),
+                                    s->state.as<uint8_t>(), g->ctr.as<Counters>()));
         for (int b = 1; b <= T; ++b) {
-            FL_LAUNCH(kProfMis, k_snapshot<<<152 * 2, 256, 0, st>>>(fr[c], &cnt[c], X, frval, &cnt[c ^ 1], nullptr, 0, nullptr, nullptr));
-            FL_LAUNCH(kProfMis, k_push<<<152 * 8, 256, 0, st>>>(fr[c], frval, &cnt[c], g->rowp.as<int64_t>(), g->cols.as<int32_t>(), 0ULL,
-                                            X, stamp, sg0 + b, fr[c ^ 1], &cnt[c ^ 1]));
-            c ^= 1;
+            if (r.n_front > 0) FL_TRY(relax_round(g, r, 0ULL, sg0 + b, kProfMis));
+            else r.sv_prev = sg0 + b;
             if (hcount[b] > 0)
-                FL_LAUNCH(kProfMis, k_decide<<<grid_for(hcount[b], 256), 256, 0, st>>>(ub + hoff[b], hcount[b], X, hi_g,
-                                                                   s->ord.as<uint32_t>(), s->state.as<uint8_t>(),
-                                                                   g->ctr.as<Counters>()));
+                FL_LAUNCH(kProfMis, k_decide<<<grid_for(hcount[b], 256), 256, 0, st>>>(
+                                        ub + hoff[b], hcount[b], r.X[r.cur], hi_g, s->ord.as<uint32_t>(),
+                                        s->state.as<uint8_t>(), g->ctr.as<Counters>()));
         }
         sv = sg0 + T + 1;
         FL_CUDA(cudaGetLastError());
 
         // ---- claim the balls of this round's winners; keep the undecided
-        FL_LAUNCH(kProfMis, k_claim<<<152 * 4, 256, 0, st>>>(s->touched.as<int32_t>(), &cnt[2], s->client.as<uint8_t>(),
+        FL_LAUNCH(kProfMis, k_claim<<<152 * 4, 256, 0, st>>>(s->touched.as<int32_t>(), &cnt[6], s->client.as<uint8_t>(),
                                          s->claimed.as<uint8_t>(), s->mval.as<uint32_t>(),
                                          s->fac_by_ord.as<int32_t>(), s->state.as<uint8_t>()));
         FL_CUDA(cudaMemsetAsync(&cnt[3], 0, 8, st));
