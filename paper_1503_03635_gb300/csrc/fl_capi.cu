@@ -33,7 +33,8 @@ void destroy_graph(fl_graph* g) {
     DBuf* bufs[] = {&g->rowp, &g->cols, &g->low_list, &g->hub_list, &g->hub_seg, &g->seg_hub, &g->part,
                     &g->S, &g->Scnt, &g->D[0], &g->D[1], &g->Dcnt[0], &g->Dcnt[1], &g->frontier[0],
                     &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent, &g->stg_grp, &g->gofs, &g->eofs,
-                    &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub, &g->ctr, &g->scratch};
+                    &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub, &g->ctr, &g->scratch,
+                    &g->relax_aux};
     for (DBuf* b : bufs) dfree(*b);
     for (cudaEvent_t e : g->prof.ev) cudaEventDestroy(e);
     if (g->h_ctr) cudaFreeHost(g->h_ctr);

@@ -94,6 +94,11 @@ __host__ __device__ __forceinline__ uint64_t facility_priority(uint64_t seed, in
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Vertices with more than kHubDeg neighbours are hubs; their edge lists are
+// processed in segments of kSeg edges, one group of lanes per segment.
+constexpr int kHubDeg = 2048;
+constexpr int kSeg = 2048;
+
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
@@ -375,6 +380,7 @@ struct fl_graph {
     fl::DBuf ctr;                  // Counters
     fl::Counters* h_ctr = nullptr; // pinned host mirror
     fl::DBuf scratch;              // general scratch (scans, sorts)
+    fl::DBuf relax_aux;            // bitmap, hub frontier tags/values, edge counter of the rounds
     fl::Prof prof;                 // launch counts and kernel timings
 };
 
@@ -428,7 +434,17 @@ struct Relax {
     uint32_t sv_prev = 0;                           // stamp of the current frontier
     unsigned long long limit = ~0ULL;               // values >= limit are ignored by pulls
     int dense_div = 8;                              // pull when frontier * dense_div >= vertices
+    int edge_div = 16;                              // pull when frontier edges * edge_div >= nnz
+    bool settle = false;                            // a value < limit is final (level-synchronous BFS)
+    // set by relax_begin (graph-owned scratch)
+    uint32_t* bm = nullptr;                         // frontier bitmap of a pull round (n bits)
+    uint32_t* hub_tag = nullptr;                    // uint32[n_hubs]: round whose push frontier holds the hub
+    unsigned long long* hub_val = nullptr;          // uint64[n_hubs]: the hub's snapshotted value
+    unsigned long long* ecnt = nullptr;             // device: frontier edge count
 };
+// Binds the graph-owned scratch of the rounds to r; call once per sweep
+// family, after r.stamp values of earlier users may have been reused.
+int relax_begin(fl_graph* g, Relax& r);
 int relax_round(fl_graph* g, Relax& r, unsigned long long add, uint32_t sv, int cls);
 int relax_prepare_list(fl_graph* g, Relax& r, int cls);
 int relax_collect_epoch(fl_graph* g, const unsigned long long* X, unsigned long long hi, int32_t* out,

@@ -4,26 +4,19 @@
 //
 // One round: every vertex v takes X'[v] = min(X[v], min_{u in N(v)} X[u] + add),
 // reading only values of the previous round, so a value moves exactly one hop
-// per round.  Sparse rounds push from a frontier list (k_snapshot + k_push, in
-// place on one buffer, the frontier's values snapshotted first); dense rounds
-// pull into the second buffer (every vertex reads its neighbours; no atomics)
-// and flag changed vertices with the next round's stamp.
+// per round.  Only the frontier (the vertices whose value changed in the
+// previous round) can lower a value.  Push rounds walk the frontier list
+// (k_snap_front + k_push_low / k_push_segs, in place on one buffer, the
+// frontier's values snapshotted first); pull rounds write the second buffer
+// (every vertex reads its frontier neighbours, found in a bitmap; no atomics
+// except per hub segment) and flag changed vertices with the next round's
+// stamp.  Hub edge lists are split into kSeg-edge segments in both.
 #include <algorithm>
 #include <cstdio>
 
 #include "fl_internal.cuh"
 
 namespace fl {
-
-__global__ void k_snapshot(const int32_t* __restrict__ fr, const unsigned long long* __restrict__ n_fr,
-                           const unsigned long long* __restrict__ X, unsigned long long* __restrict__ frval,
-                           unsigned long long* __restrict__ reset_next, uint32_t* __restrict__ tstamp, uint32_t tval,
-                           int32_t* __restrict__ touched, unsigned long long* __restrict__ n_touched);
-__global__ void k_push(const int32_t* __restrict__ fr, const unsigned long long* __restrict__ frval,
-                       const unsigned long long* __restrict__ n_fr, const int64_t* __restrict__ rowp,
-                       const int32_t* __restrict__ cols, unsigned long long add, unsigned long long* __restrict__ X,
-                       uint32_t* __restrict__ stamp, uint32_t sv, int32_t* __restrict__ fr_next,
-                       unsigned long long* __restrict__ n_next);
 
 namespace {
 
@@ -34,15 +27,34 @@ int grid_for(int64_t items, int per_block) {
     return (int)b;
 }
 
+__device__ __forceinline__ bool in_front(const uint32_t* __restrict__ bm, int32_t u) {
+    return (__ldg(&bm[u >> 5]) >> (u & 31)) & 1u;
+}
+
+// Frontier bitmap of a pull round: bit v = (stamp[v] == sv).  Only neighbours
+// whose value changed in the previous round can lower a value, so a pull
+// reads the value of a neighbour only when its bit is set; the bitmap (n/8
+// bytes) stays in L2 while the values do not.
+__global__ void k_bitmap(const uint32_t* __restrict__ stamp, uint32_t sv, int64_t n, uint32_t* __restrict__ bm) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t v = base + lane_id();
+        const unsigned w = __ballot_sync(kFull, v < n && stamp[v] == sv);
+        if (lane_id() == 0) bm[base >> 5] = w;
+    }
+}
+
 // Values >= `limit` are ignored: unset entries (BFS) or values of an earlier
-// sweep (MIS sweeps stamp each sweep into the high word).
+// sweep (MIS sweeps stamp each sweep into the high word).  With `settle`, a
+// vertex holding a value below the limit is final and is skipped.
 //
-// Dense round over non-hub vertices: four vertices per warp in lockstep, eight
+// Pull round over non-hub vertices: four vertices per warp in lockstep, eight
 // lanes per vertex striding over its neighbours; the loop runs to the largest
 // degree of the four so every shuffle and ballot involves the whole warp.
 __global__ void __launch_bounds__(256) k_pull_low(const int32_t* __restrict__ list, int64_t n_list,
                                                   const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
-                                                  unsigned long long add, unsigned long long limit,
+                                                  unsigned long long add, unsigned long long limit, bool settle,
+                                                  const uint32_t* __restrict__ bm,
                                                   const unsigned long long* __restrict__ X,
                                                   unsigned long long* __restrict__ Xn, uint32_t* __restrict__ stamp,
                                                   uint32_t sv, unsigned long long* __restrict__ n_changed) {
@@ -54,21 +66,25 @@ __global__ void __launch_bounds__(256) k_pull_low(const int32_t* __restrict__ li
         const int64_t i = w * 4 + (lane >> 3);
         const bool have = i < n_list;
         const int32_t v = have ? list[i] : 0;
-        const int64_t beg = have ? rowp[v] : 0, end = have ? rowp[v + 1] : 0;
         const unsigned long long own = have ? X[v] : ~0ULL;
+        const bool work = have && !(settle && own < limit);
+        const int64_t beg = work ? rowp[v] : 0, end = work ? rowp[v + 1] : 0;
         unsigned long long m = own;
         int64_t len = end - beg;
 #pragma unroll
         for (int o = 8; o < 32; o <<= 1) len = max(len, __shfl_xor_sync(kFull, len, o));
         for (int64_t off = sub; off < len; off += 8) {
             if (beg + off < end) {
-                const unsigned long long x = __ldg(&X[__ldg(&cols[beg + off])]);
-                if (x < limit && x + add < m) m = x + add;
+                const int32_t u = __ldcs(&cols[beg + off]);
+                if (in_front(bm, u)) {
+                    const unsigned long long x = __ldg(&X[u]);
+                    if (x < limit && x + add < m) m = x + add;
+                }
             }
         }
 #pragma unroll
         for (int o = 1; o < 8; o <<= 1) m = umin64(m, __shfl_xor_sync(kFull, m, o));
-        const bool ch = have && sub == 0 && m < own;
+        const bool ch = work && sub == 0 && m < own;
         if (ch) {
             Xn[v] = m;
             stamp[v] = sv;
@@ -78,36 +94,151 @@ __global__ void __launch_bounds__(256) k_pull_low(const int32_t* __restrict__ li
     if (lane == 0 && changed) atomicAdd(n_changed, changed);
 }
 
-// Dense round over hubs: one block per hub.
-__global__ void __launch_bounds__(256) k_pull_hubs(const int32_t* __restrict__ hubs, int64_t n_hubs,
+// Pull round over hubs: one warp per segment of kSeg edges.  Xn[v] starts as
+// X[v]; the segments lower it with atomicMin and the one that lowers it first
+// (it sees the old value) flags the hub.
+__global__ void __launch_bounds__(256) k_pull_segs(const int32_t* __restrict__ seg_hub, int64_t n_seg,
+                                                   const int64_t* __restrict__ hub_seg,
+                                                   const int32_t* __restrict__ hub_list,
                                                    const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
-                                                   unsigned long long add, unsigned long long limit,
+                                                   unsigned long long add, unsigned long long limit, bool settle,
+                                                   const uint32_t* __restrict__ bm,
                                                    const unsigned long long* __restrict__ X,
                                                    unsigned long long* __restrict__ Xn, uint32_t* __restrict__ stamp,
                                                    uint32_t sv, unsigned long long* __restrict__ n_changed) {
-    __shared__ unsigned long long red[8];
-    for (int64_t h = blockIdx.x; h < n_hubs; h += gridDim.x) {
-        const int32_t v = hubs[h];
-        const int64_t beg = rowp[v], end = rowp[v + 1];
+    const int lane = lane_id();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sidx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sidx < n_seg; sidx += warps) {
+        const int32_t h = seg_hub[sidx];
+        const int32_t v = hub_list[h];
+        const unsigned long long own = X[v];
+        if (settle && own < limit) continue;
+        const int64_t e0 = rowp[v] + (sidx - hub_seg[h]) * kSeg;
+        const int64_t e1 = min(e0 + (int64_t)kSeg, rowp[v + 1]);
         unsigned long long m = ~0ULL;
-        for (int64_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
-            const unsigned long long x = __ldg(&X[__ldg(&cols[e])]);
-            if (x < limit && x + add < m) m = x + add;
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            const int32_t u = __ldcs(&cols[e]);
+            if (in_front(bm, u)) {
+                const unsigned long long x = __ldg(&X[u]);
+                if (x < limit && x + add < m) m = x + add;
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = umin64(m, __shfl_xor_sync(kFull, m, o));
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = umin64(m, red[i]);
-            const unsigned long long own = X[v];
-            if (m < own) {
-                Xn[v] = m;
+        if (lane == 0 && m < own) {
+            const unsigned long long old = atomicMin(&Xn[v], m);
+            if (old == own) {
                 stamp[v] = sv;
                 atomicAdd(n_changed, 1ULL);
             }
         }
-        __syncthreads();
+    }
+}
+
+// Snapshot of a push frontier: frval[i] = X[fr[i]], the frontier's edge count
+// into *edges, and each hub of the frontier tagged (hub_tag = tag, hub_val =
+// its value) for the segment push.  hub_list is ascending.
+__global__ void k_snap_front(const int32_t* __restrict__ fr, const unsigned long long* __restrict__ n_fr,
+                             const unsigned long long* __restrict__ X, unsigned long long* __restrict__ frval,
+                             unsigned long long* __restrict__ reset_next, const int64_t* __restrict__ rowp,
+                             const int32_t* __restrict__ hub_list, int64_t n_hubs, uint32_t* __restrict__ hub_tag,
+                             uint32_t tag, unsigned long long* __restrict__ hub_val,
+                             unsigned long long* __restrict__ edges) {
+    const int64_t n = (int64_t)*n_fr;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *reset_next = 0;
+    unsigned long long ed = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int32_t v = fr[i];
+        const unsigned long long x = X[v];
+        frval[i] = x;
+        const int64_t d = rowp[v + 1] - rowp[v];
+        ed += (unsigned long long)d;
+        if (d > kHubDeg) {
+            int64_t lo = 0, hi = n_hubs;  // first hub_list entry >= v
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (hub_list[mid] < v) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < n_hubs && hub_list[lo] == v) {
+                hub_val[lo] = x;
+                hub_tag[lo] = tag;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ed += __shfl_xor_sync(kFull, ed, o);
+    if (lane_id() == 0 && ed) atomicAdd(edges, ed);
+}
+
+// Push from the non-hub frontier vertices: a warp per vertex, read-before-
+// atomicMin on the neighbours, stamp dedupe for the next frontier.
+__global__ void __launch_bounds__(256) k_push_low(const int32_t* __restrict__ fr,
+                                                  const unsigned long long* __restrict__ frval,
+                                                  const unsigned long long* __restrict__ n_fr,
+                                                  const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
+                                                  unsigned long long add, unsigned long long* __restrict__ X,
+                                                  uint32_t* __restrict__ stamp, uint32_t sv,
+                                                  int32_t* __restrict__ fr_next, unsigned long long* __restrict__ n_next) {
+    const int lane = lane_id();
+    const int64_t n = (int64_t)*n_fr;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; w < n; w += warps) {
+        const int32_t v = fr[w];
+        const int64_t beg = rowp[v], end = rowp[v + 1];
+        if (end - beg > kHubDeg) continue;  // hubs: k_push_segs
+        const unsigned long long val = frval[w] + add;
+        for (int64_t cb = beg; cb < end; cb += 32) {
+            const int64_t e = cb + lane;
+            bool fresh = false;
+            int32_t u = 0;
+            if (e < end) {
+                u = cols[e];
+                if (val < X[u]) {
+                    const unsigned long long old = atomicMin(&X[u], val);
+                    if (val < old) fresh = atomicExch(&stamp[u], sv) != sv;
+                }
+            }
+            const long long at = warp_append(fresh, n_next);
+            if (at >= 0) fr_next[at] = u;
+        }
+    }
+}
+
+// Push from the frontier hubs (tagged by k_snap_front): a warp per segment.
+__global__ void __launch_bounds__(256) k_push_segs(const int32_t* __restrict__ seg_hub, int64_t n_seg,
+                                                   const int64_t* __restrict__ hub_seg,
+                                                   const int32_t* __restrict__ hub_list,
+                                                   const uint32_t* __restrict__ hub_tag, uint32_t tag,
+                                                   const unsigned long long* __restrict__ hub_val,
+                                                   const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
+                                                   unsigned long long add, unsigned long long* __restrict__ X,
+                                                   uint32_t* __restrict__ stamp, uint32_t sv,
+                                                   int32_t* __restrict__ fr_next, unsigned long long* __restrict__ n_next) {
+    const int lane = lane_id();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sidx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sidx < n_seg; sidx += warps) {
+        const int32_t h = seg_hub[sidx];
+        if (hub_tag[h] != tag) continue;
+        const int32_t v = hub_list[h];
+        const unsigned long long val = hub_val[h] + add;
+        const int64_t e0 = rowp[v] + (sidx - hub_seg[h]) * kSeg;
+        const int64_t e1 = min(e0 + (int64_t)kSeg, rowp[v + 1]);
+        for (int64_t cb = e0; cb < e1; cb += 32) {
+            const int64_t e = cb + lane;
+            bool fresh = false;
+            int32_t u = 0;
+            if (e < e1) {
+                u = cols[e];
+                if (val < X[u]) {
+                    const unsigned long long old = atomicMin(&X[u], val);
+                    if (val < old) fresh = atomicExch(&stamp[u], sv) != sv;
+                }
+            }
+            const long long at = warp_append(fresh, n_next);
+            if (at >= 0) fr_next[at] = u;
+        }
     }
 }
 
@@ -122,6 +253,8 @@ __global__ void k_collect_stamped(const uint32_t* __restrict__ stamp, uint32_t s
         if (at >= 0) out[at] = (int32_t)v;
     }
 }
+
+constexpr int64_t kPushAlways = 4096;  // smaller frontiers push without counting their edges
 
 }  // namespace
 
@@ -145,13 +278,38 @@ int relax_collect_epoch(fl_graph* g, const unsigned long long* X, unsigned long 
     return FL_OK;
 }
 
+int relax_begin(fl_graph* g, Relax& r) {
+    if (!g->lists_ready) {
+        FL_TRY(build_work_lists(g));
+        g->lists_ready = 1;
+    }
+    const size_t bm_words = (size_t)(g->n + 63) / 32 + 2;
+    const size_t off_tag = ((bm_words * 4 + 255) / 256) * 256;
+    const size_t off_val = off_tag + (((size_t)g->n_hubs * 4 + 255) / 256) * 256;
+    const size_t off_cnt = off_val + (((size_t)g->n_hubs * 8 + 255) / 256) * 256;
+    FL_TRY(dalloc(g->relax_aux, off_cnt + 256));
+    char* base = g->relax_aux.as<char>();
+    r.bm = reinterpret_cast<uint32_t*>(base);
+    r.hub_tag = reinterpret_cast<uint32_t*>(base + off_tag);
+    r.hub_val = reinterpret_cast<unsigned long long*>(base + off_val);
+    r.ecnt = reinterpret_cast<unsigned long long*>(base + off_cnt);
+    if (g->n_hubs > 0) FL_CUDA(cudaMemsetAsync(r.hub_tag, 0, (size_t)g->n_hubs * 4, g->stream));
+    FL_CUDA(cudaMemsetAsync(r.ecnt, 0, 256, g->stream));
+    return FL_OK;
+}
+
 // One synchronous round.  The caller keeps the frontier count on the host
 // (r.n_front) and, for push rounds, a valid list in r.fr[r.fc] with its count
 // in r.cnt[r.fc].  `sv` is the stamp of the frontier this round produces.
+// A round pushes when its frontier is small (few vertices, or few edges);
+// otherwise it pulls with the frontier bitmap.
 int relax_round(fl_graph* g, Relax& r, unsigned long long add, uint32_t sv, int cls) {
     cudaStream_t st = g->stream;
     const int64_t n = g->n;
-    const bool dense = r.n_front * r.dense_div >= g->n_low + g->n_hubs;
+    const int64_t* rowp = g->rowp.as<int64_t>();
+    const int32_t* cols = g->cols.as<int32_t>();
+    const int32_t* hub_list = g->hub_list.as<int32_t>();
+    bool dense = r.n_front * r.dense_div >= g->n_low + g->n_hubs;
     unsigned long long* X = r.X[r.cur];
     if (!dense) {
         if (!r.list_valid) {
@@ -159,29 +317,45 @@ int relax_round(fl_graph* g, Relax& r, unsigned long long add, uint32_t sv, int 
             FL_CUDA(cudaMemsetAsync(&r.cnt[r.fc], 0, 8, st));
             FL_LAUNCH(cls, k_collect_stamped<<<grid_for(n, 256), 256, 0, st>>>(r.stamp, r.sv_prev, n, r.fr[r.fc],
                                                                               &r.cnt[r.fc]));
+            r.list_valid = true;
         }
-        FL_LAUNCH(cls, k_snapshot<<<grid_for(r.n_front, 256), 256, 0, st>>>(r.fr[r.fc], &r.cnt[r.fc], X, r.frval,
-                                                                           &r.cnt[r.fc ^ 1], nullptr, 0, nullptr,
-                                                                           nullptr));
-        FL_LAUNCH(cls, k_push<<<grid_for(r.n_front, 8), 256, 0, st>>>(r.fr[r.fc], r.frval, &r.cnt[r.fc],
-                                                                     g->rowp.as<int64_t>(), g->cols.as<int32_t>(), add,
-                                                                     X, r.stamp, sv, r.fr[r.fc ^ 1], &r.cnt[r.fc ^ 1]));
+        FL_CUDA(cudaMemsetAsync(r.ecnt, 0, 8, st));
+        FL_LAUNCH(cls, k_snap_front<<<grid_for(r.n_front, 256), 256, 0, st>>>(
+                           r.fr[r.fc], &r.cnt[r.fc], X, r.frval, &r.cnt[r.fc ^ 1], rowp, hub_list, g->n_hubs,
+                           r.hub_tag, r.sv_prev, r.hub_val, r.ecnt));
+        FL_CUDA(cudaGetLastError());
+        if (r.n_front >= kPushAlways) {
+            FL_CUDA(cudaMemcpyAsync(r.h_cnt, r.ecnt, 8, cudaMemcpyDeviceToHost, st));
+            FL_CUDA(cudaStreamSynchronize(st));
+            dense = (int64_t)*r.h_cnt * r.edge_div >= g->nnz;
+        }
+    }
+    if (!dense) {
+        FL_LAUNCH(cls, k_push_low<<<grid_for(r.n_front, 8), 256, 0, st>>>(r.fr[r.fc], r.frval, &r.cnt[r.fc], rowp, cols,
+                                                                         add, X, r.stamp, sv, r.fr[r.fc ^ 1],
+                                                                         &r.cnt[r.fc ^ 1]));
+        if (g->n_seg > 0)
+            FL_LAUNCH(cls, k_push_segs<<<grid_for(g->n_seg, 8), 256, 0, st>>>(
+                               g->seg_hub.as<int32_t>(), g->n_seg, g->hub_seg.as<int64_t>(), hub_list, r.hub_tag,
+                               r.sv_prev, r.hub_val, rowp, cols, add, X, r.stamp, sv, r.fr[r.fc ^ 1],
+                               &r.cnt[r.fc ^ 1]));
         FL_CUDA(cudaGetLastError());
         r.fc ^= 1;
         r.list_valid = true;
         FL_CUDA(cudaMemcpyAsync(r.h_cnt, &r.cnt[r.fc], 8, cudaMemcpyDeviceToHost, st));
     } else {
         unsigned long long* Xn = r.X[r.cur ^ 1];
+        FL_LAUNCH(cls, k_bitmap<<<grid_for(n, 256), 256, 0, st>>>(r.stamp, r.sv_prev, n, r.bm));
         FL_CUDA(cudaMemcpyAsync(Xn, X, (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
         FL_CUDA(cudaMemsetAsync(&r.cnt[2], 0, 8, st));
         if (g->n_low > 0)
             FL_LAUNCH(cls, k_pull_low<<<grid_for((g->n_low + 3) / 4, 8), 256, 0, st>>>(
-                               g->low_list.as<int32_t>(), g->n_low, g->rowp.as<int64_t>(), g->cols.as<int32_t>(), add,
-                               r.limit, X, Xn, r.stamp, sv, &r.cnt[2]));
-        if (g->n_hubs > 0)
-            FL_LAUNCH(cls, k_pull_hubs<<<(int)std::min<int64_t>(g->n_hubs, 152 * 8), 256, 0, st>>>(
-                               g->hub_list.as<int32_t>(), g->n_hubs, g->rowp.as<int64_t>(), g->cols.as<int32_t>(), add,
-                               r.limit, X, Xn, r.stamp, sv, &r.cnt[2]));
+                               g->low_list.as<int32_t>(), g->n_low, rowp, cols, add, r.limit, r.settle, r.bm, X, Xn,
+                               r.stamp, sv, &r.cnt[2]));
+        if (g->n_seg > 0)
+            FL_LAUNCH(cls, k_pull_segs<<<grid_for(g->n_seg, 8), 256, 0, st>>>(
+                               g->seg_hub.as<int32_t>(), g->n_seg, g->hub_seg.as<int64_t>(), hub_list, rowp, cols, add,
+                               r.limit, r.settle, r.bm, X, Xn, r.stamp, sv, &r.cnt[2]));
         FL_CUDA(cudaGetLastError());
         r.cur ^= 1;
         r.list_valid = false;

@@ -39,8 +39,6 @@ __host__ __device__ __forceinline__ uint32_t pack_info(int hop, int cnt, int cou
 }
 
 constexpr int kMaxHops = 65535;
-constexpr int kHubDeg = 2048;  // vertices with more neighbours are split into segments
-constexpr int kSeg = 2048;     // edges per hub segment
 
 // Per-group counters accumulated in registers and flushed once per group.
 struct HopCounters {

@@ -135,7 +135,8 @@ int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, i
     r.cnt = reinterpret_cast<unsigned long long*>(frval.as<char>() + (size_t)n * 8);
     r.h_cnt = &g->h_ctr->aux3;
     r.limit = ~0ULL;
-    r.dense_div = 2;  // a BFS pushes each edge once; pull only for very large levels
+    r.settle = true;  // level-synchronous: a vertex's first value is its final one
+    FL_TRY(relax_begin(g, r));
     FL_CUDA(cudaMemsetAsync(r.X[0], 0xff, (size_t)n * 8, st));
     FL_CUDA(cudaMemsetAsync(r.stamp, 0, (size_t)n * 4, st));
     FL_CUDA(cudaMemsetAsync(r.cnt, 0, 64, st));
@@ -459,6 +460,10 @@ int open_facilities(fl_solve* s) {
     r.stamp = s->stamp.as<uint32_t>();
     r.cnt = cnt;
     r.h_cnt = &g->h_ctr->aux3;
+    if ((rc = relax_begin(g, r)) != FL_OK) {
+        dfree(bcount_d);
+        return rc;
+    }
     int32_t* touched = s->touched.as<int32_t>();
     uint32_t epoch = 0;
     uint32_t sv = 0;  // frontier stamp values, unique per round

@@ -124,6 +124,25 @@ def test_rmat20_workload_full():
     _compare(w, _gpu(w), _oracle(w))
 
 
+def test_hubs_in_push_and_pull_rounds():
+    """Two hubs of several kSeg-edge segments each (degrees 6000 and 3000)
+    sharing leaves, a long path hanging off them and a few isolated vertices:
+    the BFS and the MIS sweeps push hub segments while the frontier is small
+    and pull them once it is large."""
+    n = 9000
+    edges = [(0, i) for i in range(1, 6001)]
+    edges += [(6001, i) for i in range(3500, 6500)]
+    edges += [(i, i + 1) for i in range(6500, 8990)]
+    rowp, cols = brute.csr_from_edges(n, edges)
+    client = flsynth.bernoulli(n, 21, 0.7)
+    fac = flsynth.bernoulli(n, 22, 0.2)
+    fac[[0, 6001, 8500]] = 1
+    cost = flsynth.loguniform(n, 23, 3.0, 3000.0, fac)
+    for k in (4, 16):
+        w = flsynth.from_csr("twohubs", rowp, cols, k, 5, cost, client)
+        _compare(w, _gpu(w), _oracle(w))
+
+
 # ------------------------------------------------------------------ edge cases
 
 def test_single_vertex():
