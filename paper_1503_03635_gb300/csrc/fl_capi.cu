@@ -34,7 +34,7 @@ void destroy_graph(fl_graph* g) {
                     &g->S, &g->Scnt, &g->D[0], &g->D[1], &g->Dcnt[0], &g->Dcnt[1], &g->frontier[0],
                     &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent, &g->stg_grp, &g->gofs, &g->eofs,
                     &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub, &g->ctr, &g->scratch,
-                    &g->relax_aux};
+                    &g->relax_aux, &g->U, &g->DM[0], &g->DM[1], &g->PM};
     for (DBuf* b : bufs) dfree(*b);
     for (cudaEvent_t e : g->prof.ev) cudaEventDestroy(e);
     if (g->h_ctr) cudaFreeHost(g->h_ctr);

@@ -98,6 +98,9 @@ constexpr unsigned kFull = 0xffffffffu;
 // processed in segments of kSeg edges, one group of lanes per segment.
 constexpr int kHubDeg = 2048;
 constexpr int kSeg = 2048;
+// Width of the small-rank universe of the sketch hops (the kUW smallest
+// ranks of a graph; a saturated sketch is a kUW-bit mask over them).
+constexpr int kUW = 256;
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
@@ -356,6 +359,10 @@ struct fl_graph {
     fl::DBuf seg_hub;              // int32[n_seg]: hub of each segment
     int64_t n_low = 0, n_hubs = 0, n_seg = 0;
     fl::DBuf part;                 // uint64[n_seg*k]: partial bottom-k of each hub segment (scratch)
+    fl::DBuf U;                    // uint64[kUW]: the kUW smallest ranks, ascending (kEmpty padded)
+    uint64_t ulim = 0;             // largest entry of U
+    fl::DBuf DM[2];                // uint64[n*4]: hop delta masks over U
+    fl::DBuf PM;                   // uint64[n_seg*4]: partial masks of hub segments (scratch)
     // sketches
     int k = 0;
     uint64_t seed = 0;

@@ -40,6 +40,139 @@ __host__ __device__ __forceinline__ uint32_t pack_info(int hop, int cnt, int cou
 
 constexpr int kMaxHops = 65535;
 
+// ------------------------------------------------------------------ small-rank masks
+// U = the kUW smallest ranks of the graph, ascending.  Every rank <= U[last]
+// is an entry of U, so once a sketch is full and its k-th rank is <= U[last]
+// ("saturated"), all its entries and every candidate that can still enter it
+// are entries of U: the sketch is a kUW-bit mask over U, and one hop is
+// S_h(v) = lowest k bits of (S_{h-1}(v) | OR_{u in N(v)} D_{h-1}(u)), with
+// D_{h-1}(u) kept as a mask beside its list.  Candidates above U[last] are
+// above the k-th rank and drop out either way, so the mask update is the
+// list merge exactly.
+
+struct Mask4 {
+    uint64_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+    __device__ __forceinline__ void set(int i) {
+        const uint64_t b = 1ULL << (i & 63);
+        const int q = i >> 6;
+        w0 |= q == 0 ? b : 0ULL;
+        w1 |= q == 1 ? b : 0ULL;
+        w2 |= q == 2 ? b : 0ULL;
+        w3 |= q == 3 ? b : 0ULL;
+    }
+    __device__ __forceinline__ void load(const uint64_t* __restrict__ p) {
+        const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(p));
+        const ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2*>(p) + 1);
+        w0 |= a.x;
+        w1 |= a.y;
+        w2 |= b.x;
+        w3 |= b.y;
+    }
+    __device__ __forceinline__ uint64_t word(int q) const {
+        return q == 0 ? w0 : (q == 1 ? w1 : (q == 2 ? w2 : w3));
+    }
+    __device__ __forceinline__ bool operator==(const Mask4& o) const {
+        return w0 == o.w0 && w1 == o.w1 && w2 == o.w2 && w3 == o.w3;
+    }
+    __device__ __forceinline__ bool empty() const { return (w0 | w1 | w2 | w3) == 0; }
+};
+
+// Lowest m set bits of x (m < popcount(x)).
+__device__ __forceinline__ uint64_t keep_lowest64(uint64_t x, int m) {
+    const unsigned lo = (unsigned)x, hi = (unsigned)(x >> 32);
+    const int c = __popc(lo);
+    const int p = m < c ? nth_set_bit(lo, m) : 32 + nth_set_bit(hi, m - c);
+    return x & ((1ULL << p) - 1ULL);
+}
+
+__device__ __forceinline__ uint64_t lowest_word(uint64_t x, int& left) {
+    const int c = __popcll(x);
+    const uint64_t r = left <= 0 ? 0ULL : (c > left ? keep_lowest64(x, left) : x);
+    left -= c;
+    return r;
+}
+
+// Keep the lowest k set bits of the mask.
+__device__ __forceinline__ void mask_lowest(Mask4& m, int k) {
+    int left = k;
+    m.w0 = lowest_word(m.w0, left);
+    m.w1 = lowest_word(m.w1, left);
+    m.w2 = lowest_word(m.w2, left);
+    m.w3 = lowest_word(m.w3, left);
+}
+
+// Index of the j-th set bit (0-based) of the mask; j < popcount.
+__device__ __forceinline__ int mask_nth(const Mask4& m, int j) {
+    const int c0 = __popcll(m.w0), c1 = __popcll(m.w1), c2 = __popcll(m.w2);
+    int q = 0;
+    uint64_t x = m.w0;
+    if (j >= c0) { j -= c0; q = 1; x = m.w1;
+        if (j >= c1) { j -= c1; q = 2; x = m.w2;
+            if (j >= c2) { j -= c2; q = 3; x = m.w3; } } }
+    const unsigned lo = (unsigned)x;
+    const int c = __popc(lo);
+    const int p = j < c ? nth_set_bit(lo, j) : 32 + nth_set_bit((unsigned)(x >> 32), j - c);
+    return q * 64 + p;
+}
+
+// Position of rank x in the ascending table U (x must be an entry).
+__device__ __forceinline__ int u_index(const uint64_t* sU, uint64_t x) {
+    int pos = 0;
+#pragma unroll
+    for (int s = kUW / 2; s > 0; s >>= 1)
+        if (sU[pos + s - 1] < x) pos += s;
+    return pos;
+}
+
+template <int G>
+__device__ __forceinline__ void grp_or(const Grp<G>& g, Mask4& m) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        m.w0 |= g.shfl_xor(m.w0, o);
+        m.w1 |= g.shfl_xor(m.w1, o);
+        m.w2 |= g.shfl_xor(m.w2, o);
+        m.w3 |= g.shfl_xor(m.w3, o);
+    }
+}
+
+// Mask of the entries (one per lane, kEmpty = none) that are <= ulim.
+template <int G>
+__device__ __forceinline__ Mask4 grp_mask_of(const Grp<G>& g, const uint64_t* sU, uint64_t ulim, uint64_t x) {
+    Mask4 m;
+    if (x <= ulim) m.set(u_index(sU, x));
+    grp_or(g, m);
+    return m;
+}
+
+// Saturated merge: OR of the delta masks of the neighbours in [e0, e1) that
+// gained entries at the previous hop (lane-parallel, then reduced).
+template <int G>
+__device__ __forceinline__ Mask4 gather_masks(const Grp<G>& g, const int32_t* __restrict__ cols, int64_t e0,
+                                              int64_t e1, const uint8_t* __restrict__ Dcp,
+                                              const uint64_t* __restrict__ DMp, unsigned long long& cand) {
+    Mask4 acc;
+    for (int64_t e = e0 + g.l; e < e1; e += G) {
+        const int32_t u = __ldg(&cols[e]);
+        if (__ldg(&Dcp[u]) > 0) {
+            acc.load(DMp + (int64_t)u * 4);
+            cand += 4;
+        }
+    }
+    grp_or(g, acc);
+    return acc;
+}
+
+// Sketch lanes of a saturated mask: lane j < k holds U[j-th set bit].
+template <int G>
+__device__ __forceinline__ uint64_t mask_lanes(const Grp<G>& g, int k, const uint64_t* sU, const Mask4& m) {
+    return g.l < k ? sU[mask_nth(m, g.l)] : kEmpty;
+}
+
+__device__ __forceinline__ void load_u(uint64_t* sU, const uint64_t* __restrict__ U) {
+    for (int i = threadIdx.x; i < kUW; i += blockDim.x) sU[i] = U[i];
+    __syncthreads();
+}
+
 // Per-group counters accumulated in registers and flushed once per group.
 struct HopCounters {
     unsigned long long front = 0, merges = 0, cand = 0, merging = 0;
@@ -50,10 +183,19 @@ struct HopCounters {
 __global__ void k_rank_init(int64_t n, int k, uint64_t seed, uint64_t* __restrict__ S,
                             uint8_t* __restrict__ Scnt, uint64_t* __restrict__ D0, uint8_t* __restrict__ Dcnt0,
                             int32_t* __restrict__ stg_ent, StgGroup* __restrict__ stg_grp,
-                            int32_t* __restrict__ vg, int32_t* __restrict__ ve, Counters* ctr) {
+                            int32_t* __restrict__ vg, int32_t* __restrict__ ve, const uint64_t* __restrict__ U,
+                            uint64_t ulim, uint64_t* __restrict__ DM0, Counters* ctr) {
+    __shared__ uint64_t sU[kUW];
+    load_u(sU, U);
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         uint64_t r = vertex_rank(seed, v);
+        Mask4 m;
+        if (r <= ulim) m.set(u_index(sU, r));
+        DM0[v * 4 + 0] = m.w0;
+        DM0[v * 4 + 1] = m.w1;
+        DM0[v * 4 + 2] = m.w2;
+        DM0[v * 4 + 3] = m.w3;
         if (r == kEmpty) atomicOr(&ctr->error, 1ULL);
         S[v * k] = r;
         Scnt[v] = 1;
@@ -213,6 +355,7 @@ __device__ __forceinline__ void finish_vertex(const Grp<G>& g, int k, uint64_t s
                                               uint64_t* __restrict__ Dc, uint8_t* __restrict__ Dcc,
                                               int32_t* __restrict__ vg, int32_t* __restrict__ ve,
                                               int32_t* __restrict__ stg_ent, StgGroup* __restrict__ stg_grp,
+                                              const uint64_t* sU, uint64_t ulim, uint64_t* __restrict__ DMc,
                                               HopCounters& hc) {
     const bool valid = g.l < k && s.sk != kEmpty;
     const bool was_there = grp_member(g, old, s.sk);
@@ -229,6 +372,8 @@ __device__ __forceinline__ void finish_vertex(const Grp<G>& g, int k, uint64_t s
         Dc[(int64_t)v * k + g.l] = dv;
         stg_ent[slot * k + g.l] = (int32_t)rank_vertex(seed, dv);
     }
+    const Mask4 dm = grp_mask_of(g, sU, ulim, g.l < dcnt ? dv : kEmpty);
+    if (g.l < 4) DMc[(int64_t)v * 4 + g.l] = dm.word(g.l);
     const uint64_t kth = g.shfl(s.sk, k - 1);
     if (g.l == 0) {
         const int counted = cnt_new < k ? dcnt : __popc(newm & ((1u << (k - 1)) - 1u));
@@ -272,7 +417,10 @@ __global__ void __launch_bounds__(256) k_hop_vertices(
     const int32_t* __restrict__ cols, int k, uint64_t seed, int hop, uint64_t* __restrict__ S,
     uint8_t* __restrict__ Scnt, const uint64_t* __restrict__ Dp, const uint8_t* __restrict__ Dcp,
     uint64_t* __restrict__ Dc, uint8_t* __restrict__ Dcc, int32_t* __restrict__ vg, int32_t* __restrict__ ve,
-    int32_t* __restrict__ stg_ent, StgGroup* __restrict__ stg_grp, Counters* ctr) {
+    int32_t* __restrict__ stg_ent, StgGroup* __restrict__ stg_grp, const uint64_t* __restrict__ U, uint64_t ulim,
+    const uint64_t* __restrict__ DMp, uint64_t* __restrict__ DMc, Counters* ctr) {
+    __shared__ uint64_t sU[kUW];
+    load_u(sU, U);
     const Grp<G> g;
     const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
     HopCounters hc;
@@ -286,10 +434,30 @@ __global__ void __launch_bounds__(256) k_hop_vertices(
         s.tau_base = kEmpty;
         s.retau(g, k);
         const unsigned long long cand0 = hc.cand;
-        gather_range(g, k, hop, seed, cols, beg, end, Dcp, Dp, s, hc.cand);
-        const bool merged = hop == 1 || g.ballot(hc.cand != cand0) != 0;
-        if (g.l == 0 && merged) hc.merging += 1;
-        finish_vertex(g, k, seed, hop, v, end - beg, old, s, i, S, Scnt, Dc, Dcc, vg, ve, stg_ent, stg_grp, hc);
+        if (hop > 1 && s.cnt == k && s.tau <= ulim) {
+            // saturated: mask merge
+            const Mask4 own = grp_mask_of(g, sU, ulim, g.l < k ? old : kEmpty);
+            Mask4 m = gather_masks(g, cols, beg, end, Dcp, DMp, hc.cand);
+            m.w0 |= own.w0;
+            m.w1 |= own.w1;
+            m.w2 |= own.w2;
+            m.w3 |= own.w3;
+            mask_lowest(m, k);
+            const bool merged = g.ballot(hc.cand != cand0) != 0;  // every lane votes
+            if (g.l == 0 && merged) hc.merging += 1;
+            if (m == own) {
+                if (g.l == 0) stg_grp[i].info = 0;  // unchanged: empty slot
+                continue;
+            }
+            s.sk = mask_lanes(g, k, sU, m);
+            s.cnt = k;
+        } else {
+            gather_range(g, k, hop, seed, cols, beg, end, Dcp, Dp, s, hc.cand);
+            const bool merged = hop == 1 || g.ballot(hc.cand != cand0) != 0;
+            if (g.l == 0 && merged) hc.merging += 1;
+        }
+        finish_vertex(g, k, seed, hop, v, end - beg, old, s, i, S, Scnt, Dc, Dcc, vg, ve, stg_ent, stg_grp, sU, ulim,
+                      DMc, hc);
     }
     flush_counters(g, hc, ctr);
 }
@@ -301,7 +469,8 @@ __global__ void __launch_bounds__(256) k_hop_hub_segments(
     const int32_t* __restrict__ hubs, const int64_t* __restrict__ hub_seg, const int32_t* __restrict__ seg_hub,
     int64_t n_seg, const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols, int k, uint64_t seed,
     int hop, const uint64_t* __restrict__ S, const uint8_t* __restrict__ Scnt, const uint64_t* __restrict__ Dp,
-    const uint8_t* __restrict__ Dcp, uint64_t* __restrict__ part, Counters* ctr) {
+    const uint8_t* __restrict__ Dcp, uint64_t* __restrict__ part, uint64_t ulim, const uint64_t* __restrict__ DMp,
+    uint64_t* __restrict__ PM, Counters* ctr) {
     const Grp<G> g;
     const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
     HopCounters hc;
@@ -311,6 +480,12 @@ __global__ void __launch_bounds__(256) k_hop_hub_segments(
         const int64_t e0 = rowp[v] + (sidx - hub_seg[h]) * kSeg;
         const int64_t e1 = min(e0 + (int64_t)kSeg, rowp[v + 1]);
         const uint64_t kth_old = S[(int64_t)v * k + k - 1];
+        if (hop > 1 && Scnt[v] == k && kth_old <= ulim) {
+            // saturated hub: partial mask of the segment
+            const Mask4 m = gather_masks(g, cols, e0, e1, Dcp, DMp, hc.cand);
+            if (g.l < 4) PM[sidx * 4 + g.l] = m.word(g.l);
+            continue;
+        }
         Sketch<G> s;
         s.sk = kEmpty;
         s.cnt = 0;
@@ -329,7 +504,10 @@ __global__ void __launch_bounds__(256) k_hop_hubs(
     const uint64_t* __restrict__ part, const int64_t* __restrict__ rowp, int k, uint64_t seed, int hop,
     int64_t slot0, uint64_t* __restrict__ S, uint8_t* __restrict__ Scnt, uint64_t* __restrict__ Dc,
     uint8_t* __restrict__ Dcc, int32_t* __restrict__ vg, int32_t* __restrict__ ve, int32_t* __restrict__ stg_ent,
-    StgGroup* __restrict__ stg_grp, Counters* ctr) {
+    StgGroup* __restrict__ stg_grp, const uint64_t* __restrict__ U, uint64_t ulim, const uint64_t* __restrict__ PM,
+    uint64_t* __restrict__ DMc, Counters* ctr) {
+    __shared__ uint64_t sU[kUW];
+    load_u(sU, U);
     const Grp<G> g;
     const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
     HopCounters hc;
@@ -341,6 +519,28 @@ __global__ void __launch_bounds__(256) k_hop_hubs(
         s.cnt = Scnt[v];
         s.tau_base = kEmpty;
         s.retau(g, k);
+        if (hop > 1 && s.cnt == k && s.tau <= ulim) {
+            // saturated hub: OR of the segments' partial masks
+            const Mask4 own = grp_mask_of(g, sU, ulim, g.l < k ? old : kEmpty);
+            Mask4 m;
+            for (int64_t sidx = hub_seg[h] + g.l; sidx < hub_seg[h + 1]; sidx += G) m.load(PM + sidx * 4);
+            grp_or(g, m);
+            if (g.l == 0 && !m.empty()) hc.merging += 1;
+            m.w0 |= own.w0;
+            m.w1 |= own.w1;
+            m.w2 |= own.w2;
+            m.w3 |= own.w3;
+            mask_lowest(m, k);
+            if (m == own) {
+                if (g.l == 0) stg_grp[slot0 + h].info = 0;  // unchanged: empty slot
+                continue;
+            }
+            s.sk = mask_lanes(g, k, sU, m);
+            s.cnt = k;
+            finish_vertex(g, k, seed, hop, v, rowp[v + 1] - rowp[v], old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve,
+                          stg_ent, stg_grp, sU, ulim, DMc, hc);
+            continue;
+        }
         bool any = false;
         for (int64_t sidx = hub_seg[h]; sidx < hub_seg[h + 1]; ++sidx) {
             const uint64_t x = g.l < k ? part[sidx * k + g.l] : kEmpty;
@@ -349,7 +549,7 @@ __global__ void __launch_bounds__(256) k_hop_hubs(
         }
         if (g.l == 0 && any) hc.merging += 1;
         finish_vertex(g, k, seed, hop, v, rowp[v + 1] - rowp[v], old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve,
-                      stg_ent, stg_grp, hc);
+                      stg_ent, stg_grp, sU, ulim, DMc, hc);
     }
     flush_counters(g, hc, ctr);
 }
@@ -505,6 +705,90 @@ int build_work_lists(fl_graph* g) {
     return rc;
 }
 
+// ------------------------------------------------------------------ small-rank table
+
+constexpr int kSelCap = 4096;  // candidates sorted in one block
+
+// Ranks below T -> buf (first kSelCap of them); their number -> *cnt.
+__global__ void k_small_ranks(int64_t n, uint64_t seed, uint64_t T, uint64_t* __restrict__ buf,
+                              unsigned long long* __restrict__ cnt) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t v = base + lane_id();
+        const uint64_t r = v < n ? vertex_rank(seed, v) : kEmpty;
+        const long long at = warp_append(v < n && r < T, cnt);
+        if (at >= 0 && at < kSelCap) buf[at] = r;
+    }
+}
+
+// Sort the m <= kSelCap candidates (bitonic, one block) and keep the w smallest.
+__global__ void __launch_bounds__(1024) k_sort_small(const uint64_t* __restrict__ buf, int m, int w,
+                                                     uint64_t* __restrict__ U) {
+    __shared__ uint64_t a[kSelCap];
+    for (int i = threadIdx.x; i < kSelCap; i += blockDim.x) a[i] = i < m ? buf[i] : kEmpty;
+    __syncthreads();
+    for (int size = 2; size <= kSelCap; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < kSelCap; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool asc = (i & size) == 0;
+                    const uint64_t x = a[i], y = a[j];
+                    if ((x > y) == asc) {
+                        a[i] = y;
+                        a[j] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < kUW; i += blockDim.x) U[i] = i < w ? a[i] : kEmpty;
+}
+
+// U = the min(kUW, n) smallest vertex ranks: collect the ranks below a
+// threshold expected to pass about 1024 of them (ranks are uniform), widen or
+// narrow it until between min(kUW, n) and kSelCap pass, then sort them.
+static int select_small_ranks(fl_graph* g) {
+    const int64_t n = g->n;
+    cudaStream_t st = g->stream;
+    const int w = (int)std::min<int64_t>(kUW, n);
+    DBuf buf;
+    FL_TRY(dalloc(buf, (size_t)kSelCap * 8 + 256));
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(buf.as<char>() + (size_t)kSelCap * 8);
+    uint64_t T = n <= kSelCap / 2 ? kEmpty : (kEmpty / (uint64_t)n) * 1024ULL;
+    unsigned long long c = 0;
+    int rc = FL_OK;
+    for (int it = 0;; ++it) {
+        if (it > 130) { rc = FL_ECUDA; set_error(rc, "small-rank selection did not converge"); break; }
+        cudaError_t e = cudaMemsetAsync(cnt, 0, 8, st);
+        if (e != cudaSuccess) { rc = status_of(e, "small ranks", __FILE__, __LINE__); break; }
+        FL_LAUNCH(kProfSketchOther, k_small_ranks<<<grid_for(n, 256), 256, 0, st>>>(n, g->seed, T, buf.as<uint64_t>(),
+                                                                                   cnt));
+        e = cudaMemcpyAsync(&c, cnt, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { rc = status_of(e, "small ranks", __FILE__, __LINE__); break; }
+        if ((int64_t)c < w) {
+            T = T > kEmpty / 2 ? kEmpty : T * 2;
+            continue;
+        }
+        if (c > (unsigned long long)kSelCap) {
+            T = T / 4 * 3;
+            continue;
+        }
+        break;
+    }
+    if (rc == FL_OK) {
+        FL_LAUNCH(kProfSketchOther, k_sort_small<<<1, 1024, 0, st>>>(buf.as<uint64_t>(), (int)c, w,
+                                                                     g->U.as<uint64_t>()));
+        cudaError_t e = cudaMemcpyAsync(&g->ulim, g->U.as<uint64_t>() + (w - 1), 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = status_of(e, "small ranks", __FILE__, __LINE__);
+    }
+    dfree(buf);
+    return rc;
+}
+
 // ------------------------------------------------------------------ driver
 
 template <int G>
@@ -521,19 +805,22 @@ static int launch_hop(fl_graph* g, int hop, const int32_t* list, int64_t n_list,
                                         g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[pin].as<uint64_t>(),
                                         g->Dcnt[pin].as<uint8_t>(), g->D[pout].as<uint64_t>(),
                                         g->Dcnt[pout].as<uint8_t>(), g->vg.as<int32_t>(), g->ve.as<int32_t>(), ent,
-                                        grp, g->ctr.as<Counters>()));
+                                        grp, g->U.as<uint64_t>(), g->ulim, g->DM[pin].as<uint64_t>(),
+                                        g->DM[pout].as<uint64_t>(), g->ctr.as<Counters>()));
     if (g->n_hubs > 0) {
         FL_LAUNCH(kProfSketchMerge, k_hop_hub_segments<G><<<grid_for(g->n_seg, per_block), 256, 0, st>>>(
                                         g->hub_list.as<int32_t>(), g->hub_seg.as<int64_t>(), g->seg_hub.as<int32_t>(),
                                         g->n_seg, g->rowp.as<int64_t>(), g->cols.as<int32_t>(), k, g->seed, hop,
                                         g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[pin].as<uint64_t>(),
-                                        g->Dcnt[pin].as<uint8_t>(), g->part.as<uint64_t>(), g->ctr.as<Counters>()));
+                                        g->Dcnt[pin].as<uint8_t>(), g->part.as<uint64_t>(), g->ulim,
+                                        g->DM[pin].as<uint64_t>(), g->PM.as<uint64_t>(), g->ctr.as<Counters>()));
         FL_LAUNCH(kProfSketchMerge, k_hop_hubs<G><<<grid_for(g->n_hubs, per_block), 256, 0, st>>>(
                                         g->hub_list.as<int32_t>(), g->n_hubs, g->hub_seg.as<int64_t>(),
                                         g->part.as<uint64_t>(), g->rowp.as<int64_t>(), k, g->seed, hop, n_list,
                                         g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[pout].as<uint64_t>(),
                                         g->Dcnt[pout].as<uint8_t>(), g->vg.as<int32_t>(), g->ve.as<int32_t>(), ent,
-                                        grp, g->ctr.as<Counters>()));
+                                        grp, g->U.as<uint64_t>(), g->ulim, g->PM.as<uint64_t>(),
+                                        g->DM[pout].as<uint64_t>(), g->ctr.as<Counters>()));
     }
     FL_CUDA(cudaGetLastError());
     return FL_OK;
@@ -562,6 +849,10 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     FL_TRY(dalloc(g->vg, (size_t)n * 4));
     FL_TRY(dalloc(g->ve, (size_t)n * 4));
     FL_TRY(dalloc(g->part, (size_t)std::max<int64_t>(g->n_seg, 1) * k * 8));
+    FL_TRY(dalloc(g->U, (size_t)kUW * 8));
+    FL_TRY(dalloc(g->DM[0], (size_t)n * 32));
+    FL_TRY(dalloc(g->DM[1], (size_t)n * 32));
+    FL_TRY(dalloc(g->PM, (size_t)std::max<int64_t>(g->n_seg, 1) * 32));
     // staging: slots 0..n-1 for hop 0, then one slot per work item of each hop
     const int64_t per_dense = g->n_low + g->n_hubs;
     size_t slot_cap = (size_t)n + (size_t)per_dense * 8 + 1024;
@@ -578,10 +869,18 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     FL_CUDA(cudaMemsetAsync(g->S.p, 0xff, nk * 8, st));
     FL_CUDA(cudaMemsetAsync(g->stamp.p, 0, (size_t)n * 4, st));
     FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st));
+    {
+        int rc0 = select_small_ranks(g);
+        if (rc0 != FL_OK) {
+            dfree(act);
+            return rc0;
+        }
+    }
     FL_LAUNCH(kProfSketchOther, k_rank_init<<<grid_for(n, 256), 256, 0, st>>>(
                                     n, k, seed, g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[0].as<uint64_t>(),
                                     g->Dcnt[0].as<uint8_t>(), g->stg_ent.as<int32_t>(), g->stg_grp.as<StgGroup>(),
-                                    g->vg.as<int32_t>(), g->ve.as<int32_t>(), g->ctr.as<Counters>()));
+                                    g->vg.as<int32_t>(), g->ve.as<int32_t>(), g->U.as<uint64_t>(), g->ulim,
+                                    g->DM[0].as<uint64_t>(), g->ctr.as<Counters>()));
     FL_CUDA(cudaGetLastError());
     FL_TRY(read_counters(g));
     if (g->h_ctr->error) {
