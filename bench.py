@@ -271,6 +271,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     prof = {name: g.profile_query(name) for name in fl.PROF_CLASSES}
     launches = g.profile_query(-1)["launches"]
+    hop_detail = [{"hop": h["hop"], "ms": round(h["ms"], 3), "scanned": h["scanned"],
+                   "mask_share": round(h["mask"] / h["scanned"], 4) if h["scanned"] else 0.0,
+                   "changed": h["changed"]} for h in g.hop_stats()]
     g.profile(False)
     merges_step = stats["edge_merges"]
     value = world * merges_step * args.steps / (ms / 1e3)
@@ -343,7 +346,7 @@ def run_gpu(args):
             "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
             "hops": stats["hops"], "edge_merges_per_step": merges_step, "ads_entries": stats["ads_entries"],
             "n_open": info.get("n_open"), "objective": info.get("objective"),
-            "mis_rounds": info.get("mis", {}).get("mis_rounds")}
+            "mis_rounds": info.get("mis", {}).get("mis_rounds"), "hop_detail": hop_detail}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -210,6 +210,24 @@ int fl_profile_reset(fl_graph* g);
 int fl_profile_query(const fl_graph* g, int kernel_class, int64_t* launches, double* ms, double* alg_bytes);
 
 /*
+ * fl_hop_stats -- per-hop counters of the last build (Alg. 2): the hops
+ * 1..H* that changed some sketch and the final hop H*+1 that changed none.
+ *   n_hops        set to the number of processed hops, H* + 1 (entries
+ *                 written: min(n_hops, cap)).
+ *   changed[h-1]  vertices whose sketch changed at hop h.
+ * When profiling was on (fl_profile_enable) during the build, also:
+ *   scanned[h-1]  CSR entries read at hop h (neighbours of the processed
+ *                 vertices, hub segments included), else 0;
+ *   mask[h-1]     of those, entries read by the mask merge of saturated
+ *                 sketches (full sketches whose k-th rank is among the 1024
+ *                 smallest ranks of the graph), else 0;
+ *   ms[h-1]       kernel milliseconds of hop h, else 0.
+ * Host arrays of cap entries; any of them may be NULL.
+ */
+int fl_hop_stats(const fl_graph* g, int64_t cap, int64_t* n_hops, int64_t* scanned, int64_t* mask,
+                 int64_t* changed, double* ms);
+
+/*
  * fl_assign_nearest_noalloc -- nearest open facility of every vertex without
  * any device allocation.  (The paper has no counterpart: this is a deployment
  * variant of fl_assign_clients for callers that cannot let a library call

@@ -27,7 +27,7 @@ EXPORTS = ("fl_graph_create", "fl_graph_destroy", "fl_build_sketches", "fl_sketc
            "fl_export_sketches", "fl_export_ads", "fl_solve_create", "fl_solve_destroy",
            "fl_compute_radii", "fl_open_facilities", "fl_assign_clients", "fl_objective",
            "fl_solve_stats", "fl_status_str", "fl_last_error", "fl_profile_enable", "fl_profile_reset",
-           "fl_profile_query", "fl_assign_nearest_noalloc")
+           "fl_profile_query", "fl_hop_stats", "fl_assign_nearest_noalloc")
 
 PROF_CLASSES = {"sketch_merge": 0, "sketch_expand": 1, "sketch_other": 2, "radius": 3, "keys": 4,
                 "mis": 5, "bfs": 6, "other": 7}
@@ -75,6 +75,7 @@ def load(build_if_missing: bool = True):
             "fl_profile_enable": ([vp, ci], ci),
             "fl_profile_reset": ([vp], ci),
             "fl_profile_query": ([vp, ci, P64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ci),
+            "fl_hop_stats": ([vp, i64, P64, vp, vp, vp, vp], ci),
             "fl_assign_nearest_noalloc": ([i64, vp, vp, i64, vp, vp, vp, vp], ci),
         }
         for name, (args, res) in sig.items():
@@ -162,6 +163,21 @@ class Graph:
         v = [ctypes.c_int64() for _ in range(4)]
         _check(self._lib.fl_sketch_stats(self._h, *[ctypes.byref(x) for x in v]))
         return dict(hops=v[0].value, edge_merges=v[1].value, ads_entries=v[2].value, ads_groups=v[3].value)
+
+    def hop_stats(self) -> list:
+        """Per processed hop of the last build (the last one changed no sketch):
+        vertices changed; CSR entries scanned, of them by the mask merge, and
+        kernel ms (these three 0 unless profiling was on)."""
+        H = ctypes.c_int64()
+        _check(self._lib.fl_hop_stats(self._h, 0, ctypes.byref(H), None, None, None, None))
+        h = H.value
+        sc, mk, ch = (np.zeros(h, np.int64) for _ in range(3))
+        ms = np.zeros(h, np.float64)
+        _check(self._lib.fl_hop_stats(self._h, h, ctypes.byref(H), sc.ctypes.data_as(ctypes.c_void_p),
+                                      mk.ctypes.data_as(ctypes.c_void_p), ch.ctypes.data_as(ctypes.c_void_p),
+                                      ms.ctypes.data_as(ctypes.c_void_p)))
+        return [dict(hop=i + 1, scanned=int(sc[i]), mask=int(mk[i]), changed=int(ch[i]), ms=float(ms[i]))
+                for i in range(h)]
 
     def profile(self, on: bool = True):
         _check(self._lib.fl_profile_enable(self._h, 1 if on else 0))

@@ -37,6 +37,8 @@ void destroy_graph(fl_graph* g) {
                     &g->relax_aux, &g->U, &g->DM[0], &g->DM[1], &g->PM};
     for (DBuf* b : bufs) dfree(*b);
     for (cudaEvent_t e : g->prof.ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : g->hop_ev)
+        if (e) cudaEventDestroy(e);
     if (g->h_ctr) cudaFreeHost(g->h_ctr);
     delete g;
 }
@@ -146,6 +148,22 @@ int fl_sketch_stats(const fl_graph* g, int64_t* hops, int64_t* edge_merges, int6
     if (edge_merges) *edge_merges = g->edge_merges;
     if (ads_entries) *ads_entries = g->n_entries;
     if (ads_groups) *ads_groups = g->n_groups;
+    return FL_OK;
+}
+
+int fl_hop_stats(const fl_graph* g, int64_t cap, int64_t* n_hops, int64_t* scanned, int64_t* mask,
+                 int64_t* changed, double* ms) {
+    if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    if (!g->built) FL_FAIL(FL_ESTATE, "sketches not built");
+    if (cap < 0) FL_FAIL(FL_EINVAL, "negative capacity");
+    const int64_t H = (int64_t)g->hop_scanned.size();
+    if (n_hops) *n_hops = H;
+    for (int64_t i = 0; i < std::min(H, cap); ++i) {
+        if (scanned) scanned[i] = g->hop_scanned[i];
+        if (mask) mask[i] = g->hop_mask[i];
+        if (changed) changed[i] = g->hop_changed[i];
+        if (ms) ms[i] = g->hop_ms[i];
+    }
     return FL_OK;
 }
 

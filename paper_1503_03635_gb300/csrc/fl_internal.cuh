@@ -100,7 +100,9 @@ constexpr int kHubDeg = 2048;
 constexpr int kSeg = 2048;
 // Width of the small-rank universe of the sketch hops (the kUW smallest
 // ranks of a graph; a saturated sketch is a kUW-bit mask over them).
-constexpr int kUW = 256;
+constexpr int kUW = 1024;
+constexpr int kUSlices = kUW / 256;  // a mask is read and merged in 256-bit slices
+constexpr int kUWords = kUW / 64;
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
@@ -303,6 +305,8 @@ struct Counters {
     unsigned long long cand_reads;   // merge: neighbour-delta ranks read (sum of |D_{h-1}(u)| over frontier edges)
     unsigned long long merging;      // merge: vertices with at least one frontier neighbour
     unsigned long long aux3;
+    unsigned long long scanned;      // hop census: CSR entries read this hop
+    unsigned long long mask_scanned; // hop census: of those, read by the mask merge
 };
 
 // ----------------------------------------------------------------- profiling
@@ -361,8 +365,8 @@ struct fl_graph {
     fl::DBuf part;                 // uint64[n_seg*k]: partial bottom-k of each hub segment (scratch)
     fl::DBuf U;                    // uint64[kUW]: the kUW smallest ranks, ascending (kEmpty padded)
     uint64_t ulim = 0;             // largest entry of U
-    fl::DBuf DM[2];                // uint64[n*4]: hop delta masks over U
-    fl::DBuf PM;                   // uint64[n_seg*4]: partial masks of hub segments (scratch)
+    fl::DBuf DM[2];                // uint64[n*kUWords]: hop delta masks over U
+    fl::DBuf PM;                   // uint64[n_seg*kUWords]: partial masks of hub segments (scratch)
     // sketches
     int k = 0;
     uint64_t seed = 0;
@@ -389,6 +393,10 @@ struct fl_graph {
     fl::DBuf scratch;              // general scratch (scans, sorts)
     fl::DBuf relax_aux;            // bitmap, hub frontier tags/values, edge counter of the rounds
     fl::Prof prof;                 // launch counts and kernel timings
+    // per-hop counters of the last build (index h-1)
+    std::vector<int64_t> hop_scanned, hop_mask, hop_changed;
+    std::vector<double> hop_ms;
+    cudaEvent_t hop_ev[2] = {nullptr, nullptr};
 };
 
 struct fl_solve {

@@ -48,9 +48,11 @@ constexpr int kMaxHops = 65535;
 // S_h(v) = lowest k bits of (S_{h-1}(v) | OR_{u in N(v)} D_{h-1}(u)), with
 // D_{h-1}(u) kept as a mask beside its list.  Candidates above U[last] are
 // above the k-th rank and drop out either way, so the mask update is the
-// list merge exactly.
+// list merge exactly.  Masks are merged in 256-bit slices from the smallest
+// ranks up, stopping once k bits are kept: a sketch whose k-th rank lies in
+// the first slice reads 32 bytes per neighbour.
 
-struct Mask4 {
+struct Mask4 {  // one 256-bit slice
     uint64_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
     __device__ __forceinline__ void set(int i) {
         const uint64_t b = 1ULL << (i & 63);
@@ -68,6 +70,12 @@ struct Mask4 {
         w2 |= b.x;
         w3 |= b.y;
     }
+    __device__ __forceinline__ void add(const Mask4& o) {
+        w0 |= o.w0;
+        w1 |= o.w1;
+        w2 |= o.w2;
+        w3 |= o.w3;
+    }
     __device__ __forceinline__ uint64_t word(int q) const {
         return q == 0 ? w0 : (q == 1 ? w1 : (q == 2 ? w2 : w3));
     }
@@ -75,6 +83,9 @@ struct Mask4 {
         return w0 == o.w0 && w1 == o.w1 && w2 == o.w2 && w3 == o.w3;
     }
     __device__ __forceinline__ bool empty() const { return (w0 | w1 | w2 | w3) == 0; }
+    __device__ __forceinline__ int count() const {
+        return __popcll(w0) + __popcll(w1) + __popcll(w2) + __popcll(w3);
+    }
 };
 
 // Lowest m set bits of x (m < popcount(x)).
@@ -92,7 +103,7 @@ __device__ __forceinline__ uint64_t lowest_word(uint64_t x, int& left) {
     return r;
 }
 
-// Keep the lowest k set bits of the mask.
+// Keep the lowest k set bits of the slice.
 __device__ __forceinline__ void mask_lowest(Mask4& m, int k) {
     int left = k;
     m.w0 = lowest_word(m.w0, left);
@@ -101,7 +112,7 @@ __device__ __forceinline__ void mask_lowest(Mask4& m, int k) {
     m.w3 = lowest_word(m.w3, left);
 }
 
-// Index of the j-th set bit (0-based) of the mask; j < popcount.
+// Index of the j-th set bit (0-based) of the slice; j < count().
 __device__ __forceinline__ int mask_nth(const Mask4& m, int j) {
     const int c0 = __popcll(m.w0), c1 = __popcll(m.w1), c2 = __popcll(m.w2);
     int q = 0;
@@ -115,8 +126,9 @@ __device__ __forceinline__ int mask_nth(const Mask4& m, int j) {
     return q * 64 + p;
 }
 
-// Position of rank x in the ascending table U (x must be an entry).
-__device__ __forceinline__ int u_index(const uint64_t* sU, uint64_t x) {
+// Position of rank x in U (-1 when x > ulim: not an entry).
+__device__ __forceinline__ int u_pos(const uint64_t* sU, uint64_t ulim, uint64_t x) {
+    if (x > ulim) return -1;
     int pos = 0;
 #pragma unroll
     for (int s = kUW / 2; s > 0; s >>= 1)
@@ -135,37 +147,59 @@ __device__ __forceinline__ void grp_or(const Grp<G>& g, Mask4& m) {
     }
 }
 
-// Mask of the entries (one per lane, kEmpty = none) that are <= ulim.
+// Slice q of the mask of the lanes' U positions (-1 = none).
 template <int G>
-__device__ __forceinline__ Mask4 grp_mask_of(const Grp<G>& g, const uint64_t* sU, uint64_t ulim, uint64_t x) {
+__device__ __forceinline__ Mask4 slice_mask(const Grp<G>& g, int idx, int q) {
     Mask4 m;
-    if (x <= ulim) m.set(u_index(sU, x));
+    if (idx >= 0 && (idx >> 8) == q) m.set(idx & 255);
     grp_or(g, m);
     return m;
 }
 
-// Saturated merge: OR of the delta masks of the neighbours in [e0, e1) that
-// gained entries at the previous hop (lane-parallel, then reduced).
+// Slice q of the OR of the delta masks of the neighbours in [e0, e1) that
+// gained entries at the previous hop (lane-parallel, two loads in flight per
+// lane, then reduced over the group).
 template <int G>
 __device__ __forceinline__ Mask4 gather_masks(const Grp<G>& g, const int32_t* __restrict__ cols, int64_t e0,
                                               int64_t e1, const uint8_t* __restrict__ Dcp,
-                                              const uint64_t* __restrict__ DMp, unsigned long long& cand) {
+                                              const uint64_t* __restrict__ DMp, int q, unsigned long long& cand) {
     Mask4 acc;
-    for (int64_t e = e0 + g.l; e < e1; e += G) {
-        const int32_t u = __ldg(&cols[e]);
-        if (__ldg(&Dcp[u]) > 0) {
-            acc.load(DMp + (int64_t)u * 4);
-            cand += 4;
-        }
+    for (int64_t e = e0 + g.l; e < e1; e += 2 * G) {
+        const bool in1 = e + G < e1;
+        const int32_t u0 = __ldg(&cols[e]);
+        const int32_t u1 = in1 ? __ldg(&cols[e + G]) : 0;
+        const bool c0 = __ldg(&Dcp[u0]) > 0;
+        const bool c1 = in1 && __ldg(&Dcp[u1]) > 0;
+        if (c0) acc.load(DMp + (int64_t)u0 * kUWords + q * 4);
+        if (c1) acc.load(DMp + (int64_t)u1 * kUWords + q * 4);
+        cand += (c0 ? 4ULL : 0ULL) + (c1 ? 4ULL : 0ULL);
     }
     grp_or(g, acc);
     return acc;
 }
 
-// Sketch lanes of a saturated mask: lane j < k holds U[j-th set bit].
-template <int G>
-__device__ __forceinline__ uint64_t mask_lanes(const Grp<G>& g, int k, const uint64_t* sU, const Mask4& m) {
-    return g.l < k ? sU[mask_nth(m, g.l)] : kEmpty;
+// Saturated merge, slice by slice from the smallest ranks: src(q) gives the
+// OR of the candidates' slice q; idx is the lane's old entry's U position.
+// Lanes j < k receive the new sketch in sk_new; returns whether it changed.
+template <int G, class Src>
+__device__ __forceinline__ bool merge_slices(const Grp<G>& g, int k, const uint64_t* sU, int idx, Src src,
+                                             uint64_t& sk_new) {
+    int left = k, base = 0, own_seen = 0;
+    bool changed = false;
+    sk_new = kEmpty;
+    for (int q = 0; q < kUSlices && left > 0; ++q) {
+        const Mask4 own = slice_mask(g, idx, q);
+        Mask4 m = src(q);
+        m.add(own);
+        mask_lowest(m, left);
+        changed |= !(m == own);
+        own_seen += own.count();
+        const int c = m.count();
+        if (g.l >= base && g.l < base + c) sk_new = sU[q * 256 + mask_nth(m, g.l - base)];
+        base += c;
+        left -= c;
+    }
+    return changed || own_seen < k;
 }
 
 __device__ __forceinline__ void load_u(uint64_t* sU, const uint64_t* __restrict__ U) {
@@ -173,10 +207,30 @@ __device__ __forceinline__ void load_u(uint64_t* sU, const uint64_t* __restrict_
     __syncthreads();
 }
 
-// Per-group counters accumulated in registers and flushed once per group.
+// Per-group hop counters in shared memory, one slot per group, updated by
+// the group's lane 0 without atomics and flushed once at the end of a kernel
+// (the hop kernels run at the register limit; counters in registers cost
+// spills in the merge loops).  32-bit: a group adds at most kHubDeg per
+// vertex it processes (hub degrees go to the global counter directly) and,
+// with the grids of the hop kernels, processes at most 2^31 / 77824 work
+// items.
+enum { kCFront, kCMerges, kCMerging, kNCtr };
+__shared__ unsigned s_hop_ctr[256 / 16][kNCtr];
+
 struct HopCounters {
-    unsigned long long front = 0, merges = 0, cand = 0, merging = 0;
+    unsigned long long cand = 0;  // per lane: neighbour-delta words read
 };
+
+template <int G>
+__device__ __forceinline__ void hop_ctr_init(const Grp<G>& g) {
+    if (g.l == 0)
+        for (int i = 0; i < kNCtr; ++i) s_hop_ctr[threadIdx.x / G][i] = 0;
+}
+// lane 0 of the group only
+template <int G>
+__device__ __forceinline__ void hop_ctr_add(int field, unsigned x) {
+    s_hop_ctr[threadIdx.x / G][field] += x;
+}
 
 // ------------------------------------------------------------------ hop 0
 
@@ -190,12 +244,10 @@ __global__ void k_rank_init(int64_t n, int k, uint64_t seed, uint64_t* __restric
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         uint64_t r = vertex_rank(seed, v);
-        Mask4 m;
-        if (r <= ulim) m.set(u_index(sU, r));
-        DM0[v * 4 + 0] = m.w0;
-        DM0[v * 4 + 1] = m.w1;
-        DM0[v * 4 + 2] = m.w2;
-        DM0[v * 4 + 3] = m.w3;
+        const int ri = u_pos(sU, ulim, r);
+#pragma unroll
+        for (int w = 0; w < kUWords; ++w)
+            DM0[v * kUWords + w] = (ri >= 0 && (ri >> 6) == w) ? 1ULL << (ri & 63) : 0ULL;
         if (r == kEmpty) atomicOr(&ctr->error, 1ULL);
         S[v * k] = r;
         Scnt[v] = 1;
@@ -347,9 +399,10 @@ __device__ __forceinline__ void gather_range(const Grp<G>& g, int k, int hop, ui
 }
 
 // Write the results of vertex v after its merge: new sketch, the entries it
-// gained (for the next hop) and its staged ADS group in work slot `slot`.
+// gained (for the next hop), their mask and its staged ADS group in work slot
+// `slot`.  Returns whether the sketch changed.
 template <int G>
-__device__ __forceinline__ void finish_vertex(const Grp<G>& g, int k, uint64_t seed, int hop, int32_t v,
+__device__ __forceinline__ bool finish_vertex(const Grp<G>& g, int k, uint64_t seed, int hop, int32_t v,
                                               int64_t deg, uint64_t old, const Sketch<G>& s, int64_t slot,
                                               uint64_t* __restrict__ S, uint8_t* __restrict__ Scnt,
                                               uint64_t* __restrict__ Dc, uint8_t* __restrict__ Dcc,
@@ -363,7 +416,7 @@ __device__ __forceinline__ void finish_vertex(const Grp<G>& g, int k, uint64_t s
     const int dcnt = __popc(newm);
     if (dcnt == 0) {
         if (g.l == 0) stg_grp[slot].info = 0;  // empty slot
-        return;
+        return false;
     }
     const int cnt_new = __popc(g.ballot(valid));
     if (g.l < k) S[(int64_t)v * k + g.l] = s.sk;
@@ -372,8 +425,16 @@ __device__ __forceinline__ void finish_vertex(const Grp<G>& g, int k, uint64_t s
         Dc[(int64_t)v * k + g.l] = dv;
         stg_ent[slot * k + g.l] = (int32_t)rank_vertex(seed, dv);
     }
-    const Mask4 dm = grp_mask_of(g, sU, ulim, g.l < dcnt ? dv : kEmpty);
-    if (g.l < 4) DMc[(int64_t)v * 4 + g.l] = dm.word(g.l);
+    {
+        // delta mask over U: lane w < kUWords builds word w
+        const int di = g.l < dcnt ? u_pos(sU, ulim, dv) : -1;
+        uint64_t word = 0;
+        for (int j = 0; j < dcnt; ++j) {
+            const int ij = g.shfl(di, j);
+            if (ij >= 0 && (ij >> 6) == g.l) word |= 1ULL << (ij & 63);
+        }
+        if (g.l < kUWords) DMc[(int64_t)v * kUWords + g.l] = word;
+    }
     const uint64_t kth = g.shfl(s.sk, k - 1);
     if (g.l == 0) {
         const int counted = cnt_new < k ? dcnt : __popc(newm & ((1u << (k - 1)) - 1u));
@@ -390,9 +451,10 @@ __device__ __forceinline__ void finish_vertex(const Grp<G>& g, int k, uint64_t s
         vg[v] = gr.gidx + 1;
         ve[v] = gr.eidx + dcnt;
         stg_grp[slot] = gr;
-        hc.front += 1;
-        hc.merges += (unsigned long long)deg;
+        hop_ctr_add<G>(kCFront, 1u);
+        if (deg <= kHubDeg) hop_ctr_add<G>(kCMerges, (unsigned)deg);
     }
+    return true;
 }
 
 template <int G>
@@ -401,10 +463,11 @@ __device__ __forceinline__ void flush_counters(const Grp<G>& g, HopCounters hc, 
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) hc.cand += g.shfl_xor(hc.cand, o);
     if (g.l == 0) {
-        if (hc.front) atomicAdd(&ctr->frontier, hc.front);
-        if (hc.merges) atomicAdd(&ctr->merges, hc.merges);
+        const unsigned* c = s_hop_ctr[threadIdx.x / G];
         if (hc.cand) atomicAdd(&ctr->cand_reads, hc.cand);
-        if (hc.merging) atomicAdd(&ctr->merging, hc.merging);
+        if (c[kCFront]) atomicAdd(&ctr->frontier, (unsigned long long)c[kCFront]);
+        if (c[kCMerges]) atomicAdd(&ctr->merges, (unsigned long long)c[kCMerges]);
+        if (c[kCMerging]) atomicAdd(&ctr->merging, (unsigned long long)c[kCMerging]);
     }
 }
 
@@ -424,6 +487,7 @@ __global__ void __launch_bounds__(256) k_hop_vertices(
     const Grp<G> g;
     const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
     HopCounters hc;
+    hop_ctr_init(g);
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; i < n_list; i += groups) {
         const int32_t v = list[i];
         const int64_t beg = rowp[v], end = rowp[v + 1];
@@ -434,27 +498,25 @@ __global__ void __launch_bounds__(256) k_hop_vertices(
         s.tau_base = kEmpty;
         s.retau(g, k);
         const unsigned long long cand0 = hc.cand;
-        if (hop > 1 && s.cnt == k && s.tau <= ulim) {
+        const bool sat = hop > 1 && s.cnt == k && s.tau <= ulim;
+        if (sat) {
             // saturated: mask merge
-            const Mask4 own = grp_mask_of(g, sU, ulim, g.l < k ? old : kEmpty);
-            Mask4 m = gather_masks(g, cols, beg, end, Dcp, DMp, hc.cand);
-            m.w0 |= own.w0;
-            m.w1 |= own.w1;
-            m.w2 |= own.w2;
-            m.w3 |= own.w3;
-            mask_lowest(m, k);
+            const int idx = g.l < k ? u_pos(sU, ulim, old) : -1;
+            uint64_t sk_new;
+            const bool changed = merge_slices(
+                g, k, sU, idx, [&](int q) { return gather_masks(g, cols, beg, end, Dcp, DMp, q, hc.cand); }, sk_new);
             const bool merged = g.ballot(hc.cand != cand0) != 0;  // every lane votes
-            if (g.l == 0 && merged) hc.merging += 1;
-            if (m == own) {
+            if (g.l == 0 && merged) hop_ctr_add<G>(kCMerging, 1u);
+            if (!changed) {
                 if (g.l == 0) stg_grp[i].info = 0;  // unchanged: empty slot
                 continue;
             }
-            s.sk = mask_lanes(g, k, sU, m);
+            s.sk = sk_new;
             s.cnt = k;
         } else {
             gather_range(g, k, hop, seed, cols, beg, end, Dcp, Dp, s, hc.cand);
             const bool merged = hop == 1 || g.ballot(hc.cand != cand0) != 0;
-            if (g.l == 0 && merged) hc.merging += 1;
+            if (g.l == 0 && merged) hop_ctr_add<G>(kCMerging, 1u);
         }
         finish_vertex(g, k, seed, hop, v, end - beg, old, s, i, S, Scnt, Dc, Dcc, vg, ve, stg_ent, stg_grp, sU, ulim,
                       DMc, hc);
@@ -469,21 +531,29 @@ __global__ void __launch_bounds__(256) k_hop_hub_segments(
     const int32_t* __restrict__ hubs, const int64_t* __restrict__ hub_seg, const int32_t* __restrict__ seg_hub,
     int64_t n_seg, const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols, int k, uint64_t seed,
     int hop, const uint64_t* __restrict__ S, const uint8_t* __restrict__ Scnt, const uint64_t* __restrict__ Dp,
-    const uint8_t* __restrict__ Dcp, uint64_t* __restrict__ part, uint64_t ulim, const uint64_t* __restrict__ DMp,
-    uint64_t* __restrict__ PM, Counters* ctr) {
+    const uint8_t* __restrict__ Dcp, uint64_t* __restrict__ part, const uint64_t* __restrict__ U, uint64_t ulim,
+    const uint64_t* __restrict__ DMp, uint64_t* __restrict__ PM, Counters* ctr) {
+    __shared__ uint64_t sU[kUW];
+    load_u(sU, U);
     const Grp<G> g;
     const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
     HopCounters hc;
+    hop_ctr_init(g);
     for (int64_t sidx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; sidx < n_seg; sidx += groups) {
         const int32_t h = seg_hub[sidx];
         const int32_t v = hubs[h];
         const int64_t e0 = rowp[v] + (sidx - hub_seg[h]) * kSeg;
         const int64_t e1 = min(e0 + (int64_t)kSeg, rowp[v + 1]);
         const uint64_t kth_old = S[(int64_t)v * k + k - 1];
-        if (hop > 1 && Scnt[v] == k && kth_old <= ulim) {
-            // saturated hub: partial mask of the segment
-            const Mask4 m = gather_masks(g, cols, e0, e1, Dcp, DMp, hc.cand);
-            if (g.l < 4) PM[sidx * 4 + g.l] = m.word(g.l);
+        const bool sat = hop > 1 && Scnt[v] == k && kth_old <= ulim;
+        if (sat) {
+            // saturated hub: partial masks of the segment, the slices up to
+            // the one holding the hub's k-th rank (the merge stops there)
+            const int top = u_pos(sU, ulim, kth_old) >> 8;
+            for (int q = 0; q <= top; ++q) {
+                const Mask4 m = gather_masks(g, cols, e0, e1, Dcp, DMp, q, hc.cand);
+                if (g.l < 4) PM[sidx * kUWords + q * 4 + g.l] = m.word(g.l);
+            }
             continue;
         }
         Sketch<G> s;
@@ -511,6 +581,7 @@ __global__ void __launch_bounds__(256) k_hop_hubs(
     const Grp<G> g;
     const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
     HopCounters hc;
+    hop_ctr_init(g);
     for (int64_t h = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; h < n_hubs; h += groups) {
         const int32_t v = hubs[h];
         const uint64_t old = g.l < k ? S[(int64_t)v * k + g.l] : kEmpty;
@@ -521,24 +592,32 @@ __global__ void __launch_bounds__(256) k_hop_hubs(
         s.retau(g, k);
         if (hop > 1 && s.cnt == k && s.tau <= ulim) {
             // saturated hub: OR of the segments' partial masks
-            const Mask4 own = grp_mask_of(g, sU, ulim, g.l < k ? old : kEmpty);
-            Mask4 m;
-            for (int64_t sidx = hub_seg[h] + g.l; sidx < hub_seg[h + 1]; sidx += G) m.load(PM + sidx * 4);
-            grp_or(g, m);
-            if (g.l == 0 && !m.empty()) hc.merging += 1;
-            m.w0 |= own.w0;
-            m.w1 |= own.w1;
-            m.w2 |= own.w2;
-            m.w3 |= own.w3;
-            mask_lowest(m, k);
-            if (m == own) {
+            const int idx = g.l < k ? u_pos(sU, ulim, old) : -1;
+            bool any = false;
+            uint64_t sk_new;
+            const bool changed = merge_slices(
+                g, k, sU, idx,
+                [&](int q) {
+                    Mask4 m;
+                    for (int64_t sidx = hub_seg[h] + g.l; sidx < hub_seg[h + 1]; sidx += G)
+                        m.load(PM + sidx * kUWords + q * 4);
+                    grp_or(g, m);
+                    any |= !m.empty();
+                    return m;
+                },
+                sk_new);
+            if (g.l == 0 && any) hop_ctr_add<G>(kCMerging, 1u);
+            if (!changed) {
                 if (g.l == 0) stg_grp[slot0 + h].info = 0;  // unchanged: empty slot
                 continue;
             }
-            s.sk = mask_lanes(g, k, sU, m);
+            s.sk = sk_new;
             s.cnt = k;
-            finish_vertex(g, k, seed, hop, v, rowp[v + 1] - rowp[v], old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve,
-                          stg_ent, stg_grp, sU, ulim, DMc, hc);
+            const int64_t deg = rowp[v + 1] - rowp[v];
+            if (finish_vertex(g, k, seed, hop, v, deg, old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve, stg_ent, stg_grp,
+                              sU, ulim, DMc, hc) &&
+                g.l == 0)
+                atomicAdd(&ctr->merges, (unsigned long long)deg);
             continue;
         }
         bool any = false;
@@ -547,9 +626,12 @@ __global__ void __launch_bounds__(256) k_hop_hubs(
             any |= g.ballot(x != kEmpty) != 0;
             absorb(g, k, x, s);
         }
-        if (g.l == 0 && any) hc.merging += 1;
-        finish_vertex(g, k, seed, hop, v, rowp[v + 1] - rowp[v], old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve,
-                      stg_ent, stg_grp, sU, ulim, DMc, hc);
+        if (g.l == 0 && any) hop_ctr_add<G>(kCMerging, 1u);
+        const int64_t deg = rowp[v + 1] - rowp[v];
+        if (finish_vertex(g, k, seed, hop, v, deg, old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve, stg_ent, stg_grp, sU,
+                          ulim, DMc, hc) &&
+            g.l == 0)
+            atomicAdd(&ctr->merges, (unsigned long long)deg);
     }
     flush_counters(g, hc, ctr);
 }
@@ -705,6 +787,31 @@ int build_work_lists(fl_graph* g) {
     return rc;
 }
 
+// Census of a hop's work list (profiling): CSR entries of the listed
+// vertices, and of those whose sketch is saturated (read by the mask merge).
+// Runs before the hop kernels change the sketches.
+__global__ void k_hop_census(const int32_t* __restrict__ list, int64_t n_list, const int64_t* __restrict__ rowp,
+                             const uint64_t* __restrict__ S, const uint8_t* __restrict__ Scnt, int k, int hop,
+                             uint64_t ulim, Counters* ctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long sc = 0, mk = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_list; i += stride) {
+        const int32_t v = list[i];
+        const unsigned long long d = (unsigned long long)(rowp[v + 1] - rowp[v]);
+        sc += d;
+        if (hop > 1 && Scnt[v] == k && S[(int64_t)v * k + k - 1] <= ulim) mk += d;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sc += __shfl_xor_sync(kFull, sc, o);
+        mk += __shfl_xor_sync(kFull, mk, o);
+    }
+    if (lane_id() == 0) {
+        if (sc) atomicAdd(&ctr->scanned, sc);
+        if (mk) atomicAdd(&ctr->mask_scanned, mk);
+    }
+}
+
 // ------------------------------------------------------------------ small-rank table
 
 constexpr int kSelCap = 4096;  // candidates sorted in one block
@@ -747,7 +854,7 @@ __global__ void __launch_bounds__(1024) k_sort_small(const uint64_t* __restrict_
 }
 
 // U = the min(kUW, n) smallest vertex ranks: collect the ranks below a
-// threshold expected to pass about 1024 of them (ranks are uniform), widen or
+// threshold expected to pass about 2048 of them (ranks are uniform), widen or
 // narrow it until between min(kUW, n) and kSelCap pass, then sort them.
 static int select_small_ranks(fl_graph* g) {
     const int64_t n = g->n;
@@ -756,7 +863,7 @@ static int select_small_ranks(fl_graph* g) {
     DBuf buf;
     FL_TRY(dalloc(buf, (size_t)kSelCap * 8 + 256));
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(buf.as<char>() + (size_t)kSelCap * 8);
-    uint64_t T = n <= kSelCap / 2 ? kEmpty : (kEmpty / (uint64_t)n) * 1024ULL;
+    uint64_t T = n <= kSelCap / 2 ? kEmpty : (kEmpty / (uint64_t)n) * 2048ULL;
     unsigned long long c = 0;
     int rc = FL_OK;
     for (int it = 0;; ++it) {
@@ -812,7 +919,7 @@ static int launch_hop(fl_graph* g, int hop, const int32_t* list, int64_t n_list,
                                         g->hub_list.as<int32_t>(), g->hub_seg.as<int64_t>(), g->seg_hub.as<int32_t>(),
                                         g->n_seg, g->rowp.as<int64_t>(), g->cols.as<int32_t>(), k, g->seed, hop,
                                         g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[pin].as<uint64_t>(),
-                                        g->Dcnt[pin].as<uint8_t>(), g->part.as<uint64_t>(), g->ulim,
+                                        g->Dcnt[pin].as<uint8_t>(), g->part.as<uint64_t>(), g->U.as<uint64_t>(), g->ulim,
                                         g->DM[pin].as<uint64_t>(), g->PM.as<uint64_t>(), g->ctr.as<Counters>()));
         FL_LAUNCH(kProfSketchMerge, k_hop_hubs<G><<<grid_for(g->n_hubs, per_block), 256, 0, st>>>(
                                         g->hub_list.as<int32_t>(), g->n_hubs, g->hub_seg.as<int64_t>(),
@@ -850,9 +957,9 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     FL_TRY(dalloc(g->ve, (size_t)n * 4));
     FL_TRY(dalloc(g->part, (size_t)std::max<int64_t>(g->n_seg, 1) * k * 8));
     FL_TRY(dalloc(g->U, (size_t)kUW * 8));
-    FL_TRY(dalloc(g->DM[0], (size_t)n * 32));
-    FL_TRY(dalloc(g->DM[1], (size_t)n * 32));
-    FL_TRY(dalloc(g->PM, (size_t)std::max<int64_t>(g->n_seg, 1) * 32));
+    FL_TRY(dalloc(g->DM[0], (size_t)n * kUWords * 8));
+    FL_TRY(dalloc(g->DM[1], (size_t)n * kUWords * 8));
+    FL_TRY(dalloc(g->PM, (size_t)std::max<int64_t>(g->n_seg, 1) * kUWords * 8));
     // staging: slots 0..n-1 for hop 0, then one slot per work item of each hop
     const int64_t per_dense = g->n_low + g->n_hubs;
     size_t slot_cap = (size_t)n + (size_t)per_dense * 8 + 1024;
@@ -886,6 +993,15 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     if (g->h_ctr->error) {
         dfree(act);
         FL_FAIL(FL_EINVAL, "a vertex rank equals the reserved empty-slot value; choose another seed");
+    }
+    g->hop_scanned.clear();
+    g->hop_mask.clear();
+    g->hop_changed.clear();
+    g->hop_ms.clear();
+    const bool time_hops = g->prof.on != 0;
+    if (time_hops && !g->hop_ev[0]) {
+        FL_CUDA(cudaEventCreate(&g->hop_ev[0]));
+        FL_CUDA(cudaEventCreate(&g->hop_ev[1]));
     }
     std::vector<std::pair<int64_t, int64_t>> regions;  // (slot base, slots) of each hop
     regions.push_back({0, n});
@@ -927,13 +1043,34 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
             g->stg_grp_cap = cap;
         }
         FL_CUDA(cudaMemsetAsync(g->Dcnt[pout].p, 0, (size_t)n, st));
+        if (time_hops) {
+            if (n_list > 0)
+                FL_LAUNCH(kProfSketchOther, k_hop_census<<<grid_for(n_list, 256), 256, 0, st>>>(
+                                                list, n_list, g->rowp.as<int64_t>(), g->S.as<uint64_t>(),
+                                                g->Scnt.as<uint8_t>(), k, hop, g->ulim, g->ctr.as<Counters>()));
+            if (g->n_hubs > 0)
+                FL_LAUNCH(kProfSketchOther, k_hop_census<<<grid_for(g->n_hubs, 256), 256, 0, st>>>(
+                                                g->hub_list.as<int32_t>(), g->n_hubs, g->rowp.as<int64_t>(),
+                                                g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), k, hop, g->ulim,
+                                                g->ctr.as<Counters>()));
+            FL_CUDA(cudaEventRecord(g->hop_ev[0], st));
+        }
         if (k <= 16)
             FL_TRY(launch_hop<16>(g, hop, list, n_list, pin, pout, used_slots));
         else
             FL_TRY(launch_hop<32>(g, hop, list, n_list, pin, pout, used_slots));
+        if (time_hops) FL_CUDA(cudaEventRecord(g->hop_ev[1], st));
         regions.push_back({used_slots, slots});
         used_slots += slots;
         FL_TRY(read_counters(g));
+        {
+            float hop_ms = 0.f;
+            if (time_hops) FL_CUDA(cudaEventElapsedTime(&hop_ms, g->hop_ev[0], g->hop_ev[1]));
+            g->hop_scanned.push_back(time_hops ? (int64_t)g->h_ctr->scanned : 0);
+            g->hop_mask.push_back(time_hops ? (int64_t)g->h_ctr->mask_scanned : 0);
+            g->hop_changed.push_back((int64_t)g->h_ctr->frontier);
+            g->hop_ms.push_back(hop_ms);
+        }
         n_front = (int64_t)g->h_ctr->frontier;
         next_merges = (int64_t)g->h_ctr->merges;
         // algorithmic bytes of this hop's merge: row offsets of each merging

@@ -143,6 +143,27 @@ def test_hubs_in_push_and_pull_rounds():
         _compare(w, _gpu(w), _oracle(w))
 
 
+@pytest.mark.parametrize("scale,k", [(12, 4), (15, 16)])
+def test_hop_stats_account_for_every_ads_group(scale, k):
+    """Per-hop counters: every (vertex, hop >= 1) ADS group is one changed
+    sketch, so n + sum(changed) = ADS groups; the mask merge reads a subset of
+    the scanned CSR entries and takes over once sketches fill with small ranks."""
+    rowp, cols = flsynth.rmat(scale, 16, 700 + scale)
+    n = len(rowp) - 1
+    g = fl.Graph(rowp, cols)
+    g.profile(True)
+    g.build_sketches(k, 3)
+    st = g.stats()
+    hs = g.hop_stats()
+    g.close()
+    assert len(hs) == st["hops"] + 1 and hs[-1]["changed"] == 0
+    assert n + sum(h["changed"] for h in hs) == st["ads_groups"]
+    assert all(0 <= h["mask"] <= h["scanned"] for h in hs)
+    assert hs[0]["mask"] == 0 and hs[0]["scanned"] == len(cols)
+    assert sum(h["mask"] for h in hs) > 0
+    assert all(h["ms"] > 0 for h in hs)
+
+
 # ------------------------------------------------------------------ edge cases
 
 def test_single_vertex():
