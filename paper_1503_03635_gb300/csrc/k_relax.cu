@@ -48,9 +48,35 @@ __global__ void k_bitmap(const uint32_t* __restrict__ stamp, uint32_t sv, int64_
 // sweep (MIS sweeps stamp each sweep into the high word).  With `settle`, a
 // vertex holding a value below the limit is final and is skipped.
 //
-// Pull round over non-hub vertices: four vertices per warp in lockstep, eight
-// lanes per vertex striding over its neighbours; the loop runs to the largest
-// degree of the four so every shuffle and ballot involves the whole warp.
+// Lowest value offered by the frontier neighbours cols[e], e in [e0, e1) with
+// stride `step`, four edges per lane and pass: the four column loads, then the
+// four bitmap loads, then the value loads are independent, so each lane keeps
+// up to four dependent-load chains in flight.
+__device__ __forceinline__ unsigned long long pull_min(const int32_t* __restrict__ cols, int64_t e0, int64_t e1,
+                                                       int step, const uint32_t* __restrict__ bm,
+                                                       const unsigned long long* __restrict__ X,
+                                                       unsigned long long add, unsigned long long limit,
+                                                       unsigned long long m) {
+    for (int64_t e = e0; e < e1; e += 4 * step) {
+        int32_t u[4];
+        bool f[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) u[j] = e + j * step < e1 ? __ldcs(&cols[e + j * step]) : -1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) f[j] = u[j] >= 0 && in_front(bm, u[j]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (f[j]) {
+                const unsigned long long x = __ldg(&X[u[j]]);
+                if (x < limit && x + add < m) m = x + add;
+            }
+        }
+    }
+    return m;
+}
+
+// Pull round over non-hub vertices: four vertices per warp, eight lanes per
+// vertex striding over its neighbours; the lanes meet again at the reduction.
 __global__ void __launch_bounds__(256) k_pull_low(const int32_t* __restrict__ list, int64_t n_list,
                                                   const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
                                                   unsigned long long add, unsigned long long limit, bool settle,
@@ -69,19 +95,7 @@ __global__ void __launch_bounds__(256) k_pull_low(const int32_t* __restrict__ li
         const unsigned long long own = have ? X[v] : ~0ULL;
         const bool work = have && !(settle && own < limit);
         const int64_t beg = work ? rowp[v] : 0, end = work ? rowp[v + 1] : 0;
-        unsigned long long m = own;
-        int64_t len = end - beg;
-#pragma unroll
-        for (int o = 8; o < 32; o <<= 1) len = max(len, __shfl_xor_sync(kFull, len, o));
-        for (int64_t off = sub; off < len; off += 8) {
-            if (beg + off < end) {
-                const int32_t u = __ldcs(&cols[beg + off]);
-                if (in_front(bm, u)) {
-                    const unsigned long long x = __ldg(&X[u]);
-                    if (x < limit && x + add < m) m = x + add;
-                }
-            }
-        }
+        unsigned long long m = pull_min(cols, beg + sub, end, 8, bm, X, add, limit, own);
 #pragma unroll
         for (int o = 1; o < 8; o <<= 1) m = umin64(m, __shfl_xor_sync(kFull, m, o));
         const bool ch = work && sub == 0 && m < own;
@@ -115,14 +129,7 @@ __global__ void __launch_bounds__(256) k_pull_segs(const int32_t* __restrict__ s
         if (settle && own < limit) continue;
         const int64_t e0 = rowp[v] + (sidx - hub_seg[h]) * kSeg;
         const int64_t e1 = min(e0 + (int64_t)kSeg, rowp[v + 1]);
-        unsigned long long m = ~0ULL;
-        for (int64_t e = e0 + lane; e < e1; e += 32) {
-            const int32_t u = __ldcs(&cols[e]);
-            if (in_front(bm, u)) {
-                const unsigned long long x = __ldg(&X[u]);
-                if (x < limit && x + add < m) m = x + add;
-            }
-        }
+        unsigned long long m = pull_min(cols, e0 + lane, e1, 32, bm, X, add, limit, ~0ULL);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = umin64(m, __shfl_xor_sync(kFull, m, o));
         if (lane == 0 && m < own) {

@@ -178,18 +178,19 @@ __device__ __forceinline__ Mask4 gather_masks(const Grp<G>& g, const int32_t* __
     return acc;
 }
 
-// Saturated merge, slice by slice from the smallest ranks: src(q) gives the
-// OR of the candidates' slice q; idx is the lane's old entry's U position.
-// Lanes j < k receive the new sketch in sk_new; returns whether it changed.
+// Saturated merge, slice by slice from the smallest ranks: first = the OR of
+// the candidates' slice 0, src(q) gives it for q >= 1; idx is the lane's old
+// entry's U position.  Lanes j < k receive the new sketch in sk_new; returns
+// whether it changed.
 template <int G, class Src>
-__device__ __forceinline__ bool merge_slices(const Grp<G>& g, int k, const uint64_t* sU, int idx, Src src,
-                                             uint64_t& sk_new) {
+__device__ __forceinline__ bool merge_slices(const Grp<G>& g, int k, const uint64_t* sU, int idx, const Mask4& first,
+                                             Src src, uint64_t& sk_new) {
     int left = k, base = 0, own_seen = 0;
     bool changed = false;
     sk_new = kEmpty;
     for (int q = 0; q < kUSlices && left > 0; ++q) {
         const Mask4 own = slice_mask(g, idx, q);
-        Mask4 m = src(q);
+        Mask4 m = q == 0 ? first : src(q);
         m.add(own);
         mask_lowest(m, left);
         changed |= !(m == own);
@@ -500,13 +501,20 @@ __global__ void __launch_bounds__(256) k_hop_vertices(
         const unsigned long long cand0 = hc.cand;
         const bool sat = hop > 1 && s.cnt == k && s.tau <= ulim;
         if (sat) {
-            // saturated: mask merge
+            // saturated: mask merge; nothing to do without a neighbour that
+            // gained entries at the previous hop
+            const Mask4 first = gather_masks(g, cols, beg, end, Dcp, DMp, 0, hc.cand);
+            const bool merged = g.ballot(hc.cand != cand0) != 0;  // every lane votes
+            if (g.l == 0 && merged) hop_ctr_add<G>(kCMerging, 1u);
+            if (!merged) {
+                if (g.l == 0) stg_grp[i].info = 0;  // unchanged: empty slot
+                continue;
+            }
             const int idx = g.l < k ? u_pos(sU, ulim, old) : -1;
             uint64_t sk_new;
             const bool changed = merge_slices(
-                g, k, sU, idx, [&](int q) { return gather_masks(g, cols, beg, end, Dcp, DMp, q, hc.cand); }, sk_new);
-            const bool merged = g.ballot(hc.cand != cand0) != 0;  // every lane votes
-            if (g.l == 0 && merged) hop_ctr_add<G>(kCMerging, 1u);
+                g, k, sU, idx, first, [&](int q) { return gather_masks(g, cols, beg, end, Dcp, DMp, q, hc.cand); },
+                sk_new);
             if (!changed) {
                 if (g.l == 0) stg_grp[i].info = 0;  // unchanged: empty slot
                 continue;
@@ -594,18 +602,16 @@ __global__ void __launch_bounds__(256) k_hop_hubs(
             // saturated hub: OR of the segments' partial masks
             const int idx = g.l < k ? u_pos(sU, ulim, old) : -1;
             bool any = false;
+            auto part_slice = [&](int q) {
+                Mask4 m;
+                for (int64_t sidx = hub_seg[h] + g.l; sidx < hub_seg[h + 1]; sidx += G)
+                    m.load(PM + sidx * kUWords + q * 4);
+                grp_or(g, m);
+                any |= !m.empty();
+                return m;
+            };
             uint64_t sk_new;
-            const bool changed = merge_slices(
-                g, k, sU, idx,
-                [&](int q) {
-                    Mask4 m;
-                    for (int64_t sidx = hub_seg[h] + g.l; sidx < hub_seg[h + 1]; sidx += G)
-                        m.load(PM + sidx * kUWords + q * 4);
-                    grp_or(g, m);
-                    any |= !m.empty();
-                    return m;
-                },
-                sk_new);
+            const bool changed = merge_slices(g, k, sU, idx, part_slice(0), part_slice, sk_new);
             if (g.l == 0 && any) hop_ctr_add<G>(kCMerging, 1u);
             if (!changed) {
                 if (g.l == 0) stg_grp[slot0 + h].info = 0;  // unchanged: empty slot
