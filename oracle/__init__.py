@@ -79,6 +79,11 @@ def _load():
             lib.orc_open_facilities.argtypes = [vp, vp, vp, u64, vp, ctypes.POINTER(i64)]
             lib.orc_assign.restype = ctypes.c_int
             lib.orc_assign.argtypes = [vp, vp, vp, vp]
+            lib.orc_radius_of_ads.restype = dbl
+            lib.orc_radius_of_ads.argtypes = [i64, vp, vp, vp, vp, vp, vp, dbl]
+            lib.orc_nearest_open.restype = ctypes.c_int
+            lib.orc_nearest_open.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_int32)]
             lib.orc_objective.restype = ctypes.c_int
             lib.orc_objective.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(dbl),
                                           ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -196,6 +201,16 @@ class Graph:
         return dict(eid=ids[:ne].copy(), erank=rk[:ne].copy(), ghop=gh[:g].copy(),
                     gcnt=gn[:g].copy(), gcounted=gc[:g].copy(), gwt=gw[:g].copy())
 
+    def nearest_open(self, open_: np.ndarray, v: int):
+        """(facility, distance) of v's nearest open facility by BFS from v,
+        ties to the smallest id; (-1, -1) when none is reachable."""
+        op = np.ascontiguousarray(open_, np.uint8)
+        a, d = ctypes.c_int32(), ctypes.c_int32()
+        rc = self._lib.orc_nearest_open(self._h, _p(op), v, ctypes.byref(a), ctypes.byref(d))
+        if rc != 0:
+            raise RuntimeError(f"orc_nearest_open failed ({rc})")
+        return a.value, d.value
+
     def hip_estimate(self, v: int, h: int, client=None) -> float:
         c = None if client is None else np.ascontiguousarray(client, np.uint8)
         return float(self._lib.orc_hip_estimate(self._h, v, h, None if c is None else _p(c)))
@@ -231,6 +246,19 @@ class Graph:
         if rc != 0:
             raise RuntimeError(f"orc_assign rc={rc}")
         return a, d
+
+
+def radius_of_ads(ads: dict, client: np.ndarray, cost: float) -> float:
+    """Radius (Eq. 1 at epsilon -> 0) of one vertex from its ADS groups
+    (the dict of Graph.vertex_ads: ghop, gcnt, gcounted, gwt, eid)."""
+    lib = _load()
+    gh = np.ascontiguousarray(ads["ghop"], np.int32)
+    gn = np.ascontiguousarray(ads["gcnt"], np.int32)
+    gc = np.ascontiguousarray(ads["gcounted"], np.int32)
+    gw = np.ascontiguousarray(ads["gwt"], np.float64)
+    ids = np.ascontiguousarray(ads["eid"], np.int32)
+    cl = np.ascontiguousarray(client, np.uint8)
+    return lib.orc_radius_of_ads(len(gh), _p(gh), _p(gn), _p(gc), _p(gw), _p(ids), _p(cl), float(cost))
 
 
 def objective(open_, cost, client, dist):

@@ -481,30 +481,22 @@ int64_t orc_vertex_ads(const orc_graph* g, int k, uint64_t seed, int64_t v, int6
 /* (Section 3.4, "How to estimate the number of unfrozen clients?").       */
 /* ---------------------------------------------------------------------- */
 
-/* Radius of one facility from its ADS groups (hop ascending).  W_h = the
-   HIP-estimated number of clients at distance h; N_j = sum_{h<=j} W_h;
-   G_0 = 0, G_{j+1} = G_j + N_j (so g(r) = G_j + N_j (r - j) on [j, j+1]).
-   L = hop of the last group.  r = j + (c - G_j)/N_j for the smallest
-   j < L with G_{j+1} >= c; otherwise r = L + (c - G_L)/N_L if N_L > 0,
-   else +inf.  Non-facilities (cost +inf) get +inf. */
-static double radius_one(const orc_graph* g, int64_t f, double cost, const uint8_t* client) {
-    if (!(cost < INFINITY)) return INFINITY;
-    int64_t g0 = g->gofs[f], g1 = g->gofs[f + 1];
-    if (g1 == g0) return INFINITY;
-    int64_t L = g->grp[g1 - 1].hop;
+/* Radius from per-distance client estimates (hop ascending): ng groups at
+   distances hop[0] < hop[1] < ..., W[i] = HIP-estimated clients at
+   distance hop[i]; distances without a group have W = 0.  N_j = sum_{h<=j}
+   W_h; G_0 = 0, G_{j+1} = G_j + N_j (so g(r) = G_j + N_j (r - j) on
+   [j, j+1]).  L = hop of the last group.  r = j + (c - G_j)/N_j for the
+   smallest j < L with G_{j+1} >= c; otherwise r = L + (c - G_L)/N_L if
+   N_L > 0, else +inf. */
+static double radius_walk(const int32_t* hop, const double* W, int64_t ng, double cost) {
+    if (!(cost < INFINITY) || ng == 0) return INFINITY;
+    int64_t L = hop[ng - 1];
     double N = 0.0, G = 0.0;
-    int64_t gi = g0;
+    int64_t gi = 0;
     for (int64_t j = 0; j <= L; ++j) {
-        double W = 0.0;
-        if (gi < g1 && g->grp[gi].hop == j) {
-            const orc_group* gr = &g->grp[gi];
-            int64_t clients = 0;
-            for (int32_t i = 0; i < gr->counted; ++i)
-                if (client[g->ent_id[gr->first + i]]) ++clients;
-            W = (double)clients * gr->wt;
-            ++gi;
-        }
-        N = N + W;
+        double w = 0.0;
+        if (gi < ng && hop[gi] == j) { w = W[gi]; ++gi; }
+        N = N + w;
         if (j < L) {
             double Gn = G + N;
             if (Gn >= cost) return (double)j + (cost - G) / N;
@@ -513,6 +505,88 @@ static double radius_one(const orc_graph* g, int64_t f, double cost, const uint8
     }
     if (N > 0.0) return (double)L + (cost - G) / N;
     return INFINITY;
+}
+
+/* Radius of one facility from its ADS groups: W_h = (number of counted
+   entries of the hop-h group that are clients) x the group's weight. */
+static double radius_one(const orc_graph* g, int64_t f, double cost, const uint8_t* client) {
+    if (!(cost < INFINITY)) return INFINITY;
+    int64_t g0 = g->gofs[f], g1 = g->gofs[f + 1];
+    if (g1 == g0) return INFINITY;
+    int64_t ng = g1 - g0;
+    int32_t* hop = (int32_t*)malloc((size_t)ng * sizeof(int32_t));
+    double* W = (double*)malloc((size_t)ng * sizeof(double));
+    if (!hop || !W) { free(hop); free(W); return NAN; }
+    for (int64_t i = 0; i < ng; ++i) {
+        const orc_group* gr = &g->grp[g0 + i];
+        int64_t clients = 0;
+        for (int32_t e = 0; e < gr->counted; ++e)
+            if (client[g->ent_id[gr->first + e]]) ++clients;
+        hop[i] = gr->hop;
+        W[i] = (double)clients * gr->wt;
+    }
+    double r = radius_walk(hop, W, ng, cost);
+    free(hop); free(W);
+    return r;
+}
+
+/* The same radius from one vertex's ADS given as arrays (the output of
+   orc_vertex_ads or an exported ADS row): ng groups with distance ghop,
+   entry count gcnt, counted prefix gcounted and weight gw; ids holds the
+   entries of the groups one after another. */
+double orc_radius_of_ads(int64_t ng, const int32_t* ghop, const int32_t* gcnt, const int32_t* gcounted,
+                         const double* gw, const int32_t* ids, const uint8_t* client, double cost) {
+    if (!(cost < INFINITY) || ng == 0) return INFINITY;
+    double* W = (double*)malloc((size_t)ng * sizeof(double));
+    if (!W) return NAN;
+    int64_t first = 0;
+    for (int64_t i = 0; i < ng; ++i) {
+        int64_t clients = 0;
+        for (int32_t e = 0; e < gcounted[i]; ++e)
+            if (client[ids[first + e]]) ++clients;
+        W[i] = (double)clients * gw[i];
+        first += gcnt[i];
+    }
+    double r = radius_walk(ghop, W, ng, cost);
+    free(W);
+    return r;
+}
+
+/* Nearest open facility of v by definition (Section 3.1, d(c, S)): BFS
+   from v level by level; at the first level holding an open facility the
+   smallest such id and the level are returned; -1 / -1 when v's component
+   has none. */
+int orc_nearest_open(const orc_graph* g, const uint8_t* open, int64_t v, int32_t* assign, int32_t* dist) {
+    if (!g || v < 0 || v >= g->n) return ORC_EINVAL;
+    const int64_t n = g->n;
+    int32_t* d = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    int32_t* q = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    if (!d || !q) { free(d); free(q); return ORC_ENOMEM; }
+    for (int64_t i = 0; i < n; ++i) d[i] = -1;
+    *assign = -1;
+    *dist = -1;
+    int64_t qh = 0, qt = 0;
+    d[v] = 0;
+    q[qt++] = (int32_t)v;
+    int32_t level = 0;
+    while (qh < qt) {
+        int64_t level_end = qt;
+        int32_t best = -1;
+        for (int64_t i = qh; i < level_end; ++i)
+            if (open[q[i]] && (best < 0 || q[i] < best)) best = q[i];
+        if (best >= 0) { *assign = best; *dist = level; break; }
+        for (int64_t i = qh; i < level_end; ++i) {
+            int32_t x = q[i];
+            for (int64_t e = g->rowp[x]; e < g->rowp[x + 1]; ++e) {
+                int32_t u = g->cols[e];
+                if (d[u] < 0) { d[u] = level + 1; q[qt++] = u; }
+            }
+        }
+        qh = level_end;
+        ++level;
+    }
+    free(d); free(q);
+    return ORC_OK;
 }
 
 int orc_compute_radii(const orc_graph* g, const double* cost, const uint8_t* client, double* r) {
@@ -588,21 +662,23 @@ int orc_open_facilities(const orc_graph* g, const double* r, const uint8_t* clie
         int32_t f = c[i].f;
         double fl = floor(c[i].r);
         int64_t B = fl > 2147483647.0 ? 2147483647 : (int64_t)fl;
-        /* BFS from f to depth B; stop at the first claimed client */
+        /* BFS from f to depth B; a claimed client stops it as soon as it is
+           reached (Ball(f) then meets a ball already in S) */
         int64_t qh = 0, qt = 0, nb = 0;
-        int conflict = 0;
+        int conflict = client[f] && claimed[f];
         dist[f] = 0;
         q[qt++] = f;
+        if (client[f] && !conflict) ball[nb++] = f;
         while (qh < qt && !conflict) {
             int32_t x = q[qh++];
-            if (client[x]) {
-                if (claimed[x]) { conflict = 1; break; }
-                ball[nb++] = x;
-            }
             if (dist[x] == B) continue;
             for (int64_t e = g->rowp[x]; e < g->rowp[x + 1]; ++e) {
                 int32_t u = g->cols[e];
-                if (dist[u] < 0) { dist[u] = dist[x] + 1; q[qt++] = u; }
+                if (dist[u] >= 0) continue;
+                if (client[u] && claimed[u]) { conflict = 1; break; }
+                dist[u] = dist[x] + 1;
+                q[qt++] = u;
+                if (client[u]) ball[nb++] = u;
             }
         }
         for (int64_t j = 0; j < qt; ++j) dist[q[j]] = -1;

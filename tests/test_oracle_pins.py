@@ -383,6 +383,38 @@ def test_assignment_is_nearest_open_facility_min_id(name):
     assert (d == wd).all() and (a == wa).all()
 
 
+@pytest.mark.parametrize("name", sorted(TINY))
+def test_nearest_open_single_source_matches_brute_force(name):
+    """The per-vertex nearest-open-facility BFS (used to check sampled
+    clients at full size) against all-pairs BFS: smallest distance, then
+    smallest id; -1 where no open facility is reachable."""
+    rowp, cols = TINY[name]
+    n = len(rowp) - 1
+    D = brute.apsp(rowp, cols)
+    op = np.zeros(n, np.uint8)
+    op[[v for v in range(n) if v % 3 == 2]] = 1
+    g = oracle.Graph(rowp, cols)
+    wa, wd = brute.nearest_assignment(D, set(np.flatnonzero(op)))
+    for v in range(n):
+        assert g.nearest_open(op, v) == (wa[v], wd[v])
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_radius_of_single_vertex_ads_equals_build_radius(seed):
+    """The radius read off one vertex's Algorithm-1 ADS (used to check
+    sampled facilities at full size) equals the radius of the hop-
+    synchronous build, for every vertex: the two ADS constructions agree and
+    feed the same shell walk."""
+    w = flsynth.small_er(200, 3.0, 40 + seed, k=4, cost=5.0, client_p=0.6, fac_p=0.5)
+    w.cost = np.where(np.isfinite(w.cost), flsynth.loguniform(w.n, seed, 2.0, 30.0), np.inf)
+    g = oracle.Graph(w.rowp, w.cols)
+    g.build_sketches(w.k, w.seed)
+    r = g.radii(w.cost, w.client)
+    for v in range(w.n):
+        rv = oracle.radius_of_ads(g.vertex_ads(w.k, w.seed, v), w.client, w.cost[v])
+        assert rv == r[v] or (math.isinf(rv) and math.isinf(r[v]))
+
+
 def test_objective_recomputed_from_definition():
     rowp, cols = TINY["mixed"]
     n = len(rowp) - 1
