@@ -353,13 +353,119 @@ def run_gpu(args):
     return 0
 
 
+def run_batch(args):
+    """Batched workload: solves/s of the batch form vs the plain form (one
+    instance per fl_* sequence) on the same GPU, and whether they agree."""
+    import torch
+
+    import paper_1503_03635_gb300 as fl
+
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fl.load()
+    bw = flsynth.batch_config()
+    base = bw.resident
+    R, n = len(bw.inst_cost), base.n
+    k, seed = base.k, base.seed
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        # resident graphs, costs and client sets (device memory, built once)
+        g = fl.Graph(torch.from_numpy(base.rowp).to(dev), torch.from_numpy(base.cols).to(dev), stream=stream)
+        g.build_sketches(k, seed)
+        cost_r = torch.from_numpy(np.concatenate(bw.inst_cost)).to(dev)
+        client_r = torch.from_numpy(np.concatenate(bw.inst_client)).to(dev)
+        er_csr = [(torch.from_numpy(x.rowp).to(dev), torch.from_numpy(x.cols).to(dev)) for x in bw.graphs]
+        cost_u = torch.from_numpy(np.concatenate([x.cost for x in bw.graphs])).to(dev)
+        client_u = torch.from_numpy(np.concatenate([x.client for x in bw.graphs])).to(dev)
+        er_graphs = [fl.Graph(r, c, stream=stream) for r, c in er_csr]
+        brep = fl.Batch.replicas(g, R)
+        buni = fl.Batch.union(er_csr, stream=stream)
+        N_r, N_u = brep.n_total, buni.n_total
+        out = {f: torch.empty(N_r + N_u, dtype=dt, device=dev)
+               for f, dt in (("open", torch.uint8), ("assign", torch.int32), ("dist", torch.int32))}
+        plain = {f: torch.empty_like(t) for f, t in out.items()}
+        uoff = np.concatenate([[0], np.cumsum([x.n for x in bw.graphs])])
+        plain_obj = np.zeros(R + len(bw.graphs))
+        batch_obj = np.zeros(R + len(bw.graphs))
+
+    def batched():
+        r1 = brep.solve(k, seed, cost_r, client_r, out["open"][:N_r], out["assign"][:N_r], out["dist"][:N_r])
+        r2 = buni.solve(k, seed, cost_u, client_u, out["open"][N_r:], out["assign"][N_r:], out["dist"][N_r:])
+        batch_obj[:R] = r1["objective"]
+        batch_obj[R:] = r2["objective"]
+
+    def one_by_one():
+        for i in range(R):
+            s = fl.Solve(g)
+            sl = slice(i * n, (i + 1) * n)
+            s.compute_radii(cost_r[sl], client_r[sl])
+            s.open_facilities(plain["open"][sl])
+            s.assign_clients(plain["assign"][sl], plain["dist"][sl])
+            plain_obj[i] = s.objective()[0]
+            s.close()
+        for j, gj in enumerate(er_graphs):
+            gj.build_sketches(k, seed)
+            s = fl.Solve(gj)
+            sl = slice(N_r + int(uoff[j]), N_r + int(uoff[j + 1]))
+            s.compute_radii(cost_u[int(uoff[j]):int(uoff[j + 1])], client_u[int(uoff[j]):int(uoff[j + 1])])
+            s.open_facilities(plain["open"][sl])
+            s.assign_clients(plain["assign"][sl], plain["dist"][sl])
+            plain_obj[R + j] = s.objective()[0]
+            s.close()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms_batch = timed(batched)
+    ms_plain = timed(one_by_one)
+    clk = clocks.stop()
+    same = all(torch.equal(out[f], plain[f]) for f in out)
+    obj_ok = bool(np.all(np.abs(batch_obj - plain_obj) <= 1e-9 * np.abs(plain_obj)))
+    n_inst = R + len(bw.graphs)
+    if rank == 0:
+        line = {"metric": METRIC, "value": n_inst / (ms_batch / 1e3), "unit": "solves/s", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": "batch", "instances": n_inst,
+                           "resident": f"{R} instances on rmat20 (n={n}, nnz={base.nnz}), k={k}",
+                           "graphs": f"{len(bw.graphs)} ER graphs, {N_u} vertices in all, "
+                                     f"{sum(x.nnz for x in bw.graphs)} CSR entries, k={k}",
+                           "step": "every instance solved once (radii, keys, MIS, assignment, objective; "
+                                   "the ER graphs' sketches built too)"},
+                "plain": {"value": n_inst / (ms_plain / 1e3), "unit": "solves/s", "ms_per_step": ms_plain,
+                          "form": "one fl_* sequence per instance on one stream"},
+                "speedup_vs_plain": ms_plain / ms_batch,
+                "identical_to_plain": bool(same and obj_ok), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    for x in er_graphs:
+        x.close()
+    brep.close()
+    buni.close()
+    g.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    help="er10k, rmat20, rmat26 (the named workloads) or rmatS for the rmat20 recipe at scale S")
+                    help="er10k, rmat20, rmat26 (the named workloads), batch (solves/s batched vs plain) "
+                         "or rmatS for the rmat20 recipe at scale S")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -368,6 +474,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -16,6 +16,8 @@ Section 5 and Table 1, stood in for by seeded R-MAT and Erdos-Renyi graphs):
 * ``rmat26`` -- the same recipe at scale 26; clients Bernoulli(0.5), facilities
   Bernoulli(0.1) independently, facility costs log-uniform in [10, 10^4], other
   vertices +inf; k=16.
+* ``batch`` (``batch_config``): 64 instances on the rmat20 graph with their own
+  client sets and costs, plus 256 Erdos-Renyi graphs of uneven size; k=32.
 * ``rmatS`` for other scales (tests): the rmat20 recipe at scale S;
   ``rmat26sS``: the rmat26 recipe at scale S (profiling at a smaller footprint).
 
@@ -190,6 +192,55 @@ def config(name: str) -> Workload:
         cost = loguniform(n, MASK_SEED, 5.0, 500.0)
         return from_csr(name, rowp, cols, k, SKETCH_SEED, cost, np.ones(n, np.uint8))
     raise KeyError(name)
+
+
+@dataclasses.dataclass
+class BatchWorkload:
+    """The batched workload: instances on one resident graph plus many small
+    independent graphs (each a Workload with its own costs and clients)."""
+    name: str
+    resident: Workload        # the shared graph (its own cost/client unused)
+    inst_cost: list           # float64[n] per instance on the resident graph
+    inst_client: list         # uint8[n] per instance on the resident graph
+    graphs: list              # Workload per independent graph
+
+
+def _sample_without_replacement(n: int, m: int, seed: int) -> np.ndarray:
+    """m distinct vertices of [0, n): the m smallest keys of a seeded hash."""
+    key = hashes(n, seed)
+    return np.sort(np.argpartition(key, m - 1)[:m]) if m < n else np.arange(n)
+
+
+def batch_config(n_resident: int = 64, n_graphs: int = 256) -> BatchWorkload:
+    """`batch`: n_resident instances on the rmat20 graph (k=32), each with a
+    client set of log-uniform size in [10^3, 10^6] sampled without
+    replacement, every vertex a facility, one opening cost per instance
+    uniform in [5, 500]; plus n_graphs Erdos-Renyi graphs with n log-uniform
+    in [10^3, 10^5] and average degree uniform in {4..16}, every vertex a
+    client and facility, one cost per graph uniform in [5, 500]; k=32.
+    Seeds: graphs 42 + 4, instance parameters 11 (the query seed) + offsets."""
+    base = config("rmat20")
+    n = base.n
+    sizes = loguniform(n_resident, QUERY_SEED, 1.0e3, 1.0e6)
+    inst_costs = uniform(n_resident, QUERY_SEED + 1, 5.0, 500.0)
+    inst_cost, inst_client = [], []
+    for i in range(n_resident):
+        m = min(n, int(math.floor(sizes[i])))
+        cl = np.zeros(n, np.uint8)
+        cl[_sample_without_replacement(n, m, QUERY_SEED + 100 + i)] = 1
+        inst_client.append(cl)
+        inst_cost.append(np.full(n, inst_costs[i]))
+    er_n = loguniform(n_graphs, 42 + 4, 1.0e3, 1.0e5)
+    er_deg = uniform(n_graphs, 42 + 5, 4.0, 17.0)
+    er_cost = uniform(n_graphs, 42 + 6, 5.0, 500.0)
+    graphs = []
+    for j in range(n_graphs):
+        nj = int(math.floor(er_n[j]))
+        dj = min(16, int(math.floor(er_deg[j])))
+        rowp, cols = er(nj, nj * dj // 2, 42 + 4 + 1000 * (j + 1))
+        graphs.append(from_csr(f"er{nj}", rowp, cols, 32, SKETCH_SEED, np.full(nj, er_cost[j]),
+                               np.ones(nj, np.uint8)))
+    return BatchWorkload("batch", base, inst_cost, inst_client, graphs)
 
 
 def small_er(n: int, avg_deg: float, seed: int, k: int = 16, cost: float = 20.0,

@@ -251,6 +251,65 @@ int fl_hop_stats(const fl_graph* g, int64_t cap, int64_t* n_hops, int64_t* scann
 int fl_assign_nearest_noalloc(int64_t n, const int64_t* row_off, const int32_t* cols, int64_t nnz,
                               const uint8_t* open, int32_t* assign_out, int32_t* dist_out, void* stream);
 
+/*
+ * Batches: many instances solved in one pass (one set of launches and
+ * synchronisations for all of them).  Each instance is a connected part of
+ * one device graph; ranks r(v) and priorities pi(f) use the instance's own
+ * vertex ids, and the instances share no vertex or edge, so every result is
+ * the one the plain fl_* sequence gives for that instance alone (Section 3:
+ * the objective and the conflict graph H-bar of Alg. 3 decompose over
+ * components).
+ *
+ * fl_batch_create_union -- a batch of independent graphs (one instance
+ * each).  Graph i: n_of[i] >= 1 vertices, nnz_of[i] CSR entries, row
+ * offsets row_off[i] (int64[n_of[i]+1], from 0 to nnz_of[i]) and columns
+ * cols[i] (int32, in [0, n_of[i])), all in the memory mem_kind names.  The
+ * union (at most 2^31-1 vertices) is copied and kept on the device; instance
+ * i occupies vertices [off_i, off_i + n_of[i]), off_i = n_of[0]+..+n_of[i-1].
+ * FL_EINVAL on a bad CSR or a column outside its graph.
+ */
+typedef struct fl_batch fl_batch;
+int fl_batch_create_union(int n_graphs, const int64_t* n_of, const int64_t* nnz_of, const int64_t* const* row_off,
+                          const int32_t* const* cols, int mem_kind, void* cuda_stream, fl_batch** out);
+
+/*
+ * fl_batch_create_replicas -- n_inst instances (each with its own costs and
+ * client set) on the resident graph g, whose sketches are built and shared:
+ * one kernel reads every instance's radius off g's ADS; keys, MIS and
+ * assignment run on n_inst device copies of g's CSR (n_inst * n at most
+ * 2^31-1 vertices).  Instance i occupies vertices [i*n, (i+1)*n).  g must
+ * outlive the batch; rebuilding g's sketches is allowed between solves (the
+ * solve checks k and seed against the build).
+ */
+int fl_batch_create_replicas(fl_graph* g, int n_inst, fl_batch** out);
+
+/*
+ * fl_batch_solve -- solve every instance: sketches (union batches build them
+ * here with k and seed; replica batches require g's build to have used the
+ * same k and seed, else FL_ESTATE), radii (Eq. 1), keys, MIS (Alg. 6
+ * reading), assignment and objective, as fl_compute_radii ... fl_objective.
+ *   cost, client     float64 / uint8 [N] (N = the batch's vertex count,
+ *                    instance-major as placed by the create call), memory
+ *                    as mem_kind says; cost > 0 finite for facilities, +inf
+ *                    otherwise (FL_EINVAL).
+ *   open_out         uint8[N] or NULL.
+ *   assign_out       int32[N] or NULL: nearest open facility as an id of the
+ *                    vertex's own instance, -1 if none is reachable.
+ *   dist_out         int32[N] or NULL.
+ *   n_open, objective, dist_sum, n_unserved   per instance, HOST arrays of
+ *                    n_inst entries (any may be NULL), as fl_open_facilities
+ *                    and fl_objective give them.
+ */
+int fl_batch_solve(fl_batch* b, int k, uint64_t seed, const double* cost, const uint8_t* client,
+                   uint8_t* open_out, int32_t* assign_out, int32_t* dist_out, int64_t* n_open, double* objective,
+                   int64_t* dist_sum, int64_t* n_unserved, int mem_kind);
+
+/* fl_batch_info -- number of instances and total vertices N of a batch. */
+int fl_batch_info(const fl_batch* b, int64_t* n_inst, int64_t* n_total);
+
+/* fl_batch_destroy -- free the batch (not the graph of a replica batch). */
+int fl_batch_destroy(fl_batch* b);
+
 /* fl_status_str -- static text for a status code. */
 const char* fl_status_str(int status);
 

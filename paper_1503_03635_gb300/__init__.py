@@ -27,7 +27,8 @@ EXPORTS = ("fl_graph_create", "fl_graph_destroy", "fl_build_sketches", "fl_sketc
            "fl_export_sketches", "fl_export_ads", "fl_solve_create", "fl_solve_destroy",
            "fl_compute_radii", "fl_open_facilities", "fl_assign_clients", "fl_objective",
            "fl_solve_stats", "fl_status_str", "fl_last_error", "fl_profile_enable", "fl_profile_reset",
-           "fl_profile_query", "fl_hop_stats", "fl_assign_nearest_noalloc")
+           "fl_profile_query", "fl_hop_stats", "fl_batch_create_union", "fl_batch_create_replicas",
+           "fl_batch_solve", "fl_batch_info", "fl_batch_destroy", "fl_assign_nearest_noalloc")
 
 PROF_CLASSES = {"sketch_merge": 0, "sketch_expand": 1, "sketch_other": 2, "radius": 3, "keys": 4,
                 "mis": 5, "bfs": 6, "other": 7}
@@ -76,6 +77,11 @@ def load(build_if_missing: bool = True):
             "fl_profile_reset": ([vp], ci),
             "fl_profile_query": ([vp, ci, P64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ci),
             "fl_hop_stats": ([vp, i64, P64, vp, vp, vp, vp], ci),
+            "fl_batch_create_union": ([ci, vp, vp, vp, vp, ci, vp, ctypes.POINTER(vp)], ci),
+            "fl_batch_create_replicas": ([vp, ci, ctypes.POINTER(vp)], ci),
+            "fl_batch_solve": ([vp, ci, u64, vp, vp, vp, vp, vp, vp, vp, vp, vp, ci], ci),
+            "fl_batch_info": ([vp, P64, P64], ci),
+            "fl_batch_destroy": ([vp], ci),
             "fl_assign_nearest_noalloc": ([i64, vp, vp, i64, vp, vp, vp, vp], ci),
         }
         for name, (args, res) in sig.items():
@@ -269,6 +275,87 @@ class Solve:
         r, c = ctypes.c_int64(), ctypes.c_int64()
         _check(self._lib.fl_solve_stats(self._h, ctypes.byref(r), ctypes.byref(c)))
         return dict(mis_rounds=r.value, candidates=c.value)
+
+
+class Batch:
+    """fl_batch: many instances solved in one pass (see include/fl.h).
+
+    Batch.union(graphs) -- independent graphs [(rowp, cols), ...], one
+    instance each; Batch.replicas(graph, n_inst) -- n_inst instances on one
+    resident graph with built sketches.  solve() takes the instances' costs
+    and client masks concatenated (instance-major)."""
+
+    def __init__(self, handle, keep=None):
+        self._lib = load()
+        self._h = handle
+        self._keep = keep
+        n_inst, n_total = ctypes.c_int64(), ctypes.c_int64()
+        _check(self._lib.fl_batch_info(self._h, ctypes.byref(n_inst), ctypes.byref(n_total)))
+        self.n_inst, self.n_total = n_inst.value, n_total.value
+
+    @classmethod
+    def union(cls, graphs, stream=None):
+        lib = load()
+        ptr_r, ptr_c, kinds, keep = [], [], [], []
+        n_of = np.array([len(r) - 1 for r, _ in graphs], np.int64)
+        nnz_of = np.array([len(c) for _, c in graphs], np.int64)
+        for r, c in graphs:
+            pr, kr, a = _arg(r, np.int64)
+            pc, kc, b = _arg(c, np.int32)
+            ptr_r.append(pr.value or 0)
+            ptr_c.append(pc.value or 0)
+            kinds += [kr, kc]
+            keep += [a, b]
+        kind = _kind(*kinds)
+        R = (ctypes.c_void_p * len(graphs))(*ptr_r)
+        C = (ctypes.c_void_p * len(graphs))(*ptr_c)
+        st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
+        h = ctypes.c_void_p()
+        _check(lib.fl_batch_create_union(len(graphs), n_of.ctypes.data_as(ctypes.c_void_p),
+                                         nnz_of.ctypes.data_as(ctypes.c_void_p), R, C, kind, st, ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def replicas(cls, graph, n_inst: int):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.fl_batch_create_replicas(graph.handle, int(n_inst), ctypes.byref(h)))
+        return cls(h, keep=graph)
+
+    def solve(self, k: int, seed: int, cost, client, open_out=None, assign_out=None, dist_out=None) -> dict:
+        """Per-vertex outputs (host NumPy arrays unless given) and per-instance
+        n_open, objective, dist_sum, n_unserved."""
+        N, I = self.n_total, self.n_inst
+        if open_out is None and assign_out is None and dist_out is None and isinstance(cost, np.ndarray):
+            open_out = np.zeros(N, np.uint8)
+            assign_out = np.zeros(N, np.int32)
+            dist_out = np.zeros(N, np.int32)
+        pc, kc, _ = _arg(cost, np.float64)
+        pm, km, _ = _arg(client, np.uint8)
+        po, ko, _ = _arg(open_out, np.uint8)
+        pa, ka, _ = _arg(assign_out, np.int32)
+        pd, kd, _ = _arg(dist_out, np.int32)
+        kind = _kind(kc, km, ko, ka, kd)
+        n_open = np.zeros(I, np.int64)
+        obj = np.zeros(I, np.float64)
+        ds = np.zeros(I, np.int64)
+        un = np.zeros(I, np.int64)
+        _check(self._lib.fl_batch_solve(self._h, int(k), int(seed), pc, pm, po, pa, pd,
+                                        n_open.ctypes.data_as(ctypes.c_void_p), obj.ctypes.data_as(ctypes.c_void_p),
+                                        ds.ctypes.data_as(ctypes.c_void_p), un.ctypes.data_as(ctypes.c_void_p), kind))
+        return dict(open=open_out, assign=assign_out, dist=dist_out, n_open=n_open, objective=obj, dist_sum=ds,
+                    n_unserved=un)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def assign_nearest_noalloc(rowp, cols, open_mask, assign_out, dist_out, stream=None):

@@ -4,6 +4,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "fl_internal.cuh"
 
@@ -34,7 +35,7 @@ void destroy_graph(fl_graph* g) {
                     &g->S, &g->Scnt, &g->D[0], &g->D[1], &g->Dcnt[0], &g->Dcnt[1], &g->frontier[0],
                     &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent, &g->stg_grp, &g->gofs, &g->eofs,
                     &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub, &g->ctr, &g->scratch,
-                    &g->relax_aux, &g->U, &g->DM[0], &g->DM[1], &g->PM};
+                    &g->relax_aux, &g->U, &g->DM[0], &g->DM[1], &g->PM, &g->vbase};
     for (DBuf* b : bufs) dfree(*b);
     for (cudaEvent_t e : g->prof.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : g->hop_ev)
@@ -317,6 +318,245 @@ int fl_objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserve
     if (obj) *obj = o;
     if (dist_sum) *dist_sum = ds;
     if (n_unserved) *n_unserved = un;
+    return FL_OK;
+}
+
+// ------------------------------------------------------------------ batches
+
+}  // extern "C"
+
+struct fl_batch {
+    int kind = 0;                  // 1: union of graphs, 2: replicas of a resident graph
+    fl_graph* base = nullptr;      // replicas: the resident graph (not owned)
+    fl_graph* U = nullptr;         // the batch graph (owned)
+    fl_solve* s = nullptr;         // its solve state (owned)
+    int64_t n_inst = 0;
+    std::vector<int64_t> off;      // host: first vertex of each instance, n_inst + 1 entries
+    fl::DBuf off_d;                // device copy
+    fl::DBuf res;                  // per instance: double obj, int64 n_open, dist_sum, unserved; int32 assign[N]
+};
+
+namespace {
+
+void destroy_batch(fl_batch* b) {
+    if (!b) return;
+    if (b->s) destroy_solve(b->s);
+    if (b->U) destroy_graph(b->U);
+    dfree(b->off_d);
+    dfree(b->res);
+    delete b;
+}
+
+// An empty graph handle of n vertices and nnz entries on `stream` (CSR and
+// part bases allocated, contents unset).
+int new_graph(int64_t n, int64_t nnz, cudaStream_t stream, fl_graph** out) {
+    fl_graph* g = new (std::nothrow) fl_graph();
+    if (!g) FL_FAIL(FL_ENOMEM, "host allocation failed");
+    g->n = n;
+    g->nnz = nnz;
+    g->stream = stream;
+    int rc = FL_OK;
+    do {
+        cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&g->h_ctr), sizeof(Counters));
+        if (e != cudaSuccess) { rc = status_of(e, "cudaMallocHost", __FILE__, __LINE__); break; }
+        if ((rc = dalloc(g->ctr, sizeof(Counters)))) break;
+        if ((rc = dalloc(g->rowp, (size_t)(n + 1) * 8))) break;
+        if ((rc = dalloc(g->cols, (size_t)(nnz > 0 ? nnz : 1) * 4))) break;
+        if ((rc = dalloc(g->vbase, (size_t)n * 4))) break;
+    } while (0);
+    if (rc != FL_OK) {
+        destroy_graph(g);
+        return rc;
+    }
+    *out = g;
+    return FL_OK;
+}
+
+// The batch's solve state and per-instance result buffers.
+int batch_finish(fl_batch* b) {
+    const int64_t N = b->U->n;
+    fl_solve* s = new (std::nothrow) fl_solve();
+    if (!s) FL_FAIL(FL_ENOMEM, "host allocation failed");
+    b->s = s;
+    s->g = b->U;
+    FL_TRY(dalloc(s->cost, (size_t)N * 8));
+    FL_TRY(dalloc(s->client, (size_t)N));
+    FL_TRY(dalloc(s->radii, (size_t)N * 8));
+    FL_TRY(dalloc(b->off_d, (size_t)(b->n_inst + 1) * 8));
+    FL_TRY(dalloc(b->res, (size_t)b->n_inst * 32 + (size_t)N * 4 + 64));
+    FL_CUDA(cudaMemcpyAsync(b->off_d.p, b->off.data(), (size_t)(b->n_inst + 1) * 8, cudaMemcpyHostToDevice,
+                            b->U->stream));
+    FL_CUDA(cudaStreamSynchronize(b->U->stream));
+    return FL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fl_batch_create_union(int n_graphs, const int64_t* n_of, const int64_t* nnz_of, const int64_t* const* row_off,
+                          const int32_t* const* cols, int mem_kind, void* stream, fl_batch** out) {
+    if (!out) FL_FAIL(FL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_graphs < 1 || !n_of || !nnz_of || !row_off || !cols) FL_FAIL(FL_EINVAL, "bad arguments");
+    if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    std::vector<int64_t> voff(n_graphs + 1, 0), eoff(n_graphs + 1, 0);
+    for (int i = 0; i < n_graphs; ++i) {
+        if (n_of[i] < 1 || nnz_of[i] < 0 || !row_off[i] || (nnz_of[i] > 0 && !cols[i]))
+            FL_FAIL(FL_EINVAL, "bad CSR arrays of a graph");
+        voff[i + 1] = voff[i] + n_of[i];
+        eoff[i + 1] = eoff[i] + nnz_of[i];
+        if (voff[i + 1] > 2147483647LL) FL_FAIL(FL_EINVAL, "more than 2^31-1 vertices in the batch");
+    }
+    fl_batch* b = new (std::nothrow) fl_batch();
+    if (!b) FL_FAIL(FL_ENOMEM, "host allocation failed");
+    b->kind = 1;
+    b->n_inst = n_graphs;
+    b->off = voff;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ProfScope ps(nullptr);
+    int rc = new_graph(voff[n_graphs], eoff[n_graphs], st, &b->U);
+    if (rc == FL_OK) {
+        fl_graph* U = b->U;
+        set_current_prof(&U->prof, st);
+        for (int i = 0; i < n_graphs && rc == FL_OK; ++i) {
+            // each graph's offsets must run from 0 to its nnz
+            int64_t ends[2] = {-1, -1};
+            cudaError_t e = cudaSuccess;
+            if (mem_kind == FL_MEM_HOST) {
+                ends[0] = row_off[i][0];
+                ends[1] = row_off[i][n_of[i]];
+            } else {
+                e = cudaMemcpyAsync(&ends[0], row_off[i], 8, cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(&ends[1], row_off[i] + n_of[i], 8, cudaMemcpyDeviceToHost, st);
+            }
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(U->rowp.as<int64_t>() + voff[i], row_off[i], (size_t)n_of[i] * 8,
+                                    kind_in(mem_kind), st);
+            if (e == cudaSuccess && nnz_of[i] > 0)
+                e = cudaMemcpyAsync(U->cols.as<int32_t>() + eoff[i], cols[i], (size_t)nnz_of[i] * 4,
+                                    kind_in(mem_kind), st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) rc = status_of(e, "batch CSR upload", __FILE__, __LINE__);
+            else if (ends[0] != 0 || ends[1] != nnz_of[i]) {
+                set_error(FL_EINVAL, "a graph's row offsets must run from 0 to its nnz");
+                rc = FL_EINVAL;
+            }
+        }
+        const int64_t total = eoff[n_graphs];
+        if (rc == FL_OK) rc = batch_place_parts(U, voff, eoff);
+        if (rc == FL_OK) {
+            cudaError_t e = cudaMemcpyAsync(U->rowp.as<int64_t>() + U->n, &total, 8, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) rc = status_of(e, "batch CSR", __FILE__, __LINE__);
+        }
+        if (rc == FL_OK) rc = validate_csr(U);
+        if (rc == FL_OK) rc = batch_check_parts(U);
+        if (rc == FL_OK) rc = batch_finish(b);
+    }
+    if (rc != FL_OK) {
+        destroy_batch(b);
+        return rc;
+    }
+    *out = b;
+    return FL_OK;
+}
+
+int fl_batch_create_replicas(fl_graph* g, int n_inst, fl_batch** out) {
+    if (!out) FL_FAIL(FL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    if (!g->built) FL_FAIL(FL_ESTATE, "build the sketches before creating a replica batch");
+    if (n_inst < 1) FL_FAIL(FL_EINVAL, "n_inst must be >= 1");
+    if ((int64_t)n_inst * g->n > 2147483647LL) FL_FAIL(FL_EINVAL, "n_inst * n exceeds 2^31-1 vertices");
+    fl_batch* b = new (std::nothrow) fl_batch();
+    if (!b) FL_FAIL(FL_ENOMEM, "host allocation failed");
+    b->kind = 2;
+    b->base = g;
+    b->n_inst = n_inst;
+    b->off.resize(n_inst + 1);
+    for (int i = 0; i <= n_inst; ++i) b->off[i] = (int64_t)i * g->n;
+    ProfScope ps(g);
+    int rc = new_graph((int64_t)n_inst * g->n, (int64_t)n_inst * g->nnz, g->stream, &b->U);
+    if (rc == FL_OK) rc = batch_replicate(g, n_inst, b->U);
+    if (rc == FL_OK) rc = batch_finish(b);
+    if (rc != FL_OK) {
+        destroy_batch(b);
+        return rc;
+    }
+    *out = b;
+    return FL_OK;
+}
+
+int fl_batch_solve(fl_batch* b, int k, uint64_t seed, const double* cost, const uint8_t* client,
+                   uint8_t* open_out, int32_t* assign_out, int32_t* dist_out, int64_t* n_open, double* objective,
+                   int64_t* dist_sum, int64_t* n_unserved, int mem_kind) {
+    if (!b || !b->U || !b->s) FL_FAIL(FL_EINVAL, "null batch handle");
+    if (!cost || !client) FL_FAIL(FL_EINVAL, "cost and client are required");
+    if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    if (k < 2 || k > 32) FL_FAIL(FL_EINVAL, "k must be in [2, 32]");
+    fl_graph* U = b->U;
+    fl_solve* s = b->s;
+    const int64_t N = U->n;
+    cudaStream_t st = U->stream;
+    ProfScope ps(b->kind == 2 ? b->base : U);
+    s->have_radii = s->have_open = s->have_assign = 0;
+    if (b->kind == 1) {
+        FL_TRY(build_sketches(U, k, seed));
+    } else {
+        fl_graph* G = b->base;
+        if (!G->built || G->k != k || G->seed != seed)
+            FL_FAIL(FL_ESTATE, "the resident graph's sketches were not built with this k and seed");
+        U->k = k;
+        U->seed = seed;
+        FL_TRY(batch_replicate_ecc(G, b->n_inst, U));
+        U->built = 1;
+    }
+    s->generation = U->generation;
+    FL_CUDA(cudaMemcpyAsync(s->cost.p, cost, (size_t)N * 8, kind_in(mem_kind), st));
+    FL_CUDA(cudaMemcpyAsync(s->client.p, client, (size_t)N, kind_in(mem_kind), st));
+    if (b->kind == 1)
+        FL_TRY(compute_radii(s));
+    else
+        FL_TRY(compute_radii_multi(b->base, b->n_inst, s->cost.as<double>(), s->client.as<uint8_t>(),
+                                   s->radii.as<double>()));
+    FL_TRY(open_facilities(s));
+    FL_TRY(assign_clients(s));
+    double* obj_d = b->res.as<double>();
+    long long* cnt_d = reinterpret_cast<long long*>(obj_d + b->n_inst);
+    int32_t* asg_d = reinterpret_cast<int32_t*>(cnt_d + 3 * b->n_inst);
+    FL_TRY(batch_objective(s, b->off_d.as<int64_t>(), (int)b->n_inst, obj_d, cnt_d, cnt_d + b->n_inst,
+                           cnt_d + 2 * b->n_inst));
+    if (assign_out) FL_TRY(batch_localize(s, asg_d));
+    FL_TRY(copy_out(open_out, s->open.p, (size_t)N, mem_kind, st));
+    FL_TRY(copy_out(assign_out, asg_d, (size_t)N * 4, mem_kind, st));
+    FL_TRY(copy_out(dist_out, s->dist.p, (size_t)N * 4, mem_kind, st));
+    std::vector<double> h_obj(b->n_inst);
+    std::vector<long long> h_cnt(3 * b->n_inst);
+    FL_CUDA(cudaMemcpyAsync(h_obj.data(), obj_d, (size_t)b->n_inst * 8, cudaMemcpyDeviceToHost, st));
+    FL_CUDA(cudaMemcpyAsync(h_cnt.data(), cnt_d, (size_t)b->n_inst * 24, cudaMemcpyDeviceToHost, st));
+    FL_CUDA(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < b->n_inst; ++i) {
+        if (objective) objective[i] = h_obj[i];
+        if (n_open) n_open[i] = h_cnt[i];
+        if (dist_sum) dist_sum[i] = h_cnt[b->n_inst + i];
+        if (n_unserved) n_unserved[i] = h_cnt[2 * b->n_inst + i];
+    }
+    return FL_OK;
+}
+
+int fl_batch_info(const fl_batch* b, int64_t* n_inst, int64_t* n_total) {
+    if (!b || !b->U) FL_FAIL(FL_EINVAL, "null batch handle");
+    if (n_inst) *n_inst = b->n_inst;
+    if (n_total) *n_total = b->U->n;
+    return FL_OK;
+}
+
+int fl_batch_destroy(fl_batch* b) {
+    if (!b) return FL_OK;
+    if (b->U) cudaStreamSynchronize(b->U->stream);
+    destroy_batch(b);
     return FL_OK;
 }
 

@@ -54,6 +54,11 @@ constexpr uint64_t kMul1 = 0xbf58476d1ce4e5b9ULL;
 constexpr uint64_t kMul2 = 0x94d049bb133111ebULL;
 constexpr uint64_t kEmpty = ~0ULL;                   // empty sketch slot
 
+// Local id of v in a disjoint-union graph (see fl_graph::vbase).
+__device__ __forceinline__ int64_t local_id(const int32_t* __restrict__ vbase, int64_t v) {
+    return vbase ? v - (int64_t)__ldg(&vbase[v]) : v;
+}
+
 __host__ __device__ constexpr uint64_t inv_odd(uint64_t a) {
     // Newton iteration for the inverse of an odd number mod 2^64
     uint64_t x = a;
@@ -363,6 +368,11 @@ struct fl_graph {
     fl::DBuf seg_hub;              // int32[n_seg]: hub of each segment
     int64_t n_low = 0, n_hubs = 0, n_seg = 0;
     fl::DBuf part;                 // uint64[n_seg*k]: partial bottom-k of each hub segment (scratch)
+    // A graph that is a disjoint union of parts (batched instances): vertex v
+    // of the part starting at vbase[v] has local id v - vbase[v], and ranks
+    // and priorities are those of the local id, so every part is solved
+    // exactly as it would be alone.  Empty for an ordinary graph.
+    fl::DBuf vbase;                // int32[n] or empty
     fl::DBuf U;                    // uint64[kUW]: the kUW smallest ranks, ascending (kEmpty padded)
     uint64_t ulim = 0;             // largest entry of U
     fl::DBuf DM[2];                // uint64[n*kUWords]: hop delta masks over U
@@ -468,5 +478,14 @@ int assign_clients(fl_solve* s);
 int objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserved);
 
 int read_counters(fl_graph* g);
+// batches (k_batch.cu)
+int batch_place_parts(fl_graph* U, const std::vector<int64_t>& voff, const std::vector<int64_t>& eoff);
+int batch_check_parts(fl_graph* U);
+int batch_replicate(const fl_graph* G, int64_t R, fl_graph* U);
+int batch_replicate_ecc(const fl_graph* G, int64_t R, fl_graph* U);
+int batch_objective(fl_solve* s, const int64_t* off_d, int n_inst, double* obj, long long* n_open,
+                    long long* dist_sum, long long* unserved);
+int batch_localize(fl_solve* s, int32_t* out);
+int compute_radii_multi(fl_graph* g, int64_t R, const double* cost, const uint8_t* client, double* radii);
 
 }  // namespace fl

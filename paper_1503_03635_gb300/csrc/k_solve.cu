@@ -169,15 +169,22 @@ __global__ void k_check_costs(const double* __restrict__ cost, int64_t n, Counte
 // the first j < L with G_{j+1} >= c, else L + (c - G_L) / N_L (L = last hop
 // of the ADS of f), +inf if N_L = 0.  Every operation is one IEEE-754 op in
 // this order (no contraction).
-__global__ void __launch_bounds__(256) k_radius(int64_t n, const double* __restrict__ cost,
+//
+// R > 1 (batches on one resident graph): R instances, instance i's costs,
+// client mask and radii at offset i*n; the warps of one facility's R
+// instances are adjacent, so its ADS row is read from DRAM once.
+template <bool kMulti>
+__global__ void __launch_bounds__(256) k_radius(int64_t n, int64_t R, const double* __restrict__ cost,
                                                 const uint8_t* __restrict__ client,
                                                 const int64_t* __restrict__ gofs, const int64_t* __restrict__ eofs,
                                                 const uint32_t* __restrict__ ginfo, const double* __restrict__ gwt,
                                                 const int32_t* __restrict__ eid, double* __restrict__ r_out) {
     const int lane = lane_id();
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t f = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; f < n; f += warps) {
-        const double c = cost[f];
+    for (int64_t t = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; t < n * R; t += warps) {
+        const int64_t f = kMulti ? t / R : t;
+        const int64_t io = kMulti ? (t - f * R) * n : 0;  // instance offset
+        const double c = cost[io + f];
         double res = INFINITY;
         if (c < INFINITY) {
             const int64_t g0 = gofs[f], g1 = gofs[f + 1];
@@ -203,7 +210,7 @@ __global__ void __launch_bounds__(256) k_radius(int64_t n, const double* __restr
                     }
                 }
                 if (done) break;
-                bool is_client = lane < counted && client[eid[e + lane]] != 0;
+                bool is_client = lane < counted && client[io + eid[e + lane]] != 0;
                 int clients = __popc(__ballot_sync(kFull, is_client));
                 double W = __dmul_rn((double)clients, gwt[gi]);
                 N = __dadd_rn(N, W);
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(256) k_radius(int64_t n, const double* __restr
             }
             if (!done) res = N > 0.0 ? __dadd_rn((double)L, __ddiv_rn(__dsub_rn(c, G), N)) : INFINITY;
         }
-        if (lane == 0) r_out[f] = res;
+        if (lane == 0) r_out[io + f] = res;
     }
 }
 
@@ -233,16 +240,34 @@ int compute_radii(fl_solve* s) {
     FL_CUDA(cudaGetLastError());
     FL_TRY(read_counters(g));
     if (g->h_ctr->error) FL_FAIL(FL_EINVAL, "open_cost must be finite and > 0 for facilities, +inf otherwise");
-    FL_LAUNCH(kProfRadius, k_radius<<<grid_for(g->n, 8), 256, 0, st>>>(g->n, s->cost.as<double>(), s->client.as<uint8_t>(),
+    FL_LAUNCH(kProfRadius, k_radius<false><<<grid_for(g->n, 8), 256, 0, st>>>(g->n, 1, s->cost.as<double>(), s->client.as<uint8_t>(),
                                                g->gofs.as<int64_t>(), g->eofs.as<int64_t>(), g->ginfo.as<uint32_t>(),
                                                g->gwt.as<double>(), g->eid.as<int32_t>(), s->radii.as<double>()));
     FL_CUDA(cudaGetLastError());
     return FL_OK;
 }
 
+// Radii of R instances on one built graph (batches): cost, client and radii
+// are R*n arrays, instance-major.
+int compute_radii_multi(fl_graph* g, int64_t R, const double* cost, const uint8_t* client, double* radii) {
+    cudaStream_t st = g->stream;
+    FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st));
+    FL_LAUNCH(kProfRadius, k_check_costs<<<grid_for(g->n * R, 256), 256, 0, st>>>(cost, g->n * R,
+                                                                                 g->ctr.as<Counters>()));
+    FL_CUDA(cudaGetLastError());
+    FL_TRY(read_counters(g));
+    if (g->h_ctr->error) FL_FAIL(FL_EINVAL, "open_cost must be finite and > 0 for facilities, +inf otherwise");
+    FL_LAUNCH(kProfRadius, k_radius<true><<<grid_for(g->n * R, 8), 256, 0, st>>>(
+                               g->n, R, cost, client, g->gofs.as<int64_t>(), g->eofs.as<int64_t>(),
+                               g->ginfo.as<uint32_t>(), g->gwt.as<double>(), g->eid.as<int32_t>(), radii));
+    FL_CUDA(cudaGetLastError());
+    return FL_OK;
+}
+
 // ------------------------------------------------------------------ keys (r_f, pi_f)
 
-__global__ void k_candidates(const double* __restrict__ r, int64_t n, uint64_t seed, uint64_t* __restrict__ hi,
+__global__ void k_candidates(const double* __restrict__ r, int64_t n, uint64_t seed,
+                             const int32_t* __restrict__ vbase, uint64_t* __restrict__ hi,
                              uint64_t* __restrict__ lo, uint32_t* __restrict__ val, uint8_t* __restrict__ state,
                              Counters* ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -258,7 +283,7 @@ __global__ void k_candidates(const double* __restrict__ r, int64_t n, uint64_t s
         long long at = warp_append(cand, &ctr->aux0);
         if (at >= 0) {
             hi[at] = (uint64_t)__double_as_longlong(rf);  // r >= 0: bit order = numeric order
-            lo[at] = facility_priority(seed, f);
+            lo[at] = facility_priority(seed, local_id(vbase, f));
             val[at] = (uint32_t)f;
         }
     }
@@ -420,7 +445,8 @@ int open_facilities(fl_solve* s) {
         return rc;
     }
     FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st));
-    FL_LAUNCH(kProfKeys, k_candidates<<<grid_for(n, 256), 256, 0, st>>>(s->radii.as<double>(), n, g->seed, hi.as<uint64_t>(),
+    FL_LAUNCH(kProfKeys, k_candidates<<<grid_for(n, 256), 256, 0, st>>>(s->radii.as<double>(), n, g->seed,
+                                                   g->vbase.p ? g->vbase.as<int32_t>() : nullptr, hi.as<uint64_t>(),
                                                    lo.as<uint64_t>(), val.as<uint32_t>(), s->state.as<uint8_t>(),
                                                    g->ctr.as<Counters>()));
     rc = read_counters(g);
