@@ -458,17 +458,123 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Serving workload: a resident R-MAT graph with built sketches (k=32),
+    a Poisson stream of queries (client set of log-uniform size, one
+    log-uniform cost), continuous batching over two workers; p50/p99 latency
+    (arrival -> results on the host) and solves/s, beside the same queries
+    run plain one after another."""
+    import threading
+
+    import torch
+
+    import paper_1503_03635_gb300 as fl
+    from paper_1503_03635_gb300 import serve
+
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fl.load()
+    scale = args.serve_scale
+    rowp, cols = flsynth.rmat(scale, 16, 42 + 5)
+    n = len(rowp) - 1
+    k, seed = 32, flsynth.SKETCH_SEED
+    g = fl.Graph(torch.from_numpy(rowp).to(dev), torch.from_numpy(cols).to(dev))
+    g.build_sketches(k, seed)
+    torch.cuda.synchronize()
+    rate, warm, dur = args.rate, args.serve_warmup, args.serve_seconds
+    m = int((warm + dur) * rate * 1.2) + 16
+    gaps = -np.log1p(-flsynth.uniform(m, flsynth.QUERY_SEED, 0.0, 1.0)) / rate
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < warm + dur]
+    sizes = flsynth.loguniform(len(arrivals), flsynth.QUERY_SEED + 1, 1.0e3, 1.0e6)
+    costs = flsynth.loguniform(len(arrivals), flsynth.QUERY_SEED + 2, 10.0, 1.0e3)
+    qs = [serve.Query(costs[i], client_seed=flsynth.QUERY_SEED * 1000003 + i, client_frac=min(1.0, sizes[i] / n))
+          for i in range(len(arrivals))]
+    srv = serve.Server(g, k, seed, workers=2, keep_open_mask=True)
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    for q, ta in zip(qs, arrivals):
+        delay = t0 + ta - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        srv.submit(q)
+    t_end = t0 + warm + dur
+    for q in qs:
+        q._done.wait()
+    t_drain = time.perf_counter()
+    clk = clocks.stop()
+    srv.close()
+    measured = [q for q, ta in zip(qs, arrivals) if ta >= warm]
+    served = [q for q in measured if q.error is None]
+    done_in_window = [q for q in served if q.t_done <= t_end]
+    lat = serve.latency_summary(served)
+    batch_sizes = [q.batch_size for q in served]
+
+    # the same queries run plain, one fl_* sequence at a time (a bounded prefix)
+    plain_q = measured[:args.serve_plain]
+    t_plain = []
+    mask = torch.empty(n, dtype=torch.uint8, device=dev)
+    cost_d = torch.empty(n, dtype=torch.float64, device=dev)
+    open_d = torch.empty(n, dtype=torch.uint8, device=dev)
+    same = True
+    for q in plain_q:
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        cost_d.fill_(q.cost)
+        serve.client_mask_on_device(torch, n, q.client_seed, q.client_frac, dev, mask)
+        s = fl.Solve(g)
+        s.compute_radii(cost_d, mask)
+        _, no = s.open_facilities(open_d)
+        s.assign_clients()
+        obj = s.objective()[0]
+        op_h = open_d.cpu().numpy()
+        s.close()
+        t_plain.append(time.perf_counter() - ts)
+        if q.error is None:
+            same = same and no == q.result["n_open"] and np.array_equal(op_h, q.result["open"]) and \
+                abs(obj - q.result["objective"]) <= 1e-9 * abs(obj)
+    g.close()
+    line = {"metric": METRIC, "value": len(done_in_window) / dur, "unit": "solves/s", "n_gpus": 1,
+            "steps": len(measured), "warmup": len(qs) - len(measured), "ms_per_step": lat.get("mean_ms"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"serve: resident R-MAT scale {scale} (n={n}, nnz={len(cols)}), k={k}",
+                       "arrivals": f"Poisson {rate} req/s, {warm} s warm-up + {dur} s measured",
+                       "query": "clients: each vertex with probability m/n, m log-uniform in [1e3, 1e6]; "
+                                "every vertex a facility, one cost log-uniform in [10, 1000]",
+                       "workers": 2, "slots_per_worker": srv.slots, "max_pending": srv.max_pending},
+            "latency_ms": {"p50": lat.get("p50_ms"), "p99": lat.get("p99_ms"), "mean": lat.get("mean_ms"),
+                           "max": lat.get("max_ms")},
+            "offered": len(measured), "served": len(served), "refused": srv.rejected,
+            "served_in_window": len(done_in_window), "drain_s": t_drain - t_end,
+            "mean_batch": float(np.mean(batch_sizes)) if batch_sizes else None,
+            "plain": {"queries": len(plain_q), "solves_per_sec": len(t_plain) / sum(t_plain) if t_plain else None,
+                      "p50_ms": float(np.percentile(t_plain, 50) * 1e3) if t_plain else None,
+                      "form": "one fl_* sequence per query, back to back"},
+            "identical_to_plain": bool(same), "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    help="er10k, rmat20, rmat26 (the named workloads), batch (solves/s batched vs plain) "
+                    help="er10k, rmat20, rmat26 (the named workloads), batch (solves/s batched vs plain), "
+                         "serve (Poisson query stream: p50/p99 latency, solves/s) "
                          "or rmatS for the rmat20 recipe at scale S")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (req/s)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="serve: measured seconds")
+    ap.add_argument("--serve-warmup", type=float, default=5.0, help="serve: warm-up seconds")
+    ap.add_argument("--serve-scale", type=int, default=23, help="serve: R-MAT scale of the resident graph")
+    ap.add_argument("--serve-plain", type=int, default=20, help="serve: queries also run plain")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -476,6 +582,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_gpu(args)
 
 

@@ -273,34 +273,38 @@ int fl_batch_create_union(int n_graphs, const int64_t* n_of, const int64_t* nnz_
                           const int32_t* const* cols, int mem_kind, void* cuda_stream, fl_batch** out);
 
 /*
- * fl_batch_create_replicas -- n_inst instances (each with its own costs and
- * client set) on the resident graph g, whose sketches are built and shared:
- * one kernel reads every instance's radius off g's ADS; keys, MIS and
- * assignment run on n_inst device copies of g's CSR (n_inst * n at most
- * 2^31-1 vertices).  Instance i occupies vertices [i*n, (i+1)*n).  g must
- * outlive the batch; rebuilding g's sketches is allowed between solves (the
- * solve checks k and seed against the build).
+ * fl_batch_create_replicas -- up to n_inst instances (each with its own
+ * costs and client set) on the resident graph g, whose sketches are built and
+ * shared: one kernel reads every instance's radius off g's ADS; keys, MIS and
+ * assignment run on device copies of g's CSR (n_inst * n at most 2^31-1
+ * vertices).  Instance i occupies vertices [i*n, (i+1)*n).  The batch's work
+ * runs on cuda_stream (NULL: g's stream), so batches on different streams
+ * overlap on the device; they only read g.  g must outlive the batch;
+ * rebuilding g's sketches is allowed between solves (the solve checks k and
+ * seed against the build).
  */
-int fl_batch_create_replicas(fl_graph* g, int n_inst, fl_batch** out);
+int fl_batch_create_replicas(fl_graph* g, int n_inst, void* cuda_stream, fl_batch** out);
 
 /*
- * fl_batch_solve -- solve every instance: sketches (union batches build them
- * here with k and seed; replica batches require g's build to have used the
- * same k and seed, else FL_ESTATE), radii (Eq. 1), keys, MIS (Alg. 6
- * reading), assignment and objective, as fl_compute_radii ... fl_objective.
- *   cost, client     float64 / uint8 [N] (N = the batch's vertex count,
- *                    instance-major as placed by the create call), memory
- *                    as mem_kind says; cost > 0 finite for facilities, +inf
- *                    otherwise (FL_EINVAL).
+ * fl_batch_solve -- solve the first n_active instances (all of them for a
+ * union batch; 1..n_inst for a replica batch, whose cost of a solve then
+ * scales with n_active): sketches (union batches build them here with k and
+ * seed; replica batches require g's build to have used the same k and seed,
+ * else FL_ESTATE), radii (Eq. 1), keys, MIS (Alg. 6 reading), assignment and
+ * objective, as fl_compute_radii ... fl_objective.
+ *   cost, client     float64 / uint8 [N] (N = the vertex count of the first
+ *                    n_active instances, instance-major as placed by the
+ *                    create call), memory as mem_kind says; cost > 0 finite
+ *                    for facilities, +inf otherwise (FL_EINVAL).
  *   open_out         uint8[N] or NULL.
  *   assign_out       int32[N] or NULL: nearest open facility as an id of the
  *                    vertex's own instance, -1 if none is reachable.
  *   dist_out         int32[N] or NULL.
  *   n_open, objective, dist_sum, n_unserved   per instance, HOST arrays of
- *                    n_inst entries (any may be NULL), as fl_open_facilities
- *                    and fl_objective give them.
+ *                    n_active entries (any may be NULL), as
+ *                    fl_open_facilities and fl_objective give them.
  */
-int fl_batch_solve(fl_batch* b, int k, uint64_t seed, const double* cost, const uint8_t* client,
+int fl_batch_solve(fl_batch* b, int n_active, int k, uint64_t seed, const double* cost, const uint8_t* client,
                    uint8_t* open_out, int32_t* assign_out, int32_t* dist_out, int64_t* n_open, double* objective,
                    int64_t* dist_sum, int64_t* n_unserved, int mem_kind);
 

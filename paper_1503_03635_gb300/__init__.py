@@ -78,8 +78,8 @@ def load(build_if_missing: bool = True):
             "fl_profile_query": ([vp, ci, P64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ci),
             "fl_hop_stats": ([vp, i64, P64, vp, vp, vp, vp], ci),
             "fl_batch_create_union": ([ci, vp, vp, vp, vp, ci, vp, ctypes.POINTER(vp)], ci),
-            "fl_batch_create_replicas": ([vp, ci, ctypes.POINTER(vp)], ci),
-            "fl_batch_solve": ([vp, ci, u64, vp, vp, vp, vp, vp, vp, vp, vp, vp, ci], ci),
+            "fl_batch_create_replicas": ([vp, ci, vp, ctypes.POINTER(vp)], ci),
+            "fl_batch_solve": ([vp, ci, ci, u64, vp, vp, vp, vp, vp, vp, vp, vp, vp, ci], ci),
             "fl_batch_info": ([vp, P64, P64], ci),
             "fl_batch_destroy": ([vp], ci),
             "fl_assign_nearest_noalloc": ([i64, vp, vp, i64, vp, vp, vp, vp], ci),
@@ -316,16 +316,22 @@ class Batch:
         return cls(h)
 
     @classmethod
-    def replicas(cls, graph, n_inst: int):
+    def replicas(cls, graph, n_inst: int, stream=None):
         lib = load()
+        st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
         h = ctypes.c_void_p()
-        _check(lib.fl_batch_create_replicas(graph.handle, int(n_inst), ctypes.byref(h)))
-        return cls(h, keep=graph)
+        _check(lib.fl_batch_create_replicas(graph.handle, int(n_inst), st, ctypes.byref(h)))
+        b = cls(h, keep=graph)
+        b.n_per = graph.n
+        return b
 
-    def solve(self, k: int, seed: int, cost, client, open_out=None, assign_out=None, dist_out=None) -> dict:
-        """Per-vertex outputs (host NumPy arrays unless given) and per-instance
-        n_open, objective, dist_sum, n_unserved."""
-        N, I = self.n_total, self.n_inst
+    def solve(self, k: int, seed: int, cost, client, open_out=None, assign_out=None, dist_out=None,
+              n_active=None) -> dict:
+        """Solve the first n_active instances (default all; fewer only for a
+        replica batch).  Per-vertex outputs (host NumPy arrays unless given)
+        and per-instance n_open, objective, dist_sum, n_unserved."""
+        I = self.n_inst if n_active is None else int(n_active)
+        N = self.n_total if I == self.n_inst else I * self.n_per
         if open_out is None and assign_out is None and dist_out is None and isinstance(cost, np.ndarray):
             open_out = np.zeros(N, np.uint8)
             assign_out = np.zeros(N, np.int32)
@@ -340,7 +346,7 @@ class Batch:
         obj = np.zeros(I, np.float64)
         ds = np.zeros(I, np.int64)
         un = np.zeros(I, np.int64)
-        _check(self._lib.fl_batch_solve(self._h, int(k), int(seed), pc, pm, po, pa, pd,
+        _check(self._lib.fl_batch_solve(self._h, I, int(k), int(seed), pc, pm, po, pa, pd,
                                         n_open.ctypes.data_as(ctypes.c_void_p), obj.ctypes.data_as(ctypes.c_void_p),
                                         ds.ctypes.data_as(ctypes.c_void_p), un.ctypes.data_as(ctypes.c_void_p), kind))
         return dict(open=open_out, assign=assign_out, dist=dist_out, n_open=n_open, objective=obj, dist_sum=ds,

@@ -35,7 +35,7 @@ void destroy_graph(fl_graph* g) {
                     &g->S, &g->Scnt, &g->D[0], &g->D[1], &g->Dcnt[0], &g->Dcnt[1], &g->frontier[0],
                     &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent, &g->stg_grp, &g->gofs, &g->eofs,
                     &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub, &g->ctr, &g->scratch,
-                    &g->relax_aux, &g->U, &g->DM[0], &g->DM[1], &g->PM, &g->vbase};
+                    &g->relax_aux, &g->U, &g->DM[0], &g->DM[1], &g->PM, &g->vbase, &g->vpart};
     for (DBuf* b : bufs) dfree(*b);
     for (cudaEvent_t e : g->prof.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : g->hop_ev)
@@ -47,7 +47,8 @@ void destroy_graph(fl_graph* g) {
 void destroy_solve(fl_solve* s) {
     DBuf* bufs[] = {&s->cost, &s->client, &s->radii, &s->ord, &s->fac_by_ord, &s->bcap, &s->state, &s->claimed,
                     &s->X, &s->stamp, &s->mval, &s->fr[0], &s->fr[1], &s->frval, &s->touched, &s->ulist,
-                    &s->ubuck, &s->bcount, &s->open, &s->assign, &s->dist};
+                    &s->ubuck, &s->bcount, &s->open, &s->assign, &s->dist, &s->key_hi, &s->key_lo,
+                    &s->key_val, &s->obj_tmp, &s->part_T};
     for (DBuf* b : bufs) dfree(*b);
     delete s;
 }
@@ -334,6 +335,7 @@ struct fl_batch {
     std::vector<int64_t> off;      // host: first vertex of each instance, n_inst + 1 entries
     fl::DBuf off_d;                // device copy
     fl::DBuf res;                  // per instance: double obj, int64 n_open, dist_sum, unserved; int32 assign[N]
+    uint64_t ecc_generation = ~0ULL;  // replicas: the base build whose eccentricity bounds U holds
 };
 
 namespace {
@@ -363,6 +365,7 @@ int new_graph(int64_t n, int64_t nnz, cudaStream_t stream, fl_graph** out) {
         if ((rc = dalloc(g->rowp, (size_t)(n + 1) * 8))) break;
         if ((rc = dalloc(g->cols, (size_t)(nnz > 0 ? nnz : 1) * 4))) break;
         if ((rc = dalloc(g->vbase, (size_t)n * 4))) break;
+        if ((rc = dalloc(g->vpart, (size_t)n * 4))) break;
     } while (0);
     if (rc != FL_OK) {
         destroy_graph(g);
@@ -418,6 +421,7 @@ int fl_batch_create_union(int n_graphs, const int64_t* n_of, const int64_t* nnz_
     int rc = new_graph(voff[n_graphs], eoff[n_graphs], st, &b->U);
     if (rc == FL_OK) {
         fl_graph* U = b->U;
+        U->n_parts = n_graphs;
         set_current_prof(&U->prof, st);
         for (int i = 0; i < n_graphs && rc == FL_OK; ++i) {
             // each graph's offsets must run from 0 to its nnz
@@ -463,7 +467,7 @@ int fl_batch_create_union(int n_graphs, const int64_t* n_of, const int64_t* nnz_
     return FL_OK;
 }
 
-int fl_batch_create_replicas(fl_graph* g, int n_inst, fl_batch** out) {
+int fl_batch_create_replicas(fl_graph* g, int n_inst, void* stream, fl_batch** out) {
     if (!out) FL_FAIL(FL_EINVAL, "out is NULL");
     *out = nullptr;
     if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
@@ -477,9 +481,22 @@ int fl_batch_create_replicas(fl_graph* g, int n_inst, fl_batch** out) {
     b->n_inst = n_inst;
     b->off.resize(n_inst + 1);
     for (int i = 0; i <= n_inst; ++i) b->off[i] = (int64_t)i * g->n;
-    ProfScope ps(g);
-    int rc = new_graph((int64_t)n_inst * g->n, (int64_t)n_inst * g->nnz, g->stream, &b->U);
-    if (rc == FL_OK) rc = batch_replicate(g, n_inst, b->U);
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : g->stream;
+    ProfScope ps(nullptr);
+    int rc = FL_OK;
+    // g's stream may be another one: its pending work (the build) must be done
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) rc = status_of(cudaGetLastError(), "sync", __FILE__, __LINE__);
+    if (rc == FL_OK) rc = new_graph((int64_t)n_inst * g->n, (int64_t)n_inst * g->nnz, st, &b->U);
+    if (rc == FL_OK) {
+        b->U->n_parts = n_inst;
+        set_current_prof(&b->U->prof, st);
+        rc = batch_replicate(g, n_inst, b->U);
+    }
+    if (rc == FL_OK) {
+        rc = build_work_lists(b->U);
+        b->U->lists_ready = rc == FL_OK;
+    }
+    if (rc == FL_OK) rc = relax_reserve(b->U);
     if (rc == FL_OK) rc = batch_finish(b);
     if (rc != FL_OK) {
         destroy_batch(b);
@@ -489,18 +506,20 @@ int fl_batch_create_replicas(fl_graph* g, int n_inst, fl_batch** out) {
     return FL_OK;
 }
 
-int fl_batch_solve(fl_batch* b, int k, uint64_t seed, const double* cost, const uint8_t* client,
+int fl_batch_solve(fl_batch* b, int n_active, int k, uint64_t seed, const double* cost, const uint8_t* client,
                    uint8_t* open_out, int32_t* assign_out, int32_t* dist_out, int64_t* n_open, double* objective,
                    int64_t* dist_sum, int64_t* n_unserved, int mem_kind) {
     if (!b || !b->U || !b->s) FL_FAIL(FL_EINVAL, "null batch handle");
     if (!cost || !client) FL_FAIL(FL_EINVAL, "cost and client are required");
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
     if (k < 2 || k > 32) FL_FAIL(FL_EINVAL, "k must be in [2, 32]");
+    if (n_active < 1 || n_active > b->n_inst) FL_FAIL(FL_EINVAL, "n_active must be in [1, n_inst]");
+    if (b->kind == 1 && n_active != b->n_inst) FL_FAIL(FL_EINVAL, "a union batch solves all its instances");
     fl_graph* U = b->U;
     fl_solve* s = b->s;
-    const int64_t N = U->n;
+    const int64_t N = b->off[n_active];
     cudaStream_t st = U->stream;
-    ProfScope ps(b->kind == 2 ? b->base : U);
+    ProfScope ps(U);
     s->have_radii = s->have_open = s->have_assign = 0;
     if (b->kind == 1) {
         FL_TRY(build_sketches(U, k, seed));
@@ -508,42 +527,66 @@ int fl_batch_solve(fl_batch* b, int k, uint64_t seed, const double* cost, const 
         fl_graph* G = b->base;
         if (!G->built || G->k != k || G->seed != seed)
             FL_FAIL(FL_ESTATE, "the resident graph's sketches were not built with this k and seed");
+        if (b->ecc_generation != G->generation) {
+            FL_TRY(batch_replicate_ecc(G, b->n_inst, U));
+            b->ecc_generation = G->generation;
+        }
         U->k = k;
         U->seed = seed;
-        FL_TRY(batch_replicate_ecc(G, b->n_inst, U));
         U->built = 1;
     }
-    s->generation = U->generation;
-    FL_CUDA(cudaMemcpyAsync(s->cost.p, cost, (size_t)N * 8, kind_in(mem_kind), st));
-    FL_CUDA(cudaMemcpyAsync(s->client.p, client, (size_t)N, kind_in(mem_kind), st));
-    if (b->kind == 1)
-        FL_TRY(compute_radii(s));
-    else
-        FL_TRY(compute_radii_multi(b->base, b->n_inst, s->cost.as<double>(), s->client.as<uint8_t>(),
-                                   s->radii.as<double>()));
-    FL_TRY(open_facilities(s));
-    FL_TRY(assign_clients(s));
-    double* obj_d = b->res.as<double>();
-    long long* cnt_d = reinterpret_cast<long long*>(obj_d + b->n_inst);
-    int32_t* asg_d = reinterpret_cast<int32_t*>(cnt_d + 3 * b->n_inst);
-    FL_TRY(batch_objective(s, b->off_d.as<int64_t>(), (int)b->n_inst, obj_d, cnt_d, cnt_d + b->n_inst,
-                           cnt_d + 2 * b->n_inst));
-    if (assign_out) FL_TRY(batch_localize(s, asg_d));
-    FL_TRY(copy_out(open_out, s->open.p, (size_t)N, mem_kind, st));
-    FL_TRY(copy_out(assign_out, asg_d, (size_t)N * 4, mem_kind, st));
-    FL_TRY(copy_out(dist_out, s->dist.p, (size_t)N * 4, mem_kind, st));
-    std::vector<double> h_obj(b->n_inst);
-    std::vector<long long> h_cnt(3 * b->n_inst);
-    FL_CUDA(cudaMemcpyAsync(h_obj.data(), obj_d, (size_t)b->n_inst * 8, cudaMemcpyDeviceToHost, st));
-    FL_CUDA(cudaMemcpyAsync(h_cnt.data(), cnt_d, (size_t)b->n_inst * 24, cudaMemcpyDeviceToHost, st));
-    FL_CUDA(cudaStreamSynchronize(st));
-    for (int64_t i = 0; i < b->n_inst; ++i) {
-        if (objective) objective[i] = h_obj[i];
-        if (n_open) n_open[i] = h_cnt[i];
-        if (dist_sum) dist_sum[i] = h_cnt[b->n_inst + i];
-        if (n_unserved) n_unserved[i] = h_cnt[2 * b->n_inst + i];
+    // the first n_active instances: a prefix view of U (vertices, CSR entries
+    // and work lists of the leading replicas; the lists are sorted by id)
+    fl_graph view = *U;
+    if (b->kind == 2) {
+        const int64_t R = b->n_inst;
+        view.n = N;
+        view.nnz = n_active * b->base->nnz;
+        view.n_low = U->n_low / R * n_active;
+        view.n_hubs = U->n_hubs / R * n_active;
+        view.n_seg = U->n_seg / R * n_active;
     }
-    return FL_OK;
+    s->g = &view;
+    s->generation = view.generation;
+    auto run = [&]() -> int {
+        FL_CUDA(cudaMemcpyAsync(s->cost.p, cost, (size_t)N * 8, kind_in(mem_kind), st));
+        FL_CUDA(cudaMemcpyAsync(s->client.p, client, (size_t)N, kind_in(mem_kind), st));
+        if (b->kind == 1)
+            FL_TRY(compute_radii(s));
+        else
+            FL_TRY(compute_radii_multi(b->base, &view, n_active, s->cost.as<double>(), s->client.as<uint8_t>(),
+                                       s->radii.as<double>()));
+        FL_TRY(open_facilities(s));
+        FL_TRY(assign_clients(s));
+        double* obj_d = b->res.as<double>();
+        long long* cnt_d = reinterpret_cast<long long*>(obj_d + b->n_inst);
+        int32_t* asg_d = reinterpret_cast<int32_t*>(cnt_d + 3 * b->n_inst);
+        FL_TRY(batch_objective(s, b->off_d.as<int64_t>(), n_active, obj_d, cnt_d, cnt_d + b->n_inst,
+                               cnt_d + 2 * b->n_inst));
+        if (assign_out) FL_TRY(batch_localize(s, asg_d));
+        FL_TRY(copy_out(open_out, s->open.p, (size_t)N, mem_kind, st));
+        FL_TRY(copy_out(assign_out, asg_d, (size_t)N * 4, mem_kind, st));
+        FL_TRY(copy_out(dist_out, s->dist.p, (size_t)N * 4, mem_kind, st));
+        std::vector<double> h_obj(n_active);
+        std::vector<long long> h_cnt(3 * b->n_inst);
+        FL_CUDA(cudaMemcpyAsync(h_obj.data(), obj_d, (size_t)n_active * 8, cudaMemcpyDeviceToHost, st));
+        FL_CUDA(cudaMemcpyAsync(h_cnt.data(), cnt_d, (size_t)b->n_inst * 24, cudaMemcpyDeviceToHost, st));
+        FL_CUDA(cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < n_active; ++i) {
+            if (objective) objective[i] = h_obj[i];
+            if (n_open) n_open[i] = h_cnt[i];
+            if (dist_sum) dist_sum[i] = h_cnt[b->n_inst + i];
+            if (n_unserved) n_unserved[i] = h_cnt[2 * b->n_inst + i];
+        }
+        return FL_OK;
+    };
+    const int rc = run();
+    // graph-owned buffers the solve may have (re)allocated through the view
+    // (scan/sort scratch, round scratch; work lists are built at creation)
+    U->scratch = view.scratch;
+    U->relax_aux = view.relax_aux;
+    s->g = U;
+    return rc;
 }
 
 int fl_batch_info(const fl_batch* b, int64_t* n_inst, int64_t* n_total) {

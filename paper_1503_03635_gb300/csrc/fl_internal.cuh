@@ -373,6 +373,8 @@ struct fl_graph {
     // and priorities are those of the local id, so every part is solved
     // exactly as it would be alone.  Empty for an ordinary graph.
     fl::DBuf vbase;                // int32[n] or empty
+    fl::DBuf vpart;                // int32[n]: part of each vertex (with vbase)
+    int64_t n_parts = 0;           // 0: not a union
     fl::DBuf U;                    // uint64[kUW]: the kUW smallest ranks, ascending (kEmpty padded)
     uint64_t ulim = 0;             // largest entry of U
     fl::DBuf DM[2];                // uint64[n*kUWords]: hop delta masks over U
@@ -417,6 +419,8 @@ struct fl_solve {
     fl::DBuf radii;                // double[n]
     fl::DBuf ord, fac_by_ord, bcap, state, claimed;  // MIS state
     fl::DBuf X, stamp, mval, fr[2], frval, touched, ulist, ubuck, bcount;
+    fl::DBuf key_hi, key_lo, key_val, obj_tmp;  // key sort and objective scratch
+    fl::DBuf part_T;               // int32[n_parts]: largest ball radius of a part's undecided facilities
     fl::DBuf open;                 // uint8[n]
     fl::DBuf assign, dist;         // int32[n]
     int64_t n_cand = 0, n_open = 0, mis_rounds = 0;
@@ -466,6 +470,9 @@ struct Relax {
     uint32_t* hub_tag = nullptr;                    // uint32[n_hubs]: round whose push frontier holds the hub
     unsigned long long* hub_val = nullptr;          // uint64[n_hubs]: the hub's snapshotted value
     unsigned long long* ecnt = nullptr;             // device: frontier edge count
+    int32_t* part_cnt = nullptr;                    // device int32[n_parts]: frontier vertices per part
+    const int32_t* part_limit = nullptr;            // device int32[n_parts] or NULL: a part whose limit is
+    int32_t part_round = 0;                         //   below part_round sits the pull rounds out
 };
 // Binds the graph-owned scratch of the rounds to r; call once per sweep
 // family, after r.stamp values of earlier users may have been reused.
@@ -486,6 +493,8 @@ int batch_replicate_ecc(const fl_graph* G, int64_t R, fl_graph* U);
 int batch_objective(fl_solve* s, const int64_t* off_d, int n_inst, double* obj, long long* n_open,
                     long long* dist_sum, long long* unserved);
 int batch_localize(fl_solve* s, int32_t* out);
-int compute_radii_multi(fl_graph* g, int64_t R, const double* cost, const uint8_t* client, double* radii);
+int compute_radii_multi(const fl_graph* src, fl_graph* g, int64_t R, const double* cost, const uint8_t* client,
+                        double* radii);
+int relax_reserve(fl_graph* g);
 
 }  // namespace fl

@@ -31,13 +31,15 @@ int grid_for(int64_t items, int per_block) {
 
 // Part i's CSR, already copied into U (its first n_i row offsets at voff,
 // its columns at eoff), shifted to U's numbering.
-__global__ void k_place_part(int64_t n_i, int64_t nnz_i, int64_t voff, int64_t eoff,
-                             int64_t* __restrict__ rowp, int32_t* __restrict__ cols, int32_t* __restrict__ vbase) {
+__global__ void k_place_part(int part, int64_t n_i, int64_t nnz_i, int64_t voff, int64_t eoff,
+                             int64_t* __restrict__ rowp, int32_t* __restrict__ cols, int32_t* __restrict__ vbase,
+                             int32_t* __restrict__ vpart) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_i || t < nnz_i; t += stride) {
         if (t < n_i) {
             rowp[voff + t] += eoff;
             vbase[voff + t] = (int32_t)voff;
+            vpart[voff + t] = part;
         }
         if (t < nnz_i) cols[eoff + t] += (int32_t)voff;
     }
@@ -60,7 +62,7 @@ __global__ void k_check_parts(const int64_t* __restrict__ rowp, const int32_t* _
 // U = R copies of G: vertex i*n + v, entries i*nnz + e.
 __global__ void k_replicate_csr(const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols, int64_t n,
                                 int64_t nnz, int64_t R, int64_t* __restrict__ Urowp, int32_t* __restrict__ Ucols,
-                                int32_t* __restrict__ vbase) {
+                                int32_t* __restrict__ vbase, int32_t* __restrict__ vpart) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t total_e = R * nnz, total_v = R * n;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total_e || t <= total_v; t += stride) {
@@ -72,6 +74,7 @@ __global__ void k_replicate_csr(const int64_t* __restrict__ rowp, const int32_t*
             const int64_t i = t / n, v = t - i * n;
             Urowp[t] = i * nnz + rowp[v];
             vbase[t] = (int32_t)(i * n);
+            vpart[t] = (int32_t)i;
         } else if (t == total_v) {
             Urowp[t] = total_e;
         }
@@ -145,8 +148,6 @@ __global__ void k_localize(const int32_t* __restrict__ assign, const int32_t* __
 
 }  // namespace
 
-// Radii of R instances from one graph's ADS (k_solve.cu).
-int compute_radii_multi(fl_graph* g, int64_t R, const double* cost, const uint8_t* client, double* radii);
 
 int batch_place_parts(fl_graph* U, const std::vector<int64_t>& voff, const std::vector<int64_t>& eoff) {
     cudaStream_t st = U->stream;
@@ -154,8 +155,8 @@ int batch_place_parts(fl_graph* U, const std::vector<int64_t>& voff, const std::
     for (int i = 0; i < n_parts; ++i) {
         const int64_t n_i = voff[i + 1] - voff[i], nnz_i = eoff[i + 1] - eoff[i];
         FL_LAUNCH(kProfOther, k_place_part<<<grid_for(std::max(n_i, nnz_i), 256), 256, 0, st>>>(
-                                  n_i, nnz_i, voff[i], eoff[i], U->rowp.as<int64_t>(), U->cols.as<int32_t>(),
-                                  U->vbase.as<int32_t>()));
+                                  i, n_i, nnz_i, voff[i], eoff[i], U->rowp.as<int64_t>(), U->cols.as<int32_t>(),
+                                  U->vbase.as<int32_t>(), U->vpart.as<int32_t>()));
     }
     FL_CUDA(cudaGetLastError());
     return FL_OK;
@@ -177,7 +178,7 @@ int batch_replicate(const fl_graph* G, int64_t R, fl_graph* U) {
     cudaStream_t st = U->stream;
     FL_LAUNCH(kProfOther, k_replicate_csr<<<grid_for(std::max(R * G->nnz, R * G->n + 1), 256), 256, 0, st>>>(
                               G->rowp.as<int64_t>(), G->cols.as<int32_t>(), G->n, G->nnz, R, U->rowp.as<int64_t>(),
-                              U->cols.as<int32_t>(), U->vbase.as<int32_t>()));
+                              U->cols.as<int32_t>(), U->vbase.as<int32_t>(), U->vpart.as<int32_t>()));
     FL_CUDA(cudaGetLastError());
     return FL_OK;
 }

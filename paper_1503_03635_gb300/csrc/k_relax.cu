@@ -35,13 +35,32 @@ __device__ __forceinline__ bool in_front(const uint32_t* __restrict__ bm, int32_
 // whose value changed in the previous round can lower a value, so a pull
 // reads the value of a neighbour only when its bit is set; the bitmap (n/8
 // bytes) stays in L2 while the values do not.
-__global__ void k_bitmap(const uint32_t* __restrict__ stamp, uint32_t sv, int64_t n, uint32_t* __restrict__ bm) {
+//
+// In a graph made of disjoint parts (batches) the frontier is also counted
+// per part: a part without frontier vertices has no vertex that can change,
+// and pull rounds skip it.  A part whose limit is below `round` no longer
+// needs its values (nothing of it reads them any more) and sits out too.
+__global__ void k_bitmap(const uint32_t* __restrict__ stamp, uint32_t sv, int64_t n, uint32_t* __restrict__ bm,
+                         const int32_t* __restrict__ vpart, int32_t* __restrict__ part_cnt,
+                         const int32_t* __restrict__ part_limit, int32_t round) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
         const int64_t v = base + lane_id();
-        const unsigned w = __ballot_sync(kFull, v < n && stamp[v] == sv);
+        const bool in = v < n && stamp[v] == sv && !(part_limit && part_limit[vpart[v]] < round);
+        const unsigned w = __ballot_sync(kFull, in);
         if (lane_id() == 0) bm[base >> 5] = w;
+        if (vpart && w) {
+            const int32_t p = v < n ? vpart[v] : -1;
+            const unsigned same = __match_any_sync(kFull, p);
+            const int lead = __ffs(same & w) - 1;  // first frontier lane of this part
+            if (in && lane_id() == lead) atomicAdd(&part_cnt[p], __popc(same & w));
+        }
     }
+}
+
+__device__ __forceinline__ bool part_idle(const int32_t* __restrict__ vpart, const int32_t* __restrict__ part_cnt,
+                                          int32_t v) {
+    return vpart && __ldg(&part_cnt[__ldg(&vpart[v])]) == 0;
 }
 
 // Values >= `limit` are ignored: unset entries (BFS) or values of an earlier
@@ -83,15 +102,17 @@ __global__ void __launch_bounds__(256) k_pull_low(const int32_t* __restrict__ li
                                                   const uint32_t* __restrict__ bm,
                                                   const unsigned long long* __restrict__ X,
                                                   unsigned long long* __restrict__ Xn, uint32_t* __restrict__ stamp,
-                                                  uint32_t sv, unsigned long long* __restrict__ n_changed) {
+                                                  uint32_t sv, unsigned long long* __restrict__ n_changed,
+                                                  const int32_t* __restrict__ vpart,
+                                                  const int32_t* __restrict__ part_cnt) {
     const int lane = lane_id();
     const int sub = lane & 7;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long changed = 0;
     for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 4 < n_list; w += warps) {
         const int64_t i = w * 4 + (lane >> 3);
-        const bool have = i < n_list;
-        const int32_t v = have ? list[i] : 0;
+        const int32_t v = i < n_list ? list[i] : 0;
+        const bool have = i < n_list && !part_idle(vpart, part_cnt, v);
         const unsigned long long own = have ? X[v] : ~0ULL;
         const bool work = have && !(settle && own < limit);
         const int64_t beg = work ? rowp[v] : 0, end = work ? rowp[v + 1] : 0;
@@ -119,14 +140,16 @@ __global__ void __launch_bounds__(256) k_pull_segs(const int32_t* __restrict__ s
                                                    const uint32_t* __restrict__ bm,
                                                    const unsigned long long* __restrict__ X,
                                                    unsigned long long* __restrict__ Xn, uint32_t* __restrict__ stamp,
-                                                   uint32_t sv, unsigned long long* __restrict__ n_changed) {
+                                                   uint32_t sv, unsigned long long* __restrict__ n_changed,
+                                                   const int32_t* __restrict__ vpart,
+                                                   const int32_t* __restrict__ part_cnt) {
     const int lane = lane_id();
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t sidx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sidx < n_seg; sidx += warps) {
         const int32_t h = seg_hub[sidx];
         const int32_t v = hub_list[h];
         const unsigned long long own = X[v];
-        if (settle && own < limit) continue;
+        if ((settle && own < limit) || part_idle(vpart, part_cnt, v)) continue;
         const int64_t e0 = rowp[v] + (sidx - hub_seg[h]) * kSeg;
         const int64_t e1 = min(e0 + (int64_t)kSeg, rowp[v + 1]);
         unsigned long long m = pull_min(cols, e0 + lane, e1, 32, bm, X, add, limit, ~0ULL);
@@ -285,6 +308,13 @@ int relax_collect_epoch(fl_graph* g, const unsigned long long* X, unsigned long 
     return FL_OK;
 }
 
+// Work lists and round scratch of g allocated ahead (so that a solve on a
+// prefix view of g allocates nothing graph-owned).
+int relax_reserve(fl_graph* g) {
+    Relax r;
+    return relax_begin(g, r);
+}
+
 int relax_begin(fl_graph* g, Relax& r) {
     if (!g->lists_ready) {
         FL_TRY(build_work_lists(g));
@@ -294,12 +324,14 @@ int relax_begin(fl_graph* g, Relax& r) {
     const size_t off_tag = ((bm_words * 4 + 255) / 256) * 256;
     const size_t off_val = off_tag + (((size_t)g->n_hubs * 4 + 255) / 256) * 256;
     const size_t off_cnt = off_val + (((size_t)g->n_hubs * 8 + 255) / 256) * 256;
-    FL_TRY(dalloc(g->relax_aux, off_cnt + 256));
+    const size_t off_part = off_cnt + 256;
+    FL_TRY(dalloc(g->relax_aux, off_part + (size_t)(g->n_parts + 1) * 4));
     char* base = g->relax_aux.as<char>();
     r.bm = reinterpret_cast<uint32_t*>(base);
     r.hub_tag = reinterpret_cast<uint32_t*>(base + off_tag);
     r.hub_val = reinterpret_cast<unsigned long long*>(base + off_val);
     r.ecnt = reinterpret_cast<unsigned long long*>(base + off_cnt);
+    r.part_cnt = reinterpret_cast<int32_t*>(base + off_part);
     if (g->n_hubs > 0) FL_CUDA(cudaMemsetAsync(r.hub_tag, 0, (size_t)g->n_hubs * 4, g->stream));
     FL_CUDA(cudaMemsetAsync(r.ecnt, 0, 256, g->stream));
     return FL_OK;
@@ -352,17 +384,20 @@ int relax_round(fl_graph* g, Relax& r, unsigned long long add, uint32_t sv, int 
         FL_CUDA(cudaMemcpyAsync(r.h_cnt, &r.cnt[r.fc], 8, cudaMemcpyDeviceToHost, st));
     } else {
         unsigned long long* Xn = r.X[r.cur ^ 1];
-        FL_LAUNCH(cls, k_bitmap<<<grid_for(n, 256), 256, 0, st>>>(r.stamp, r.sv_prev, n, r.bm));
+        const int32_t* vpart = g->n_parts > 0 ? g->vpart.as<int32_t>() : nullptr;
+        if (vpart) FL_CUDA(cudaMemsetAsync(r.part_cnt, 0, (size_t)g->n_parts * 4, st));
+        FL_LAUNCH(cls, k_bitmap<<<grid_for(n, 256), 256, 0, st>>>(r.stamp, r.sv_prev, n, r.bm, vpart, r.part_cnt,
+                                                                  vpart ? r.part_limit : nullptr, r.part_round));
         FL_CUDA(cudaMemcpyAsync(Xn, X, (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
         FL_CUDA(cudaMemsetAsync(&r.cnt[2], 0, 8, st));
         if (g->n_low > 0)
             FL_LAUNCH(cls, k_pull_low<<<grid_for((g->n_low + 3) / 4, 8), 256, 0, st>>>(
                                g->low_list.as<int32_t>(), g->n_low, rowp, cols, add, r.limit, r.settle, r.bm, X, Xn,
-                               r.stamp, sv, &r.cnt[2]));
+                               r.stamp, sv, &r.cnt[2], vpart, r.part_cnt));
         if (g->n_seg > 0)
             FL_LAUNCH(cls, k_pull_segs<<<grid_for(g->n_seg, 8), 256, 0, st>>>(
                                g->seg_hub.as<int32_t>(), g->n_seg, g->hub_seg.as<int64_t>(), hub_list, rowp, cols, add,
-                               r.limit, r.settle, r.bm, X, Xn, r.stamp, sv, &r.cnt[2]));
+                               r.limit, r.settle, r.bm, X, Xn, r.stamp, sv, &r.cnt[2], vpart, r.part_cnt));
         FL_CUDA(cudaGetLastError());
         r.cur ^= 1;
         r.list_valid = false;

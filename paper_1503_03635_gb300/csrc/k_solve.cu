@@ -247,19 +247,21 @@ int compute_radii(fl_solve* s) {
     return FL_OK;
 }
 
-// Radii of R instances on one built graph (batches): cost, client and radii
-// are R*n arrays, instance-major.
-int compute_radii_multi(fl_graph* g, int64_t R, const double* cost, const uint8_t* client, double* radii) {
+// Radii of R instances on the built graph src (batches): cost, client and
+// radii are R*n arrays, instance-major.  Runs on g's stream with g's
+// counters (src is only read).
+int compute_radii_multi(const fl_graph* src, fl_graph* g, int64_t R, const double* cost, const uint8_t* client,
+                        double* radii) {
     cudaStream_t st = g->stream;
+    const int64_t n = src->n;
     FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st));
-    FL_LAUNCH(kProfRadius, k_check_costs<<<grid_for(g->n * R, 256), 256, 0, st>>>(cost, g->n * R,
-                                                                                 g->ctr.as<Counters>()));
+    FL_LAUNCH(kProfRadius, k_check_costs<<<grid_for(n * R, 256), 256, 0, st>>>(cost, n * R, g->ctr.as<Counters>()));
     FL_CUDA(cudaGetLastError());
     FL_TRY(read_counters(g));
     if (g->h_ctr->error) FL_FAIL(FL_EINVAL, "open_cost must be finite and > 0 for facilities, +inf otherwise");
-    FL_LAUNCH(kProfRadius, k_radius<true><<<grid_for(g->n * R, 8), 256, 0, st>>>(
-                               g->n, R, cost, client, g->gofs.as<int64_t>(), g->eofs.as<int64_t>(),
-                               g->ginfo.as<uint32_t>(), g->gwt.as<double>(), g->eid.as<int32_t>(), radii));
+    FL_LAUNCH(kProfRadius, k_radius<true><<<grid_for(n * R, 8), 256, 0, st>>>(
+                               n, R, cost, client, src->gofs.as<int64_t>(), src->eofs.as<int64_t>(),
+                               src->ginfo.as<uint32_t>(), src->gwt.as<double>(), src->eid.as<int32_t>(), radii));
     FL_CUDA(cudaGetLastError());
     return FL_OK;
 }
@@ -310,13 +312,26 @@ __global__ void k_ordinals(const uint32_t* __restrict__ sorted_f, int64_t m, con
 
 // ------------------------------------------------------------------ MIS rounds (phase iii)
 
+// Bucket sizes by ball radius, the largest radius, and (for a graph made of
+// parts) each part's largest radius; maxima reduced per warp first.
 __global__ void k_bucket_count(const int32_t* __restrict__ ulist, int64_t n_u, const int32_t* __restrict__ bcap,
-                               int32_t* __restrict__ bcount, unsigned long long* __restrict__ tmax) {
+                               int32_t* __restrict__ bcount, unsigned long long* __restrict__ tmax,
+                               const int32_t* __restrict__ vpart, int32_t* __restrict__ part_T) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_u; i += stride) {
-        int32_t b = bcap[ulist[i]];
-        atomicAdd(&bcount[b], 1);
-        atomicMax(tmax, (unsigned long long)b);
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_u; base += stride) {
+        const int64_t i = base + lane_id();
+        const bool valid = i < n_u;
+        const int32_t f = valid ? ulist[i] : 0;
+        const int32_t b = valid ? bcap[f] : 0;
+        if (valid) atomicAdd(&bcount[b], 1);
+        const unsigned mx = __reduce_max_sync(kFull, (unsigned)b);
+        if (lane_id() == 0) atomicMax(tmax, (unsigned long long)mx);
+        if (vpart) {
+            const int32_t p = valid ? vpart[f] : -1;
+            const unsigned same = __match_any_sync(kFull, p);
+            const unsigned pm = __reduce_max_sync(same, (unsigned)b);
+            if (valid && lane_id() == __ffs(same) - 1) atomicMax(&part_T[p], (int)pm);
+        }
     }
 }
 
@@ -437,24 +452,23 @@ int open_facilities(fl_solve* s) {
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(s->frval.as<char>() + (size_t)n * 8);
     // cnt[0], cnt[1]: frontier counts; cnt[2]: changed count (dense rounds);
     // cnt[3]: undecided; cnt[4]: T max; cnt[5]: open list; cnt[6]: touched
-    DBuf hi, lo, val;
-    auto free_keys = [&]() { dfree(hi); dfree(lo); dfree(val); };
-    int rc = FL_OK;
-    if ((rc = dalloc(hi, (size_t)n * 8)) || (rc = dalloc(lo, (size_t)n * 8)) || (rc = dalloc(val, (size_t)n * 4))) {
-        free_keys();
-        return rc;
-    }
+    // solve-owned, grow-only scratch: a cudaFree per solve would synchronise
+    // the whole device (and stall other solves running on other streams)
+    DBuf& hi = s->key_hi;
+    DBuf& lo = s->key_lo;
+    DBuf& val = s->key_val;
+    FL_TRY(dalloc(hi, (size_t)n * 8));
+    FL_TRY(dalloc(lo, (size_t)n * 8));
+    FL_TRY(dalloc(val, (size_t)n * 4));
     FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st));
     FL_LAUNCH(kProfKeys, k_candidates<<<grid_for(n, 256), 256, 0, st>>>(s->radii.as<double>(), n, g->seed,
                                                    g->vbase.p ? g->vbase.as<int32_t>() : nullptr, hi.as<uint64_t>(),
                                                    lo.as<uint64_t>(), val.as<uint32_t>(), s->state.as<uint8_t>(),
                                                    g->ctr.as<Counters>()));
-    rc = read_counters(g);
-    if (rc) { free_keys(); return rc; }
+    FL_TRY(read_counters(g));
     const int64_t m = (int64_t)g->h_ctr->aux0;
     s->n_cand = m;
-    rc = sort_pairs_u128(hi.as<uint64_t>(), lo.as<uint64_t>(), val.as<uint32_t>(), m, st, g->scratch);
-    if (rc) { free_keys(); return rc; }
+    FL_TRY(sort_pairs_u128(hi.as<uint64_t>(), lo.as<uint64_t>(), val.as<uint32_t>(), m, st, g->scratch));
     int32_t* ulist[2] = {s->ulist.as<int32_t>(), s->ulist.as<int32_t>() + n};
     FL_CUDA(cudaMemsetAsync(cnt, 0, 64, st));
     if (m > 0) {
@@ -463,7 +477,6 @@ int open_facilities(fl_solve* s) {
                                                      s->fac_by_ord.as<int32_t>(), s->bcap.as<int32_t>(), ulist[0],
                                                      &cnt[4]));
     }
-    free_keys();
     FL_CUDA(cudaGetLastError());
     unsigned long long bmax = 0;
     FL_CUDA(cudaMemcpyAsync(&bmax, &cnt[4], 8, cudaMemcpyDeviceToHost, st));
@@ -471,7 +484,7 @@ int open_facilities(fl_solve* s) {
     FL_CUDA(cudaMemsetAsync(s->X.p, 0xff, (size_t)n * 16, st));
     FL_CUDA(cudaMemsetAsync(s->stamp.p, 0, (size_t)n * 4, st));
     FL_CUDA(cudaStreamSynchronize(st));
-    DBuf bcount_d;
+    DBuf& bcount_d = s->bcount;
     FL_TRY(dalloc(bcount_d, (bmax + 2) * 4 * 2));
     int32_t* bcount = bcount_d.as<int32_t>();
     int32_t* cursor = bcount + (bmax + 2);
@@ -486,9 +499,14 @@ int open_facilities(fl_solve* s) {
     r.stamp = s->stamp.as<uint32_t>();
     r.cnt = cnt;
     r.h_cnt = &g->h_ctr->aux3;
-    if ((rc = relax_begin(g, r)) != FL_OK) {
-        dfree(bcount_d);
-        return rc;
+    FL_TRY(relax_begin(g, r));
+    // a graph made of parts (batches): each part's gather sweep stops after
+    // its own largest ball radius
+    const int32_t* vpart = g->n_parts > 0 ? g->vpart.as<int32_t>() : nullptr;
+    int32_t* part_T = nullptr;
+    if (vpart) {
+        FL_TRY(dalloc(s->part_T, (size_t)g->n_parts * 4));
+        part_T = s->part_T.as<int32_t>();
     }
     int32_t* touched = s->touched.as<int32_t>();
     uint32_t epoch = 0;
@@ -497,15 +515,13 @@ int open_facilities(fl_solve* s) {
     int cu = 0;
     int64_t rounds = 0;
     while (n_u > 0) {
-        if (++rounds > m + 1) {
-            dfree(bcount_d);
-            FL_FAIL(FL_ETIMEOUT, "greedy MIS did not converge");
-        }
+        if (++rounds > m + 1) FL_FAIL(FL_ETIMEOUT, "greedy MIS did not converge");
         // bucket the undecided facilities by ball radius
         FL_CUDA(cudaMemsetAsync(bcount, 0, (bmax + 1) * 4, st));
         FL_CUDA(cudaMemsetAsync(&cnt[4], 0, 8, st));
-        FL_LAUNCH(kProfMis, k_bucket_count<<<grid_for(n_u, 256), 256, 0, st>>>(ulist[cu], n_u, s->bcap.as<int32_t>(),
-                                                                               bcount, &cnt[4]));
+        if (part_T) FL_CUDA(cudaMemsetAsync(part_T, 0xff, (size_t)g->n_parts * 4, st));  // -1: no undecided facility
+        FL_LAUNCH(kProfMis, k_bucket_count<<<grid_for(n_u, 256), 256, 0, st>>>(
+                                ulist[cu], n_u, s->bcap.as<int32_t>(), bcount, &cnt[4], vpart, part_T));
         FL_CUDA(cudaGetLastError());
         unsigned long long T64 = 0;
         FL_CUDA(cudaMemcpyAsync(&T64, &cnt[4], 8, cudaMemcpyDeviceToHost, st));
@@ -568,7 +584,9 @@ int open_facilities(fl_solve* s) {
             FL_LAUNCH(kProfMis, k_decide<<<grid_for(hcount[0], 256), 256, 0, st>>>(
                                     ub + hoff[0], hcount[0], r.X[r.cur], hi_g, s->ord.as<uint32_t>(),
                                     s->state.as<uint8_t>(), g->ctr.as<Counters>()));
+        r.part_limit = part_T;
         for (int b = 1; b <= T; ++b) {
+            r.part_round = b;
             if (r.n_front > 0) FL_TRY(relax_round(g, r, 0ULL, sg0 + b, kProfMis));
             else r.sv_prev = sg0 + b;
             if (hcount[b] > 0)
@@ -577,6 +595,7 @@ int open_facilities(fl_solve* s) {
                                         s->state.as<uint8_t>(), g->ctr.as<Counters>()));
         }
         sv = sg0 + T + 1;
+        r.part_limit = nullptr;
         FL_CUDA(cudaGetLastError());
 
         // ---- claim the balls of this round's winners; keep the undecided
@@ -590,14 +609,10 @@ int open_facilities(fl_solve* s) {
         unsigned long long nu = 0;
         FL_CUDA(cudaMemcpyAsync(&nu, &cnt[3], 8, cudaMemcpyDeviceToHost, st));
         FL_TRY(read_counters(g));
-        if (g->h_ctr->error) {
-            dfree(bcount_d);
-            FL_FAIL(FL_ECUDA, "greedy MIS: inconsistent gather state");
-        }
+        if (g->h_ctr->error) FL_FAIL(FL_ECUDA, "greedy MIS: inconsistent gather state");
         n_u = (int64_t)nu;
         cu ^= 1;
     }
-    dfree(bcount_d);
     s->mis_rounds = rounds;
     // open set
     FL_CUDA(cudaMemsetAsync(&cnt[5], 0, 8, st));
@@ -652,7 +667,7 @@ __global__ void k_objective(int64_t n, const uint8_t* __restrict__ open, const d
 int objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserved) {
     fl_graph* g = s->g;
     cudaStream_t st = g->stream;
-    DBuf tmp;
+    DBuf& tmp = s->obj_tmp;
     FL_TRY(dalloc(tmp, kObjBlocks * 8 + 64));
     double* partial = tmp.as<double>();
     unsigned long long* sums = reinterpret_cast<unsigned long long*>(partial + kObjBlocks);
@@ -669,7 +684,7 @@ int objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserved) 
     if (e == cudaSuccess) e = cudaMemcpyAsync(hs, sums, 16, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = status_of(e, "objective", __FILE__, __LINE__);
-    dfree(tmp);
+
     if (rc) return rc;
     double open_cost = 0.0;
     for (int b = 0; b < kObjBlocks; ++b) open_cost += hp[b];

@@ -100,6 +100,16 @@ def test_replica_batch_matches_plain_solves_on_the_resident_graph():
         s.close()
         want = dict(open=op, assign=a, dist=d, n_open=no, objective=obj, dist_sum=ds, n_unserved=un)
         _check_instance(res, i * n, (i + 1) * n, i, want)
+    # the first 2 instances alone (a prefix of the batch), then all again
+    part = b.solve(k, seed, np.concatenate(costs[:2]), np.concatenate(clients[:2]), n_active=2)
+    assert len(part["open"]) == 2 * n and len(part["objective"]) == 2
+    for i in range(2):
+        _check_instance(part, i * n, (i + 1) * n, i, {key: res[key][i * n:(i + 1) * n] if key in
+                                                      ("open", "assign", "dist") else res[key][i]
+                                                      for key in res})
+    again = b.solve(k, seed, np.concatenate(costs), np.concatenate(clients))
+    for key in ("open", "assign", "dist", "n_open", "dist_sum", "n_unserved"):
+        assert np.array_equal(again[key], res[key])
     # the solve must use the resident graph's k and seed
     with pytest.raises(fl.FLError):
         b.solve(k, seed + 1, np.concatenate(costs), np.concatenate(clients))
