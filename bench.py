@@ -491,7 +491,7 @@ def run_serve(args):
     costs = flsynth.loguniform(len(arrivals), flsynth.QUERY_SEED + 2, 10.0, 1.0e3)
     qs = [serve.Query(costs[i], client_seed=flsynth.QUERY_SEED * 1000003 + i, client_frac=min(1.0, sizes[i] / n))
           for i in range(len(arrivals))]
-    srv = serve.Server(g, k, seed, workers=2, keep_open_mask=True)
+    srv = serve.Server(g, k, seed, workers=args.serve_workers, max_slots=args.serve_slots, keep_open_mask=True)
     clocks = Clocks(local)
     clocks.start()
     t0 = time.perf_counter()
@@ -544,7 +544,8 @@ def run_serve(args):
                        "arrivals": f"Poisson {rate} req/s, {warm} s warm-up + {dur} s measured",
                        "query": "clients: each vertex with probability m/n, m log-uniform in [1e3, 1e6]; "
                                 "every vertex a facility, one cost log-uniform in [10, 1000]",
-                       "workers": 2, "slots_per_worker": srv.slots, "max_pending": srv.max_pending},
+                       "workers": args.serve_workers, "slots_per_worker": srv.slots,
+                       "max_pending": srv.max_pending},
             "latency_ms": {"p50": lat.get("p50_ms"), "p99": lat.get("p99_ms"), "mean": lat.get("mean_ms"),
                            "max": lat.get("max_ms")},
             "offered": len(measured), "served": len(served), "refused": srv.rejected,
@@ -575,6 +576,8 @@ def main():
     ap.add_argument("--serve-warmup", type=float, default=5.0, help="serve: warm-up seconds")
     ap.add_argument("--serve-scale", type=int, default=23, help="serve: R-MAT scale of the resident graph")
     ap.add_argument("--serve-plain", type=int, default=20, help="serve: queries also run plain")
+    ap.add_argument("--serve-workers", type=int, default=2, help="serve: worker threads (streams)")
+    ap.add_argument("--serve-slots", type=int, default=4, help="serve: most queries per batch solve")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
