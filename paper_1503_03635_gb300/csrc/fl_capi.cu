@@ -35,7 +35,8 @@ void destroy_graph(fl_graph* g) {
                     &g->S, &g->Scnt, &g->D[0], &g->D[1], &g->Dcnt[0], &g->Dcnt[1], &g->frontier[0],
                     &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent, &g->stg_grp, &g->gofs, &g->eofs,
                     &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub, &g->ctr, &g->scratch,
-                    &g->relax_aux, &g->U, &g->DM[0], &g->DM[1], &g->PM, &g->vbase, &g->vpart};
+                    &g->relax_aux, &g->U, &g->DM[0], &g->DM[1], &g->PM, &g->vbase, &g->vpart, &g->rid,
+                    &g->inv};
     for (DBuf* b : bufs) dfree(*b);
     for (cudaEvent_t e : g->prof.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : g->hop_ev)
@@ -48,7 +49,7 @@ void destroy_solve(fl_solve* s) {
     DBuf* bufs[] = {&s->cost, &s->client, &s->radii, &s->ord, &s->fac_by_ord, &s->bcap, &s->state, &s->claimed,
                     &s->X, &s->stamp, &s->mval, &s->fr[0], &s->fr[1], &s->frval, &s->touched, &s->ulist,
                     &s->ubuck, &s->bcount, &s->open, &s->assign, &s->dist, &s->key_hi, &s->key_lo,
-                    &s->key_val, &s->obj_tmp, &s->part_T};
+                    &s->key_val, &s->obj_tmp, &s->part_T, &s->io};
     for (DBuf* b : bufs) dfree(*b);
     delete s;
 }
@@ -119,6 +120,7 @@ int fl_graph_create(int64_t n, const int64_t* row_off, const int32_t* cols, int6
         if (e != cudaSuccess) { rc = status_of(e, "CSR upload", __FILE__, __LINE__); break; }
         set_current_prof(&g->prof, g->stream);
         if ((rc = validate_csr(g))) break;
+        if ((rc = relabel_graph(g))) break;
     } while (0);
     if (rc != FL_OK) {
         destroy_graph(g);
@@ -192,13 +194,30 @@ int fl_export_sketches(fl_graph* g, uint64_t* S, int32_t* cnt, int mem_kind) {
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
     ProfScope ps(g);
     cudaStream_t st = g->stream;
-    FL_TRY(copy_out(S, g->S.p, (size_t)g->n * g->k * 8, mem_kind, st));
+    if (S && g->relabelled) {
+        DBuf tmp;
+        FL_TRY(dalloc(tmp, (size_t)g->n * g->k * 8));
+        int rc = sketch_rows_original(g, tmp.as<uint64_t>());
+        if (!rc) rc = copy_out(S, tmp.p, (size_t)g->n * g->k * 8, mem_kind, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        dfree(tmp);
+        if (rc) return rc;
+        if (e != cudaSuccess) return status_of(e, "export sketches", __FILE__, __LINE__);
+    } else {
+        FL_TRY(copy_out(S, g->S.p, (size_t)g->n * g->k * 8, mem_kind, st));
+    }
     if (cnt) {
         DBuf tmp;
-        FL_TRY(dalloc(tmp, (size_t)g->n * 4));
+        FL_TRY(dalloc(tmp, (size_t)g->n * 8));
         FL_LAUNCH(kProfOther, k_export_sketch<<<152 * 4, 256, 0, st>>>(g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->n,
                                                  tmp.as<int32_t>()));
-        int rc = copy_out(cnt, tmp.p, (size_t)g->n * 4, mem_kind, st);
+        int32_t* src = tmp.as<int32_t>();
+        int rc = FL_OK;
+        if (g->relabelled) {
+            rc = permute_vertices<int32_t>(g, src, src + g->n, 1, false, g->stream);
+            src += g->n;
+        }
+        if (!rc) rc = copy_out(cnt, src, (size_t)g->n * 4, mem_kind, st);
         cudaError_t e = cudaStreamSynchronize(st);
         dfree(tmp);
         if (rc) return rc;
@@ -215,25 +234,58 @@ int fl_export_ads(fl_graph* g, int64_t* gofs, int64_t* eofs, int32_t* ghop, int3
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
     ProfScope ps(g);
     cudaStream_t st = g->stream;
-    FL_TRY(copy_out(gofs, g->gofs.p, (size_t)(g->n + 1) * 8, mem_kind, st));
-    FL_TRY(copy_out(eofs, g->eofs.p, (size_t)(g->n + 1) * 8, mem_kind, st));
-    FL_TRY(copy_out(gwt, g->gwt.p, (size_t)g->n_groups * 8, mem_kind, st));
-    FL_TRY(copy_out(eid, g->eid.p, (size_t)g->n_entries * 4, mem_kind, st));
+    const size_t n1 = (size_t)(g->n + 1), m = (size_t)g->n_groups, ne = (size_t)g->n_entries;
+    // a relabelled graph's ADS in original vertex order and ids (device copy)
+    DBuf orig;
+    const int64_t* src_gofs = g->gofs.as<int64_t>();
+    const int64_t* src_eofs = g->eofs.as<int64_t>();
+    const uint32_t* src_ginfo = g->ginfo.as<uint32_t>();
+    const double* src_gwt = g->gwt.as<double>();
+    const int32_t* src_eid = g->eid.as<int32_t>();
+    if (g->relabelled) {
+        FL_TRY(dalloc(orig, n1 * 16 + m * 12 + ne * 4 + 64));
+        int64_t* go = orig.as<int64_t>();
+        int64_t* eo = go + n1;
+        double* wt = reinterpret_cast<double*>(eo + n1);
+        uint32_t* gi = reinterpret_cast<uint32_t*>(wt + m);
+        int32_t* ei = reinterpret_cast<int32_t*>(gi + m);
+        int rc = ads_original(g, go, eo, gi, wt, ei);
+        if (rc) {
+            dfree(orig);
+            return rc;
+        }
+        src_gofs = go;
+        src_eofs = eo;
+        src_ginfo = gi;
+        src_gwt = wt;
+        src_eid = ei;
+    }
+    int rc0 = copy_out(gofs, src_gofs, n1 * 8, mem_kind, st);
+    if (!rc0) rc0 = copy_out(eofs, src_eofs, n1 * 8, mem_kind, st);
+    if (!rc0) rc0 = copy_out(gwt, src_gwt, m * 8, mem_kind, st);
+    if (!rc0) rc0 = copy_out(eid, src_eid, ne * 4, mem_kind, st);
+    if (rc0) {
+        dfree(orig);
+        return rc0;
+    }
     if (ghop || gcnt || gcounted) {
         DBuf tmp;
-        const size_t m = (size_t)g->n_groups;
         FL_TRY(dalloc(tmp, m * 12 + 16));
         int32_t* h = tmp.as<int32_t>();
-        FL_LAUNCH(kProfOther, k_unpack_ginfo<<<152 * 4, 256, 0, st>>>(g->ginfo.as<uint32_t>(), (int64_t)m, h, h + m, h + 2 * m));
+        FL_LAUNCH(kProfOther, k_unpack_ginfo<<<152 * 4, 256, 0, st>>>(src_ginfo, (int64_t)m, h, h + m, h + 2 * m));
         int rc = copy_out(ghop, h, m * 4, mem_kind, st);
         if (!rc) rc = copy_out(gcnt, h + m, m * 4, mem_kind, st);
         if (!rc) rc = copy_out(gcounted, h + 2 * m, m * 4, mem_kind, st);
         cudaError_t e = cudaStreamSynchronize(st);
         dfree(tmp);
-        if (rc) return rc;
-        if (e != cudaSuccess) return status_of(e, "export ADS", __FILE__, __LINE__);
+        if (rc || e != cudaSuccess) {
+            dfree(orig);
+            return rc ? rc : status_of(e, "export ADS", __FILE__, __LINE__);
+        }
     }
-    FL_CUDA(cudaStreamSynchronize(st));
+    cudaError_t e = cudaStreamSynchronize(st);
+    dfree(orig);
+    if (e != cudaSuccess) return status_of(e, "export ADS", __FILE__, __LINE__);
     return FL_OK;
 }
 
@@ -273,10 +325,25 @@ int fl_compute_radii(fl_solve* s, const double* open_cost, const uint8_t* client
     ProfScope ps(g);
     cudaStream_t st = g->stream;
     s->have_radii = s->have_open = s->have_assign = 0;
-    FL_CUDA(cudaMemcpyAsync(s->cost.p, open_cost, (size_t)g->n * 8, kind_in(mem_kind), st));
-    FL_CUDA(cudaMemcpyAsync(s->client.p, client_mask, (size_t)g->n, kind_in(mem_kind), st));
+    if (g->relabelled) {  // inputs in original order -> internal order
+        FL_TRY(dalloc(s->io, (size_t)g->n * 9));
+        uint8_t* io = s->io.as<uint8_t>();
+        FL_CUDA(cudaMemcpyAsync(io, open_cost, (size_t)g->n * 8, kind_in(mem_kind), st));
+        FL_CUDA(cudaMemcpyAsync(io + (size_t)g->n * 8, client_mask, (size_t)g->n, kind_in(mem_kind), st));
+        FL_TRY(permute_vertices<double>(g, reinterpret_cast<double*>(io), s->cost.as<double>(), 1, true, g->stream));
+        FL_TRY(permute_vertices<uint8_t>(g, io + (size_t)g->n * 8, s->client.as<uint8_t>(), 1, true, g->stream));
+    } else {
+        FL_CUDA(cudaMemcpyAsync(s->cost.p, open_cost, (size_t)g->n * 8, kind_in(mem_kind), st));
+        FL_CUDA(cudaMemcpyAsync(s->client.p, client_mask, (size_t)g->n, kind_in(mem_kind), st));
+    }
     FL_TRY(compute_radii(s));
-    FL_TRY(copy_out(radii_out, s->radii.p, (size_t)g->n * 8, mem_kind, st));
+    if (radii_out && g->relabelled) {
+        FL_TRY(dalloc(s->io, (size_t)g->n * 9));
+        FL_TRY(permute_vertices<double>(g, s->radii.as<double>(), s->io.as<double>(), 1, false, g->stream));
+        FL_TRY(copy_out(radii_out, s->io.p, (size_t)g->n * 8, mem_kind, st));
+    } else {
+        FL_TRY(copy_out(radii_out, s->radii.p, (size_t)g->n * 8, mem_kind, st));
+    }
     FL_CUDA(cudaStreamSynchronize(st));
     s->have_radii = 1;
     return FL_OK;
@@ -289,7 +356,13 @@ int fl_open_facilities(fl_solve* s, uint8_t* open_out, int64_t* n_open, int mem_
     s->have_open = s->have_assign = 0;
     ProfScope ps(s->g);
     FL_TRY(open_facilities(s));
-    FL_TRY(copy_out(open_out, s->open.p, (size_t)s->g->n, mem_kind, s->g->stream));
+    if (open_out && s->g->relabelled) {
+        FL_TRY(dalloc(s->io, (size_t)s->g->n * 9));
+        FL_TRY(permute_vertices<uint8_t>(s->g, s->open.as<uint8_t>(), s->io.as<uint8_t>(), 1, false, s->g->stream));
+        FL_TRY(copy_out(open_out, s->io.p, (size_t)s->g->n, mem_kind, s->g->stream));
+    } else {
+        FL_TRY(copy_out(open_out, s->open.p, (size_t)s->g->n, mem_kind, s->g->stream));
+    }
     FL_CUDA(cudaStreamSynchronize(s->g->stream));
     if (n_open) *n_open = s->n_open;
     s->have_open = 1;
@@ -302,8 +375,18 @@ int fl_assign_clients(fl_solve* s, int32_t* assign_out, int32_t* dist_out, int m
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
     ProfScope ps(s->g);
     FL_TRY(assign_clients(s));
-    FL_TRY(copy_out(assign_out, s->assign.p, (size_t)s->g->n * 4, mem_kind, s->g->stream));
-    FL_TRY(copy_out(dist_out, s->dist.p, (size_t)s->g->n * 4, mem_kind, s->g->stream));
+    const int32_t* a = s->assign.as<int32_t>();
+    const int32_t* d = s->dist.as<int32_t>();
+    if (s->g->relabelled && (assign_out || dist_out)) {  // facility ids are already original ids
+        FL_TRY(dalloc(s->io, (size_t)s->g->n * 9));
+        int32_t* io = s->io.as<int32_t>();
+        FL_TRY(permute_vertices<int32_t>(s->g, a, io, 1, false, s->g->stream));
+        FL_TRY(permute_vertices<int32_t>(s->g, d, io + s->g->n, 1, false, s->g->stream));
+        a = io;
+        d = io + s->g->n;
+    }
+    FL_TRY(copy_out(assign_out, a, (size_t)s->g->n * 4, mem_kind, s->g->stream));
+    FL_TRY(copy_out(dist_out, d, (size_t)s->g->n * 4, mem_kind, s->g->stream));
     FL_CUDA(cudaStreamSynchronize(s->g->stream));
     s->have_assign = 1;
     return FL_OK;
@@ -366,6 +449,7 @@ int new_graph(int64_t n, int64_t nnz, cudaStream_t stream, fl_graph** out) {
         if ((rc = dalloc(g->cols, (size_t)(nnz > 0 ? nnz : 1) * 4))) break;
         if ((rc = dalloc(g->vbase, (size_t)n * 4))) break;
         if ((rc = dalloc(g->vpart, (size_t)n * 4))) break;
+        if ((rc = dalloc(g->rid, (size_t)n * 4))) break;
     } while (0);
     if (rc != FL_OK) {
         destroy_graph(g);
@@ -548,9 +632,20 @@ int fl_batch_solve(fl_batch* b, int n_active, int k, uint64_t seed, const double
     }
     s->g = &view;
     s->generation = view.generation;
+    // replicas of a relabelled graph: per-instance arrays in original order
+    const fl_graph* P = (b->kind == 2 && b->base->relabelled) ? b->base : nullptr;
     auto run = [&]() -> int {
-        FL_CUDA(cudaMemcpyAsync(s->cost.p, cost, (size_t)N * 8, kind_in(mem_kind), st));
-        FL_CUDA(cudaMemcpyAsync(s->client.p, client, (size_t)N, kind_in(mem_kind), st));
+        if (P) {
+            FL_TRY(dalloc(s->io, (size_t)b->U->n * 9));
+            uint8_t* io = s->io.as<uint8_t>();
+            FL_CUDA(cudaMemcpyAsync(io, cost, (size_t)N * 8, kind_in(mem_kind), st));
+            FL_CUDA(cudaMemcpyAsync(io + (size_t)N * 8, client, (size_t)N, kind_in(mem_kind), st));
+            FL_TRY(permute_vertices<double>(P, reinterpret_cast<double*>(io), s->cost.as<double>(), n_active, true, st));
+            FL_TRY(permute_vertices<uint8_t>(P, io + (size_t)N * 8, s->client.as<uint8_t>(), n_active, true, st));
+        } else {
+            FL_CUDA(cudaMemcpyAsync(s->cost.p, cost, (size_t)N * 8, kind_in(mem_kind), st));
+            FL_CUDA(cudaMemcpyAsync(s->client.p, client, (size_t)N, kind_in(mem_kind), st));
+        }
         if (b->kind == 1)
             FL_TRY(compute_radii(s));
         else
@@ -563,10 +658,24 @@ int fl_batch_solve(fl_batch* b, int n_active, int k, uint64_t seed, const double
         int32_t* asg_d = reinterpret_cast<int32_t*>(cnt_d + 3 * b->n_inst);
         FL_TRY(batch_objective(s, b->off_d.as<int64_t>(), n_active, obj_d, cnt_d, cnt_d + b->n_inst,
                                cnt_d + 2 * b->n_inst));
-        if (assign_out) FL_TRY(batch_localize(s, asg_d));
-        FL_TRY(copy_out(open_out, s->open.p, (size_t)N, mem_kind, st));
-        FL_TRY(copy_out(assign_out, asg_d, (size_t)N * 4, mem_kind, st));
-        FL_TRY(copy_out(dist_out, s->dist.p, (size_t)N * 4, mem_kind, st));
+        // facility labels are rank ids already: part-local (unions) or
+        // original ids of the resident graph (replicas)
+        const uint8_t* op = s->open.as<uint8_t>();
+        const int32_t* as = s->assign.as<int32_t>();
+        const int32_t* ds = s->dist.as<int32_t>();
+        if (P) {
+            FL_TRY(dalloc(s->io, (size_t)b->U->n * 9));
+            uint8_t* io = s->io.as<uint8_t>();
+            if (open_out) FL_TRY(permute_vertices<uint8_t>(P, op, io, n_active, false, st));
+            if (assign_out) FL_TRY(permute_vertices<int32_t>(P, as, asg_d, n_active, false, st));
+            if (dist_out) FL_TRY(permute_vertices<int32_t>(P, ds, reinterpret_cast<int32_t*>(io + N), n_active, false, st));
+            op = io;
+            as = asg_d;
+            ds = reinterpret_cast<int32_t*>(io + N);
+        }
+        FL_TRY(copy_out(open_out, op, (size_t)N, mem_kind, st));
+        FL_TRY(copy_out(assign_out, as, (size_t)N * 4, mem_kind, st));
+        FL_TRY(copy_out(dist_out, ds, (size_t)N * 4, mem_kind, st));
         std::vector<double> h_obj(n_active);
         std::vector<long long> h_cnt(3 * b->n_inst);
         FL_CUDA(cudaMemcpyAsync(h_obj.data(), obj_d, (size_t)n_active * 8, cudaMemcpyDeviceToHost, st));

@@ -54,9 +54,25 @@ constexpr uint64_t kMul1 = 0xbf58476d1ce4e5b9ULL;
 constexpr uint64_t kMul2 = 0x94d049bb133111ebULL;
 constexpr uint64_t kEmpty = ~0ULL;                   // empty sketch slot
 
-// Local id of v in a disjoint-union graph (see fl_graph::vbase).
-__device__ __forceinline__ int64_t local_id(const int32_t* __restrict__ vbase, int64_t v) {
-    return vbase ? v - (int64_t)__ldg(&vbase[v]) : v;
+// Vertex ids.  Kernels work on internal ids.  A graph may relabel its
+// vertices (by descending degree, so that the values of high-degree vertices,
+// read by most edges, share cache sectors) or be a disjoint union of parts
+// (batches).  The rank id of a vertex is the id that ranks, priorities and
+// reported facility labels use: the original id of a relabelled graph, the
+// part-local id in a union, else the id itself.
+struct IdMap {
+    const int32_t* rid = nullptr;    // rank id of each internal vertex (NULL: the id itself)
+    const int32_t* inv = nullptr;    // relabelled graph: internal id of each original id
+    const int32_t* vbase = nullptr;  // union: first internal id of each vertex's part
+};
+
+__device__ __forceinline__ int64_t rank_id(const IdMap& m, int64_t v) {
+    return m.rid ? (int64_t)__ldg(&m.rid[v]) : v;
+}
+
+// Internal id of the vertex with rank id r, in the part of vertex v.
+__device__ __forceinline__ int64_t internal_of(const IdMap& m, int64_t r, int64_t v) {
+    return m.inv ? (int64_t)__ldg(&m.inv[r]) : (m.vbase ? r + (int64_t)__ldg(&m.vbase[v]) : r);
 }
 
 __host__ __device__ constexpr uint64_t inv_odd(uint64_t a) {
@@ -374,6 +390,10 @@ struct fl_graph {
     // exactly as it would be alone.  Empty for an ordinary graph.
     fl::DBuf vbase;                // int32[n] or empty
     fl::DBuf vpart;                // int32[n]: part of each vertex (with vbase)
+    // relabelled graphs (see IdMap): rid = original id of each internal
+    // vertex, inv = internal id of each original id; unions keep rid = local id
+    fl::DBuf rid, inv;             // int32[n] or empty
+    bool relabelled = false;
     int64_t n_parts = 0;           // 0: not a union
     fl::DBuf U;                    // uint64[kUW]: the kUW smallest ranks, ascending (kEmpty padded)
     uint64_t ulim = 0;             // largest entry of U
@@ -411,6 +431,16 @@ struct fl_graph {
     cudaEvent_t hop_ev[2] = {nullptr, nullptr};
 };
 
+namespace fl {
+inline IdMap idmap_of(const fl_graph* g) {
+    IdMap m;
+    m.rid = g->rid.p ? g->rid.as<int32_t>() : nullptr;
+    m.inv = g->relabelled ? g->inv.as<int32_t>() : nullptr;
+    m.vbase = (!g->relabelled && g->vbase.p) ? g->vbase.as<int32_t>() : nullptr;
+    return m;
+}
+}  // namespace fl
+
 struct fl_solve {
     fl_graph* g = nullptr;
     uint64_t generation = 0;
@@ -421,6 +451,7 @@ struct fl_solve {
     fl::DBuf X, stamp, mval, fr[2], frval, touched, ulist, ubuck, bcount;
     fl::DBuf key_hi, key_lo, key_val, obj_tmp;  // key sort and objective scratch
     fl::DBuf part_T;               // int32[n_parts]: largest ball radius of a part's undecided facilities
+    fl::DBuf io;                   // per-vertex inputs/outputs in original order (relabelled graphs)
     fl::DBuf open;                 // uint8[n]
     fl::DBuf assign, dist;         // int32[n]
     int64_t n_cand = 0, n_open = 0, mis_rounds = 0;
@@ -492,9 +523,14 @@ int batch_replicate(const fl_graph* G, int64_t R, fl_graph* U);
 int batch_replicate_ecc(const fl_graph* G, int64_t R, fl_graph* U);
 int batch_objective(fl_solve* s, const int64_t* off_d, int n_inst, double* obj, long long* n_open,
                     long long* dist_sum, long long* unserved);
-int batch_localize(fl_solve* s, int32_t* out);
 int compute_radii_multi(const fl_graph* src, fl_graph* g, int64_t R, const double* cost, const uint8_t* client,
                         double* radii);
 int relax_reserve(fl_graph* g);
+// vertex numbering by descending degree (k_relabel.cu)
+int relabel_graph(fl_graph* g);
+template <class T>
+int permute_vertices(const fl_graph* g, const T* in, T* out, int64_t reps, bool to_internal, cudaStream_t st);
+int sketch_rows_original(const fl_graph* g, uint64_t* out);
+int ads_original(fl_graph* g, int64_t* gofs_o, int64_t* eofs_o, uint32_t* ginfo_o, double* gwt_o, int32_t* eid_o);
 
 }  // namespace fl

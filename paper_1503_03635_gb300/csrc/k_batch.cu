@@ -33,13 +33,14 @@ int grid_for(int64_t items, int per_block) {
 // its columns at eoff), shifted to U's numbering.
 __global__ void k_place_part(int part, int64_t n_i, int64_t nnz_i, int64_t voff, int64_t eoff,
                              int64_t* __restrict__ rowp, int32_t* __restrict__ cols, int32_t* __restrict__ vbase,
-                             int32_t* __restrict__ vpart) {
+                             int32_t* __restrict__ vpart, int32_t* __restrict__ rid) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_i || t < nnz_i; t += stride) {
         if (t < n_i) {
             rowp[voff + t] += eoff;
             vbase[voff + t] = (int32_t)voff;
             vpart[voff + t] = part;
+            rid[voff + t] = (int32_t)t;
         }
         if (t < nnz_i) cols[eoff + t] += (int32_t)voff;
     }
@@ -62,7 +63,8 @@ __global__ void k_check_parts(const int64_t* __restrict__ rowp, const int32_t* _
 // U = R copies of G: vertex i*n + v, entries i*nnz + e.
 __global__ void k_replicate_csr(const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols, int64_t n,
                                 int64_t nnz, int64_t R, int64_t* __restrict__ Urowp, int32_t* __restrict__ Ucols,
-                                int32_t* __restrict__ vbase, int32_t* __restrict__ vpart) {
+                                int32_t* __restrict__ vbase, int32_t* __restrict__ vpart,
+                                const int32_t* __restrict__ base_rid, int32_t* __restrict__ rid) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t total_e = R * nnz, total_v = R * n;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total_e || t <= total_v; t += stride) {
@@ -75,6 +77,7 @@ __global__ void k_replicate_csr(const int64_t* __restrict__ rowp, const int32_t*
             Urowp[t] = i * nnz + rowp[v];
             vbase[t] = (int32_t)(i * n);
             vpart[t] = (int32_t)i;
+            rid[t] = base_rid ? base_rid[v] : (int32_t)v;
         } else if (t == total_v) {
             Urowp[t] = total_e;
         }
@@ -136,16 +139,6 @@ __global__ void __launch_bounds__(256) k_batch_objective(const int64_t* __restri
     }
 }
 
-// Facility ids of the assignment in part-local numbering.
-__global__ void k_localize(const int32_t* __restrict__ assign, const int32_t* __restrict__ vbase, int64_t n,
-                           int32_t* __restrict__ out) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const int32_t a = assign[v];
-        out[v] = a < 0 ? -1 : a - vbase[v];
-    }
-}
-
 }  // namespace
 
 
@@ -156,7 +149,7 @@ int batch_place_parts(fl_graph* U, const std::vector<int64_t>& voff, const std::
         const int64_t n_i = voff[i + 1] - voff[i], nnz_i = eoff[i + 1] - eoff[i];
         FL_LAUNCH(kProfOther, k_place_part<<<grid_for(std::max(n_i, nnz_i), 256), 256, 0, st>>>(
                                   i, n_i, nnz_i, voff[i], eoff[i], U->rowp.as<int64_t>(), U->cols.as<int32_t>(),
-                                  U->vbase.as<int32_t>(), U->vpart.as<int32_t>()));
+                                  U->vbase.as<int32_t>(), U->vpart.as<int32_t>(), U->rid.as<int32_t>()));
     }
     FL_CUDA(cudaGetLastError());
     return FL_OK;
@@ -178,7 +171,8 @@ int batch_replicate(const fl_graph* G, int64_t R, fl_graph* U) {
     cudaStream_t st = U->stream;
     FL_LAUNCH(kProfOther, k_replicate_csr<<<grid_for(std::max(R * G->nnz, R * G->n + 1), 256), 256, 0, st>>>(
                               G->rowp.as<int64_t>(), G->cols.as<int32_t>(), G->n, G->nnz, R, U->rowp.as<int64_t>(),
-                              U->cols.as<int32_t>(), U->vbase.as<int32_t>(), U->vpart.as<int32_t>()));
+                              U->cols.as<int32_t>(), U->vbase.as<int32_t>(), U->vpart.as<int32_t>(),
+                              G->rid.p ? G->rid.as<int32_t>() : nullptr, U->rid.as<int32_t>()));
     FL_CUDA(cudaGetLastError());
     return FL_OK;
 }
@@ -201,12 +195,5 @@ int batch_objective(fl_solve* s, const int64_t* off_d, int n_inst, double* obj, 
     return FL_OK;
 }
 
-int batch_localize(fl_solve* s, int32_t* out) {
-    fl_graph* g = s->g;
-    FL_LAUNCH(kProfOther, k_localize<<<grid_for(g->n, 256), 256, 0, g->stream>>>(
-                              s->assign.as<int32_t>(), g->vbase.as<int32_t>(), g->n, out));
-    FL_CUDA(cudaGetLastError());
-    return FL_OK;
-}
 
 }  // namespace fl

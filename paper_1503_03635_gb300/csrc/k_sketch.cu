@@ -239,13 +239,13 @@ __global__ void k_rank_init(int64_t n, int k, uint64_t seed, uint64_t* __restric
                             uint8_t* __restrict__ Scnt, uint64_t* __restrict__ D0, uint8_t* __restrict__ Dcnt0,
                             int32_t* __restrict__ stg_ent, StgGroup* __restrict__ stg_grp,
                             int32_t* __restrict__ vg, int32_t* __restrict__ ve, const uint64_t* __restrict__ U,
-                            uint64_t ulim, uint64_t* __restrict__ DM0, const int32_t* __restrict__ vbase,
+                            uint64_t ulim, uint64_t* __restrict__ DM0, IdMap ids,
                             Counters* ctr) {
     __shared__ uint64_t sU[kUW];
     load_u(sU, U);
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        uint64_t r = vertex_rank(seed, local_id(vbase, v));
+        uint64_t r = vertex_rank(seed, rank_id(ids, v));
         const int ri = u_pos(sU, ulim, r);
 #pragma unroll
         for (int w = 0; w < kUWords; ++w)
@@ -359,14 +359,14 @@ template <int G>
 __device__ __forceinline__ void gather_range(const Grp<G>& g, int k, int hop, uint64_t seed,
                                              const int32_t* __restrict__ cols, int64_t e0, int64_t e1,
                                              const uint8_t* __restrict__ Dcp, const uint64_t* __restrict__ Dp,
-                                             const int32_t* __restrict__ vbase, Sketch<G>& s,
+                                             IdMap ids, Sketch<G>& s,
                                              unsigned long long& cand) {
     for (int64_t cb = e0; cb < e1; cb += G) {
         const int64_t e = cb + g.l;
         const bool in = e < e1;
         const int32_t u = in ? __ldg(&cols[e]) : 0;
         if (hop == 1) {
-            absorb(g, k, in ? vertex_rank(seed, local_id(vbase, u)) : kEmpty, s);
+            absorb(g, k, in ? vertex_rank(seed, rank_id(ids, u)) : kEmpty, s);
             continue;
         }
         const int c = in ? (int)__ldg(&Dcp[u]) : 0;
@@ -412,7 +412,7 @@ __device__ __forceinline__ bool finish_vertex(const Grp<G>& g, int k, uint64_t s
                                               int32_t* __restrict__ vg, int32_t* __restrict__ ve,
                                               int32_t* __restrict__ stg_ent, StgGroup* __restrict__ stg_grp,
                                               const uint64_t* sU, uint64_t ulim, uint64_t* __restrict__ DMc,
-                                              const int32_t* __restrict__ vbase, HopCounters& hc) {
+                                              IdMap ids, HopCounters& hc) {
     const bool valid = g.l < k && s.sk != kEmpty;
     const bool was_there = grp_member(g, old, s.sk);
     const unsigned newm = g.ballot(valid && !was_there);
@@ -426,7 +426,7 @@ __device__ __forceinline__ bool finish_vertex(const Grp<G>& g, int k, uint64_t s
     const uint64_t dv = grp_compact(g, s.sk, newm, kEmpty);
     if (g.l < dcnt) {
         Dc[(int64_t)v * k + g.l] = dv;
-        stg_ent[slot * k + g.l] = (int32_t)(rank_vertex(seed, dv) + (vbase ? __ldg(&vbase[v]) : 0));
+        stg_ent[slot * k + g.l] = (int32_t)internal_of(ids, (int64_t)rank_vertex(seed, dv), v);
     }
     {
         // delta mask over U: lane w < kUWords builds word w
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(256) k_hop_vertices(
     uint8_t* __restrict__ Scnt, const uint64_t* __restrict__ Dp, const uint8_t* __restrict__ Dcp,
     uint64_t* __restrict__ Dc, uint8_t* __restrict__ Dcc, int32_t* __restrict__ vg, int32_t* __restrict__ ve,
     int32_t* __restrict__ stg_ent, StgGroup* __restrict__ stg_grp, const uint64_t* __restrict__ U, uint64_t ulim,
-    const uint64_t* __restrict__ DMp, uint64_t* __restrict__ DMc, const int32_t* __restrict__ vbase,
+    const uint64_t* __restrict__ DMp, uint64_t* __restrict__ DMc, IdMap ids,
     Counters* ctr) {
     __shared__ uint64_t sU[kUW];
     load_u(sU, U);
@@ -525,12 +525,12 @@ __global__ void __launch_bounds__(256) k_hop_vertices(
             s.sk = sk_new;
             s.cnt = k;
         } else {
-            gather_range(g, k, hop, seed, cols, beg, end, Dcp, Dp, vbase, s, hc.cand);
+            gather_range(g, k, hop, seed, cols, beg, end, Dcp, Dp, ids, s, hc.cand);
             const bool merged = hop == 1 || g.ballot(hc.cand != cand0) != 0;
             if (g.l == 0 && merged) hop_ctr_add<G>(kCMerging, 1u);
         }
         finish_vertex(g, k, seed, hop, v, end - beg, old, s, i, S, Scnt, Dc, Dcc, vg, ve, stg_ent, stg_grp, sU, ulim,
-                      DMc, vbase, hc);
+                      DMc, ids, hc);
     }
     flush_counters(g, hc, ctr);
 }
@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(256) k_hop_hub_segments(
     int64_t n_seg, const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols, int k, uint64_t seed,
     int hop, const uint64_t* __restrict__ S, const uint8_t* __restrict__ Scnt, const uint64_t* __restrict__ Dp,
     const uint8_t* __restrict__ Dcp, uint64_t* __restrict__ part, const uint64_t* __restrict__ U, uint64_t ulim,
-    const uint64_t* __restrict__ DMp, uint64_t* __restrict__ PM, const int32_t* __restrict__ vbase, Counters* ctr) {
+    const uint64_t* __restrict__ DMp, uint64_t* __restrict__ PM, IdMap ids, Counters* ctr) {
     __shared__ uint64_t sU[kUW];
     load_u(sU, U);
     const Grp<G> g;
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(256) k_hop_hub_segments(
         s.cnt = 0;
         s.tau_base = Scnt[v] == k ? kth_old : kEmpty;
         s.tau = s.tau_base;
-        gather_range(g, k, hop, seed, cols, e0, e1, Dcp, Dp, vbase, s, hc.cand);
+        gather_range(g, k, hop, seed, cols, e0, e1, Dcp, Dp, ids, s, hc.cand);
         if (g.l < k) part[sidx * k + g.l] = s.sk;
     }
     flush_counters(g, hc, ctr);
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(256) k_hop_hubs(
     int64_t slot0, uint64_t* __restrict__ S, uint8_t* __restrict__ Scnt, uint64_t* __restrict__ Dc,
     uint8_t* __restrict__ Dcc, int32_t* __restrict__ vg, int32_t* __restrict__ ve, int32_t* __restrict__ stg_ent,
     StgGroup* __restrict__ stg_grp, const uint64_t* __restrict__ U, uint64_t ulim, const uint64_t* __restrict__ PM,
-    uint64_t* __restrict__ DMc, const int32_t* __restrict__ vbase, Counters* ctr) {
+    uint64_t* __restrict__ DMc, IdMap ids, Counters* ctr) {
     __shared__ uint64_t sU[kUW];
     load_u(sU, U);
     const Grp<G> g;
@@ -624,7 +624,7 @@ __global__ void __launch_bounds__(256) k_hop_hubs(
             s.cnt = k;
             const int64_t deg = rowp[v + 1] - rowp[v];
             if (finish_vertex(g, k, seed, hop, v, deg, old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve, stg_ent, stg_grp,
-                              sU, ulim, DMc, vbase, hc) &&
+                              sU, ulim, DMc, ids, hc) &&
                 g.l == 0)
                 atomicAdd(&ctr->merges, (unsigned long long)deg);
             continue;
@@ -638,7 +638,7 @@ __global__ void __launch_bounds__(256) k_hop_hubs(
         if (g.l == 0 && any) hop_ctr_add<G>(kCMerging, 1u);
         const int64_t deg = rowp[v + 1] - rowp[v];
         if (finish_vertex(g, k, seed, hop, v, deg, old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve, stg_ent, stg_grp, sU,
-                          ulim, DMc, vbase, hc) &&
+                          ulim, DMc, ids, hc) &&
             g.l == 0)
             atomicAdd(&ctr->merges, (unsigned long long)deg);
     }
@@ -826,12 +826,12 @@ __global__ void k_hop_census(const int32_t* __restrict__ list, int64_t n_list, c
 constexpr int kSelCap = 4096;  // candidates sorted in one block
 
 // Ranks below T -> buf (first kSelCap of them); their number -> *cnt.
-__global__ void k_small_ranks(int64_t n, uint64_t seed, uint64_t T, const int32_t* __restrict__ vbase,
+__global__ void k_small_ranks(int64_t n, uint64_t seed, uint64_t T, IdMap ids,
                               uint64_t* __restrict__ buf, unsigned long long* __restrict__ cnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
         const int64_t v = base + lane_id();
-        const uint64_t r = v < n ? vertex_rank(seed, local_id(vbase, v)) : kEmpty;
+        const uint64_t r = v < n ? vertex_rank(seed, rank_id(ids, v)) : kEmpty;
         const long long at = warp_append(v < n && r < T, cnt);
         if (at >= 0 && at < kSelCap) buf[at] = r;
     }
@@ -880,7 +880,7 @@ static int select_small_ranks(fl_graph* g) {
         cudaError_t e = cudaMemsetAsync(cnt, 0, 8, st);
         if (e != cudaSuccess) { rc = status_of(e, "small ranks", __FILE__, __LINE__); break; }
         FL_LAUNCH(kProfSketchOther, k_small_ranks<<<grid_for(n, 256), 256, 0, st>>>(
-                                        n, g->seed, T, g->vbase.p ? g->vbase.as<int32_t>() : nullptr,
+                                        n, g->seed, T, idmap_of(g),
                                         buf.as<uint64_t>(), cnt));
         e = cudaMemcpyAsync(&c, cnt, 8, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -915,7 +915,7 @@ static int launch_hop(fl_graph* g, int hop, const int32_t* list, int64_t n_list,
     const int k = g->k;
     const int per_block = 256 / G;
     StgGroup* grp = g->stg_grp.as<StgGroup>() + slot_base;
-    const int32_t* vb = g->vbase.p ? g->vbase.as<int32_t>() : nullptr;
+    const IdMap vb = idmap_of(g);
     int32_t* ent = g->stg_ent.as<int32_t>() + slot_base * k;
     if (n_list > 0)
         FL_LAUNCH(kProfSketchMerge, k_hop_vertices<G><<<grid_for(n_list, per_block), 256, 0, st>>>(
@@ -998,7 +998,7 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
                                     n, k, seed, g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[0].as<uint64_t>(),
                                     g->Dcnt[0].as<uint8_t>(), g->stg_ent.as<int32_t>(), g->stg_grp.as<StgGroup>(),
                                     g->vg.as<int32_t>(), g->ve.as<int32_t>(), g->U.as<uint64_t>(), g->ulim,
-                                    g->DM[0].as<uint64_t>(), g->vbase.p ? g->vbase.as<int32_t>() : nullptr,
+                                    g->DM[0].as<uint64_t>(), idmap_of(g),
                                     g->ctr.as<Counters>()));
     FL_CUDA(cudaGetLastError());
     FL_TRY(read_counters(g));
@@ -1148,12 +1148,12 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
 // and ecc(root), and ecc(v) <= d(v, root) + ecc(root).
 
 __global__ void k_roots(const uint64_t* __restrict__ S, int k, uint64_t seed, int64_t n,
-                        const int32_t* __restrict__ vbase, int32_t* __restrict__ roots, Counters* ctr) {
+                        IdMap ids, int32_t* __restrict__ roots, Counters* ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
         int64_t v = base + lane_id();
         bool is_root = false;
-        if (v < n) is_root = (int64_t)rank_vertex(seed, S[v * k]) == local_id(vbase, v);
+        if (v < n) is_root = (int64_t)rank_vertex(seed, S[v * k]) == rank_id(ids, v);
         long long at = warp_append(is_root, &ctr->aux0);
         if (at >= 0) roots[at] = (int32_t)v;
     }
@@ -1189,7 +1189,7 @@ int compute_ecc_bound(fl_graph* g) {
         if (e != cudaSuccess) { rc = status_of(e, "ecc init", __FILE__, __LINE__); break; }
         FL_LAUNCH(kProfSketchOther, k_roots<<<grid_for(n, 256), 256, 0, st>>>(
                                         g->S.as<uint64_t>(), g->k, g->seed, n,
-                                        g->vbase.p ? g->vbase.as<int32_t>() : nullptr, roots.as<int32_t>(),
+                                        idmap_of(g), roots.as<int32_t>(),
                                         g->ctr.as<Counters>()));
         if ((rc = read_counters(g))) break;
         int64_t n_roots = (int64_t)g->h_ctr->aux0;

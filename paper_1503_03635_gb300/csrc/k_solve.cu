@@ -141,7 +141,10 @@ int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, i
     FL_CUDA(cudaMemsetAsync(r.stamp, 0, (size_t)n * 4, st));
     FL_CUDA(cudaMemsetAsync(r.cnt, 0, 64, st));
     if (n_src > 0) {
-        FL_LAUNCH(cls, k_inject<<<grid_for(n_src, 256), 256, 0, st>>>(src_list, n_src, nullptr, 0ULL, nullptr, r.X[0],
+        // labels are the sources' rank ids: ties go to the smallest original
+        // (or part-local) facility id whatever the internal numbering
+        const uint32_t* label_of = g->rid.p ? g->rid.as<uint32_t>() : nullptr;
+        FL_LAUNCH(cls, k_inject<<<grid_for(n_src, 256), 256, 0, st>>>(src_list, n_src, nullptr, 0ULL, label_of, r.X[0],
                                                                       r.stamp, 1u, r.fr[0], &r.cnt[0]));
         FL_CUDA(cudaGetLastError());
     }
@@ -269,7 +272,7 @@ int compute_radii_multi(const fl_graph* src, fl_graph* g, int64_t R, const doubl
 // ------------------------------------------------------------------ keys (r_f, pi_f)
 
 __global__ void k_candidates(const double* __restrict__ r, int64_t n, uint64_t seed,
-                             const int32_t* __restrict__ vbase, uint64_t* __restrict__ hi,
+                             IdMap ids, uint64_t* __restrict__ hi,
                              uint64_t* __restrict__ lo, uint32_t* __restrict__ val, uint8_t* __restrict__ state,
                              Counters* ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -285,7 +288,7 @@ __global__ void k_candidates(const double* __restrict__ r, int64_t n, uint64_t s
         long long at = warp_append(cand, &ctr->aux0);
         if (at >= 0) {
             hi[at] = (uint64_t)__double_as_longlong(rf);  // r >= 0: bit order = numeric order
-            lo[at] = facility_priority(seed, local_id(vbase, f));
+            lo[at] = facility_priority(seed, rank_id(ids, f));
             val[at] = (uint32_t)f;
         }
     }
@@ -462,7 +465,7 @@ int open_facilities(fl_solve* s) {
     FL_TRY(dalloc(val, (size_t)n * 4));
     FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st));
     FL_LAUNCH(kProfKeys, k_candidates<<<grid_for(n, 256), 256, 0, st>>>(s->radii.as<double>(), n, g->seed,
-                                                   g->vbase.p ? g->vbase.as<int32_t>() : nullptr, hi.as<uint64_t>(),
+                                                   idmap_of(g), hi.as<uint64_t>(),
                                                    lo.as<uint64_t>(), val.as<uint32_t>(), s->state.as<uint8_t>(),
                                                    g->ctr.as<Counters>()));
     FL_TRY(read_counters(g));
