@@ -58,6 +58,49 @@ __global__ void k_relabel_rows(const int64_t* __restrict__ rowp, const int32_t* 
     }
 }
 
+// Rows of at most kSortMax entries sorted ascending (new ids: descending
+// degree first), one warp per row through a shared-memory bitonic sort.
+// Hub rows keep their order.  Sorting does not change any result (every step
+// is order-independent); it makes a vertex meet its high-degree neighbours
+// first, whose sketch entries are the smallest ranks and tighten its filter.
+constexpr int kSortMax = 2048;
+constexpr int kSortWarps = 4;
+
+__global__ void __launch_bounds__(32 * kSortWarps) k_sort_rows(const int64_t* __restrict__ rowp, int64_t n,
+                                                                 int32_t* __restrict__ cols) {
+    __shared__ int32_t buf[kSortWarps][kSortMax];
+    int32_t* a = buf[threadIdx.x >> 5];
+    const int lane = lane_id();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        const int64_t b = rowp[v];
+        const int len = (int)(rowp[v + 1] - b);
+        if (len < 2 || len > kSortMax) continue;  // warp-uniform
+        int m = 2;
+        while (m < len) m <<= 1;
+        for (int j = lane; j < m; j += 32) a[j] = j < len ? cols[b + j] : 0x7fffffff;
+        __syncwarp();
+        for (int size = 2; size <= m; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = lane; i < m; i += 32) {
+                    const int j = i ^ stride;
+                    if (j > i) {
+                        const bool asc = (i & size) == 0;
+                        const int32_t x = a[i], y = a[j];
+                        if ((x > y) == asc) {
+                            a[i] = y;
+                            a[j] = x;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int j = lane; j < len; j += 32) cols[b + j] = a[j];
+        __syncwarp();
+    }
+}
+
 // out[r*n + i] = in[r*n + map[i]] for each of `reps` consecutive blocks of n.
 template <class T>
 __global__ void k_gather_map(const T* __restrict__ in, const int32_t* __restrict__ map, int64_t n, int64_t reps,
@@ -140,6 +183,9 @@ int relabel_graph(fl_graph* g) {
             FL_LAUNCH(kProfOther, k_relabel_rows<<<grid_for(n, 8), 256, 0, st>>>(
                                       g->rowp.as<int64_t>(), g->cols.as<int32_t>(), g->rid.as<int32_t>(),
                                       g->inv.as<int32_t>(), rowp_new.as<int64_t>(), n, cols_new.as<int32_t>()));
+        if (g->nnz > 0)
+            FL_LAUNCH(kProfOther, k_sort_rows<<<grid_for(n, kSortWarps), 32 * kSortWarps, 0, st>>>(
+                                      rowp_new.as<int64_t>(), n, cols_new.as<int32_t>()));
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { rc = status_of(e, "relabel", __FILE__, __LINE__); break; }
