@@ -235,27 +235,18 @@ __device__ __forceinline__ void hop_ctr_add(int field, unsigned x) {
 
 // ------------------------------------------------------------------ hop 0
 
+// Hop 0: S_0(v) = {r(v)} and v's ADS group at distance 0.  (Hop 1 recomputes
+// the neighbours' ranks from their ids, so no hop-0 delta list or mask is
+// stored; the group's single entry is v itself, written by the compaction.)
 __global__ void k_rank_init(int64_t n, int k, uint64_t seed, uint64_t* __restrict__ S,
-                            uint8_t* __restrict__ Scnt, uint64_t* __restrict__ D0, uint8_t* __restrict__ Dcnt0,
-                            int32_t* __restrict__ stg_ent, StgGroup* __restrict__ stg_grp,
-                            int32_t* __restrict__ vg, int32_t* __restrict__ ve, const uint64_t* __restrict__ U,
-                            uint64_t ulim, uint64_t* __restrict__ DM0, IdMap ids,
-                            Counters* ctr) {
-    __shared__ uint64_t sU[kUW];
-    load_u(sU, U);
+                            uint8_t* __restrict__ Scnt, StgGroup* __restrict__ stg_grp,
+                            int32_t* __restrict__ vg, int32_t* __restrict__ ve, IdMap ids, Counters* ctr) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         uint64_t r = vertex_rank(seed, rank_id(ids, v));
-        const int ri = u_pos(sU, ulim, r);
-#pragma unroll
-        for (int w = 0; w < kUWords; ++w)
-            DM0[v * kUWords + w] = (ri >= 0 && (ri >> 6) == w) ? 1ULL << (ri & 63) : 0ULL;
         if (r == kEmpty) atomicOr(&ctr->error, 1ULL);
         S[v * k] = r;
         Scnt[v] = 1;
-        D0[v * k] = r;
-        Dcnt0[v] = 1;
-        stg_ent[v * k] = (int32_t)v;
         StgGroup gr;
         gr.wt = 1.0;  // a one-vertex ball: fewer than k ranks (k >= 2)
         gr.v = (int32_t)v;
@@ -684,21 +675,30 @@ __global__ void k_collect_frontier(const int32_t* __restrict__ list, int64_t n, 
 
 // ------------------------------------------------------------------ ADS compaction
 
+// Staged groups -> vertex-major ADS.  kp = k rounded up to a power of two; a
+// thread per (slot, entry) pair, so that a slot's entries are copied by
+// adjacent threads (coalesced); the first thread of a slot writes the group.
+// In the hop-0 region the single entry of slot v is v itself.
 __global__ void k_ads_scatter(const StgGroup* __restrict__ stg_grp, int64_t n_slots, int64_t slot_base, int k,
-                              const int32_t* __restrict__ stg_ent, const int64_t* __restrict__ gofs,
-                              const int64_t* __restrict__ eofs, uint32_t* __restrict__ ginfo,
-                              double* __restrict__ gwt, int32_t* __restrict__ eid) {
+                              int log2_kp, bool hop0, const int32_t* __restrict__ stg_ent,
+                              const int64_t* __restrict__ gofs, const int64_t* __restrict__ eofs,
+                              uint32_t* __restrict__ ginfo, double* __restrict__ gwt, int32_t* __restrict__ eid) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += stride) {
+    const int64_t total = n_slots << log2_kp;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const int64_t i = t >> log2_kp;
+        const int j = (int)(t & ((1 << log2_kp) - 1));
         const StgGroup gr = stg_grp[slot_base + i];
         if (gr.info == 0) continue;
-        const int64_t dg = gofs[gr.v] + gr.gidx;
-        const int64_t de = eofs[gr.v] + gr.eidx;
-        ginfo[dg] = gr.info;
-        gwt[dg] = gr.wt;
         const int cnt = (int)((gr.info >> 16) & 0xff);
-        const int32_t* src = stg_ent + (slot_base + i) * k;
-        for (int j = 0; j < cnt; ++j) eid[de + j] = src[j];
+        if (j >= cnt) continue;
+        const int64_t de = eofs[gr.v] + gr.eidx;
+        if (j == 0) {
+            const int64_t dg = gofs[gr.v] + gr.gidx;
+            ginfo[dg] = gr.info;
+            gwt[dg] = gr.wt;
+        }
+        eid[de + j] = hop0 ? gr.v : stg_ent[(slot_base + i) * k + j];
     }
 }
 
@@ -995,11 +995,8 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
         }
     }
     FL_LAUNCH(kProfSketchOther, k_rank_init<<<grid_for(n, 256), 256, 0, st>>>(
-                                    n, k, seed, g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[0].as<uint64_t>(),
-                                    g->Dcnt[0].as<uint8_t>(), g->stg_ent.as<int32_t>(), g->stg_grp.as<StgGroup>(),
-                                    g->vg.as<int32_t>(), g->ve.as<int32_t>(), g->U.as<uint64_t>(), g->ulim,
-                                    g->DM[0].as<uint64_t>(), idmap_of(g),
-                                    g->ctr.as<Counters>()));
+                                    n, k, seed, g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->stg_grp.as<StgGroup>(),
+                                    g->vg.as<int32_t>(), g->ve.as<int32_t>(), idmap_of(g), g->ctr.as<Counters>()));
     FL_CUDA(cudaGetLastError());
     FL_TRY(read_counters(g));
     if (g->h_ctr->error) {
@@ -1129,12 +1126,17 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     FL_TRY(dalloc(g->eid, (size_t)std::max<int64_t>(g->n_entries, 1) * 4));
     FL_CUDA(cudaMemcpyAsync(g->gofs.as<int64_t>() + n, &g->n_groups, 8, cudaMemcpyHostToDevice, st));
     FL_CUDA(cudaMemcpyAsync(g->eofs.as<int64_t>() + n, &g->n_entries, 8, cudaMemcpyHostToDevice, st));
+    int log2_kp = 0;
+    while ((1 << log2_kp) < k) ++log2_kp;
     for (const auto& r : regions)
-        if (r.second > 0)
-            FL_LAUNCH(kProfSketchOther, k_ads_scatter<<<grid_for(r.second, 256), 256, 0, st>>>(
-                                            g->stg_grp.as<StgGroup>(), r.second, r.first, k, g->stg_ent.as<int32_t>(),
-                                            g->gofs.as<int64_t>(), g->eofs.as<int64_t>(), g->ginfo.as<uint32_t>(),
-                                            g->gwt.as<double>(), g->eid.as<int32_t>()));
+        if (r.second > 0) {
+            const bool hop0 = r.first == 0;
+            const int lk = hop0 ? 0 : log2_kp;
+            FL_LAUNCH(kProfSketchOther, k_ads_scatter<<<grid_for(r.second << lk, 256), 256, 0, st>>>(
+                                            g->stg_grp.as<StgGroup>(), r.second, r.first, k, lk, hop0,
+                                            g->stg_ent.as<int32_t>(), g->gofs.as<int64_t>(), g->eofs.as<int64_t>(),
+                                            g->ginfo.as<uint32_t>(), g->gwt.as<double>(), g->eid.as<int32_t>()));
+        }
     FL_CUDA(cudaGetLastError());
     FL_CUDA(cudaStreamSynchronize(st));
     FL_TRY(compute_ecc_bound(g));
