@@ -31,13 +31,14 @@ int copy_out(void* dst, const void* src, size_t bytes, int mem_kind, cudaStream_
 }
 
 void destroy_graph(fl_graph* g) {
+    cudaStreamSynchronize(g->stream);  // its buffers go to the idle-block cache
     DBuf* bufs[] = {&g->rowp, &g->cols, &g->low_list, &g->hub_list, &g->hub_seg, &g->seg_hub, &g->part,
                     &g->S, &g->Scnt, &g->D[0], &g->D[1], &g->Dcnt[0], &g->Dcnt[1], &g->frontier[0],
                     &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent, &g->stg_grp, &g->gofs, &g->eofs,
                     &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub, &g->ctr, &g->scratch,
                     &g->relax_aux, &g->U, &g->DM[0], &g->DM[1], &g->PM, &g->vbase, &g->vpart, &g->rid,
                     &g->inv};
-    for (DBuf* b : bufs) dfree(*b);
+    for (DBuf* b : bufs) dfree_idle(*b);
     for (cudaEvent_t e : g->prof.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : g->hop_ev)
         if (e) cudaEventDestroy(e);
@@ -46,11 +47,12 @@ void destroy_graph(fl_graph* g) {
 }
 
 void destroy_solve(fl_solve* s) {
+    if (s->g) cudaStreamSynchronize(s->g->stream);
     DBuf* bufs[] = {&s->cost, &s->client, &s->radii, &s->ord, &s->fac_by_ord, &s->bcap, &s->state, &s->claimed,
                     &s->X, &s->stamp, &s->mval, &s->fr[0], &s->fr[1], &s->frval, &s->touched, &s->ulist,
                     &s->ubuck, &s->bcount, &s->open, &s->assign, &s->dist, &s->key_hi, &s->key_lo,
                     &s->key_val, &s->obj_tmp, &s->part_T, &s->io};
-    for (DBuf* b : bufs) dfree(*b);
+    for (DBuf* b : bufs) dfree_idle(*b);
     delete s;
 }
 
@@ -427,8 +429,8 @@ void destroy_batch(fl_batch* b) {
     if (!b) return;
     if (b->s) destroy_solve(b->s);
     if (b->U) destroy_graph(b->U);
-    dfree(b->off_d);
-    dfree(b->res);
+    dfree_idle(b->off_d);
+    dfree_idle(b->res);
     delete b;
 }
 

@@ -46,6 +46,7 @@ struct DBuf {
 int dalloc(DBuf& b, size_t bytes);            // free + allocate (no copy)
 int dgrow(DBuf& b, size_t bytes, size_t keep, cudaStream_t st);  // grow keeping `keep` bytes
 void dfree(DBuf& b);
+void dfree_idle(DBuf& b);                     // to the idle-block cache (no pending work uses b)
 
 // ----------------------------------------------------------------- constants
 

@@ -1,6 +1,7 @@
 // k_util.cu -- errors, device buffers, scans, radix sort, CSR checks.
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -88,12 +89,83 @@ int prof_drain(Prof* p) {
 }
 
 // ----------------------------------------------------------------- buffers
+// Device buffers.  Buffers of destroyed handles (whose streams have been
+// synchronised, so no work uses them any more) go to a per-device cache of
+// idle blocks instead of cudaFree; dalloc takes the smallest cached block
+// that fits (and is at most twice the request) before calling cudaMalloc.
+// Repeated create/solve/destroy sequences then allocate nothing new and skip
+// cudaMalloc/cudaFree, which are slow for the tens of GB a large graph holds.
+// The cache holds at most half of the device's memory; a failed cudaMalloc
+// releases it and retries.
+
+namespace {
+
+constexpr int kMaxPoolDevices = 64;
+
+struct Pool {
+    std::mutex mu;
+    std::multimap<size_t, void*> blocks[kMaxPoolDevices];
+    size_t bytes[kMaxPoolDevices] = {};
+    size_t cap[kMaxPoolDevices] = {};
+};
+
+Pool& pool() {
+    static Pool* p = new Pool();  // never destroyed: blocks live until the process exits
+    return *p;
+}
+
+int current_device() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxPoolDevices) return -1;
+    return d;
+}
+
+void* pool_take(size_t bytes, size_t* got) {
+    const int d = current_device();
+    if (d < 0) return nullptr;
+    Pool& P = pool();
+    std::lock_guard<std::mutex> lock(P.mu);
+    auto it = P.blocks[d].lower_bound(bytes);
+    if (it == P.blocks[d].end() || it->first > 2 * bytes + (1 << 20)) return nullptr;
+    void* p = it->second;
+    *got = it->first;
+    P.bytes[d] -= it->first;
+    P.blocks[d].erase(it);
+    return p;
+}
+
+void pool_release_all() {
+    const int d = current_device();
+    if (d < 0) return;
+    Pool& P = pool();
+    std::lock_guard<std::mutex> lock(P.mu);
+    for (auto& kv : P.blocks[d]) cudaFree(kv.second);
+    P.blocks[d].clear();
+    P.bytes[d] = 0;
+}
+
+}  // namespace
 
 int dalloc(DBuf& b, size_t bytes) {
     if (b.p && b.bytes >= bytes) return FL_OK;
     dfree(b);
     if (bytes == 0) bytes = 16;
-    FL_CUDA(cudaMalloc(&b.p, bytes));
+    size_t got = 0;
+    if (void* p = pool_take(bytes, &got)) {
+        b.p = p;
+        b.bytes = got;
+        return FL_OK;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        pool_release_all();
+        e = cudaMalloc(&b.p, bytes);
+    }
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return status_of(e, "cudaMalloc", __FILE__, __LINE__);
+    }
     b.bytes = bytes;
     return FL_OK;
 }
@@ -118,6 +190,29 @@ int dgrow(DBuf& b, size_t bytes, size_t keep, cudaStream_t st) {
 
 void dfree(DBuf& b) {
     if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// For buffers no pending work uses (their handle's stream is synchronised).
+void dfree_idle(DBuf& b) {
+    if (!b.p) return;
+    const int d = current_device();
+    bool kept = false;
+    if (d >= 0) {
+        Pool& P = pool();
+        std::lock_guard<std::mutex> lock(P.mu);
+        if (P.cap[d] == 0) {
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) P.cap[d] = total_b / 2;
+        }
+        if (P.bytes[d] + b.bytes <= P.cap[d]) {
+            P.blocks[d].insert({b.bytes, b.p});
+            P.bytes[d] += b.bytes;
+            kept = true;
+        }
+    }
+    if (!kept) cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
 }
