@@ -467,8 +467,11 @@ int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t 
                        int cls = kProfSketchOther);
 int scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st, DBuf& tmp,
                               int cls = kProfSketchOther);
+// Stable LSD radix sort of (hi, lo) pairs with a payload, 4 bits per pass:
+// passes 0-15 take lo's digits, 16-31 hi's; [pass_begin, pass_end) (an even
+// count) may skip digits known to be equal.
 int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaStream_t st, DBuf& tmp,
-                    int cls = kProfKeys);
+                    int cls = kProfKeys, int pass_begin = 0, int pass_end = 32);
 
 int validate_csr(fl_graph* g);
 int build_work_lists(fl_graph* g);

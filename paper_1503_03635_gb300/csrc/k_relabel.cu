@@ -23,12 +23,14 @@ int grid_for(int64_t items, int per_block) {
     return (int)b;
 }
 
-// Sort keys: descending degree, then ascending id.
+// Sort keys: descending degree (a 31-bit key), then ascending id (the input
+// order, kept by the stable sort).
 __global__ void k_degree_keys(const int64_t* __restrict__ rowp, int64_t n, uint64_t* __restrict__ hi,
                               uint64_t* __restrict__ lo, uint32_t* __restrict__ val) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        hi[v] = ~(uint64_t)(rowp[v + 1] - rowp[v]);
+        const int64_t d = rowp[v + 1] - rowp[v];
+        hi[v] = 0x7fffffffULL - (uint64_t)(d < 0x7fffffffLL ? d : 0x7fffffffLL);
         lo[v] = (uint64_t)v;
         val[v] = (uint32_t)v;
     }
@@ -76,6 +78,22 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_sort_rows(const int64_t* __
         const int64_t b = rowp[v];
         const int len = (int)(rowp[v + 1] - b);
         if (len < 2 || len > kSortMax) continue;  // warp-uniform
+        if (len <= 32) {
+            // one entry per lane: bitonic network through shuffles
+            int32_t x = lane < len ? cols[b + lane] : 0x7fffffff;
+#pragma unroll
+            for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    const int32_t y = __shfl_xor_sync(kFull, x, stride);
+                    const bool up = ((lane & size) == 0) || size == 32;
+                    const bool low = (lane & stride) == 0;
+                    x = (low == up) ? min(x, y) : max(x, y);
+                }
+            }
+            if (lane < len) cols[b + lane] = x;
+            continue;
+        }
         int m = 2;
         while (m < len) m <<= 1;
         for (int j = lane; j < m; j += 32) a[j] = j < len ? cols[b + j] : 0x7fffffff;
@@ -169,7 +187,7 @@ int relabel_graph(fl_graph* g) {
         FL_LAUNCH(kProfOther, k_degree_keys<<<grid_for(n, 256), 256, 0, st>>>(
                                   g->rowp.as<int64_t>(), n, hi.as<uint64_t>(), lo.as<uint64_t>(), val.as<uint32_t>()));
         if ((rc = sort_pairs_u128(hi.as<uint64_t>(), lo.as<uint64_t>(), val.as<uint32_t>(), n, st, g->scratch,
-                                  kProfOther)))
+                                  kProfOther, 16, 24)))  // the low 32 bits of hi
             break;
         FL_LAUNCH(kProfOther, k_perm_maps<<<grid_for(n, 256), 256, 0, st>>>(
                                   val.as<uint32_t>(), g->rowp.as<int64_t>(), n, g->rid.as<int32_t>(),

@@ -384,8 +384,11 @@ __global__ void k_digit_scatter(const uint64_t* __restrict__ key, const uint64_t
     }
 }
 
-int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaStream_t st, DBuf& tmp, int cls) {
+int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaStream_t st, DBuf& tmp, int cls,
+                    int pass_begin, int pass_end) {
     if (n <= 1) return FL_OK;
+    if (pass_begin < 0 || pass_end > 32 || pass_begin > pass_end || ((pass_end - pass_begin) & 1))
+        FL_FAIL(FL_EINVAL, "radix sort: bad pass range");
     int nblocks = (int)((n + kSortTile - 1) / kSortTile);
     int64_t hn = 16LL * nblocks;
     size_t need = (size_t)n * (8 + 8 + 4) + 256 * 8 + (size_t)hn * (4 + 8) + scan_tmp_bytes(hn);
@@ -404,7 +407,7 @@ int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaSt
     char* stmp = take(scan_tmp_bytes(hn));
     uint64_t *ahi = hi, *alo = lo, *bhi = hi2, *blo = lo2;
     uint32_t *aval = val, *bval = val2;
-    for (int pass = 0; pass < 32; ++pass) {
+    for (int pass = pass_begin; pass < pass_end; ++pass) {
         const uint64_t* key = pass < 16 ? alo : ahi;
         int shift = 4 * (pass & 15);
         FL_LAUNCH(cls, k_digit_hist<<<nblocks, kSortThreads, 0, st>>>(key, n, shift, nblocks, hist));
@@ -417,7 +420,7 @@ int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaSt
         std::swap(alo, blo);
         std::swap(aval, bval);
     }
-    // 32 passes: the result is back in the caller's arrays
+    // an even number of passes: the result is back in the caller's arrays
     return FL_OK;
 }
 
