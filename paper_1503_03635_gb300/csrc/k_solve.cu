@@ -326,7 +326,8 @@ __global__ void k_bucket_count(const int32_t* __restrict__ ulist, int64_t n_u, c
         const bool valid = i < n_u;
         const int32_t f = valid ? ulist[i] : 0;
         const int32_t b = valid ? bcap[f] : 0;
-        if (valid) atomicAdd(&bcount[b], 1);
+        const unsigned sameb = __match_any_sync(kFull, valid ? b : -1);  // one atomic per bucket and warp
+        if (valid && lane_id() == __ffs(sameb) - 1) atomicAdd(&bcount[b], __popc(sameb));
         const unsigned mx = __reduce_max_sync(kFull, (unsigned)b);
         if (lane_id() == 0) atomicMax(tmax, (unsigned long long)mx);
         if (vpart) {
@@ -338,12 +339,23 @@ __global__ void k_bucket_count(const int32_t* __restrict__ ulist, int64_t n_u, c
     }
 }
 
+// Facilities to their bucket's range; the lanes of a warp with the same
+// bucket take consecutive places with one atomic.
 __global__ void k_bucket_scatter(const int32_t* __restrict__ ulist, int64_t n_u, const int32_t* __restrict__ bcap,
                                  int32_t* __restrict__ cursor, int32_t* __restrict__ ubuck) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_u; i += stride) {
-        int32_t f = ulist[i];
-        ubuck[atomicAdd(&cursor[bcap[f]], 1)] = f;
+    const int lane = lane_id();
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_u; base += stride) {
+        const int64_t i = base + lane;
+        const bool valid = i < n_u;
+        const int32_t f = valid ? ulist[i] : 0;
+        const int32_t b = valid ? bcap[f] : -1;
+        const unsigned same = __match_any_sync(kFull, b);
+        const int lead = __ffs(same) - 1;
+        int at = 0;
+        if (valid && lane == lead) at = atomicAdd(&cursor[b], __popc(same));
+        at = __shfl_sync(kFull, at, lead);
+        if (valid) ubuck[at + __popc(same & ((1u << lane) - 1u))] = f;
     }
 }
 
