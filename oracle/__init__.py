@@ -84,6 +84,12 @@ def _load():
             lib.orc_nearest_open.restype = ctypes.c_int
             lib.orc_nearest_open.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.c_int32),
                                              ctypes.POINTER(ctypes.c_int32)]
+            lib.orc_ball_sizes.restype = ctypes.c_int
+            lib.orc_ball_sizes.argtypes = [vp, i64, vp, i64, vp, vp]
+            lib.orc_exact_radii.restype = ctypes.c_int
+            lib.orc_exact_radii.argtypes = [vp, vp, vp, vp]
+            lib.orc_exact_radii_of.restype = ctypes.c_int
+            lib.orc_exact_radii_of.argtypes = [vp, i64, vp, vp, vp, vp]
             lib.orc_objective.restype = ctypes.c_int
             lib.orc_objective.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(dbl),
                                           ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -214,6 +220,35 @@ class Graph:
     def hip_estimate(self, v: int, h: int, client=None) -> float:
         c = None if client is None else np.ascontiguousarray(client, np.uint8)
         return float(self._lib.orc_hip_estimate(self._h, v, h, None if c is None else _p(c)))
+
+    # -- exact sizes and radii (Section 5.1, Fig. 1) ---------------------
+    def ball_sizes(self, src, max_dist: int, pred=None) -> np.ndarray:
+        """int64 [len(src), max_dist+1]: entry [s, h] = number of vertices w
+        with d(src[s], w) <= h and pred[w] (pred None: all), by BFS."""
+        src = np.ascontiguousarray(src, np.int32)
+        p = None if pred is None else np.ascontiguousarray(pred, np.uint8)
+        out = np.zeros((len(src), max_dist + 1), np.int64)
+        rc = self._lib.orc_ball_sizes(self._h, len(src), _p(src), max_dist,
+                                      None if p is None else _p(p), _p(out))
+        if rc != 0:
+            raise RuntimeError(f"orc_ball_sizes rc={rc}")
+        return out
+
+    def exact_radii(self, cost: np.ndarray, client: np.ndarray, facilities=None) -> np.ndarray:
+        """Radii of Eq. 1 at epsilon -> 0 with exact client counts per
+        distance (BFS); for all vertices, or for the ids in `facilities`."""
+        cost = np.ascontiguousarray(cost, np.float64)
+        client = np.ascontiguousarray(client, np.uint8)
+        if facilities is None:
+            r = np.zeros(self.n, np.float64)
+            rc = self._lib.orc_exact_radii(self._h, _p(cost), _p(client), _p(r))
+        else:
+            fac = np.ascontiguousarray(facilities, np.int32)
+            r = np.zeros(len(fac), np.float64)
+            rc = self._lib.orc_exact_radii_of(self._h, len(fac), _p(fac), _p(cost), _p(client), _p(r))
+        if rc != 0:
+            raise RuntimeError(f"orc_exact_radii rc={rc}")
+        return r
 
     # -- phase (ii): Eq. 1 at epsilon -> 0 -------------------------------
     def radii(self, cost: np.ndarray, client: np.ndarray) -> np.ndarray:

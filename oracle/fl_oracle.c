@@ -589,6 +589,128 @@ int orc_nearest_open(const orc_graph* g, const uint8_t* open, int64_t v, int32_t
     return ORC_OK;
 }
 
+/* ---------------------------------------------------------------------- */
+/* Exact neighbourhood sizes: the ground truth of the ADS accuracy study   */
+/* (Section 5.1, "Accuracy vs. k", Fig. 1), by breadth-first search.       */
+/* ---------------------------------------------------------------------- */
+
+/* BFS from v; cnt[h] (h = 0..D) receives the number of vertices w with
+   d(v, w) = h exactly and pred[w] != 0 (pred NULL: every vertex); returns
+   the eccentricity of v (the last distance holding a vertex), capped at D
+   when the search stops there; D < 0 searches the whole component (cnt
+   then needs n entries).  dist and q are n-long scratch arrays (dist all
+   -1 on entry and on return). */
+static int64_t bfs_levels(const orc_graph* g, int64_t v, int64_t D, const uint8_t* pred,
+                          int64_t* cnt, int32_t* dist, int32_t* q) {
+    int64_t qh = 0, qt = 0, ecc = 0;
+    cnt[0] = 0;
+    dist[v] = 0;
+    q[qt++] = (int32_t)v;
+    while (qh < qt) {
+        int32_t x = q[qh++];
+        int32_t dx = dist[x];
+        while (ecc < dx) cnt[++ecc] = 0;  /* first vertex of a new distance */
+        if (!pred || pred[x]) ++cnt[dx];
+        if (dx == D) continue;
+        for (int64_t e = g->rowp[x]; e < g->rowp[x + 1]; ++e) {
+            int32_t u = g->cols[e];
+            if (dist[u] < 0) { dist[u] = dx + 1; q[qt++] = u; }
+        }
+    }
+    for (int64_t j = 0; j < qt; ++j) dist[q[j]] = -1;
+    for (int64_t h = ecc + 1; h <= D; ++h) cnt[h] = 0;
+    return ecc;
+}
+
+/* out[s*(D+1) + h] = |{w : d(src[s], w) <= h and pred[w] != 0}| for
+   h = 0..D (cumulative sums of the per-distance counts). */
+int orc_ball_sizes(const orc_graph* g, int64_t n_src, const int32_t* src, int64_t D, const uint8_t* pred,
+                   int64_t* out) {
+    if (!g || D < 0) return ORC_EINVAL;
+    for (int64_t s = 0; s < n_src; ++s)
+        if (src[s] < 0 || src[s] >= g->n) return ORC_EINVAL;
+    int rc = ORC_OK;
+#pragma omp parallel
+    {
+        int32_t* dist = (int32_t*)malloc((size_t)(g->n > 0 ? g->n : 1) * sizeof(int32_t));
+        int32_t* q = (int32_t*)malloc((size_t)(g->n > 0 ? g->n : 1) * sizeof(int32_t));
+        int64_t* cnt = (int64_t*)malloc((size_t)(D + 1) * sizeof(int64_t));
+        if (!dist || !q || !cnt) {
+#pragma omp atomic write
+            rc = ORC_ENOMEM;
+        } else {
+            for (int64_t v = 0; v < g->n; ++v) dist[v] = -1;
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t s = 0; s < n_src; ++s) {
+                bfs_levels(g, src[s], D, pred, cnt, dist, q);
+                int64_t acc = 0;
+                for (int64_t h = 0; h <= D; ++h) {
+                    acc += cnt[h];
+                    out[s * (D + 1) + h] = acc;
+                }
+            }
+        }
+        free(dist); free(q); free(cnt);
+    }
+    return rc;
+}
+
+/* Radius of facility f with exact client counts (the exact-radius mode of
+   the accuracy study): W_h = number of clients at distance exactly h of f,
+   for h = 0..L with L the eccentricity of f, fed to the same walk as the
+   sketch radius (radius_walk: Eq. 1 at epsilon -> 0).  With every vertex
+   in f's sketch (k >= component size) the HIP weights are all 1 and the
+   two radii are the same numbers. */
+static double exact_radius_one(const orc_graph* g, int64_t f, double cost, const uint8_t* client,
+                               int32_t* dist, int32_t* q, int64_t* cnt, int32_t* hop, double* W) {
+    if (!(cost < INFINITY)) return INFINITY;
+    int64_t L = bfs_levels(g, f, -1, client, cnt, dist, q);
+    for (int64_t h = 0; h <= L; ++h) { hop[h] = (int32_t)h; W[h] = (double)cnt[h]; }
+    return radius_walk(hop, W, L + 1, cost);
+}
+
+static int exact_radii_range(const orc_graph* g, int64_t m, const int32_t* fac, const double* cost,
+                             const uint8_t* client, double* r) {
+    const int64_t n = g->n;
+    int rc = ORC_OK;
+#pragma omp parallel
+    {
+        int32_t* dist = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+        int32_t* q = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+        int64_t* cnt = (int64_t*)malloc((size_t)(n + 1) * sizeof(int64_t));
+        int32_t* hop = (int32_t*)malloc((size_t)(n + 1) * sizeof(int32_t));
+        double* W = (double*)malloc((size_t)(n + 1) * sizeof(double));
+        if (!dist || !q || !cnt || !hop || !W) {
+#pragma omp atomic write
+            rc = ORC_ENOMEM;
+        } else {
+            for (int64_t v = 0; v < n; ++v) dist[v] = -1;
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t i = 0; i < m; ++i) {
+                int64_t f = fac ? fac[i] : i;
+                r[i] = exact_radius_one(g, f, cost[f], client, dist, q, cnt, hop, W);
+            }
+        }
+        free(dist); free(q); free(cnt); free(hop); free(W);
+    }
+    return rc;
+}
+
+/* r[f] for every vertex (+inf for non-facilities). */
+int orc_exact_radii(const orc_graph* g, const double* cost, const uint8_t* client, double* r) {
+    if (!g) return ORC_EINVAL;
+    return exact_radii_range(g, g->n, NULL, cost, client, r);
+}
+
+/* r[i] = the exact radius of facility fac[i] (a sample of the facilities). */
+int orc_exact_radii_of(const orc_graph* g, int64_t m, const int32_t* fac, const double* cost,
+                       const uint8_t* client, double* r) {
+    if (!g) return ORC_EINVAL;
+    for (int64_t i = 0; i < m; ++i)
+        if (fac[i] < 0 || fac[i] >= g->n) return ORC_EINVAL;
+    return exact_radii_range(g, m, fac, cost, client, r);
+}
+
 int orc_compute_radii(const orc_graph* g, const double* cost, const uint8_t* client, double* r) {
     if (!g || !g->built) return ORC_ESTATE;
 #pragma omp parallel for schedule(dynamic, 1024)
