@@ -41,6 +41,12 @@ DEFAULT_WORKLOAD = "rmat26"
 # bounded oracle samples (hops of its sketch build) per workload: ~10-30 s of CPU work
 CPU_SAMPLE_HOPS = {"er10k": 64, "rmat20": 64, "rmat26": 1}
 PROFILE_DIR = os.path.join(ROOT, "profiles")
+# exact-size workload: sampled sources, facilities and the k of the accuracy study
+EXACT_SEED = 13
+EXACT_SOURCES = 4096
+EXACT_FACILITIES = 16384
+EXACT_CPU_SOURCES = 256
+ACCURACY_K = (4, 8, 16, 32)
 
 
 def env_int(name, default):
@@ -168,10 +174,45 @@ def workload_config(w):
             "parallelism": "replicas (one instance per GPU)"}
 
 
+def run_reference_exact(args):
+    """The oracle's BFS ball sizes on the exact workload's graph: a bounded
+    sample of its sources per step (sources/s on the host cores)."""
+    import oracle
+
+    w = flsynth.config("rmat20")
+    rng = np.random.default_rng(EXACT_SEED)
+    src = rng.choice(w.n, size=EXACT_SOURCES, replace=False).astype(np.int32)[:EXACT_CPU_SOURCES]
+    g = oracle.Graph(w.rowp, w.cols)
+    for _ in range(args.warmup):
+        g.ball_sizes(src, 20)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        g.ball_sizes(src, 20)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = len(src) * len(times) / total
+    unit = "sources/s"
+    line = {"impl": "reference", "metric": "exact neighbourhood sizes (sources/s) and ADS accuracy vs k",
+            "value": value, "unit": unit, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "exact", "graph": f"rmat20 (n={w.n}, nnz={w.nnz})", "sources": len(src),
+                       "max_dist": 20},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"oracle BFS ball sizes of the first {len(src)} of the "
+                                       f"{EXACT_SOURCES} sampled sources per step"},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = env_int("RANK", 0)
     if rank != 0:
         return 0
+    if args.workload == "exact":
+        return run_reference_exact(args)
     w = flsynth.config(args.workload)
     hops = CPU_SAMPLE_HOPS.get(args.workload, 1)
     import oracle
@@ -350,6 +391,123 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+    return 0
+
+
+def run_exact(args):
+    """Exact neighbourhood sizes (bit-parallel BFS) on the R-MAT scale-20
+    graph: sources/s of fl_ball_sizes to distance 20, the ADS accuracy study
+    of Section 5.1 (Fig. 1: relative error of the HIP estimate against the
+    exact size, per k), and exact-count radii against the sketch radii."""
+    import torch
+
+    import paper_1503_03635_gb300 as fl
+
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fl.load()
+    w = flsynth.config("rmat20")
+    n = w.n
+    D = 20
+    rng = np.random.default_rng(EXACT_SEED)
+    src = rng.choice(n, size=EXACT_SOURCES, replace=False).astype(np.int32)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        g = fl.Graph(torch.from_numpy(w.rowp).to(dev), torch.from_numpy(w.cols).to(dev), stream=stream)
+        src_d = torch.from_numpy(src).to(dev)
+        out_d = torch.empty((len(src), D + 1), dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        g.ball_sizes(src_d, D, None, out=out_d)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    g.profile(True)
+    g.profile_reset()
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    px = g.profile_query("exact")
+    launches = g.profile_query(-1)["launches"]
+    g.profile(False)
+    peak, peak_kind = measured_peaks()
+    achieved = px["alg_bytes"] / (px["ms"] / 1e3) / 1e9 if px["ms"] > 0 else None
+    roofline = {"kernel": "k_x_light + k_x_heavy (one bottom-up level of 256 sources)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": ncu_traffic("k_x_level", "exact"),
+                "peak_kind": f"{peak_kind} copy bandwidth",
+                "alg_bytes_per_launch": px["alg_bytes"] / max(1, px["launches"]), "launches": px["launches"],
+                "kernel_ms": px["ms"], "share_of_step": px["ms"] / (ms * args.steps) if ms > 0 else None}
+    exact = out_d.cpu().numpy()
+
+    # ---- ADS accuracy vs k: 100 sampled vertices per distance 1..20
+    samp = np.stack([rng.choice(n, size=100, replace=False) for _ in range(D)]).astype(np.int32)
+    flat = samp.reshape(-1)
+    ex = g.ball_sizes(flat, D)
+    accuracy = {}
+    for k in ACCURACY_K:
+        g.build_sketches(k, w.seed)
+        est = g.ball_estimates(flat, D)
+        errs = []
+        for d in range(1, D + 1):
+            rows = slice((d - 1) * 100, d * 100)
+            se = ex[rows, d].astype(np.float64)
+            errs.append(np.abs(se - est[rows, d]) / se)
+        e = np.concatenate(errs)
+        accuracy[str(k)] = {"mean_rel_err": float(e.mean()), "var_rel_err": float(e.var()),
+                            "per_distance_mean": [round(float(x.mean()), 5) for x in errs]}
+
+    # ---- exact-count radii of sampled facilities vs the sketch radii
+    fac = rng.choice(n, size=EXACT_FACILITIES, replace=False).astype(np.int32)
+    cost = np.full(n, np.inf)
+    cost[fac] = w.cost[fac]
+    radii = {}
+    g.build_sketches(w.k, w.seed)
+    s = fl.Solve(g)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r_exact = s.compute_radii_exact(cost, w.client)
+    t_exact = time.perf_counter() - t0
+    s.open_facilities()
+    s.assign_clients()
+    obj_exact = s.objective()[0]
+    s.close()
+    for k in ACCURACY_K:
+        g.build_sketches(k, w.seed)
+        s = fl.Solve(g)
+        r = s.compute_radii(cost, w.client)
+        s.open_facilities()
+        s.assign_clients()
+        obj = s.objective()[0]
+        s.close()
+        fin = np.isfinite(r_exact[fac]) & np.isfinite(r[fac])
+        rel = np.abs(r[fac][fin] - r_exact[fac][fin]) / r_exact[fac][fin]
+        radii[str(k)] = {"mean_rel_err": float(rel.mean()), "p90_rel_err": float(np.percentile(rel, 90)),
+                         "objective_vs_exact": obj / obj_exact}
+    g.close()
+    if rank != 0:
+        return 0
+    line = {"metric": "exact neighbourhood sizes (sources/s) and ADS accuracy vs k", "value": len(src) / (ms / 1e3),
+            "unit": "sources/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "exact", "graph": f"rmat20 (n={n}, nnz={w.nnz})", "sources": len(src),
+                       "max_dist": D, "l2": "bit arrays (96 MB) mostly L2-resident; no flush"},
+            "roofline": roofline, "gpu_launches": launches, "clocks": clk,
+            "accuracy_vs_k": {"samples": "100 vertices per distance 1..20 (Section 5.1)", "by_k": accuracy},
+            "exact_radii": {"facilities": len(fac), "seconds": t_exact, "facilities_per_s": len(fac) / t_exact,
+                            "sketch_vs_exact_by_k": radii}}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -566,7 +724,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     help="er10k, rmat20, rmat26 (the named workloads), batch (solves/s batched vs plain), "
-                         "serve (Poisson query stream: p50/p99 latency, solves/s) "
+                         "serve (Poisson query stream: p50/p99 latency, solves/s), "
+                         "exact (exact neighbourhood sizes, ADS accuracy vs k, exact-count radii) "
                          "or rmatS for the rmat20 recipe at scale S")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -587,6 +746,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "exact":
+        return run_exact(args)
     return run_gpu(args)
 
 

@@ -178,6 +178,57 @@ int fl_objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserve
 int fl_solve_stats(const fl_solve* s, int64_t* mis_rounds, int64_t* candidates);
 
 /*
+ * Exact neighbourhood sizes and exact-count radii.  The paper checks the
+ * ADS estimates against exact neighbourhood sizes on sampled vertices
+ * (Section 5.1, "Accuracy vs. k", Fig. 1: relative error |S_E - S_ADS| / S_E
+ * per distance, against k).  These calls give both sides of that comparison
+ * on the GPU and an exact-radius mode of phase (ii).  The exact sizes come
+ * from a bit-parallel breadth-first search (256 sources per sweep, 96 bytes
+ * of device scratch per vertex, held by the graph), so their cost grows
+ * with the number of sources times the balls' edges: meant for sampled
+ * vertices and small or medium graphs.
+ */
+
+/*
+ * fl_ball_sizes -- exact sizes: out[s * (max_dist + 1) + h] = the number of
+ * vertices w with d(src[s], w) <= h and pred[w] != 0 (pred NULL: every
+ * vertex), h = 0..max_dist.  Needs fl_graph_create only.
+ *   src       int32[n_src], ids in [0, n) (else FL_EINVAL); repeats allowed.
+ *   max_dist  >= 0 (else FL_EINVAL).
+ *   pred      uint8[n] or NULL.
+ *   out       int64[n_src * (max_dist + 1)], source-major.
+ *   mem_kind  memory kind of src, pred and out.
+ */
+int fl_ball_sizes(fl_graph* g, int64_t n_src, const int32_t* src, int32_t max_dist, const uint8_t* pred,
+                  int mem_kind, int64_t* out);
+
+/*
+ * fl_ball_estimates -- the HIP estimates of the same sizes read off the ADS
+ * (Section 2.3's neighbourhood queries; with a predicate, the estimator of
+ * Section 3.4): out[s * (max_dist + 1) + h] = the sum over src[s]'s ADS
+ * groups at distance <= h, in distance order, of (entries of the group's
+ * weighted prefix with pred != 0) x the group's HIP weight, one FP64 add and
+ * multiply per group.  Needs fl_build_sketches (else FL_ESTATE).  Arguments
+ * as for fl_ball_sizes; out is double[n_src * (max_dist + 1)].
+ */
+int fl_ball_estimates(fl_graph* g, int64_t n_src, const int32_t* src, int32_t max_dist, const uint8_t* pred,
+                      int mem_kind, double* out);
+
+/*
+ * fl_compute_radii_exact -- phase (ii) with exact client counts: Eq. 1 at
+ * epsilon -> 0 as in fl_compute_radii, with W_h = the number of clients at
+ * distance exactly h of f (from breadth-first search) for h = 0..L, L the
+ * eccentricity of f.  r_f = j + (c - G_j) / N_j at the first j < L with
+ * G_{j+1} >= c, else L + (c - G_L) / N_L, +inf when N_L = 0 (N_j, G_j exact
+ * integers; three IEEE FP64 operations).  With k at least the component
+ * size every HIP weight is 1 and fl_compute_radii gives the same numbers.
+ * Arguments, state and errors as for fl_compute_radii; the later phases
+ * (fl_open_facilities ...) then run on these radii.
+ */
+int fl_compute_radii_exact(fl_solve* s, const double* open_cost, const uint8_t* client_mask, int mem_kind,
+                           double* radii_out);
+
+/*
  * Profiling (launch accounting and kernel timing of a graph and its solves).
  * The paper reports per-phase running times (Section 5); these calls give the
  * same split on the GPU.  Every kernel launch is counted per class; when
@@ -186,11 +237,15 @@ int fl_solve_stats(const fl_solve* s, int64_t* mis_rounds, int64_t* candidates);
  * Classes: FL_PROF_SKETCH_MERGE (the hop merge kernel), FL_PROF_SKETCH_EXPAND
  * (frontier expansion), FL_PROF_SKETCH_OTHER (rank init, ADS compaction,
  * eccentricity bound), FL_PROF_RADIUS, FL_PROF_KEYS (candidate sort),
- * FL_PROF_MIS, FL_PROF_BFS (assignment), FL_PROF_OTHER; -1 = all classes.
+ * FL_PROF_MIS, FL_PROF_BFS (assignment), FL_PROF_OTHER, FL_PROF_EXACT
+ * (exact sizes, their estimates, exact-count radii); -1 = all classes.
  * alg_bytes is filled for FL_PROF_SKETCH_MERGE: per hop, 8 B per merging
  * vertex (row offsets) + 4 B per edge-merge (column) + 8 B per neighbour
  * delta rank read + 16k B per merging vertex (own sketch read and write) +
- * 12 B per new ADS entry.
+ * 12 B per new ADS entry; and for FL_PROF_EXACT: per search level, 68 B per
+ * vertex (list id, visited words read, next words written) + 16 B per
+ * scanned row (offsets) + 36 B per scanned entry (column and the
+ * neighbour's frontier words).
  */
 #define FL_PROF_SKETCH_MERGE 0
 #define FL_PROF_SKETCH_EXPAND 1
@@ -200,6 +255,7 @@ int fl_solve_stats(const fl_solve* s, int64_t* mis_rounds, int64_t* candidates);
 #define FL_PROF_MIS 5
 #define FL_PROF_BFS 6
 #define FL_PROF_OTHER 7
+#define FL_PROF_EXACT 8
 
 /* fl_profile_enable -- turn CUDA-event timing of launches on (1) or off (0). */
 int fl_profile_enable(fl_graph* g, int on);

@@ -28,10 +28,11 @@ EXPORTS = ("fl_graph_create", "fl_graph_destroy", "fl_build_sketches", "fl_sketc
            "fl_compute_radii", "fl_open_facilities", "fl_assign_clients", "fl_objective",
            "fl_solve_stats", "fl_status_str", "fl_last_error", "fl_profile_enable", "fl_profile_reset",
            "fl_profile_query", "fl_hop_stats", "fl_batch_create_union", "fl_batch_create_replicas",
-           "fl_batch_solve", "fl_batch_info", "fl_batch_destroy", "fl_assign_nearest_noalloc")
+           "fl_batch_solve", "fl_batch_info", "fl_batch_destroy", "fl_assign_nearest_noalloc",
+           "fl_ball_sizes", "fl_ball_estimates", "fl_compute_radii_exact")
 
 PROF_CLASSES = {"sketch_merge": 0, "sketch_expand": 1, "sketch_other": 2, "radius": 3, "keys": 4,
-                "mis": 5, "bfs": 6, "other": 7}
+                "mis": 5, "bfs": 6, "other": 7, "exact": 8}
 
 
 class FLError(RuntimeError):
@@ -83,6 +84,9 @@ def load(build_if_missing: bool = True):
             "fl_batch_info": ([vp, P64, P64], ci),
             "fl_batch_destroy": ([vp], ci),
             "fl_assign_nearest_noalloc": ([i64, vp, vp, i64, vp, vp, vp, vp], ci),
+            "fl_ball_sizes": ([vp, i64, vp, ctypes.c_int32, vp, ci, vp], ci),
+            "fl_ball_estimates": ([vp, i64, vp, ctypes.c_int32, vp, ci, vp], ci),
+            "fl_compute_radii_exact": ([vp, vp, vp, ci, vp], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -198,6 +202,25 @@ class Graph:
         _check(self._lib.fl_profile_query(self._h, c, ctypes.byref(l), ctypes.byref(ms), ctypes.byref(b)))
         return dict(launches=l.value, ms=ms.value, alg_bytes=b.value)
 
+    def _ball_query(self, fn, dtype, src, max_dist, pred, out):
+        p_s, k_s, _ = _arg(src, np.int32)
+        p_p, k_p, _ = _arg(pred, np.uint8)
+        n_src = len(src)
+        if out is None and k_s != FL_MEM_DEVICE:
+            out = np.zeros((n_src, max_dist + 1), dtype)
+        p_o, k_o, _ = _arg(out)
+        _check(fn(self._h, n_src, p_s, int(max_dist), p_p, _kind(k_s, k_p, k_o), p_o))
+        return out
+
+    def ball_sizes(self, src, max_dist: int, pred=None, out=None):
+        """Exact |{w : d(v, w) <= h, pred[w]}| for v in src and h = 0..max_dist
+        (int64, one row per source) by bit-parallel BFS (Section 5.1, Fig. 1)."""
+        return self._ball_query(self._lib.fl_ball_sizes, np.int64, src, max_dist, pred, out)
+
+    def ball_estimates(self, src, max_dist: int, pred=None, out=None):
+        """HIP estimates of the same sizes from the ADS (float64 rows)."""
+        return self._ball_query(self._lib.fl_ball_estimates, np.float64, src, max_dist, pred, out)
+
     def export_sketches(self):
         S = np.zeros((self.n, self.k), np.uint64)
         cnt = np.zeros(self.n, np.int32)
@@ -246,6 +269,17 @@ class Solve:
             radii_out = np.zeros(self.graph.n, np.float64)
         p_r, k_r, _ = _arg(radii_out)
         _check(self._lib.fl_compute_radii(self._h, p_c, p_m, _kind(k_c, k_m, k_r), p_r))
+        return radii_out
+
+    def compute_radii_exact(self, cost, client, radii_out=None):
+        """Phase (ii) with exact client counts per distance (BFS) in place of
+        the HIP estimates; the later phases then use these radii."""
+        p_c, k_c, _ = _arg(cost, np.float64)
+        p_m, k_m, _ = _arg(client, np.uint8)
+        if radii_out is None and k_c != FL_MEM_DEVICE:
+            radii_out = np.zeros(self.graph.n, np.float64)
+        p_r, k_r, _ = _arg(radii_out)
+        _check(self._lib.fl_compute_radii_exact(self._h, p_c, p_m, _kind(k_c, k_m, k_r), p_r))
         return radii_out
 
     def open_facilities(self, open_out=None):

@@ -37,7 +37,7 @@ void destroy_graph(fl_graph* g) {
                     &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent, &g->stg_grp, &g->gofs, &g->eofs,
                     &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub, &g->ctr, &g->scratch,
                     &g->relax_aux, &g->U, &g->DM[0], &g->DM[1], &g->PM, &g->vbase, &g->vpart, &g->rid,
-                    &g->inv};
+                    &g->inv, &g->xbits, &g->xaux, &g->xio};
     for (DBuf* b : bufs) dfree_idle(*b);
     for (cudaEvent_t e : g->prof.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : g->hop_ev)
@@ -75,6 +75,72 @@ int check_solve(fl_solve* s) {
     if (!s || !s->g) FL_FAIL(FL_EINVAL, "null solve handle");
     if (!s->g->built || s->generation != s->g->generation)
         FL_FAIL(FL_ESTATE, "the graph's sketches were rebuilt after this solve was created");
+    return FL_OK;
+}
+
+// Opening costs and client mask (original order) into the solve (internal order).
+int load_solve_inputs(fl_solve* s, const double* open_cost, const uint8_t* client_mask, int mem_kind) {
+    fl_graph* g = s->g;
+    cudaStream_t st = g->stream;
+    if (g->relabelled) {
+        FL_TRY(dalloc(s->io, (size_t)g->n * 9));
+        uint8_t* io = s->io.as<uint8_t>();
+        FL_CUDA(cudaMemcpyAsync(io, open_cost, (size_t)g->n * 8, kind_in(mem_kind), st));
+        FL_CUDA(cudaMemcpyAsync(io + (size_t)g->n * 8, client_mask, (size_t)g->n, kind_in(mem_kind), st));
+        FL_TRY(permute_vertices<double>(g, reinterpret_cast<double*>(io), s->cost.as<double>(), 1, true, st));
+        FL_TRY(permute_vertices<uint8_t>(g, io + (size_t)g->n * 8, s->client.as<uint8_t>(), 1, true, st));
+    } else {
+        FL_CUDA(cudaMemcpyAsync(s->cost.p, open_cost, (size_t)g->n * 8, kind_in(mem_kind), st));
+        FL_CUDA(cudaMemcpyAsync(s->client.p, client_mask, (size_t)g->n, kind_in(mem_kind), st));
+    }
+    return FL_OK;
+}
+
+// The solve's radii (internal order) to radii_out (original order, or
+// nothing when NULL); waits for the stream.
+int copy_radii_out(fl_solve* s, double* radii_out, int mem_kind) {
+    fl_graph* g = s->g;
+    if (radii_out && g->relabelled) {
+        FL_TRY(dalloc(s->io, (size_t)g->n * 9));
+        FL_TRY(permute_vertices<double>(g, s->radii.as<double>(), s->io.as<double>(), 1, false, g->stream));
+        FL_TRY(copy_out(radii_out, s->io.p, (size_t)g->n * 8, mem_kind, g->stream));
+    } else {
+        FL_TRY(copy_out(radii_out, s->radii.p, (size_t)g->n * 8, mem_kind, g->stream));
+    }
+    FL_CUDA(cudaStreamSynchronize(g->stream));
+    return FL_OK;
+}
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Stages a neighbourhood query in g->xio: the sources mapped to internal
+// ids, the predicate in internal order (NULL stays NULL) and an output of
+// n_src * (D + 1) elements of `elem` bytes.
+int stage_query(fl_graph* g, int64_t n_src, const int32_t* src, int64_t D, const uint8_t* pred, int mem_kind,
+                size_t elem, int32_t** src_d, uint8_t** pred_d, void** out_d) {
+    cudaStream_t st = g->stream;
+    if ((double)n_src * (double)(D + 1) * (double)elem > 9.0e15) FL_FAIL(FL_ENOMEM, "query output too large");
+    const size_t a = up256((size_t)n_src * 4), p = pred ? up256((size_t)g->n) : 0;
+    const size_t o = (size_t)n_src * (size_t)(D + 1) * elem;
+    FL_TRY(dalloc(g->xio, 2 * a + 2 * p + o));
+    char* base = g->xio.as<char>();
+    int32_t* raw = reinterpret_cast<int32_t*>(base);
+    *src_d = reinterpret_cast<int32_t*>(base + a);
+    FL_CUDA(cudaMemcpyAsync(raw, src, (size_t)n_src * 4, kind_in(mem_kind), st));
+    FL_TRY(map_sources(g, raw, n_src, *src_d));
+    *pred_d = nullptr;
+    if (pred) {
+        uint8_t* p0 = reinterpret_cast<uint8_t*>(base + 2 * a);
+        uint8_t* p1 = p0 + p;
+        FL_CUDA(cudaMemcpyAsync(p0, pred, (size_t)g->n, kind_in(mem_kind), st));
+        if (g->relabelled) {
+            FL_TRY(permute_vertices<uint8_t>(g, p0, p1, 1, true, st));
+            *pred_d = p1;
+        } else {
+            *pred_d = p0;
+        }
+    }
+    *out_d = base + 2 * a + 2 * p;
     return FL_OK;
 }
 
@@ -323,30 +389,25 @@ int fl_compute_radii(fl_solve* s, const double* open_cost, const uint8_t* client
     FL_TRY(check_solve(s));
     if (!open_cost || !client_mask) FL_FAIL(FL_EINVAL, "open_cost and client_mask are required");
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
-    fl_graph* g = s->g;
-    ProfScope ps(g);
-    cudaStream_t st = g->stream;
+    ProfScope ps(s->g);
     s->have_radii = s->have_open = s->have_assign = 0;
-    if (g->relabelled) {  // inputs in original order -> internal order
-        FL_TRY(dalloc(s->io, (size_t)g->n * 9));
-        uint8_t* io = s->io.as<uint8_t>();
-        FL_CUDA(cudaMemcpyAsync(io, open_cost, (size_t)g->n * 8, kind_in(mem_kind), st));
-        FL_CUDA(cudaMemcpyAsync(io + (size_t)g->n * 8, client_mask, (size_t)g->n, kind_in(mem_kind), st));
-        FL_TRY(permute_vertices<double>(g, reinterpret_cast<double*>(io), s->cost.as<double>(), 1, true, g->stream));
-        FL_TRY(permute_vertices<uint8_t>(g, io + (size_t)g->n * 8, s->client.as<uint8_t>(), 1, true, g->stream));
-    } else {
-        FL_CUDA(cudaMemcpyAsync(s->cost.p, open_cost, (size_t)g->n * 8, kind_in(mem_kind), st));
-        FL_CUDA(cudaMemcpyAsync(s->client.p, client_mask, (size_t)g->n, kind_in(mem_kind), st));
-    }
+    FL_TRY(load_solve_inputs(s, open_cost, client_mask, mem_kind));
     FL_TRY(compute_radii(s));
-    if (radii_out && g->relabelled) {
-        FL_TRY(dalloc(s->io, (size_t)g->n * 9));
-        FL_TRY(permute_vertices<double>(g, s->radii.as<double>(), s->io.as<double>(), 1, false, g->stream));
-        FL_TRY(copy_out(radii_out, s->io.p, (size_t)g->n * 8, mem_kind, st));
-    } else {
-        FL_TRY(copy_out(radii_out, s->radii.p, (size_t)g->n * 8, mem_kind, st));
-    }
-    FL_CUDA(cudaStreamSynchronize(st));
+    FL_TRY(copy_radii_out(s, radii_out, mem_kind));
+    s->have_radii = 1;
+    return FL_OK;
+}
+
+int fl_compute_radii_exact(fl_solve* s, const double* open_cost, const uint8_t* client_mask, int mem_kind,
+                           double* radii_out) {
+    FL_TRY(check_solve(s));
+    if (!open_cost || !client_mask) FL_FAIL(FL_EINVAL, "open_cost and client_mask are required");
+    if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    ProfScope ps(s->g);
+    s->have_radii = s->have_open = s->have_assign = 0;
+    FL_TRY(load_solve_inputs(s, open_cost, client_mask, mem_kind));
+    FL_TRY(exact_radii(s));
+    FL_TRY(copy_radii_out(s, radii_out, mem_kind));
     s->have_radii = 1;
     return FL_OK;
 }
@@ -404,6 +465,44 @@ int fl_objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserve
     if (obj) *obj = o;
     if (dist_sum) *dist_sum = ds;
     if (n_unserved) *n_unserved = un;
+    return FL_OK;
+}
+
+
+int fl_ball_sizes(fl_graph* g, int64_t n_src, const int32_t* src, int32_t max_dist, const uint8_t* pred,
+                  int mem_kind, int64_t* out) {
+    if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    if (n_src < 0 || max_dist < 0) FL_FAIL(FL_EINVAL, "n_src and max_dist must be >= 0");
+    if (n_src > 0 && (!src || !out)) FL_FAIL(FL_EINVAL, "src and out are required");
+    if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    if (n_src == 0) return FL_OK;
+    ProfScope ps(g);
+    int32_t* src_d;
+    uint8_t* pred_d;
+    void* out_d;
+    FL_TRY(stage_query(g, n_src, src, max_dist, pred, mem_kind, 8, &src_d, &pred_d, &out_d));
+    FL_TRY(exact_ball_sizes(g, n_src, src_d, max_dist, pred_d, static_cast<int64_t*>(out_d)));
+    FL_TRY(copy_out(out, out_d, (size_t)n_src * (size_t)(max_dist + 1) * 8, mem_kind, g->stream));
+    FL_CUDA(cudaStreamSynchronize(g->stream));
+    return FL_OK;
+}
+
+int fl_ball_estimates(fl_graph* g, int64_t n_src, const int32_t* src, int32_t max_dist, const uint8_t* pred,
+                      int mem_kind, double* out) {
+    if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    if (!g->built) FL_FAIL(FL_ESTATE, "sketches not built");
+    if (n_src < 0 || max_dist < 0) FL_FAIL(FL_EINVAL, "n_src and max_dist must be >= 0");
+    if (n_src > 0 && (!src || !out)) FL_FAIL(FL_EINVAL, "src and out are required");
+    if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    if (n_src == 0) return FL_OK;
+    ProfScope ps(g);
+    int32_t* src_d;
+    uint8_t* pred_d;
+    void* out_d;
+    FL_TRY(stage_query(g, n_src, src, max_dist, pred, mem_kind, 8, &src_d, &pred_d, &out_d));
+    FL_TRY(hip_ball_estimates(g, n_src, src_d, max_dist, pred_d, static_cast<double*>(out_d)));
+    FL_TRY(copy_out(out, out_d, (size_t)n_src * (size_t)(max_dist + 1) * 8, mem_kind, g->stream));
+    FL_CUDA(cudaStreamSynchronize(g->stream));
     return FL_OK;
 }
 

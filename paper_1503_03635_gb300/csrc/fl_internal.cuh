@@ -342,7 +342,8 @@ enum ProfClass {
     kProfMis = 5,          // greedy-MIS rounds
     kProfBfs = 6,          // assignment BFS
     kProfOther = 7,        // validation, exports, objective
-    kProfClasses = 8
+    kProfExact = 8,        // exact ball sizes, their HIP estimates, exact-count radii
+    kProfClasses = 9
 };
 
 struct Prof {
@@ -430,6 +431,9 @@ struct fl_graph {
     std::vector<int64_t> hop_scanned, hop_mask, hop_changed;
     std::vector<double> hop_ms;
     cudaEvent_t hop_ev[2] = {nullptr, nullptr};
+    // exact sizes and radii: source bits (visited, two frontiers), row-length
+    // lists and sweep state, staged query inputs and outputs
+    fl::DBuf xbits, xaux, xio;
 };
 
 namespace fl {
@@ -517,6 +521,11 @@ int relax_prepare_list(fl_graph* g, Relax& r, int cls);
 int relax_collect_epoch(fl_graph* g, const unsigned long long* X, unsigned long long hi, int32_t* out,
                         unsigned long long* n_out, int cls);
 int assign_clients(fl_solve* s);
+// exact neighbourhood sizes, their HIP estimates, exact-count radii (k_exact.cu)
+int map_sources(fl_graph* g, const int32_t* in, int64_t n_src, int32_t* out);
+int exact_ball_sizes(fl_graph* g, int64_t n_src, const int32_t* src, int64_t D, const uint8_t* pred, int64_t* out);
+int hip_ball_estimates(fl_graph* g, int64_t n_src, const int32_t* src, int64_t D, const uint8_t* pred, double* out);
+int exact_radii(fl_solve* s);
 int objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserved);
 
 int read_counters(fl_graph* g);
