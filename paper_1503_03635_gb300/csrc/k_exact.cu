@@ -6,17 +6,24 @@
 //
 // Exact sizes come from a bit-parallel breadth-first search.  One sweep
 // serves 256 sources; every vertex holds 4 words of source bits for
-// "visited", "frontier" and "next".  A level is one bottom-up pass: vertex v
-// ORs its neighbours' frontier words, keeps the bits of running sources
-// that have not reached it yet, and counts them per source (under the
-// predicate).  A source stops when its question is answered -- ball sizes at
-// the largest distance asked for or when its component is exhausted, a
-// radius when the walk of Eq. 1 has its root -- and its bit is masked out of
-// every later level, so vertices every running source has reached are
-// skipped.  Rows longer than 32 entries get a whole warp (8 neighbours x 4
-// words per step, stopping once every needed bit is in); shorter rows get 4
-// lanes, one word each, so the 4 words of a neighbour are one 32-byte
-// sector.
+// "visited", "frontier" and "next".  A source stops when its question is
+// answered -- ball sizes at the largest distance asked for or when its
+// component is exhausted, a radius when the walk of Eq. 1 has its root --
+// and its bit is masked out of every later level.  Each level runs in one of
+// two directions (Beamer, Asanovic, Patterson, SC 2012), chosen from the
+// frontier's row entries against the entries of rows that still need bits:
+//   bottom-up: every vertex that some running source has not reached ORs
+//     its neighbours' frontier words and keeps the new bits.  Rows longer
+//     than 32 entries get a whole warp (8 neighbours x 4 words per step,
+//     stopping once every needed bit is in); shorter rows get 4 lanes, one
+//     word each, so the 4 words of a neighbour are one 32-byte sector.
+//   top-down (sparse frontiers, e.g. the sources themselves): the frontier
+//     rows, cut into work items of 256 entries (so a hub's row is spread
+//     over many warps), OR their bits into the neighbours' next words
+//     (atomicOr); one pass over all vertices then folds the new bits into
+//     "visited" and counts them.
+// Both directions count the new bits per source under the predicate and
+// list the next frontier with its row entries.
 #include <cmath>
 
 #include "fl_internal.cuh"
@@ -38,7 +45,15 @@ struct XState {
     unsigned long long cnt[kXS];     // this level's newly reached vertices under the predicate
     long long N[kXS];                // sizes: running ball size; radius: N_j
     long long G[kXS], Gp[kXS];       // radius: G_{j+1} and G_j of the walk
-    unsigned long long rows, entries;  // rows scanned and their entries read (this sweep)
+    unsigned long long rows, entries;  // rows scanned and their entries read (this sweep, cumulative)
+    unsigned long long n_next;       // this level: vertices listed in the next frontier
+    unsigned long long fr_edges;     // this level: row entries of the next frontier
+    unsigned long long rem_edges;    // bottom-up level: row entries of vertices that still need bits
+};
+
+// Per-lane sums a level kernel flushes once.
+struct XSums {
+    unsigned long long rows = 0, entries = 0, fr_edges = 0, rem_edges = 0;
 };
 
 int blocks_for(int64_t items, int64_t per_block) {
@@ -99,16 +114,12 @@ __global__ void k_x_facilities(const double* __restrict__ cost, int64_t n, int32
 }
 
 // Start of a sweep: the sources' own bits in "visited" and "frontier"
-// (which the host cleared), cleared counters.  One block of kXS threads.
-__global__ void k_x_seed(const int32_t* __restrict__ src, int64_t nb, unsigned long long* __restrict__ vis,
-                         unsigned long long* __restrict__ cur, XState* __restrict__ st) {
+// (which the host cleared), the sources as the first frontier list, cleared
+// counters.  One block of kXS threads.
+__global__ void k_x_seed(const int32_t* __restrict__ src, int64_t nb, const int64_t* __restrict__ rowp,
+                         unsigned long long* __restrict__ vis, unsigned long long* __restrict__ cur,
+                         int32_t* __restrict__ front, XState* __restrict__ st) {
     const int s = threadIdx.x;
-    if (s < nb) {
-        const int32_t v = src[s];
-        const unsigned long long bit = 1ULL << (s & 63);
-        atomicOr(&vis[(int64_t)v * kXW + (s >> 6)], bit);
-        atomicOr(&cur[(int64_t)v * kXW + (s >> 6)], bit);
-    }
     st->cnt[s] = 0;
     st->N[s] = 0;
     st->G[s] = 0;
@@ -118,15 +129,28 @@ __global__ void k_x_seed(const int32_t* __restrict__ src, int64_t nb, unsigned l
         st->active[s] = m <= 0 ? 0ULL : (m >= 64 ? ~0ULL : ((1ULL << m) - 1ULL));
         st->any[s] = 0;
     }
-    if (s == 0) st->rows = st->entries = 0;
+    if (s == 0) {
+        st->rows = st->entries = 0;
+        st->n_next = (unsigned long long)nb;
+        st->fr_edges = st->rem_edges = 0;
+    }
+    __syncthreads();
+    if (s < nb) {
+        const int32_t v = src[s];
+        const unsigned long long bit = 1ULL << (s & 63);
+        atomicOr(&vis[(int64_t)v * kXW + (s >> 6)], bit);
+        atomicOr(&cur[(int64_t)v * kXW + (s >> 6)], bit);
+        front[s] = v;  // a source listed twice is harmless
+        atomicAdd(&st->fr_edges, (unsigned long long)(rowp[v + 1] - rowp[v]));
+    }
 }
 
+
 // Per-lane counters of one word's bits -> the sweep's per-source counts
-// (lane (q, w) owns bits 8j + q of word w, j = 0..7), and the OR of the new
-// bits.  Every thread of the block calls.
-__device__ __forceinline__ void x_flush(const unsigned (&c)[8], unsigned long long any, unsigned long long rows,
-                                        unsigned long long entries, unsigned* s_cnt, unsigned long long* s_any,
-                                        XState* st) {
+// (lane (q, w) owns bits 8j + q of word w, j = 0..7), the OR of the new
+// bits and the level's sums.  Every thread of the block calls.
+__device__ __forceinline__ void x_flush(const unsigned (&c)[8], unsigned long long any, XSums m, unsigned* s_cnt,
+                                        unsigned long long* s_any, XState* st) {
     const int lane = lane_id();
     const int w = lane & 3, q = lane >> 2;
 #pragma unroll
@@ -138,12 +162,16 @@ __device__ __forceinline__ void x_flush(const unsigned (&c)[8], unsigned long lo
     if (lane < kXW && any) atomicOr(&s_any[lane], any);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        rows += __shfl_xor_sync(kFull, rows, o);
-        entries += __shfl_xor_sync(kFull, entries, o);
+        m.rows += __shfl_xor_sync(kFull, m.rows, o);
+        m.entries += __shfl_xor_sync(kFull, m.entries, o);
+        m.fr_edges += __shfl_xor_sync(kFull, m.fr_edges, o);
+        m.rem_edges += __shfl_xor_sync(kFull, m.rem_edges, o);
     }
-    if (lane == 0 && rows) {
-        atomicAdd(&st->rows, rows);
-        atomicAdd(&st->entries, entries);
+    if (lane == 0) {
+        if (m.rows) atomicAdd(&st->rows, m.rows);
+        if (m.entries) atomicAdd(&st->entries, m.entries);
+        if (m.fr_edges) atomicAdd(&st->fr_edges, m.fr_edges);
+        if (m.rem_edges) atomicAdd(&st->rem_edges, m.rem_edges);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kXS; i += blockDim.x)
@@ -151,13 +179,28 @@ __device__ __forceinline__ void x_flush(const unsigned (&c)[8], unsigned long lo
     if (threadIdx.x < kXW && s_any[threadIdx.x]) atomicOr(&st->any[threadIdx.x], s_any[threadIdx.x]);
 }
 
-// One level for vertices with short rows: 4 lanes per vertex (lane w holds
-// word w), 8 vertices per warp.
+// Counts bit b of word w of cv over the warp's 8 vertices (lanes w, w+4,
+// ..., w+28 hold word w) into the owning lanes' counters.
+__device__ __forceinline__ void x_count_quads(unsigned long long cv, unsigned (&c)[8]) {
+    const int lane = lane_id();
+    const unsigned wm = 0x11111111u << (lane & 3);
+    const int q = lane >> 2;
+#pragma unroll
+    for (int b = 0; b < 64; ++b) {
+        const unsigned bal = __ballot_sync(kFull, (cv >> b) & 1ULL);
+        if (q == (b & 7)) c[b >> 3] += __popc(bal & wm);
+    }
+}
+
+// Bottom-up level for vertices with short rows: 4 lanes per vertex (lane w
+// holds word w), 8 vertices per warp; each lane loads every fourth column of
+// the row and the quad shares them, so 8 neighbours' words are in flight.
 __global__ void __launch_bounds__(256) k_x_light(const int32_t* __restrict__ list, int64_t n_list,
                                                  const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
                                                  const unsigned long long* __restrict__ cur,
                                                  unsigned long long* __restrict__ nxt, unsigned long long* vis,
-                                                 const uint8_t* __restrict__ pred, XState* __restrict__ st) {
+                                                 const uint8_t* __restrict__ pred, int32_t* __restrict__ next_front,
+                                                 XState* __restrict__ st) {
     __shared__ unsigned s_cnt[kXS];
     __shared__ unsigned long long s_any[kXW];
     for (int i = threadIdx.x; i < kXS; i += blockDim.x) s_cnt[i] = 0;
@@ -165,9 +208,11 @@ __global__ void __launch_bounds__(256) k_x_light(const int32_t* __restrict__ lis
     __syncthreads();
     const int lane = lane_id();
     const int w = lane & 3, q = lane >> 2;
+    const unsigned qm = 0xFu << (lane & ~3);
     const unsigned long long act = st->active[w];
     unsigned c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    unsigned long long any = 0, rows = 0, entries = 0;
+    unsigned long long any = 0;
+    XSums m;
     const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 2;
     for (int64_t base = (((int64_t)blockIdx.x * blockDim.x) + (threadIdx.x & ~31)) >> 2; base < n_list;
          base += stride) {
@@ -178,19 +223,27 @@ __global__ void __launch_bounds__(256) k_x_light(const int32_t* __restrict__ lis
         const unsigned long long need = act & ~vw;
         const unsigned nb = __ballot_sync(kFull, need != 0);
         unsigned long long nx = 0;
+        int64_t deg = 0;
         if ((nb >> (lane & ~3)) & 0xFu) {  // some word of this vertex still needs bits
-            int64_t e = __ldg(&rowp[v]);
-            const int64_t end = __ldg(&rowp[v + 1]);
+            const int64_t beg = __ldg(&rowp[v]), end = __ldg(&rowp[v + 1]);
+            deg = end - beg;
             if (w == 0) {
-                ++rows;
-                entries += (unsigned long long)(end - e);
+                ++m.rows;
+                m.entries += (unsigned long long)deg;
             }
             unsigned long long acc = 0;
-            for (; e + 1 < end; e += 2) {
-                const int32_t u0 = __ldg(&cols[e]), u1 = __ldg(&cols[e + 1]);
-                acc |= __ldg(&cur[(int64_t)u0 * kXW + w]) | __ldg(&cur[(int64_t)u1 * kXW + w]);
+            for (int64_t e0 = beg; e0 < end; e0 += 8) {
+                const int64_t ea = e0 + w, eb = e0 + 4 + w;
+                const int32_t ua = ea < end ? __ldg(&cols[ea]) : -1;
+                const int32_t ub = eb < end ? __ldg(&cols[eb]) : -1;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int32_t x = __shfl_sync(qm, ua, j, 4);
+                    const int32_t y = __shfl_sync(qm, ub, j, 4);
+                    if (x >= 0) acc |= __ldg(&cur[(int64_t)x * kXW + w]);
+                    if (y >= 0) acc |= __ldg(&cur[(int64_t)y * kXW + w]);
+                }
             }
-            if (e < end) acc |= __ldg(&cur[(int64_t)__ldg(&cols[e]) * kXW + w]);
             nx = acc & need;
         }
         if (valid) {
@@ -198,29 +251,30 @@ __global__ void __launch_bounds__(256) k_x_light(const int32_t* __restrict__ lis
             if (nx) vis[(int64_t)v * kXW + w] = vw | nx;
         }
         any |= nx;
-        const unsigned long long cv = (valid && (!pred || pred[v])) ? nx : 0ULL;
-        if (__ballot_sync(kFull, cv != 0)) {
-            // count bit b of word w over the warp's 8 vertices: the lanes
-            // holding word w are w, w+4, ..., w+28
-            const unsigned wm = 0x11111111u << w;
-#pragma unroll
-            for (int b = 0; b < 64; ++b) {
-                const unsigned bal = __ballot_sync(kFull, (cv >> b) & 1ULL);
-                if (q == (b & 7)) c[b >> 3] += __popc(bal & wm);
-            }
+        // the vertex joins the next frontier; or still needs bits afterwards
+        const bool got = (__ballot_sync(kFull, nx != 0) >> (lane & ~3)) & 0xFu;
+        const bool left = (__ballot_sync(kFull, (need & ~nx) != 0) >> (lane & ~3)) & 0xFu;
+        const long long at = warp_append(w == 0 && got, &st->n_next);
+        if (at >= 0) {
+            next_front[at] = v;
+            m.fr_edges += (unsigned long long)deg;
         }
+        if (w == 0 && left) m.rem_edges += (unsigned long long)deg;
+        const unsigned long long cv = (valid && (!pred || pred[v])) ? nx : 0ULL;
+        if (__ballot_sync(kFull, cv != 0)) x_count_quads(cv, c);
     }
-    x_flush(c, any, rows, entries, s_cnt, s_any, st);
+    x_flush(c, any, m, s_cnt, s_any, st);
 }
 
-// One level for vertices with long rows: a warp per vertex, lane (t, w)
-// reads word w of neighbours t, t+8, ...; every 256 entries the warp stops
-// if its OR already holds every bit the vertex needs.
+// Bottom-up level for vertices with long rows: a warp per vertex, lane
+// (t, w) reads word w of neighbours t, t+8, ...; every 256 entries the warp
+// stops if its OR already holds every bit the vertex needs.
 __global__ void __launch_bounds__(256) k_x_heavy(const int32_t* __restrict__ list, int64_t n_list,
                                                  const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
                                                  const unsigned long long* __restrict__ cur,
                                                  unsigned long long* __restrict__ nxt, unsigned long long* vis,
-                                                 const uint8_t* __restrict__ pred, XState* __restrict__ st) {
+                                                 const uint8_t* __restrict__ pred, int32_t* __restrict__ next_front,
+                                                 XState* __restrict__ st) {
     __shared__ unsigned s_cnt[kXS];
     __shared__ unsigned long long s_any[kXW];
     for (int i = threadIdx.x; i < kXS; i += blockDim.x) s_cnt[i] = 0;
@@ -230,15 +284,18 @@ __global__ void __launch_bounds__(256) k_x_heavy(const int32_t* __restrict__ lis
     const int w = lane & 3, t = lane >> 2;
     const unsigned long long act = st->active[w];
     unsigned c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    unsigned long long any = 0, rows = 0, entries = 0;
+    unsigned long long any = 0;
+    XSums m;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; i < n_list; i += warps) {
         const int32_t v = __ldg(&list[i]);
         const unsigned long long vw = vis[(int64_t)v * kXW + w];
         const unsigned long long need = act & ~vw;
         unsigned long long nx = 0;
+        int64_t deg = 0;
         if (__any_sync(kFull, need != 0)) {
             const int64_t beg = __ldg(&rowp[v]), end = __ldg(&rowp[v + 1]);
+            deg = end - beg;
             int64_t stop = end;
             unsigned long long acc = 0;
             for (int64_t b0 = beg; b0 < end; b0 += 16) {
@@ -262,8 +319,8 @@ __global__ void __launch_bounds__(256) k_x_heavy(const int32_t* __restrict__ lis
             acc |= __shfl_xor_sync(kFull, acc, 16);
             nx = acc & need;
             if (lane == 0) {
-                ++rows;
-                entries += (unsigned long long)(stop - beg);
+                ++m.rows;
+                m.entries += (unsigned long long)(stop - beg);
             }
         }
         if (t == 0) {
@@ -271,12 +328,133 @@ __global__ void __launch_bounds__(256) k_x_heavy(const int32_t* __restrict__ lis
             if (nx) vis[(int64_t)v * kXW + w] = vw | nx;
         }
         any |= nx;
+        const bool got = __any_sync(kFull, nx != 0);
+        const bool left = __any_sync(kFull, (need & ~nx) != 0);
+        const long long at = warp_append(lane == 0 && got, &st->n_next);
+        if (at >= 0) {
+            next_front[at] = v;
+            m.fr_edges += (unsigned long long)deg;
+        }
+        if (lane == 0 && left) m.rem_edges += (unsigned long long)deg;
         // every lane holds its word's new bits; lane (t, w) counts bits 8j + t
         const unsigned long long cv = (!pred || pred[v]) ? nx : 0ULL;
 #pragma unroll
         for (int j = 0; j < 8; ++j) c[j] += (unsigned)((cv >> (8 * j + t)) & 1ULL);
     }
-    x_flush(c, any, rows, entries, s_cnt, s_any, st);
+    x_flush(c, any, m, s_cnt, s_any, st);
+}
+
+// Top-down level, step 1: the frontier rows as work items of at most
+// kXSeg entries (vertex << 32 | segment), so that a hub's row is spread over
+// many warps.  A vertex without running bits gives none.
+constexpr int kXSeg = 256;
+
+__global__ void k_x_td_items(const int32_t* __restrict__ front, int64_t n_front, const int64_t* __restrict__ rowp,
+                             const unsigned long long* __restrict__ cur, unsigned long long* __restrict__ items,
+                             XState* __restrict__ st) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = lane_id();
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_front; base += stride) {
+        const int64_t i = base + lane;
+        int segs = 0;
+        int32_t u = 0;
+        if (i < n_front) {
+            u = __ldg(&front[i]);
+            const int64_t o = (int64_t)u * kXW;
+            const bool live = ((__ldg(&cur[o]) & st->active[0]) | (__ldg(&cur[o + 1]) & st->active[1]) |
+                               (__ldg(&cur[o + 2]) & st->active[2]) | (__ldg(&cur[o + 3]) & st->active[3])) != 0;
+            const int64_t deg = __ldg(&rowp[u + 1]) - __ldg(&rowp[u]);
+            segs = live ? (int)((deg + kXSeg - 1) / kXSeg) : 0;
+        }
+        const int incl = warp_incl_scan(segs);
+        const int total = __shfl_sync(kFull, incl, 31);
+        unsigned long long at = 0;
+        if (lane == 31 && total) at = atomicAdd(&st->n_next, (unsigned long long)total);
+        at = __shfl_sync(kFull, at, 31) + (unsigned long long)(incl - segs);
+        for (int j = 0; j < segs; ++j) items[at + j] = ((unsigned long long)(uint32_t)u << 32) | (unsigned)j;
+    }
+}
+
+// Step 2: a warp per work item, lane (t, w) takes word w of the row owner's
+// running bits to entries t, t+8, ...: the bits a neighbour has not visited
+// go into its next words (atomicOr; the host cleared them).
+__global__ void __launch_bounds__(256) k_x_td(const unsigned long long* __restrict__ items,
+                                              const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
+                                              const unsigned long long* __restrict__ cur,
+                                              unsigned long long* __restrict__ nxt,
+                                              const unsigned long long* __restrict__ vis, XState* __restrict__ st) {
+    const int lane = lane_id();
+    const int w = lane & 3, t = lane >> 2;
+    const unsigned long long act = st->active[w];
+    const int64_t n_items = (int64_t)st->n_next;
+    unsigned long long rows = 0, entries = 0;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; i < n_items; i += warps) {
+        const unsigned long long it = __ldg(&items[i]);
+        const int32_t u = (int32_t)(it >> 32);
+        const int64_t seg = (int64_t)(it & 0xffffffffULL);
+        const unsigned long long bits = __ldg(&cur[(int64_t)u * kXW + w]) & act;
+        const int64_t row_end = __ldg(&rowp[u + 1]);
+        const int64_t beg = __ldg(&rowp[u]) + seg * kXSeg;
+        const int64_t end = beg + kXSeg < row_end ? beg + kXSeg : row_end;
+        if (lane == 0) {
+            rows += seg == 0 ? 1 : 0;
+            entries += (unsigned long long)(end - beg);
+        }
+#pragma unroll 4
+        for (int64_t b0 = beg; b0 < end; b0 += 8) {
+            const int64_t e = b0 + t;
+            if (e < end) {
+                const int32_t v = __ldg(&cols[e]);
+                const unsigned long long nb = bits & ~__ldg(&vis[(int64_t)v * kXW + w]);
+                if (nb) atomicOr(&nxt[(int64_t)v * kXW + w], nb);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rows += __shfl_xor_sync(kFull, rows, o);
+        entries += __shfl_xor_sync(kFull, entries, o);
+    }
+    if (lane == 0 && rows) {
+        atomicAdd(&st->rows, rows);
+        atomicAdd(&st->entries, entries);
+    }
+}
+
+// Step 3, over every vertex (4 lanes per vertex): fold the new bits into
+// "visited", count them, list the next frontier and its row entries.
+__global__ void __launch_bounds__(256) k_x_td_finish(int64_t n, const int64_t* __restrict__ rowp,
+                                                     const unsigned long long* __restrict__ nxt,
+                                                     unsigned long long* vis, const uint8_t* __restrict__ pred,
+                                                     int32_t* __restrict__ next_front, XState* __restrict__ st) {
+    __shared__ unsigned s_cnt[kXS];
+    __shared__ unsigned long long s_any[kXW];
+    for (int i = threadIdx.x; i < kXS; i += blockDim.x) s_cnt[i] = 0;
+    if (threadIdx.x < kXW) s_any[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = lane_id();
+    const int w = lane & 3, q = lane >> 2;
+    unsigned c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long any = 0;
+    XSums m;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 2;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x) + (threadIdx.x & ~31)) >> 2; base < n; base += stride) {
+        const int64_t v = base + q;
+        const bool valid = v < n;
+        const unsigned long long nx = valid ? nxt[v * kXW + w] : 0ULL;
+        if (nx) vis[v * kXW + w] |= nx;
+        any |= nx;
+        const bool got = (__ballot_sync(kFull, nx != 0) >> (lane & ~3)) & 0xFu;
+        const long long at = warp_append(w == 0 && got, &st->n_next);
+        if (at >= 0) {
+            next_front[at] = (int32_t)v;
+            m.fr_edges += (unsigned long long)(__ldg(&rowp[v + 1]) - __ldg(&rowp[v]));
+        }
+        const unsigned long long cv = (valid && (!pred || pred[v])) ? nx : 0ULL;
+        if (__ballot_sync(kFull, cv != 0)) x_count_quads(cv, c);
+    }
+    x_flush(c, any, m, s_cnt, s_any, st);
 }
 
 // End of a level (one block of kXS threads, thread s = source s of the
@@ -358,6 +536,10 @@ __global__ void k_x_finish(XState* __restrict__ st, int mode, int64_t level, con
         ctr->aux0 = tot;
         ctr->scanned = st->rows;
         ctr->cand_reads = st->entries;
+        ctr->frontier = st->n_next;
+        ctr->merges = st->fr_edges;
+        ctr->aux3 = st->rem_edges;
+        st->n_next = st->fr_edges = st->rem_edges = 0;
     }
 }
 
@@ -402,17 +584,25 @@ __global__ void __launch_bounds__(256) k_x_estimates(const int32_t* __restrict__
 int run_sweeps(fl_graph* g, int mode, int64_t n_src, const int32_t* src, int64_t D, const uint8_t* pred,
                const double* cost, int64_t* sizes, double* radius) {
     cudaStream_t st = g->stream;
-    const int64_t n = g->n;
+    const int64_t n = g->n, nnz = g->nnz;
     const int cls = kProfExact;
     const size_t words = (size_t)n * kXW;
     FL_TRY(dalloc(g->xbits, words * 8 * 3));
-    const size_t lists = ((size_t)n * 8 + 255) & ~(size_t)255;
-    FL_TRY(dalloc(g->xaux, lists + sizeof(XState)));
+    // int32 lists: light rows (n), heavy rows (n), two frontiers (n + kXS
+    // each: the first frontier lists the sweep's sources, repeats included);
+    // then the top-down work items (uint64, one per kXSeg entries of a
+    // frontier row: at most n + kXS + nnz / kXSeg) and the sweep state
+    const size_t lists = ((size_t)(4 * n + 2 * kXS) * 4 + 255) & ~(size_t)255;
+    const size_t n_items = (size_t)(n + kXS + nnz / kXSeg + 1);
+    const size_t items_b = (n_items * 8 + 255) & ~(size_t)255;
+    FL_TRY(dalloc(g->xaux, lists + items_b + sizeof(XState)));
     unsigned long long* vis = g->xbits.as<unsigned long long>();
     unsigned long long* buf[2] = {vis + words, vis + 2 * words};
     int32_t* light = g->xaux.as<int32_t>();
     int32_t* heavy = light + n;
-    XState* xs = reinterpret_cast<XState*>(g->xaux.as<char>() + lists);
+    int32_t* front[2] = {light + 2 * n, light + 3 * n + kXS};
+    unsigned long long* items = reinterpret_cast<unsigned long long*>(g->xaux.as<char>() + lists);
+    XState* xs = reinterpret_cast<XState*>(g->xaux.as<char>() + lists + items_b);
     Counters* ctr = g->ctr.as<Counters>();
     const int64_t* rowp = g->rowp.as<int64_t>();
     const int32_t* cols = g->cols.as<int32_t>();
@@ -428,35 +618,70 @@ int run_sweeps(fl_graph* g, int mode, int64_t n_src, const int32_t* src, int64_t
     for (int64_t b0 = 0; b0 < n_src; b0 += kXS) {
         const int64_t nb = n_src - b0 < kXS ? n_src - b0 : kXS;
         int64_t* rows = sizes ? sizes + b0 * (D + 1) : nullptr;
-        // every listed vertex rewrites its "next" words each level, so only
-        // the first frontier and the visited bits need clearing
+        // a bottom-up level rewrites the next words of every vertex; a
+        // top-down level gets them cleared first
         FL_CUDA(cudaMemsetAsync(vis, 0, words * 8, st));
         FL_CUDA(cudaMemsetAsync(buf[0], 0, words * 8, st));
-        int c = 0;
-        FL_LAUNCH(cls, k_x_seed<<<1, kXS, 0, st>>>(src + b0, nb, vis, buf[0], xs));
+        int c = 0, fc = 0;
+        FL_LAUNCH(cls, k_x_seed<<<1, kXS, 0, st>>>(src + b0, nb, rowp, vis, buf[0], front[0], xs));
         FL_LAUNCH(cls, k_x_finish<<<1, kXS, 0, st>>>(xs, mode, 0, src + b0, pred, cost, D, rows, radius, ctr));
         FL_CUDA(cudaGetLastError());
         FL_TRY(read_counters(g));
-        int64_t level = 1;
-        for (; g->h_ctr->aux0 > 0; ++level) {
+        int64_t n_front = (int64_t)g->h_ctr->frontier;
+        int64_t fr_edges = (int64_t)g->h_ctr->merges;
+        int64_t rem = nnz;  // entries of rows that may still need bits
+        unsigned long long rows_prev = 0, entries_prev = 0;
+        for (int64_t level = 1; g->h_ctr->aux0 > 0; ++level) {
             if (level > n + 1) FL_FAIL(FL_ETIMEOUT, "exact search did not finish");
-            if (n_heavy > 0)
-                FL_LAUNCH(cls, k_x_heavy<<<grid_h, 256, 0, st>>>(heavy, n_heavy, rowp, cols, buf[c], buf[c ^ 1], vis,
-                                                                 pred, xs));
-            if (n_light > 0)
-                FL_LAUNCH(cls, k_x_light<<<grid_l, 256, 0, st>>>(light, n_light, rowp, cols, buf[c], buf[c ^ 1], vis,
-                                                                 pred, xs));
+            // top-down when the frontier's rows are much shorter than the
+            // rows bottom-up would scan, and their work items fit
+            const bool td = 2 * fr_edges < rem && n_front + fr_edges / kXSeg + 1 <= (int64_t)n_items;
+            if (td) {
+                FL_CUDA(cudaMemsetAsync(buf[c ^ 1], 0, words * 8, st));
+                // work items (their count in st->n_next), then the pushes;
+                // k_x_td_finish restarts n_next for the next frontier
+                FL_LAUNCH(cls, k_x_td_items<<<blocks_for(n_front, 256), 256, 0, st>>>(front[fc], n_front, rowp,
+                                                                                     buf[c], items, xs));
+                const int64_t most = n_front + fr_edges / kXSeg;  // work items at most
+                FL_LAUNCH(cls, k_x_td<<<blocks_for(most, 8), 256, 0, st>>>(items, rowp, cols, buf[c], buf[c ^ 1], vis,
+                                                                           xs));
+                FL_CUDA(cudaMemsetAsync(&xs->n_next, 0, 8, st));
+                FL_LAUNCH(cls, k_x_td_finish<<<blocks_for(n, 64), 256, 0, st>>>(n, rowp, buf[c ^ 1], vis, pred,
+                                                                                front[fc ^ 1], xs));
+            } else {
+                if (n_heavy > 0)
+                    FL_LAUNCH(cls, k_x_heavy<<<grid_h, 256, 0, st>>>(heavy, n_heavy, rowp, cols, buf[c], buf[c ^ 1],
+                                                                     vis, pred, front[fc ^ 1], xs));
+                if (n_light > 0)
+                    FL_LAUNCH(cls, k_x_light<<<grid_l, 256, 0, st>>>(light, n_light, rowp, cols, buf[c], buf[c ^ 1],
+                                                                     vis, pred, front[fc ^ 1], xs));
+            }
             FL_LAUNCH(cls, k_x_finish<<<1, kXS, 0, st>>>(xs, mode, level, src + b0, pred, cost, D, rows, radius, ctr));
             FL_CUDA(cudaGetLastError());
             c ^= 1;
+            fc ^= 1;
             FL_TRY(read_counters(g));
+            const int64_t touched = (int64_t)g->h_ctr->frontier;
+            // algorithmic bytes of the level.  Bottom-up: every listed vertex
+            // reads its list id and visited words and writes its next words
+            // (4 + 32 + 32 B); a scanned row reads two offsets (16 B) and, per
+            // entry, the column and the neighbour's frontier words (4 + 32 B).
+            // Top-down: a frontier vertex reads its list id, frontier words
+            // and offsets (4 + 32 + 16 B); per entry the column and the
+            // neighbour's visited words (4 + 32 B); every vertex reads its
+            // next words (32 B) and a newly reached one reads and writes its
+            // visited words, reads its offsets and is listed (32 + 32 + 16 + 4 B).
+            const double d_rows = (double)(g->h_ctr->scanned - rows_prev);
+            const double d_entries = (double)(g->h_ctr->cand_reads - entries_prev);
+            rows_prev = g->h_ctr->scanned;
+            entries_prev = g->h_ctr->cand_reads;
+            g->prof.bytes[cls] += td ? 52.0 * (double)n_front + 36.0 * d_entries + 32.0 * (double)n +
+                                           84.0 * (double)touched
+                                     : 68.0 * (double)n + 16.0 * d_rows + 36.0 * d_entries;
+            n_front = touched;
+            fr_edges = (int64_t)g->h_ctr->merges;
+            if (!td) rem = (int64_t)g->h_ctr->aux3;
         }
-        // algorithmic bytes of the sweep's levels 1..: every listed vertex
-        // reads its list id and visited words and writes its next words
-        // (4 + 32 + 32 B); a scanned row reads two offsets (16 B) and, per
-        // entry, the column (4 B) and the neighbour's frontier words (32 B)
-        g->prof.bytes[cls] += 68.0 * (double)n * (double)(level - 1) + 16.0 * (double)g->h_ctr->scanned +
-                              36.0 * (double)g->h_ctr->cand_reads;
     }
     return FL_OK;
 }
