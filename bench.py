@@ -443,7 +443,7 @@ def run_exact(args):
     g.profile(False)
     peak, peak_kind = measured_peaks()
     achieved = px["alg_bytes"] / (px["ms"] / 1e3) / 1e9 if px["ms"] > 0 else None
-    roofline = {"kernel": "k_x_light + k_x_heavy (one bottom-up level of 256 sources)", "bound": "hbm",
+    roofline = {"kernel": "exact-size class: bit-parallel BFS levels (k_x_heavy, k_x_light, k_x_td, k_x_td_finish)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": ncu_traffic("k_x_level", "exact"),
                 "peak_kind": f"{peak_kind} copy bandwidth",
