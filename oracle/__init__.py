@@ -90,6 +90,12 @@ def _load():
             lib.orc_exact_radii.argtypes = [vp, vp, vp, vp]
             lib.orc_exact_radii_of.restype = ctypes.c_int
             lib.orc_exact_radii_of.argtypes = [vp, i64, vp, vp, vp, vp]
+            lib.orc_fl_optimum.restype = ctypes.c_int
+            lib.orc_fl_optimum.argtypes = [vp, vp, vp, vp, ctypes.POINTER(dbl)]
+            lib.orc_fl_local_search.restype = ctypes.c_int
+            lib.orc_fl_local_search.argtypes = [vp, vp, vp, i64, vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)]
+            lib.orc_fl_cost.restype = dbl
+            lib.orc_fl_cost.argtypes = [vp, vp, vp, vp]
             lib.orc_objective.restype = ctypes.c_int
             lib.orc_objective.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(dbl),
                                           ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -249,6 +255,41 @@ class Graph:
         if rc != 0:
             raise RuntimeError(f"orc_exact_radii rc={rc}")
         return r
+
+    # -- quality references (Section 5.2, Table 2) ----------------------
+    def fl_cost(self, cost, client, open_) -> float:
+        """sum of opening costs + sum of client distances to the open set;
+        clients no facility reaches are left out; +inf if a reachable client
+        is unserved."""
+        c = np.ascontiguousarray(cost, np.float64)
+        m = np.ascontiguousarray(client, np.uint8)
+        o = np.ascontiguousarray(open_, np.uint8)
+        return float(self._lib.orc_fl_cost(self._h, _p(c), _p(m), _p(o)))
+
+    def optimum(self, cost, client):
+        """(open mask, cost) of an optimal open set, by enumerating every set
+        of at most 24 facilities."""
+        c = np.ascontiguousarray(cost, np.float64)
+        m = np.ascontiguousarray(client, np.uint8)
+        op = np.zeros(self.n, np.uint8)
+        obj = dbl(0)
+        rc = self._lib.orc_fl_optimum(self._h, _p(c), _p(m), _p(op), ctypes.byref(obj))
+        if rc != 0:
+            raise RuntimeError(f"orc_fl_optimum rc={rc}")
+        return op, float(obj.value)
+
+    def local_search(self, cost, client, start=None, max_moves: int = 1 << 30):
+        """(open mask, cost, moves) of add/drop/swap local search from
+        `start` (None: the cheapest facility alone)."""
+        c = np.ascontiguousarray(cost, np.float64)
+        m = np.ascontiguousarray(client, np.uint8)
+        op = np.zeros(self.n, np.uint8) if start is None else np.array(start, np.uint8)
+        obj, mv = dbl(0), i64(0)
+        rc = self._lib.orc_fl_local_search(self._h, _p(c), _p(m), max_moves, _p(op), ctypes.byref(obj),
+                                           ctypes.byref(mv))
+        if rc != 0:
+            raise RuntimeError(f"orc_fl_local_search rc={rc}")
+        return op, float(obj.value), int(mv.value)
 
     # -- phase (ii): Eq. 1 at epsilon -> 0 -------------------------------
     def radii(self, cost: np.ndarray, client: np.ndarray) -> np.ndarray:

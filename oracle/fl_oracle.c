@@ -711,6 +711,244 @@ int orc_exact_radii_of(const orc_graph* g, int64_t m, const int32_t* fac, const 
     return exact_radii_range(g, m, fac, cost, client, r);
 }
 
+/* ---------------------------------------------------------------------- */
+/* Quality references (Section 5.2, Table 2: the method's cost against a   */
+/* sequential local-search algorithm): the optimum by enumeration on tiny  */
+/* instances and a local search.  Cost of an open set S (Section 3.1):     */
+/* sum_{f in S} c(f) + sum_{c in C} d(c, S); clients that no facility can  */
+/* reach are left out, and a set that leaves a reachable client unserved   */
+/* is infeasible.                                                          */
+/* ---------------------------------------------------------------------- */
+
+/* Hop distances from every facility to every vertex: D[i * n + v] for the
+   i-th facility fac[i] (-1 = unreachable).  Caller frees. */
+static int32_t* facility_distances(const orc_graph* g, int64_t nf, const int32_t* fac) {
+    const int64_t n = g->n;
+    int32_t* D = (int32_t*)malloc((size_t)(nf > 0 ? nf : 1) * (size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!D) return NULL;
+    int fail = 0;
+#pragma omp parallel
+    {
+        int32_t* q = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+        if (!q) {
+#pragma omp atomic write
+            fail = 1;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t i = 0; i < nf; ++i) {
+                int32_t* d = D + i * n;
+                for (int64_t v = 0; v < n; ++v) d[v] = -1;
+                int64_t qh = 0, qt = 0;
+                d[fac[i]] = 0;
+                q[qt++] = fac[i];
+                while (qh < qt) {
+                    int32_t x = q[qh++];
+                    for (int64_t e = g->rowp[x]; e < g->rowp[x + 1]; ++e) {
+                        int32_t u = g->cols[e];
+                        if (d[u] < 0) { d[u] = d[x] + 1; q[qt++] = u; }
+                    }
+                }
+            }
+        }
+        free(q);
+    }
+    if (fail) { free(D); return NULL; }
+    return D;
+}
+
+/* Cost of the open set given by flags sel[i] over the facilities; returns
+   +inf when a client that some facility reaches is left unserved. */
+static double set_cost(const int32_t* D, int64_t n, int64_t nf, const int32_t* fac, const double* cost,
+                       const uint8_t* client, const uint8_t* sel) {
+    double open_cost = 0.0;
+    for (int64_t i = 0; i < nf; ++i)
+        if (sel[i]) open_cost = open_cost + cost[fac[i]];
+    int64_t ds = 0;
+    for (int64_t c = 0; c < n; ++c) {
+        if (!client[c]) continue;
+        int32_t best = -1, reach = 0;
+        for (int64_t i = 0; i < nf; ++i) {
+            int32_t d = D[i * n + c];
+            if (d < 0) continue;
+            reach = 1;
+            if (sel[i] && (best < 0 || d < best)) best = d;
+        }
+        if (!reach) continue;
+        if (best < 0) return INFINITY;
+        ds += best;
+    }
+    return open_cost + (double)ds;
+}
+
+/* Facilities: vertices with finite cost, ascending. */
+static int64_t facility_list(int64_t n, const double* cost, int32_t* fac) {
+    int64_t nf = 0;
+    for (int64_t v = 0; v < n; ++v)
+        if (cost[v] < INFINITY) fac[nf++] = (int32_t)v;
+    return nf;
+}
+
+/* The optimum by enumerating every non-empty set of at most 24 facilities;
+   open[] receives an optimal set (the first found in the enumeration
+   order of the subsets' bit patterns); *obj its cost. */
+int orc_fl_optimum(const orc_graph* g, const double* cost, const uint8_t* client, uint8_t* open, double* obj) {
+    if (!g) return ORC_EINVAL;
+    const int64_t n = g->n;
+    int32_t* fac = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!fac) return ORC_ENOMEM;
+    const int64_t nf = facility_list(n, cost, fac);
+    if (nf > 24) { free(fac); return ORC_EINVAL; }
+    int32_t* D = facility_distances(g, nf, fac);
+    uint8_t* sel = (uint8_t*)calloc((size_t)(nf > 0 ? nf : 1), 1);
+    if (!D || !sel) { free(fac); free(D); free(sel); return ORC_ENOMEM; }
+    double best = INFINITY;
+    uint64_t best_mask = 0;
+    for (uint64_t mask = 1; nf > 0 && mask < (1ULL << nf); ++mask) {
+        for (int64_t i = 0; i < nf; ++i) sel[i] = (uint8_t)((mask >> i) & 1ULL);
+        double c = set_cost(D, n, nf, fac, cost, client, sel);
+        if (c < best) { best = c; best_mask = mask; }
+    }
+    for (int64_t v = 0; v < n; ++v) open[v] = 0;
+    for (int64_t i = 0; i < nf; ++i)
+        if ((best_mask >> i) & 1ULL) open[fac[i]] = 1;
+    *obj = nf > 0 ? best : 0.0;
+    free(fac); free(D); free(sel);
+    return ORC_OK;
+}
+
+/* Nearest and second-nearest open facility distance of every client
+   (-1 = none; reachable[c] = some facility reaches c). */
+static void nearest_two(const int32_t* D, int64_t n, int64_t nf, const uint8_t* sel, const uint8_t* client,
+                        int32_t* d1, int32_t* a1, int32_t* d2) {
+    for (int64_t c = 0; c < n; ++c) {
+        d1[c] = d2[c] = a1[c] = -1;
+        if (!client[c]) continue;
+        for (int64_t i = 0; i < nf; ++i) {
+            int32_t d = D[i * n + c];
+            if (!sel[i] || d < 0) continue;
+            if (d1[c] < 0 || d < d1[c]) { d2[c] = d1[c]; d1[c] = d; a1[c] = (int32_t)i; }
+            else if (d2[c] < 0 || d < d2[c]) d2[c] = d;
+        }
+    }
+}
+
+/* Local search with add, drop and swap moves (Arya, Garg, Khandekar,
+   Meyerson, Munagala, Pandit, SIAM J. Comput. 2004: a local optimum costs at
+   most 3 x the optimum) from the open set in open[] (an empty start opens
+   the facility of least cost first).  Each pass takes the first improving
+   move (adds, then drops, then swaps, in ascending facility order) whose
+   cost change, from the clients' nearest and second-nearest open
+   facilities, is below -1e-9 x the current cost; the cost is then
+   recomputed from scratch.  Stops at a local optimum or after max_moves
+   moves; open[], *obj and *moves receive the result. */
+int orc_fl_local_search(const orc_graph* g, const double* cost, const uint8_t* client, int64_t max_moves,
+                        uint8_t* open, double* obj, int64_t* moves) {
+    if (!g) return ORC_EINVAL;
+    const int64_t n = g->n;
+    int32_t* fac = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!fac) return ORC_ENOMEM;
+    const int64_t nf = facility_list(n, cost, fac);
+    int32_t* D = facility_distances(g, nf, fac);
+    uint8_t* sel = (uint8_t*)calloc((size_t)(nf > 0 ? nf : 1), 1);
+    uint8_t* reach = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+    int32_t* d1 = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t* a1 = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t* d2 = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!D || !sel || !reach || !d1 || !a1 || !d2) {
+        free(fac); free(D); free(sel); free(reach); free(d1); free(a1); free(d2);
+        return ORC_ENOMEM;
+    }
+    for (int64_t c = 0; c < n; ++c)
+        for (int64_t i = 0; i < nf && client[c] && !reach[c]; ++i)
+            if (D[i * n + c] >= 0) reach[c] = 1;
+    int any = 0;
+    for (int64_t i = 0; i < nf; ++i) { sel[i] = open[fac[i]] ? 1 : 0; any |= sel[i]; }
+    if (!any && nf > 0) {
+        int64_t b = 0;
+        for (int64_t i = 1; i < nf; ++i)
+            if (cost[fac[i]] < cost[fac[b]]) b = i;
+        sel[b] = 1;
+    }
+    double cur = set_cost(D, n, nf, fac, cost, client, sel);
+    int64_t m = 0;
+    while (m < max_moves && nf > 0) {
+        nearest_two(D, n, nf, sel, client, d1, a1, d2);
+        const double tol = -1e-9 * (cur < INFINITY ? cur : 1.0);
+        int64_t mi = -1, mj = -1;  /* move: close mi (or none), open mj (or none) */
+        /* adds: every client moves to the new facility when it is nearer.
+           While some reachable client is unserved (cur = +inf), the first
+           facility that reaches an unserved client is added. */
+        for (int64_t j = 0; j < nf && mi < 0 && mj < 0; ++j) {
+            if (sel[j]) continue;
+            double delta = cost[fac[j]];
+            int64_t newly = 0;
+            for (int64_t c = 0; c < n; ++c) {
+                if (!client[c] || !reach[c]) continue;
+                int32_t d = D[j * n + c];
+                if (d1[c] < 0) { if (d >= 0) ++newly; continue; }
+                if (d >= 0 && d < d1[c]) delta += (double)(d - d1[c]);
+            }
+            if (cur == INFINITY ? newly > 0 : delta < tol) mj = j;
+        }
+        if (cur == INFINITY && mj < 0) break;  /* cannot happen: every reachable client has a facility */
+        /* drops: clients of the dropped facility move to their second nearest */
+        for (int64_t i = 0; i < nf && mi < 0 && mj < 0; ++i) {
+            if (!sel[i]) continue;
+            double delta = -cost[fac[i]];
+            for (int64_t c = 0; c < n && delta < INFINITY; ++c) {
+                if (!client[c] || a1[c] != i) continue;
+                if (d2[c] < 0) delta = INFINITY; else delta += (double)(d2[c] - d1[c]);
+            }
+            if (delta < tol) mi = i;
+        }
+        /* swaps: close i, open j */
+        for (int64_t i = 0; i < nf && mi < 0 && mj < 0; ++i) {
+            if (!sel[i]) continue;
+            for (int64_t j = 0; j < nf && mi < 0 && mj < 0; ++j) {
+                if (sel[j]) continue;
+                double delta = cost[fac[j]] - cost[fac[i]];
+                for (int64_t c = 0; c < n && delta < INFINITY; ++c) {
+                    if (!client[c] || d1[c] < 0) continue;
+                    int32_t keep = a1[c] == i ? d2[c] : d1[c];
+                    int32_t d = D[j * n + c];
+                    int32_t nb = keep < 0 ? d : (d >= 0 && d < keep ? d : keep);
+                    if (nb < 0) delta = INFINITY; else delta += (double)(nb - d1[c]);
+                }
+                if (delta < tol) { mi = i; mj = j; }
+            }
+        }
+        if (mi < 0 && mj < 0) break;
+        if (mi >= 0) sel[mi] = 0;
+        if (mj >= 0) sel[mj] = 1;
+        cur = set_cost(D, n, nf, fac, cost, client, sel);
+        ++m;
+    }
+    for (int64_t v = 0; v < n; ++v) open[v] = 0;
+    for (int64_t i = 0; i < nf; ++i)
+        if (sel[i]) open[fac[i]] = 1;
+    *obj = nf > 0 ? cur : 0.0;
+    *moves = m;
+    free(fac); free(D); free(sel); free(reach); free(d1); free(a1); free(d2);
+    return ORC_OK;
+}
+
+/* Cost of an open set by the same rule (+inf if a reachable client is left
+   unserved). */
+double orc_fl_cost(const orc_graph* g, const double* cost, const uint8_t* client, const uint8_t* open) {
+    if (!g) return NAN;
+    const int64_t n = g->n;
+    int32_t* fac = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!fac) return NAN;
+    const int64_t nf = facility_list(n, cost, fac);
+    int32_t* D = facility_distances(g, nf, fac);
+    uint8_t* sel = (uint8_t*)calloc((size_t)(nf > 0 ? nf : 1), 1);
+    if (!D || !sel) { free(fac); free(D); free(sel); return NAN; }
+    for (int64_t i = 0; i < nf; ++i) sel[i] = open[fac[i]] ? 1 : 0;
+    double c = nf > 0 ? set_cost(D, n, nf, fac, cost, client, sel) : 0.0;
+    free(fac); free(D); free(sel);
+    return c;
+}
+
 int orc_compute_radii(const orc_graph* g, const double* cost, const uint8_t* client, double* r) {
     if (!g || !g->built) return ORC_ESTATE;
 #pragma omp parallel for schedule(dynamic, 1024)
