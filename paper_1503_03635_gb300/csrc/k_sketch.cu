@@ -352,10 +352,13 @@ __device__ __forceinline__ void gather_range(const Grp<G>& g, int k, int hop, ui
                                              const uint8_t* __restrict__ Dcp, const uint64_t* __restrict__ Dp,
                                              IdMap ids, Sketch<G>& s,
                                              unsigned long long& cand) {
+    // the next chunk's columns are loaded while this chunk merges
+    int32_t u_next = e0 + g.l < e1 ? __ldg(&cols[e0 + g.l]) : 0;
     for (int64_t cb = e0; cb < e1; cb += G) {
         const int64_t e = cb + g.l;
         const bool in = e < e1;
-        const int32_t u = in ? __ldg(&cols[e]) : 0;
+        const int32_t u = u_next;
+        u_next = e + G < e1 ? __ldg(&cols[e + G]) : 0;
         if (hop == 1) {
             absorb(g, k, in ? vertex_rank(seed, rank_id(ids, u)) : kEmpty, s);
             continue;
