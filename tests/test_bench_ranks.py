@@ -25,3 +25,20 @@ def test_reference_arm_two_ranks_one_line():
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["config"]["workload"] == "er10k"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_of_the_exact_workload():
+    """The oracle's BFS ball sizes on a bounded sample of the exact workload's
+    sources: one JSON line with the contract's fields."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "exact",
+           "--steps", "1", "--warmup", "0"]
+    env = dict(os.environ, OMP_NUM_THREADS="4")
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "sources/s" and d["value"] > 0
+    assert d["config"]["workload"] == "exact" and d["config"]["max_dist"] == 20
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["d2h_bytes_per_step"] == 0
