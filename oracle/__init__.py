@@ -77,6 +77,8 @@ def _load():
             lib.orc_hip_estimate.argtypes = [vp, i64, i64, vp]
             lib.orc_open_facilities.restype = ctypes.c_int
             lib.orc_open_facilities.argtypes = [vp, vp, vp, u64, vp, ctypes.POINTER(i64)]
+            lib.orc_check_open_facilities.restype = ctypes.c_int
+            lib.orc_check_open_facilities.argtypes = [vp, vp, vp, u64, vp, ctypes.POINTER(i64)]
             lib.orc_assign.restype = ctypes.c_int
             lib.orc_assign.argtypes = [vp, vp, vp, vp]
             lib.orc_radius_of_ads.restype = dbl
@@ -312,6 +314,19 @@ class Graph:
         if rc != 0:
             raise RuntimeError(f"orc_open_facilities rc={rc}")
         return op, int(nopen.value)
+
+    def check_open_facilities(self, r: np.ndarray, client: np.ndarray, seed: int, open_: np.ndarray):
+        """(ok, witness): whether open_ is the lexicographically-first MIS of
+        H-bar under (r_f, pi_f), checked by its characterisation in parallel
+        (independent; every other candidate conflicts with an earlier member)."""
+        r = np.ascontiguousarray(r, np.float64)
+        client = np.ascontiguousarray(client, np.uint8)
+        op = np.ascontiguousarray(open_, np.uint8)
+        bad = i64(-1)
+        rc = self._lib.orc_check_open_facilities(self._h, _p(r), _p(client), seed, _p(op), ctypes.byref(bad))
+        if rc < 0:
+            raise RuntimeError(f"orc_check_open_facilities rc={rc}")
+        return rc == 1, int(bad.value)
 
     # -- assignment + objective (Section 3.1) ----------------------------
     def assign(self, open_: np.ndarray):

@@ -1052,6 +1052,126 @@ int orc_open_facilities(const orc_graph* g, const double* r, const uint8_t* clie
     return ORC_OK;
 }
 
+/* Check that open[] is the lexicographically-first MIS of H-bar under the
+   keys (r_f, pi_f), without running the sequential greedy.  A set S of
+   candidates is that MIS iff (i) S is independent and (ii) every candidate
+   outside S conflicts with a member of S of smaller key (induction over the
+   key order: the smallest candidate must be in S, and every later one is in S
+   exactly when no earlier member conflicts with it).  With S independent,
+   every client of a member's ball has exactly one owner, so (ii) reads: the
+   ball of f holds a client whose owner has a smaller key.  Both steps are
+   independent per facility (parallel).  Returns 1 when open[] is that MIS,
+   0 when not (*bad = a facility that witnesses it), < 0 on error. */
+static int key_less(const double* r, uint64_t seed, int32_t a, int32_t b) {
+    if (r[a] < r[b]) return 1;
+    if (r[a] > r[b]) return 0;
+    return orc_priority(seed, a) < orc_priority(seed, b);
+}
+
+static int64_t ball_depth(double rf) {
+    double fl = floor(rf);
+    return fl > 2147483647.0 ? 2147483647 : (int64_t)fl;
+}
+
+int orc_check_open_facilities(const orc_graph* g, const double* r, const uint8_t* client, uint64_t seed,
+                              const uint8_t* open, int64_t* bad) {
+    if (!g) return -ORC_EINVAL;
+    const int64_t n = g->n;
+    *bad = -1;
+    for (int64_t f = 0; f < n; ++f)
+        if (open[f] && !(r[f] < INFINITY)) { *bad = f; return 0; }
+    int32_t* owner = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    if (!owner) return -ORC_ENOMEM;
+    for (int64_t v = 0; v < n; ++v) owner[v] = -1;
+    int64_t witness = -1;
+    int fail = 0;
+    /* (i) members claim their balls; a client claimed twice breaks independence */
+#pragma omp parallel
+    {
+        int32_t* dist = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+        int32_t* q = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+        if (!dist || !q) {
+#pragma omp atomic write
+            fail = 1;
+        } else {
+            for (int64_t v = 0; v < n; ++v) dist[v] = -1;
+#pragma omp for schedule(dynamic, 64)
+            for (int64_t f = 0; f < n; ++f) {
+                if (!open[f]) continue;
+                const int64_t B = ball_depth(r[f]);
+                int64_t qh = 0, qt = 0;
+                dist[f] = 0;
+                q[qt++] = (int32_t)f;
+                while (qh < qt) {
+                    int32_t x = q[qh++];
+                    if (client[x]) {
+                        int32_t prev = __sync_val_compare_and_swap(&owner[x], -1, (int32_t)f);
+                        if (prev != -1 && prev != (int32_t)f) {
+#pragma omp critical
+                            { if (witness < 0) witness = f; }
+                        }
+                    }
+                    if (dist[x] == B) continue;
+                    for (int64_t e = g->rowp[x]; e < g->rowp[x + 1]; ++e) {
+                        int32_t u = g->cols[e];
+                        if (dist[u] < 0) { dist[u] = dist[x] + 1; q[qt++] = u; }
+                    }
+                }
+                for (int64_t j = 0; j < qt; ++j) dist[q[j]] = -1;
+            }
+        }
+        free(dist); free(q);
+    }
+    if (fail) { free(owner); return -ORC_ENOMEM; }
+    if (witness >= 0) { free(owner); *bad = witness; return 0; }
+    /* (ii) every other candidate meets a client owned by an earlier member */
+#pragma omp parallel
+    {
+        int32_t* dist = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+        int32_t* q = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+        if (!dist || !q) {
+#pragma omp atomic write
+            fail = 1;
+        } else {
+            for (int64_t v = 0; v < n; ++v) dist[v] = -1;
+#pragma omp for schedule(dynamic, 64)
+            for (int64_t f = 0; f < n; ++f) {
+                if (open[f] || !(r[f] < INFINITY)) continue;
+                const int64_t B = ball_depth(r[f]);
+                int64_t qh = 0, qt = 0;
+                /* a client is tested when the search first reaches it */
+                int dominated = client[f] && owner[f] >= 0 && key_less(r, seed, owner[f], (int32_t)f);
+                dist[f] = 0;
+                q[qt++] = (int32_t)f;
+                while (qh < qt && !dominated) {
+                    int32_t x = q[qh++];
+                    if (dist[x] == B) continue;
+                    for (int64_t e = g->rowp[x]; e < g->rowp[x + 1]; ++e) {
+                        int32_t u = g->cols[e];
+                        if (dist[u] >= 0) continue;
+                        dist[u] = dist[x] + 1;
+                        q[qt++] = u;
+                        if (client[u] && owner[u] >= 0 && key_less(r, seed, owner[u], (int32_t)f)) {
+                            dominated = 1;
+                            break;
+                        }
+                    }
+                }
+                for (int64_t j = 0; j < qt; ++j) dist[q[j]] = -1;
+                if (!dominated) {
+#pragma omp critical
+                    { if (witness < 0) witness = f; }
+                }
+            }
+        }
+        free(dist); free(q);
+    }
+    free(owner);
+    if (fail) return -ORC_ENOMEM;
+    if (witness >= 0) { *bad = witness; return 0; }
+    return 1;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Assignment: every vertex to its nearest open facility (ties: smallest  */
 /* facility id); Section 3.1 objective d(c,S) = min_{f in S} d(c,f), and  */

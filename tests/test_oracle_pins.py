@@ -442,3 +442,57 @@ def test_full_solve_runs_on_er10k():
     assert out["n_open"] > 0
     assert out["n_unserved"] == 0 or (out["dist"][w.client > 0] < 0).sum() == out["n_unserved"]
     assert (out["assign"][out["open"] > 0] == np.flatnonzero(out["open"])).all()
+
+
+@pytest.mark.parametrize("name", sorted(TINY))
+def test_mis_check_accepts_exactly_the_lexicographically_first_mis(name):
+    """The parallel characterisation check (independent; every other
+    candidate conflicts with an earlier member) accepts the brute-force
+    lexicographically-first MIS of the materialised H-bar and rejects every
+    set that differs from it by one facility."""
+    rowp, cols = TINY[name]
+    n = len(rowp) - 1
+    D = brute.apsp(rowp, cols)
+    client = (np.arange(n) % 3 != 1).astype(np.uint8)
+    cost = np.array([1.5 + (5 * v % 7) for v in range(n)], float)
+    seed = 33
+    g = oracle.Graph(rowp, cols)
+    g.build_sketches(4, seed)
+    r = g.radii(cost, client)
+    cand, _, adj = brute.conflict_graph(D, r, client)
+    S = brute.lfmis(cand, adj, lambda f: (r[f], oracle.priority(seed, f)))
+    op = np.zeros(n, np.uint8)
+    op[list(S)] = 1
+    assert g.check_open_facilities(r, client, seed, op) == (True, -1)
+    for f in cand:
+        flipped = op.copy()
+        flipped[f] ^= 1
+        ok, bad = g.check_open_facilities(r, client, seed, flipped)
+        assert not ok and bad >= 0, f
+
+
+@pytest.mark.parametrize("scale,const_cost", [(11, False), (12, True)])
+def test_mis_check_agrees_with_the_greedy_on_rmat(scale, const_cost):
+    """On R-MAT graphs (hubs; equal radii when every cost is the same, so the
+    priorities decide) the greedy's set passes and one-facility changes fail."""
+    rowp, cols = flsynth.rmat(scale, 8, 40 + scale)
+    n = len(rowp) - 1
+    client = flsynth.bernoulli(n, 41, 0.5)
+    fac = flsynth.bernoulli(n, 42, 0.3)
+    cost = np.where(fac > 0, 25.0 if const_cost else flsynth.loguniform(n, 43, 5.0, 500.0), np.inf)
+    g = oracle.Graph(rowp, cols)
+    g.build_sketches(16, 7)
+    r = g.radii(cost, client)
+    op, nopen = g.open_facilities(r, client, 7)
+    assert nopen > 3
+    assert g.check_open_facilities(r, client, 7, op) == (True, -1)
+    members = np.flatnonzero(op)
+    others = np.flatnonzero((op == 0) & np.isfinite(r))
+    for f in list(members[:5]) + list(others[:5]):
+        flipped = op.copy()
+        flipped[f] ^= 1
+        assert not g.check_open_facilities(r, client, 7, flipped)[0], f
+    # another seed's priorities give another set (when it differs, it fails here)
+    op2, _ = g.open_facilities(r, client, 8)
+    if not np.array_equal(op2, op):
+        assert not g.check_open_facilities(r, client, 7, op2)[0]
