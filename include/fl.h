@@ -6,12 +6,12 @@
  * Sozio ("Scalable Facility Location for Massive Graphs on Pregel-like
  * Systems"):
  *   (i)   bottom-k min-hash sketches and all-distances sketches (ADS) with HIP
- *         weights, by hop-synchronous propagation (Section 2.3, Alg. 1-2);
+ *         weights, by hop-synchronous propagation (Section 3.3, Alg. 1-2);
  *   (ii)  per-facility opening radii from predicated HIP estimates of client
- *         counts (Eq. 1 at epsilon -> 0, Section 3.2 and 3.4);
+ *         counts (Eq. 1 at epsilon -> 0, Sections 4.2 and 4.5);
  *   (iii) facility selection as the lexicographically-first maximal
  *         independent set of the conflict graph H-bar under key (r_f, pi_f)
- *         (Alg. 3 and Section 3.3, Alg. 6);
+ *         (Alg. 3 and Section 4.3, Alg. 6);
  *   then each client's nearest open facility and the objective (Section 3.1).
  *
  * Conventions for every entry point:
@@ -31,7 +31,7 @@
  *   - Vertex ids are int32 in [0, n); row offsets are int64 (graphs with
  *     more than 2^31 directed edges are supported).
  *   - The graph must be undirected: the CSR must be symmetric (u in N(v) iff
- *     v in N(u)), as in the paper's undirected setting (Section 2.1).
+ *     v in N(u)), as in the paper's undirected setting (Section 3.1).
  */
 #ifndef FL_H
 #define FL_H
@@ -59,7 +59,7 @@ typedef struct fl_graph fl_graph; /* device CSR + sketches + ADS of one graph */
 typedef struct fl_solve fl_solve; /* one instance: costs, clients, radii, open set, assignment */
 
 /*
- * fl_graph_create -- upload a graph (Section 2.1: G = (V, E), unweighted).
+ * fl_graph_create -- upload a graph (Section 3.1: G = (V, E), unweighted).
  *   n        number of vertices, 1 <= n <= 2^31 - 1.
  *   row_off  int64[n+1] CSR row offsets, row_off[0] = 0, non-decreasing,
  *            row_off[n] = nnz.
@@ -79,7 +79,7 @@ int fl_graph_destroy(fl_graph* g);
 
 /*
  * fl_build_sketches -- phase (i): per-vertex bottom-k sketches and the ADS.
- * Section 2.3 (Alg. 1 sequential, Alg. 2 vertex program): hop h merges into
+ * Section 3.3 (Alg. 1 sequential, Alg. 2 vertex program): hop h merges into
  * each vertex the sketch entries its neighbours gained at hop h-1 and keeps
  * the k smallest ranks; it stops when no sketch changes.  Ranks are
  * r(v) = SplitMix64 output v+1 from state `seed`.  Every entry that joins
@@ -132,10 +132,10 @@ int fl_solve_destroy(fl_solve* s);
 
 /*
  * fl_compute_radii -- phase (ii): opening radius of every facility.
- * Eq. 1 with all clients unfrozen and alpha(c) = r (Section 3.2), at
+ * Eq. 1 with all clients unfrozen and alpha(c) = r (Section 4.2), at
  * epsilon -> 0: r_f solves sum_h W_h max(0, r - h) = c(f), where W_h is the
  * HIP estimate of the clients at distance h of f, read off f's ADS with the
- * client predicate (Section 3.4).  In FP64 with a fixed operation order.
+ * client predicate (Section 4.5).  In FP64 with a fixed operation order.
  *   open_cost   double[n]; +INFINITY = not a facility; facilities need a
  *               finite cost > 0 (else FL_EINVAL).
  *   client_mask uint8[n]; nonzero = client.
@@ -148,7 +148,7 @@ int fl_compute_radii(fl_solve* s, const double* open_cost, const uint8_t* client
 
 /*
  * fl_open_facilities -- phase (iii): the lexicographically-first maximal
- * independent set S of H-bar (Section 3.3, Alg. 6 with the greedy MIS of
+ * independent set S of H-bar (Section 4.3, Alg. 6 with the greedy MIS of
  * Blelloch, Fineman and Shun).  Candidates: facilities with finite r_f.
  * Ball(f) = clients within floor(r_f) hops of f; f, g conflict iff their
  * balls share a client.  Keys (r_f, pi_f), pi_f = SplitMix64 output f+1 from
@@ -204,8 +204,8 @@ int fl_ball_sizes(fl_graph* g, int64_t n_src, const int32_t* src, int32_t max_di
 
 /*
  * fl_ball_estimates -- the HIP estimates of the same sizes read off the ADS
- * (Section 2.3's neighbourhood queries; with a predicate, the estimator of
- * Section 3.4): out[s * (max_dist + 1) + h] = the sum over src[s]'s ADS
+ * (Section 3.3's neighbourhood queries; with a predicate, the estimator of
+ * Section 4.5): out[s * (max_dist + 1) + h] = the sum over src[s]'s ADS
  * groups at distance <= h, in distance order, of (entries of the group's
  * weighted prefix with pred != 0) x the group's HIP weight, one FP64 add and
  * multiply per group.  Needs fl_build_sketches (else FL_ESTATE).  Arguments
@@ -300,9 +300,12 @@ int fl_hop_stats(const fl_graph* g, int64_t cap, int64_t* n_hops, int64_t* scann
  *   stream                  cudaStream_t for all work; returns after it ends.
  * Scratch (about 28 MB) is one fixed device array of the library, held by
  * every GPU that loads it until the process exits.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) and
- * should come before any stream capture.  All calls share the array and each
- * clears what must start at zero; calls that overlap on the GPU race.
+ * device looks up that array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture on the device.  Every call
+ * synchronises `stream` several times: after validating the CSR and once per
+ * BFS level, to read the next frontier's size into host memory.  All calls
+ * share the array and each clears what must start at zero; calls that
+ * overlap on the GPU race.
  */
 int fl_assign_nearest_noalloc(int64_t n, const int64_t* row_off, const int32_t* cols, int64_t nnz,
                               const uint8_t* open, int32_t* assign_out, int32_t* dist_out, void* stream);
@@ -312,7 +315,7 @@ int fl_assign_nearest_noalloc(int64_t n, const int64_t* row_off, const int32_t* 
  * synchronisations for all of them).  Each instance is a connected part of
  * one device graph; ranks r(v) and priorities pi(f) use the instance's own
  * vertex ids, and the instances share no vertex or edge, so every result is
- * the one the plain fl_* sequence gives for that instance alone (Section 3:
+ * the one the plain fl_* sequence gives for that instance alone (Sections 3.1, 4.1:
  * the objective and the conflict graph H-bar of Alg. 3 decompose over
  * components).
  *

@@ -132,7 +132,7 @@ def ranks(seed: int, n: int) -> np.ndarray:
 
 
 def priority(seed: int, f: int) -> int:
-    """pi(f): the random facility ID of the greedy MIS (Section 3.3)."""
+    """pi(f): the random facility ID of the greedy MIS (Section 4.3)."""
     return int(_load().orc_priority(seed, f))
 
 
@@ -161,7 +161,7 @@ class Graph:
         except Exception:
             pass
 
-    # -- phase (i): Section 2.3, Algorithms 1-2 ---------------------------
+    # -- phase (i): Section 3.3, Algorithms 1-2 ---------------------------
     def build_sketches(self, k: int, seed: int, max_hops: int | None = None) -> None:
         """Phase (i); with max_hops, stop after that many hops (a bounded sample)."""
         if max_hops is None:
@@ -303,7 +303,7 @@ class Graph:
             raise RuntimeError(f"orc_compute_radii rc={rc}")
         return r
 
-    # -- phase (iii): lexicographically-first MIS (Section 3.3) -----------
+    # -- phase (iii): lexicographically-first MIS (Section 4.3) -----------
     def open_facilities(self, r: np.ndarray, client: np.ndarray, seed: int):
         r = np.ascontiguousarray(r, np.float64)
         client = np.ascontiguousarray(client, np.uint8)

@@ -38,7 +38,7 @@
 
 /* ---------------------------------------------------------------------- */
 /* Ranks: SplitMix64 (Steele, Lea, Flood, OOPSLA 2014).                    */
-/* The paper only says r(u) is a hash of u (Section 2.3, Algorithm 1).     */
+/* The paper only says r(u) is a hash of u (Section 3.3, Algorithm 1).     */
 /* ---------------------------------------------------------------------- */
 
 #define SM_GAMMA 0x9e3779b97f4a7c15ULL
@@ -59,7 +59,7 @@ uint64_t orc_rank(uint64_t seed, int64_t v) {
     return orc_splitmix64_next(&state);
 }
 
-/* pi(f): MIS priority (Section 3.3 draws a random ID per facility).  The
+/* pi(f): MIS priority (Section 4.3 draws a random ID per facility).  The
    (f+1)-th output of a second SplitMix64 stream whose starting state is
    the first SplitMix64 output for `seed`.  Injective in f, like r. */
 uint64_t orc_priority(uint64_t seed, int64_t f) {
@@ -168,7 +168,7 @@ static int rank_id_cmp(const void* a, const void* b) {
    estimator iff len < k or i < k-1; its inclusion probability conditioned
    on all other ranks is then 1 (len < k) or t / 2^64 with t = S_h(v)[k-1]
    (the (k-1)-th smallest rank of the ball without w).  The adjusted weight
-   is the inverse (Cohen 2014, HIP; cited in Section 2.3). */
+   is the inverse (Cohen 2014, HIP; cited in Section 3.3). */
 static double hip_weight(const uint64_t* Sh, int32_t len, int k) {
     if (len < k) return 1.0;
     return 18446744073709551616.0 / (double)Sh[k - 1];
@@ -176,7 +176,7 @@ static double hip_weight(const uint64_t* Sh, int32_t len, int k) {
 
 /* ---------------------------------------------------------------------- */
 /* Phase (i): sketches and ADS by hop-synchronous propagation.             */
-/* Section 2.3, Algorithm 2 (unweighted: no CleanUp is needed because one  */
+/* Section 3.3, Algorithm 2 (unweighted: no CleanUp is needed because one  */
 /* superstep delivers exactly the vertices of one distance).               */
 /* ---------------------------------------------------------------------- */
 
@@ -474,11 +474,11 @@ int64_t orc_vertex_ads(const orc_graph* g, int k, uint64_t seed, int64_t v, int6
 
 /* ---------------------------------------------------------------------- */
 /* Phase (ii): per-facility radius.                                        */
-/* Eq. 1 (Section 3) with all clients unfrozen and alpha(c) = alpha, as in */
-/* Section 3.2 before Eq. 2, taken at epsilon -> 0: the served-client      */
+/* Eq. 1 (Section 4.1) with all clients unfrozen and alpha(c) = alpha, as in */
+/* Section 4.2 before Eq. 2, taken at epsilon -> 0: the served-client      */
 /* slack sum_c max{0, r - d(c,f)} equals the opening cost c(f).  Client    */
 /* counts per distance come from predicated HIP queries on the ADS         */
-/* (Section 3.4, "How to estimate the number of unfrozen clients?").       */
+/* (Section 4.5, "How to estimate the number of unfrozen clients?").       */
 /* ---------------------------------------------------------------------- */
 
 /* Radius from per-distance client estimates (hop ascending): ng groups at
@@ -957,7 +957,7 @@ int orc_compute_radii(const orc_graph* g, const double* cost, const uint8_t* cli
 }
 
 /* HIP estimate of the number of clients within distance h of v (the
-   predicated neighbourhood query of Section 2.3): sum of counted client
+   predicated neighbourhood query of Section 3.3): sum of counted client
    weights over groups with hop <= h.  Summed group by group in hop order:
    each group adds (#counted clients) * weight. */
 double orc_hip_estimate(const orc_graph* g, int64_t v, int64_t h, const uint8_t* client) {
@@ -976,7 +976,7 @@ double orc_hip_estimate(const orc_graph* g, int64_t v, int64_t h, const uint8_t*
 
 /* ---------------------------------------------------------------------- */
 /* Phase (iii): facility selection = lexicographically-first MIS of H-bar. */
-/* Section 3.3 (Algorithm 3 lines building H-bar; Algorithm 6; the greedy  */
+/* Section 4.3 (Algorithm 3 lines building H-bar; Algorithm 6; the greedy  */
 /* MIS of Blelloch, Fineman, Shun returns the lexicographically-first MIS  */
 /* for its priority order).  Candidate facilities: r_f finite.  Ball(f) =  */
 /* clients c with d(c,f) <= floor(r_f).  f ~ g iff their balls share a     */

@@ -119,11 +119,25 @@ def _arg(a, dtype=None):
     except ImportError:  # pragma: no cover
         torch = None
     if torch is not None and isinstance(a, torch.Tensor):
+        if dtype is not None and _TORCH_DTYPES.get(a.dtype) != np.dtype(dtype):
+            raise TypeError(f"expected {np.dtype(dtype)}, got {a.dtype}")
         if not a.is_contiguous():
             raise ValueError("tensor must be contiguous")
         kind = FL_MEM_DEVICE if a.is_cuda else FL_MEM_HOST
         return ctypes.c_void_p(a.data_ptr()), kind, a
     raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _torch_dtypes():
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        return {}
+    return {torch.int64: np.dtype(np.int64), torch.int32: np.dtype(np.int32), torch.uint8: np.dtype(np.uint8),
+            torch.bool: np.dtype(np.bool_), torch.float64: np.dtype(np.float64), torch.uint64: np.dtype(np.uint64)}
+
+
+_TORCH_DTYPES = _torch_dtypes()
 
 
 def _kind(*kinds):
@@ -402,16 +416,48 @@ def assign_nearest_noalloc(rowp, cols, open_mask, assign_out, dist_out, stream=N
     """fl_assign_nearest_noalloc: nearest open facility with no device allocation.
 
     For callers that cannot let the library allocate device memory; all arrays are
-    CUDA tensors the caller owns (row offsets int64, columns int32, open mask uint8,
-    outputs int32).  Graphs up to 2^20 vertices; calls that overlap on the GPU race.
+    CUDA tensors the caller owns, on the current device: row offsets int64[n+1],
+    columns int32[nnz] with nnz = row offsets[-1], open mask uint8 or bool [n],
+    outputs int32[n] (either may be None).  Graphs up to 2^20 vertices; calls that
+    overlap on the GPU race.  Types, lengths and devices are checked here, before
+    anything is launched.
     """
+    import torch
+
     lib = load()
-    args = [_arg(a) for a in (rowp, cols, open_mask, assign_out, dist_out)]
-    if any(kind != FL_MEM_DEVICE for _, kind, _ in args if kind is not None):
-        raise ValueError("fl_assign_nearest_noalloc takes device memory only")
+    n = len(rowp) - 1
+    want = ((rowp, "row offsets", (torch.int64,), n + 1), (cols, "columns", (torch.int32,), None),
+            (open_mask, "open mask", (torch.uint8, torch.bool), n), (assign_out, "assign_out", (torch.int32,), n),
+            (dist_out, "dist_out", (torch.int32,), n))
+    for a, what, dtypes, length in want:
+        if a is None:
+            if what in ("assign_out", "dist_out"):
+                continue
+            raise ValueError(f"{what} is required")
+        if not isinstance(a, torch.Tensor):
+            raise TypeError(f"{what} must be a torch.Tensor in device memory")
+        if a.dtype not in dtypes:
+            raise TypeError(f"{what}: expected {' or '.join(str(d) for d in dtypes)}, got {a.dtype}")
+        if a.dim() != 1 or not a.is_contiguous():
+            raise ValueError(f"{what} must be a contiguous 1-D tensor")
+        if length is not None and a.numel() != length:
+            raise ValueError(f"{what} has {a.numel()} elements, expected {length}")
+    if assign_out is None and dist_out is None:
+        raise ValueError("at least one of assign_out, dist_out is required")
+    for a, what, _, _ in want:
+        if a is not None and not a.is_cuda:
+            raise ValueError(f"{what} must be in device memory")
+    dev = torch.cuda.current_device()
+    for a, what, _, _ in want:
+        if a is not None and a.device.index != dev:
+            raise ValueError(f"{what} is on cuda:{a.device.index}, the current device is cuda:{dev}")
+    nnz = int(rowp[-1].item()) if n >= 0 else 0
+    if nnz != cols.numel():
+        raise ValueError(f"row offsets end at {nnz} but there are {cols.numel()} columns")
+    ptr = [ctypes.c_void_p(a.data_ptr()) if a is not None else None
+           for a in (rowp, cols, open_mask, assign_out, dist_out)]
     st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
-    _check(lib.fl_assign_nearest_noalloc(len(rowp) - 1, args[0][0], args[1][0], len(cols), args[2][0],
-                                         args[3][0], args[4][0], st))
+    _check(lib.fl_assign_nearest_noalloc(n, ptr[0], ptr[1], cols.numel(), ptr[2], ptr[3], ptr[4], st))
     return assign_out, dist_out
 
 

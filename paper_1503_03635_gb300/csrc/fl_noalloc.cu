@@ -49,6 +49,8 @@ constexpr size_t kOffFr1 = kOffFr0 + 4 * kMaxN;
 constexpr size_t kOffCnt = kOffFr1 + 4 * kMaxN;
 constexpr size_t kOffCtr = kOffCnt + 256;
 constexpr size_t kScratchBytes = kOffCtr + 256;
+static_assert(sizeof(Counters) <= 256, "the Counters block must fit its 256-byte slot of the scratch");
+static_assert(2 * sizeof(unsigned long long) <= 256, "the frontier counters must fit their 256-byte slot");
 
 static __device__ __align__(256) unsigned char noalloc_scratch[kScratchBytes];
 

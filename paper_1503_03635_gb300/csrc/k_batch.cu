@@ -10,7 +10,7 @@
 //     CSR; the instances share G's ADS: radii of all R instances are read
 //     off it in one kernel, and only keys, MIS and BFS run on U.
 // Ranks and priorities use part-local ids (fl_graph::vbase), so each part
-// is solved exactly as it would be alone (Section 3: the instances share no
+// is solved exactly as it would be alone (Sections 3.1 and 4.1: the instances share no
 // client, facility or edge).
 #include <algorithm>
 #include <cstdio>

@@ -544,7 +544,7 @@ __global__ void k_x_finish(XState* __restrict__ st, int mode, int64_t level, con
 }
 
 // HIP estimates of the same sizes from the ADS (the predicated
-// neighbourhood query of Section 2.3; the estimator of Section 3.4): a warp
+// neighbourhood query of Section 3.3; the estimator of Section 4.5): a warp
 // per source; out row h = sum over the groups at hop <= h, in hop order, of
 // (counted entries under the predicate) x the group's weight.
 __global__ void __launch_bounds__(256) k_x_estimates(const int32_t* __restrict__ src, int64_t n_src, int64_t D,

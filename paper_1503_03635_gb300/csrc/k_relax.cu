@@ -1,6 +1,6 @@
 // k_relax.cu -- synchronous min-propagation rounds over the CSR, used by the
 // multi-source BFS (assignment, eccentricity bound) and by the cover / gather
-// sweeps of the greedy MIS ("send to all vertices within distance d", §3.4).
+// sweeps of the greedy MIS ("send to all vertices within distance d", §4.5).
 //
 // One round: every vertex v takes X'[v] = min(X[v], min_{u in N(v)} X[u] + add),
 // reading only values of the previous round, so a value moves exactly one hop

@@ -1,5 +1,5 @@
 // k_sketch.cu -- phase (i): bottom-k sketches and ADS by hop-synchronous
-// propagation (Section 2.3, Algorithm 2 for unweighted graphs), with HIP
+// propagation (Section 3.3, Algorithm 2 for unweighted graphs), with HIP
 // weights computed where each entry joins a sketch.
 //
 // Data layout (k <= 32):

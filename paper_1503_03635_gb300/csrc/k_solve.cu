@@ -1,7 +1,7 @@
 // k_solve.cu -- phases (ii) and (iii) plus assignment and objective:
 //   radius solve (Eq. 1 at epsilon -> 0 from predicated HIP estimates),
 //   key ordinals (r_f, pi_f), greedy-MIS rounds on the implicit conflict
-//   graph H-bar (Section 3.3, Algorithm 6), nearest-open-facility BFS and
+//   graph H-bar (Section 4.3, Algorithm 6), nearest-open-facility BFS and
 //   the objective (Section 3.1).
 #include <algorithm>
 #include <cmath>

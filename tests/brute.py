@@ -3,10 +3,10 @@
 Everything here is computed from first principles on a materialised
 all-pairs distance table, independently of the oracle's propagation code:
 
-* balls and bottom-k sketches of balls (Section 2.3: the ADS is the union of
+* balls and bottom-k sketches of balls (Section 3.3: the ADS is the union of
   the min-hash sketches of the l closest vertices, for every l);
 * the ADS by definition, with HIP weights from the definition of the
-  conditional inclusion probability (Cohen 2014, cited in Section 2.3);
+  conditional inclusion probability (Cohen 2014, cited in Section 3.3);
 * the exact root of the epsilon->0 opening condition (Eq. 1) from exact
   client distances, in rational arithmetic;
 * the conflict graph H-bar (Algorithm 3) and its lexicographically-first MIS;

@@ -8,7 +8,7 @@ The oracle cannot rebuild every sketch at this size, so it checks:
     counted prefixes, HIP weights bit-exact) and their radii (Eq. 1);
   * the radii of 2000 sampled facilities read off the GPU's own ADS rows;
   * the whole open set: that it is the lexicographically-first MIS of the
-    conflict graph under the GPU radii (Section 3.3), by its characterisation
+    conflict graph under the GPU radii (Section 4.3), by its characterisation
     (independent, and every other candidate conflicts with a member of
     smaller key), checked in parallel over facilities;
   * the whole assignment and distances: the oracle's multi-source BFS from

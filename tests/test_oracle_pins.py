@@ -104,7 +104,7 @@ def test_sketch_equals_bottom_k_of_component(name, k):
 @pytest.mark.parametrize("k", [2, 3, 4, 16])
 def test_ads_and_hip_weights_by_definition(name, k):
     """ADS entries, hops, counted flags and HIP weights equal the definition
-    evaluated on all-pairs BFS balls (Section 2.3; HIP per Cohen 2014)."""
+    evaluated on all-pairs BFS balls (Section 3.3; HIP per Cohen 2014)."""
     rowp, cols = TINY[name]
     D = brute.apsp(rowp, cols)
     seed = 11
@@ -167,7 +167,7 @@ def test_hop_count_and_edge_merges(name):
 @pytest.mark.parametrize("name", ["er60", "mixed", "star7", "er30dense"])
 def test_algorithm1_single_vertex_matches_propagation(name):
     """Algorithm 1 (sequential, per vertex) and hop-synchronous Algorithm 2
-    build the same ADS for unweighted graphs (Section 2.3)."""
+    build the same ADS for unweighted graphs (Section 3.3)."""
     rowp, cols = TINY[name]
     k = 4
     g = oracle.Graph(rowp, cols)
@@ -326,7 +326,7 @@ def test_radius_residual_with_estimates():
 @pytest.mark.parametrize("name", sorted(TINY))
 def test_mis_is_lexicographically_first_on_materialised_hbar(name):
     """Open set = lexicographically-first MIS of the materialised conflict
-    graph H-bar under key (r_f, pi_f) (Algorithm 3 and Section 3.3)."""
+    graph H-bar under key (r_f, pi_f) (Algorithm 3 and Section 4.3)."""
     rowp, cols = TINY[name]
     n = len(rowp) - 1
     D = brute.apsp(rowp, cols)
@@ -348,7 +348,7 @@ def test_mis_is_lexicographically_first_on_materialised_hbar(name):
     for f in cand:
         if f not in S:
             assert any(key(s) < key(f) for s in adj[f] & S)
-    # each client is claimed by at most one open facility (Section 3.1)
+    # each client is claimed by at most one open facility (Section 4.1)
     for c in range(n):
         if client[c]:
             assert sum(1 for f in S if c in balls[f]) <= 1
