@@ -286,7 +286,6 @@ def run_gpu(args):
 
     for _ in range(args.warmup):
         step()
-    stats = g.stats()
 
     # ---------------- timed region (device-resident inputs)
     g.profile(True)
@@ -310,11 +309,20 @@ def run_gpu(args):
         ms = float(t.item())
         dist.barrier()
     torch.cuda.synchronize()
+    stats = g.stats()
     prof = {name: g.profile_query(name) for name in fl.PROF_CLASSES}
     launches = g.profile_query(-1)["launches"]
+    model = g.hop_model()
     hop_detail = [{"hop": h["hop"], "ms": round(h["ms"], 3), "scanned": h["scanned"],
                    "mask_share": round(h["mask"] / h["scanned"], 4) if h["scanned"] else 0.0,
-                   "changed": h["changed"]} for h in g.hop_stats()]
+                   "changed": h["changed"], "E": m["edge_merges"], "A": m["merging"], "delta_sum": m["delta_sum"],
+                   "delta_read": m["delta_read"], "new": m["new_entries"]}
+                  for h, m in zip(g.hop_stats(), model)]
+    # algorithmic bytes of one build by the per-hop model: row offsets and own
+    # sketch (read + write) per merging vertex, a column and the neighbour's
+    # delta ranks per edge-merge, an ADS id + weight per new entry
+    model_bytes = sum(8 * m["merging"] + 4 * m["edge_merges"] + 8 * m["delta_sum"] + 16 * w.k * m["merging"]
+                      + 12 * m["new_entries"] for m in model)
     g.profile(False)
     merges_step = stats["edge_merges"]
     value = world * merges_step * args.steps / (ms / 1e3)
@@ -366,12 +374,22 @@ def run_gpu(args):
     # ---------------- roofline of the dominant kernel (the sketch merge)
     peak, peak_kind = measured_peaks()
     mp = prof["sketch_merge"]
-    achieved = mp["alg_bytes"] / (mp["ms"] / 1e3) / 1e9 if mp["ms"] > 0 else None
-    per_launch_bytes = mp["alg_bytes"] / mp["launches"] if mp["launches"] else None
+    # numerator: the model's bytes of every timed build (the same graph and
+    # seed each step); beside it, the bytes the merge kernels' loads touched
+    alg_bytes = model_bytes * args.steps
+    achieved = alg_bytes / (mp["ms"] / 1e3) / 1e9 if mp["ms"] > 0 else None
+    achieved_reads = mp["alg_bytes"] / (mp["ms"] / 1e3) / 1e9 if mp["ms"] > 0 else None
+    per_launch_bytes = alg_bytes / mp["launches"] if mp["launches"] else None
     traffic = ncu_traffic("k_merge_hop", w.name)
     roofline = {"kernel": "k_merge_hop", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "peak_kind": f"{peak_kind} copy bandwidth", "alg_bytes_per_launch": per_launch_bytes,
+                "alg_bytes_per_build": model_bytes,
+                "alg_model": "per hop: 8 A + 4 E + 8 sum|D_{h-1}(u)| + 16 k A + 12 |D_h| (hop_detail terms)",
+                "achieved_reads": achieved_reads, "frac_reads": (achieved_reads / peak) if achieved_reads else None,
+                "reads_bytes_per_build": mp["alg_bytes"] / args.steps,
+                "reads_model": "as alg_model with the neighbour-delta ranks the kernels' loads read (delta_read) "
+                               "in place of sum|D_{h-1}(u)|",
                 "launches": mp["launches"], "kernel_ms": mp["ms"],
                 "share_of_step": mp["ms"] / ms if ms > 0 else None}
 

@@ -284,6 +284,27 @@ int fl_hop_stats(const fl_graph* g, int64_t cap, int64_t* n_hops, int64_t* scann
                  int64_t* changed, double* ms);
 
 /*
+ * fl_hop_model -- per-hop terms of the algorithmic-bytes model of the sketch
+ * hop (Alg. 2; one hop of the last build is one round of messages), filled
+ * by every build whether or not profiling is on.  For hop h = 1..n_hops:
+ *   edge_merges[h-1]  E_h: CSR entries (v, u) whose u gained entries at hop
+ *                     h-1 (every entry at hop 1);
+ *   merging[h-1]      A_h: vertices with at least one such entry;
+ *   delta_read[h-1]   neighbour-delta ranks the merge kernels read (filtering
+ *                     loads of the list merge; 4 words per neighbour and
+ *                     256-bit slice in the mask merge; 0 at hop 1, which
+ *                     recomputes its neighbours' ranks);
+ *   delta_sum[h-1]    the sum of |D_{h-1}(u)| over the E_h edge-merges (the
+ *                     ranks the paper's messages carry; = E_1 at hop 1);
+ *   new_entries[h-1]  |D_h|: ADS entries gained at hop h.
+ * The model's bytes of hop h are 8 A_h + 4 E_h + 8 delta_sum + 16 k A_h +
+ * 12 |D_h| (row offsets, columns, neighbour delta ranks, own sketch read and
+ * write, ADS id and weight).  Host arrays of cap entries; any may be NULL.
+ */
+int fl_hop_model(const fl_graph* g, int64_t cap, int64_t* n_hops, int64_t* edge_merges, int64_t* merging,
+                 int64_t* delta_read, int64_t* delta_sum, int64_t* new_entries);
+
+/*
  * fl_assign_nearest_noalloc -- nearest open facility of every vertex without
  * any device allocation.  (The paper has no counterpart: this is a deployment
  * variant of fl_assign_clients for callers that cannot let a library call

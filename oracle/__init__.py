@@ -186,16 +186,19 @@ class Graph:
         self._lib.orc_export_sketch(self._h, _p(S), _p(cnt))
         return S, cnt
 
-    def ads(self) -> dict:
+    def ads(self, ranks: bool = True) -> dict:
+        """The ADS, vertex-major (ranks=False leaves out the entries' ranks)."""
         ng = int(self._lib.orc_ads_groups(self._h))
         ne = int(self._lib.orc_ads_entries(self._h))
         out = dict(gofs=np.zeros(self.n + 1, np.int64), eofs=np.zeros(self.n + 1, np.int64),
                    ghop=np.zeros(ng, np.int32), gcnt=np.zeros(ng, np.int32),
                    gcounted=np.zeros(ng, np.int32), gwt=np.zeros(ng, np.float64),
-                   eid=np.zeros(ne, np.int32), erank=np.zeros(ne, np.uint64))
+                   eid=np.zeros(ne, np.int32))
+        if ranks:
+            out["erank"] = np.zeros(ne, np.uint64)
         self._lib.orc_export_ads(self._h, _p(out["gofs"]), _p(out["eofs"]), _p(out["ghop"]),
                                  _p(out["gcnt"]), _p(out["gcounted"]), _p(out["gwt"]),
-                                 _p(out["eid"]), _p(out["erank"]))
+                                 _p(out["eid"]), _p(out["erank"]) if ranks else None)
         return out
 
     def vertex_ads(self, k: int, seed: int, v: int, cap: int = 1 << 16) -> dict:

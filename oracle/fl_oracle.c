@@ -1235,3 +1235,363 @@ int orc_objective(int64_t n, const uint8_t* open, const double* cost, const uint
     *n_unserved = un;
     return ORC_OK;
 }
+
+/* ====================================================================== */
+/* The opening phase with epsilon > 0 (Section 4.1, Algorithm 3;          */
+/* Section 4.2, Algorithms 4 and 5 with Eq. 2/3; Section 4.3, Algorithm 6).*/
+/*                                                                        */
+/* Readings (where the paper is silent or at odds with itself):           */
+/*  - the grid R: alpha_0 = (gamma * (1 + eps)) / (m * m), m = |F||C| as   */
+/*    doubles, alpha_j = alpha_{j-1} * (1 + eps); iteration j = 1, 2, ...  */
+/*    runs at alpha_j (Algorithm 4 grows the radius before anything else); */
+/*  - gamma = max over clients c with a reachable facility of             */
+/*    min_f (c(f) + d(c,f)), one FP64 addition per pair;                  */
+/*  - a client at hop distance delta lies in the shell of the smallest    */
+/*    grid value >= delta: the shells (d/(1+eps), d] of Eq. 2/3, the first */
+/*    read as [0, alpha_0] so that a client at distance 0 is counted;     */
+/*  - q(f): Eq. 2 in the first iteration and Eq. 3 in every later one add */
+/*    up, per client, to [d_c <= alpha(c)] ((1+eps) alpha(c) - d_c), with */
+/*    d_c the client's shell value and alpha(c) the current radius, or    */
+/*    the radius at which c was frozen (the increments telescope).  The   */
+/*    oracle evaluates that sum over f's ADS (HIP-weighted client entries, */
+/*    in ADS order); mode 1 runs the literal incremental Eq. 2/3 instead  */
+/*    (a pin of the closed form);                                         */
+/*  - in an iteration, every unopened facility with q(f) >= c(f) opens    */
+/*    (alpha(f) = alpha_j); then every unfrozen client with an open       */
+/*    facility within (1 + eps) alpha_j freezes (alpha(c) = alpha_j): the */
+/*    freezing rule of Algorithm 3, which is also condition (2) of H's    */
+/*    edges;                                                              */
+/*  - U holds only clients with a facility in their component (the others */
+/*    can never freeze); the loop runs while some facility is unopened    */
+/*    and U is not empty (Algorithms 3 and 4);                            */
+/*  - clients still unfrozen when every facility is open take            */
+/*    alpha(c) = min_f d(c,f) (Algorithm 4's final step, "argmin" read as */
+/*    min); that is no grid value, so they have no edge in H;             */
+/*  - H has an edge (c, f) iff f is open, alpha(c) = alpha(f) and         */
+/*    d(c,f) <= (1 + eps) alpha(c) (Section 4.2); H-bar joins facilities  */
+/*    sharing a client; S is the lexicographically-first MIS of H-bar     */
+/*    under pi (Algorithm 6 run until no facility is active).            */
+/* ====================================================================== */
+
+#define EPS_MAX_GRID (1 << 22)
+
+/* gamma (see above); -1 when no client reaches a facility. */
+double orc_eps_gamma(const orc_graph* g, const double* cost, const uint8_t* client) {
+    if (!g) return NAN;
+    const int64_t n = g->n;
+    double gamma = -1.0;
+#pragma omp parallel
+    {
+        int32_t* dist = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+        int32_t* q = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+        double local = -1.0;
+        if (dist && q) {
+            for (int64_t v = 0; v < n; ++v) dist[v] = -1;
+#pragma omp for schedule(dynamic, 16)
+            for (int64_t c = 0; c < n; ++c) {
+                if (!client[c]) continue;
+                double best = INFINITY;
+                int64_t qh = 0, qt = 0;
+                dist[c] = 0;
+                q[qt++] = (int32_t)c;
+                while (qh < qt) {
+                    int32_t x = q[qh++];
+                    if (cost[x] < INFINITY) {
+                        double t = cost[x] + (double)dist[x];
+                        if (t < best) best = t;
+                    }
+                    for (int64_t e = g->rowp[x]; e < g->rowp[x + 1]; ++e) {
+                        int32_t u = g->cols[e];
+                        if (dist[u] < 0) { dist[u] = dist[x] + 1; q[qt++] = u; }
+                    }
+                }
+                for (int64_t j = 0; j < qt; ++j) dist[q[j]] = -1;
+                if (best < INFINITY && best > local) local = best;
+            }
+        }
+#pragma omp critical
+        { if (local > gamma) gamma = local; }
+        free(dist); free(q);
+    }
+    return gamma;
+}
+
+/* The grid: grid[0] = alpha_0, grid[j] = grid[j-1] * (1 + eps), up to the
+   first value >= bound.  Returns J (the last index) or -1. */
+static int64_t eps_grid(double alpha0, double eps, double bound, double** out) {
+    const double onepe = 1.0 + eps;
+    int64_t cap = 1024, J = 0;
+    double* grid = (double*)malloc((size_t)cap * sizeof(double));
+    if (!grid) return -1;
+    grid[0] = alpha0;
+    while (grid[J] < bound) {
+        if (J + 1 >= EPS_MAX_GRID) { free(grid); return -1; }
+        if (J + 1 == cap) {
+            cap *= 2;
+            double* t = (double*)realloc(grid, (size_t)cap * sizeof(double));
+            if (!t) { free(grid); return -1; }
+            grid = t;
+        }
+        grid[J + 1] = grid[J] * onepe;
+        ++J;
+    }
+    *out = grid;
+    return J;
+}
+
+/* Index of the smallest grid value >= delta (J + 1 when none). */
+static int64_t shell_index(const double* grid, int64_t J, int64_t delta) {
+    int64_t lo = 0, hi = J + 1;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (grid[mid] >= (double)delta) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+/* Multi-source BFS from the open facilities: dist[v] = hop distance to the
+   nearest one, -1 when none is reachable. */
+static void dist_to_open(const orc_graph* g, const int32_t* fac_iter, int32_t* dist, int32_t* q) {
+    const int64_t n = g->n;
+    int64_t qh = 0, qt = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        dist[v] = -1;
+        if (fac_iter[v] >= 0) { dist[v] = 0; q[qt++] = (int32_t)v; }
+    }
+    while (qh < qt) {
+        int32_t x = q[qh++];
+        for (int64_t e = g->rowp[x]; e < g->rowp[x + 1]; ++e) {
+            int32_t u = g->cols[e];
+            if (dist[u] < 0) { dist[u] = dist[x] + 1; q[qt++] = u; }
+        }
+    }
+}
+
+/* Component label of every vertex (smallest id of the component). */
+static void components(const orc_graph* g, int32_t* comp, int32_t* q) {
+    const int64_t n = g->n;
+    for (int64_t v = 0; v < n; ++v) comp[v] = -1;
+    for (int64_t s = 0; s < n; ++s) {
+        if (comp[s] >= 0) continue;
+        int64_t qh = 0, qt = 0;
+        comp[s] = (int32_t)s;
+        q[qt++] = (int32_t)s;
+        while (qh < qt) {
+            int32_t x = q[qh++];
+            for (int64_t e = g->rowp[x]; e < g->rowp[x + 1]; ++e) {
+                int32_t u = g->cols[e];
+                if (comp[u] < 0) { comp[u] = (int32_t)s; q[qt++] = u; }
+            }
+        }
+    }
+}
+
+/* q(f) at iteration j by the closed form (see above), summed over f's ADS
+   groups in hop order and their counted client entries in rank order. */
+static double eps_q(const orc_graph* g, int64_t f, int64_t j, const double* grid, double onepe,
+                    const int64_t* shell_of_hop, int64_t nhop, const uint8_t* client, const int32_t* cli_iter) {
+    double q = 0.0;
+    for (int64_t gi = g->gofs[f]; gi < g->gofs[f + 1]; ++gi) {
+        const orc_group* gr = &g->grp[gi];
+        const int64_t sj = gr->hop < nhop ? shell_of_hop[gr->hop] : INT64_MAX;
+        for (int32_t e = 0; e < gr->counted; ++e) {
+            const int32_t w = g->ent_id[gr->first + e];
+            if (!client[w]) continue;
+            const int64_t jw = cli_iter[w] >= 0 ? cli_iter[w] : j;
+            if (sj > jw) continue;                      /* d_c > alpha(c): not yet counted */
+            const double a = grid[jw];
+            q = q + gr->wt * (onepe * a - grid[sj]);
+        }
+    }
+    return q;
+}
+
+/* The literal increment of iteration j (Eq. 2 when j == 1, Eq. 3 after):
+   t = sum over shells d <= alpha_j of n-hat(f, d) times the bracket, with
+   n-hat(f, d) the HIP-estimated clients unfrozen at the start of the
+   iteration whose hop distance lies in shell d. */
+static double eps_increment(const orc_graph* g, int64_t f, int64_t j, const double* grid, double onepe,
+                            const int64_t* shell_of_hop, int64_t nhop, const uint8_t* client,
+                            const int32_t* cli_iter) {
+    double t = 0.0;
+    const double alpha = grid[j];
+    int64_t gi = g->gofs[f];
+    const int64_t g1 = g->gofs[f + 1];
+    while (gi < g1) {
+        const int64_t sj = g->grp[gi].hop < nhop ? shell_of_hop[g->grp[gi].hop] : INT64_MAX;
+        if (sj > j) break;
+        /* n-hat of shell sj: every group whose hop falls in it */
+        double nhat = 0.0;
+        while (gi < g1 && (g->grp[gi].hop < nhop ? shell_of_hop[g->grp[gi].hop] : INT64_MAX) == sj) {
+            const orc_group* gr = &g->grp[gi];
+            int64_t cnt = 0;
+            for (int32_t e = 0; e < gr->counted; ++e) {
+                const int32_t w = g->ent_id[gr->first + e];
+                if (client[w] && cli_iter[w] < 0) ++cnt;
+            }
+            nhat = nhat + (double)cnt * gr->wt;
+            ++gi;
+        }
+        const double d = grid[sj];
+        const double hi = onepe * alpha - d > 0.0 ? onepe * alpha - d : 0.0;
+        const double lo = alpha - d > 0.0 ? alpha - d : 0.0;
+        t = t + nhat * (j == 1 ? hi : hi - lo);
+    }
+    return t;
+}
+
+/* Algorithms 3-5 with epsilon > 0.  fac_iter[f] = iteration at which f
+   opened, cli_iter[c] = iteration at which c froze (-1: never); q_out[f] =
+   q(f) at its opening, or at the last iteration for facilities that stay
+   closed.  mode 0: q by the closed form; mode 1: q accumulated by Eq. 2/3.
+   Returns ORC_OK, or ORC_ESTATE when the grid would exceed its cap. */
+int orc_eps_open(const orc_graph* g, double eps, const double* cost, const uint8_t* client, int mode,
+                 int32_t* fac_iter, int32_t* cli_iter, double* q_out, double* alpha0_out, double* gamma_out,
+                 int64_t* iters_out) {
+    if (!g || !g->built || !(eps > 0.0)) return ORC_EINVAL;
+    const int64_t n = g->n;
+    const double onepe = 1.0 + eps;
+    int64_t nF = 0, nC = 0;
+    double max_cost = 0.0;
+    for (int64_t v = 0; v < n; ++v) {
+        fac_iter[v] = -1;
+        cli_iter[v] = -1;
+        q_out[v] = 0.0;
+        if (cost[v] < INFINITY) { ++nF; if (cost[v] > max_cost) max_cost = cost[v]; }
+        if (client[v]) ++nC;
+    }
+    *iters_out = 0;
+    *alpha0_out = 0.0;
+    *gamma_out = -1.0;
+    if (nF == 0 || nC == 0) return ORC_OK;
+    const double gamma = orc_eps_gamma(g, cost, client);
+    *gamma_out = gamma;
+    if (!(gamma >= 0.0)) return ORC_OK;        /* no client reaches a facility */
+    const double m = (double)nF * (double)nC;
+    const double alpha0 = (gamma * onepe) / (m * m);
+    *alpha0_out = alpha0;
+    double* grid = NULL;
+    const int64_t J = eps_grid(alpha0, eps, 2.0 * (max_cost + (double)n + 1.0), &grid);
+    if (J < 0) return ORC_ESTATE;
+    int64_t nhop = 0;
+    for (int64_t i = 0; i < g->ngroups; ++i) if (g->grp[i].hop + 1 > nhop) nhop = g->grp[i].hop + 1;
+    int64_t* shell_of_hop = (int64_t*)malloc((size_t)(nhop > 0 ? nhop : 1) * sizeof(int64_t));
+    int32_t* comp = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    int32_t* q = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    int32_t* dist = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    uint8_t* comp_has_fac = (uint8_t*)calloc((size_t)n, 1);
+    uint8_t* newly = (uint8_t*)calloc((size_t)n, 1);
+    if (!shell_of_hop || !comp || !q || !dist || !comp_has_fac || !newly) {
+        free(grid); free(shell_of_hop); free(comp); free(q); free(dist); free(comp_has_fac); free(newly);
+        return ORC_ENOMEM;
+    }
+    for (int64_t h = 0; h < nhop; ++h) shell_of_hop[h] = shell_index(grid, J, h);
+    components(g, comp, q);
+    for (int64_t v = 0; v < n; ++v) if (cost[v] < INFINITY) comp_has_fac[comp[v]] = 1;
+    int64_t unopened = nF, unfrozen = 0;
+    for (int64_t v = 0; v < n; ++v) if (client[v] && comp_has_fac[comp[v]]) ++unfrozen;
+    int64_t j = 0;
+    while (unopened > 0 && unfrozen > 0) {
+        ++j;
+        if (j > J) { free(grid); free(shell_of_hop); free(comp); free(q); free(dist); free(comp_has_fac); free(newly);
+                     return ORC_ESTATE; }
+        /* OpenFacilities (Algorithm 5): every unopened facility at once */
+        int64_t opened = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : opened)
+        for (int64_t f = 0; f < n; ++f) {
+            newly[f] = 0;
+            if (!(cost[f] < INFINITY) || fac_iter[f] >= 0) continue;
+            double qf;
+            if (mode == 0)
+                qf = eps_q(g, f, j, grid, onepe, shell_of_hop, nhop, client, cli_iter);
+            else
+                qf = q_out[f] + eps_increment(g, f, j, grid, onepe, shell_of_hop, nhop, client, cli_iter);
+            q_out[f] = qf;
+            if (qf >= cost[f]) { newly[f] = 1; ++opened; }
+        }
+        if (opened > 0) {
+            for (int64_t f = 0; f < n; ++f) if (newly[f]) fac_iter[f] = (int32_t)j;
+            unopened -= opened;
+        }
+        /* freeze every unfrozen client with an open facility within (1+eps) alpha_j */
+        dist_to_open(g, fac_iter, dist, q);
+        const double reach = onepe * grid[j];
+        for (int64_t c = 0; c < n; ++c) {
+            if (!client[c] || cli_iter[c] >= 0 || !comp_has_fac[comp[c]]) continue;
+            if (dist[c] >= 0 && (double)dist[c] <= reach) { cli_iter[c] = (int32_t)j; --unfrozen; }
+        }
+    }
+    *iters_out = j;
+    free(grid); free(shell_of_hop); free(comp); free(q); free(dist); free(comp_has_fac); free(newly);
+    return ORC_OK;
+}
+
+/* Algorithm 6 (Section 4.3): the lexicographically-first MIS under pi of
+   H-bar, H's edges as read above.  Sequential greedy in pi order: an open
+   facility f joins S iff no client c with alpha(c) = alpha(f) within
+   floor((1+eps) alpha(f)) hops of f is claimed; then it claims them.
+   Clients frozen at different iterations never meet, so this is the greedy
+   of every iteration's facilities on their own. */
+int orc_eps_select(const orc_graph* g, double eps, double alpha0, const int32_t* fac_iter,
+                   const int32_t* cli_iter, uint64_t seed, uint8_t* open, int64_t* n_open) {
+    if (!g || !(eps > 0.0)) return ORC_EINVAL;
+    const int64_t n = g->n;
+    const double onepe = 1.0 + eps;
+    int64_t jmax = 0, m = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        open[v] = 0;
+        if (fac_iter[v] > jmax) jmax = fac_iter[v];
+        if (fac_iter[v] >= 0) ++m;
+    }
+    *n_open = 0;
+    if (m == 0) return ORC_OK;
+    /* grid values up to jmax (the same products as the opening phase) */
+    double* grid = (double*)malloc((size_t)(jmax + 1) * sizeof(double));
+    cand_t* c = (cand_t*)malloc((size_t)m * sizeof(cand_t));
+    uint8_t* claimed = (uint8_t*)calloc((size_t)n, 1);
+    int32_t* dist = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    int32_t* q = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    int32_t* ball = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    if (!grid || !c || !claimed || !dist || !q || !ball) {
+        free(grid); free(c); free(claimed); free(dist); free(q); free(ball);
+        return ORC_ENOMEM;
+    }
+    grid[0] = alpha0;
+    for (int64_t j = 1; j <= jmax; ++j) grid[j] = grid[j - 1] * onepe;
+    m = 0;
+    for (int64_t f = 0; f < n; ++f)
+        if (fac_iter[f] >= 0) { c[m].r = 0.0; c[m].pi = orc_priority(seed, f); c[m].f = (int32_t)f; ++m; }
+    qsort(c, (size_t)m, sizeof(cand_t), cand_cmp);   /* all r equal: pi order */
+    for (int64_t v = 0; v < n; ++v) dist[v] = -1;
+    int64_t opened = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        const int32_t f = c[i].f;
+        const int32_t jf = fac_iter[f];
+        const int64_t B = ball_depth(onepe * grid[jf]);
+        int64_t qh = 0, qt = 0, nb = 0;
+        int conflict = cli_iter[f] == jf && claimed[f];
+        dist[f] = 0;
+        q[qt++] = f;
+        if (cli_iter[f] == jf && !conflict) ball[nb++] = f;
+        while (qh < qt && !conflict) {
+            int32_t x = q[qh++];
+            if (dist[x] == B) continue;
+            for (int64_t e = g->rowp[x]; e < g->rowp[x + 1]; ++e) {
+                int32_t u = g->cols[e];
+                if (dist[u] >= 0) continue;
+                if (cli_iter[u] == jf && claimed[u]) { conflict = 1; break; }
+                dist[u] = dist[x] + 1;
+                q[qt++] = u;
+                if (cli_iter[u] == jf) ball[nb++] = u;
+            }
+        }
+        for (int64_t k2 = 0; k2 < qt; ++k2) dist[q[k2]] = -1;
+        if (conflict) continue;
+        open[f] = 1;
+        ++opened;
+        for (int64_t k2 = 0; k2 < nb; ++k2) claimed[ball[k2]] = 1;
+    }
+    *n_open = opened;
+    free(grid); free(c); free(claimed); free(dist); free(q); free(ball);
+    return ORC_OK;
+}

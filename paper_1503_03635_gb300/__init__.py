@@ -27,7 +27,7 @@ EXPORTS = ("fl_graph_create", "fl_graph_destroy", "fl_build_sketches", "fl_sketc
            "fl_export_sketches", "fl_export_ads", "fl_solve_create", "fl_solve_destroy",
            "fl_compute_radii", "fl_open_facilities", "fl_assign_clients", "fl_objective",
            "fl_solve_stats", "fl_status_str", "fl_last_error", "fl_profile_enable", "fl_profile_reset",
-           "fl_profile_query", "fl_hop_stats", "fl_batch_create_union", "fl_batch_create_replicas",
+           "fl_profile_query", "fl_hop_stats", "fl_hop_model", "fl_batch_create_union", "fl_batch_create_replicas",
            "fl_batch_solve", "fl_batch_info", "fl_batch_destroy", "fl_assign_nearest_noalloc",
            "fl_ball_sizes", "fl_ball_estimates", "fl_compute_radii_exact")
 
@@ -78,6 +78,7 @@ def load(build_if_missing: bool = True):
             "fl_profile_reset": ([vp], ci),
             "fl_profile_query": ([vp, ci, P64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ci),
             "fl_hop_stats": ([vp, i64, P64, vp, vp, vp, vp], ci),
+            "fl_hop_model": ([vp, i64, P64, vp, vp, vp, vp, vp], ci),
             "fl_batch_create_union": ([ci, vp, vp, vp, vp, ci, vp, ctypes.POINTER(vp)], ci),
             "fl_batch_create_replicas": ([vp, ci, vp, ctypes.POINTER(vp)], ci),
             "fl_batch_solve": ([vp, ci, ci, u64, vp, vp, vp, vp, vp, vp, vp, vp, vp, ci], ci),
@@ -202,6 +203,18 @@ class Graph:
                                       ms.ctypes.data_as(ctypes.c_void_p)))
         return [dict(hop=i + 1, scanned=int(sc[i]), mask=int(mk[i]), changed=int(ch[i]), ms=float(ms[i]))
                 for i in range(h)]
+
+    def hop_model(self) -> list:
+        """Per hop of the last build: edge-merges E, merging vertices A,
+        neighbour-delta ranks read, sum of |D_{h-1}(u)| over the edge-merges,
+        new entries (the terms of the algorithmic-bytes model of a hop)."""
+        H = ctypes.c_int64()
+        _check(self._lib.fl_hop_model(self._h, 0, ctypes.byref(H), None, None, None, None, None))
+        h = H.value
+        cols = [np.zeros(h, np.int64) for _ in range(5)]
+        _check(self._lib.fl_hop_model(self._h, h, ctypes.byref(H), *[c.ctypes.data_as(ctypes.c_void_p) for c in cols]))
+        names = ("edge_merges", "merging", "delta_read", "delta_sum", "new_entries")
+        return [dict(hop=i + 1, **{nm: int(c[i]) for nm, c in zip(names, cols)}) for i in range(h)]
 
     def profile(self, on: bool = True):
         _check(self._lib.fl_profile_enable(self._h, 1 if on else 0))

@@ -36,7 +36,7 @@ void destroy_graph(fl_graph* g) {
                     &g->S, &g->Scnt, &g->D[0], &g->D[1], &g->Dcnt[0], &g->Dcnt[1], &g->frontier[0],
                     &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent, &g->stg_grp, &g->gofs, &g->eofs,
                     &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub, &g->ctr, &g->scratch,
-                    &g->relax_aux, &g->U, &g->DM[0], &g->DM[1], &g->PM, &g->vbase, &g->vpart, &g->rid,
+                    &g->relax_aux, &g->U, &g->DM[0], &g->DM[1], &g->PM, &g->seg_flag, &g->vbase, &g->vpart, &g->rid,
                     &g->inv, &g->xbits, &g->xaux, &g->xio};
     for (DBuf* b : bufs) dfree_idle(*b);
     for (cudaEvent_t e : g->prof.ev) cudaEventDestroy(e);
@@ -235,6 +235,23 @@ int fl_hop_stats(const fl_graph* g, int64_t cap, int64_t* n_hops, int64_t* scann
         if (mask) mask[i] = g->hop_mask[i];
         if (changed) changed[i] = g->hop_changed[i];
         if (ms) ms[i] = g->hop_ms[i];
+    }
+    return FL_OK;
+}
+
+int fl_hop_model(const fl_graph* g, int64_t cap, int64_t* n_hops, int64_t* edge_merges, int64_t* merging,
+                 int64_t* delta_read, int64_t* delta_sum, int64_t* new_entries) {
+    if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    if (!g->built) FL_FAIL(FL_ESTATE, "sketches not built");
+    if (cap < 0) FL_FAIL(FL_EINVAL, "negative capacity");
+    const int64_t H = (int64_t)g->hop_E.size();
+    if (n_hops) *n_hops = H;
+    for (int64_t i = 0; i < std::min(H, cap); ++i) {
+        if (edge_merges) edge_merges[i] = g->hop_E[i];
+        if (merging) merging[i] = g->hop_A[i];
+        if (delta_read) delta_read[i] = g->hop_R[i];
+        if (delta_sum) delta_sum[i] = g->hop_SD[i];
+        if (new_entries) new_entries[i] = g->hop_new[i];
     }
     return FL_OK;
 }

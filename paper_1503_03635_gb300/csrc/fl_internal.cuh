@@ -329,6 +329,8 @@ struct Counters {
     unsigned long long aux3;
     unsigned long long scanned;      // hop census: CSR entries read this hop
     unsigned long long mask_scanned; // hop census: of those, read by the mask merge
+    unsigned long long delta_next;   // merge: sum of deg(u) * |D_h(u)| over changed u (delta ranks of the next hop's edge-merges)
+    unsigned long long new_entries;  // merge: entries gained this hop (sum of |D_h(v)|)
 };
 
 // ----------------------------------------------------------------- profiling
@@ -401,6 +403,7 @@ struct fl_graph {
     uint64_t ulim = 0;             // largest entry of U
     fl::DBuf DM[2];                // uint64[n*kUWords]: hop delta masks over U
     fl::DBuf PM;                   // uint64[n_seg*kUWords]: partial masks of hub segments (scratch)
+    fl::DBuf seg_flag;             // uint8[n_seg]: the segment had a neighbour that gained entries (scratch)
     // sketches
     int k = 0;
     uint64_t seed = 0;
@@ -430,6 +433,10 @@ struct fl_graph {
     // per-hop counters of the last build (index h-1)
     std::vector<int64_t> hop_scanned, hop_mask, hop_changed;
     std::vector<double> hop_ms;
+    // per-hop terms of the algorithmic-bytes model of a hop: edge-merges E_h,
+    // merging vertices A_h, neighbour-delta ranks the kernels read R_h, the
+    // delta ranks of the edge-merges sum |D_{h-1}(u)| over E_h, new entries |D_h|
+    std::vector<int64_t> hop_E, hop_A, hop_R, hop_SD, hop_new;
     cudaEvent_t hop_ev[2] = {nullptr, nullptr};
     // exact sizes and radii: source bits (visited, two frontiers), row-length
     // lists and sweep state, staged query inputs and outputs

@@ -211,11 +211,11 @@ __device__ __forceinline__ void load_u(uint64_t* sU, const uint64_t* __restrict_
 // Per-group hop counters in shared memory, one slot per group, updated by
 // the group's lane 0 without atomics and flushed once at the end of a kernel
 // (the hop kernels run at the register limit; counters in registers cost
-// spills in the merge loops).  32-bit: a group adds at most kHubDeg per
-// vertex it processes (hub degrees go to the global counter directly) and,
-// with the grids of the hop kernels, processes at most 2^31 / 77824 work
-// items.
-enum { kCFront, kCMerges, kCMerging, kNCtr };
+// spills in the merge loops).  32-bit: a group adds at most 32 * kHubDeg
+// per vertex it processes (hub degrees go to the global counters directly)
+// and, with the grids of the hop kernels, processes at most 2^31 / 77824 <
+// 2^16 work items.
+enum { kCFront, kCMerges, kCMerging, kCDelta, kCNew, kNCtr };
 __shared__ unsigned s_hop_ctr[256 / 16][kNCtr];
 
 struct HopCounters {
@@ -397,9 +397,9 @@ __device__ __forceinline__ void gather_range(const Grp<G>& g, int k, int hop, ui
 
 // Write the results of vertex v after its merge: new sketch, the entries it
 // gained (for the next hop), their mask and its staged ADS group in work slot
-// `slot`.  Returns whether the sketch changed.
+// `slot`.  Returns the number of entries gained (0: the sketch is unchanged).
 template <int G>
-__device__ __forceinline__ bool finish_vertex(const Grp<G>& g, int k, uint64_t seed, int hop, int32_t v,
+__device__ __forceinline__ int finish_vertex(const Grp<G>& g, int k, uint64_t seed, int hop, int32_t v,
                                               int64_t deg, uint64_t old, const Sketch<G>& s, int64_t slot,
                                               uint64_t* __restrict__ S, uint8_t* __restrict__ Scnt,
                                               uint64_t* __restrict__ Dc, uint8_t* __restrict__ Dcc,
@@ -413,7 +413,7 @@ __device__ __forceinline__ bool finish_vertex(const Grp<G>& g, int k, uint64_t s
     const int dcnt = __popc(newm);
     if (dcnt == 0) {
         if (g.l == 0) stg_grp[slot].info = 0;  // empty slot
-        return false;
+        return 0;
     }
     const int cnt_new = __popc(g.ballot(valid));
     if (g.l < k) S[(int64_t)v * k + g.l] = s.sk;
@@ -449,9 +449,13 @@ __device__ __forceinline__ bool finish_vertex(const Grp<G>& g, int k, uint64_t s
         ve[v] = gr.eidx + dcnt;
         stg_grp[slot] = gr;
         hop_ctr_add<G>(kCFront, 1u);
-        if (deg <= kHubDeg) hop_ctr_add<G>(kCMerges, (unsigned)deg);
+        hop_ctr_add<G>(kCNew, (unsigned)dcnt);
+        if (deg <= kHubDeg) {
+            hop_ctr_add<G>(kCMerges, (unsigned)deg);
+            hop_ctr_add<G>(kCDelta, (unsigned)(deg * dcnt));
+        }
     }
-    return true;
+    return dcnt;
 }
 
 template <int G>
@@ -465,6 +469,8 @@ __device__ __forceinline__ void flush_counters(const Grp<G>& g, HopCounters hc, 
         if (c[kCFront]) atomicAdd(&ctr->frontier, (unsigned long long)c[kCFront]);
         if (c[kCMerges]) atomicAdd(&ctr->merges, (unsigned long long)c[kCMerges]);
         if (c[kCMerging]) atomicAdd(&ctr->merging, (unsigned long long)c[kCMerging]);
+        if (c[kCDelta]) atomicAdd(&ctr->delta_next, (unsigned long long)c[kCDelta]);
+        if (c[kCNew]) atomicAdd(&ctr->new_entries, (unsigned long long)c[kCNew]);
     }
 }
 
@@ -537,7 +543,8 @@ __global__ void __launch_bounds__(256) k_hop_hub_segments(
     int64_t n_seg, const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols, int k, uint64_t seed,
     int hop, const uint64_t* __restrict__ S, const uint8_t* __restrict__ Scnt, const uint64_t* __restrict__ Dp,
     const uint8_t* __restrict__ Dcp, uint64_t* __restrict__ part, const uint64_t* __restrict__ U, uint64_t ulim,
-    const uint64_t* __restrict__ DMp, uint64_t* __restrict__ PM, IdMap ids, Counters* ctr) {
+    const uint64_t* __restrict__ DMp, uint64_t* __restrict__ PM, uint8_t* __restrict__ seg_flag,
+    const uint32_t* __restrict__ hub_stamp, uint32_t sparse_hop, IdMap ids, Counters* ctr) {
     __shared__ uint64_t sU[kUW];
     load_u(sU, U);
     const Grp<G> g;
@@ -545,8 +552,14 @@ __global__ void __launch_bounds__(256) k_hop_hub_segments(
     HopCounters hc;
     hop_ctr_init(g);
     for (int64_t sidx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; sidx < n_seg; sidx += groups) {
+        const unsigned long long cand0 = hc.cand;
         const int32_t h = seg_hub[sidx];
         const int32_t v = hubs[h];
+        if (sparse_hop && hub_stamp[v] != sparse_hop) {
+            // sparse hop: no neighbour of this hub gained entries
+            if (g.l == 0) seg_flag[sidx] = 0;
+            continue;
+        }
         const int64_t e0 = rowp[v] + (sidx - hub_seg[h]) * kSeg;
         const int64_t e1 = min(e0 + (int64_t)kSeg, rowp[v + 1]);
         const uint64_t kth_old = S[(int64_t)v * k + k - 1];
@@ -559,6 +572,9 @@ __global__ void __launch_bounds__(256) k_hop_hub_segments(
                 const Mask4 m = gather_masks(g, cols, e0, e1, Dcp, DMp, q, hc.cand);
                 if (g.l < 4) PM[sidx * kUWords + q * 4 + g.l] = m.word(g.l);
             }
+            // a neighbour of this segment gained entries at the previous hop
+            const bool merged = g.ballot(hc.cand != cand0) != 0;
+            if (g.l == 0) seg_flag[sidx] = merged ? 1 : 0;
             continue;
         }
         Sketch<G> s;
@@ -568,8 +584,19 @@ __global__ void __launch_bounds__(256) k_hop_hub_segments(
         s.tau = s.tau_base;
         gather_range(g, k, hop, seed, cols, e0, e1, Dcp, Dp, ids, s, hc.cand);
         if (g.l < k) part[sidx * k + g.l] = s.sk;
+        const bool merged = hop == 1 || g.ballot(hc.cand != cand0) != 0;
+        if (g.l == 0) seg_flag[sidx] = merged ? 1 : 0;
     }
     flush_counters(g, hc, ctr);
+}
+
+// Did some segment of hub h have a neighbour that gained entries?
+template <int G>
+__device__ __forceinline__ bool hub_merged(const Grp<G>& g, const int64_t* __restrict__ hub_seg,
+                                           const uint8_t* __restrict__ seg_flag, int64_t h) {
+    bool any = false;
+    for (int64_t sidx = hub_seg[h] + g.l; sidx < hub_seg[h + 1]; sidx += G) any |= seg_flag[sidx] != 0;
+    return g.ballot(any) != 0;
 }
 
 // Hubs: merge the partial lists of all segments into the hub's sketch.
@@ -580,6 +607,7 @@ __global__ void __launch_bounds__(256) k_hop_hubs(
     int64_t slot0, uint64_t* __restrict__ S, uint8_t* __restrict__ Scnt, uint64_t* __restrict__ Dc,
     uint8_t* __restrict__ Dcc, int32_t* __restrict__ vg, int32_t* __restrict__ ve, int32_t* __restrict__ stg_ent,
     StgGroup* __restrict__ stg_grp, const uint64_t* __restrict__ U, uint64_t ulim, const uint64_t* __restrict__ PM,
+    const uint8_t* __restrict__ seg_flag, const uint32_t* __restrict__ hub_stamp, uint32_t sparse_hop,
     uint64_t* __restrict__ DMc, IdMap ids, Counters* ctr) {
     __shared__ uint64_t sU[kUW];
     load_u(sU, U);
@@ -589,6 +617,10 @@ __global__ void __launch_bounds__(256) k_hop_hubs(
     hop_ctr_init(g);
     for (int64_t h = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; h < n_hubs; h += groups) {
         const int32_t v = hubs[h];
+        if (sparse_hop && hub_stamp[v] != sparse_hop) {
+            if (g.l == 0) stg_grp[slot0 + h].info = 0;  // unchanged: empty slot
+            continue;
+        }
         const uint64_t old = g.l < k ? S[(int64_t)v * k + g.l] : kEmpty;
         Sketch<G> s;
         s.sk = old;
@@ -598,17 +630,16 @@ __global__ void __launch_bounds__(256) k_hop_hubs(
         if (hop > 1 && s.cnt == k && s.tau <= ulim) {
             // saturated hub: OR of the segments' partial masks
             const int idx = g.l < k ? u_pos(sU, ulim, old) : -1;
-            bool any = false;
             auto part_slice = [&](int q) {
                 Mask4 m;
                 for (int64_t sidx = hub_seg[h] + g.l; sidx < hub_seg[h + 1]; sidx += G)
                     m.load(PM + sidx * kUWords + q * 4);
                 grp_or(g, m);
-                any |= !m.empty();
                 return m;
             };
             uint64_t sk_new;
             const bool changed = merge_slices(g, k, sU, idx, part_slice(0), part_slice, sk_new);
+            const bool any = hub_merged(g, hub_seg, seg_flag, h);
             if (g.l == 0 && any) hop_ctr_add<G>(kCMerging, 1u);
             if (!changed) {
                 if (g.l == 0) stg_grp[slot0 + h].info = 0;  // unchanged: empty slot
@@ -617,30 +648,34 @@ __global__ void __launch_bounds__(256) k_hop_hubs(
             s.sk = sk_new;
             s.cnt = k;
             const int64_t deg = rowp[v + 1] - rowp[v];
-            if (finish_vertex(g, k, seed, hop, v, deg, old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve, stg_ent, stg_grp,
-                              sU, ulim, DMc, ids, hc) &&
-                g.l == 0)
+            const int dc = finish_vertex(g, k, seed, hop, v, deg, old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve, stg_ent,
+                                         stg_grp, sU, ulim, DMc, ids, hc);
+            if (dc && g.l == 0) {
                 atomicAdd(&ctr->merges, (unsigned long long)deg);
+                atomicAdd(&ctr->delta_next, (unsigned long long)(deg * dc));
+            }
             continue;
         }
-        bool any = false;
         for (int64_t sidx = hub_seg[h]; sidx < hub_seg[h + 1]; ++sidx) {
             const uint64_t x = g.l < k ? part[sidx * k + g.l] : kEmpty;
-            any |= g.ballot(x != kEmpty) != 0;
             absorb(g, k, x, s);
         }
+        const bool any = hub_merged(g, hub_seg, seg_flag, h);
         if (g.l == 0 && any) hop_ctr_add<G>(kCMerging, 1u);
         const int64_t deg = rowp[v + 1] - rowp[v];
-        if (finish_vertex(g, k, seed, hop, v, deg, old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve, stg_ent, stg_grp, sU,
-                          ulim, DMc, ids, hc) &&
-            g.l == 0)
+        const int dc = finish_vertex(g, k, seed, hop, v, deg, old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve, stg_ent,
+                                     stg_grp, sU, ulim, DMc, ids, hc);
+        if (dc && g.l == 0) {
             atomicAdd(&ctr->merges, (unsigned long long)deg);
+            atomicAdd(&ctr->delta_next, (unsigned long long)(deg * dc));
+        }
     }
     flush_counters(g, hc, ctr);
 }
 
 // Sparse hops: the non-hub part of N(frontier).  Warp per frontier vertex;
-// each neighbour is appended once (stamp = hop).
+// each neighbour is appended once (stamp = hop); hubs in N(frontier) get
+// stamp = hop too, and the hub kernels skip the others.
 __global__ void k_expand(const int32_t* __restrict__ fr, int64_t n_fr, const int64_t* __restrict__ rowp,
                          const int32_t* __restrict__ cols, uint32_t* __restrict__ stamp, uint32_t hop,
                          int32_t* __restrict__ act, Counters* ctr) {
@@ -655,7 +690,10 @@ __global__ void k_expand(const int32_t* __restrict__ fr, int64_t n_fr, const int
             int32_t v = 0;
             if (e < end) {
                 v = cols[e];
-                if (rowp[v + 1] - rowp[v] <= kHubDeg) fresh = atomicExch(&stamp[v], hop) != hop;
+                if (rowp[v + 1] - rowp[v] <= kHubDeg)
+                    fresh = atomicExch(&stamp[v], hop) != hop;
+                else
+                    stamp[v] = hop;  // a hub with a frontier neighbour: its segments run this hop
             }
             long long at = warp_append(fresh, &ctr->active);
             if (at >= 0) act[at] = v;
@@ -804,11 +842,12 @@ int build_work_lists(fl_graph* g) {
 // Runs before the hop kernels change the sketches.
 __global__ void k_hop_census(const int32_t* __restrict__ list, int64_t n_list, const int64_t* __restrict__ rowp,
                              const uint64_t* __restrict__ S, const uint8_t* __restrict__ Scnt, int k, int hop,
-                             uint64_t ulim, Counters* ctr) {
+                             uint64_t ulim, const uint32_t* __restrict__ stamp, uint32_t sparse_hop, Counters* ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long sc = 0, mk = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_list; i += stride) {
         const int32_t v = list[i];
+        if (sparse_hop && stamp[v] != sparse_hop) continue;  // a hub the hop skips
         const unsigned long long d = (unsigned long long)(rowp[v + 1] - rowp[v]);
         sc += d;
         if (hop > 1 && Scnt[v] == k && S[(int64_t)v * k + k - 1] <= ulim) mk += d;
@@ -913,7 +952,8 @@ static int select_small_ranks(fl_graph* g) {
 
 template <int G>
 static int launch_hop(fl_graph* g, int hop, const int32_t* list, int64_t n_list, int pin, int pout,
-                      int64_t slot_base) {
+                      int64_t slot_base, bool sparse) {
+    const uint32_t sparse_hop = sparse ? (uint32_t)hop : 0u;
     cudaStream_t st = g->stream;
     const int k = g->k;
     const int per_block = 256 / G;
@@ -934,13 +974,15 @@ static int launch_hop(fl_graph* g, int hop, const int32_t* list, int64_t n_list,
                                         g->n_seg, g->rowp.as<int64_t>(), g->cols.as<int32_t>(), k, g->seed, hop,
                                         g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[pin].as<uint64_t>(),
                                         g->Dcnt[pin].as<uint8_t>(), g->part.as<uint64_t>(), g->U.as<uint64_t>(), g->ulim,
-                                        g->DM[pin].as<uint64_t>(), g->PM.as<uint64_t>(), vb, g->ctr.as<Counters>()));
+                                        g->DM[pin].as<uint64_t>(), g->PM.as<uint64_t>(), g->seg_flag.as<uint8_t>(),
+                                        g->stamp.as<uint32_t>(), sparse_hop, vb, g->ctr.as<Counters>()));
         FL_LAUNCH(kProfSketchMerge, k_hop_hubs<G><<<grid_for(g->n_hubs, per_block), 256, 0, st>>>(
                                         g->hub_list.as<int32_t>(), g->n_hubs, g->hub_seg.as<int64_t>(),
                                         g->part.as<uint64_t>(), g->rowp.as<int64_t>(), k, g->seed, hop, n_list,
                                         g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[pout].as<uint64_t>(),
                                         g->Dcnt[pout].as<uint8_t>(), g->vg.as<int32_t>(), g->ve.as<int32_t>(), ent,
                                         grp, g->U.as<uint64_t>(), g->ulim, g->PM.as<uint64_t>(),
+                                        g->seg_flag.as<uint8_t>(), g->stamp.as<uint32_t>(), sparse_hop,
                                         g->DM[pout].as<uint64_t>(), vb, g->ctr.as<Counters>()));
     }
     FL_CUDA(cudaGetLastError());
@@ -974,6 +1016,7 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     FL_TRY(dalloc(g->DM[0], (size_t)n * kUWords * 8));
     FL_TRY(dalloc(g->DM[1], (size_t)n * kUWords * 8));
     FL_TRY(dalloc(g->PM, (size_t)std::max<int64_t>(g->n_seg, 1) * kUWords * 8));
+    FL_TRY(dalloc(g->seg_flag, (size_t)std::max<int64_t>(g->n_seg, 1)));
     // staging: slots 0..n-1 for hop 0, then one slot per work item of each hop
     const int64_t per_dense = g->n_low + g->n_hubs;
     size_t slot_cap = (size_t)n + (size_t)per_dense * 8 + 1024;
@@ -1010,6 +1053,7 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     g->hop_mask.clear();
     g->hop_changed.clear();
     g->hop_ms.clear();
+    for (auto* vec : {&g->hop_E, &g->hop_A, &g->hop_R, &g->hop_SD, &g->hop_new}) vec->clear();
     const bool time_hops = g->prof.on != 0;
     if (time_hops && !g->hop_ev[0]) {
         FL_CUDA(cudaEventCreate(&g->hop_ev[0]));
@@ -1020,13 +1064,15 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     int64_t used_slots = n;
     int64_t n_front = n;  // hop 0: every vertex gained its own rank
     bool fr_list_ready = false;
-    int64_t total_merges = 0, next_merges = g->nnz;
+    // hop 1: every vertex gained its own rank at hop 0, so each CSR entry is
+    // an edge-merge carrying one delta rank
+    int64_t total_merges = 0, next_merges = g->nnz, next_delta = g->nnz;
     int hop = 1;
     int rc = FL_OK;
     for (;; ++hop) {
         if (hop > kMaxHops) { rc = FL_ETIMEOUT; set_error(rc, "more than 65535 hops"); break; }
         total_merges += next_merges;
-        const int64_t hop_merges = next_merges;
+        const int64_t hop_merges = next_merges, hop_delta = next_delta;
         const int pin = (hop - 1) & 1, pout = hop & 1;
         const int32_t* list;
         int64_t n_list;
@@ -1059,18 +1105,20 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
             if (n_list > 0)
                 FL_LAUNCH(kProfSketchOther, k_hop_census<<<grid_for(n_list, 256), 256, 0, st>>>(
                                                 list, n_list, g->rowp.as<int64_t>(), g->S.as<uint64_t>(),
-                                                g->Scnt.as<uint8_t>(), k, hop, g->ulim, g->ctr.as<Counters>()));
+                                                g->Scnt.as<uint8_t>(), k, hop, g->ulim, nullptr, 0u,
+                                                g->ctr.as<Counters>()));
             if (g->n_hubs > 0)
                 FL_LAUNCH(kProfSketchOther, k_hop_census<<<grid_for(g->n_hubs, 256), 256, 0, st>>>(
                                                 g->hub_list.as<int32_t>(), g->n_hubs, g->rowp.as<int64_t>(),
                                                 g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), k, hop, g->ulim,
+                                                g->stamp.as<uint32_t>(), dense ? 0u : (uint32_t)hop,
                                                 g->ctr.as<Counters>()));
             FL_CUDA(cudaEventRecord(g->hop_ev[0], st));
         }
         if (k <= 16)
-            FL_TRY(launch_hop<16>(g, hop, list, n_list, pin, pout, used_slots));
+            FL_TRY(launch_hop<16>(g, hop, list, n_list, pin, pout, used_slots, !dense));
         else
-            FL_TRY(launch_hop<32>(g, hop, list, n_list, pin, pout, used_slots));
+            FL_TRY(launch_hop<32>(g, hop, list, n_list, pin, pout, used_slots, !dense));
         if (time_hops) FL_CUDA(cudaEventRecord(g->hop_ev[1], st));
         regions.push_back({used_slots, slots});
         used_slots += slots;
@@ -1082,9 +1130,15 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
             g->hop_mask.push_back(time_hops ? (int64_t)g->h_ctr->mask_scanned : 0);
             g->hop_changed.push_back((int64_t)g->h_ctr->frontier);
             g->hop_ms.push_back(hop_ms);
+            g->hop_E.push_back(hop_merges);
+            g->hop_A.push_back((int64_t)g->h_ctr->merging);
+            g->hop_R.push_back((int64_t)g->h_ctr->cand_reads);
+            g->hop_SD.push_back(hop_delta);
+            g->hop_new.push_back((int64_t)g->h_ctr->new_entries);
         }
         n_front = (int64_t)g->h_ctr->frontier;
         next_merges = (int64_t)g->h_ctr->merges;
+        next_delta = (int64_t)g->h_ctr->delta_next;
         // algorithmic bytes of this hop's merge: row offsets of each merging
         // vertex (8 B), frontier columns (4 B per edge-merge), neighbour delta
         // ranks read (8 B each), own sketch read + write (16k B per merging

@@ -1,7 +1,8 @@
 """GPU parity of batches (fl_batch_*): every instance of a batch gives the
 result of the plain fl_* sequence on that instance alone (bit-exact open
 sets, assignments, distances, counts; objective within 1e-9 relative), and
-the plain results are checked against the oracle on some instances."""
+equals the oracle's result for that instance (every instance of the union
+batches, four instances of the replica batch)."""
 import numpy as np
 import pytest
 
@@ -60,9 +61,8 @@ def test_union_batch_matches_plain_solves(k):
         n = len(rowp) - 1
         want = _plain(rowp, cols, k, 3, costs[i], clients[i])
         _check_instance(res, lo, lo + n, i, want)
-        if i in (0, 3):
-            orc = oracle.solve(rowp, cols, k, 3, costs[i], clients[i])
-            assert np.array_equal(want["open"], orc["open"]) and np.array_equal(want["assign"], orc["assign"])
+        # every instance of the batch against the oracle, too
+        _check_instance(res, lo, lo + n, i, oracle.solve(rowp, cols, k, 3, costs[i], clients[i]))
         lo += n
     # a second solve on the same batch (new costs) is independent of the first
     costs2 = [np.where(np.isfinite(c), c * 1.7, np.inf) for c in costs]
@@ -107,6 +107,17 @@ def test_replica_batch_matches_plain_solves_on_the_resident_graph():
         _check_instance(part, i * n, (i + 1) * n, i, {key: res[key][i * n:(i + 1) * n] if key in
                                                       ("open", "assign", "dist") else res[key][i]
                                                       for key in res})
+    # four instances against the oracle's solve on the resident graph
+    og = oracle.Graph(rowp, cols)
+    og.build_sketches(k, seed)
+    for i in (0, 2, 4, 5):
+        r = og.radii(costs[i], clients[i])
+        op, no = og.open_facilities(r, clients[i], seed)
+        a, d = og.assign(op)
+        obj, ds, un = oracle.objective(op, costs[i], clients[i], d)
+        _check_instance(res, i * n, (i + 1) * n, i, dict(open=op, assign=a, dist=d, n_open=no, objective=obj,
+                                                         dist_sum=ds, n_unserved=un))
+    og.close()
     again = b.solve(k, seed, np.concatenate(costs), np.concatenate(clients))
     for key in ("open", "assign", "dist", "n_open", "dist_sum", "n_unserved"):
         assert np.array_equal(again[key], res[key])

@@ -250,3 +250,50 @@ def test_device_memory_arguments():
     assert np.array_equal(op.cpu().numpy(), orc["open"]) and nopen == orc["n_open"]
     assert np.array_equal(a.cpu().numpy(), orc["assign"])
     assert np.array_equal(d.cpu().numpy(), orc["dist"])
+
+
+# ------------------------------------------------------------------ hop model
+
+def _model_from_ads(rowp, cols, ads, hops):
+    """Per-hop terms of the algorithmic-bytes model, recomputed from the
+    oracle's ADS: |D_h(u)| is the entry count of u's group at hop h."""
+    n = len(rowp) - 1
+    deg = np.diff(rowp)
+    H = hops + 1
+    dcnt = np.zeros((H + 1, n), np.int64)
+    owner = np.repeat(np.arange(n), np.diff(ads["gofs"]))
+    dcnt[ads["ghop"], owner] = ads["gcnt"]
+    src = np.repeat(np.arange(n), deg)
+    out = []
+    for h in range(1, H + 1):
+        prev = dcnt[h - 1]
+        in_front = prev[cols] > 0
+        E = int(in_front.sum())
+        A = int(np.unique(src[in_front]).size)
+        SD = int((deg * prev).sum())
+        out.append(dict(edge_merges=E, merging=A, delta_sum=SD, new_entries=int(dcnt[h].sum())))
+    return out
+
+
+@pytest.mark.parametrize("name", ["er10k", "rmat12"])
+def test_hop_model_terms_match_the_oracle_ads(name):
+    if name == "er10k":
+        w = flsynth.config("er10k")
+    else:
+        rowp, cols = flsynth.rmat(12, 16, 45)
+        n = len(rowp) - 1
+        w = flsynth.from_csr("rmat12", rowp, cols, 16, 1, np.full(n, 30.0), np.ones(n, np.uint8))
+    og = oracle.Graph(w.rowp, w.cols)
+    og.build_sketches(w.k, w.seed)
+    want = _model_from_ads(w.rowp, w.cols, og.ads(ranks=False), og.hops)
+    g = fl.Graph(w.rowp, w.cols)
+    g.build_sketches(w.k, w.seed)
+    got = g.hop_model()
+    assert len(got) == len(want) == og.hops + 1
+    for h, (a, b) in enumerate(zip(got, want)):
+        for key in ("edge_merges", "merging", "delta_sum", "new_entries"):
+            assert a[key] == b[key], (h + 1, key, a[key], b[key])
+        assert a["delta_read"] >= 0
+    assert sum(m["edge_merges"] for m in got) == og.edge_merges
+    g.close()
+    og.close()
