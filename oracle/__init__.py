@@ -98,6 +98,13 @@ def _load():
             lib.orc_fl_local_search.argtypes = [vp, vp, vp, i64, vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)]
             lib.orc_fl_cost.restype = dbl
             lib.orc_fl_cost.argtypes = [vp, vp, vp, vp]
+            lib.orc_eps_gamma.restype = dbl
+            lib.orc_eps_gamma.argtypes = [vp, vp, vp]
+            lib.orc_eps_open.restype = ctypes.c_int
+            lib.orc_eps_open.argtypes = [vp, dbl, vp, vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(dbl),
+                                         ctypes.POINTER(dbl), ctypes.POINTER(i64)]
+            lib.orc_eps_select.restype = ctypes.c_int
+            lib.orc_eps_select.argtypes = [vp, dbl, dbl, vp, vp, u64, vp, ctypes.POINTER(i64)]
             lib.orc_objective.restype = ctypes.c_int
             lib.orc_objective.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(dbl),
                                           ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -331,6 +338,42 @@ class Graph:
             raise RuntimeError(f"orc_check_open_facilities rc={rc}")
         return rc == 1, int(bad.value)
 
+    # -- the opening phase with epsilon > 0 (Algorithms 3-6, Eq. 2/3) ------
+    def eps_gamma(self, cost, client) -> float:
+        """gamma = max over clients reaching a facility of min_f (c(f) + d(c,f))."""
+        c = np.ascontiguousarray(cost, np.float64)
+        m = np.ascontiguousarray(client, np.uint8)
+        return float(self._lib.orc_eps_gamma(self._h, _p(c), _p(m)))
+
+    def eps_open(self, eps: float, cost, client, mode: int = 0) -> dict:
+        """Facility opening and client freezing (Algorithms 3-5): per vertex
+        the iteration at which it opened (fac_iter) or froze (cli_iter), -1
+        for never; q(f) at opening (or at the end); alpha_0, gamma and the
+        iterations run.  mode 1 accumulates q by Eq. 2/3 literally."""
+        c = np.ascontiguousarray(cost, np.float64)
+        m = np.ascontiguousarray(client, np.uint8)
+        fi = np.zeros(self.n, np.int32)
+        ci = np.zeros(self.n, np.int32)
+        q = np.zeros(self.n, np.float64)
+        a0, gm, it = dbl(0), dbl(0), i64(0)
+        rc = self._lib.orc_eps_open(self._h, float(eps), _p(c), _p(m), int(mode), _p(fi), _p(ci), _p(q),
+                                    ctypes.byref(a0), ctypes.byref(gm), ctypes.byref(it))
+        if rc != 0:
+            raise RuntimeError(f"orc_eps_open rc={rc}")
+        return dict(fac_iter=fi, cli_iter=ci, q=q, alpha0=a0.value, gamma=gm.value, iterations=it.value)
+
+    def eps_select(self, eps: float, alpha0: float, fac_iter, cli_iter, seed: int):
+        """Algorithm 6: lexicographically-first MIS under pi of H-bar."""
+        fi = np.ascontiguousarray(fac_iter, np.int32)
+        ci = np.ascontiguousarray(cli_iter, np.int32)
+        op = np.zeros(self.n, np.uint8)
+        no = i64(0)
+        rc = self._lib.orc_eps_select(self._h, float(eps), float(alpha0), _p(fi), _p(ci), seed, _p(op),
+                                      ctypes.byref(no))
+        if rc != 0:
+            raise RuntimeError(f"orc_eps_select rc={rc}")
+        return op, int(no.value)
+
     # -- assignment + objective (Section 3.1) ----------------------------
     def assign(self, open_: np.ndarray):
         op = np.ascontiguousarray(open_, np.uint8)
@@ -380,3 +423,16 @@ def solve(rowp, cols, k, seed, cost, client) -> dict:
                ads=g.ads(), radii=r, open=op, n_open=nopen, assign=a, dist=d,
                objective=obj, dist_sum=ds, n_unserved=un)
     return out
+
+
+def solve_eps(rowp, cols, k, seed, eps, cost, client) -> dict:
+    """The epsilon > 0 path on the CPU: sketches, opening phase, Algorithm 6
+    selection, assignment, objective."""
+    g = Graph(rowp, cols)
+    g.build_sketches(k, seed)
+    o = g.eps_open(eps, cost, client)
+    op, nopen = g.eps_select(eps, o["alpha0"], o["fac_iter"], o["cli_iter"], seed)
+    a, d = g.assign(op)
+    obj, ds, un = objective(op, cost, client, d)
+    return dict(graph=g, opening=o, open=op, n_open=nopen, assign=a, dist=d, objective=obj, dist_sum=ds,
+                n_unserved=un)

@@ -169,3 +169,102 @@ def nearest_assignment(D, open_set):
         if best is not None:
             d[v] = best
     return a, d
+
+
+# ---------------------------------------------------------------- epsilon > 0
+# The opening phase of Algorithms 3-5 and the selection of Algorithm 6 on an
+# all-pairs distance table (exact client counts instead of ADS estimates),
+# written from the paper's text with the readings listed in the oracle:
+# alpha_0 = gamma (1 + eps) / m^2, alpha_j = alpha_{j-1} (1 + eps); a client
+# at distance delta counts in the shell of the smallest grid value >= delta;
+# q(f) sums (1 + eps) alpha(c) - d_c over clients whose shell value d_c is at
+# most alpha(c); facilities open before clients freeze, within one iteration.
+
+def eps_gamma(D, cost, client) -> float:
+    """max over clients with a reachable facility of min_f (c(f) + d(c, f)); -1 if none."""
+    n = D.shape[0]
+    best = -1.0
+    for c in range(n):
+        if not client[c]:
+            continue
+        vals = [cost[f] + float(D[c, f]) for f in range(n) if np.isfinite(cost[f]) and D[c, f] >= 0]
+        if vals:
+            best = max(best, min(vals))
+    return best
+
+
+def eps_opening(D, cost, client, eps):
+    n = D.shape[0]
+    onepe = 1.0 + eps
+    fac = [f for f in range(n) if np.isfinite(cost[f])]
+    cli = [c for c in range(n) if client[c]]
+    fac_iter = np.full(n, -1, np.int64)
+    cli_iter = np.full(n, -1, np.int64)
+    q = np.zeros(n)
+    if not fac or not cli:
+        return dict(fac_iter=fac_iter, cli_iter=cli_iter, q=q, alpha0=0.0, iterations=0)
+    gamma = eps_gamma(D, cost, client)
+    if gamma < 0:
+        return dict(fac_iter=fac_iter, cli_iter=cli_iter, q=q, alpha0=0.0, iterations=0)
+    m = float(len(fac)) * float(len(cli))
+    alpha0 = (gamma * onepe) / (m * m)
+    grid = [alpha0]
+
+    def alpha(j):
+        while len(grid) <= j:
+            grid.append(grid[-1] * onepe)
+        return grid[j]
+
+    def shell(delta):
+        j = 0
+        while alpha(j) < delta:
+            j += 1
+        return j
+
+    reach = [c for c in cli if any(D[c, f] >= 0 for f in fac)]
+    unfrozen = set(reach)
+    unopened = set(fac)
+    j = 0
+    while unopened and unfrozen:
+        j += 1
+        new = []
+        for f in sorted(unopened):
+            total = 0.0
+            for c in cli:
+                if D[f, c] < 0:
+                    continue
+                jc = cli_iter[c] if cli_iter[c] >= 0 else j
+                sc = shell(D[f, c])
+                if sc <= jc:
+                    total += onepe * alpha(jc) - alpha(sc)
+            q[f] = total
+            if total >= cost[f]:
+                new.append(f)
+        for f in new:
+            fac_iter[f] = j
+            unopened.discard(f)
+        opened = [f for f in range(n) if fac_iter[f] >= 0]
+        for c in sorted(unfrozen):
+            d = min((D[c, f] for f in opened if D[c, f] >= 0), default=-1)
+            if d >= 0 and float(d) <= onepe * alpha(j):
+                cli_iter[c] = j
+                unfrozen.discard(c)
+    return dict(fac_iter=fac_iter, cli_iter=cli_iter, q=q, alpha0=alpha0, iterations=j)
+
+
+def eps_hbar(D, eps, alpha0, fac_iter, cli_iter):
+    """H-bar of Algorithm 6: open facilities f_a, f_b conflict iff a client
+    c with alpha(c) = alpha(f_a) = alpha(f_b) is within (1 + eps) alpha(c)
+    of both."""
+    n = D.shape[0]
+    onepe = 1.0 + eps
+    grid = [alpha0]
+    for _ in range(int(max(fac_iter.max(), 0))):
+        grid.append(grid[-1] * onepe)
+    opened = [f for f in range(n) if fac_iter[f] >= 0]
+    wit = {}
+    for f in opened:
+        j = int(fac_iter[f])
+        wit[f] = {c for c in range(n) if cli_iter[c] == j and 0 <= D[f, c] and float(D[f, c]) <= onepe * grid[j]}
+    adj = {f: {g for g in opened if g != f and wit[f] & wit[g]} for f in opened}
+    return opened, adj
