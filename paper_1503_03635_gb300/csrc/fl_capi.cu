@@ -36,7 +36,8 @@ void destroy_graph(fl_graph* g) {
                     &g->S, &g->Scnt, &g->D[0], &g->D[1], &g->Dcnt[0], &g->Dcnt[1], &g->frontier[0],
                     &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent, &g->stg_grp, &g->gofs, &g->eofs,
                     &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub, &g->ctr, &g->scratch,
-                    &g->relax_aux, &g->U, &g->DM[0], &g->DM[1], &g->PM, &g->seg_flag, &g->vbase, &g->vpart, &g->rid,
+                    &g->relax_aux, &g->U, &g->DM[0], &g->DM[1], &g->PM, &g->seg_flag, &g->PH, &g->F[0], &g->F[1], &g->H[0],
+                    &g->H[1], &g->W, &g->fbm, &g->URid, &g->vbase, &g->vpart, &g->rid,
                     &g->inv, &g->xbits, &g->xaux, &g->xio};
     for (DBuf* b : bufs) dfree_idle(*b);
     for (cudaEvent_t e : g->prof.ev) cudaEventDestroy(e);

@@ -401,9 +401,15 @@ struct fl_graph {
     int64_t n_parts = 0;           // 0: not a union
     fl::DBuf U;                    // uint64[kUW]: the kUW smallest ranks, ascending (kEmpty padded)
     uint64_t ulim = 0;             // largest entry of U
-    fl::DBuf DM[2];                // uint64[n*kUWords]: hop delta masks over U
+    fl::DBuf DM[2];                // uint64[kUSlices][n][4]: hop delta masks over U, slice-major
     fl::DBuf PM;                   // uint64[n_seg*kUWords]: partial masks of hub segments (scratch)
     fl::DBuf seg_flag;             // uint8[n_seg]: the segment had a neighbour that gained entries (scratch)
+    fl::DBuf PH;                   // uint64[n_seg]: OR of the segment's neighbours' delta heads (scratch)
+    fl::DBuf F[2], H[2];           // uint64[n]: smallest new rank of the hop (kEmpty: none), delta bits over U[0..63]
+    fl::DBuf W;                    // uint64[n]: own sketch's mask over U[0..63] of head vertices, else 0
+    fl::DBuf fbm;                  // uint32[n/32+1]: frontier bitmap of the previous hop
+    fl::DBuf URid;                 // int32[kUW]: rank id of the vertex of each entry of U
+    uint64_t hlim = 0;             // U[min(63, |U| - 1)]
     // sketches
     int k = 0;
     uint64_t seed = 0;

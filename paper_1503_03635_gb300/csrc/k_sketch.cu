@@ -156,28 +156,6 @@ __device__ __forceinline__ Mask4 slice_mask(const Grp<G>& g, int idx, int q) {
     return m;
 }
 
-// Slice q of the OR of the delta masks of the neighbours in [e0, e1) that
-// gained entries at the previous hop (lane-parallel, two loads in flight per
-// lane, then reduced over the group).
-template <int G>
-__device__ __forceinline__ Mask4 gather_masks(const Grp<G>& g, const int32_t* __restrict__ cols, int64_t e0,
-                                              int64_t e1, const uint8_t* __restrict__ Dcp,
-                                              const uint64_t* __restrict__ DMp, int q, unsigned long long& cand) {
-    Mask4 acc;
-    for (int64_t e = e0 + g.l; e < e1; e += 2 * G) {
-        const bool in1 = e + G < e1;
-        const int32_t u0 = __ldg(&cols[e]);
-        const int32_t u1 = in1 ? __ldg(&cols[e + G]) : 0;
-        const bool c0 = __ldg(&Dcp[u0]) > 0;
-        const bool c1 = in1 && __ldg(&Dcp[u1]) > 0;
-        if (c0) acc.load(DMp + (int64_t)u0 * kUWords + q * 4);
-        if (c1) acc.load(DMp + (int64_t)u1 * kUWords + q * 4);
-        cand += (c0 ? 4ULL : 0ULL) + (c1 ? 4ULL : 0ULL);
-    }
-    grp_or(g, acc);
-    return acc;
-}
-
 // Saturated merge, slice by slice from the smallest ranks: first = the OR of
 // the candidates' slice 0, src(q) gives it for q >= 1; idx is the lane's old
 // entry's U position.  Lanes j < k receive the new sketch in sk_new; returns
@@ -203,11 +181,6 @@ __device__ __forceinline__ bool merge_slices(const Grp<G>& g, int k, const uint6
     return changed || own_seen < k;
 }
 
-__device__ __forceinline__ void load_u(uint64_t* sU, const uint64_t* __restrict__ U) {
-    for (int i = threadIdx.x; i < kUW; i += blockDim.x) sU[i] = U[i];
-    __syncthreads();
-}
-
 // Per-group hop counters in shared memory, one slot per group, updated by
 // the group's lane 0 without atomics and flushed once at the end of a kernel
 // (the hop kernels run at the register limit; counters in registers cost
@@ -231,6 +204,142 @@ __device__ __forceinline__ void hop_ctr_init(const Grp<G>& g) {
 template <int G>
 __device__ __forceinline__ void hop_ctr_add(int field, unsigned x) {
     s_hop_ctr[threadIdx.x / G][field] += x;
+}
+
+// Per-hop inputs and outputs of the merge kernels (p = previous hop's
+// buffers, read-only during a hop; c = this hop's).  Besides each vertex's
+// delta list D and delta mask DM, two dense per-vertex words make the
+// per-edge reads small and cache-friendly:
+//   F[u]  the smallest rank u gained at the hop (kEmpty: none), the filter of
+//         the list and slice merges: a neighbour whose F is not below the
+//         vertex's k-th rank cannot change its sketch;
+//   H[u]  the bits of u's delta mask over U[0..63] (word 0 of DM);
+// and W[v], the mask over U[0..63] of v's own sketch once the sketch is full
+// and its k-th rank is at most U[63] ("head" vertices; 0 otherwise).  A head
+// vertex takes S_h(v) = lowest k bits of (W[v] | OR_u H[u]): every candidate
+// that can still enter is among U[0..63], so this is the list merge's result.
+// Frontier membership for the counters comes from a bitmap of the previous
+// hop's frontier (n/8 bytes, cache-resident).
+struct HopIO {
+    const int64_t* __restrict__ rowp;
+    const int32_t* __restrict__ cols;
+    int k;
+    int hop;
+    uint64_t seed;
+    uint64_t* __restrict__ S;
+    uint8_t* __restrict__ Scnt;
+    const uint64_t* __restrict__ Dp;
+    const uint8_t* __restrict__ Dcp;
+    uint64_t* __restrict__ Dc;
+    uint8_t* __restrict__ Dcc;
+    const uint64_t* __restrict__ Fp;
+    uint64_t* __restrict__ Fc;
+    const uint64_t* __restrict__ Hp;
+    uint64_t* __restrict__ Hc;
+    uint64_t* __restrict__ W;
+    const uint32_t* __restrict__ bm;
+    const uint64_t* __restrict__ DMp;  // slice-major: slice q of vertex v at [(q * n + v) * 4]
+    uint64_t* __restrict__ DMc;
+    int64_t n;
+    int32_t* __restrict__ vg;
+    int32_t* __restrict__ ve;
+    int32_t* __restrict__ stg_ent;
+    StgGroup* __restrict__ stg_grp;
+    const uint64_t* __restrict__ U;
+    const int32_t* __restrict__ URid;  // rank id of the vertex of each U rank
+    uint64_t ulim;                     // U's largest entry
+    uint64_t hlim;                     // U[min(63, |U| - 1)]: the head's largest rank
+    IdMap ids;
+    Counters* ctr;
+};
+
+__device__ __forceinline__ bool in_bitmap(const uint32_t* __restrict__ bm, int32_t u) {
+    return (__ldg(&bm[u >> 5]) >> (u & 31)) & 1u;
+}
+
+// Position of the n-th (0-based) set bit of a 64-bit word (n < popcount).
+__device__ __forceinline__ int nth_bit64(uint64_t x, int n) {
+    const unsigned lo = (unsigned)x;
+    const int c = __popc(lo);
+    return n < c ? nth_set_bit(lo, n) : 32 + nth_set_bit((unsigned)(x >> 32), n - c);
+}
+
+// The lowest k set bits of x.
+__device__ __forceinline__ uint64_t lowest_k64(uint64_t x, int k) {
+    return __popcll(x) <= k ? x : keep_lowest64(x, k);
+}
+
+template <int G>
+__device__ __forceinline__ uint64_t grp_or64(const Grp<G>& g, uint64_t x) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) x |= g.shfl_xor(x, o);
+    return x;
+}
+
+// Index of word w of vertex v's delta mask in the slice-major layout (each
+// 256-bit slice of all vertices is one dense array, so that the hot slices
+// of high-degree vertices share cache lines).
+__device__ __forceinline__ int64_t dm_word(int64_t n, int64_t v, int w) {
+    return ((int64_t)(w >> 2) * n + v) * 4 + (w & 3);
+}
+
+// Slice q of the OR of the delta masks of the neighbours in [e0, e1) that
+// gained entries at the previous hop (frontier bitmap; lane-parallel, four
+// columns per lane in flight, then reduced over the group); `front` tells
+// whether there is such a neighbour.
+template <int G>
+__device__ __forceinline__ Mask4 gather_masks(const Grp<G>& g, const HopIO& io, int64_t e0, int64_t e1, int q,
+                                              bool& front, unsigned long long& cand) {
+    Mask4 acc;
+    bool f = false;
+    const uint64_t* __restrict__ slice = io.DMp + (int64_t)q * io.n * 4;
+    for (int64_t e = e0 + g.l; e < e1; e += 4 * G) {
+        int32_t u[4];
+        bool in[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) u[j] = e + j * G < e1 ? __ldcs(&io.cols[e + j * G]) : -1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) in[j] = u[j] >= 0 && in_bitmap(io.bm, u[j]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (in[j]) {
+                acc.load(slice + (int64_t)u[j] * 4);
+                f = true;
+                cand += 4ULL;
+            }
+        }
+    }
+    grp_or(g, acc);
+    front = g.ballot(f) != 0;
+    return acc;
+}
+
+// OR of the delta heads H[u] of the neighbours in [e0, e1) that are in the
+// previous hop's frontier (four columns per lane in flight); `front` tells
+// whether there is such a neighbour.
+template <int G>
+__device__ __forceinline__ uint64_t gather_heads(const Grp<G>& g, const HopIO& io, int64_t e0, int64_t e1,
+                                                 bool& front, unsigned long long& cand) {
+    uint64_t acc = 0;
+    bool f = false;
+    for (int64_t e = e0 + g.l; e < e1; e += 4 * G) {
+        int32_t u[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) u[j] = e + j * G < e1 ? __ldcs(&io.cols[e + j * G]) : -1;
+        bool in[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) in[j] = u[j] >= 0 && in_bitmap(io.bm, u[j]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (in[j]) {
+                acc |= __ldg(&io.Hp[u[j]]);
+                f = true;
+                cand += 1ULL;
+            }
+        }
+    }
+    front = g.ballot(f) != 0;
+    return grp_or64(g, acc);
 }
 
 // ------------------------------------------------------------------ hop 0
@@ -341,31 +450,32 @@ __device__ __forceinline__ void absorb(const Grp<G>& g, int k, uint64_t x, Sketc
 // Absorb the candidates of CSR entries [e0, e1): at hop 1 the neighbours' own
 // ranks (recomputed from their ids), later the entries each neighbour gained
 // at the previous hop.  Lane j of the group owns neighbour j of a chunk of G
-// neighbours and loads the first (smallest) entry of its list: G independent
-// loads that also filter whole lists.  Each neighbour whose smallest entry is
-// below the filter then has its list loaded across the group; the entries
-// below the filter form an ascending prefix, absorbed by 1-2 insertions or one
-// bitonic merge.
+// neighbours and loads its smallest new rank F[u] (independent loads into a
+// dense array that also filter whole lists).  Each neighbour whose smallest
+// new rank is below the filter then has its list loaded across the group;
+// the entries below the filter form an ascending prefix, absorbed by 1-2
+// insertions or one bitonic merge.  `front`: some neighbour gained entries.
 template <int G>
-__device__ __forceinline__ void gather_range(const Grp<G>& g, int k, int hop, uint64_t seed,
-                                             const int32_t* __restrict__ cols, int64_t e0, int64_t e1,
-                                             const uint8_t* __restrict__ Dcp, const uint64_t* __restrict__ Dp,
-                                             IdMap ids, Sketch<G>& s,
-                                             unsigned long long& cand) {
+__device__ __forceinline__ void gather_range(const Grp<G>& g, const HopIO& io, int64_t e0, int64_t e1,
+                                             Sketch<G>& s, bool& front, unsigned long long& cand) {
+    const int k = io.k;
+    bool fr = false;
     // the next chunk's columns are loaded while this chunk merges
-    int32_t u_next = e0 + g.l < e1 ? __ldg(&cols[e0 + g.l]) : 0;
+    int32_t u_next = e0 + g.l < e1 ? __ldcs(&io.cols[e0 + g.l]) : 0;
     for (int64_t cb = e0; cb < e1; cb += G) {
         const int64_t e = cb + g.l;
         const bool in = e < e1;
         const int32_t u = u_next;
-        u_next = e + G < e1 ? __ldg(&cols[e + G]) : 0;
-        if (hop == 1) {
-            absorb(g, k, in ? vertex_rank(seed, rank_id(ids, u)) : kEmpty, s);
+        u_next = e + G < e1 ? __ldcs(&io.cols[e + G]) : 0;
+        if (io.hop == 1) {
+            absorb(g, k, in ? vertex_rank(io.seed, rank_id(io.ids, u)) : kEmpty, s);
             continue;
         }
-        const int c = in ? (int)__ldg(&Dcp[u]) : 0;
-        const uint64_t first = c > 0 ? __ldg(&Dp[(int64_t)u * k]) : kEmpty;
-        cand += c > 0 ? 1ULL : 0ULL;
+        const uint64_t first = in ? __ldg(&io.Fp[u]) : kEmpty;
+        fr |= first != kEmpty;
+        cand += first != kEmpty ? 1ULL : 0ULL;
+        // list lengths of the neighbours that pass the filter, loaded together
+        const int c = first < s.tau ? (int)__ldg(&io.Dcp[u]) : 0;
         unsigned live = g.ballot(first < s.tau);
         while (live) {
             const int j = __ffs(live) - 1;
@@ -378,7 +488,7 @@ __device__ __forceinline__ void gather_range(const Grp<G>& g, int k, int hop, ui
                 continue;
             }
             const int uj = g.shfl(u, j);
-            uint64_t x = (g.l > 0 && g.l < cj) ? __ldg(&Dp[(int64_t)uj * k + g.l]) : kEmpty;
+            uint64_t x = (g.l > 0 && g.l < cj) ? __ldg(&io.Dp[(int64_t)uj * k + g.l]) : kEmpty;
             cand += (g.l > 0 && g.l < cj) ? 1ULL : 0ULL;
             if (g.l == 0) x = fj;
             const unsigned pm = g.ballot(x < s.tau);  // an ascending prefix of the list
@@ -393,69 +503,113 @@ __device__ __forceinline__ void gather_range(const Grp<G>& g, int k, int hop, ui
             }
         }
     }
+    front = io.hop == 1 || g.ballot(fr) != 0;
 }
 
-// Write the results of vertex v after its merge: new sketch, the entries it
-// gained (for the next hop), their mask and its staged ADS group in work slot
-// `slot`.  Returns the number of entries gained (0: the sketch is unchanged).
+// Record a changed vertex's ADS group in staging slot `slot` and count it
+// (lane 0 of the group).
 template <int G>
-__device__ __forceinline__ int finish_vertex(const Grp<G>& g, int k, uint64_t seed, int hop, int32_t v,
-                                              int64_t deg, uint64_t old, const Sketch<G>& s, int64_t slot,
-                                              uint64_t* __restrict__ S, uint8_t* __restrict__ Scnt,
-                                              uint64_t* __restrict__ Dc, uint8_t* __restrict__ Dcc,
-                                              int32_t* __restrict__ vg, int32_t* __restrict__ ve,
-                                              int32_t* __restrict__ stg_ent, StgGroup* __restrict__ stg_grp,
-                                              const uint64_t* sU, uint64_t ulim, uint64_t* __restrict__ DMc,
-                                              IdMap ids, HopCounters& hc) {
+__device__ __forceinline__ void stage_group(const HopIO& io, int32_t v, int64_t deg, int64_t slot, int dcnt,
+                                            int counted, double wt) {
+    StgGroup gr;
+    gr.wt = wt;
+    gr.v = v;
+    gr.gidx = io.vg[v];
+    gr.eidx = io.ve[v];
+    gr.info = pack_info(io.hop, dcnt, counted);
+    io.vg[v] = gr.gidx + 1;
+    io.ve[v] = gr.eidx + dcnt;
+    io.stg_grp[slot] = gr;
+    hop_ctr_add<G>(kCFront, 1u);
+    hop_ctr_add<G>(kCNew, (unsigned)dcnt);
+    if (deg <= kHubDeg) {
+        hop_ctr_add<G>(kCMerges, (unsigned)deg);
+        hop_ctr_add<G>(kCDelta, (unsigned)(deg * dcnt));
+    }
+}
+
+// HIP weight of a group whose ball holds cnt ranks with k-th smallest kth:
+// 1 while the ball has fewer than k vertices, else 1 / Pr[rank < k-th] =
+// 2^64 / kth (one IEEE division).
+__device__ __forceinline__ double hip_weight(int cnt, int k, uint64_t kth) {
+    return cnt < k ? 1.0 : __ddiv_rn(18446744073709551616.0, __ull2double_rn(kth));
+}
+
+// Write the results of vertex v after a list or slice merge: new sketch, the
+// entries it gained (list, mask, head word, smallest one, for the next hop),
+// its own head mask once the sketch is a head sketch, and its staged ADS
+// group in work slot `slot`.  Returns the number of entries gained (0: the
+// sketch is unchanged).
+template <int G>
+__device__ __forceinline__ int finish_vertex(const Grp<G>& g, const HopIO& io, int32_t v, int64_t deg, uint64_t old,
+                                             const Sketch<G>& s, int64_t slot, const uint64_t* sU) {
+    const int k = io.k;
     const bool valid = g.l < k && s.sk != kEmpty;
     const bool was_there = grp_member(g, old, s.sk);
     const unsigned newm = g.ballot(valid && !was_there);
     const int dcnt = __popc(newm);
     if (dcnt == 0) {
-        if (g.l == 0) stg_grp[slot].info = 0;  // empty slot
+        if (g.l == 0) io.stg_grp[slot].info = 0;  // empty slot
         return 0;
     }
     const int cnt_new = __popc(g.ballot(valid));
-    if (g.l < k) S[(int64_t)v * k + g.l] = s.sk;
+    if (g.l < k) io.S[(int64_t)v * k + g.l] = s.sk;
     const uint64_t dv = grp_compact(g, s.sk, newm, kEmpty);
     if (g.l < dcnt) {
-        Dc[(int64_t)v * k + g.l] = dv;
-        stg_ent[slot * k + g.l] = (int32_t)internal_of(ids, (int64_t)rank_vertex(seed, dv), v);
+        io.Dc[(int64_t)v * k + g.l] = dv;
+        io.stg_ent[slot * k + g.l] = (int32_t)internal_of(io.ids, (int64_t)rank_vertex(io.seed, dv), v);
     }
-    {
-        // delta mask over U: lane w < kUWords builds word w
-        const int di = g.l < dcnt ? u_pos(sU, ulim, dv) : -1;
-        uint64_t word = 0;
-        for (int j = 0; j < dcnt; ++j) {
-            const int ij = g.shfl(di, j);
-            if (ij >= 0 && (ij >> 6) == g.l) word |= 1ULL << (ij & 63);
-        }
-        if (g.l < kUWords) DMc[(int64_t)v * kUWords + g.l] = word;
+    // delta mask over U: lane w < kUWords builds word w
+    const int di = g.l < dcnt ? u_pos(sU, io.ulim, dv) : -1;
+    uint64_t word = 0;
+    for (int j = 0; j < dcnt; ++j) {
+        const int ij = g.shfl(di, j);
+        if (ij >= 0 && (ij >> 6) == g.l) word |= 1ULL << (ij & 63);
     }
+    if (g.l < kUWords) io.DMc[dm_word(io.n, v, g.l)] = word;
     const uint64_t kth = g.shfl(s.sk, k - 1);
+    // a full sketch whose k-th rank is in U's head becomes a head vertex
+    if (cnt_new == k && kth <= io.hlim) {
+        const int p = g.l < k ? u_pos(sU, io.ulim, s.sk) : -1;
+        const uint64_t own = grp_or64(g, p >= 0 ? 1ULL << p : 0ULL);
+        if (g.l == 0) io.W[v] = own;
+    }
     if (g.l == 0) {
+        io.Fc[v] = dv;    // lane 0 holds the smallest new rank
+        io.Hc[v] = word;  // lane 0 built word 0
+        io.Scnt[v] = (uint8_t)cnt_new;
+        io.Dcc[v] = (uint8_t)dcnt;
         const int counted = cnt_new < k ? dcnt : __popc(newm & ((1u << (k - 1)) - 1u));
-        Scnt[v] = (uint8_t)cnt_new;
-        Dcc[v] = (uint8_t)dcnt;
-        StgGroup gr;
-        // HIP weight: 1 while the ball has fewer than k vertices, else
-        // 1 / Pr[rank < k-th] = 2^64 / S_h(v)[k-1] (one IEEE division)
-        gr.wt = cnt_new < k ? 1.0 : __ddiv_rn(18446744073709551616.0, __ull2double_rn(kth));
-        gr.v = v;
-        gr.gidx = vg[v];
-        gr.eidx = ve[v];
-        gr.info = pack_info(hop, dcnt, counted);
-        vg[v] = gr.gidx + 1;
-        ve[v] = gr.eidx + dcnt;
-        stg_grp[slot] = gr;
-        hop_ctr_add<G>(kCFront, 1u);
-        hop_ctr_add<G>(kCNew, (unsigned)dcnt);
-        if (deg <= kHubDeg) {
-            hop_ctr_add<G>(kCMerges, (unsigned)deg);
-            hop_ctr_add<G>(kCDelta, (unsigned)(deg * dcnt));
-        }
+        stage_group<G>(io, v, deg, slot, dcnt, counted, hip_weight(cnt_new, k, kth));
     }
     return dcnt;
+}
+
+// Write the results of head vertex v whose new sketch is the mask nw over
+// U[0..63] (k bits) with gained bits delta (nonzero); the same outputs as
+// finish_vertex.
+template <int G>
+__device__ __forceinline__ void finish_head(const Grp<G>& g, const HopIO& io, int32_t v, int64_t deg, uint64_t nw,
+                                            uint64_t delta, int64_t slot, const uint64_t* sU,
+                                            const int32_t* sURid) {
+    const int k = io.k;
+    const int dcnt = __popcll(delta);
+    if (g.l < k) io.S[(int64_t)v * k + g.l] = sU[nth_bit64(nw, g.l)];
+    if (g.l < dcnt) {
+        const int p = nth_bit64(delta, g.l);
+        io.Dc[(int64_t)v * k + g.l] = sU[p];
+        io.stg_ent[slot * k + g.l] = (int32_t)internal_of(io.ids, (int64_t)sURid[p], v);
+    }
+    if (g.l < kUWords) io.DMc[dm_word(io.n, v, g.l)] = g.l == 0 ? delta : 0ULL;
+    if (g.l == 0) {
+        const int top = 63 - __clzll(nw);  // the k-th smallest rank's position
+        io.W[v] = nw;
+        io.Fc[v] = sU[__ffsll(delta) - 1];
+        io.Hc[v] = delta;
+        io.Dcc[v] = (uint8_t)dcnt;
+        const int counted = dcnt - (int)((delta >> top) & 1ULL);
+        stage_group<G>(io, v, deg, slot, dcnt, counted, hip_weight(k, k, sU[top]));
+    }
 }
 
 template <int G>
@@ -474,85 +628,106 @@ __device__ __forceinline__ void flush_counters(const Grp<G>& g, HopCounters hc, 
     }
 }
 
+// U and the rank ids of its entries, staged in shared memory by every hop kernel.
+__device__ __forceinline__ void load_tables(uint64_t* sU, int32_t* sURid, const HopIO& io) {
+    for (int i = threadIdx.x; i < kUW; i += blockDim.x) {
+        sU[i] = io.U[i];
+        sURid[i] = io.URid[i];
+    }
+    __syncthreads();
+}
+
 // ------------------------------------------------------------------ hop kernels
 
-// Non-hub vertices: S_h(v) = bottom-k(S_{h-1}(v) U union_{u in N(v)} D_{h-1}(u)).
+// Non-hub vertices: S_h(v) = bottom-k(S_{h-1}(v) U union_{u in N(v)} D_{h-1}(u)),
+// by the head merge (head vertices), the mask merge (other saturated
+// sketches) or the list merge.
 template <int G>
-__global__ void __launch_bounds__(256) k_hop_vertices(
-    const int32_t* __restrict__ list, int64_t n_list, const int64_t* __restrict__ rowp,
-    const int32_t* __restrict__ cols, int k, uint64_t seed, int hop, uint64_t* __restrict__ S,
-    uint8_t* __restrict__ Scnt, const uint64_t* __restrict__ Dp, const uint8_t* __restrict__ Dcp,
-    uint64_t* __restrict__ Dc, uint8_t* __restrict__ Dcc, int32_t* __restrict__ vg, int32_t* __restrict__ ve,
-    int32_t* __restrict__ stg_ent, StgGroup* __restrict__ stg_grp, const uint64_t* __restrict__ U, uint64_t ulim,
-    const uint64_t* __restrict__ DMp, uint64_t* __restrict__ DMc, IdMap ids,
-    Counters* ctr) {
+__global__ void __launch_bounds__(256, 4) k_hop_vertices(const int32_t* __restrict__ list, int64_t n_list, HopIO io) {
     __shared__ uint64_t sU[kUW];
-    load_u(sU, U);
+    __shared__ int32_t sURid[kUW];
+    load_tables(sU, sURid, io);
     const Grp<G> g;
+    const int k = io.k;
     const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
     HopCounters hc;
     hop_ctr_init(g);
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; i < n_list; i += groups) {
         const int32_t v = list[i];
-        const int64_t beg = rowp[v], end = rowp[v + 1];
-        const uint64_t old = g.l < k ? S[(int64_t)v * k + g.l] : kEmpty;
-        Sketch<G> s;
-        s.sk = old;
-        s.cnt = Scnt[v];
-        s.tau_base = kEmpty;
-        s.retau(g, k);
-        const unsigned long long cand0 = hc.cand;
-        const bool sat = hop > 1 && s.cnt == k && s.tau <= ulim;
-        if (sat) {
-            // saturated: mask merge; nothing to do without a neighbour that
-            // gained entries at the previous hop
-            const Mask4 first = gather_masks(g, cols, beg, end, Dcp, DMp, 0, hc.cand);
-            const bool merged = g.ballot(hc.cand != cand0) != 0;  // every lane votes
-            if (g.l == 0 && merged) hop_ctr_add<G>(kCMerging, 1u);
-            if (!merged) {
-                if (g.l == 0) stg_grp[i].info = 0;  // unchanged: empty slot
+        const int64_t beg = io.rowp[v], end = io.rowp[v + 1];
+        const uint64_t wv = io.hop > 1 ? io.W[v] : 0ULL;
+        bool front = false;
+        if (wv != 0) {
+            // head vertex: the head merge
+            const uint64_t acc = gather_heads(g, io, beg, end, front, hc.cand);
+            if (g.l == 0 && front) hop_ctr_add<G>(kCMerging, 1u);
+            const uint64_t nw = lowest_k64(wv | acc, k);
+            const uint64_t delta = nw & ~wv;
+            if (delta == 0) {
+                if (g.l == 0) io.stg_grp[i].info = 0;  // unchanged: empty slot
                 continue;
             }
-            const int idx = g.l < k ? u_pos(sU, ulim, old) : -1;
+            finish_head(g, io, v, end - beg, nw, delta, i, sU, sURid);
+            continue;
+        }
+        const uint64_t old = g.l < k ? io.S[(int64_t)v * k + g.l] : kEmpty;
+        Sketch<G> s;
+        s.sk = old;
+        s.cnt = io.Scnt[v];
+        s.tau_base = kEmpty;
+        s.retau(g, k);
+        const bool sat = io.hop > 1 && s.cnt == k && s.tau <= io.ulim;
+        if (sat) {
+            // saturated: mask merge over the neighbours whose smallest new
+            // rank is below the k-th rank
+            const Mask4 first = gather_masks(g, io, beg, end, 0, front, hc.cand);
+            if (g.l == 0 && front) hop_ctr_add<G>(kCMerging, 1u);
+            if (!front) {
+                if (g.l == 0) io.stg_grp[i].info = 0;  // unchanged: empty slot
+                continue;
+            }
+            const int idx = g.l < k ? u_pos(sU, io.ulim, old) : -1;
             uint64_t sk_new;
+            bool fq;
             const bool changed = merge_slices(
-                g, k, sU, idx, first, [&](int q) { return gather_masks(g, cols, beg, end, Dcp, DMp, q, hc.cand); },
+                g, k, sU, idx, first, [&](int q) { return gather_masks(g, io, beg, end, q, fq, hc.cand); },
                 sk_new);
             if (!changed) {
-                if (g.l == 0) stg_grp[i].info = 0;  // unchanged: empty slot
+                if (g.l == 0) io.stg_grp[i].info = 0;  // unchanged: empty slot
                 continue;
             }
             s.sk = sk_new;
             s.cnt = k;
         } else {
-            gather_range(g, k, hop, seed, cols, beg, end, Dcp, Dp, ids, s, hc.cand);
-            const bool merged = hop == 1 || g.ballot(hc.cand != cand0) != 0;
-            if (g.l == 0 && merged) hop_ctr_add<G>(kCMerging, 1u);
+            gather_range(g, io, beg, end, s, front, hc.cand);
+            if (g.l == 0 && front) hop_ctr_add<G>(kCMerging, 1u);
         }
-        finish_vertex(g, k, seed, hop, v, end - beg, old, s, i, S, Scnt, Dc, Dcc, vg, ve, stg_ent, stg_grp, sU, ulim,
-                      DMc, ids, hc);
+        finish_vertex(g, io, v, end - beg, old, s, i, sU);
     }
-    flush_counters(g, hc, ctr);
+    flush_counters(g, hc, io.ctr);
 }
 
-// Hub segments: partial bottom-k of the candidates of one segment, filtered by
-// the hub's old k-th rank, written to part[seg * k ..].
+// Hub segments: partial results of one segment, written per segment -- the
+// OR of its neighbours' delta heads (head hubs), the slices of their delta
+// masks up to the hub's k-th rank (other saturated hubs), or the bottom-k of
+// its candidates below the hub's old k-th rank (list hubs).
 template <int G>
-__global__ void __launch_bounds__(256) k_hop_hub_segments(
-    const int32_t* __restrict__ hubs, const int64_t* __restrict__ hub_seg, const int32_t* __restrict__ seg_hub,
-    int64_t n_seg, const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols, int k, uint64_t seed,
-    int hop, const uint64_t* __restrict__ S, const uint8_t* __restrict__ Scnt, const uint64_t* __restrict__ Dp,
-    const uint8_t* __restrict__ Dcp, uint64_t* __restrict__ part, const uint64_t* __restrict__ U, uint64_t ulim,
-    const uint64_t* __restrict__ DMp, uint64_t* __restrict__ PM, uint8_t* __restrict__ seg_flag,
-    const uint32_t* __restrict__ hub_stamp, uint32_t sparse_hop, IdMap ids, Counters* ctr) {
+__global__ void __launch_bounds__(256) k_hop_hub_segments(const int32_t* __restrict__ hubs,
+                                                          const int64_t* __restrict__ hub_seg,
+                                                          const int32_t* __restrict__ seg_hub, int64_t n_seg,
+                                                          uint64_t* __restrict__ part, uint64_t* __restrict__ PM,
+                                                          uint64_t* __restrict__ PH, uint8_t* __restrict__ seg_flag,
+                                                          const uint32_t* __restrict__ hub_stamp, uint32_t sparse_hop,
+                                                          HopIO io) {
     __shared__ uint64_t sU[kUW];
-    load_u(sU, U);
+    __shared__ int32_t sURid[kUW];
+    load_tables(sU, sURid, io);
     const Grp<G> g;
+    const int k = io.k;
     const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
     HopCounters hc;
     hop_ctr_init(g);
     for (int64_t sidx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; sidx < n_seg; sidx += groups) {
-        const unsigned long long cand0 = hc.cand;
         const int32_t h = seg_hub[sidx];
         const int32_t v = hubs[h];
         if (sparse_hop && hub_stamp[v] != sparse_hop) {
@@ -560,34 +735,42 @@ __global__ void __launch_bounds__(256) k_hop_hub_segments(
             if (g.l == 0) seg_flag[sidx] = 0;
             continue;
         }
-        const int64_t e0 = rowp[v] + (sidx - hub_seg[h]) * kSeg;
-        const int64_t e1 = min(e0 + (int64_t)kSeg, rowp[v + 1]);
-        const uint64_t kth_old = S[(int64_t)v * k + k - 1];
-        const bool sat = hop > 1 && Scnt[v] == k && kth_old <= ulim;
+        const int64_t e0 = io.rowp[v] + (sidx - hub_seg[h]) * kSeg;
+        const int64_t e1 = min(e0 + (int64_t)kSeg, io.rowp[v + 1]);
+        bool front = false;
+        if (io.hop > 1 && io.W[v] != 0) {
+            const uint64_t acc = gather_heads(g, io, e0, e1, front, hc.cand);
+            if (g.l == 0) {
+                PH[sidx] = acc;
+                seg_flag[sidx] = front ? 1 : 0;
+            }
+            continue;
+        }
+        const uint64_t kth_old = io.S[(int64_t)v * k + k - 1];
+        const bool sat = io.hop > 1 && io.Scnt[v] == k && kth_old <= io.ulim;
         if (sat) {
             // saturated hub: partial masks of the segment, the slices up to
             // the one holding the hub's k-th rank (the merge stops there)
-            const int top = u_pos(sU, ulim, kth_old) >> 8;
+            const int top = u_pos(sU, io.ulim, kth_old) >> 8;
             for (int q = 0; q <= top; ++q) {
-                const Mask4 m = gather_masks(g, cols, e0, e1, Dcp, DMp, q, hc.cand);
+                bool fq;
+                const Mask4 m = gather_masks(g, io, e0, e1, q, fq, hc.cand);
+                if (q == 0) front = fq;
                 if (g.l < 4) PM[sidx * kUWords + q * 4 + g.l] = m.word(g.l);
             }
-            // a neighbour of this segment gained entries at the previous hop
-            const bool merged = g.ballot(hc.cand != cand0) != 0;
-            if (g.l == 0) seg_flag[sidx] = merged ? 1 : 0;
+            if (g.l == 0) seg_flag[sidx] = front ? 1 : 0;
             continue;
         }
         Sketch<G> s;
         s.sk = kEmpty;
         s.cnt = 0;
-        s.tau_base = Scnt[v] == k ? kth_old : kEmpty;
+        s.tau_base = io.Scnt[v] == k ? kth_old : kEmpty;
         s.tau = s.tau_base;
-        gather_range(g, k, hop, seed, cols, e0, e1, Dcp, Dp, ids, s, hc.cand);
+        gather_range(g, io, e0, e1, s, front, hc.cand);
         if (g.l < k) part[sidx * k + g.l] = s.sk;
-        const bool merged = hop == 1 || g.ballot(hc.cand != cand0) != 0;
-        if (g.l == 0) seg_flag[sidx] = merged ? 1 : 0;
+        if (g.l == 0) seg_flag[sidx] = front ? 1 : 0;
     }
-    flush_counters(g, hc, ctr);
+    flush_counters(g, hc, io.ctr);
 }
 
 // Did some segment of hub h have a neighbour that gained entries?
@@ -599,78 +782,87 @@ __device__ __forceinline__ bool hub_merged(const Grp<G>& g, const int64_t* __res
     return g.ballot(any) != 0;
 }
 
-// Hubs: merge the partial lists of all segments into the hub's sketch.
+// Hubs: merge the partial results of all segments into the hub's sketch.
 template <int G>
-__global__ void __launch_bounds__(256) k_hop_hubs(
-    const int32_t* __restrict__ hubs, int64_t n_hubs, const int64_t* __restrict__ hub_seg,
-    const uint64_t* __restrict__ part, const int64_t* __restrict__ rowp, int k, uint64_t seed, int hop,
-    int64_t slot0, uint64_t* __restrict__ S, uint8_t* __restrict__ Scnt, uint64_t* __restrict__ Dc,
-    uint8_t* __restrict__ Dcc, int32_t* __restrict__ vg, int32_t* __restrict__ ve, int32_t* __restrict__ stg_ent,
-    StgGroup* __restrict__ stg_grp, const uint64_t* __restrict__ U, uint64_t ulim, const uint64_t* __restrict__ PM,
-    const uint8_t* __restrict__ seg_flag, const uint32_t* __restrict__ hub_stamp, uint32_t sparse_hop,
-    uint64_t* __restrict__ DMc, IdMap ids, Counters* ctr) {
+__global__ void __launch_bounds__(256) k_hop_hubs(const int32_t* __restrict__ hubs, int64_t n_hubs,
+                                                  const int64_t* __restrict__ hub_seg,
+                                                  const uint64_t* __restrict__ part, const uint64_t* __restrict__ PM,
+                                                  const uint64_t* __restrict__ PH,
+                                                  const uint8_t* __restrict__ seg_flag,
+                                                  const uint32_t* __restrict__ hub_stamp, uint32_t sparse_hop,
+                                                  int64_t slot0, HopIO io) {
     __shared__ uint64_t sU[kUW];
-    load_u(sU, U);
+    __shared__ int32_t sURid[kUW];
+    load_tables(sU, sURid, io);
     const Grp<G> g;
+    const int k = io.k;
     const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
     HopCounters hc;
     hop_ctr_init(g);
     for (int64_t h = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; h < n_hubs; h += groups) {
         const int32_t v = hubs[h];
+        const int64_t slot = slot0 + h;
         if (sparse_hop && hub_stamp[v] != sparse_hop) {
-            if (g.l == 0) stg_grp[slot0 + h].info = 0;  // unchanged: empty slot
+            if (g.l == 0) io.stg_grp[slot].info = 0;  // unchanged: empty slot
             continue;
         }
-        const uint64_t old = g.l < k ? S[(int64_t)v * k + g.l] : kEmpty;
-        Sketch<G> s;
-        s.sk = old;
-        s.cnt = Scnt[v];
-        s.tau_base = kEmpty;
-        s.retau(g, k);
-        if (hop > 1 && s.cnt == k && s.tau <= ulim) {
-            // saturated hub: OR of the segments' partial masks
-            const int idx = g.l < k ? u_pos(sU, ulim, old) : -1;
-            auto part_slice = [&](int q) {
-                Mask4 m;
-                for (int64_t sidx = hub_seg[h] + g.l; sidx < hub_seg[h + 1]; sidx += G)
-                    m.load(PM + sidx * kUWords + q * 4);
-                grp_or(g, m);
-                return m;
-            };
-            uint64_t sk_new;
-            const bool changed = merge_slices(g, k, sU, idx, part_slice(0), part_slice, sk_new);
-            const bool any = hub_merged(g, hub_seg, seg_flag, h);
-            if (g.l == 0 && any) hop_ctr_add<G>(kCMerging, 1u);
-            if (!changed) {
-                if (g.l == 0) stg_grp[slot0 + h].info = 0;  // unchanged: empty slot
-                continue;
-            }
-            s.sk = sk_new;
-            s.cnt = k;
-            const int64_t deg = rowp[v + 1] - rowp[v];
-            const int dc = finish_vertex(g, k, seed, hop, v, deg, old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve, stg_ent,
-                                         stg_grp, sU, ulim, DMc, ids, hc);
-            if (dc && g.l == 0) {
-                atomicAdd(&ctr->merges, (unsigned long long)deg);
-                atomicAdd(&ctr->delta_next, (unsigned long long)(deg * dc));
-            }
-            continue;
-        }
-        for (int64_t sidx = hub_seg[h]; sidx < hub_seg[h + 1]; ++sidx) {
-            const uint64_t x = g.l < k ? part[sidx * k + g.l] : kEmpty;
-            absorb(g, k, x, s);
-        }
+        const int64_t deg = io.rowp[v + 1] - io.rowp[v];
         const bool any = hub_merged(g, hub_seg, seg_flag, h);
         if (g.l == 0 && any) hop_ctr_add<G>(kCMerging, 1u);
-        const int64_t deg = rowp[v + 1] - rowp[v];
-        const int dc = finish_vertex(g, k, seed, hop, v, deg, old, s, slot0 + h, S, Scnt, Dc, Dcc, vg, ve, stg_ent,
-                                     stg_grp, sU, ulim, DMc, ids, hc);
+        const uint64_t wv = io.hop > 1 ? io.W[v] : 0ULL;
+        int dc = 0;
+        if (wv != 0) {
+            uint64_t acc = 0;
+            for (int64_t sidx = hub_seg[h] + g.l; sidx < hub_seg[h + 1]; sidx += G) acc |= PH[sidx];
+            acc = grp_or64(g, acc);
+            const uint64_t nw = lowest_k64(wv | acc, k);
+            const uint64_t delta = nw & ~wv;
+            if (delta != 0) {
+                finish_head(g, io, v, deg, nw, delta, slot, sU, sURid);
+                dc = __popcll(delta);
+            } else if (g.l == 0) {
+                io.stg_grp[slot].info = 0;  // unchanged: empty slot
+            }
+        } else {
+            const uint64_t old = g.l < k ? io.S[(int64_t)v * k + g.l] : kEmpty;
+            Sketch<G> s;
+            s.sk = old;
+            s.cnt = io.Scnt[v];
+            s.tau_base = kEmpty;
+            s.retau(g, k);
+            bool changed = true;
+            if (io.hop > 1 && s.cnt == k && s.tau <= io.ulim) {
+                // saturated hub: OR of the segments' partial masks
+                const int idx = g.l < k ? u_pos(sU, io.ulim, old) : -1;
+                auto part_slice = [&](int q) {
+                    Mask4 m;
+                    for (int64_t sidx = hub_seg[h] + g.l; sidx < hub_seg[h + 1]; sidx += G)
+                        m.load(PM + sidx * kUWords + q * 4);
+                    grp_or(g, m);
+                    return m;
+                };
+                uint64_t sk_new;
+                changed = merge_slices(g, k, sU, idx, part_slice(0), part_slice, sk_new);
+                s.sk = sk_new;
+                s.cnt = k;
+            } else {
+                for (int64_t sidx = hub_seg[h]; sidx < hub_seg[h + 1]; ++sidx) {
+                    const uint64_t x = g.l < k ? part[sidx * k + g.l] : kEmpty;
+                    absorb(g, k, x, s);
+                }
+            }
+            if (changed) {
+                dc = finish_vertex(g, io, v, deg, old, s, slot, sU);
+            } else if (g.l == 0) {
+                io.stg_grp[slot].info = 0;  // unchanged: empty slot
+            }
+        }
         if (dc && g.l == 0) {
-            atomicAdd(&ctr->merges, (unsigned long long)deg);
-            atomicAdd(&ctr->delta_next, (unsigned long long)(deg * dc));
+            atomicAdd(&io.ctr->merges, (unsigned long long)deg);
+            atomicAdd(&io.ctr->delta_next, (unsigned long long)(deg * dc));
         }
     }
-    flush_counters(g, hc, ctr);
+    flush_counters(g, hc, io.ctr);
 }
 
 // Sparse hops: the non-hub part of N(frontier).  Warp per frontier vertex;
@@ -904,6 +1096,22 @@ __global__ void __launch_bounds__(1024) k_sort_small(const uint64_t* __restrict_
     for (int i = threadIdx.x; i < kUW; i += blockDim.x) U[i] = i < w ? a[i] : kEmpty;
 }
 
+// Rank id of the vertex of each rank of U (-1 for padding).
+__global__ void k_rank_ids(const uint64_t* __restrict__ U, int w, uint64_t seed, int32_t* __restrict__ URid) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kUW) URid[i] = i < w ? (int32_t)rank_vertex(seed, U[i]) : -1;
+}
+
+// The frontier of the previous hop as a bitmap: bit v = (Dcnt[v] > 0).
+__global__ void k_front_bitmap(const uint8_t* __restrict__ Dcnt, int64_t n, uint32_t* __restrict__ bm) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t v = base + lane_id();
+        const unsigned w = __ballot_sync(kFull, v < n && Dcnt[v] > 0);
+        if (lane_id() == 0) bm[base >> 5] = w;
+    }
+}
+
 // U = the min(kUW, n) smallest vertex ranks: collect the ranks below a
 // threshold expected to pass about 2048 of them (ranks are uniform), widen or
 // narrow it until between min(kUW, n) and kSelCap pass, then sort them.
@@ -940,7 +1148,11 @@ static int select_small_ranks(fl_graph* g) {
     if (rc == FL_OK) {
         FL_LAUNCH(kProfSketchOther, k_sort_small<<<1, 1024, 0, st>>>(buf.as<uint64_t>(), (int)c, w,
                                                                      g->U.as<uint64_t>()));
+        FL_LAUNCH(kProfSketchOther, k_rank_ids<<<(kUW + 255) / 256, 256, 0, st>>>(
+                                        g->U.as<uint64_t>(), w, g->seed, g->URid.as<int32_t>()));
         cudaError_t e = cudaMemcpyAsync(&g->ulim, g->U.as<uint64_t>() + (w - 1), 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&g->hlim, g->U.as<uint64_t>() + (std::min(w, 64) - 1), 8, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = status_of(e, "small ranks", __FILE__, __LINE__);
     }
@@ -953,37 +1165,52 @@ static int select_small_ranks(fl_graph* g) {
 template <int G>
 static int launch_hop(fl_graph* g, int hop, const int32_t* list, int64_t n_list, int pin, int pout,
                       int64_t slot_base, bool sparse) {
-    const uint32_t sparse_hop = sparse ? (uint32_t)hop : 0u;
     cudaStream_t st = g->stream;
     const int k = g->k;
     const int per_block = 256 / G;
-    StgGroup* grp = g->stg_grp.as<StgGroup>() + slot_base;
-    const IdMap vb = idmap_of(g);
-    int32_t* ent = g->stg_ent.as<int32_t>() + slot_base * k;
+    const uint32_t sparse_hop = sparse ? (uint32_t)hop : 0u;
+    HopIO io;
+    io.rowp = g->rowp.as<int64_t>();
+    io.cols = g->cols.as<int32_t>();
+    io.k = k;
+    io.hop = hop;
+    io.seed = g->seed;
+    io.S = g->S.as<uint64_t>();
+    io.Scnt = g->Scnt.as<uint8_t>();
+    io.Dp = g->D[pin].as<uint64_t>();
+    io.Dcp = g->Dcnt[pin].as<uint8_t>();
+    io.Dc = g->D[pout].as<uint64_t>();
+    io.Dcc = g->Dcnt[pout].as<uint8_t>();
+    io.Fp = g->F[pin].as<uint64_t>();
+    io.Fc = g->F[pout].as<uint64_t>();
+    io.Hp = g->H[pin].as<uint64_t>();
+    io.Hc = g->H[pout].as<uint64_t>();
+    io.W = g->W.as<uint64_t>();
+    io.bm = g->fbm.as<uint32_t>();
+    io.DMp = g->DM[pin].as<uint64_t>();
+    io.DMc = g->DM[pout].as<uint64_t>();
+    io.n = g->n;
+    io.vg = g->vg.as<int32_t>();
+    io.ve = g->ve.as<int32_t>();
+    io.stg_ent = g->stg_ent.as<int32_t>() + slot_base * k;
+    io.stg_grp = g->stg_grp.as<StgGroup>() + slot_base;
+    io.U = g->U.as<uint64_t>();
+    io.URid = g->URid.as<int32_t>();
+    io.ulim = g->ulim;
+    io.hlim = g->hlim;
+    io.ids = idmap_of(g);
+    io.ctr = g->ctr.as<Counters>();
     if (n_list > 0)
-        FL_LAUNCH(kProfSketchMerge, k_hop_vertices<G><<<grid_for(n_list, per_block), 256, 0, st>>>(
-                                        list, n_list, g->rowp.as<int64_t>(), g->cols.as<int32_t>(), k, g->seed, hop,
-                                        g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[pin].as<uint64_t>(),
-                                        g->Dcnt[pin].as<uint8_t>(), g->D[pout].as<uint64_t>(),
-                                        g->Dcnt[pout].as<uint8_t>(), g->vg.as<int32_t>(), g->ve.as<int32_t>(), ent,
-                                        grp, g->U.as<uint64_t>(), g->ulim, g->DM[pin].as<uint64_t>(),
-                                        g->DM[pout].as<uint64_t>(), vb, g->ctr.as<Counters>()));
+        FL_LAUNCH(kProfSketchMerge, k_hop_vertices<G><<<grid_for(n_list, per_block), 256, 0, st>>>(list, n_list, io));
     if (g->n_hubs > 0) {
         FL_LAUNCH(kProfSketchMerge, k_hop_hub_segments<G><<<grid_for(g->n_seg, per_block), 256, 0, st>>>(
                                         g->hub_list.as<int32_t>(), g->hub_seg.as<int64_t>(), g->seg_hub.as<int32_t>(),
-                                        g->n_seg, g->rowp.as<int64_t>(), g->cols.as<int32_t>(), k, g->seed, hop,
-                                        g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[pin].as<uint64_t>(),
-                                        g->Dcnt[pin].as<uint8_t>(), g->part.as<uint64_t>(), g->U.as<uint64_t>(), g->ulim,
-                                        g->DM[pin].as<uint64_t>(), g->PM.as<uint64_t>(), g->seg_flag.as<uint8_t>(),
-                                        g->stamp.as<uint32_t>(), sparse_hop, vb, g->ctr.as<Counters>()));
+                                        g->n_seg, g->part.as<uint64_t>(), g->PM.as<uint64_t>(), g->PH.as<uint64_t>(),
+                                        g->seg_flag.as<uint8_t>(), g->stamp.as<uint32_t>(), sparse_hop, io));
         FL_LAUNCH(kProfSketchMerge, k_hop_hubs<G><<<grid_for(g->n_hubs, per_block), 256, 0, st>>>(
                                         g->hub_list.as<int32_t>(), g->n_hubs, g->hub_seg.as<int64_t>(),
-                                        g->part.as<uint64_t>(), g->rowp.as<int64_t>(), k, g->seed, hop, n_list,
-                                        g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), g->D[pout].as<uint64_t>(),
-                                        g->Dcnt[pout].as<uint8_t>(), g->vg.as<int32_t>(), g->ve.as<int32_t>(), ent,
-                                        grp, g->U.as<uint64_t>(), g->ulim, g->PM.as<uint64_t>(),
-                                        g->seg_flag.as<uint8_t>(), g->stamp.as<uint32_t>(), sparse_hop,
-                                        g->DM[pout].as<uint64_t>(), vb, g->ctr.as<Counters>()));
+                                        g->part.as<uint64_t>(), g->PM.as<uint64_t>(), g->PH.as<uint64_t>(),
+                                        g->seg_flag.as<uint8_t>(), g->stamp.as<uint32_t>(), sparse_hop, n_list, io));
     }
     FL_CUDA(cudaGetLastError());
     return FL_OK;
@@ -1016,7 +1243,15 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     FL_TRY(dalloc(g->DM[0], (size_t)n * kUWords * 8));
     FL_TRY(dalloc(g->DM[1], (size_t)n * kUWords * 8));
     FL_TRY(dalloc(g->PM, (size_t)std::max<int64_t>(g->n_seg, 1) * kUWords * 8));
+    FL_TRY(dalloc(g->PH, (size_t)std::max<int64_t>(g->n_seg, 1) * 8));
     FL_TRY(dalloc(g->seg_flag, (size_t)std::max<int64_t>(g->n_seg, 1)));
+    for (int p = 0; p < 2; ++p) {
+        FL_TRY(dalloc(g->F[p], (size_t)n * 8));
+        FL_TRY(dalloc(g->H[p], (size_t)n * 8));
+    }
+    FL_TRY(dalloc(g->W, (size_t)n * 8));
+    FL_TRY(dalloc(g->fbm, ((size_t)(n + 31) / 32 + 1) * 4));
+    FL_TRY(dalloc(g->URid, (size_t)kUW * 4));
     // staging: slots 0..n-1 for hop 0, then one slot per work item of each hop
     const int64_t per_dense = g->n_low + g->n_hubs;
     size_t slot_cap = (size_t)n + (size_t)per_dense * 8 + 1024;
@@ -1031,6 +1266,7 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     FL_TRY(dalloc(act, (size_t)n * 4));
 
     FL_CUDA(cudaMemsetAsync(g->S.p, 0xff, nk * 8, st));
+    FL_CUDA(cudaMemsetAsync(g->W.p, 0, (size_t)n * 8, st));
     FL_CUDA(cudaMemsetAsync(g->stamp.p, 0, (size_t)n * 4, st));
     FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st));
     {
@@ -1100,7 +1336,13 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
             FL_TRY(dgrow(g->stg_ent, cap * k * 4, (size_t)used_slots * k * 4, st));
             g->stg_grp_cap = cap;
         }
+        // this hop's outputs read "no new entries" for every vertex that does not change
         FL_CUDA(cudaMemsetAsync(g->Dcnt[pout].p, 0, (size_t)n, st));
+        FL_CUDA(cudaMemsetAsync(g->F[pout].p, 0xff, (size_t)n * 8, st));
+        FL_CUDA(cudaMemsetAsync(g->H[pout].p, 0, (size_t)n * 8, st));
+        if (hop > 1)
+            FL_LAUNCH(kProfSketchOther, k_front_bitmap<<<grid_for(n, 256), 256, 0, st>>>(
+                                            g->Dcnt[pin].as<uint8_t>(), n, g->fbm.as<uint32_t>()));
         if (time_hops) {
             if (n_list > 0)
                 FL_LAUNCH(kProfSketchOther, k_hop_census<<<grid_for(n_list, 256), 256, 0, st>>>(
