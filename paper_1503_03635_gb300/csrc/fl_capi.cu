@@ -32,7 +32,7 @@ int copy_out(void* dst, const void* src, size_t bytes, int mem_kind, cudaStream_
 
 void destroy_graph(fl_graph* g) {
     cudaStreamSynchronize(g->stream);  // its buffers go to the idle-block cache
-    DBuf* bufs[] = {&g->rowp, &g->cols, &g->low_list, &g->hub_list, &g->hub_seg, &g->seg_hub, &g->part,
+    DBuf* bufs[] = {&g->rowp, &g->cols, &g->low_list, &g->small_list, &g->mid_list, &g->hub_list, &g->hub_seg, &g->seg_hub, &g->part,
                     &g->S, &g->Scnt, &g->D[0], &g->D[1], &g->Dcnt[0], &g->Dcnt[1], &g->frontier[0],
                     &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent, &g->stg_grp, &g->gofs, &g->eofs,
                     &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub, &g->ctr, &g->scratch,
@@ -746,6 +746,8 @@ int fl_batch_solve(fl_batch* b, int n_active, int k, uint64_t seed, const double
         view.n = N;
         view.nnz = n_active * b->base->nnz;
         view.n_low = U->n_low / R * n_active;
+        view.n_small = U->n_small / R * n_active;
+        view.n_mid = U->n_mid / R * n_active;
         view.n_hubs = U->n_hubs / R * n_active;
         view.n_seg = U->n_seg / R * n_active;
     }

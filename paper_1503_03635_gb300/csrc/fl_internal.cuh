@@ -120,6 +120,8 @@ constexpr unsigned kFull = 0xffffffffu;
 // processed in segments of kSeg edges, one group of lanes per segment.
 constexpr int kHubDeg = 2048;
 constexpr int kSeg = 2048;
+// Non-hub vertices with at most kSmallDeg neighbours are pulled by one thread each.
+constexpr int kSmallDeg = 8;
 // Width of the small-rank universe of the sketch hops (the kUW smallest
 // ranks of a graph; a saturated sketch is a kUW-bit mask over them).
 constexpr int kUW = 1024;
@@ -384,6 +386,10 @@ struct fl_graph {
     // static work lists: non-hub non-isolated vertices, hubs, hub segments
     int lists_ready = 0;
     fl::DBuf low_list, hub_list;   // int32[n_low], int32[n_hubs]
+    // the non-hub vertices split by degree for the relaxation rounds: at most
+    // kSmallDeg neighbours (a thread each), more (a group of lanes each)
+    fl::DBuf small_list, mid_list; // int32[n_small], int32[n_mid]
+    int64_t n_small = 0, n_mid = 0;
     fl::DBuf hub_seg;              // int64[n_hubs+1]: first segment of each hub
     fl::DBuf seg_hub;              // int32[n_seg]: hub of each segment
     int64_t n_low = 0, n_hubs = 0, n_seg = 0;

@@ -94,8 +94,44 @@ __device__ __forceinline__ unsigned long long pull_min(const int32_t* __restrict
     return m;
 }
 
-// Pull round over non-hub vertices: four vertices per warp, eight lanes per
-// vertex striding over its neighbours; the lanes meet again at the reduction.
+// Pull round over vertices of at most kSmallDeg neighbours: a thread per
+// vertex, its neighbours loaded four at a time (column, bitmap and value
+// loads each independent of the others), so that a warp keeps 32 vertices'
+// chains in flight.
+__global__ void __launch_bounds__(256) k_pull_small(const int32_t* __restrict__ list, int64_t n_list,
+                                                    const int64_t* __restrict__ rowp,
+                                                    const int32_t* __restrict__ cols, unsigned long long add,
+                                                    unsigned long long limit, bool settle,
+                                                    const uint32_t* __restrict__ bm,
+                                                    const unsigned long long* __restrict__ X,
+                                                    unsigned long long* __restrict__ Xn,
+                                                    uint32_t* __restrict__ stamp, uint32_t sv,
+                                                    unsigned long long* __restrict__ n_changed,
+                                                    const int32_t* __restrict__ vpart,
+                                                    const int32_t* __restrict__ part_cnt) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long changed = 0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_list; base += stride) {
+        const int64_t i = base + lane_id();
+        const int32_t v = i < n_list ? list[i] : 0;
+        const bool have = i < n_list && !part_idle(vpart, part_cnt, v);
+        const unsigned long long own = have ? X[v] : ~0ULL;
+        const bool work = have && !(settle && own < limit);
+        const int64_t beg = work ? rowp[v] : 0, end = work ? rowp[v + 1] : 0;
+        const unsigned long long m = pull_min(cols, beg, end, 1, bm, X, add, limit, own);
+        const bool ch = work && m < own;
+        if (ch) {
+            Xn[v] = m;
+            stamp[v] = sv;
+        }
+        changed += __popc(__ballot_sync(kFull, ch));
+    }
+    if (lane_id() == 0 && changed) atomicAdd(n_changed, changed);
+}
+
+// Pull round over the other non-hub vertices: four vertices per warp, eight
+// lanes per vertex striding over its neighbours; the lanes meet again at the
+// reduction.
 __global__ void __launch_bounds__(256) k_pull_low(const int32_t* __restrict__ list, int64_t n_list,
                                                   const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
                                                   unsigned long long add, unsigned long long limit, bool settle,
@@ -390,9 +426,13 @@ int relax_round(fl_graph* g, Relax& r, unsigned long long add, uint32_t sv, int 
                                                                   vpart ? r.part_limit : nullptr, r.part_round));
         FL_CUDA(cudaMemcpyAsync(Xn, X, (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
         FL_CUDA(cudaMemsetAsync(&r.cnt[2], 0, 8, st));
-        if (g->n_low > 0)
-            FL_LAUNCH(cls, k_pull_low<<<grid_for((g->n_low + 3) / 4, 8), 256, 0, st>>>(
-                               g->low_list.as<int32_t>(), g->n_low, rowp, cols, add, r.limit, r.settle, r.bm, X, Xn,
+        if (g->n_small > 0)
+            FL_LAUNCH(cls, k_pull_small<<<grid_for(g->n_small, 256), 256, 0, st>>>(
+                               g->small_list.as<int32_t>(), g->n_small, rowp, cols, add, r.limit, r.settle, r.bm, X,
+                               Xn, r.stamp, sv, &r.cnt[2], vpart, r.part_cnt));
+        if (g->n_mid > 0)
+            FL_LAUNCH(cls, k_pull_low<<<grid_for((g->n_mid + 3) / 4, 8), 256, 0, st>>>(
+                               g->mid_list.as<int32_t>(), g->n_mid, rowp, cols, add, r.limit, r.settle, r.bm, X, Xn,
                                r.stamp, sv, &r.cnt[2], vpart, r.part_cnt));
         if (g->n_seg > 0)
             FL_LAUNCH(cls, k_pull_segs<<<grid_for(g->n_seg, 8), 256, 0, st>>>(

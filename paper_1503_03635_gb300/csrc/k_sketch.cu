@@ -938,13 +938,25 @@ __global__ void k_ads_scatter(const StgGroup* __restrict__ stg_grp, int64_t n_sl
 // ------------------------------------------------------------------ graph work lists
 
 __global__ void k_flag_degree(const int64_t* __restrict__ rowp, int64_t n, int32_t* __restrict__ low,
-                              int32_t* __restrict__ hub, int32_t* __restrict__ nseg) {
+                              int32_t* __restrict__ hub, int32_t* __restrict__ nseg, int32_t* __restrict__ small) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         const int64_t d = rowp[v + 1] - rowp[v];
         low[v] = (d > 0 && d <= kHubDeg) ? 1 : 0;
         hub[v] = d > kHubDeg ? 1 : 0;
         nseg[v] = d > kHubDeg ? (int32_t)((d + kSeg - 1) / kSeg) : 0;
+        small[v] = (d > 0 && d <= kSmallDeg) ? 1 : 0;
+    }
+}
+
+// Split the non-hub vertices by degree (ids ascending in both lists).
+__global__ void k_scatter_by_degree(const int32_t* __restrict__ low, const int32_t* __restrict__ small,
+                                    const int64_t* __restrict__ small_pos, const int64_t* __restrict__ low_pos,
+                                    int64_t n, int32_t* __restrict__ small_list, int32_t* __restrict__ mid_list) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        if (small[v]) small_list[small_pos[v]] = (int32_t)v;
+        else if (low[v]) mid_list[low_pos[v] - small_pos[v]] = (int32_t)v;
     }
 }
 
@@ -991,23 +1003,35 @@ static int scan_total(const int64_t* pos, const int32_t* flag, int64_t n, cudaSt
 int build_work_lists(fl_graph* g) {
     const int64_t n = g->n;
     cudaStream_t st = g->stream;
-    DBuf low, hub, nseg, low_pos, hub_pos, seg_pos;
+    DBuf low, hub, nseg, low_pos, hub_pos, seg_pos, small, small_pos;
     int rc = FL_OK;
     do {
         if ((rc = dalloc(low, (size_t)n * 4)) || (rc = dalloc(hub, (size_t)n * 4)) ||
             (rc = dalloc(nseg, (size_t)n * 4)) || (rc = dalloc(low_pos, (size_t)n * 8)) ||
-            (rc = dalloc(hub_pos, (size_t)n * 8)) || (rc = dalloc(seg_pos, (size_t)n * 8)))
+            (rc = dalloc(hub_pos, (size_t)n * 8)) || (rc = dalloc(seg_pos, (size_t)n * 8)) ||
+            (rc = dalloc(small, (size_t)n * 4)) || (rc = dalloc(small_pos, (size_t)n * 8)))
             break;
         FL_LAUNCH(kProfOther, k_flag_degree<<<grid_for(n, 256), 256, 0, st>>>(
-                                  g->rowp.as<int64_t>(), n, low.as<int32_t>(), hub.as<int32_t>(), nseg.as<int32_t>()));
+                                  g->rowp.as<int64_t>(), n, low.as<int32_t>(), hub.as<int32_t>(), nseg.as<int32_t>(),
+                                  small.as<int32_t>()));
         if ((rc = scan_exclusive_i32_to_i64(low.as<int32_t>(), low_pos.as<int64_t>(), n, st, g->scratch, kProfOther)) ||
             (rc = scan_exclusive_i32_to_i64(hub.as<int32_t>(), hub_pos.as<int64_t>(), n, st, g->scratch, kProfOther)) ||
-            (rc = scan_exclusive_i32_to_i64(nseg.as<int32_t>(), seg_pos.as<int64_t>(), n, st, g->scratch, kProfOther)))
+            (rc = scan_exclusive_i32_to_i64(nseg.as<int32_t>(), seg_pos.as<int64_t>(), n, st, g->scratch, kProfOther)) ||
+            (rc = scan_exclusive_i32_to_i64(small.as<int32_t>(), small_pos.as<int64_t>(), n, st, g->scratch,
+                                            kProfOther)))
             break;
         if ((rc = scan_total(low_pos.as<int64_t>(), low.as<int32_t>(), n, st, &g->n_low)) ||
             (rc = scan_total(hub_pos.as<int64_t>(), hub.as<int32_t>(), n, st, &g->n_hubs)) ||
-            (rc = scan_total(seg_pos.as<int64_t>(), nseg.as<int32_t>(), n, st, &g->n_seg)))
+            (rc = scan_total(seg_pos.as<int64_t>(), nseg.as<int32_t>(), n, st, &g->n_seg)) ||
+            (rc = scan_total(small_pos.as<int64_t>(), small.as<int32_t>(), n, st, &g->n_small)))
             break;
+        g->n_mid = g->n_low - g->n_small;
+        if ((rc = dalloc(g->small_list, (size_t)std::max<int64_t>(g->n_small, 1) * 4)) ||
+            (rc = dalloc(g->mid_list, (size_t)std::max<int64_t>(g->n_mid, 1) * 4)))
+            break;
+        FL_LAUNCH(kProfOther, k_scatter_by_degree<<<grid_for(n, 256), 256, 0, st>>>(
+                                  low.as<int32_t>(), small.as<int32_t>(), small_pos.as<int64_t>(),
+                                  low_pos.as<int64_t>(), n, g->small_list.as<int32_t>(), g->mid_list.as<int32_t>()));
         if ((rc = dalloc(g->low_list, (size_t)std::max<int64_t>(g->n_low, 1) * 4)) ||
             (rc = dalloc(g->hub_list, (size_t)std::max<int64_t>(g->n_hubs, 1) * 4)) ||
             (rc = dalloc(g->hub_seg, (size_t)(g->n_hubs + 1) * 8)) ||
@@ -1025,7 +1049,8 @@ int build_work_lists(fl_graph* g) {
         e = cudaStreamSynchronize(st);
         if (e) { rc = status_of(e, "work lists", __FILE__, __LINE__); break; }
     } while (0);
-    dfree(low); dfree(hub); dfree(nseg); dfree(low_pos); dfree(hub_pos); dfree(seg_pos);
+    dfree(low); dfree(hub); dfree(nseg); dfree(low_pos); dfree(hub_pos); dfree(seg_pos); dfree(small);
+    dfree(small_pos);
     return rc;
 }
 
