@@ -159,6 +159,48 @@ int fl_compute_radii(fl_solve* s, const double* open_cost, const uint8_t* client
 int fl_open_facilities(fl_solve* s, uint8_t* open_out, int64_t* n_open, int mem_kind);
 
 /*
+ * fl_open_facilities_eps -- the paper's opening phase with accuracy eps > 0
+ * (Section 4.1, Algorithm 3; Section 4.2, Algorithms 4-5 and Eq. 2/3) and the
+ * facility selection of Algorithm 6 (Section 4.3), in place of
+ * fl_compute_radii + fl_open_facilities.  Radii grow on the grid alpha_j =
+ * alpha_{j-1} (1 + eps) from alpha_0 = gamma (1 + eps) / m^2 (m = |F||C|,
+ * gamma = max over clients reaching a facility of min_f c(f) + d(c, f)); in
+ * iteration j every unopened facility with q(f) >= c(f) opens, then every
+ * unfrozen client within (1 + eps) alpha_j of an open facility freezes.
+ * q(f) is the sum Eq. 2 and Eq. 3 accumulate, over the HIP-weighted client
+ * entries of f's ADS, each client counted at the smallest grid value >= its
+ * hop distance (the first shell read as [0, alpha_0]).  Clients that reach
+ * no facility never freeze; the phase ends when every facility is open or
+ * every client that reaches one is frozen.  Selection: the lexicographically
+ * first MIS under pi(f) of H-bar, where a client joins the facilities that
+ * opened in the iteration it froze and lie within (1 + eps) alpha of it.
+ *   eps            accuracy, 0 < eps <= 1e6 (FL_EINVAL otherwise; FL_EINVAL
+ *                  too when the grid would need more than 2^22 radii).
+ *   open_cost      double[n]: > 0 finite for facilities, +inf otherwise.
+ *   client_mask    uint8[n]: nonzero = client.
+ *   open_out       uint8[n] or NULL: the selected facilities.
+ *   n_open         int64 or NULL: their number.
+ *   fac_iter_out   int32[n] or NULL: iteration at which each vertex opened
+ *                  as a facility (-1: never).
+ *   cli_iter_out   int32[n] or NULL: iteration at which each client froze
+ *                  (-1: never).
+ * Arrays live in the memory mem_kind names; outputs are complete on return.
+ * Afterwards fl_assign_clients and fl_objective serve the selected set.
+ * Requires built sketches (FL_ESTATE).
+ */
+int fl_open_facilities_eps(fl_solve* s, double eps, const double* open_cost, const uint8_t* client_mask,
+                           int mem_kind, uint8_t* open_out, int64_t* n_open, int32_t* fac_iter_out,
+                           int32_t* cli_iter_out);
+
+/* fl_eps_stats -- gamma, alpha_0, the last iteration run, the number of
+   iterations with an opening or a freezing ("events", the ones the GPU
+   evaluates), and of iterations whose facilities needed an MIS, for the
+   last fl_open_facilities_eps of s (FL_ESTATE before one); pointers may be
+   NULL. */
+int fl_eps_stats(const fl_solve* s, double* gamma, double* alpha0, int64_t* iterations, int64_t* events,
+                 int64_t* groups);
+
+/*
  * fl_assign_clients -- nearest open facility of every vertex (Section 3.1,
  * d(c, S) = min over open f of d(c, f)); ties go to the smallest facility id.
  *   assign_out int32[n] or NULL (-1 = no open facility in the component).

@@ -1444,7 +1444,8 @@ static double eps_increment(const orc_graph* g, int64_t f, int64_t j, const doub
    opened, cli_iter[c] = iteration at which c froze (-1: never); q_out[f] =
    q(f) at its opening, or at the last iteration for facilities that stay
    closed.  mode 0: q by the closed form; mode 1: q accumulated by Eq. 2/3.
-   Returns ORC_OK, or ORC_ESTATE when the grid would exceed its cap. */
+   Returns ORC_OK, or ORC_ESTATE when the grid would exceed its cap (eps too
+   small). */
 int orc_eps_open(const orc_graph* g, double eps, const double* cost, const uint8_t* client, int mode,
                  int32_t* fac_iter, int32_t* cli_iter, double* q_out, double* alpha0_out, double* gamma_out,
                  int64_t* iters_out) {
@@ -1490,11 +1491,14 @@ int orc_eps_open(const orc_graph* g, double eps, const double* cost, const uint8
     for (int64_t v = 0; v < n; ++v) if (cost[v] < INFINITY) comp_has_fac[comp[v]] = 1;
     int64_t unopened = nF, unfrozen = 0;
     for (int64_t v = 0; v < n; ++v) if (client[v] && comp_has_fac[comp[v]]) ++unfrozen;
+    /* iterations beyond alpha_J change nothing: with alpha >= max cost + n + 1
+       every facility that has an unfrozen client in its ADS has opened and
+       every client that reaches an open facility has frozen (a sampled ADS
+       may show a facility none of its component's clients, which then never
+       opens) */
     int64_t j = 0;
-    while (unopened > 0 && unfrozen > 0) {
+    while (unopened > 0 && unfrozen > 0 && j < J) {
         ++j;
-        if (j > J) { free(grid); free(shell_of_hop); free(comp); free(q); free(dist); free(comp_has_fac); free(newly);
-                     return ORC_ESTATE; }
         /* OpenFacilities (Algorithm 5): every unopened facility at once */
         int64_t opened = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : opened)

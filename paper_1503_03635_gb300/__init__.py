@@ -29,7 +29,8 @@ EXPORTS = ("fl_graph_create", "fl_graph_destroy", "fl_build_sketches", "fl_sketc
            "fl_solve_stats", "fl_status_str", "fl_last_error", "fl_profile_enable", "fl_profile_reset",
            "fl_profile_query", "fl_hop_stats", "fl_hop_model", "fl_batch_create_union", "fl_batch_create_replicas",
            "fl_batch_solve", "fl_batch_info", "fl_batch_destroy", "fl_assign_nearest_noalloc",
-           "fl_ball_sizes", "fl_ball_estimates", "fl_compute_radii_exact")
+           "fl_ball_sizes", "fl_ball_estimates", "fl_compute_radii_exact", "fl_open_facilities_eps",
+           "fl_eps_stats")
 
 PROF_CLASSES = {"sketch_merge": 0, "sketch_expand": 1, "sketch_other": 2, "radius": 3, "keys": 4,
                 "mis": 5, "bfs": 6, "other": 7, "exact": 8}
@@ -88,6 +89,9 @@ def load(build_if_missing: bool = True):
             "fl_ball_sizes": ([vp, i64, vp, ctypes.c_int32, vp, ci, vp], ci),
             "fl_ball_estimates": ([vp, i64, vp, ctypes.c_int32, vp, ci, vp], ci),
             "fl_compute_radii_exact": ([vp, vp, vp, ci, vp], ci),
+            "fl_open_facilities_eps": ([vp, ctypes.c_double, vp, vp, ci, vp, P64, vp, vp], ci),
+            "fl_eps_stats": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P64, P64,
+                              P64], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -309,6 +313,33 @@ class Solve:
         _check(self._lib.fl_compute_radii_exact(self._h, p_c, p_m, _kind(k_c, k_m, k_r), p_r))
         return radii_out
 
+    def open_facilities_eps(self, eps: float, cost, client, open_out=None, fac_iter_out=None, cli_iter_out=None):
+        """The opening phase with eps > 0 and the selection of Algorithm 6.
+        Returns (open mask, number opened, opening iterations, freezing
+        iterations); outputs are allocated on the host when not given and the
+        inputs are host arrays."""
+        p_c, k_c, _ = _arg(cost, np.float64)
+        p_m, k_m, _ = _arg(client, np.uint8)
+        if k_c != FL_MEM_DEVICE:
+            n = self.graph.n
+            open_out = np.zeros(n, np.uint8) if open_out is None else open_out
+            fac_iter_out = np.zeros(n, np.int32) if fac_iter_out is None else fac_iter_out
+            cli_iter_out = np.zeros(n, np.int32) if cli_iter_out is None else cli_iter_out
+        p_o, k_o, _ = _arg(open_out, np.uint8)
+        p_f, k_f, _ = _arg(fac_iter_out, np.int32)
+        p_i, k_i, _ = _arg(cli_iter_out, np.int32)
+        nopen = ctypes.c_int64()
+        _check(self._lib.fl_open_facilities_eps(self._h, float(eps), p_c, p_m, _kind(k_c, k_m, k_o, k_f, k_i), p_o,
+                                                ctypes.byref(nopen), p_f, p_i))
+        return open_out, nopen.value, fac_iter_out, cli_iter_out
+
+    def eps_stats(self) -> dict:
+        g, a = ctypes.c_double(), ctypes.c_double()
+        it, ev, gr = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(self._lib.fl_eps_stats(self._h, ctypes.byref(g), ctypes.byref(a), ctypes.byref(it), ctypes.byref(ev),
+                                      ctypes.byref(gr)))
+        return dict(gamma=g.value, alpha0=a.value, iterations=it.value, events=ev.value, groups=gr.value)
+
     def open_facilities(self, open_out=None):
         """Phase (iii).  Returns (open mask, number opened)."""
         if open_out is None:
@@ -485,3 +516,16 @@ def solve(rowp, cols, k, seed, cost, client, stream=None) -> dict:
     obj, ds, un = s.objective()
     return dict(graph=g, solve=s, stats=g.stats(), radii=r, open=op, n_open=nopen, assign=a, dist=d,
                 objective=obj, dist_sum=ds, n_unserved=un, mis=s.stats())
+
+
+def solve_eps(rowp, cols, k, seed, eps, cost, client, stream=None) -> dict:
+    """The eps > 0 path through the C ABI with host arrays: sketches, the
+    opening phase and Algorithm 6, assignment, objective."""
+    g = Graph(rowp, cols, stream)
+    g.build_sketches(k, seed)
+    s = Solve(g)
+    op, nopen, fi, ci = s.open_facilities_eps(eps, cost, client)
+    a, d = s.assign_clients()
+    obj, ds, un = s.objective()
+    return dict(graph=g, solve=s, open=op, n_open=nopen, fac_iter=fi, cli_iter=ci, assign=a, dist=d, objective=obj,
+                dist_sum=ds, n_unserved=un, stats=s.eps_stats())

@@ -52,7 +52,8 @@ void destroy_solve(fl_solve* s) {
     DBuf* bufs[] = {&s->cost, &s->client, &s->radii, &s->ord, &s->fac_by_ord, &s->bcap, &s->state, &s->claimed,
                     &s->X, &s->stamp, &s->mval, &s->fr[0], &s->fr[1], &s->frval, &s->touched, &s->ulist,
                     &s->ubuck, &s->bcount, &s->open, &s->assign, &s->dist, &s->key_hi, &s->key_lo,
-                    &s->key_val, &s->obj_tmp, &s->part_T, &s->io};
+                    &s->key_val, &s->obj_tmp, &s->part_T, &s->io, &s->eps, &s->eps_tab, &s->eps_r,
+                    &s->eps_c};
     for (DBuf* b : bufs) dfree_idle(*b);
     delete s;
 }
@@ -447,6 +448,58 @@ int fl_open_facilities(fl_solve* s, uint8_t* open_out, int64_t* n_open, int mem_
     FL_CUDA(cudaStreamSynchronize(s->g->stream));
     if (n_open) *n_open = s->n_open;
     s->have_open = 1;
+    return FL_OK;
+}
+
+int fl_open_facilities_eps(fl_solve* s, double eps, const double* open_cost, const uint8_t* client_mask,
+                           int mem_kind, uint8_t* open_out, int64_t* n_open, int32_t* fac_iter_out,
+                           int32_t* cli_iter_out) {
+    FL_TRY(check_solve(s));
+    if (!(eps > 0.0) || !(eps <= 1.0e6)) FL_FAIL(FL_EINVAL, "eps must be in (0, 1e6]");
+    if (!open_cost || !client_mask) FL_FAIL(FL_EINVAL, "open_cost and client_mask are required");
+    if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    ProfScope ps(s->g);
+    fl_graph* g = s->g;
+    cudaStream_t st = g->stream;
+    s->have_radii = s->have_open = s->have_assign = s->have_eps = 0;
+    FL_TRY(load_solve_inputs(s, open_cost, client_mask, mem_kind));
+    FL_TRY(check_costs(s));
+    FL_TRY(open_facilities_eps(s, eps));
+    if (open_out && g->relabelled) {
+        FL_TRY(dalloc(s->io, (size_t)g->n * 9));
+        FL_TRY(permute_vertices<uint8_t>(g, s->open.as<uint8_t>(), s->io.as<uint8_t>(), 1, false, st));
+        FL_TRY(copy_out(open_out, s->io.p, (size_t)g->n, mem_kind, st));
+    } else {
+        FL_TRY(copy_out(open_out, s->open.p, (size_t)g->n, mem_kind, st));
+    }
+    for (int c = 0; c < 2; ++c) {
+        int32_t* out = c ? cli_iter_out : fac_iter_out;
+        if (!out) continue;
+        const int32_t* it = eps_iterations_of(s, c == 1);
+        if (g->relabelled) {
+            FL_TRY(dalloc(s->io, (size_t)g->n * 9));
+            FL_TRY(permute_vertices<int32_t>(g, it, s->io.as<int32_t>(), 1, false, st));
+            it = s->io.as<int32_t>();
+        }
+        FL_TRY(copy_out(out, it, (size_t)g->n * 4, mem_kind, st));
+        FL_CUDA(cudaStreamSynchronize(st));
+    }
+    FL_CUDA(cudaStreamSynchronize(st));
+    if (n_open) *n_open = s->n_open;
+    s->have_open = 1;
+    s->have_eps = 1;
+    return FL_OK;
+}
+
+int fl_eps_stats(const fl_solve* s, double* gamma, double* alpha0, int64_t* iterations, int64_t* events,
+                 int64_t* groups) {
+    if (!s) FL_FAIL(FL_EINVAL, "null solve handle");
+    if (!s->have_eps) FL_FAIL(FL_ESTATE, "no epsilon phase has run on this solve");
+    if (gamma) *gamma = s->eps_gamma;
+    if (alpha0) *alpha0 = s->eps_alpha0;
+    if (iterations) *iterations = s->eps_iterations;
+    if (events) *events = s->eps_events;
+    if (groups) *groups = s->eps_groups;
     return FL_OK;
 }
 

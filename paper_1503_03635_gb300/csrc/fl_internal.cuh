@@ -479,6 +479,12 @@ struct fl_solve {
     fl::DBuf open;                 // uint8[n]
     fl::DBuf assign, dist;         // int32[n]
     int64_t n_cand = 0, n_open = 0, mis_rounds = 0;
+    // opening phase with eps > 0: per-vertex iterations and scratch, the grid
+    // tables, one iteration's selection inputs, statistics of the last run
+    fl::DBuf eps, eps_tab, eps_r, eps_c;
+    double eps_gamma = -1.0, eps_alpha0 = 0.0;
+    int64_t eps_iterations = 0, eps_events = 0, eps_groups = 0;
+    int have_eps = 0;
 };
 
 namespace fl {
@@ -501,6 +507,7 @@ int build_work_lists(fl_graph* g);
 int build_sketches(fl_graph* g, int k, uint64_t seed);
 int compute_ecc_bound(fl_graph* g);
 
+int check_costs(fl_solve* s);
 int compute_radii(fl_solve* s);
 int open_facilities(fl_solve* s);
 int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, int32_t* dist,
@@ -540,6 +547,9 @@ int relax_prepare_list(fl_graph* g, Relax& r, int cls);
 int relax_collect_epoch(fl_graph* g, const unsigned long long* X, unsigned long long hi, int32_t* out,
                         unsigned long long* n_out, int cls);
 int assign_clients(fl_solve* s);
+// the opening phase with eps > 0 and the selection of Algorithm 6 (k_eps.cu)
+int open_facilities_eps(fl_solve* s, double eps);
+const int32_t* eps_iterations_of(const fl_solve* s, bool clients);
 // exact neighbourhood sizes, their HIP estimates, exact-count radii (k_exact.cu)
 int map_sources(fl_graph* g, const int32_t* in, int64_t n_src, int32_t* out);
 int exact_ball_sizes(fl_graph* g, int64_t n_src, const int32_t* src, int64_t D, const uint8_t* pred, int64_t* out);

@@ -235,7 +235,8 @@ __global__ void __launch_bounds__(256) k_radius(int64_t n, int64_t R, const doub
     }
 }
 
-int compute_radii(fl_solve* s) {
+// The solve's opening costs are finite and > 0, or +inf (not a facility).
+int check_costs(fl_solve* s) {
     fl_graph* g = s->g;
     cudaStream_t st = g->stream;
     FL_CUDA(cudaMemsetAsync(g->ctr.p, 0, sizeof(Counters), st));
@@ -243,6 +244,13 @@ int compute_radii(fl_solve* s) {
     FL_CUDA(cudaGetLastError());
     FL_TRY(read_counters(g));
     if (g->h_ctr->error) FL_FAIL(FL_EINVAL, "open_cost must be finite and > 0 for facilities, +inf otherwise");
+    return FL_OK;
+}
+
+int compute_radii(fl_solve* s) {
+    fl_graph* g = s->g;
+    cudaStream_t st = g->stream;
+    FL_TRY(check_costs(s));
     FL_LAUNCH(kProfRadius, k_radius<false><<<grid_for(g->n, 8), 256, 0, st>>>(g->n, 1, s->cost.as<double>(), s->client.as<uint8_t>(),
                                                g->gofs.as<int64_t>(), g->eofs.as<int64_t>(), g->ginfo.as<uint32_t>(),
                                                g->gwt.as<double>(), g->eid.as<int32_t>(), s->radii.as<double>()));
