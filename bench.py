@@ -271,6 +271,12 @@ def run_gpu(args):
     torch.cuda.synchronize()
     g = fl.Graph(rowp_d, cols_d, stream=stream)
     info = {}
+    tune = None
+    if not args.no_autotune:
+        # the graph's launch and round-switch schedule, picked by timing the
+        # path on it (results do not depend on it)
+        tune = g.autotune(w.k, w.seed, cost_d, client_d, max_trials=args.tune_trials)
+        tune["trials"] = args.tune_trials
 
     def step():
         g.build_sketches(w.k, w.seed)
@@ -310,6 +316,7 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     stats = g.stats()
+    g_schedule = g.schedule
     prof = {name: g.profile_query(name) for name in fl.PROF_CLASSES}
     launches = g.profile_query(-1)["launches"]
     model = g.hop_model()
@@ -343,6 +350,7 @@ def run_gpu(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             g2 = fl.Graph(rowp_h, cols_h, stream=stream)      # H2D of the CSR
+            g2.set_schedule(**g_schedule)                        # the schedule tuned above
             g2.build_sketches(w.k, w.seed)
             s2 = fl.Solve(g2)
             s2.compute_radii(cost_h, client_h)                  # H2D of costs and mask
@@ -403,6 +411,7 @@ def run_gpu(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "solves_per_sec": world * args.steps / (ms / 1e3),
             "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
+            "schedule": g_schedule, "autotune": tune,
             "hops": stats["hops"], "edge_merges_per_step": merges_step, "ads_entries": stats["ads_entries"],
             "n_open": info.get("n_open"), "objective": info.get("objective"),
             "mis_rounds": info.get("mis", {}).get("mis_rounds"), "hop_detail": hop_detail}
@@ -549,14 +558,19 @@ def run_batch(args):
     with torch.cuda.stream(stream):
         # resident graphs, costs and client sets (device memory, built once)
         g = fl.Graph(torch.from_numpy(base.rowp).to(dev), torch.from_numpy(base.cols).to(dev), stream=stream)
-        g.build_sketches(k, seed)
         cost_r = torch.from_numpy(np.concatenate(bw.inst_cost)).to(dev)
         client_r = torch.from_numpy(np.concatenate(bw.inst_client)).to(dev)
+        tune = None
+        if not args.no_autotune:
+            # tuned on the resident graph with the first instance's inputs
+            tune = g.autotune(k, seed, cost_r[:n], client_r[:n], max_trials=args.tune_trials)
+        g.build_sketches(k, seed)
         er_csr = [(torch.from_numpy(x.rowp).to(dev), torch.from_numpy(x.cols).to(dev)) for x in bw.graphs]
         cost_u = torch.from_numpy(np.concatenate([x.cost for x in bw.graphs])).to(dev)
         client_u = torch.from_numpy(np.concatenate([x.client for x in bw.graphs])).to(dev)
         er_graphs = [fl.Graph(r, c, stream=stream) for r, c in er_csr]
         brep = fl.Batch.replicas(g, R)
+        brep.set_schedule(g.schedule)
         buni = fl.Batch.union(er_csr, stream=stream)
         N_r, N_u = brep.n_total, buni.n_total
         out = {f: torch.empty(N_r + N_u, dtype=dt, device=dev)
@@ -624,7 +638,8 @@ def run_batch(args):
                 "plain": {"value": n_inst / (ms_plain / 1e3), "unit": "solves/s", "ms_per_step": ms_plain,
                           "form": "one fl_* sequence per instance on one stream"},
                 "speedup_vs_plain": ms_plain / ms_batch,
-                "identical_to_plain": bool(same and obj_ok), "clocks": clk}
+                "identical_to_plain": bool(same and obj_ok), "schedule": g.schedule, "autotune": tune,
+                "clocks": clk}
         print(json.dumps(line), flush=True)
     for x in er_graphs:
         x.close()
@@ -667,7 +682,16 @@ def run_serve(args):
     costs = flsynth.loguniform(len(arrivals), flsynth.QUERY_SEED + 2, 10.0, 1.0e3)
     qs = [serve.Query(costs[i], client_seed=flsynth.QUERY_SEED * 1000003 + i, client_frac=min(1.0, sizes[i] / n))
           for i in range(len(arrivals))]
-    srv = serve.Server(g, k, seed, workers=args.serve_workers, max_slots=args.serve_slots, keep_open_mask=True)
+    tune = None
+    if not args.no_autotune:
+        # the resident graph's schedule, tuned on one query's inputs
+        m0 = torch.empty(n, dtype=torch.uint8, device=dev)
+        serve.client_mask_on_device(torch, n, qs[0].client_seed, qs[0].client_frac, dev, m0)
+        tune = g.autotune(k, seed, torch.full((n,), qs[0].cost, dtype=torch.float64, device=dev), m0,
+                          max_trials=args.tune_trials)
+        torch.cuda.synchronize()
+    srv = serve.Server(g, k, seed, workers=args.serve_workers, max_slots=args.serve_slots, keep_open_mask=True,
+                       schedule=g.schedule)
     clocks = Clocks(local)
     clocks.start()
     t0 = time.perf_counter()
@@ -721,7 +745,8 @@ def run_serve(args):
                        "query": "clients: each vertex with probability m/n, m log-uniform in [1e3, 1e6]; "
                                 "every vertex a facility, one cost log-uniform in [10, 1000]",
                        "workers": args.serve_workers, "slots_per_worker": srv.slots,
-                       "max_pending": srv.max_pending},
+                       "max_pending": srv.max_pending, "admission": "per query, by free device memory",
+                       "waited_for_memory": srv.waited_for_memory, "schedule": g.schedule, "autotune": tune},
             "latency_ms": {"p50": lat.get("p50_ms"), "p99": lat.get("p99_ms"), "mean": lat.get("mean_ms"),
                            "max": lat.get("max_ms")},
             "offered": len(measured), "served": len(served), "refused": srv.rejected,
@@ -731,6 +756,123 @@ def run_serve(args):
                       "p50_ms": float(np.percentile(t_plain, 50) * 1e3) if t_plain else None,
                       "form": "one fl_* sequence per query, back to back"},
             "identical_to_plain": bool(same), "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_eps(args):
+    """The opening phase with eps > 0 (Algorithms 3-6) on the R-MAT scale-20
+    workload (k = 32, costs log-uniform in [5, 500], every vertex a client
+    and a facility): solves/s of fl_open_facilities_eps + assignment +
+    objective for eps in {0.01, 0.1, 1} (sketches built once beforehand),
+    beside the eps -> 0 path on the same instance, and the oracle's time for
+    eps = 1 on the host cores."""
+    import torch
+
+    import paper_1503_03635_gb300 as fl
+
+    if env_int("RANK", 0) != 0:
+        return 0
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fl.load()
+    w = flsynth.config("rmat20")
+    stream = torch.cuda.Stream(device=dev)
+    g = fl.Graph(torch.from_numpy(w.rowp).to(dev), torch.from_numpy(w.cols).to(dev), stream=stream)
+    g.build_sketches(w.k, w.seed)
+    cost_d = torch.from_numpy(w.cost).to(dev)
+    client_d = torch.from_numpy(w.client).to(dev)
+    open_d = torch.empty(w.n, dtype=torch.uint8, device=dev)
+    fi_d = torch.empty(w.n, dtype=torch.int32, device=dev)
+    ci_d = torch.empty(w.n, dtype=torch.int32, device=dev)
+    asg_d = torch.empty(w.n, dtype=torch.int32, device=dev)
+    dist_d = torch.empty(w.n, dtype=torch.int32, device=dev)
+    radii_d = torch.empty(w.n, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    rows = []
+    clocks = Clocks(local)
+    clocks.start()
+    for eps in (0.01, 0.1, 1.0):
+        s = fl.Solve(g)
+        out = {}
+
+        def one():
+            _, out["n_open"], _, _ = s.open_facilities_eps(eps, cost_d, client_d, open_d, fi_d, ci_d)
+            s.assign_clients(asg_d, dist_d)
+            out["objective"] = s.objective()[0]
+
+        ms = timed(one)
+        rows.append({"eps": eps, "ms_per_solve": ms, "solves_per_sec": 1e3 / ms, "n_open": out["n_open"],
+                     "objective": out["objective"], **s.eps_stats()})
+        s.close()
+    s = fl.Solve(g)
+    out = {}
+
+    def limit():
+        s.compute_radii(cost_d, client_d, radii_d)
+        _, out["n_open"] = s.open_facilities(open_d)
+        s.assign_clients(asg_d, dist_d)
+        out["objective"] = s.objective()[0]
+
+    ms0 = timed(limit)
+    s.close()
+    clk = clocks.stop()
+    g.close()
+    cpu = None
+    small = None
+    if not args.no_cpu_baseline:
+        # a bounded sample: the 10^4-vertex ER workload at eps = 1, on the
+        # host cores (the oracle evaluates every iteration of the grid) and on
+        # the GPU
+        import oracle
+
+        we = flsynth.config("er10k")
+        og = oracle.Graph(we.rowp, we.cols)
+        og.build_sketches(we.k, we.seed)
+        t0 = time.perf_counter()
+        o = og.eps_open(1.0, we.cost, we.client)
+        og.eps_select(1.0, o["alpha0"], o["fac_iter"], o["cli_iter"], we.seed)
+        t = time.perf_counter() - t0
+        og.close()
+        cpu = {"value": 1.0 / t, "unit": "solves/s", "cores": oracle.threads(), "kind": "oracle",
+               "sample": f"oracle opening phase and selection, eps = 1, on the er10k workload: {t:.3f} s "
+                         f"({o['iterations']} iterations, every one evaluated)"}
+        ge = fl.Graph(we.rowp, we.cols)
+        ge.build_sketches(we.k, we.seed)
+        se = fl.Solve(ge)
+        se.open_facilities_eps(1.0, we.cost, we.client)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            se.open_facilities_eps(1.0, we.cost, we.client)
+        small = {"workload": "er10k, eps = 1, host arrays", "gpu_ms_per_solve": (time.perf_counter() - t0) / 5 * 1e3,
+                 "oracle_ms_per_solve": t * 1e3}
+        se.close()
+        ge.close()
+    line = {"metric": METRIC, "value": rows[1]["solves_per_sec"], "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rows[1]["ms_per_solve"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "eps: opening phase with eps > 0 on rmat20", "n": w.n, "nnz": w.nnz, "k": w.k,
+                       "value_is": "eps = 0.1",
+                       "step": "fl_open_facilities_eps + assignment + objective (sketches built once)"},
+            "by_eps": rows,
+            "eps_to_zero": {"ms_per_solve": ms0, "n_open": out["n_open"], "objective": out["objective"],
+                            "form": "fl_compute_radii + fl_open_facilities + assignment + objective"},
+            "cpu_baseline": cpu, "same_instance_gpu_vs_oracle": small, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -765,9 +907,17 @@ def run_quality(args):
         g.close()
         return op, obj
 
+    def ours_eps(rowp, cols, k, eps, cost, client):
+        r = fl.solve_eps(rowp, cols, k, 1, eps, cost, client)
+        r["solve"].close()
+        r["graph"].close()
+        return r["objective"]
+
     t0 = time.perf_counter()
     modes = (("k4", 4, False), ("k32", 32, False), ("exact", 32, True))
+    eps_modes = (("eps0.01", 0.01), ("eps0.1", 0.1), ("eps1", 1.0))
     tiny = {key: [] for key, _, _ in modes}
+    tiny.update({key: [] for key, _ in eps_modes})
     for seed in range(tiny_n):
         w = flsynth.small_er(16, 2.2, 4000 + seed)
         cost = flsynth.loguniform(16, 4100 + seed, 0.5, 12.0)
@@ -775,6 +925,8 @@ def run_quality(args):
         _, opt = oracle.Graph(w.rowp, w.cols).optimum(cost, client)
         for key, k, ex in modes:
             tiny[key].append(ours(w.rowp, w.cols, k, cost, client, ex)[1] / opt)
+        for key, eps in eps_modes:
+            tiny[key].append(ours_eps(w.rowp, w.cols, 32, eps, cost, client) / opt)
     table = []
     graphs = [("rmat10", flsynth.rmat(10, 16, 52)), ("rmat11", flsynth.rmat(11, 16, 53))]
     for n in (1000, 2000):
@@ -793,6 +945,9 @@ def run_quality(args):
             if key == "k32":
                 _, ls2, _ = orc.local_search(cost, client, start=op, max_moves=max_moves)
                 row["local_search_from_k32"] = ls2
+        for key, eps in eps_modes:
+            obj = ours_eps(rowp, cols, 32, eps, cost, client)
+            row[key] = {"objective": obj, "vs_local_search": obj / ls}
         table.append(row)
     print(json.dumps({"workload": "quality", "seconds": time.perf_counter() - t0,
                       "vs_optimum": {"instances": f"{tiny_n} ER graphs, n = 16",
@@ -811,18 +966,21 @@ def main():
                     help="er10k, rmat20, rmat26 (the named workloads), batch (solves/s batched vs plain), "
                          "serve (Poisson query stream: p50/p99 latency, solves/s), "
                          "exact (exact neighbourhood sizes, ADS accuracy vs k, exact-count radii), "
-                         "quality (objective against the optimum and a local search) "
+                         "quality (objective against the optimum and a local search), "
+                         "eps (the opening phase with eps > 0) "
                          "or rmatS for the rmat20 recipe at scale S")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (no tuning pass)")
+    ap.add_argument("--tune-trials", type=int, default=10, help="timed schedules of the autotuner, at most")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (req/s)")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serve: measured seconds")
     ap.add_argument("--serve-warmup", type=float, default=5.0, help="serve: warm-up seconds")
     ap.add_argument("--serve-scale", type=int, default=23, help="serve: R-MAT scale of the resident graph")
     ap.add_argument("--serve-plain", type=int, default=20, help="serve: queries also run plain")
-    ap.add_argument("--serve-workers", type=int, default=2, help="serve: worker threads (streams)")
-    ap.add_argument("--serve-slots", type=int, default=4, help="serve: most queries per batch solve")
+    ap.add_argument("--serve-workers", type=int, default=4, help="serve: worker threads (streams)")
+    ap.add_argument("--serve-slots", type=int, default=2, help="serve: most queries per batch solve")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gpu":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -836,6 +994,8 @@ def main():
         return run_exact(args)
     if args.workload == "quality":
         return run_quality(args)
+    if args.workload == "eps":
+        return run_eps(args)
     return run_gpu(args)
 
 

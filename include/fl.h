@@ -326,6 +326,58 @@ int fl_hop_stats(const fl_graph* g, int64_t cap, int64_t* n_hops, int64_t* scann
                  int64_t* changed, double* ms);
 
 /*
+ * Schedules: how the kernels lay out work, never what they compute.
+ *   hop_group   lanes per vertex in the sketch hop when k <= 16: 16 or 32
+ *               (0 = 16); k > 16 always uses 32.
+ *   sparse_div  a hop runs sparse (only the neighbours of the previous
+ *               hop's frontier) when frontier * sparse_div < the listed
+ *               vertices (default 16).
+ *   dense_div   a relaxation round (MIS sweeps, BFS levels) pulls when its
+ *               frontier * dense_div >= the listed vertices (default 8) ...
+ *   edge_div    ... or when its frontier's edges * edge_div >= nnz
+ *               (default 16); otherwise it pushes.
+ *   graph_bfs   1: the assignment BFS runs as one CUDA graph whose
+ *               conditional WHILE node repeats one pull level on the device
+ *               (no host round trip per level; capped at n + 2 levels,
+ *               FL_ETIMEOUT beyond); 0 (default): push/pull levels driven by
+ *               the host.
+ *   level_cap   BFS levels at most (both forms; 0 = n + 2, never reached by
+ *               a BFS); a BFS that would need more returns FL_ETIMEOUT.
+ * Divisors lie in [1, 1024], graph_bfs in {0, 1}, level_cap >= 0 (FL_EINVAL
+ * otherwise).
+ */
+typedef struct fl_schedule {
+    int32_t hop_group;
+    int32_t sparse_div;
+    int32_t dense_div;
+    int32_t edge_div;
+    int32_t graph_bfs;
+    int32_t level_cap;
+} fl_schedule;
+
+/* fl_get_schedule / fl_set_schedule -- the graph's schedule (the default
+   until set or tuned); it applies to every later build and solve. */
+int fl_get_schedule(const fl_graph* g, fl_schedule* out);
+int fl_set_schedule(fl_graph* g, const fl_schedule* sched);
+
+/*
+ * fl_autotune -- pick g's schedule for k: times the whole path (sketches
+ * with `seed`, radii, keys and MIS, assignment) on g with the given costs and
+ * clients (memory per mem_kind) under candidate schedules, by coordinate
+ * descent from the default over at most max_trials timed configurations
+ * (each the best of two passes), keeps the fastest (a change needs a 1 %
+ * gain) and sets it on g; g's sketches are left built with (k, seed).  The
+ * choice is cached for the process per graph signature (vertices, CSR
+ * entries, hub / small / medium vertex counts) and k: a later call on a
+ * graph of the same signature sets the cached schedule without timing.
+ * chosen, ms_default, ms_tuned (per pass) may be NULL.
+ */
+int fl_autotune(fl_graph* g, int k, uint64_t seed, const double* open_cost, const uint8_t* client_mask, int mem_kind,
+                int max_trials, fl_schedule* chosen, double* ms_default, double* ms_tuned);
+/* fl_autotune_forget -- empty the autotuner's cache. */
+int fl_autotune_forget(void);
+
+/*
  * fl_hop_model -- per-hop terms of the algorithmic-bytes model of the sketch
  * hop (Alg. 2; one hop of the last build is one round of messages), filled
  * by every build whether or not profiling is on.  For hop h = 1..n_hops:
@@ -434,6 +486,9 @@ int fl_batch_solve(fl_batch* b, int n_active, int k, uint64_t seed, const double
 int fl_batch_info(const fl_batch* b, int64_t* n_inst, int64_t* n_total);
 
 /* fl_batch_destroy -- free the batch (not the graph of a replica batch). */
+/* fl_batch_set_schedule -- the schedule of the batch's union graph (see
+   fl_set_schedule). */
+int fl_batch_set_schedule(fl_batch* b, const fl_schedule* sched);
 int fl_batch_destroy(fl_batch* b);
 
 /* fl_status_str -- static text for a status code. */

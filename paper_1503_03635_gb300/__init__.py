@@ -30,10 +30,20 @@ EXPORTS = ("fl_graph_create", "fl_graph_destroy", "fl_build_sketches", "fl_sketc
            "fl_profile_query", "fl_hop_stats", "fl_hop_model", "fl_batch_create_union", "fl_batch_create_replicas",
            "fl_batch_solve", "fl_batch_info", "fl_batch_destroy", "fl_assign_nearest_noalloc",
            "fl_ball_sizes", "fl_ball_estimates", "fl_compute_radii_exact", "fl_open_facilities_eps",
-           "fl_eps_stats")
+           "fl_eps_stats", "fl_get_schedule", "fl_set_schedule", "fl_autotune", "fl_autotune_forget",
+           "fl_batch_set_schedule")
 
 PROF_CLASSES = {"sketch_merge": 0, "sketch_expand": 1, "sketch_other": 2, "radius": 3, "keys": 4,
                 "mis": 5, "bfs": 6, "other": 7, "exact": 8}
+
+
+class Schedule(ctypes.Structure):
+    """fl_schedule: launch and round-switch parameters (never results)."""
+    _fields_ = [("hop_group", ctypes.c_int32), ("sparse_div", ctypes.c_int32), ("dense_div", ctypes.c_int32),
+                ("edge_div", ctypes.c_int32), ("graph_bfs", ctypes.c_int32), ("level_cap", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
 class FLError(RuntimeError):
@@ -92,6 +102,12 @@ def load(build_if_missing: bool = True):
             "fl_open_facilities_eps": ([vp, ctypes.c_double, vp, vp, ci, vp, P64, vp, vp], ci),
             "fl_eps_stats": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P64, P64,
                               P64], ci),
+            "fl_get_schedule": ([vp, ctypes.POINTER(Schedule)], ci),
+            "fl_set_schedule": ([vp, ctypes.POINTER(Schedule)], ci),
+            "fl_autotune": ([vp, ci, u64, vp, vp, ci, ci, ctypes.POINTER(Schedule), ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double)], ci),
+            "fl_autotune_forget": ([], ci),
+            "fl_batch_set_schedule": ([vp, ctypes.POINTER(Schedule)], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -207,6 +223,26 @@ class Graph:
                                       ms.ctypes.data_as(ctypes.c_void_p)))
         return [dict(hop=i + 1, scanned=int(sc[i]), mask=int(mk[i]), changed=int(ch[i]), ms=float(ms[i]))
                 for i in range(h)]
+
+    @property
+    def schedule(self) -> dict:
+        sc = Schedule()
+        _check(self._lib.fl_get_schedule(self._h, ctypes.byref(sc)))
+        return sc.as_dict()
+
+    def set_schedule(self, **kw):
+        sc = Schedule(**{**self.schedule, **kw})
+        _check(self._lib.fl_set_schedule(self._h, ctypes.byref(sc)))
+
+    def autotune(self, k: int, seed: int, cost, client, max_trials: int = 16) -> dict:
+        """Pick this graph's schedule for k by timing the path (see fl_autotune)."""
+        p_c, k_c, _ = _arg(cost, np.float64)
+        p_m, k_m, _ = _arg(client, np.uint8)
+        sc, d, t = Schedule(), ctypes.c_double(), ctypes.c_double()
+        _check(self._lib.fl_autotune(self._h, int(k), int(seed), p_c, p_m, _kind(k_c, k_m), int(max_trials),
+                                     ctypes.byref(sc), ctypes.byref(d), ctypes.byref(t)))
+        self.k, self.seed = k, seed
+        return dict(schedule=sc.as_dict(), ms_default=d.value, ms_tuned=t.value)
 
     def hop_model(self) -> list:
         """Per hop of the last build: edge-merges E, merging vertices A,
@@ -444,6 +480,10 @@ class Batch:
         return dict(open=open_out, assign=assign_out, dist=dist_out, n_open=n_open, objective=obj, dist_sum=ds,
                     n_unserved=un)
 
+    def set_schedule(self, schedule: dict):
+        sc = Schedule(**schedule)
+        _check(self._lib.fl_batch_set_schedule(self._h, ctypes.byref(sc)))
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.fl_batch_destroy(self._h)
@@ -529,3 +569,8 @@ def solve_eps(rowp, cols, k, seed, eps, cost, client, stream=None) -> dict:
     obj, ds, un = s.objective()
     return dict(graph=g, solve=s, open=op, n_open=nopen, fac_iter=fi, cli_iter=ci, assign=a, dist=d, objective=obj,
                 dist_sum=ds, n_unserved=un, stats=s.eps_stats())
+
+
+def autotune_forget():
+    """Empty the autotuner's per-process cache."""
+    _check(load().fl_autotune_forget())

@@ -40,6 +40,11 @@ void destroy_graph(fl_graph* g) {
                     &g->H[1], &g->W, &g->fbm, &g->URid, &g->vbase, &g->vpart, &g->rid,
                     &g->inv, &g->xbits, &g->xaux, &g->xio};
     for (DBuf* b : bufs) dfree_idle(*b);
+    if (g->gbfs) {
+        graph_bfs_release(g->gbfs);
+        delete g->gbfs;
+        g->gbfs = nullptr;
+    }
     for (cudaEvent_t e : g->prof.ev) cudaEventDestroy(e);
     for (cudaEvent_t e : g->hop_ev)
         if (e) cudaEventDestroy(e);
@@ -877,6 +882,11 @@ int fl_batch_info(const fl_batch* b, int64_t* n_inst, int64_t* n_total) {
     if (n_inst) *n_inst = b->n_inst;
     if (n_total) *n_total = b->U->n;
     return FL_OK;
+}
+
+int fl_batch_set_schedule(fl_batch* b, const fl_schedule* sched) {
+    if (!b) FL_FAIL(FL_EINVAL, "null batch handle");
+    return fl_set_schedule(b->U, sched);
 }
 
 int fl_batch_destroy(fl_batch* b) {

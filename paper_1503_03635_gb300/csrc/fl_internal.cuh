@@ -375,6 +375,30 @@ int prof_drain(Prof* p);           // after a stream sync: accumulate elapsed ti
         ::fl::prof_end(slot__);                  \
     } while (0)
 
+// ----------------------------------------------------------------- schedules
+// Launch and round-switch parameters of a graph: they change how fast the
+// path runs, never what it computes.
+struct Sched {
+    int hop_group = 0;    // lanes per vertex in the sketch hop for k <= 16 (16 or 32; 0: 16)
+    int sparse_div = 16;  // a hop runs sparse when frontier * sparse_div < listed vertices
+    int dense_div = 8;    // a relaxation round pulls when frontier * dense_div >= listed vertices
+    int edge_div = 16;    // ... or when frontier edges * edge_div >= nnz
+    int graph_bfs = 0;    // 1: the assignment BFS runs as one CUDA graph (a device-side level loop)
+    int level_cap = 0;    // BFS levels at most (0: n + 2); beyond it FL_ETIMEOUT
+};
+
+// ----------------------------------------------------------------- graph BFS
+// A level-synchronous BFS run as one CUDA graph (k_solve.cu): its
+// instantiation, cached per graph handle (prefix views of a batch share it)
+// and rebuilt when the buffers or sizes it was built for change.
+struct GraphBfs {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void* key[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t key_n[4] = {0, 0, 0, 0};
+    DBuf state;  // level (uint32), vertices reached this level, error flag
+};
+
 // ----------------------------------------------------------------- handles
 
 }  // namespace fl
@@ -442,6 +466,8 @@ struct fl_graph {
     fl::DBuf scratch;              // general scratch (scans, sorts)
     fl::DBuf relax_aux;            // bitmap, hub frontier tags/values, edge counter of the rounds
     fl::Prof prof;                 // launch counts and kernel timings
+    fl::Sched sched;               // launch and round-switch schedule (fl_set_schedule, fl_autotune)
+    fl::GraphBfs* gbfs = new fl::GraphBfs();  // the CUDA-graph BFS of this handle (shared by prefix views)
     // per-hop counters of the last build (index h-1)
     std::vector<int64_t> hop_scanned, hop_mask, hop_changed;
     std::vector<double> hop_ms;
@@ -512,6 +538,9 @@ int compute_radii(fl_solve* s);
 int open_facilities(fl_solve* s);
 int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, int32_t* dist,
           DBuf& X, DBuf& stampb, DBuf* fr, DBuf& frval, int cls);
+int msbfs_graph(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, int32_t* dist, DBuf& X,
+                DBuf& stampb, int cls);
+void graph_bfs_release(GraphBfs* c);
 
 // State of a sequence of synchronous min-propagation rounds (k_relax.cu).
 struct Relax {

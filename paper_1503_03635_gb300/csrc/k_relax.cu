@@ -356,6 +356,8 @@ int relax_begin(fl_graph* g, Relax& r) {
         FL_TRY(build_work_lists(g));
         g->lists_ready = 1;
     }
+    r.dense_div = g->sched.dense_div;
+    r.edge_div = g->sched.edge_div;
     const size_t bm_words = (size_t)(g->n + 63) / 32 + 2;
     const size_t off_tag = ((bm_words * 4 + 255) / 256) * 256;
     const size_t off_val = off_tag + (((size_t)g->n_hubs * 4 + 255) / 256) * 256;

@@ -1382,7 +1382,7 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
                                                 g->ctr.as<Counters>()));
             FL_CUDA(cudaEventRecord(g->hop_ev[0], st));
         }
-        if (k <= 16)
+        if (k <= 16 && g->sched.hop_group != 32)
             FL_TRY(launch_hop<16>(g, hop, list, n_list, pin, pout, used_slots, !dense));
         else
             FL_TRY(launch_hop<32>(g, hop, list, n_list, pin, pout, used_slots, !dense));
@@ -1417,7 +1417,7 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
         if (n_front == 0) break;
         // a small frontier makes the next hop sparse: collect its list
         fr_list_ready = false;
-        if (n_front * 16 < g->n_low + g->n_hubs) {
+        if (n_front * g->sched.sparse_div < g->n_low + g->n_hubs) {
             FL_CUDA(cudaMemsetAsync(&g->ctr.as<Counters>()->aux0, 0, 8, st));
             if (n_list > 0)
                 FL_LAUNCH(kProfSketchExpand, k_collect_frontier<<<grid_for(n_list, 256), 256, 0, st>>>(

@@ -150,9 +150,229 @@ int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, i
     }
     r.n_front = n_src;
     r.sv_prev = 1;
-    for (uint32_t level = 0; r.n_front > 0; ++level) FL_TRY(relax_round(g, r, 1ULL << 32, level + 2, cls));
+    const int64_t cap = g->sched.level_cap > 0 ? g->sched.level_cap : n + 2;
+    for (uint32_t level = 0; r.n_front > 0; ++level) {
+        if ((int64_t)level >= cap) FL_FAIL(FL_ETIMEOUT, "BFS reached its level cap");
+        FL_TRY(relax_round(g, r, 1ULL << 32, level + 2, cls));
+    }
     FL_LAUNCH(cls, k_unpack_bfs<<<grid_for(n, 256), 256, 0, st>>>(r.X[r.cur], n, label, dist));
     FL_CUDA(cudaGetLastError());
+    return FL_OK;
+}
+
+// ------------------------------------------------------------------ BFS as one CUDA graph
+// The same BFS with its level loop on the device: a CUDA graph whose
+// conditional WHILE node repeats one pull level and a kernel that advances
+// the level, ending the loop when a level reaches no vertex.  Values are
+// updated in place: a vertex reached at level L gets stamp L, and level L
+// reads only neighbours stamped L - 1, whose values are final, so no level
+// sees a value written in the same level.  The level count is capped (n + 2
+// levels); at the cap the loop stops with an error flag (FL_ETIMEOUT).  One
+// graph launch and one synchronisation replace a launch sequence and a
+// synchronisation per level.
+
+namespace {
+
+struct GbfsState {
+    uint32_t level;
+    uint32_t pad;
+    unsigned long long reached;
+    unsigned long long error;
+};
+
+__device__ __forceinline__ bool gbfs_front(const uint32_t* __restrict__ stamp, int32_t u, uint32_t prev) {
+    return __ldg(&stamp[u]) == prev;
+}
+
+// Vertices of at most kSmallDeg neighbours: a thread each.
+__global__ void __launch_bounds__(256) k_gbfs_small(const int32_t* __restrict__ list, int64_t n_list,
+                                                    const int64_t* __restrict__ rowp,
+                                                    const int32_t* __restrict__ cols, unsigned long long* X,
+                                                    uint32_t* stamp, GbfsState* st, unsigned long long add) {
+    const uint32_t L = st->level;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long cnt = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_list; i += stride) {
+        const int32_t v = list[i];
+        if (X[v] != ~0ULL) continue;
+        unsigned long long m = ~0ULL;
+        for (int64_t e = rowp[v]; e < rowp[v + 1]; ++e) {
+            const int32_t u = __ldg(&cols[e]);
+            if (gbfs_front(stamp, u, L - 1)) m = umin64(m, X[u]);
+        }
+        if (m != ~0ULL) {
+            X[v] = m + add;
+            stamp[v] = L;
+            ++cnt;
+        }
+    }
+    if (cnt) atomicAdd(&st->reached, cnt);
+}
+
+// Other vertices: a group of G lanes each (8 for the middle degrees, 32 for
+// hubs), 32 / G vertices per warp; every lane of a warp runs every pass (the
+// group reductions are warp shuffles).
+template <int G>
+__global__ void __launch_bounds__(256) k_gbfs_group(const int32_t* __restrict__ list, int64_t n_list,
+                                                    const int64_t* __restrict__ rowp,
+                                                    const int32_t* __restrict__ cols, unsigned long long* X,
+                                                    uint32_t* stamp, GbfsState* st, unsigned long long add) {
+    constexpr int kPerWarp = 32 / G;
+    const uint32_t L = st->level;
+    const int lane = lane_id(), sub = lane & (G - 1);
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long cnt = 0;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * kPerWarp < n_list; w += warps) {
+        const int64_t i = w * kPerWarp + lane / G;
+        const int32_t v = i < n_list ? list[i] : 0;
+        const bool work = i < n_list && X[v] == ~0ULL;
+        unsigned long long m = ~0ULL;
+        if (work)
+            for (int64_t e = rowp[v] + sub; e < rowp[v + 1]; e += G) {
+                const int32_t u = __ldg(&cols[e]);
+                if (gbfs_front(stamp, u, L - 1)) m = umin64(m, X[u]);
+            }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) m = umin64(m, __shfl_xor_sync(kFull, m, o, G));
+        if (work && sub == 0 && m != ~0ULL) {
+            X[v] = m + add;
+            stamp[v] = L;
+            ++cnt;
+        }
+    }
+    if (cnt) atomicAdd(&st->reached, cnt);
+}
+
+// Sources: level 1, value = the source's label (distance 0).
+__global__ void k_gbfs_sources(const int32_t* __restrict__ src, int64_t n_src, const uint32_t* __restrict__ lo_of,
+                               unsigned long long* __restrict__ X, uint32_t* __restrict__ stamp) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_src; i += stride) {
+        const int32_t s = src[i];
+        atomicMin(&X[s], (unsigned long long)(lo_of ? lo_of[s] : (uint32_t)s));
+        stamp[s] = 1u;
+    }
+}
+
+// End of a level: stop when it reached no vertex (or at the level cap, with
+// the error flag), else go on with the next level.
+__global__ void k_gbfs_next(GbfsState* st, uint32_t cap, cudaGraphConditionalHandle h) {
+    if (st->reached == 0) {
+        cudaGraphSetConditional(h, 0);
+        return;
+    }
+    if (st->level >= cap) {
+        st->error = 1;
+        cudaGraphSetConditional(h, 0);
+        return;
+    }
+    st->level += 1;
+    st->reached = 0;
+    cudaGraphSetConditional(h, 1);
+}
+
+int graph_grid(int64_t items, int per_block) {
+    int64_t b = (items + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+}  // namespace
+
+void graph_bfs_release(GraphBfs* c) {
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+    dfree(c->state);
+}
+
+int msbfs_graph(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, int32_t* dist, DBuf& X,
+                DBuf& stampb, int cls) {
+    const int64_t n = g->n;
+    cudaStream_t st = g->stream;
+    if (!g->lists_ready) {
+        FL_TRY(build_work_lists(g));
+        g->lists_ready = 1;
+    }
+    GraphBfs* c = g->gbfs;
+    FL_TRY(dalloc(X, (size_t)n * 8));
+    FL_TRY(dalloc(stampb, (size_t)n * 4));
+    FL_TRY(dalloc(c->state, sizeof(GbfsState)));
+    unsigned long long* Xp = X.as<unsigned long long>();
+    uint32_t* stamp = stampb.as<uint32_t>();
+    GbfsState* state = c->state.as<GbfsState>();
+    const unsigned long long add = 1ULL << 32;
+    const uint32_t cap = (uint32_t)std::min<int64_t>(g->sched.level_cap > 0 ? g->sched.level_cap + 1 : n + 2,
+                                                     0x7fffffff);
+    // (re)build the graph when its buffers or sizes changed
+    const void* key[4] = {Xp, stamp, state, g->small_list.p};
+    const int64_t key_n[4] = {n, g->n_small + ((int64_t)cap << 32), g->n_mid, g->n_hubs};
+    bool same = c->exec != nullptr;
+    for (int i = 0; i < 4; ++i) same = same && c->key[i] == key[i] && c->key_n[i] == key_n[i];
+    if (!same) {
+        if (c->exec) cudaGraphExecDestroy(c->exec);
+        if (c->graph) cudaGraphDestroy(c->graph);
+        c->exec = nullptr;
+        c->graph = nullptr;
+        FL_CUDA(cudaGraphCreate(&c->graph, 0));
+        cudaGraphConditionalHandle h;
+        FL_CUDA(cudaGraphConditionalHandleCreate(&h, c->graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        FL_CUDA(cudaGraphAddNode(&node, c->graph, nullptr, nullptr, 0, &p));
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        cudaStream_t cs;
+        FL_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            const int64_t* rowp = g->rowp.as<int64_t>();
+            const int32_t* cols = g->cols.as<int32_t>();
+            if (g->n_small > 0)
+                k_gbfs_small<<<graph_grid(g->n_small, 256), 256, 0, cs>>>(g->small_list.as<int32_t>(), g->n_small,
+                                                                          rowp, cols, Xp, stamp, state, add);
+            if (g->n_mid > 0)
+                k_gbfs_group<8><<<graph_grid((g->n_mid + 3) / 4, 8), 256, 0, cs>>>(
+                    g->mid_list.as<int32_t>(), g->n_mid, rowp, cols, Xp, stamp, state, add);
+            if (g->n_hubs > 0)
+                k_gbfs_group<32><<<graph_grid(g->n_hubs, 8), 256, 0, cs>>>(g->hub_list.as<int32_t>(), g->n_hubs,
+                                                                           rowp, cols, Xp, stamp, state, add);
+            k_gbfs_next<<<1, 1, 0, cs>>>(state, cap, h);
+            cudaGraph_t captured = body;
+            e = cudaStreamEndCapture(cs, &captured);
+        }
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return status_of(e, "graph BFS capture", __FILE__, __LINE__);
+        FL_CUDA(cudaGraphInstantiate(&c->exec, c->graph, 0));
+        for (int i = 0; i < 4; ++i) {
+            c->key[i] = key[i];
+            c->key_n[i] = key_n[i];
+        }
+    }
+    FL_CUDA(cudaMemsetAsync(Xp, 0xff, (size_t)n * 8, st));
+    FL_CUDA(cudaMemsetAsync(stamp, 0, (size_t)n * 4, st));
+    const GbfsState init = {2u, 0u, 0ULL, 0ULL};  // sources are level 1; the loop starts at level 2
+    FL_CUDA(cudaMemcpyAsync(state, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+    if (n_src > 0) {
+        // labels are the sources' rank ids, as in msbfs
+        const uint32_t* label_of = g->rid.p ? g->rid.as<uint32_t>() : nullptr;
+        FL_LAUNCH(cls, k_gbfs_sources<<<grid_for(n_src, 256), 256, 0, st>>>(src_list, n_src, label_of, Xp, stamp));
+        FL_CUDA(cudaGetLastError());
+        cudaError_t le = cudaSuccess;
+        FL_LAUNCH(cls, le = cudaGraphLaunch(c->exec, st));
+        FL_CUDA(le);
+    }
+    FL_LAUNCH(cls, k_unpack_bfs<<<grid_for(n, 256), 256, 0, st>>>(Xp, n, label, dist));
+    FL_CUDA(cudaGetLastError());
+    GbfsState out;
+    FL_CUDA(cudaMemcpyAsync(&out, state, sizeof(out), cudaMemcpyDeviceToHost, st));
+    FL_CUDA(cudaStreamSynchronize(st));
+    if (out.error) FL_FAIL(FL_ETIMEOUT, "graph BFS reached its level cap");
     return FL_OK;
 }
 
@@ -656,6 +876,9 @@ int assign_clients(fl_solve* s) {
     FL_TRY(dalloc(s->assign, (size_t)g->n * 4));
     FL_TRY(dalloc(s->dist, (size_t)g->n * 4));
     // the open list was left in ulist by open_facilities
+    if (g->sched.graph_bfs)
+        return msbfs_graph(g, s->ulist.as<int32_t>(), s->n_open, s->assign.as<int32_t>(), s->dist.as<int32_t>(),
+                           s->X, s->stamp, kProfBfs);
     return msbfs(g, s->ulist.as<int32_t>(), s->n_open, s->assign.as<int32_t>(), s->dist.as<int32_t>(), s->X,
                  s->stamp, s->fr, s->frval, kProfBfs);
 }

@@ -3,12 +3,15 @@
 The graph and its sketches stay on the device.  A query is a client set
 (drawn on the device from a seed and a fraction, or given as a mask) and one
 opening cost for every vertex.  Worker threads, each with its own CUDA stream
-and replica batch (fl_batch_create_replicas), take every query that is
-waiting when they become free, up to the batch's slots, and solve them in one
-fl_batch_solve: a query that arrives while others are on the GPU is admitted
-as soon as a worker and its slots free up, and the workers' batches overlap
-on the device.  Slots per worker are set from free device memory at start-up
-(admission by memory).  Each query's result is the plain fl_* result for it
+and replica batch (fl_batch_create_replicas), take the queries that are
+waiting when they become free and solve them in one fl_batch_solve: a query
+that arrives while others are on the GPU is admitted as soon as a worker is
+free, and the in-flight workers' solves interleave on the device round by
+round.  Admission is by memory, per query: a worker takes another waiting
+query only while the device's free memory (cudaMemGetInfo at that moment)
+covers the query's solve state beyond a reserve; otherwise the query waits
+for memory to free up.  The replica batch of each worker holds at most
+max_slots CSR copies.  Each query's result is the plain fl_* result for it
 alone (the batch's instances share nothing but the read-only graph).
 
 Latency of a query = arrival (submit) -> its results on the host.
@@ -23,10 +26,12 @@ import numpy as np
 
 from . import Batch
 
-# device bytes per vertex of one batch slot beyond the CSR copy: costs,
+# device bytes per vertex of one query's solve beyond its CSR copy: costs,
 # client mask, radii, MIS and BFS state, outputs (an estimate of the sum of
 # the solve's per-vertex arrays, rounded up)
 _SLOT_BYTES_PER_VERTEX = 128
+# device memory kept free for the rest of the process when admitting queries
+_RESERVE_BYTES = 2 << 30
 
 
 class Query:
@@ -65,8 +70,9 @@ def client_mask_on_device(torch, n, seed, frac, device, out):
 
 
 class Server:
-    def __init__(self, graph, k: int, seed: int, workers: int = 2, max_slots: int = 16,
-                 mem_fraction: float = 0.6, keep_open_mask: bool = True, max_pending: int | None = None):
+    def __init__(self, graph, k: int, seed: int, workers: int = 4, max_slots: int = 2,
+                 mem_fraction: float = 0.6, keep_open_mask: bool = True, max_pending: int | None = None,
+                 schedule: dict | None = None):
         import torch
 
         self.torch = torch
@@ -75,9 +81,12 @@ class Server:
         self.keep_open_mask = keep_open_mask
         dev = torch.device("cuda", torch.cuda.current_device())
         self.device = dev
-        per_slot = graph.nnz * 4 + (graph.n + 1) * 8 + graph.n * _SLOT_BYTES_PER_VERTEX
+        # the workers' replica batches (CSR copies) within mem_fraction of the free memory
+        per_slot = graph.nnz * 4 + (graph.n + 1) * 8
         free, _ = torch.cuda.mem_get_info(dev)
         self.slots = max(1, min(max_slots, int(free * mem_fraction / (workers * per_slot))))
+        self.query_bytes = graph.n * _SLOT_BYTES_PER_VERTEX
+        self.waited_for_memory = 0
         # queries waiting beyond this are refused at submission (the queue
         # holds at most a few batches' worth)
         self.max_pending = max_pending if max_pending is not None else 4 * workers * self.slots
@@ -89,6 +98,8 @@ class Server:
         for w in range(workers):
             stream = torch.cuda.Stream(device=dev)
             batch = Batch.replicas(graph, self.slots, stream=stream)
+            if schedule:
+                batch.set_schedule(schedule)
             n_all = self.slots * self.n
             with torch.cuda.stream(stream):
                 bufs = dict(cost=torch.empty(n_all, dtype=torch.float64, device=dev),
@@ -123,6 +134,11 @@ class Server:
             b.close()
         self._workers = []
 
+    def _admissible(self, want: int) -> int:
+        """How many more queries the device's free memory admits now (of want)."""
+        free, _ = self.torch.cuda.mem_get_info(self.device)
+        return max(0, min(want, int((free - _RESERVE_BYTES) // self.query_bytes)))
+
     def _run(self, stream, batch, bufs):
         torch = self.torch
         torch.cuda.set_device(self.device)
@@ -133,7 +149,14 @@ class Server:
                     self._cv.wait()
                 if self._stop and not self._q:
                     return
-                take = [self._q.popleft() for _ in range(min(self.slots, len(self._q)))]
+                r = self._admissible(min(self.slots, len(self._q)))
+                if r == 0:
+                    # not enough free memory for one more query: wait for
+                    # another worker to finish (its solve state returns)
+                    self.waited_for_memory += 1
+                    self._cv.wait(0.005)
+                    continue
+                take = [self._q.popleft() for _ in range(r)]
             r = len(take)
             try:
                 with torch.cuda.stream(stream):
@@ -160,6 +183,8 @@ class Server:
                     q.batch_size = r
                     q.t_done = now
                     q._done.set()
+                with self._cv:
+                    self._cv.notify_all()  # memory may have freed for a waiting worker
             except Exception as e:  # the worker keeps serving; the queries carry the error
                 for q in take:
                     q.error = e

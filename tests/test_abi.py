@@ -116,3 +116,16 @@ def test_oracle_is_not_imported_by_the_product():
     for f in os.listdir(os.path.join(ROOT, "oracle")):
         if f.endswith((".py", ".c")):
             assert not bad2.search(open(os.path.join(ROOT, "oracle", f)).read()), f
+
+
+def test_schedule_struct_and_null_handles():
+    lib = fl.load()
+    assert ctypes.sizeof(fl.Schedule) == 24
+    sc = fl.Schedule(0, 16, 8, 16, 0, 0)
+    assert lib.fl_set_schedule(None, ctypes.byref(sc)) == fl.FL_EINVAL
+    assert lib.fl_get_schedule(None, ctypes.byref(sc)) == fl.FL_EINVAL
+    assert lib.fl_batch_set_schedule(None, ctypes.byref(sc)) == fl.FL_EINVAL
+    assert lib.fl_autotune(None, 16, 1, None, None, 0, 4, None, None, None) == fl.FL_EINVAL
+    assert lib.fl_eps_stats(None, None, None, None, None, None) == fl.FL_EINVAL
+    assert lib.fl_open_facilities_eps(None, 0.1, None, None, 0, None, None, None, None) == fl.FL_EINVAL
+    assert lib.fl_autotune_forget() == fl.FL_OK
