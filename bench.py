@@ -572,6 +572,7 @@ def run_batch(args):
         brep = fl.Batch.replicas(g, R)
         brep.set_schedule(g.schedule)
         buni = fl.Batch.union(er_csr, stream=stream)
+        buni_sched = dict(hop_group=0, sparse_div=16, dense_div=8, edge_div=16, graph_bfs=0, level_cap=0)
         N_r, N_u = brep.n_total, buni.n_total
         out = {f: torch.empty(N_r + N_u, dtype=dt, device=dev)
                for f, dt in (("open", torch.uint8), ("assign", torch.int32), ("dist", torch.int32))}
@@ -621,8 +622,15 @@ def run_batch(args):
     clocks.start()
     ms_batch = timed(batched)
     ms_plain = timed(one_by_one)
+    # the same batches with the assignment BFS as one CUDA graph (device-side level loop)
+    host_out = {f: t.clone() for f, t in out.items()}
+    sched_graph = dict(g.schedule, graph_bfs=1)
+    brep.set_schedule(sched_graph)
+    buni.set_schedule(dict(buni_sched, graph_bfs=1))
+    ms_graph = timed(batched)
+    graph_same = all(torch.equal(out[f], host_out[f]) for f in out)
     clk = clocks.stop()
-    same = all(torch.equal(out[f], plain[f]) for f in out)
+    same = all(torch.equal(host_out[f], plain[f]) for f in out)
     obj_ok = bool(np.all(np.abs(batch_obj - plain_obj) <= 1e-9 * np.abs(plain_obj)))
     n_inst = R + len(bw.graphs)
     if rank == 0:
@@ -638,6 +646,10 @@ def run_batch(args):
                 "plain": {"value": n_inst / (ms_plain / 1e3), "unit": "solves/s", "ms_per_step": ms_plain,
                           "form": "one fl_* sequence per instance on one stream"},
                 "speedup_vs_plain": ms_plain / ms_batch,
+                "graph_form": {"value": n_inst / (ms_graph / 1e3), "unit": "solves/s", "ms_per_step": ms_graph,
+                               "form": "the same batches, the assignment BFS as one CUDA graph (conditional WHILE "
+                                       "node: the level loop on the device)",
+                               "identical_to_host_driven": bool(graph_same)},
                 "identical_to_plain": bool(same and obj_ok), "schedule": g.schedule, "autotune": tune,
                 "clocks": clk}
         print(json.dumps(line), flush=True)
@@ -690,8 +702,9 @@ def run_serve(args):
         tune = g.autotune(k, seed, torch.full((n,), qs[0].cost, dtype=torch.float64, device=dev), m0,
                           max_trials=args.tune_trials)
         torch.cuda.synchronize()
+    sched = g.schedule
     srv = serve.Server(g, k, seed, workers=args.serve_workers, max_slots=args.serve_slots, keep_open_mask=True,
-                       schedule=g.schedule)
+                       schedule=sched)
     clocks = Clocks(local)
     clocks.start()
     t0 = time.perf_counter()
@@ -746,7 +759,7 @@ def run_serve(args):
                                 "every vertex a facility, one cost log-uniform in [10, 1000]",
                        "workers": args.serve_workers, "slots_per_worker": srv.slots,
                        "max_pending": srv.max_pending, "admission": "per query, by free device memory",
-                       "waited_for_memory": srv.waited_for_memory, "schedule": g.schedule, "autotune": tune},
+                       "waited_for_memory": srv.waited_for_memory, "schedule": sched, "autotune": tune},
             "latency_ms": {"p50": lat.get("p50_ms"), "p99": lat.get("p99_ms"), "mean": lat.get("mean_ms"),
                            "max": lat.get("max_ms")},
             "offered": len(measured), "served": len(served), "refused": srv.rejected,
