@@ -240,6 +240,28 @@ def run_reference(args):
     return 0
 
 
+def mis_summary(rows):
+    """Per greedy round of the last step's MIS: undecided facilities at its
+    start, those it decided, its largest ball radius T, host ms, the bucket
+    sizes by ball radius, and per cover / gather round [step, frontier,
+    pulled, ms] (fl_mis_log rows)."""
+    if rows is None or len(rows) == 0:
+        return None
+    out = []
+    for rd in sorted(set(int(x) for x in rows[:, 0])):
+        R = rows[rows[:, 0] == rd]
+        tot = R[R[:, 1] == 3]
+        d = {"round": rd}
+        if len(tot):
+            d.update(undecided=int(tot[0, 3]), decided=int(tot[0, 4]), T=int(tot[0, 2]),
+                     ms=round(tot[0, 5] / 1e3, 2))
+        d["buckets"] = {int(b): int(c) for b, c in R[R[:, 1] == 2][:, 2:4]}
+        for kind, name in ((0, "cover"), (1, "gather")):
+            d[name] = [[int(x[2]), int(x[3]), int(x[4]), round(x[5] / 1e3, 2)] for x in R[R[:, 1] == kind]]
+        out.append(d)
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -288,6 +310,7 @@ def run_gpu(args):
         info["n_open"] = nopen
         info["objective"] = obj[0]
         info["mis"] = s.stats()
+        info["mis_log"] = s.mis_log()
         s.close()
 
     for _ in range(args.warmup):
@@ -414,7 +437,8 @@ def run_gpu(args):
             "schedule": g_schedule, "autotune": tune,
             "hops": stats["hops"], "edge_merges_per_step": merges_step, "ads_entries": stats["ads_entries"],
             "n_open": info.get("n_open"), "objective": info.get("objective"),
-            "mis_rounds": info.get("mis", {}).get("mis_rounds"), "hop_detail": hop_detail}
+            "mis_rounds": info.get("mis", {}).get("mis_rounds"), "hop_detail": hop_detail,
+            "mis_detail": mis_summary(info.get("mis_log"))}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

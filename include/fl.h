@@ -220,6 +220,23 @@ int fl_objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserve
 int fl_solve_stats(const fl_solve* s, int64_t* mis_rounds, int64_t* candidates);
 
 /*
+ * fl_mis_log -- the rounds of the last greedy MIS (fl_open_facilities), six
+ * int64 per row: (greedy round, kind, step, frontier size at the start,
+ * pulled (1) or pushed (0), host microseconds).  kind 0: a round of the cover
+ * sweep (step = time t); 1: a round of the gather sweep (step = radius b);
+ * 2: a bucket of the undecided facilities (step = ball radius, frontier =
+ * its size); 3: the greedy round's total (step = its largest ball radius T,
+ * frontier = undecided facilities at its start, pulled = those it decided);
+ * 4: a round of the kill sweep that removes the facilities whose ball holds
+ * a client claimed in that greedy round (step = distance, frontier = the
+ * vertices it marked).
+ *   rows    int64[6 * cap] or NULL; the first min(cap, *n_rows) rows are written.
+ *   n_rows  receives the number of rows of the last MIS.
+ * Host-side timings include the launches and the synchronisation of a round.
+ */
+int fl_mis_log(const fl_solve* s, int64_t cap, int64_t* n_rows, int64_t* rows);
+
+/*
  * Exact neighbourhood sizes and exact-count radii.  The paper checks the
  * ADS estimates against exact neighbourhood sizes on sampled vertices
  * (Section 5.1, "Accuracy vs. k", Fig. 1: relative error |S_E - S_ADS| / S_E

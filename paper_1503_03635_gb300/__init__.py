@@ -26,7 +26,7 @@ FL_MEM_HOST, FL_MEM_DEVICE = 0, 1
 EXPORTS = ("fl_graph_create", "fl_graph_destroy", "fl_build_sketches", "fl_sketch_stats",
            "fl_export_sketches", "fl_export_ads", "fl_solve_create", "fl_solve_destroy",
            "fl_compute_radii", "fl_open_facilities", "fl_assign_clients", "fl_objective",
-           "fl_solve_stats", "fl_status_str", "fl_last_error", "fl_profile_enable", "fl_profile_reset",
+           "fl_solve_stats", "fl_mis_log", "fl_status_str", "fl_last_error", "fl_profile_enable", "fl_profile_reset",
            "fl_profile_query", "fl_hop_stats", "fl_hop_model", "fl_batch_create_union", "fl_batch_create_replicas",
            "fl_batch_solve", "fl_batch_info", "fl_batch_destroy", "fl_assign_nearest_noalloc",
            "fl_ball_sizes", "fl_ball_estimates", "fl_compute_radii_exact", "fl_open_facilities_eps",
@@ -83,6 +83,7 @@ def load(build_if_missing: bool = True):
             "fl_assign_clients": ([vp, vp, vp, ci], ci),
             "fl_objective": ([vp, ctypes.POINTER(ctypes.c_double), P64, P64], ci),
             "fl_solve_stats": ([vp, P64, P64], ci),
+            "fl_mis_log": ([vp, i64, P64, vp], ci),
             "fl_status_str": ([ci], ctypes.c_char_p),
             "fl_last_error": ([ctypes.c_char_p, ctypes.c_size_t], ci),
             "fl_profile_enable": ([vp, ci], ci),
@@ -403,6 +404,16 @@ class Solve:
         r, c = ctypes.c_int64(), ctypes.c_int64()
         _check(self._lib.fl_solve_stats(self._h, ctypes.byref(r), ctypes.byref(c)))
         return dict(mis_rounds=r.value, candidates=c.value)
+
+    def mis_log(self) -> np.ndarray:
+        """Rounds of the last greedy MIS: int64 rows (greedy round, kind,
+        step, frontier, pulled, microseconds); kinds as fl_mis_log."""
+        n = ctypes.c_int64()
+        _check(self._lib.fl_mis_log(self._h, 0, ctypes.byref(n), None))
+        rows = np.zeros((n.value, 6), dtype=np.int64)
+        if n.value:
+            _check(self._lib.fl_mis_log(self._h, n.value, ctypes.byref(n), rows.ctypes.data_as(ctypes.c_void_p)))
+        return rows
 
 
 class Batch:

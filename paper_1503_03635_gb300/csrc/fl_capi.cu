@@ -1,4 +1,5 @@
 // fl_capi.cu -- the extern "C" entry points declared in include/fl.h.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -935,6 +936,18 @@ int fl_solve_stats(const fl_solve* s, int64_t* mis_rounds, int64_t* candidates) 
     if (!s) FL_FAIL(FL_EINVAL, "null solve handle");
     if (mis_rounds) *mis_rounds = s->mis_rounds;
     if (candidates) *candidates = s->n_cand;
+    return FL_OK;
+}
+
+int fl_mis_log(const fl_solve* s, int64_t cap, int64_t* n_rows, int64_t* rows) {
+    if (!s || !n_rows) FL_FAIL(FL_EINVAL, "null argument");
+    if (cap < 0) FL_FAIL(FL_EINVAL, "cap must be >= 0");
+    const int64_t total = (int64_t)s->mis_log.size() / 6;
+    *n_rows = total;
+    if (rows && cap > 0) {
+        const int64_t k = std::min(cap, total);
+        std::copy(s->mis_log.begin(), s->mis_log.begin() + 6 * k, rows);
+    }
     return FL_OK;
 }
 

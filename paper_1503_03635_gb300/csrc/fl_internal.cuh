@@ -234,6 +234,35 @@ __device__ __forceinline__ long long warp_append(bool pred, unsigned long long* 
     return pred ? (long long)(base + __popc(m & ((1u << lane) - 1u))) : -1LL;
 }
 
+// Append with one global atomic per block and call: the block's warps take
+// consecutive places.  Every thread of the block calls it the same number of
+// times (a block-uniform loop); blockDim.x = 32 * W.  Which places a block
+// gets depends on the order of the blocks' atomics, like warp_append.
+template <int W>
+struct BlockAppend {
+    unsigned cnt[W];
+    unsigned long long off[W];
+};
+
+template <int W>
+__device__ __forceinline__ long long block_append(bool pred, unsigned long long* counter, BlockAppend<W>& sh) {
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const unsigned m = __ballot_sync(kFull, pred);
+    if (lane == 0) sh.cnt[warp] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long total = 0;
+        for (int w = 0; w < W; ++w) {
+            sh.off[w] = total;
+            total += sh.cnt[w];
+        }
+        const unsigned long long base = total ? atomicAdd(counter, total) : 0ULL;
+        for (int w = 0; w < W; ++w) sh.off[w] += base;
+    }
+    __syncthreads();
+    return pred ? (long long)(sh.off[warp] + __popc(m & ((1u << lane) - 1u))) : -1LL;
+}
+
 // ----------------------------------------------------------------- group primitives
 // A group is G consecutive lanes of a warp (G = 16 or 32) that works on one
 // vertex; a G-lane list holds up to G uint64 values, one per lane, ascending,
@@ -333,6 +362,9 @@ struct Counters {
     unsigned long long mask_scanned; // hop census: of those, read by the mask merge
     unsigned long long delta_next;   // merge: sum of deg(u) * |D_h(u)| over changed u (delta ranks of the next hop's edge-merges)
     unsigned long long new_entries;  // merge: entries gained this hop (sum of |D_h(v)|)
+    unsigned long long key_or[2];    // keys: OR of the candidates' (hi, lo) key words
+    unsigned long long key_orn[2];   // keys: OR of their complements (a bit set in both varies)
+    unsigned long long key_ties;     // keys: adjacent equal hi words after sorting by hi
 };
 
 // ----------------------------------------------------------------- profiling
@@ -498,6 +530,9 @@ struct fl_solve {
     fl::DBuf cost, client;         // double[n], uint8[n]
     fl::DBuf radii;                // double[n]
     fl::DBuf ord, fac_by_ord, bcap, state, claimed;  // MIS state
+    fl::DBuf reach;                // uint8[n]: 1 + slack of a vertex in the current cover (gather pruning)
+    fl::DBuf kill;                 // uint8[n]: 1 + distance to a client claimed in the current round
+    std::vector<int64_t> mis_log;  // rows of 6: the rounds of the last MIS (fl_mis_log)
     fl::DBuf X, stamp, mval, fr[2], frval, touched, ulist, ubuck, bcount;
     fl::DBuf key_hi, key_lo, key_val, obj_tmp;  // key sort and objective scratch
     fl::DBuf part_T;               // int32[n_parts]: largest ball radius of a part's undecided facilities
@@ -527,6 +562,12 @@ int scan_exclusive_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaSt
 // count) may skip digits known to be equal.
 int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaStream_t st, DBuf& tmp,
                     int cls = kProfKeys, int pass_begin = 0, int pass_end = 32);
+// The same sort over the digits whose bit is set in `digits` (bit p: pass p
+// of the full sort, 0-15 lo's digits, 16-31 hi's), least significant first.
+// Leaving out digits that are equal in every key changes nothing: a pass
+// over such a digit is the identity.
+int sort_pairs_u128_digits(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaStream_t st, DBuf& tmp,
+                           int cls, uint32_t digits);
 
 int validate_csr(fl_graph* g);
 int build_work_lists(fl_graph* g);
@@ -541,6 +582,16 @@ int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, i
 int msbfs_graph(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, int32_t* dist, DBuf& X,
                 DBuf& stampb, int cls);
 void graph_bfs_release(GraphBfs* c);
+
+// Per-vertex pruning of the rounds of a sweep (the MIS cover and gather
+// sweeps).  A round that first gives v a value below the limit records
+// reach[v] = reach_val; a round skips every v with need[v] <= round: it does
+// not lower v's value, and a push does not offer v one.
+struct Prune {
+    uint8_t* reach = nullptr;
+    const uint8_t* need = nullptr;
+    uint32_t reach_val = 0, round = 0;
+};
 
 // State of a sequence of synchronous min-propagation rounds (k_relax.cu).
 struct Relax {
@@ -567,12 +618,18 @@ struct Relax {
     int32_t* part_cnt = nullptr;                    // device int32[n_parts]: frontier vertices per part
     const int32_t* part_limit = nullptr;            // device int32[n_parts] or NULL: a part whose limit is
     int32_t part_round = 0;                         //   below part_round sits the pull rounds out
+    Prune prune;                                    // per-vertex reach / need of the sweep
+    bool last_dense = false;                        // the last round pulled
 };
 // Binds the graph-owned scratch of the rounds to r; call once per sweep
 // family, after r.stamp values of earlier users may have been reused.
 int relax_begin(fl_graph* g, Relax& r);
 int relax_round(fl_graph* g, Relax& r, unsigned long long add, uint32_t sv, int cls);
 int relax_prepare_list(fl_graph* g, Relax& r, int cls);
+// One round of a bounded marking BFS over g (k_relax.cu): kr[v] = b + 1 for
+// every unmarked v with need[v] > b (need may be NULL) and a neighbour whose
+// kr is in [1, b]; *marked = the marks made (hubs may count more than once).
+int mark_round(fl_graph* g, Relax& r, uint8_t* kr, const uint8_t* need, uint32_t b, int cls, int64_t* marked);
 int relax_collect_epoch(fl_graph* g, const unsigned long long* X, unsigned long long hi, int32_t* out,
                         unsigned long long* n_out, int cls);
 int assign_clients(fl_solve* s);

@@ -31,6 +31,7 @@ __device__ __forceinline__ bool in_front(const uint32_t* __restrict__ bm, int32_
     return (__ldg(&bm[u >> 5]) >> (u & 31)) & 1u;
 }
 
+
 // Frontier bitmap of a pull round: bit v = (stamp[v] == sv).  Only neighbours
 // whose value changed in the previous round can lower a value, so a pull
 // reads the value of a neighbour only when its bit is set; the bitmap (n/8
@@ -63,24 +64,35 @@ __device__ __forceinline__ bool part_idle(const int32_t* __restrict__ vpart, con
     return vpart && __ldg(&part_cnt[__ldg(&vpart[v])]) == 0;
 }
 
+__device__ __forceinline__ bool skipped(const Prune& pr, int32_t u) {
+    return pr.need && __ldg(&pr.need[u]) <= pr.round;
+}
+
 // Values >= `limit` are ignored: unset entries (BFS) or values of an earlier
 // sweep (MIS sweeps stamp each sweep into the high word).  With `settle`, a
 // vertex holding a value below the limit is final and is skipped.
 //
 // Lowest value offered by the frontier neighbours cols[e], e in [e0, e1) with
-// stride `step`, four edges per lane and pass: the four column loads, then the
-// four bitmap loads, then the value loads are independent, so each lane keeps
-// up to four dependent-load chains in flight.
+// stride `step`, four edges per lane and pass: the four bitmap loads, then
+// the value loads are independent, so each lane keeps up to four dependent-
+// load chains in flight; the columns of the next pass are loaded at the start
+// of a pass, so their DRAM latency overlaps this pass's bitmap and value loads.
 __device__ __forceinline__ unsigned long long pull_min(const int32_t* __restrict__ cols, int64_t e0, int64_t e1,
                                                        int step, const uint32_t* __restrict__ bm,
                                                        const unsigned long long* __restrict__ X,
                                                        unsigned long long add, unsigned long long limit,
                                                        unsigned long long m) {
+    int32_t nx[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) nx[j] = e0 + j * step < e1 ? __ldcs(&cols[e0 + j * step]) : -1;
     for (int64_t e = e0; e < e1; e += 4 * step) {
         int32_t u[4];
         bool f[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) u[j] = e + j * step < e1 ? __ldcs(&cols[e + j * step]) : -1;
+        for (int j = 0; j < 4; ++j) u[j] = nx[j];
+        const int64_t en = e + 4 * step;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) nx[j] = en + j * step < e1 ? __ldcs(&cols[en + j * step]) : -1;
 #pragma unroll
         for (int j = 0; j < 4; ++j) f[j] = u[j] >= 0 && in_front(bm, u[j]);
 #pragma unroll
@@ -108,13 +120,13 @@ __global__ void __launch_bounds__(256) k_pull_small(const int32_t* __restrict__ 
                                                     uint32_t* __restrict__ stamp, uint32_t sv,
                                                     unsigned long long* __restrict__ n_changed,
                                                     const int32_t* __restrict__ vpart,
-                                                    const int32_t* __restrict__ part_cnt) {
+                                                    const int32_t* __restrict__ part_cnt, Prune pr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long changed = 0;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_list; base += stride) {
         const int64_t i = base + lane_id();
         const int32_t v = i < n_list ? list[i] : 0;
-        const bool have = i < n_list && !part_idle(vpart, part_cnt, v);
+        const bool have = i < n_list && !part_idle(vpart, part_cnt, v) && !skipped(pr, v);
         const unsigned long long own = have ? X[v] : ~0ULL;
         const bool work = have && !(settle && own < limit);
         const int64_t beg = work ? rowp[v] : 0, end = work ? rowp[v + 1] : 0;
@@ -123,6 +135,7 @@ __global__ void __launch_bounds__(256) k_pull_small(const int32_t* __restrict__ 
         if (ch) {
             Xn[v] = m;
             stamp[v] = sv;
+            if (pr.reach && own >= limit) pr.reach[v] = (uint8_t)pr.reach_val;
         }
         changed += __popc(__ballot_sync(kFull, ch));
     }
@@ -140,7 +153,7 @@ __global__ void __launch_bounds__(256) k_pull_low(const int32_t* __restrict__ li
                                                   unsigned long long* __restrict__ Xn, uint32_t* __restrict__ stamp,
                                                   uint32_t sv, unsigned long long* __restrict__ n_changed,
                                                   const int32_t* __restrict__ vpart,
-                                                  const int32_t* __restrict__ part_cnt) {
+                                                  const int32_t* __restrict__ part_cnt, Prune pr) {
     const int lane = lane_id();
     const int sub = lane & 7;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -148,7 +161,7 @@ __global__ void __launch_bounds__(256) k_pull_low(const int32_t* __restrict__ li
     for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 4 < n_list; w += warps) {
         const int64_t i = w * 4 + (lane >> 3);
         const int32_t v = i < n_list ? list[i] : 0;
-        const bool have = i < n_list && !part_idle(vpart, part_cnt, v);
+        const bool have = i < n_list && !part_idle(vpart, part_cnt, v) && !skipped(pr, v);
         const unsigned long long own = have ? X[v] : ~0ULL;
         const bool work = have && !(settle && own < limit);
         const int64_t beg = work ? rowp[v] : 0, end = work ? rowp[v + 1] : 0;
@@ -159,6 +172,7 @@ __global__ void __launch_bounds__(256) k_pull_low(const int32_t* __restrict__ li
         if (ch) {
             Xn[v] = m;
             stamp[v] = sv;
+            if (pr.reach && own >= limit) pr.reach[v] = (uint8_t)pr.reach_val;
         }
         changed += __popc(__ballot_sync(kFull, ch));
     }
@@ -178,14 +192,14 @@ __global__ void __launch_bounds__(256) k_pull_segs(const int32_t* __restrict__ s
                                                    unsigned long long* __restrict__ Xn, uint32_t* __restrict__ stamp,
                                                    uint32_t sv, unsigned long long* __restrict__ n_changed,
                                                    const int32_t* __restrict__ vpart,
-                                                   const int32_t* __restrict__ part_cnt) {
+                                                   const int32_t* __restrict__ part_cnt, Prune pr) {
     const int lane = lane_id();
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t sidx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sidx < n_seg; sidx += warps) {
         const int32_t h = seg_hub[sidx];
         const int32_t v = hub_list[h];
         const unsigned long long own = X[v];
-        if ((settle && own < limit) || part_idle(vpart, part_cnt, v)) continue;
+        if ((settle && own < limit) || part_idle(vpart, part_cnt, v) || skipped(pr, v)) continue;
         const int64_t e0 = rowp[v] + (sidx - hub_seg[h]) * kSeg;
         const int64_t e1 = min(e0 + (int64_t)kSeg, rowp[v + 1]);
         unsigned long long m = pull_min(cols, e0 + lane, e1, 32, bm, X, add, limit, ~0ULL);
@@ -195,6 +209,7 @@ __global__ void __launch_bounds__(256) k_pull_segs(const int32_t* __restrict__ s
             const unsigned long long old = atomicMin(&Xn[v], m);
             if (old == own) {
                 stamp[v] = sv;
+                if (pr.reach && own >= limit) pr.reach[v] = (uint8_t)pr.reach_val;
                 atomicAdd(n_changed, 1ULL);
             }
         }
@@ -244,9 +259,11 @@ __global__ void __launch_bounds__(256) k_push_low(const int32_t* __restrict__ fr
                                                   const unsigned long long* __restrict__ frval,
                                                   const unsigned long long* __restrict__ n_fr,
                                                   const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
-                                                  unsigned long long add, unsigned long long* __restrict__ X,
+                                                  unsigned long long add, unsigned long long limit,
+                                                  unsigned long long* __restrict__ X,
                                                   uint32_t* __restrict__ stamp, uint32_t sv,
-                                                  int32_t* __restrict__ fr_next, unsigned long long* __restrict__ n_next) {
+                                                  int32_t* __restrict__ fr_next, unsigned long long* __restrict__ n_next,
+                                                  Prune pr) {
     const int lane = lane_id();
     const int64_t n = (int64_t)*n_fr;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -261,9 +278,12 @@ __global__ void __launch_bounds__(256) k_push_low(const int32_t* __restrict__ fr
             int32_t u = 0;
             if (e < end) {
                 u = cols[e];
-                if (val < X[u]) {
+                if (val < X[u] && !skipped(pr, u)) {
                     const unsigned long long old = atomicMin(&X[u], val);
-                    if (val < old) fresh = atomicExch(&stamp[u], sv) != sv;
+                    if (val < old) {
+                        if (pr.reach && old >= limit) pr.reach[u] = (uint8_t)pr.reach_val;
+                        fresh = atomicExch(&stamp[u], sv) != sv;
+                    }
                 }
             }
             const long long at = warp_append(fresh, n_next);
@@ -279,9 +299,11 @@ __global__ void __launch_bounds__(256) k_push_segs(const int32_t* __restrict__ s
                                                    const uint32_t* __restrict__ hub_tag, uint32_t tag,
                                                    const unsigned long long* __restrict__ hub_val,
                                                    const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
-                                                   unsigned long long add, unsigned long long* __restrict__ X,
+                                                   unsigned long long add, unsigned long long limit,
+                                                   unsigned long long* __restrict__ X,
                                                    uint32_t* __restrict__ stamp, uint32_t sv,
-                                                   int32_t* __restrict__ fr_next, unsigned long long* __restrict__ n_next) {
+                                                   int32_t* __restrict__ fr_next, unsigned long long* __restrict__ n_next,
+                                                   Prune pr) {
     const int lane = lane_id();
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t sidx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sidx < n_seg; sidx += warps) {
@@ -297,9 +319,12 @@ __global__ void __launch_bounds__(256) k_push_segs(const int32_t* __restrict__ s
             int32_t u = 0;
             if (e < e1) {
                 u = cols[e];
-                if (val < X[u]) {
+                if (val < X[u] && !skipped(pr, u)) {
                     const unsigned long long old = atomicMin(&X[u], val);
-                    if (val < old) fresh = atomicExch(&stamp[u], sv) != sv;
+                    if (val < old) {
+                        if (pr.reach && old >= limit) pr.reach[u] = (uint8_t)pr.reach_val;
+                        fresh = atomicExch(&stamp[u], sv) != sv;
+                    }
                 }
             }
             const long long at = warp_append(fresh, n_next);
@@ -311,11 +336,12 @@ __global__ void __launch_bounds__(256) k_push_segs(const int32_t* __restrict__ s
 // Vertices flagged with stamp sv -> list.
 __global__ void k_collect_stamped(const uint32_t* __restrict__ stamp, uint32_t sv, int64_t n,
                                   int32_t* __restrict__ out, unsigned long long* __restrict__ n_out) {
+    __shared__ BlockAppend<8> sh;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-        const int64_t v = base + lane_id();
+    for (int64_t bb = (int64_t)blockIdx.x * blockDim.x; bb < n; bb += stride) {
+        const int64_t v = bb + threadIdx.x;
         const bool in = v < n && stamp[v] == sv;
-        const long long at = warp_append(in, n_out);
+        const long long at = block_append<8>(in, n_out, sh);
         if (at >= 0) out[at] = (int32_t)v;
     }
 }
@@ -327,11 +353,12 @@ constexpr int64_t kPushAlways = 4096;  // smaller frontiers push without countin
 // Vertices whose value carries high word `hi` -> list (the vertices a sweep reached).
 __global__ void k_collect_epoch(const unsigned long long* __restrict__ X, unsigned long long hi, int64_t n,
                                 int32_t* __restrict__ out, unsigned long long* __restrict__ n_out) {
+    __shared__ BlockAppend<8> sh;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-        const int64_t v = base + lane_id();
+    for (int64_t bb = (int64_t)blockIdx.x * blockDim.x; bb < n; bb += stride) {
+        const int64_t v = bb + threadIdx.x;
         const bool in = v < n && (X[v] >> 32) == hi;
-        const long long at = warp_append(in, n_out);
+        const long long at = block_append<8>(in, n_out, sh);
         if (at >= 0) out[at] = (int32_t)v;
     }
 }
@@ -409,13 +436,13 @@ int relax_round(fl_graph* g, Relax& r, unsigned long long add, uint32_t sv, int 
     }
     if (!dense) {
         FL_LAUNCH(cls, k_push_low<<<grid_for(r.n_front, 8), 256, 0, st>>>(r.fr[r.fc], r.frval, &r.cnt[r.fc], rowp, cols,
-                                                                         add, X, r.stamp, sv, r.fr[r.fc ^ 1],
-                                                                         &r.cnt[r.fc ^ 1]));
+                                                                         add, r.limit, X, r.stamp, sv, r.fr[r.fc ^ 1],
+                                                                         &r.cnt[r.fc ^ 1], r.prune));
         if (g->n_seg > 0)
             FL_LAUNCH(cls, k_push_segs<<<grid_for(g->n_seg, 8), 256, 0, st>>>(
                                g->seg_hub.as<int32_t>(), g->n_seg, g->hub_seg.as<int64_t>(), hub_list, r.hub_tag,
-                               r.sv_prev, r.hub_val, rowp, cols, add, X, r.stamp, sv, r.fr[r.fc ^ 1],
-                               &r.cnt[r.fc ^ 1]));
+                               r.sv_prev, r.hub_val, rowp, cols, add, r.limit, X, r.stamp, sv, r.fr[r.fc ^ 1],
+                               &r.cnt[r.fc ^ 1], r.prune));
         FL_CUDA(cudaGetLastError());
         r.fc ^= 1;
         r.list_valid = true;
@@ -431,15 +458,16 @@ int relax_round(fl_graph* g, Relax& r, unsigned long long add, uint32_t sv, int 
         if (g->n_small > 0)
             FL_LAUNCH(cls, k_pull_small<<<grid_for(g->n_small, 256), 256, 0, st>>>(
                                g->small_list.as<int32_t>(), g->n_small, rowp, cols, add, r.limit, r.settle, r.bm, X,
-                               Xn, r.stamp, sv, &r.cnt[2], vpart, r.part_cnt));
+                               Xn, r.stamp, sv, &r.cnt[2], vpart, r.part_cnt, r.prune));
         if (g->n_mid > 0)
             FL_LAUNCH(cls, k_pull_low<<<grid_for((g->n_mid + 3) / 4, 8), 256, 0, st>>>(
                                g->mid_list.as<int32_t>(), g->n_mid, rowp, cols, add, r.limit, r.settle, r.bm, X, Xn,
-                               r.stamp, sv, &r.cnt[2], vpart, r.part_cnt));
+                               r.stamp, sv, &r.cnt[2], vpart, r.part_cnt, r.prune));
         if (g->n_seg > 0)
             FL_LAUNCH(cls, k_pull_segs<<<grid_for(g->n_seg, 8), 256, 0, st>>>(
                                g->seg_hub.as<int32_t>(), g->n_seg, g->hub_seg.as<int64_t>(), hub_list, rowp, cols, add,
-                               r.limit, r.settle, r.bm, X, Xn, r.stamp, sv, &r.cnt[2], vpart, r.part_cnt));
+                               r.limit, r.settle, r.bm, X, Xn, r.stamp, sv, &r.cnt[2], vpart, r.part_cnt,
+                               r.prune));
         FL_CUDA(cudaGetLastError());
         r.cur ^= 1;
         r.list_valid = false;
@@ -448,6 +476,169 @@ int relax_round(fl_graph* g, Relax& r, unsigned long long add, uint32_t sv, int 
     FL_CUDA(cudaStreamSynchronize(st));
     r.n_front = (int64_t)*r.h_cnt;
     r.sv_prev = sv;
+    r.last_dense = dense;
+    return FL_OK;
+}
+
+// ------------------------------------------------------------------ marking rounds
+// A bounded BFS that only records whether a vertex lies within distance b of
+// the seeds: kr[v] = 1 + its distance, 0 while it is farther than the rounds
+// run so far (seeds carry 1).  Round b marks every unmarked vertex with
+// need[v] > b that has a neighbour marked in an earlier round (kr in [1, b],
+// read from a bitmap); a vertex stops reading its row at the first such
+// neighbour, so a dense round costs far less than a min-propagation round.
+
+namespace {
+
+__global__ void k_mark_bitmap(const uint8_t* __restrict__ kr, int64_t n, uint32_t b, uint32_t* __restrict__ bm) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t v = base + lane_id();
+        const uint32_t k = v < n ? kr[v] : 0u;
+        const unsigned w = __ballot_sync(kFull, k != 0 && k <= b);
+        if (lane_id() == 0) bm[base >> 5] = w;
+    }
+}
+
+__device__ __forceinline__ bool unmarked_needed(const uint8_t* __restrict__ kr, const uint8_t* __restrict__ need,
+                                                int32_t v, uint32_t b) {
+    return kr[v] == 0 && (!need || __ldg(&need[v]) > b);
+}
+
+// Vertices of at most kSmallDeg neighbours: a thread each.
+__global__ void __launch_bounds__(256) k_mark_small(const int32_t* __restrict__ list, int64_t n_list,
+                                                    const int64_t* __restrict__ rowp,
+                                                    const int32_t* __restrict__ cols,
+                                                    const uint32_t* __restrict__ bm, uint8_t* __restrict__ kr,
+                                                    const uint8_t* __restrict__ need, uint32_t b,
+                                                    unsigned long long* __restrict__ n_marked) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long marked = 0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_list; base += stride) {
+        const int64_t i = base + lane_id();
+        const int32_t v = i < n_list ? list[i] : 0;
+        bool hit = false;
+        if (i < n_list && unmarked_needed(kr, need, v, b)) {
+            const int64_t beg = rowp[v], end = rowp[v + 1];
+            for (int64_t e = beg; e < end && !hit; e += 4) {
+                int32_t u[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) u[j] = e + j < end ? __ldcs(&cols[e + j]) : -1;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) hit |= u[j] >= 0 && in_front(bm, u[j]);
+            }
+            if (hit) kr[v] = (uint8_t)(b + 1);
+        }
+        marked += __popc(__ballot_sync(kFull, hit));
+    }
+    if (lane_id() == 0 && marked) atomicAdd(n_marked, marked);
+}
+
+// Other non-hub vertices: eight lanes each (four per warp), 32 entries of a
+// row per pass; a group leaves at the first pass that finds a marked neighbour.
+__global__ void __launch_bounds__(256) k_mark_low(const int32_t* __restrict__ list, int64_t n_list,
+                                                  const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
+                                                  const uint32_t* __restrict__ bm, uint8_t* __restrict__ kr,
+                                                  const uint8_t* __restrict__ need, uint32_t b,
+                                                  unsigned long long* __restrict__ n_marked) {
+    const int lane = lane_id();
+    const int sub = lane & 7;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long marked = 0;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 4 < n_list; w += warps) {
+        const int64_t i = w * 4 + (lane >> 3);
+        const int32_t v = i < n_list ? list[i] : 0;
+        bool work = i < n_list && unmarked_needed(kr, need, v, b);
+        const int64_t beg = work ? rowp[v] : 0, end = work ? rowp[v + 1] : 0;
+        for (int64_t at = beg;; at += 32) {
+            bool hit = false;
+            if (work) {
+                int32_t u[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t e = at + sub + 8 * j;
+                    u[j] = e < end ? __ldcs(&cols[e]) : -1;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) hit |= u[j] >= 0 && in_front(bm, u[j]);
+            }
+            const bool group_hit = (__ballot_sync(kFull, hit) >> (lane & ~7)) & 0xffu;
+            if (work && group_hit) {
+                if (sub == 0) {
+                    kr[v] = (uint8_t)(b + 1);
+                    ++marked;
+                }
+                work = false;
+            }
+            if (at + 32 >= end) work = false;
+            if (!__any_sync(kFull, work)) break;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) marked += __shfl_xor_sync(kFull, marked, o);
+    if (lane == 0 && marked) atomicAdd(n_marked, marked);
+}
+
+// Hubs: a warp per segment of kSeg entries; every segment that finds a marked
+// neighbour marks the hub (the count may hold a hub more than once).
+__global__ void __launch_bounds__(256) k_mark_segs(const int32_t* __restrict__ seg_hub, int64_t n_seg,
+                                                   const int64_t* __restrict__ hub_seg,
+                                                   const int32_t* __restrict__ hub_list,
+                                                   const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
+                                                   const uint32_t* __restrict__ bm, uint8_t* __restrict__ kr,
+                                                   const uint8_t* __restrict__ need, uint32_t b,
+                                                   unsigned long long* __restrict__ n_marked) {
+    const int lane = lane_id();
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sidx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sidx < n_seg; sidx += warps) {
+        const int32_t h = seg_hub[sidx];
+        const int32_t v = hub_list[h];
+        if (!unmarked_needed(kr, need, v, b)) continue;
+        const int64_t e0 = rowp[v] + (sidx - hub_seg[h]) * kSeg;
+        const int64_t e1 = min(e0 + (int64_t)kSeg, rowp[v + 1]);
+        for (int64_t at = e0; at < e1; at += 128) {
+            bool hit = false;
+            int32_t u[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t e = at + lane + 32 * j;
+                u[j] = e < e1 ? __ldcs(&cols[e]) : -1;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) hit |= u[j] >= 0 && in_front(bm, u[j]);
+            if (__any_sync(kFull, hit)) {
+                if (lane == 0) {
+                    kr[v] = (uint8_t)(b + 1);
+                    atomicAdd(n_marked, 1ULL);
+                }
+                break;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int mark_round(fl_graph* g, Relax& r, uint8_t* kr, const uint8_t* need, uint32_t b, int cls, int64_t* marked) {
+    cudaStream_t st = g->stream;
+    const int64_t* rowp = g->rowp.as<int64_t>();
+    const int32_t* cols = g->cols.as<int32_t>();
+    FL_CUDA(cudaMemsetAsync(&r.cnt[2], 0, 8, st));
+    FL_LAUNCH(cls, k_mark_bitmap<<<grid_for(g->n, 256), 256, 0, st>>>(kr, g->n, b, r.bm));
+    if (g->n_small > 0)
+        FL_LAUNCH(cls, k_mark_small<<<grid_for(g->n_small, 256), 256, 0, st>>>(
+                           g->small_list.as<int32_t>(), g->n_small, rowp, cols, r.bm, kr, need, b, &r.cnt[2]));
+    if (g->n_mid > 0)
+        FL_LAUNCH(cls, k_mark_low<<<grid_for((g->n_mid + 3) / 4, 8), 256, 0, st>>>(
+                           g->mid_list.as<int32_t>(), g->n_mid, rowp, cols, r.bm, kr, need, b, &r.cnt[2]));
+    if (g->n_seg > 0)
+        FL_LAUNCH(cls, k_mark_segs<<<grid_for(g->n_seg, 8), 256, 0, st>>>(
+                           g->seg_hub.as<int32_t>(), g->n_seg, g->hub_seg.as<int64_t>(), g->hub_list.as<int32_t>(),
+                           rowp, cols, r.bm, kr, need, b, &r.cnt[2]));
+    FL_CUDA(cudaGetLastError());
+    FL_CUDA(cudaMemcpyAsync(r.h_cnt, &r.cnt[2], 8, cudaMemcpyDeviceToHost, st));
+    FL_CUDA(cudaStreamSynchronize(st));
+    *marked = (int64_t)*r.h_cnt;
     return FL_OK;
 }
 

@@ -4,6 +4,7 @@
 //   graph H-bar (Section 4.3, Algorithm 6), nearest-open-facility BFS and
 //   the objective (Section 3.1).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -80,22 +81,28 @@ __global__ void __launch_bounds__(256) k_push(const int32_t* __restrict__ fr, co
 }
 
 // Seeds: X[s] = min(X[s], val(s)); s joins the frontier when it decreases.
-__global__ void k_inject(const int32_t* __restrict__ src, int64_t n_src, const unsigned long long* __restrict__ base_val,
+// With `reach`, a seed that held no value below `limit` records reach_val.
+__global__ void k_inject(const int32_t* __restrict__ src, int64_t n_src, uint8_t* __restrict__ reach,
+                         uint32_t reach_val, unsigned long long limit,
                          unsigned long long hi, const uint32_t* __restrict__ lo_of, unsigned long long* __restrict__ X,
                          uint32_t* __restrict__ stamp, uint32_t sv, int32_t* __restrict__ fr,
                          unsigned long long* __restrict__ n_fr) {
+    __shared__ BlockAppend<8> sh;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_src; base += stride) {
-        int64_t i = base + lane_id();
+    for (int64_t bb = (int64_t)blockIdx.x * blockDim.x; bb < n_src; bb += stride) {
+        const int64_t i = bb + threadIdx.x;
         bool fresh = false;
         int32_t s = 0;
         if (i < n_src) {
             s = src[i];
             unsigned long long val = (hi << 32) | (lo_of ? lo_of[s] : (uint32_t)s);
             unsigned long long old = atomicMin(&X[s], val);
-            if (val < old) fresh = atomicExch(&stamp[s], sv) != sv;
+            if (val < old) {
+                if (reach && old >= limit) reach[s] = (uint8_t)reach_val;
+                fresh = atomicExch(&stamp[s], sv) != sv;
+            }
         }
-        long long at = warp_append(fresh, n_fr);
+        long long at = block_append<8>(fresh, n_fr, sh);
         if (at >= 0) fr[at] = s;
     }
 }
@@ -144,8 +151,9 @@ int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, i
         // labels are the sources' rank ids: ties go to the smallest original
         // (or part-local) facility id whatever the internal numbering
         const uint32_t* label_of = g->rid.p ? g->rid.as<uint32_t>() : nullptr;
-        FL_LAUNCH(cls, k_inject<<<grid_for(n_src, 256), 256, 0, st>>>(src_list, n_src, nullptr, 0ULL, label_of, r.X[0],
-                                                                      r.stamp, 1u, r.fr[0], &r.cnt[0]));
+        FL_LAUNCH(cls, k_inject<<<grid_for(n_src, 256), 256, 0, st>>>(src_list, n_src, nullptr, 0u, ~0ULL, 0ULL,
+                                                                      label_of, r.X[0], r.stamp, 1u, r.fr[0],
+                                                                      &r.cnt[0]));
         FL_CUDA(cudaGetLastError());
     }
     r.n_front = n_src;
@@ -503,9 +511,15 @@ __global__ void k_candidates(const double* __restrict__ r, int64_t n, uint64_t s
                              IdMap ids, uint64_t* __restrict__ hi,
                              uint64_t* __restrict__ lo, uint32_t* __restrict__ val, uint8_t* __restrict__ state,
                              Counters* ctr) {
+    // which key bits vary: OR of the words and of their complements, per
+    // block in shared memory, then one global OR per block
+    __shared__ unsigned long long bits[4];
+    if (threadIdx.x < 4) bits[threadIdx.x] = 0;
+    __syncthreads();
+    __shared__ BlockAppend<8> sh;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-        int64_t f = base + lane_id();
+    for (int64_t bb = (int64_t)blockIdx.x * blockDim.x; bb < n; bb += stride) {
+        int64_t f = bb + threadIdx.x;
         bool cand = false;
         double rf = 0.0;
         if (f < n) {
@@ -513,13 +527,54 @@ __global__ void k_candidates(const double* __restrict__ r, int64_t n, uint64_t s
             cand = rf < INFINITY;
             state[f] = cand ? 0 : 3;
         }
-        long long at = warp_append(cand, &ctr->aux0);
+        long long at = block_append<8>(cand, &ctr->aux0, sh);
+        const uint64_t h = cand ? (uint64_t)__double_as_longlong(rf) : 0;  // r >= 0: bit order = numeric order
+        const uint64_t l = cand ? facility_priority(seed, rank_id(ids, f)) : 0;
         if (at >= 0) {
-            hi[at] = (uint64_t)__double_as_longlong(rf);  // r >= 0: bit order = numeric order
-            lo[at] = facility_priority(seed, rank_id(ids, f));
+            hi[at] = h;
+            lo[at] = l;
             val[at] = (uint32_t)f;
         }
+        if (__ballot_sync(kFull, cand)) {
+            const uint64_t hn = cand ? ~h : 0, ln = cand ? ~l : 0;
+            uint64_t w[4] = {h, l, hn, ln};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const unsigned a = __reduce_or_sync(kFull, (unsigned)w[q]);
+                const unsigned b = __reduce_or_sync(kFull, (unsigned)(w[q] >> 32));
+                w[q] = ((uint64_t)b << 32) | a;
+            }
+            if (lane_id() == 0)
+                for (int q = 0; q < 4; ++q)
+                    if (w[q] & ~bits[q]) atomicOr(&bits[q], (unsigned long long)w[q]);
+        }
     }
+    __syncthreads();
+    if (threadIdx.x < 4 && bits[threadIdx.x]) {
+        unsigned long long* dst = threadIdx.x < 2 ? &ctr->key_or[threadIdx.x] : &ctr->key_orn[threadIdx.x - 2];
+        atomicOr(dst, bits[threadIdx.x]);
+    }
+}
+
+// Any two adjacent equal hi words (radius ties) after sorting by hi.
+__global__ void k_key_ties(const uint64_t* __restrict__ hi, int64_t m, Counters* ctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool tie = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i + 1 < m; i += stride)
+        tie |= hi[i] == hi[i + 1];
+    if (__any_sync(kFull, tie) && lane_id() == 0) atomicOr(&ctr->key_ties, 1ULL);
+}
+
+// Nibble digits (bit p: pass p of sort_pairs_u128_digits) of the key bits
+// that vary between candidates.
+static uint32_t varying_digits(const Counters& c) {
+    uint32_t d = 0;
+    for (int w = 0; w < 2; ++w) {
+        const uint64_t var = c.key_or[w] & c.key_orn[w];
+        for (int q = 0; q < 16; ++q)
+            if ((var >> (4 * q)) & 15u) d |= 1u << (q + (w == 0 ? 16 : 0));
+    }
+    return d;
 }
 
 __global__ void k_ordinals(const uint32_t* __restrict__ sorted_f, int64_t m, const double* __restrict__ r,
@@ -527,6 +582,7 @@ __global__ void k_ordinals(const uint32_t* __restrict__ sorted_f, int64_t m, con
                            int32_t* __restrict__ fac_by_ord, int32_t* __restrict__ bcap, int32_t* __restrict__ ulist,
                            unsigned long long* __restrict__ bmax) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int32_t mx = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
         int32_t f = (int32_t)sorted_f[i];
         ord[f] = (uint32_t)i;
@@ -537,8 +593,11 @@ __global__ void k_ordinals(const uint32_t* __restrict__ sorted_f, int64_t m, con
         int32_t cap = ecc_ub[f];
         int32_t b = fl >= (double)cap ? cap : (int32_t)fl;
         bcap[f] = b;
-        atomicMax(bmax, (unsigned long long)b);
+        mx = max(mx, b);
     }
+    // the largest ball radius: one atomic per warp
+    mx = (int32_t)__reduce_max_sync(kFull, (unsigned)mx);
+    if (lane_id() == 0 && mx > 0) atomicMax(bmax, (unsigned long long)mx);
 }
 
 // ------------------------------------------------------------------ MIS rounds (phase iii)
@@ -595,10 +654,11 @@ __global__ void k_gather_seed(const int32_t* __restrict__ touched, const unsigne
                               unsigned long long hi, unsigned long long* __restrict__ X, uint32_t* __restrict__ mval,
                               uint32_t* __restrict__ stamp, uint32_t sv, int32_t* __restrict__ fr,
                               unsigned long long* __restrict__ n_fr) {
+    __shared__ BlockAppend<8> sh;
     const int64_t n = (int64_t)*n_touched;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-        int64_t i = base + lane_id();
+    for (int64_t bb = (int64_t)blockIdx.x * blockDim.x; bb < n; bb += stride) {
+        int64_t i = bb + threadIdx.x;
         bool seed = false;
         int32_t v = 0;
         if (i < n) {
@@ -611,7 +671,7 @@ __global__ void k_gather_seed(const int32_t* __restrict__ touched, const unsigne
                 seed = true;
             }
         }
-        long long at = warp_append(seed, n_fr);
+        long long at = block_append<8>(seed, n_fr, sh);
         if (at >= 0) fr[at] = v;
     }
 }
@@ -636,38 +696,68 @@ __global__ void k_decide(const int32_t* __restrict__ fl, int64_t m, const unsign
     }
 }
 
+// Clients of this round's winners' balls become claimed; with `kr`, each
+// newly claimed client is a seed (kr = 1) of the round's kill sweep, and
+// *n_new counts them.
 __global__ void k_claim(const int32_t* __restrict__ touched, const unsigned long long* __restrict__ n_touched,
                         const uint8_t* __restrict__ client, uint8_t* __restrict__ claimed,
                         const uint32_t* __restrict__ mval, const int32_t* __restrict__ fac_by_ord,
-                        const uint8_t* __restrict__ state) {
+                        const uint8_t* __restrict__ state, uint8_t* __restrict__ kr,
+                        unsigned long long* __restrict__ n_new) {
     const int64_t n = (int64_t)*n_touched;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        int32_t v = touched[i];
-        if (client[v] && !claimed[v] && state[fac_by_ord[mval[v]]] == 1) claimed[v] = 1;
+    unsigned long long fresh = 0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t i = base + lane_id();
+        bool now = false;
+        if (i < n) {
+            const int32_t v = touched[i];
+            if (client[v] && !claimed[v] && state[fac_by_ord[mval[v]]] == 1) {
+                claimed[v] = 1;
+                if (kr) kr[v] = 1;
+                now = true;
+            }
+        }
+        fresh += __popc(__ballot_sync(kFull, now));
+    }
+    if (lane_id() == 0 && fresh) atomicAdd(n_new, fresh);
+}
+
+// Kill sweep decision: an undecided facility with a client claimed in this
+// round within its ball radius (kr[f] = 1 + that distance <= B_f + 1) can no
+// longer join S.
+__global__ void k_kill(const int32_t* __restrict__ ulist, int64_t n_u, const uint8_t* __restrict__ kr,
+                       const int32_t* __restrict__ bcap, uint8_t* __restrict__ state) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_u; i += stride) {
+        const int32_t f = ulist[i];
+        const uint32_t k = kr[f];
+        if (k != 0 && (int64_t)k <= (int64_t)bcap[f] + 1) state[f] = 2;
     }
 }
 
 __global__ void k_compact_undecided(const int32_t* __restrict__ ulist, int64_t n_u, const uint8_t* __restrict__ state,
                                     int32_t* __restrict__ out, unsigned long long* __restrict__ n_out) {
+    __shared__ BlockAppend<8> sh;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_u; base += stride) {
-        int64_t i = base + lane_id();
+    for (int64_t bb = (int64_t)blockIdx.x * blockDim.x; bb < n_u; bb += stride) {
+        int64_t i = bb + threadIdx.x;
         int32_t f = i < n_u ? ulist[i] : 0;
         bool keep = i < n_u && state[f] == 0;
-        long long at = warp_append(keep, n_out);
+        long long at = block_append<8>(keep, n_out, sh);
         if (at >= 0) out[at] = f;
     }
 }
 
 __global__ void k_open_list(const uint8_t* __restrict__ state, int64_t n, uint8_t* __restrict__ open,
                             int32_t* __restrict__ list, unsigned long long* __restrict__ n_list) {
+    __shared__ BlockAppend<8> sh;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-        int64_t v = base + lane_id();
+    for (int64_t bb = (int64_t)blockIdx.x * blockDim.x; bb < n; bb += stride) {
+        int64_t v = bb + threadIdx.x;
         bool is_open = v < n && state[v] == 1;
         if (v < n) open[v] = is_open ? 1 : 0;
-        long long at = warp_append(is_open, n_list);
+        long long at = block_append<8>(is_open, n_list, sh);
         if (at >= 0) list[at] = (int32_t)v;
     }
 }
@@ -692,6 +782,9 @@ int open_facilities(fl_solve* s) {
     FL_TRY(dalloc(s->ulist, (size_t)n * 4 * 2));
     FL_TRY(dalloc(s->ubuck, (size_t)n * 4));
     FL_TRY(dalloc(s->open, (size_t)n));
+    FL_TRY(dalloc(s->reach, (size_t)n));
+    FL_TRY(dalloc(s->kill, (size_t)n));
+    s->mis_log.clear();
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(s->frval.as<char>() + (size_t)n * 8);
     // cnt[0], cnt[1]: frontier counts; cnt[2]: changed count (dense rounds);
     // cnt[3]: undecided; cnt[4]: T max; cnt[5]: open list; cnt[6]: touched
@@ -711,7 +804,20 @@ int open_facilities(fl_solve* s) {
     FL_TRY(read_counters(g));
     const int64_t m = (int64_t)g->h_ctr->aux0;
     s->n_cand = m;
-    FL_TRY(sort_pairs_u128(hi.as<uint64_t>(), lo.as<uint64_t>(), val.as<uint32_t>(), m, st, g->scratch));
+    // Keys (r_f, pi_f): sort by r_f's varying digits; only when two radii are
+    // equal does the order need pi_f, and then the keys are sorted again by
+    // every varying digit (least significant first, so the result is the
+    // order of the whole 128-bit key).
+    const uint32_t digits = varying_digits(*g->h_ctr);
+    FL_TRY(sort_pairs_u128_digits(hi.as<uint64_t>(), lo.as<uint64_t>(), val.as<uint32_t>(), m, st, g->scratch,
+                                  kProfKeys, digits & 0xffff0000u));
+    if (m > 1) {
+        FL_LAUNCH(kProfKeys, k_key_ties<<<grid_for(m, 256), 256, 0, st>>>(hi.as<uint64_t>(), m, g->ctr.as<Counters>()));
+        FL_TRY(read_counters(g));
+        if (g->h_ctr->key_ties)
+            FL_TRY(sort_pairs_u128_digits(hi.as<uint64_t>(), lo.as<uint64_t>(), val.as<uint32_t>(), m, st, g->scratch,
+                                          kProfKeys, digits));
+    }
     int32_t* ulist[2] = {s->ulist.as<int32_t>(), s->ulist.as<int32_t>() + n};
     FL_CUDA(cudaMemsetAsync(cnt, 0, 64, st));
     if (m > 0) {
@@ -752,6 +858,24 @@ int open_facilities(fl_solve* s) {
         part_T = s->part_T.as<int32_t>();
     }
     int32_t* touched = s->touched.as<int32_t>();
+    uint8_t* reach = s->reach.as<uint8_t>();
+    uint8_t* kill = s->kill.as<uint8_t>();
+    // rows of the round log: (greedy round, kind, step, frontier in, pulled, microseconds);
+    // kind 0 cover round, 1 gather round, 2 bucket size (step = ball radius), 3 greedy-round total,
+    // 4 kill-sweep round (frontier = marks made)
+    using clock = std::chrono::steady_clock;
+    auto log_row = [&](int64_t rd, int64_t kind, int64_t step, int64_t front, int64_t dense, double us) {
+        const int64_t row[6] = {rd, kind, step, front, dense, (int64_t)us};
+        s->mis_log.insert(s->mis_log.end(), row, row + 6);
+    };
+    auto timed_round = [&](int64_t rd, int64_t kind, int64_t step, uint32_t svr) -> int {
+        const int64_t front = r.n_front;
+        const auto t0 = clock::now();
+        FL_TRY(relax_round(g, r, 0ULL, svr, kProfMis));
+        log_row(rd, kind, step, front, r.last_dense ? 1 : 0,
+                std::chrono::duration<double, std::micro>(clock::now() - t0).count());
+        return FL_OK;
+    };
     uint32_t epoch = 0;
     uint32_t sv = 0;  // frontier stamp values, unique per round
     int64_t n_u = m;
@@ -759,6 +883,7 @@ int open_facilities(fl_solve* s) {
     int64_t rounds = 0;
     while (n_u > 0) {
         if (++rounds > m + 1) FL_FAIL(FL_ETIMEOUT, "greedy MIS did not converge");
+        const auto round_t0 = clock::now();
         // bucket the undecided facilities by ball radius
         FL_CUDA(cudaMemsetAsync(bcount, 0, (bmax + 1) * 4, st));
         FL_CUDA(cudaMemsetAsync(&cnt[4], 0, 8, st));
@@ -772,7 +897,16 @@ int open_facilities(fl_solve* s) {
         FL_CUDA(cudaStreamSynchronize(st));
         const int T = (int)T64;
         int32_t acc = 0;
-        for (int b = 0; b <= T; ++b) { hoff[b] = acc; acc += hcount[b]; }
+        for (int b = 0; b <= T; ++b) {
+            hoff[b] = acc;
+            acc += hcount[b];
+            if (hcount[b] > 0) log_row(rounds, 2, b, hcount[b], 0, 0.0);
+        }
+        // Gather pruning: the cover records reach = 1 + max_f (B_f - d(v, f))
+        // (T minus the time its first wave arrived); gather round b needs only
+        // vertices with B_f - d(v, f) >= b for some f, the others sit out.
+        const bool prune = T < 255;
+        if (prune) FL_CUDA(cudaMemsetAsync(reach, 0, (size_t)n, st));
         FL_CUDA(cudaMemcpyAsync(cursor, hoff.data(), (T + 1) * 4, cudaMemcpyHostToDevice, st));
         FL_LAUNCH(kProfMis, k_bucket_scatter<<<grid_for(n_u, 256), 256, 0, st>>>(
                                 ulist[cu], n_u, s->bcap.as<int32_t>(), cursor, s->ubuck.as<int32_t>()));
@@ -789,19 +923,24 @@ int open_facilities(fl_solve* s) {
         r.list_valid = true;
         const uint32_t sv0 = sv;
         r.sv_prev = sv0 + 1;
+        r.prune = Prune();
+        r.prune.reach = prune ? reach : nullptr;
         for (int t = 0; t <= T; ++t) {
             const int b = T - t;
             if (hcount[b] > 0) {
                 FL_TRY(relax_prepare_list(g, r, kProfMis));
                 FL_LAUNCH(kProfMis, k_inject<<<grid_for(hcount[b], 256), 256, 0, st>>>(
-                                        ub + hoff[b], hcount[b], nullptr, hi_c, s->ord.as<uint32_t>(), r.X[r.cur],
-                                        r.stamp, sv0 + 1 + t, r.fr[r.fc], &r.cnt[r.fc]));
+                                        ub + hoff[b], hcount[b], r.prune.reach, (uint32_t)b + 1u, r.limit, hi_c,
+                                        s->ord.as<uint32_t>(), r.X[r.cur], r.stamp, sv0 + 1 + t, r.fr[r.fc],
+                                        &r.cnt[r.fc]));
                 FL_CUDA(cudaGetLastError());
                 r.n_front += hcount[b];
             }
-            if (t < T && r.n_front > 0) FL_TRY(relax_round(g, r, 0ULL, sv0 + 2 + t, kProfMis));
+            r.prune.reach_val = (uint32_t)(T - t);  // first reached at time t + 1
+            if (t < T && r.n_front > 0) FL_TRY(timed_round(rounds, 0, t, sv0 + 2 + t));
             else if (t < T) r.sv_prev = sv0 + 2 + t;
         }
+        r.prune = Prune();
         sv = sv0 + T + 2;
         // every vertex the cover reached (its value carries this sweep's epoch)
         FL_TRY(relax_collect_epoch(g, r.X[r.cur], hi_c, touched, &cnt[6], kProfMis));
@@ -828,9 +967,11 @@ int open_facilities(fl_solve* s) {
                                     ub + hoff[0], hcount[0], r.X[r.cur], hi_g, s->ord.as<uint32_t>(),
                                     s->state.as<uint8_t>(), g->ctr.as<Counters>()));
         r.part_limit = part_T;
+        r.prune.need = prune ? reach : nullptr;
         for (int b = 1; b <= T; ++b) {
             r.part_round = b;
-            if (r.n_front > 0) FL_TRY(relax_round(g, r, 0ULL, sg0 + b, kProfMis));
+            r.prune.round = (uint32_t)b;
+            if (r.n_front > 0) FL_TRY(timed_round(rounds, 1, b, sg0 + b));
             else r.sv_prev = sg0 + b;
             if (hcount[b] > 0)
                 FL_LAUNCH(kProfMis, k_decide<<<grid_for(hcount[b], 256), 256, 0, st>>>(
@@ -839,22 +980,55 @@ int open_facilities(fl_solve* s) {
         }
         sv = sg0 + T + 1;
         r.part_limit = nullptr;
+        r.prune = Prune();
         FL_CUDA(cudaGetLastError());
 
         // ---- claim the balls of this round's winners; keep the undecided
+        if (prune) FL_CUDA(cudaMemsetAsync(kill, 0, (size_t)n, st));
+        FL_CUDA(cudaMemsetAsync(&cnt[7], 0, 8, st));
         FL_LAUNCH(kProfMis, k_claim<<<152 * 4, 256, 0, st>>>(s->touched.as<int32_t>(), &cnt[6], s->client.as<uint8_t>(),
                                          s->claimed.as<uint8_t>(), s->mval.as<uint32_t>(),
-                                         s->fac_by_ord.as<int32_t>(), s->state.as<uint8_t>()));
+                                         s->fac_by_ord.as<int32_t>(), s->state.as<uint8_t>(),
+                                         prune ? kill : nullptr, &cnt[7]));
         FL_CUDA(cudaMemsetAsync(&cnt[3], 0, 8, st));
         FL_LAUNCH(kProfMis, k_compact_undecided<<<grid_for(n_u, 256), 256, 0, st>>>(ulist[cu], n_u, s->state.as<uint8_t>(),
                                                                ulist[cu ^ 1], &cnt[3]));
         FL_CUDA(cudaGetLastError());
-        unsigned long long nu = 0;
+        unsigned long long nu = 0, n_claimed = 0;
         FL_CUDA(cudaMemcpyAsync(&nu, &cnt[3], 8, cudaMemcpyDeviceToHost, st));
+        FL_CUDA(cudaMemcpyAsync(&n_claimed, &cnt[7], 8, cudaMemcpyDeviceToHost, st));
         FL_TRY(read_counters(g));
         if (g->h_ctr->error) FL_FAIL(FL_ECUDA, "greedy MIS: inconsistent gather state");
-        n_u = (int64_t)nu;
         cu ^= 1;
+        // ---- kill sweep: an undecided facility whose ball holds a client
+        // claimed in this round is adjacent in H-bar to a facility of S and
+        // can never join it.  The next round's gather would find the claim
+        // too, but only after a cover sweep in which the dead facility still
+        // competes; removing it now lets its neighbours decide a round earlier
+        // (the result stays the lexicographically-first MIS).  A bounded
+        // marking BFS from the newly claimed clients, pruned like the gather.
+        if (prune && nu > 0 && n_claimed > 0) {
+            for (int b = 1; b <= T; ++b) {
+                const auto t0 = clock::now();
+                int64_t marked = 0;
+                FL_TRY(mark_round(g, r, kill, reach, (uint32_t)b, kProfMis, &marked));
+                log_row(rounds, 4, b, marked, 1, std::chrono::duration<double, std::micro>(clock::now() - t0).count());
+                if (marked == 0) break;
+            }
+            FL_LAUNCH(kProfMis, k_kill<<<grid_for((int64_t)nu, 256), 256, 0, st>>>(ulist[cu], (int64_t)nu, kill,
+                                                                                  s->bcap.as<int32_t>(),
+                                                                                  s->state.as<uint8_t>()));
+            FL_CUDA(cudaMemsetAsync(&cnt[3], 0, 8, st));
+            FL_LAUNCH(kProfMis, k_compact_undecided<<<grid_for((int64_t)nu, 256), 256, 0, st>>>(
+                                    ulist[cu], (int64_t)nu, s->state.as<uint8_t>(), ulist[cu ^ 1], &cnt[3]));
+            FL_CUDA(cudaGetLastError());
+            FL_CUDA(cudaMemcpyAsync(&nu, &cnt[3], 8, cudaMemcpyDeviceToHost, st));
+            FL_CUDA(cudaStreamSynchronize(st));
+            cu ^= 1;
+        }
+        log_row(rounds, 3, T, n_u, n_u - (int64_t)nu,
+                std::chrono::duration<double, std::micro>(clock::now() - round_t0).count());
+        n_u = (int64_t)nu;
     }
     s->mis_rounds = rounds;
     // open set

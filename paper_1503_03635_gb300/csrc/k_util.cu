@@ -386,9 +386,16 @@ __global__ void k_digit_scatter(const uint64_t* __restrict__ key, const uint64_t
 
 int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaStream_t st, DBuf& tmp, int cls,
                     int pass_begin, int pass_end) {
-    if (n <= 1) return FL_OK;
     if (pass_begin < 0 || pass_end > 32 || pass_begin > pass_end || ((pass_end - pass_begin) & 1))
         FL_FAIL(FL_EINVAL, "radix sort: bad pass range");
+    uint32_t digits = 0;
+    for (int p = pass_begin; p < pass_end; ++p) digits |= 1u << p;
+    return sort_pairs_u128_digits(hi, lo, val, n, st, tmp, cls, digits);
+}
+
+int sort_pairs_u128_digits(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaStream_t st, DBuf& tmp,
+                           int cls, uint32_t digits) {
+    if (n <= 1 || digits == 0) return FL_OK;
     int nblocks = (int)((n + kSortTile - 1) / kSortTile);
     int64_t hn = 16LL * nblocks;
     size_t need = (size_t)n * (8 + 8 + 4) + 256 * 8 + (size_t)hn * (4 + 8) + scan_tmp_bytes(hn);
@@ -407,7 +414,8 @@ int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaSt
     char* stmp = take(scan_tmp_bytes(hn));
     uint64_t *ahi = hi, *alo = lo, *bhi = hi2, *blo = lo2;
     uint32_t *aval = val, *bval = val2;
-    for (int pass = pass_begin; pass < pass_end; ++pass) {
+    for (int pass = 0; pass < 32; ++pass) {
+        if (!((digits >> pass) & 1u)) continue;
         const uint64_t* key = pass < 16 ? alo : ahi;
         int shift = 4 * (pass & 15);
         FL_LAUNCH(cls, k_digit_hist<<<nblocks, kSortThreads, 0, st>>>(key, n, shift, nblocks, hist));
@@ -420,7 +428,11 @@ int sort_pairs_u128(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n, cudaSt
         std::swap(alo, blo);
         std::swap(aval, bval);
     }
-    // an even number of passes: the result is back in the caller's arrays
+    if (__builtin_popcount(digits) & 1) {  // an odd number of passes: copy the result back
+        FL_CUDA(cudaMemcpyAsync(hi, ahi, (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
+        FL_CUDA(cudaMemcpyAsync(lo, alo, (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
+        FL_CUDA(cudaMemcpyAsync(val, aval, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+    }
     return FL_OK;
 }
 

@@ -297,3 +297,56 @@ def test_hop_model_terms_match_the_oracle_ads(name):
     assert sum(m["edge_merges"] for m in got) == og.edge_merges
     g.close()
     og.close()
+
+
+def test_long_balls_without_gather_pruning():
+    """Ball radii above 254 (a 700-vertex path, costs 1e5): the MIS runs its
+    gather sweeps without the per-vertex pruning (its reach counters are one
+    byte), and still matches the oracle."""
+    n = 700
+    rowp, cols = brute.csr_from_edges(n, [(i, i + 1) for i in range(n - 1)])
+    client = np.ones(n, np.uint8)
+    cost = np.full(n, np.inf)
+    cost[[0, 350, 699]] = [1.0e5, 1.0e5, 3.0e4]
+    w = flsynth.from_csr("longpath", rowp, cols, 32, 3, cost, client)
+    gpu = _gpu(w)
+    _compare(w, gpu, _oracle(w))
+    assert np.nanmax(np.where(np.isfinite(gpu["radii"]), gpu["radii"], np.nan)) >= 255
+
+
+@pytest.mark.parametrize("name", ["rmat12", "er10k"])
+def test_mis_log_accounts_for_every_candidate(name):
+    """fl_mis_log: one total row per greedy round; the bucket sizes of a
+    round add up to its undecided facilities, the rounds decide every
+    candidate, and each round's undecided count is the previous one's minus
+    what it decided."""
+    if name == "rmat12":
+        rowp, cols = flsynth.rmat(12, 16, 512)
+        n = len(rowp) - 1
+        w = flsynth.from_csr(name, rowp, cols, 16, 1, flsynth.loguniform(n, 5, 10.0, 1.0e4, flsynth.bernoulli(n, 4, 0.3)),
+                             flsynth.bernoulli(n, 3, 0.5))
+    else:
+        w = flsynth.config(name)
+    g = fl.Graph(w.rowp, w.cols)
+    g.build_sketches(w.k, w.seed)
+    s = fl.Solve(g)
+    s.compute_radii(w.cost, w.client)
+    s.open_facilities()
+    st = s.stats()
+    log = s.mis_log()
+    s.close()
+    g.close()
+    assert log.shape[1] == 6
+    tot = log[log[:, 1] == 3]
+    assert len(tot) == st["mis_rounds"]
+    assert list(tot[:, 0]) == list(range(1, st["mis_rounds"] + 1))
+    assert tot[0, 3] == st["candidates"]
+    assert tot[:, 4].sum() == st["candidates"]
+    for i, row in enumerate(tot):
+        b = log[(log[:, 0] == row[0]) & (log[:, 1] == 2)]
+        assert b[:, 3].sum() == row[3]
+        assert b[:, 2].max() == row[2]
+        if i + 1 < len(tot):
+            assert tot[i + 1, 3] == row[3] - row[4]
+    rounds = log[np.isin(log[:, 1], [0, 1])]
+    assert np.all(rounds[:, 3] > 0) and np.all(np.isin(rounds[:, 4], [0, 1]))
