@@ -1010,7 +1010,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule (no tuning pass)")
-    ap.add_argument("--tune-trials", type=int, default=10, help="timed schedules of the autotuner, at most")
+    ap.add_argument("--tune-trials", type=int, default=15, help="timed schedules of the autotuner, at most")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (req/s)")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serve: measured seconds")
     ap.add_argument("--serve-warmup", type=float, default=5.0, help="serve: warm-up seconds")

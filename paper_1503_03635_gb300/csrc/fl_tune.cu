@@ -133,13 +133,16 @@ int fl_autotune(fl_graph* g, int k, uint64_t seed, const double* open_cost, cons
     const double default_ms = best_ms;
     Sched best = base;
     int trials = 1;
-    // coordinate descent: each parameter in turn over its candidates
+    // coordinate descent: each parameter in turn over its candidates, the
+    // ones that move the most time first (the sparse-hop cut-off sets which
+    // sketch hops scan every row; the round switches set which relaxation
+    // rounds pull)
     std::vector<std::pair<int Sched::*, std::vector<int>>> params;
-    if (k <= 16) params.push_back({&Sched::hop_group, {32}});
-    params.push_back({&Sched::graph_bfs, {1}});
+    params.push_back({&Sched::sparse_div, {8, 32, 4, 64}});
     params.push_back({&Sched::edge_div, {8, 32, 4, 64}});
     params.push_back({&Sched::dense_div, {4, 16, 2, 32}});
-    params.push_back({&Sched::sparse_div, {8, 32, 4, 64}});
+    if (k <= 16) params.push_back({&Sched::hop_group, {32}});
+    params.push_back({&Sched::graph_bfs, {1}});
     for (const auto& p : params) {
         for (int v : p.second) {
             if (trials >= max_trials) break;
