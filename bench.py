@@ -369,22 +369,34 @@ def run_gpu(args):
         dist_h = torch.empty(w.n, dtype=torch.int32).pin_memory()
         g.close()
         times = []
+        parts = {}
         for i in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
+            marks = []
             g2 = fl.Graph(rowp_h, cols_h, stream=stream)      # H2D of the CSR
+            marks.append(("graph_create", time.perf_counter()))
             g2.set_schedule(**g_schedule)                        # the schedule tuned above
             g2.build_sketches(w.k, w.seed)
+            marks.append(("build_sketches", time.perf_counter()))
             s2 = fl.Solve(g2)
             s2.compute_radii(cost_h, client_h)                  # H2D of costs and mask
+            marks.append(("radii", time.perf_counter()))
             s2.open_facilities(open_h)                          # D2H of the open set
+            marks.append(("open_facilities", time.perf_counter()))
             s2.assign_clients(assign_h, dist_h)                 # D2H of assignment and distance
+            marks.append(("assign", time.perf_counter()))
             s2.objective()
             s2.close()
             g2.close()
+            marks.append(("objective_close", time.perf_counter()))
             dt = time.perf_counter() - t0
             if i > 0:  # the first pass warms allocations
                 times.append(dt)
+                prev = t0
+                for name, t in marks:  # host wall time of each call (each returns with its work done)
+                    parts[name] = parts.get(name, 0.0) + 1e3 * (t - prev) / args.e2e_steps
+                    prev = t
         t_e2e = sum(times) / len(times)
         if dist:
             t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
@@ -393,7 +405,8 @@ def run_gpu(args):
         e2e = {"value": world * merges_step / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": int(w.rowp.nbytes + w.cols.nbytes + w.cost.nbytes + w.client.nbytes),
                "d2h_bytes_per_step": int(open_h.numel() + 4 * assign_h.numel() + 4 * dist_h.numel()),
-               "ms_per_step": 1e3 * t_e2e, "steps": len(times)}
+               "ms_per_step": 1e3 * t_e2e, "steps": len(times),
+               "calls_ms": {k: round(v, 2) for k, v in parts.items()}}
     else:
         g.close()
 

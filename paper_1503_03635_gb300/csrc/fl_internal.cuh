@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <initializer_list>
 #include <vector>
 
 #include "../../include/fl.h"
@@ -47,6 +48,8 @@ int dalloc(DBuf& b, size_t bytes);            // free + allocate (no copy)
 int dgrow(DBuf& b, size_t bytes, size_t keep, cudaStream_t st);  // grow keeping `keep` bytes
 void dfree(DBuf& b);
 void dfree_idle(DBuf& b);                     // to the idle-block cache (no pending work uses b)
+// A call's temporaries: to the idle-block cache once `st` has finished with them.
+void dfree_after(cudaStream_t st, std::initializer_list<DBuf*> bufs);
 
 // ----------------------------------------------------------------- constants
 

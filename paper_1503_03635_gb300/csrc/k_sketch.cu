@@ -1049,8 +1049,7 @@ int build_work_lists(fl_graph* g) {
         e = cudaStreamSynchronize(st);
         if (e) { rc = status_of(e, "work lists", __FILE__, __LINE__); break; }
     } while (0);
-    dfree(low); dfree(hub); dfree(nseg); dfree(low_pos); dfree(hub_pos); dfree(seg_pos); dfree(small);
-    dfree(small_pos);
+    dfree_after(st, {&low, &hub, &nseg, &low_pos, &hub_pos, &seg_pos, &small, &small_pos});
     return rc;
 }
 
@@ -1181,7 +1180,7 @@ static int select_small_ranks(fl_graph* g) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = status_of(e, "small ranks", __FILE__, __LINE__);
     }
-    dfree(buf);
+    dfree_after(st, {&buf});
     return rc;
 }
 
@@ -1297,7 +1296,7 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     {
         int rc0 = select_small_ranks(g);
         if (rc0 != FL_OK) {
-            dfree(act);
+            dfree_after(st, {&act});
             return rc0;
         }
     }
@@ -1307,7 +1306,7 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     FL_CUDA(cudaGetLastError());
     FL_TRY(read_counters(g));
     if (g->h_ctr->error) {
-        dfree(act);
+        dfree_after(st, {&act});
         FL_FAIL(FL_EINVAL, "a vertex rank equals the reserved empty-slot value; choose another seed");
     }
     g->hop_scanned.clear();
@@ -1432,7 +1431,7 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
             fr_list_ready = true;
         }
     }
-    dfree(act);
+    dfree_after(st, {&act});
     if (rc != FL_OK) return rc;
     g->hops = hop - 1;
     g->edge_merges = total_merges;
@@ -1531,8 +1530,7 @@ int compute_ecc_bound(fl_graph* g) {
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { rc = status_of(e, "ecc bound", __FILE__, __LINE__); break; }
     } while (0);
-    dfree(roots); dfree(label); dfree(dist); dfree(eccr);
-    dfree(X); dfree(stampb); dfree(fr[0]); dfree(fr[1]); dfree(frval);
+    dfree_after(st, {&roots, &label, &dist, &eccr, &X, &stampb, &fr[0], &fr[1], &frval});
     return rc;
 }
 

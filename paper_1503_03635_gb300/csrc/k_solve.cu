@@ -395,15 +395,76 @@ __global__ void k_check_costs(const double* __restrict__ cost, int64_t n, Counte
     }
 }
 
-// Warp per facility.  W_h = (#counted client entries of the hop-h group) x
-// weight; N_j = N_{j-1} + W_j; G_{j+1} = G_j + N_j; r = j + (c - G_j) / N_j at
-// the first j < L with G_{j+1} >= c, else L + (c - G_L) / N_L (L = last hop
-// of the ADS of f), +inf if N_L = 0.  Every operation is one IEEE-754 op in
-// this order (no contraction).
+// Radius of facility f with opening cost c (Eq. 1 at eps -> 0), by the
+// warp: W_h = (#counted client entries of the hop-h group) x weight;
+// N_j = N_{j-1} + W_j; G_{j+1} = G_j + N_j; r = j + (c - G_j) / N_j at the
+// first j < L with G_{j+1} >= c, else L + (c - G_L) / N_L (L = last hop of
+// the ADS of f), +inf if N_L = 0.  Every operation is one IEEE-754 op in this
+// order (no contraction).  The loads are issued a row at a time: the group
+// words of up to 32 groups (one per lane), then the row's entry ids and their
+// client flags 32 at a time; per-group client counts come from ballots, and
+// the recurrence runs on registers.  Every lane returns the same value.
+__device__ double facility_radius(int64_t f, double c, int64_t io, const uint8_t* __restrict__ client,
+                                  const int64_t* __restrict__ gofs, const int64_t* __restrict__ eofs,
+                                  const uint32_t* __restrict__ ginfo, const double* __restrict__ gwt,
+                                  const int32_t* __restrict__ eid) {
+    const int lane = lane_id();
+    const int64_t g0 = gofs[f], ng = gofs[f + 1] - g0;
+    const int L = (int)(ginfo[g0 + ng - 1] & 0xffffu);
+    int64_t e = eofs[f];
+    double N = 0.0, G = 0.0;
+    int j = 0;
+    for (int64_t gc = 0; gc < ng; gc += 32) {
+        const int m = ng - gc < 32 ? (int)(ng - gc) : 32;
+        const uint32_t info = lane < m ? ginfo[g0 + gc + lane] : 0u;
+        const double wt = lane < m ? gwt[g0 + gc + lane] : 0.0;
+        const int cnt = (int)((info >> 16) & 0xffu);
+        const int counted = (int)(info >> 24);
+        const int incl = warp_incl_scan(cnt);
+        const int off = incl - cnt;  // first entry of group `lane` within this chunk
+        const int tot = __shfl_sync(kFull, incl, 31);
+        int clients = 0;             // lane g: counted client entries of group g
+        for (int p = 0; p < tot; p += 32) {
+            const int pos = p + lane;
+            const bool is_client = pos < tot && client[io + eid[e + pos]] != 0;
+            for (int gg = 0; gg < m; ++gg) {
+                const int s0 = __shfl_sync(kFull, off, gg);
+                const int cc = __shfl_sync(kFull, counted, gg);
+                const unsigned hit = __ballot_sync(kFull, is_client && pos >= s0 && pos < s0 + cc);
+                if (lane == gg) clients += __popc(hit);
+            }
+        }
+        for (int gg = 0; gg < m; ++gg) {
+            const int hop = (int)(__shfl_sync(kFull, info, gg) & 0xffffu);
+            const int cl = __shfl_sync(kFull, clients, gg);
+            const double w = __shfl_sync(kFull, wt, gg);
+            for (; j < hop; ++j) {  // hops without new entries: W_j = 0
+                if (j < L) {
+                    const double Gn = __dadd_rn(G, N);
+                    if (Gn >= c) return __dadd_rn((double)j, __ddiv_rn(__dsub_rn(c, G), N));
+                    G = Gn;
+                }
+            }
+            N = __dadd_rn(N, __dmul_rn((double)cl, w));
+            if (j < L) {
+                const double Gn = __dadd_rn(G, N);
+                if (Gn >= c) return __dadd_rn((double)j, __ddiv_rn(__dsub_rn(c, G), N));
+                G = Gn;
+            }
+            ++j;
+        }
+        e += tot;
+    }
+    return N > 0.0 ? __dadd_rn((double)L, __ddiv_rn(__dsub_rn(c, G), N)) : INFINITY;
+}
+
+// A warp per 32 consecutive vertices: one ballot finds the facilities (finite
+// cost), the others get +inf, and the warp computes each facility's radius in
+// turn.
 //
 // R > 1 (batches on one resident graph): R instances, instance i's costs,
-// client mask and radii at offset i*n; the warps of one facility's R
-// instances are adjacent, so its ADS row is read from DRAM once.
+// client mask and radii at offset i*n; the warps of one vertex block's R
+// instances are adjacent, so its ADS rows are read from DRAM once.
 template <bool kMulti>
 __global__ void __launch_bounds__(256) k_radius(int64_t n, int64_t R, const double* __restrict__ cost,
                                                 const uint8_t* __restrict__ client,
@@ -412,54 +473,22 @@ __global__ void __launch_bounds__(256) k_radius(int64_t n, int64_t R, const doub
                                                 const int32_t* __restrict__ eid, double* __restrict__ r_out) {
     const int lane = lane_id();
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; t < n * R; t += warps) {
-        const int64_t f = kMulti ? t / R : t;
-        const int64_t io = kMulti ? (t - f * R) * n : 0;  // instance offset
-        const double c = cost[io + f];
-        double res = INFINITY;
-        if (c < INFINITY) {
-            const int64_t g0 = gofs[f], g1 = gofs[f + 1];
-            const int L = (int)(ginfo[g1 - 1] & 0xffffu);
-            int64_t e = eofs[f];
-            double N = 0.0, G = 0.0;
-            int j = 0;
-            bool done = false;
-            for (int64_t gi = g0; gi < g1 && !done; ++gi) {
-                const uint32_t info = ginfo[gi];
-                const int hop = (int)(info & 0xffffu);
-                const int cnt = (int)((info >> 16) & 0xffu);
-                const int counted = (int)(info >> 24);
-                for (; j < hop; ++j) {  // hops without new entries: W_j = 0
-                    if (j < L) {
-                        double Gn = __dadd_rn(G, N);
-                        if (Gn >= c) {
-                            res = __dadd_rn((double)j, __ddiv_rn(__dsub_rn(c, G), N));
-                            done = true;
-                            break;
-                        }
-                        G = Gn;
-                    }
-                }
-                if (done) break;
-                bool is_client = lane < counted && client[io + eid[e + lane]] != 0;
-                int clients = __popc(__ballot_sync(kFull, is_client));
-                double W = __dmul_rn((double)clients, gwt[gi]);
-                N = __dadd_rn(N, W);
-                if (j < L) {
-                    double Gn = __dadd_rn(G, N);
-                    if (Gn >= c) {
-                        res = __dadd_rn((double)j, __ddiv_rn(__dsub_rn(c, G), N));
-                        done = true;
-                        break;
-                    }
-                    G = Gn;
-                }
-                ++j;
-                e += cnt;
-            }
-            if (!done) res = N > 0.0 ? __dadd_rn((double)L, __ddiv_rn(__dsub_rn(c, G), N)) : INFINITY;
+    const int64_t nb = (n + 31) >> 5;
+    for (int64_t t = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; t < nb * R; t += warps) {
+        const int64_t blk = kMulti ? t / R : t;
+        const int64_t io = kMulti ? (t - blk * R) * n : 0;  // instance offset
+        const int64_t v = (blk << 5) + lane;
+        const double cv = v < n ? cost[io + v] : INFINITY;
+        unsigned fac = __ballot_sync(kFull, cv < INFINITY);
+        double rv = INFINITY;
+        while (fac) {
+            const int b = __ffs(fac) - 1;
+            fac &= fac - 1;
+            const double c = __shfl_sync(kFull, cv, b);
+            const double res = facility_radius((blk << 5) + b, c, io, client, gofs, eofs, ginfo, gwt, eid);
+            if (lane == b) rv = res;
         }
-        if (lane == 0) r_out[io + f] = res;
+        if (v < n) r_out[io + v] = rv;
     }
 }
 
@@ -479,7 +508,7 @@ int compute_radii(fl_solve* s) {
     fl_graph* g = s->g;
     cudaStream_t st = g->stream;
     FL_TRY(check_costs(s));
-    FL_LAUNCH(kProfRadius, k_radius<false><<<grid_for(g->n, 8), 256, 0, st>>>(g->n, 1, s->cost.as<double>(), s->client.as<uint8_t>(),
+    FL_LAUNCH(kProfRadius, k_radius<false><<<grid_for((g->n + 31) / 32, 8), 256, 0, st>>>(g->n, 1, s->cost.as<double>(), s->client.as<uint8_t>(),
                                                g->gofs.as<int64_t>(), g->eofs.as<int64_t>(), g->ginfo.as<uint32_t>(),
                                                g->gwt.as<double>(), g->eid.as<int32_t>(), s->radii.as<double>()));
     FL_CUDA(cudaGetLastError());
@@ -498,7 +527,7 @@ int compute_radii_multi(const fl_graph* src, fl_graph* g, int64_t R, const doubl
     FL_CUDA(cudaGetLastError());
     FL_TRY(read_counters(g));
     if (g->h_ctr->error) FL_FAIL(FL_EINVAL, "open_cost must be finite and > 0 for facilities, +inf otherwise");
-    FL_LAUNCH(kProfRadius, k_radius<true><<<grid_for(n * R, 8), 256, 0, st>>>(
+    FL_LAUNCH(kProfRadius, k_radius<true><<<grid_for((n + 31) / 32 * R, 8), 256, 0, st>>>(
                                n, R, cost, client, src->gofs.as<int64_t>(), src->eofs.as<int64_t>(),
                                src->ginfo.as<uint32_t>(), src->gwt.as<double>(), src->eid.as<int32_t>(), radii));
     FL_CUDA(cudaGetLastError());

@@ -173,17 +173,15 @@ int dalloc(DBuf& b, size_t bytes) {
 int dgrow(DBuf& b, size_t bytes, size_t keep, cudaStream_t st) {
     if (b.p && b.bytes >= bytes) return FL_OK;
     DBuf nb;
-    FL_CUDA(cudaMalloc(&nb.p, bytes));
-    nb.bytes = bytes;
-    if (b.p && keep) {
-        cudaError_t e = cudaMemcpyAsync(nb.p, b.p, keep, cudaMemcpyDeviceToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            cudaFree(nb.p);
-            return status_of(e, "dgrow copy", __FILE__, __LINE__);
-        }
+    FL_TRY(dalloc(nb, bytes));
+    cudaError_t e = cudaSuccess;
+    if (b.p && keep) e = cudaMemcpyAsync(nb.p, b.p, keep, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        dfree(nb);
+        return status_of(e, "dgrow copy", __FILE__, __LINE__);
     }
-    dfree(b);
+    dfree_idle(b);  // the stream is idle: nothing uses the old block any more
     b = nb;
     return FL_OK;
 }
@@ -215,6 +213,15 @@ void dfree_idle(DBuf& b) {
     if (!kept) cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
+}
+
+void dfree_after(cudaStream_t st, std::initializer_list<DBuf*> bufs) {
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        for (DBuf* b : bufs) dfree(*b);  // cudaFree waits for the device itself
+        return;
+    }
+    for (DBuf* b : bufs) dfree_idle(*b);
 }
 
 // ----------------------------------------------------------------- scan
