@@ -588,11 +588,13 @@ void graph_bfs_release(GraphBfs* c);
 
 // Per-vertex pruning of the rounds of a sweep (the MIS cover and gather
 // sweeps).  A round that first gives v a value below the limit records
-// reach[v] = reach_val; a round skips every v with need[v] <= round: it does
-// not lower v's value, and a push does not offer v one.
+// reach[v] = reach_val; a round skips every v with need[v] <= round, and
+// every v with only[v] == 0: it does not lower v's value, and a push does
+// not offer v one.
 struct Prune {
     uint8_t* reach = nullptr;
     const uint8_t* need = nullptr;
+    const uint8_t* only = nullptr;
     uint32_t reach_val = 0, round = 0;
 };
 

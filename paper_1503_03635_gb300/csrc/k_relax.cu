@@ -65,7 +65,7 @@ __device__ __forceinline__ bool part_idle(const int32_t* __restrict__ vpart, con
 }
 
 __device__ __forceinline__ bool skipped(const Prune& pr, int32_t u) {
-    return pr.need && __ldg(&pr.need[u]) <= pr.round;
+    return (pr.need && __ldg(&pr.need[u]) <= pr.round) || (pr.only && !__ldg(&pr.only[u]));
 }
 
 // Values >= `limit` are ignored: unset entries (BFS) or values of an earlier

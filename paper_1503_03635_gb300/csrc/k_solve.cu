@@ -966,6 +966,11 @@ int open_facilities(fl_solve* s) {
                 r.n_front += hcount[b];
             }
             r.prune.reach_val = (uint32_t)(T - t);  // first reached at time t + 1
+            // the last round: nothing relays a value past time T, and of the
+            // values at time T only the clients' are read (gather seeds and
+            // claims), so the other vertices sit it out (left unreached, they
+            // have the same effect on the gather and kill sweeps as slack 0)
+            r.prune.only = (prune && t == T - 1) ? s->client.as<uint8_t>() : nullptr;
             if (t < T && r.n_front > 0) FL_TRY(timed_round(rounds, 0, t, sv0 + 2 + t));
             else if (t < T) r.sv_prev = sv0 + 2 + t;
         }
