@@ -145,6 +145,25 @@ def hashes(m: int, seed: int) -> np.ndarray:
     return out
 
 
+def edge_weights(rowp: np.ndarray, cols: np.ndarray, seed: int, lo: int = 1, hi: int = 100) -> np.ndarray:
+    """Integer edge lengths uniform in [lo, hi] (Section 5 draws weights
+    between 1 and 100), one per CSR entry and equal for (u, v) and (v, u):
+    a hash (the 64-bit finaliser of MurmurHash3) of the unordered pair and
+    the seed, reduced modulo the range."""
+    rowp = np.asarray(rowp, np.int64)
+    n = len(rowp) - 1
+    src = np.repeat(np.arange(n, dtype=np.uint64), np.diff(rowp).astype(np.int64))
+    dst = np.asarray(cols).astype(np.uint64)
+    a, b = np.minimum(src, dst), np.maximum(src, dst)
+    x = (a << np.uint64(32)) ^ b ^ np.uint64((seed * 0x9E3779B97F4A7C15) % (1 << 64))
+    x ^= x >> np.uint64(33)
+    x *= np.uint64(0xFF51AFD7ED558CCD)
+    x ^= x >> np.uint64(33)
+    x *= np.uint64(0xC4CEB9FE1A85EC53)
+    x ^= x >> np.uint64(33)
+    return (np.int64(lo) + (x % np.uint64(hi - lo + 1)).astype(np.int64)).astype(np.int32)
+
+
 @dataclasses.dataclass
 class Workload:
     """One facility-location instance: CSR graph + per-vertex inputs."""

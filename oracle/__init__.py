@@ -105,6 +105,17 @@ def _load():
                                          ctypes.POINTER(dbl), ctypes.POINTER(i64)]
             lib.orc_eps_select.restype = ctypes.c_int
             lib.orc_eps_select.argtypes = [vp, dbl, dbl, vp, vp, u64, vp, ctypes.POINTER(i64)]
+            lib.orc_graph_set_weights.restype = ctypes.c_int
+            lib.orc_graph_set_weights.argtypes = [vp, vp]
+            lib.orc_build_sketches_weighted.restype = ctypes.c_int
+            lib.orc_build_sketches_weighted.argtypes = [vp, ctypes.c_int, u64]
+            lib.orc_wads_rounds.restype = ctypes.c_int
+            lib.orc_wads_rounds.argtypes = [vp, ctypes.c_int, u64, i64, vp, vp, vp,
+                                            ctypes.POINTER(i64), ctypes.POINTER(i64)]
+            lib.orc_open_facilities_weighted.restype = ctypes.c_int
+            lib.orc_open_facilities_weighted.argtypes = [vp, vp, vp, u64, vp, ctypes.POINTER(i64)]
+            lib.orc_assign_weighted.restype = ctypes.c_int
+            lib.orc_assign_weighted.argtypes = [vp, vp, vp, vp]
             lib.orc_objective.restype = ctypes.c_int
             lib.orc_objective.argtypes = [i64, vp, vp, vp, vp, ctypes.POINTER(dbl),
                                           ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -167,6 +178,60 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+    # -- weighted graphs (NEXT f3): Section 3.3 after Algorithm 2 ----------
+    def set_weights(self, w: np.ndarray) -> None:
+        """Edge lengths, one positive integer per CSR entry, equal for (u, v)
+        and (v, u) (Section 5 draws them uniformly in [1, 100])."""
+        self.w = np.ascontiguousarray(w, np.int32)
+        rc = self._lib.orc_graph_set_weights(self._h, _p(self.w))
+        if rc != 0:
+            raise ValueError(f"orc_graph_set_weights rc={rc}")
+
+    def build_sketches_weighted(self, k: int, seed: int) -> None:
+        """The ADS of every vertex by Algorithm 1 in Dijkstra order; groups
+        are per distance ("ghop" holds the distance)."""
+        rc = self._lib.orc_build_sketches_weighted(self._h, k, seed)
+        if rc != 0:
+            raise RuntimeError(f"orc_build_sketches_weighted rc={rc}")
+        self.k, self.seed = k, seed
+
+    def wads_rounds(self, k: int, seed: int, cap: int | None = None) -> dict:
+        """The ADS by the paper's Algorithm 2 with CleanUp (supersteps in BFS
+        order); per vertex its (id, distance) entries in (distance, rank)
+        order, the supersteps run and the entries CleanUp removed."""
+        cap = cap if cap is not None else max(64, 8 * self.n * k)
+        eofs = np.zeros(self.n + 1, np.int64)
+        eid = np.zeros(cap, np.int32)
+        edist = np.zeros(cap, np.int64)
+        steps, cleaned = i64(0), i64(0)
+        rc = self._lib.orc_wads_rounds(self._h, k, seed, cap, _p(eofs), _p(eid), _p(edist),
+                                       ctypes.byref(steps), ctypes.byref(cleaned))
+        if rc != 0:
+            raise RuntimeError(f"orc_wads_rounds rc={rc}")
+        ne = int(eofs[-1])
+        return dict(eofs=eofs, eid=eid[:ne].copy(), edist=edist[:ne].copy(), steps=int(steps.value),
+                    cleaned=int(cleaned.value))
+
+    def open_facilities_weighted(self, r: np.ndarray, client: np.ndarray, seed: int):
+        r = np.ascontiguousarray(r, np.float64)
+        client = np.ascontiguousarray(client, np.uint8)
+        op = np.zeros(self.n, np.uint8)
+        nopen = i64(0)
+        rc = self._lib.orc_open_facilities_weighted(self._h, _p(r), _p(client), seed, _p(op),
+                                                    ctypes.byref(nopen))
+        if rc != 0:
+            raise RuntimeError(f"orc_open_facilities_weighted rc={rc}")
+        return op, int(nopen.value)
+
+    def assign_weighted(self, open_: np.ndarray):
+        op = np.ascontiguousarray(open_, np.uint8)
+        a = np.zeros(self.n, np.int32)
+        d = np.zeros(self.n, np.int32)
+        rc = self._lib.orc_assign_weighted(self._h, _p(op), _p(a), _p(d))
+        if rc != 0:
+            raise RuntimeError(f"orc_assign_weighted rc={rc}")
+        return a, d
 
     # -- phase (i): Section 3.3, Algorithms 1-2 ---------------------------
     def build_sketches(self, k: int, seed: int, max_hops: int | None = None) -> None:
@@ -436,3 +501,19 @@ def solve_eps(rowp, cols, k, seed, eps, cost, client) -> dict:
     obj, ds, un = objective(op, cost, client, d)
     return dict(graph=g, opening=o, open=op, n_open=nopen, assign=a, dist=d, objective=obj, dist_sum=ds,
                 n_unserved=un)
+
+
+def solve_weighted(rowp, cols, w, k, seed, cost, client) -> dict:
+    """The whole path on a weighted graph (NEXT f3): ADS in Dijkstra order,
+    radii (Eq. 1 at epsilon -> 0 over integer distances), the
+    lexicographically-first MIS with weighted balls, nearest open facility by
+    weighted distance, objective."""
+    g = Graph(rowp, cols)
+    g.set_weights(w)
+    g.build_sketches_weighted(k, seed)
+    r = g.radii(cost, client)
+    op, nopen = g.open_facilities_weighted(r, client, seed)
+    a, d = g.assign_weighted(op)
+    obj, ds, un = objective(op, cost, client, d)
+    return dict(graph=g, radii=r, open=op, n_open=nopen, assign=a, dist=d, objective=obj, dist_sum=ds,
+                n_unserved=un, hops=g.hops)

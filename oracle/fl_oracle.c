@@ -101,6 +101,7 @@ typedef struct {
     int32_t* ent_id;
     uint64_t* ent_rank;
     int64_t ngroups, nentries;
+    int32_t* wts;     /* edge lengths per CSR entry (weighted graphs), or NULL */
 } orc_graph;
 
 static void orc_clear_ads(orc_graph* g) {
@@ -128,7 +129,7 @@ orc_graph* orc_graph_create(int64_t n, const int64_t* rowp, const int32_t* cols)
 void orc_graph_destroy(orc_graph* g) {
     if (!g) return;
     orc_clear_ads(g);
-    free(g->rowp); free(g->cols);
+    free(g->rowp); free(g->cols); free(g->wts);
     free(g);
 }
 
@@ -1598,4 +1599,500 @@ int orc_eps_select(const orc_graph* g, double eps, double alpha0, const int32_t*
     *n_open = opened;
     free(grid); free(c); free(claimed); free(dist); free(q); free(ball);
     return ORC_OK;
+}
+
+/* ====================================================================== */
+/* Weighted graphs (NEXT f3).  Section 3.3, after Algorithm 2: the Giraph  */
+/* algorithm handles weighted graphs too; vertices then reach an ADS in    */
+/* BFS order rather than by distance, so an entry accepted early can stop  */
+/* belonging to the ADS when a closer one arrives, and a CleanUp step      */
+/* removes it.  Section 5 draws edge weights uniformly in [1, 100].        */
+/* Readings: lengths are positive integers, equal in both directions of an */
+/* edge (the graph is undirected), so distances are exact integers; equal  */
+/* distances are presented in ascending rank, as in the unweighted build;  */
+/* an ADS group is the set of entries at one distance, and its HIP weight  */
+/* and counted prefix follow the unweighted build with "hop" read as       */
+/* "distance".                                                             */
+/* ====================================================================== */
+
+/* Edge lengths, one per CSR entry: positive, equal for (u, v) and (v, u). */
+int orc_graph_set_weights(orc_graph* g, const int32_t* w) {
+    if (!g || !w) return ORC_EINVAL;
+    const int64_t nnz = g->rowp[g->n];
+    for (int64_t e = 0; e < nnz; ++e)
+        if (w[e] < 1) return ORC_EINVAL;
+    int32_t* c = (int32_t*)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    if (!c) return ORC_ENOMEM;
+    if (nnz > 0) memcpy(c, w, (size_t)nnz * sizeof(int32_t));
+    free(g->wts);
+    g->wts = c;
+    orc_clear_ads(g);
+    return ORC_OK;
+}
+
+/* ---- binary min-heap of (key, tie, vertex), lexicographic ---- */
+typedef struct { int64_t key; int64_t tie; int32_t v; } heap_item;
+
+static int heap_less(const heap_item* a, const heap_item* b) {
+    if (a->key != b->key) return a->key < b->key;
+    if (a->tie != b->tie) return a->tie < b->tie;
+    return a->v < b->v;
+}
+
+static void heap_push(heap_item* h, int64_t* n, heap_item x) {
+    int64_t i = (*n)++;
+    h[i] = x;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (!heap_less(&h[i], &h[p])) break;
+        heap_item t = h[i]; h[i] = h[p]; h[p] = t;
+        i = p;
+    }
+}
+
+static heap_item heap_pop(heap_item* h, int64_t* n) {
+    heap_item top = h[0];
+    h[0] = h[--(*n)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, m = i;
+        if (l < *n && heap_less(&h[l], &h[m])) m = l;
+        if (r < *n && heap_less(&h[r], &h[m])) m = r;
+        if (m == i) break;
+        heap_item t = h[i]; h[i] = h[m]; h[m] = t;
+        i = m;
+    }
+    return top;
+}
+
+/* Dijkstra from src: dist[x] = d(src, x), -1 when unreachable.  The heap
+   holds at most one item per relaxed edge plus the source. */
+static int dijkstra(const orc_graph* g, int32_t src, int64_t* dist, heap_item* heap) {
+    const int64_t n = g->n;
+    for (int64_t i = 0; i < n; ++i) dist[i] = -1;
+    int64_t hn = 0;
+    heap_item s0 = {0, 0, src};
+    heap_push(heap, &hn, s0);
+    while (hn > 0) {
+        heap_item it = heap_pop(heap, &hn);
+        if (dist[it.v] >= 0) continue;
+        dist[it.v] = it.key;
+        for (int64_t e = g->rowp[it.v]; e < g->rowp[it.v + 1]; ++e) {
+            int32_t u = g->cols[e];
+            if (dist[u] >= 0) continue;
+            heap_item nx = {it.key + g->wts[e], 0, u};
+            heap_push(heap, &hn, nx);
+        }
+    }
+    return ORC_OK;
+}
+
+typedef struct { int64_t d; uint64_t rank; int32_t id; } dist_rank;
+
+static int dist_rank_cmp(const void* a, const void* b) {
+    const dist_rank* x = (const dist_rank*)a;
+    const dist_rank* y = (const dist_rank*)b;
+    if (x->d != y->d) return (x->d > y->d) - (x->d < y->d);
+    return (x->rank > y->rank) - (x->rank < y->rank);
+}
+
+/* One vertex's ADS by Algorithm 1 in Dijkstra order (see the section
+   comment); appends its groups and entries to the per-vertex buffers. */
+typedef struct {
+    int32_t ng, ne;
+    orc_group* grp;   /* .first relative to this vertex's entries */
+    int32_t* id;
+    uint64_t* rank;
+    uint64_t S[64];
+    int32_t slen;
+} wads_row;
+
+static int wads_one(const orc_graph* g, int k, uint64_t seed, int32_t v, int64_t* dist, heap_item* heap,
+                    dist_rank* order, wads_row* row) {
+    const int64_t n = g->n;
+    dijkstra(g, v, dist, heap);
+    int64_t m = 0;
+    for (int64_t x = 0; x < n; ++x)
+        if (dist[x] >= 0) { order[m].d = dist[x]; order[m].rank = orc_rank(seed, x); order[m].id = (int32_t)x; ++m; }
+    qsort(order, (size_t)m, sizeof(dist_rank), dist_rank_cmp);
+    row->grp = (orc_group*)malloc((size_t)(m > 0 ? m : 1) * sizeof(orc_group));
+    row->id = (int32_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+    row->rank = (uint64_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(uint64_t));
+    if (!row->grp || !row->id || !row->rank) return ORC_ENOMEM;
+    int32_t blen = 0, ne = 0, ng = 0;
+    for (int64_t i = 0; i < m;) {
+        int64_t j = i;
+        while (j < m && order[j].d == order[i].d) ++j;
+        if (order[i].d > 2147483647LL) return ORC_EINVAL;
+        const int32_t first = ne;
+        for (int64_t t = i; t < j; ++t) {
+            uint64_t r = order[t].rank;
+            if (blen < k || r < row->S[k - 1]) {
+                row->id[ne] = order[t].id;
+                row->rank[ne] = r;
+                ++ne;
+                bottomk_insert(row->S, &blen, k, r);
+            }
+        }
+        if (ne > first) {
+            int32_t counted = 0;
+            for (int32_t e = first; e < ne; ++e) {
+                int32_t pos = 0;
+                while (row->S[pos] != row->rank[e]) ++pos;
+                if (blen < k || pos < k - 1) ++counted;
+            }
+            row->grp[ng].hop = (int32_t)order[i].d;
+            row->grp[ng].cnt = ne - first;
+            row->grp[ng].counted = counted;
+            row->grp[ng].wt = hip_weight(row->S, blen, k);
+            row->grp[ng].first = first;
+            ++ng;
+        }
+        i = j;
+    }
+    row->ng = ng;
+    row->ne = ne;
+    row->slen = blen;
+    return ORC_OK;
+}
+
+/* Every vertex's ADS of a weighted graph by the definition (Algorithm 1 in
+   Dijkstra order), stored like the unweighted build (group "hop" = the
+   distance); the final sketch S is the bottom-k of each component.  hops =
+   the largest distance of an entry; edge_merges = 0 (no propagation). */
+int orc_build_sketches_weighted(orc_graph* g, int k, uint64_t seed) {
+    if (!g || !g->wts || k < 2 || k > 64) return ORC_EINVAL;
+    orc_clear_ads(g);
+    const int64_t n = g->n;
+    const int64_t nnz = g->rowp[n];
+    wads_row* rows = (wads_row*)calloc((size_t)(n > 0 ? n : 1), sizeof(wads_row));
+    if (!rows) return ORC_ENOMEM;
+    int rc = ORC_OK;
+#pragma omp parallel
+    {
+        int64_t* dist = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+        heap_item* heap = (heap_item*)malloc((size_t)(nnz + 2) * sizeof(heap_item));
+        dist_rank* order = (dist_rank*)malloc((size_t)(n > 0 ? n : 1) * sizeof(dist_rank));
+        int lrc = (dist && heap && order) ? ORC_OK : ORC_ENOMEM;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t v = 0; v < n; ++v)
+            if (lrc == ORC_OK) lrc = wads_one(g, k, seed, (int32_t)v, dist, heap, order, &rows[v]);
+        if (lrc != ORC_OK) {
+#pragma omp critical
+            rc = lrc;
+        }
+        free(dist); free(heap); free(order);
+    }
+    if (rc == ORC_OK) {
+        g->gofs = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+        g->eofs = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+        g->S = (uint64_t*)malloc((size_t)(n > 0 ? n : 1) * k * sizeof(uint64_t));
+        g->Scnt = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+        if (!g->gofs || !g->eofs || !g->S || !g->Scnt) rc = ORC_ENOMEM;
+    }
+    if (rc == ORC_OK) {
+        for (int64_t v = 0; v < n; ++v) {
+            g->gofs[v + 1] = g->gofs[v] + rows[v].ng;
+            g->eofs[v + 1] = g->eofs[v] + rows[v].ne;
+        }
+        g->ngroups = g->gofs[n];
+        g->nentries = g->eofs[n];
+        g->grp = (orc_group*)malloc((size_t)(g->ngroups > 0 ? g->ngroups : 1) * sizeof(orc_group));
+        g->ent_id = (int32_t*)malloc((size_t)(g->nentries > 0 ? g->nentries : 1) * sizeof(int32_t));
+        g->ent_rank = (uint64_t*)malloc((size_t)(g->nentries > 0 ? g->nentries : 1) * sizeof(uint64_t));
+        if (!g->grp || !g->ent_id || !g->ent_rank) rc = ORC_ENOMEM;
+    }
+    if (rc == ORC_OK) {
+        int64_t maxd = 0;
+        for (int64_t v = 0; v < n; ++v) {
+            const wads_row* w = &rows[v];
+            for (int32_t i = 0; i < w->ng; ++i) {
+                orc_group gr = w->grp[i];
+                gr.first += g->eofs[v];
+                g->grp[g->gofs[v] + i] = gr;
+                if (gr.hop > maxd) maxd = gr.hop;
+            }
+            if (w->ne > 0) {
+                memcpy(&g->ent_id[g->eofs[v]], w->id, (size_t)w->ne * sizeof(int32_t));
+                memcpy(&g->ent_rank[g->eofs[v]], w->rank, (size_t)w->ne * sizeof(uint64_t));
+            }
+            g->Scnt[v] = w->slen;
+            for (int i = 0; i < k; ++i) g->S[v * k + i] = i < w->slen ? w->S[i] : UINT64_MAX;
+        }
+        g->k = k;
+        g->seed = seed;
+        g->hops = maxd;
+        g->edge_merges = 0;
+        g->built = 1;
+    }
+    for (int64_t v = 0; v < n; ++v) { free(rows[v].grp); free(rows[v].id); free(rows[v].rank); }
+    free(rows);
+    if (rc != ORC_OK) orc_clear_ads(g);
+    return rc;
+}
+
+/* ---- the paper's Algorithm 2 with CleanUp (the second form) ---- */
+
+typedef struct { uint64_t rank; int64_t d; int32_t id; int32_t fresh; } went;
+
+static int dist_rank_cmp_went(const void* a, const void* b) {
+    const went* x = (const went*)a;
+    const went* y = (const went*)b;
+    if (x->d != y->d) return (x->d > y->d) - (x->d < y->d);
+    return (x->rank > y->rank) - (x->rank < y->rank);
+}
+
+/* Position of the first entry after (d, rank) in (distance, rank) order. */
+static int32_t went_upper(const went* L, int32_t len, int64_t d, uint64_t rank) {
+    int32_t lo = 0, hi = len;
+    while (lo < hi) {
+        int32_t mid = (lo + hi) / 2;
+        if (L[mid].d < d || (L[mid].d == d && L[mid].rank <= rank)) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+/* Receiver test of Algorithm 2 for a candidate (id, d): fewer than k
+   entries of the list precede it in (distance, rank) order with a smaller
+   rank.  Entries of the list sit at their current (upper-bound) distances. */
+static int went_accepts(const went* L, int32_t len, int k, int64_t d, uint64_t rank) {
+    int32_t smaller = 0;
+    for (int32_t i = 0; i < len; ++i) {
+        if (L[i].d > d || (L[i].d == d && L[i].rank >= rank)) break;
+        if (L[i].rank < rank && ++smaller >= k) return 0;
+    }
+    return 1;
+}
+
+/* CleanUp: keep an entry iff fewer than k kept entries before it (in
+   (distance, rank) order) have a smaller rank.  Returns entries removed. */
+static int64_t went_cleanup(went* L, int32_t* len, int k) {
+    uint64_t B[64];
+    int32_t blen = 0, out = 0;
+    int64_t removed = 0;
+    for (int32_t i = 0; i < *len; ++i) {
+        uint64_t r = L[i].rank;
+        if (blen < k || r < B[k - 1]) {
+            bottomk_insert(B, &blen, k, r);
+            L[out++] = L[i];
+        } else {
+            ++removed;
+        }
+    }
+    *len = out;
+    return removed;
+}
+
+/* Supersteps: in each, every vertex sends the entries it accepted in the
+   previous superstep (distance + edge length) to its neighbours; each
+   receiver takes its candidates in (distance, rank) order, skips those whose
+   vertex it already holds at a distance <= d, drops a farther entry of the
+   same vertex, inserts the candidate when the receiver test passes, and then
+   runs CleanUp.  Until no vertex accepts anything.  Output: per vertex its
+   entries in (distance, rank) order (eofs n+1 offsets; eid, edist up to
+   `cap` entries), the supersteps run and the entries CleanUp removed. */
+int orc_wads_rounds(const orc_graph* g, int k, uint64_t seed, int64_t cap, int64_t* eofs, int32_t* eid,
+                    int64_t* edist, int64_t* steps, int64_t* cleaned) {
+    if (!g || !g->wts || k < 2 || k > 64) return ORC_EINVAL;
+    const int64_t n = g->n;
+    went** L = (went**)calloc((size_t)(n > 0 ? n : 1), sizeof(went*));
+    int32_t* len = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    int32_t* capv = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    if (!L || !len || !capv) { free(L); free(len); free(capv); return ORC_ENOMEM; }
+    int rc = ORC_OK;
+    for (int64_t v = 0; v < n && rc == ORC_OK; ++v) {
+        capv[v] = 8;
+        L[v] = (went*)malloc(8 * sizeof(went));
+        if (!L[v]) { rc = ORC_ENOMEM; break; }
+        L[v][0].rank = orc_rank(seed, v); L[v][0].d = 0; L[v][0].id = (int32_t)v; L[v][0].fresh = 1;
+        len[v] = 1;
+    }
+    int64_t step = 0, removed = 0;
+    went* cand = NULL;
+    int64_t cand_cap = 0;
+    while (rc == ORC_OK) {
+        /* snapshot of this superstep's messages: the fresh entries */
+        int64_t nmsg = 0;
+        for (int64_t v = 0; v < n; ++v)
+            for (int32_t i = 0; i < len[v]; ++i) nmsg += L[v][i].fresh ? 1 : 0;
+        if (nmsg == 0) break;
+        ++step;
+        went** msg = (went**)calloc((size_t)n, sizeof(went*));
+        int32_t* mlen = (int32_t*)calloc((size_t)n, sizeof(int32_t));
+        if (!msg || !mlen) { free(msg); free(mlen); rc = ORC_ENOMEM; break; }
+        for (int64_t v = 0; v < n && rc == ORC_OK; ++v) {
+            int32_t c = 0;
+            for (int32_t i = 0; i < len[v]; ++i) c += L[v][i].fresh ? 1 : 0;
+            msg[v] = (went*)malloc((size_t)(c > 0 ? c : 1) * sizeof(went));
+            if (!msg[v]) { rc = ORC_ENOMEM; break; }
+            c = 0;
+            for (int32_t i = 0; i < len[v]; ++i)
+                if (L[v][i].fresh) { msg[v][c++] = L[v][i]; L[v][i].fresh = 0; }
+            mlen[v] = c;
+        }
+        for (int64_t v = 0; v < n && rc == ORC_OK; ++v) {
+            /* candidates from every neighbour's messages */
+            int64_t nc = 0;
+            for (int64_t e = g->rowp[v]; e < g->rowp[v + 1]; ++e) nc += mlen[g->cols[e]];
+            if (nc == 0) continue;
+            if (nc > cand_cap) {
+                cand_cap = nc * 2;
+                went* t = (went*)realloc(cand, (size_t)cand_cap * sizeof(went));
+                if (!t) { rc = ORC_ENOMEM; break; }
+                cand = t;
+            }
+            nc = 0;
+            for (int64_t e = g->rowp[v]; e < g->rowp[v + 1]; ++e) {
+                int32_t u = g->cols[e];
+                for (int32_t i = 0; i < mlen[u]; ++i) {
+                    cand[nc] = msg[u][i];
+                    cand[nc].d = msg[u][i].d + g->wts[e];
+                    cand[nc].fresh = 1;
+                    ++nc;
+                }
+            }
+            qsort(cand, (size_t)nc, sizeof(went), dist_rank_cmp_went);
+            for (int64_t c = 0; c < nc; ++c) {
+                went x = cand[c];
+                int32_t at = -1;
+                for (int32_t i = 0; i < len[v]; ++i)
+                    if (L[v][i].id == x.id) { at = i; break; }
+                if (at >= 0 && L[v][at].d <= x.d) continue;
+                if (!went_accepts(L[v], len[v], k, x.d, x.rank)) continue;
+                if (at >= 0) {  /* the same vertex, farther: replaced */
+                    memmove(&L[v][at], &L[v][at + 1], (size_t)(len[v] - at - 1) * sizeof(went));
+                    --len[v];
+                }
+                if (len[v] == capv[v]) {
+                    capv[v] *= 2;
+                    went* t = (went*)realloc(L[v], (size_t)capv[v] * sizeof(went));
+                    if (!t) { rc = ORC_ENOMEM; break; }
+                    L[v] = t;
+                }
+                int32_t pos = went_upper(L[v], len[v], x.d, x.rank);
+                memmove(&L[v][pos + 1], &L[v][pos], (size_t)(len[v] - pos) * sizeof(went));
+                L[v][pos] = x;
+                ++len[v];
+            }
+            removed += went_cleanup(L[v], &len[v], k);
+        }
+        for (int64_t v = 0; v < n; ++v) free(msg[v]);
+        free(msg); free(mlen);
+    }
+    free(cand);
+    if (rc == ORC_OK) {
+        eofs[0] = 0;
+        for (int64_t v = 0; v < n; ++v) eofs[v + 1] = eofs[v] + len[v];
+        if (eofs[n] > cap) rc = ORC_EINVAL;
+    }
+    if (rc == ORC_OK) {
+        for (int64_t v = 0; v < n; ++v)
+            for (int32_t i = 0; i < len[v]; ++i) {
+                eid[eofs[v] + i] = L[v][i].id;
+                edist[eofs[v] + i] = L[v][i].d;
+            }
+        *steps = step;
+        *cleaned = removed;
+    }
+    for (int64_t v = 0; v < n; ++v) free(L[v]);
+    free(L); free(len); free(capv);
+    return rc;
+}
+
+/* ---- phase (iii) and assignment on weighted distances ---- */
+
+/* The lexicographically-first MIS of H-bar under (r_f, pi_f) with balls of
+   weighted distance: Ball(f) = clients within distance floor(r_f) of f,
+   found by Dijkstra from f, stopped at the first claimed client. */
+int orc_open_facilities_weighted(const orc_graph* g, const double* r, const uint8_t* client, uint64_t seed,
+                                 uint8_t* open, int64_t* n_open) {
+    if (!g || !g->wts) return ORC_EINVAL;
+    const int64_t n = g->n;
+    const int64_t nnz = g->rowp[n];
+    int64_t m = 0;
+    for (int64_t f = 0; f < n; ++f) if (r[f] < INFINITY) ++m;
+    cand_t* c = (cand_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(cand_t));
+    uint8_t* claimed = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+    int64_t* dist = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int32_t* seen = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t* ball = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    heap_item* heap = (heap_item*)malloc((size_t)(nnz + 2) * sizeof(heap_item));
+    if (!c || !claimed || !dist || !seen || !ball || !heap) {
+        free(c); free(claimed); free(dist); free(seen); free(ball); free(heap);
+        return ORC_ENOMEM;
+    }
+    m = 0;
+    for (int64_t f = 0; f < n; ++f)
+        if (r[f] < INFINITY) { c[m].r = r[f]; c[m].pi = orc_priority(seed, f); c[m].f = (int32_t)f; ++m; }
+    qsort(c, (size_t)m, sizeof(cand_t), cand_cmp);
+    for (int64_t v = 0; v < n; ++v) { dist[v] = -1; open[v] = 0; }
+    int64_t opened = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        const int32_t f = c[i].f;
+        const int64_t B = ball_depth(c[i].r);
+        int64_t hn = 0, ns = 0, nb = 0;
+        int conflict = 0;
+        heap_item s0 = {0, 0, f};
+        heap_push(heap, &hn, s0);
+        while (hn > 0 && !conflict) {
+            heap_item it = heap_pop(heap, &hn);
+            if (dist[it.v] >= 0) continue;
+            dist[it.v] = it.key;
+            seen[ns++] = it.v;
+            if (client[it.v]) {
+                if (claimed[it.v]) { conflict = 1; break; }
+                ball[nb++] = it.v;
+            }
+            for (int64_t e = g->rowp[it.v]; e < g->rowp[it.v + 1]; ++e) {
+                int32_t u = g->cols[e];
+                int64_t du = it.key + g->wts[e];
+                if (dist[u] >= 0 || du > B) continue;
+                heap_item nx = {du, 0, u};
+                heap_push(heap, &hn, nx);
+            }
+        }
+        for (int64_t j = 0; j < ns; ++j) dist[seen[j]] = -1;
+        if (conflict) continue;
+        open[f] = 1;
+        ++opened;
+        for (int64_t j = 0; j < nb; ++j) claimed[ball[j]] = 1;
+    }
+    *n_open = opened;
+    free(c); free(claimed); free(dist); free(seen); free(ball); free(heap);
+    return ORC_OK;
+}
+
+/* Nearest open facility by weighted distance (Section 3.1, d(c, S)): one
+   Dijkstra from every open facility at once, ordered by (distance, facility
+   id), so a vertex is settled with its smallest distance and, among the
+   facilities at that distance, the smallest id.  -1 / -1 when none is
+   reachable. */
+int orc_assign_weighted(const orc_graph* g, const uint8_t* open, int32_t* assign, int32_t* dist) {
+    if (!g || !g->wts) return ORC_EINVAL;
+    const int64_t n = g->n;
+    const int64_t nnz = g->rowp[n];
+    heap_item* heap = (heap_item*)malloc((size_t)(nnz + n + 2) * sizeof(heap_item));
+    if (!heap) return ORC_ENOMEM;
+    int64_t hn = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        dist[v] = -1;
+        assign[v] = -1;
+        if (open[v]) { heap_item s0 = {0, v, (int32_t)v}; heap_push(heap, &hn, s0); }
+    }
+    int rc = ORC_OK;
+    while (hn > 0) {
+        heap_item it = heap_pop(heap, &hn);
+        if (dist[it.v] >= 0) continue;
+        if (it.key > 2147483647LL) { rc = ORC_EINVAL; break; }
+        dist[it.v] = (int32_t)it.key;
+        assign[it.v] = (int32_t)it.tie;
+        for (int64_t e = g->rowp[it.v]; e < g->rowp[it.v + 1]; ++e) {
+            int32_t u = g->cols[e];
+            if (dist[u] >= 0) continue;
+            heap_item nx = {it.key + g->wts[e], it.tie, u};
+            heap_push(heap, &hn, nx);
+        }
+    }
+    free(heap);
+    return rc;
 }

@@ -59,6 +59,32 @@ def apsp(rowp, cols) -> np.ndarray:
     return D
 
 
+def apsp_weighted(rowp, cols, w) -> np.ndarray:
+    """All-pairs distances with edge lengths w (one per CSR entry) by
+    Floyd-Warshall; -1 = unreachable."""
+    n = len(rowp) - 1
+    INF = 1 << 60
+    D = [[INF] * n for _ in range(n)]
+    for v in range(n):
+        D[v][v] = 0
+        for e in range(int(rowp[v]), int(rowp[v + 1])):
+            u = int(cols[e])
+            D[v][u] = min(D[v][u], int(w[e]))
+    for m in range(n):
+        Dm = D[m]
+        for i in range(n):
+            dim = D[i][m]
+            if dim >= INF:
+                continue
+            Di = D[i]
+            for j in range(n):
+                if dim + Dm[j] < Di[j]:
+                    Di[j] = dim + Dm[j]
+    out = np.array(D, np.int64)
+    out[out >= INF] = -1
+    return out
+
+
 def ball(D, v, h):
     return [w for w in range(D.shape[0]) if 0 <= D[v, w] <= h]
 
