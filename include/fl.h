@@ -74,6 +74,26 @@ typedef struct fl_solve fl_solve; /* one instance: costs, clients, radii, open s
 int fl_graph_create(int64_t n, const int64_t* row_off, const int32_t* cols, int64_t nnz,
                     int mem_kind, void* stream, fl_graph** out);
 
+/*
+ * fl_graph_create_weighted -- upload a weighted graph (Section 3.3, after
+ * Algorithm 2: the Giraph ADS algorithm also handles weighted graphs;
+ * Section 5 draws weights uniformly in [1, 100]).  Arguments as
+ * fl_graph_create, plus
+ *   lengths  int32[nnz] edge length of each CSR entry, an integer in
+ *            [1, 65535], equal for (u, v) and (v, u) (same mem_kind).
+ * fl_build_sketches then builds the ADS in Dijkstra order: one group per
+ * distance (the group's "hop" is the distance, at most 65535, else
+ * FL_EINVAL), with the HIP weights and counted prefixes of the unweighted
+ * build, equal to the ADS that the paper's BFS-order supersteps reach after
+ * CleanUp; fl_sketch_stats reports the largest distance as hops and 0
+ * edge-merges.  fl_compute_radii solves Eq. 1 over these distances.  The
+ * selection, the assignment, the epsilon > 0 phase, exact ball sizes and
+ * batches are not built for weighted graphs: those calls return FL_ESTATE.
+ * The graph keeps the caller's vertex numbering.
+ */
+int fl_graph_create_weighted(int64_t n, const int64_t* row_off, const int32_t* cols, const int32_t* lengths,
+                             int64_t nnz, int mem_kind, void* stream, fl_graph** out);
+
 /* fl_graph_destroy -- free the handle and all its device memory (NULL ok). */
 int fl_graph_destroy(fl_graph* g);
 

@@ -23,7 +23,7 @@ _lib = None
 FL_OK, FL_EINVAL, FL_ESTATE, FL_ENOMEM, FL_ECUDA, FL_ETIMEOUT = range(6)
 FL_MEM_HOST, FL_MEM_DEVICE = 0, 1
 
-EXPORTS = ("fl_graph_create", "fl_graph_destroy", "fl_build_sketches", "fl_sketch_stats",
+EXPORTS = ("fl_graph_create", "fl_graph_create_weighted", "fl_graph_destroy", "fl_build_sketches", "fl_sketch_stats",
            "fl_export_sketches", "fl_export_ads", "fl_solve_create", "fl_solve_destroy",
            "fl_compute_radii", "fl_open_facilities", "fl_assign_clients", "fl_objective",
            "fl_solve_stats", "fl_mis_log", "fl_status_str", "fl_last_error", "fl_profile_enable", "fl_profile_reset",
@@ -71,6 +71,7 @@ def load(build_if_missing: bool = True):
         P64 = ctypes.POINTER(i64)
         sig = {
             "fl_graph_create": ([i64, vp, vp, i64, ci, vp, ctypes.POINTER(vp)], ci),
+            "fl_graph_create_weighted": ([i64, vp, vp, vp, i64, ci, vp, ctypes.POINTER(vp)], ci),
             "fl_graph_destroy": ([vp], ci),
             "fl_build_sketches": ([vp, ci, u64], ci),
             "fl_sketch_stats": ([vp, P64, P64, P64, P64], ci),
@@ -172,16 +173,26 @@ def _kind(*kinds):
 class Graph:
     """fl_graph: a CSR graph on the device with its sketches and ADS."""
 
-    def __init__(self, rowp, cols, stream=None):
+    def __init__(self, rowp, cols, stream=None, lengths=None):
+        """lengths: int32 edge length per CSR entry (a weighted graph, see
+        fl_graph_create_weighted), or None."""
         self._lib = load()
         p_r, k_r, _ = _arg(rowp, np.int64)
         p_c, k_c, _ = _arg(cols, np.int32)
-        kind = _kind(k_r, k_c)
         self.n = int(len(rowp) - 1)
         self.nnz = int(len(cols))
         st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
         h = ctypes.c_void_p()
-        _check(self._lib.fl_graph_create(self.n, p_r, p_c, self.nnz, kind, st, ctypes.byref(h)))
+        self.weighted = lengths is not None
+        if lengths is None:
+            kind = _kind(k_r, k_c)
+            _check(self._lib.fl_graph_create(self.n, p_r, p_c, self.nnz, kind, st, ctypes.byref(h)))
+        else:
+            if len(lengths) != len(cols):
+                raise ValueError("lengths must have one entry per CSR column")
+            p_w, k_w, _ = _arg(lengths, np.int32)
+            kind = _kind(k_r, k_c, k_w)
+            _check(self._lib.fl_graph_create_weighted(self.n, p_r, p_c, p_w, self.nnz, kind, st, ctypes.byref(h)))
         self._h = h
         self.k = None
         self.seed = None

@@ -33,7 +33,7 @@ int copy_out(void* dst, const void* src, size_t bytes, int mem_kind, cudaStream_
 
 void destroy_graph(fl_graph* g) {
     cudaStreamSynchronize(g->stream);  // its buffers go to the idle-block cache
-    DBuf* bufs[] = {&g->rowp, &g->cols, &g->low_list, &g->small_list, &g->mid_list, &g->hub_list, &g->hub_seg, &g->seg_hub, &g->part,
+    DBuf* bufs[] = {&g->rowp, &g->cols, &g->wts, &g->low_list, &g->small_list, &g->mid_list, &g->hub_list, &g->hub_seg, &g->seg_hub, &g->part,
                     &g->S, &g->Scnt, &g->D[0], &g->D[1], &g->Dcnt[0], &g->Dcnt[1], &g->frontier[0],
                     &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent, &g->stg_grp, &g->gofs, &g->eofs,
                     &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub, &g->ctr, &g->scratch,
@@ -197,6 +197,46 @@ int fl_graph_create(int64_t n, const int64_t* row_off, const int32_t* cols, int6
         set_current_prof(&g->prof, g->stream);
         if ((rc = validate_csr(g))) break;
         if ((rc = relabel_graph(g))) break;
+    } while (0);
+    if (rc != FL_OK) {
+        destroy_graph(g);
+        return rc;
+    }
+    *out = g;
+    return FL_OK;
+}
+
+int fl_graph_create_weighted(int64_t n, const int64_t* row_off, const int32_t* cols, const int32_t* lengths,
+                             int64_t nnz, int mem_kind, void* stream, fl_graph** out) {
+    if (!out) FL_FAIL(FL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 2147483647LL) FL_FAIL(FL_EINVAL, "n must be in [1, 2^31-1]");
+    if (nnz < 0 || !row_off || (nnz > 0 && (!cols || !lengths))) FL_FAIL(FL_EINVAL, "bad CSR arrays");
+    if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
+    fl_graph* g = new (std::nothrow) fl_graph();
+    if (!g) FL_FAIL(FL_ENOMEM, "host allocation failed");
+    ProfScope ps(nullptr);
+    g->n = n;
+    g->nnz = nnz;
+    g->stream = static_cast<cudaStream_t>(stream);
+    int rc = FL_OK;
+    do {
+        cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&g->h_ctr), sizeof(Counters));
+        if (e != cudaSuccess) { rc = status_of(e, "cudaMallocHost", __FILE__, __LINE__); break; }
+        if ((rc = dalloc(g->ctr, sizeof(Counters)))) break;
+        if ((rc = dalloc(g->rowp, (size_t)(n + 1) * 8))) break;
+        if ((rc = dalloc(g->cols, (size_t)(nnz > 0 ? nnz : 1) * 4))) break;
+        if ((rc = dalloc(g->wts, (size_t)(nnz > 0 ? nnz : 1) * 4))) break;
+        e = cudaMemcpyAsync(g->rowp.p, row_off, (size_t)(n + 1) * 8, kind_in(mem_kind), g->stream);
+        if (e == cudaSuccess && nnz > 0)
+            e = cudaMemcpyAsync(g->cols.p, cols, (size_t)nnz * 4, kind_in(mem_kind), g->stream);
+        if (e == cudaSuccess && nnz > 0)
+            e = cudaMemcpyAsync(g->wts.p, lengths, (size_t)nnz * 4, kind_in(mem_kind), g->stream);
+        if (e != cudaSuccess) { rc = status_of(e, "CSR upload", __FILE__, __LINE__); break; }
+        set_current_prof(&g->prof, g->stream);
+        if ((rc = validate_csr(g))) break;
+        if ((rc = check_weights(g))) break;
+        // kept in the caller's numbering: the lengths stay aligned with the columns
     } while (0);
     if (rc != FL_OK) {
         destroy_graph(g);
@@ -423,9 +463,18 @@ int fl_compute_radii(fl_solve* s, const double* open_cost, const uint8_t* client
     return FL_OK;
 }
 
+// The selection, the assignment, the epsilon > 0 phase, exact ball sizes and
+// batches are built for unweighted graphs; on a weighted graph they return
+// FL_ESTATE (sketches, ADS and radii are built for both).
+static int unweighted_only(const fl_graph* g, const char* what) {
+    if (g && g->wts.p) FL_FAIL(FL_ESTATE, std::string(what) + " is not built for weighted graphs");
+    return FL_OK;
+}
+
 int fl_compute_radii_exact(fl_solve* s, const double* open_cost, const uint8_t* client_mask, int mem_kind,
                            double* radii_out) {
     FL_TRY(check_solve(s));
+    FL_TRY(unweighted_only(s->g, "fl_compute_radii_exact"));
     if (!open_cost || !client_mask) FL_FAIL(FL_EINVAL, "open_cost and client_mask are required");
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
     ProfScope ps(s->g);
@@ -439,6 +488,7 @@ int fl_compute_radii_exact(fl_solve* s, const double* open_cost, const uint8_t* 
 
 int fl_open_facilities(fl_solve* s, uint8_t* open_out, int64_t* n_open, int mem_kind) {
     FL_TRY(check_solve(s));
+    FL_TRY(unweighted_only(s->g, "fl_open_facilities"));
     if (!s->have_radii) FL_FAIL(FL_ESTATE, "compute radii first");
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
     s->have_open = s->have_assign = 0;
@@ -461,6 +511,7 @@ int fl_open_facilities_eps(fl_solve* s, double eps, const double* open_cost, con
                            int mem_kind, uint8_t* open_out, int64_t* n_open, int32_t* fac_iter_out,
                            int32_t* cli_iter_out) {
     FL_TRY(check_solve(s));
+    FL_TRY(unweighted_only(s->g, "fl_open_facilities_eps"));
     if (!(eps > 0.0) || !(eps <= 1.0e6)) FL_FAIL(FL_EINVAL, "eps must be in (0, 1e6]");
     if (!open_cost || !client_mask) FL_FAIL(FL_EINVAL, "open_cost and client_mask are required");
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
@@ -511,6 +562,7 @@ int fl_eps_stats(const fl_solve* s, double* gamma, double* alpha0, int64_t* iter
 
 int fl_assign_clients(fl_solve* s, int32_t* assign_out, int32_t* dist_out, int mem_kind) {
     FL_TRY(check_solve(s));
+    FL_TRY(unweighted_only(s->g, "fl_assign_clients"));
     if (!s->have_open) FL_FAIL(FL_ESTATE, "open facilities first");
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
     ProfScope ps(s->g);
@@ -549,6 +601,7 @@ int fl_objective(fl_solve* s, double* obj, int64_t* dist_sum, int64_t* n_unserve
 int fl_ball_sizes(fl_graph* g, int64_t n_src, const int32_t* src, int32_t max_dist, const uint8_t* pred,
                   int mem_kind, int64_t* out) {
     if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    FL_TRY(unweighted_only(g, "fl_ball_sizes"));
     if (n_src < 0 || max_dist < 0) FL_FAIL(FL_EINVAL, "n_src and max_dist must be >= 0");
     if (n_src > 0 && (!src || !out)) FL_FAIL(FL_EINVAL, "src and out are required");
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
@@ -733,6 +786,7 @@ int fl_batch_create_replicas(fl_graph* g, int n_inst, void* stream, fl_batch** o
     if (!out) FL_FAIL(FL_EINVAL, "out is NULL");
     *out = nullptr;
     if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
+    FL_TRY(unweighted_only(g, "a batch"));
     if (!g->built) FL_FAIL(FL_ESTATE, "build the sketches before creating a replica batch");
     if (n_inst < 1) FL_FAIL(FL_EINVAL, "n_inst must be >= 1");
     if ((int64_t)n_inst * g->n > 2147483647LL) FL_FAIL(FL_EINVAL, "n_inst * n exceeds 2^31-1 vertices");

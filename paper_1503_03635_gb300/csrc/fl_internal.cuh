@@ -185,6 +185,13 @@ __device__ __forceinline__ bool warp_member(uint64_t L, uint64_t x) {
     return pos < 32 && y == x;
 }
 
+// HIP weight of a group whose ball holds cnt ranks with k-th smallest kth:
+// 1 while the ball has fewer than k vertices, else 1 / Pr[rank < k-th] =
+// 2^64 / kth (one IEEE division).
+__device__ __forceinline__ double hip_weight(int cnt, int k, uint64_t kth) {
+    return cnt < k ? 1.0 : __ddiv_rn(18446744073709551616.0, __ull2double_rn(kth));
+}
+
 // Position of the n-th (0-based) set bit of m (m must have > n set bits).
 __device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
     int pos = 0;
@@ -442,6 +449,9 @@ struct fl_graph {
     int64_t n = 0, nnz = 0;
     cudaStream_t stream = nullptr;
     fl::DBuf rowp, cols;           // int64[n+1], int32[nnz]
+    fl::DBuf wts;                  // int32[nnz]: edge lengths of a weighted graph, else empty
+    int max_w = 0;                 // largest edge length
+    int64_t wlevels = 0;           // distance levels with active vertices in the last weighted build
     // static work lists: non-hub non-isolated vertices, hubs, hub segments
     int lists_ready = 0;
     fl::DBuf low_list, hub_list;   // int32[n_low], int32[n_hubs]
@@ -575,6 +585,9 @@ int sort_pairs_u128_digits(uint64_t* hi, uint64_t* lo, uint32_t* val, int64_t n,
 int validate_csr(fl_graph* g);
 int build_work_lists(fl_graph* g);
 int build_sketches(fl_graph* g, int k, uint64_t seed);
+// weighted graphs (k_wsketch.cu): length check, and the build in Dijkstra order
+int check_weights(fl_graph* g);
+int build_sketches_weighted(fl_graph* g, int k, uint64_t seed);
 int compute_ecc_bound(fl_graph* g);
 
 int check_costs(fl_solve* s);

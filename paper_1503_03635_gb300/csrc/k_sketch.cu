@@ -528,12 +528,6 @@ __device__ __forceinline__ void stage_group(const HopIO& io, int32_t v, int64_t 
     }
 }
 
-// HIP weight of a group whose ball holds cnt ranks with k-th smallest kth:
-// 1 while the ball has fewer than k vertices, else 1 / Pr[rank < k-th] =
-// 2^64 / kth (one IEEE division).
-__device__ __forceinline__ double hip_weight(int cnt, int k, uint64_t kth) {
-    return cnt < k ? 1.0 : __ddiv_rn(18446744073709551616.0, __ull2double_rn(kth));
-}
 
 // Write the results of vertex v after a list or slice merge: new sketch, the
 // entries it gained (list, mask, head word, smallest one, for the next hop),
@@ -1247,6 +1241,16 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     ++g->generation;
     g->k = k;
     g->seed = seed;
+    if (g->wts.p) {  // a weighted graph: levels in Dijkstra order (k_wsketch.cu)
+        g->hop_scanned.clear();
+        g->hop_mask.clear();
+        g->hop_changed.clear();
+        g->hop_ms.clear();
+        for (auto* vec : {&g->hop_E, &g->hop_A, &g->hop_R, &g->hop_SD, &g->hop_new}) vec->clear();
+        FL_TRY(build_sketches_weighted(g, k, seed));
+        g->built = 1;
+        return FL_OK;
+    }
     if (!g->lists_ready) {
         FL_TRY(build_work_lists(g));
         g->lists_ready = 1;
