@@ -342,6 +342,11 @@ def run_gpu(args):
     g_schedule = g.schedule
     prof = {name: g.profile_query(name) for name in fl.PROF_CLASSES}
     launches = g.profile_query(-1)["launches"]
+    # the per-hop census (scanned / mask-merged entries) takes extra kernels:
+    # one more build outside the timed region collects it
+    g.profile(True, census=True)
+    g.build_sketches(w.k, w.seed)
+    g.profile(False)
     model = g.hop_model()
     hop_detail = [{"hop": h["hop"], "ms": round(h["ms"], 3), "scanned": h["scanned"],
                    "mask_share": round(h["mask"] / h["scanned"], 4) if h["scanned"] else 0.0,

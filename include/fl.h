@@ -336,7 +336,9 @@ int fl_compute_radii_exact(fl_solve* s, const double* open_cost, const uint8_t* 
 #define FL_PROF_OTHER 7
 #define FL_PROF_EXACT 8
 
-/* fl_profile_enable -- turn CUDA-event timing of launches on (1) or off (0). */
+/* fl_profile_enable -- CUDA-event timing of launches off (0), on (1), or on
+   with the per-hop census of the sketch build (2: extra kernels that count
+   the scanned and mask-merged CSR entries of each hop, fl_hop_stats). */
 int fl_profile_enable(fl_graph* g, int on);
 /* fl_profile_reset -- zero all counters and times (synchronises the stream). */
 int fl_profile_reset(fl_graph* g);
@@ -350,12 +352,13 @@ int fl_profile_query(const fl_graph* g, int kernel_class, int64_t* launches, dou
  *   n_hops        set to the number of processed hops, H* + 1 (entries
  *                 written: min(n_hops, cap)).
  *   changed[h-1]  vertices whose sketch changed at hop h.
- * When profiling was on (fl_profile_enable) during the build, also:
+ * With the census on (fl_profile_enable level 2) during the build, also:
  *   scanned[h-1]  CSR entries read at hop h (neighbours of the processed
  *                 vertices, hub segments included), else 0;
  *   mask[h-1]     of those, entries read by the mask merge of saturated
  *                 sketches (full sketches whose k-th rank is among the 1024
  *                 smallest ranks of the graph), else 0;
+ * and with profiling on (level 1 or 2):
  *   ms[h-1]       kernel milliseconds of hop h, else 0.
  * Host arrays of cap entries; any of them may be NULL.
  */

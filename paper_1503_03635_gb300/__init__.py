@@ -268,8 +268,10 @@ class Graph:
         names = ("edge_merges", "merging", "delta_read", "delta_sum", "new_entries")
         return [dict(hop=i + 1, **{nm: int(c[i]) for nm, c in zip(names, cols)}) for i in range(h)]
 
-    def profile(self, on: bool = True):
-        _check(self._lib.fl_profile_enable(self._h, 1 if on else 0))
+    def profile(self, on: bool = True, census: bool = False):
+        """CUDA-event timing of launches; census adds the per-hop counts of
+        the sketch build (extra kernels, see fl_hop_stats)."""
+        _check(self._lib.fl_profile_enable(self._h, (2 if census else 1) if on else 0))
 
     def profile_reset(self):
         _check(self._lib.fl_profile_reset(self._h))

@@ -953,7 +953,8 @@ int fl_batch_destroy(fl_batch* b) {
 
 int fl_profile_enable(fl_graph* g, int on) {
     if (!g) FL_FAIL(FL_EINVAL, "null graph handle");
-    g->prof.on = on ? 1 : 0;
+    if (on < 0 || on > 2) FL_FAIL(FL_EINVAL, "on must be 0, 1 or 2");
+    g->prof.on = on;
     return FL_OK;
 }
 

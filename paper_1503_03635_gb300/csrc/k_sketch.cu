@@ -1319,6 +1319,7 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
     g->hop_ms.clear();
     for (auto* vec : {&g->hop_E, &g->hop_A, &g->hop_R, &g->hop_SD, &g->hop_new}) vec->clear();
     const bool time_hops = g->prof.on != 0;
+    const bool census = g->prof.on >= 2;  // per-hop scanned / mask counts (extra kernels)
     if (time_hops && !g->hop_ev[0]) {
         FL_CUDA(cudaEventCreate(&g->hop_ev[0]));
         FL_CUDA(cudaEventCreate(&g->hop_ev[1]));
@@ -1371,7 +1372,7 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
         if (hop > 1)
             FL_LAUNCH(kProfSketchOther, k_front_bitmap<<<grid_for(n, 256), 256, 0, st>>>(
                                             g->Dcnt[pin].as<uint8_t>(), n, g->fbm.as<uint32_t>()));
-        if (time_hops) {
+        if (census) {
             if (n_list > 0)
                 FL_LAUNCH(kProfSketchOther, k_hop_census<<<grid_for(n_list, 256), 256, 0, st>>>(
                                                 list, n_list, g->rowp.as<int64_t>(), g->S.as<uint64_t>(),
@@ -1383,8 +1384,8 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
                                                 g->S.as<uint64_t>(), g->Scnt.as<uint8_t>(), k, hop, g->ulim,
                                                 g->stamp.as<uint32_t>(), dense ? 0u : (uint32_t)hop,
                                                 g->ctr.as<Counters>()));
-            FL_CUDA(cudaEventRecord(g->hop_ev[0], st));
         }
+        if (time_hops) FL_CUDA(cudaEventRecord(g->hop_ev[0], st));
         if (k <= 16 && g->sched.hop_group != 32)
             FL_TRY(launch_hop<16>(g, hop, list, n_list, pin, pout, used_slots, !dense));
         else
@@ -1396,8 +1397,8 @@ int build_sketches(fl_graph* g, int k, uint64_t seed) {
         {
             float hop_ms = 0.f;
             if (time_hops) FL_CUDA(cudaEventElapsedTime(&hop_ms, g->hop_ev[0], g->hop_ev[1]));
-            g->hop_scanned.push_back(time_hops ? (int64_t)g->h_ctr->scanned : 0);
-            g->hop_mask.push_back(time_hops ? (int64_t)g->h_ctr->mask_scanned : 0);
+            g->hop_scanned.push_back(census ? (int64_t)g->h_ctr->scanned : 0);
+            g->hop_mask.push_back(census ? (int64_t)g->h_ctr->mask_scanned : 0);
             g->hop_changed.push_back((int64_t)g->h_ctr->frontier);
             g->hop_ms.push_back(hop_ms);
             g->hop_E.push_back(hop_merges);

@@ -151,7 +151,7 @@ def test_hop_stats_account_for_every_ads_group(scale, k):
     rowp, cols = flsynth.rmat(scale, 16, 700 + scale)
     n = len(rowp) - 1
     g = fl.Graph(rowp, cols)
-    g.profile(True)
+    g.profile(True, census=True)
     g.build_sketches(k, 3)
     st = g.stats()
     hs = g.hop_stats()
