@@ -934,11 +934,13 @@ def run_eps(args):
 
 def run_weighted(args):
     """Weighted graphs (Section 3.3 after Algorithm 2; weights uniform in
-    [1, 100] as in Section 5): the ADS build in Dijkstra order plus the radii
-    on the rmat20 graph with edge lengths from flsynth.edge_weights (k = 16,
-    the rmat20 costs and clients), device-resident inputs.  Value: ADS
-    entries per second of the build.  The oracle's definitional build (one
-    Dijkstra per vertex) on a 2000-vertex ER graph is the CPU baseline."""
+    [1, 100] as in Section 5): the whole path on the rmat20 graph with edge
+    lengths from flsynth.edge_weights (k = 16, the rmat20 costs and clients),
+    device-resident inputs: the ADS build in Dijkstra order, the radii, the
+    greedy MIS with balls by weighted distance, the assignment and the
+    objective.  Value: ADS entries per second of the step.  The oracle's
+    definitional build (one Dijkstra per vertex) on a 2000-vertex ER graph is
+    the CPU baseline."""
     import torch
 
     import paper_1503_03635_gb300 as fl
@@ -960,10 +962,22 @@ def run_weighted(args):
     radii_d = torch.empty(w.n, dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
 
+    open_d = torch.empty(w.n, dtype=torch.uint8, device=dev)
+    assign_d = torch.empty(w.n, dtype=torch.int32, device=dev)
+    dist_d = torch.empty(w.n, dtype=torch.int32, device=dev)
+    out = {}
+
     def step():
         g.build_sketches(k, w.seed)
         s = fl.Solve(g)
         s.compute_radii(cost_d, client_d, radii_d)
+        _, out["n_open"] = s.open_facilities(open_d)
+        s.assign_clients(assign_d, dist_d)
+        out["objective"] = s.objective()
+        out["mis"] = s.stats()
+        log = s.mis_log()
+        out["largest_ball"] = int(log[log[:, 1] == 3][:, 2].max()) if len(log) else 0
+        out["sweep_steps"] = int(log[log[:, 1] != 3][:, 3].sum()) if len(log) else 0
         s.close()
 
     for _ in range(args.warmup):
@@ -1005,8 +1019,12 @@ def run_weighted(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "weighted: rmat20 with edge lengths uniform in [1, 100]", "n": w.n, "nnz": w.nnz,
-                       "k": k, "step": "fl_build_sketches (weighted, Dijkstra order) + fl_compute_radii"},
+                       "k": k, "step": "fl_build_sketches (weighted, Dijkstra order) + fl_compute_radii + "
+                                        "fl_open_facilities + fl_assign_clients + fl_objective"},
             "ads_entries": st["ads_entries"], "ads_groups": st["ads_groups"], "largest_distance": st["hops"],
+            "n_open": out["n_open"], "objective": out["objective"][0], "unserved": out["objective"][2],
+            "mis_rounds": out["mis"]["mis_rounds"], "candidates": out["mis"]["candidates"],
+            "largest_ball_radius": out["largest_ball"], "mis_sweep_steps": out["sweep_steps"],
             "phases_ms_per_step": {kk: v["ms"] / args.steps for kk, v in prof.items()},
             "gpu_launches": launches, "cpu_baseline": cpu, "clocks": clk}
     print(json.dumps(line), flush=True)

@@ -86,10 +86,12 @@ int fl_graph_create(int64_t n, const int64_t* row_off, const int32_t* cols, int6
  * FL_EINVAL), with the HIP weights and counted prefixes of the unweighted
  * build, equal to the ADS that the paper's BFS-order supersteps reach after
  * CleanUp; fl_sketch_stats reports the largest distance as hops and 0
- * edge-merges.  fl_compute_radii solves Eq. 1 over these distances.  The
- * selection, the assignment, the epsilon > 0 phase, exact ball sizes and
- * batches are not built for weighted graphs: those calls return FL_ESTATE.
- * The graph keeps the caller's vertex numbering.
+ * edge-merges.  fl_compute_radii solves Eq. 1 over these distances, and
+ * fl_open_facilities / fl_assign_clients / fl_objective measure balls and
+ * nearest facilities by the sum of lengths (Section 3.1's d(u, v)).  The
+ * epsilon > 0 phase, exact ball sizes and batches are not built for weighted
+ * graphs: those calls return FL_ESTATE.  The graph keeps the caller's vertex
+ * numbering.
  */
 int fl_graph_create_weighted(int64_t n, const int64_t* row_off, const int32_t* cols, const int32_t* lengths,
                              int64_t nnz, int mem_kind, void* stream, fl_graph** out);
@@ -170,8 +172,8 @@ int fl_compute_radii(fl_solve* s, const double* open_cost, const uint8_t* client
  * fl_open_facilities -- phase (iii): the lexicographically-first maximal
  * independent set S of H-bar (Section 4.3, Alg. 6 with the greedy MIS of
  * Blelloch, Fineman and Shun).  Candidates: facilities with finite r_f.
- * Ball(f) = clients within floor(r_f) hops of f; f, g conflict iff their
- * balls share a client.  Keys (r_f, pi_f), pi_f = SplitMix64 output f+1 from
+ * Ball(f) = clients within floor(r_f) hops of f (distance: the sum of the
+ * lengths on a weighted graph); f, g conflict iff their balls share a client.  Keys (r_f, pi_f), pi_f = SplitMix64 output f+1 from
  * the state given by the first output for the sketch seed.
  *   open_out  uint8[n] or NULL (1 = open).   n_open  receives |S| (or NULL).
  * Needs fl_compute_radii first (else FL_ESTATE).
@@ -224,7 +226,9 @@ int fl_eps_stats(const fl_solve* s, double* gamma, double* alpha0, int64_t* iter
  * fl_assign_clients -- nearest open facility of every vertex (Section 3.1,
  * d(c, S) = min over open f of d(c, f)); ties go to the smallest facility id.
  *   assign_out int32[n] or NULL (-1 = no open facility in the component).
- *   dist_out   int32[n] or NULL (hop distance, -1 when unassigned).
+ *   dist_out   int32[n] or NULL (hop distance, -1 when unassigned; on a
+ *              weighted graph the sum of lengths, FL_EINVAL when one is
+ *              above 2^31 - 1).
  */
 int fl_assign_clients(fl_solve* s, int32_t* assign_out, int32_t* dist_out, int mem_kind);
 
@@ -249,7 +253,10 @@ int fl_solve_stats(const fl_solve* s, int64_t* mis_rounds, int64_t* candidates);
  * frontier = undecided facilities at its start, pulled = those it decided);
  * 4: a round of the kill sweep that removes the facilities whose ball holds
  * a client claimed in that greedy round (step = distance, frontier = the
- * vertices it marked).
+ * vertices it marked).  On a weighted graph each sweep (a time-stepped
+ * propagation over the lengths) logs one row: kinds 0 (cover), 1 (gather) and 4
+ * (kill) with step = the last time step run and frontier = the time steps
+ * run, pulled 0; kind 3 as above.
  *   rows    int64[6 * cap] or NULL; the first min(cap, *n_rows) rows are written.
  *   n_rows  receives the number of rows of the last MIS.
  * Host-side timings include the launches and the synchronisation of a round.

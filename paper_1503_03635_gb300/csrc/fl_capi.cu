@@ -463,9 +463,9 @@ int fl_compute_radii(fl_solve* s, const double* open_cost, const uint8_t* client
     return FL_OK;
 }
 
-// The selection, the assignment, the epsilon > 0 phase, exact ball sizes and
-// batches are built for unweighted graphs; on a weighted graph they return
-// FL_ESTATE (sketches, ADS and radii are built for both).
+// The epsilon > 0 phase, exact ball sizes and batches are built for
+// unweighted graphs; on a weighted graph they return FL_ESTATE (sketches, ADS,
+// radii, the selection and the assignment are built for both).
 static int unweighted_only(const fl_graph* g, const char* what) {
     if (g && g->wts.p) FL_FAIL(FL_ESTATE, std::string(what) + " is not built for weighted graphs");
     return FL_OK;
@@ -488,12 +488,11 @@ int fl_compute_radii_exact(fl_solve* s, const double* open_cost, const uint8_t* 
 
 int fl_open_facilities(fl_solve* s, uint8_t* open_out, int64_t* n_open, int mem_kind) {
     FL_TRY(check_solve(s));
-    FL_TRY(unweighted_only(s->g, "fl_open_facilities"));
     if (!s->have_radii) FL_FAIL(FL_ESTATE, "compute radii first");
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
     s->have_open = s->have_assign = 0;
     ProfScope ps(s->g);
-    FL_TRY(open_facilities(s));
+    FL_TRY(s->g->wts.p ? open_facilities_weighted(s) : open_facilities(s));
     if (open_out && s->g->relabelled) {
         FL_TRY(dalloc(s->io, (size_t)s->g->n * 9));
         FL_TRY(permute_vertices<uint8_t>(s->g, s->open.as<uint8_t>(), s->io.as<uint8_t>(), 1, false, s->g->stream));
@@ -562,11 +561,10 @@ int fl_eps_stats(const fl_solve* s, double* gamma, double* alpha0, int64_t* iter
 
 int fl_assign_clients(fl_solve* s, int32_t* assign_out, int32_t* dist_out, int mem_kind) {
     FL_TRY(check_solve(s));
-    FL_TRY(unweighted_only(s->g, "fl_assign_clients"));
     if (!s->have_open) FL_FAIL(FL_ESTATE, "open facilities first");
     if (bad_kind(mem_kind)) FL_FAIL(FL_EINVAL, "bad mem_kind");
     ProfScope ps(s->g);
-    FL_TRY(assign_clients(s));
+    FL_TRY(s->g->wts.p ? assign_weighted(s) : assign_clients(s));
     const int32_t* a = s->assign.as<int32_t>();
     const int32_t* d = s->dist.as<int32_t>();
     if (s->g->relabelled && (assign_out || dist_out)) {  // facility ids are already original ids

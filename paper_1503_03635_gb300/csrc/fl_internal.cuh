@@ -592,7 +592,11 @@ int compute_ecc_bound(fl_graph* g);
 
 int check_costs(fl_solve* s);
 int compute_radii(fl_solve* s);
+int sort_candidates(fl_solve* s, int64_t* m_out);
 int open_facilities(fl_solve* s);
+// the greedy MIS and the assignment by weighted distance (k_wsolve.cu)
+int open_facilities_weighted(fl_solve* s);
+int assign_weighted(fl_solve* s);
 int msbfs(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, int32_t* dist,
           DBuf& X, DBuf& stampb, DBuf* fr, DBuf& frval, int cls);
 int msbfs_graph(fl_graph* g, const int32_t* src_list, int64_t n_src, int32_t* label, int32_t* dist, DBuf& X,

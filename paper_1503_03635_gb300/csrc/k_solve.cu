@@ -791,34 +791,13 @@ __global__ void k_open_list(const uint8_t* __restrict__ state, int64_t n, uint8_
     }
 }
 
-int open_facilities(fl_solve* s) {
+// Candidates (finite r_f) sorted by the key (r_f, pi_f): s->key_val holds
+// their ids in key order, s->state is 0 for a candidate and 3 otherwise.
+int sort_candidates(fl_solve* s, int64_t* m_out) {
     fl_graph* g = s->g;
     const int64_t n = g->n;
     cudaStream_t st = g->stream;
-    // -------- keys: candidates sorted by (r_f, pi_f) -> ordinals
-    FL_TRY(dalloc(s->ord, (size_t)n * 4));
-    FL_TRY(dalloc(s->fac_by_ord, (size_t)n * 4));
-    FL_TRY(dalloc(s->bcap, (size_t)n * 4));
     FL_TRY(dalloc(s->state, (size_t)n));
-    FL_TRY(dalloc(s->claimed, (size_t)n));
-    FL_TRY(dalloc(s->X, (size_t)n * 16));          // two value buffers
-    FL_TRY(dalloc(s->stamp, (size_t)n * 4));
-    FL_TRY(dalloc(s->mval, (size_t)n * 4));
-    FL_TRY(dalloc(s->fr[0], (size_t)n * 4));
-    FL_TRY(dalloc(s->fr[1], (size_t)n * 4));
-    FL_TRY(dalloc(s->frval, (size_t)n * 8 + 64));
-    FL_TRY(dalloc(s->touched, (size_t)n * 4));
-    FL_TRY(dalloc(s->ulist, (size_t)n * 4 * 2));
-    FL_TRY(dalloc(s->ubuck, (size_t)n * 4));
-    FL_TRY(dalloc(s->open, (size_t)n));
-    FL_TRY(dalloc(s->reach, (size_t)n));
-    FL_TRY(dalloc(s->kill, (size_t)n));
-    s->mis_log.clear();
-    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(s->frval.as<char>() + (size_t)n * 8);
-    // cnt[0], cnt[1]: frontier counts; cnt[2]: changed count (dense rounds);
-    // cnt[3]: undecided; cnt[4]: T max; cnt[5]: open list; cnt[6]: touched
-    // solve-owned, grow-only scratch: a cudaFree per solve would synchronise
-    // the whole device (and stall other solves running on other streams)
     DBuf& hi = s->key_hi;
     DBuf& lo = s->key_lo;
     DBuf& val = s->key_val;
@@ -847,6 +826,41 @@ int open_facilities(fl_solve* s) {
             FL_TRY(sort_pairs_u128_digits(hi.as<uint64_t>(), lo.as<uint64_t>(), val.as<uint32_t>(), m, st, g->scratch,
                                           kProfKeys, digits));
     }
+    *m_out = m;
+    return FL_OK;
+}
+
+int open_facilities(fl_solve* s) {
+    fl_graph* g = s->g;
+    const int64_t n = g->n;
+    cudaStream_t st = g->stream;
+    // -------- keys: candidates sorted by (r_f, pi_f) -> ordinals
+    FL_TRY(dalloc(s->ord, (size_t)n * 4));
+    FL_TRY(dalloc(s->fac_by_ord, (size_t)n * 4));
+    FL_TRY(dalloc(s->bcap, (size_t)n * 4));
+    FL_TRY(dalloc(s->state, (size_t)n));
+    FL_TRY(dalloc(s->claimed, (size_t)n));
+    FL_TRY(dalloc(s->X, (size_t)n * 16));          // two value buffers
+    FL_TRY(dalloc(s->stamp, (size_t)n * 4));
+    FL_TRY(dalloc(s->mval, (size_t)n * 4));
+    FL_TRY(dalloc(s->fr[0], (size_t)n * 4));
+    FL_TRY(dalloc(s->fr[1], (size_t)n * 4));
+    FL_TRY(dalloc(s->frval, (size_t)n * 8 + 64));
+    FL_TRY(dalloc(s->touched, (size_t)n * 4));
+    FL_TRY(dalloc(s->ulist, (size_t)n * 4 * 2));
+    FL_TRY(dalloc(s->ubuck, (size_t)n * 4));
+    FL_TRY(dalloc(s->open, (size_t)n));
+    FL_TRY(dalloc(s->reach, (size_t)n));
+    FL_TRY(dalloc(s->kill, (size_t)n));
+    s->mis_log.clear();
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(s->frval.as<char>() + (size_t)n * 8);
+    // cnt[0], cnt[1]: frontier counts; cnt[2]: changed count (dense rounds);
+    // cnt[3]: undecided; cnt[4]: T max; cnt[5]: open list; cnt[6]: touched
+    // solve-owned, grow-only scratch: a cudaFree per solve would synchronise
+    // the whole device (and stall other solves running on other streams)
+    int64_t m = 0;
+    FL_TRY(sort_candidates(s, &m));
+    DBuf& val = s->key_val;
     int32_t* ulist[2] = {s->ulist.as<int32_t>(), s->ulist.as<int32_t>() + n};
     FL_CUDA(cudaMemsetAsync(cnt, 0, 64, st));
     if (m > 0) {

@@ -1,13 +1,16 @@
-"""GPU parity of the weighted-graph build (NEXT f3: Section 3.3 after
+"""GPU parity of the weighted-graph path (NEXT f3: Section 3.3 after
 Algorithm 2; weights uniform in [1, 100] as in Section 5) through the C ABI,
-against the oracle's weighted ADS.
+against the oracle's weighted ADS, selection and assignment.
 
 Bit-exact: sketches, ADS groups (distance, entry count, counted prefix),
-entry ids and HIP weights, the largest distance; radii within 1e-9 relative
-(in practice bit-identical: the same operation order).  The oracle's ADS is
-pinned to the paper's Algorithm 2 with CleanUp and to Floyd-Warshall brute
-force (tests/test_oracle_weighted.py), so these cases also show that the
-Dijkstra-order build on the GPU ends where CleanUp does."""
+entry ids and HIP weights, the largest distance, the open set (balls by
+weighted distance), assignments and distances, the distance sum; radii and
+the objective within 1e-9 relative (radii in practice bit-identical: the
+same operation order).  The oracle's ADS is pinned to the paper's
+Algorithm 2 with CleanUp and to Floyd-Warshall brute force, its selection to
+the lexicographically-first MIS by brute force and its assignment to
+all-pairs distances (tests/test_oracle_weighted.py), so these cases also show
+that the Dijkstra-order build on the GPU ends where CleanUp does."""
 import numpy as np
 import pytest
 
@@ -44,6 +47,20 @@ def _compare(rowp, cols, w, k, seed, cost, client):
     fin = np.isfinite(ro)
     assert np.array_equal(np.isfinite(r), fin)
     assert np.all(np.abs(r[fin] - ro[fin]) <= RTOL * np.abs(ro[fin]))
+    # selection and assignment by weighted distance
+    op, nopen = s.open_facilities()
+    op_o, nopen_o = og.open_facilities_weighted(ro, client, seed)
+    assert nopen == nopen_o and np.array_equal(op, op_o)
+    a, d = s.assign_clients()
+    a_o, d_o = og.assign_weighted(op_o)
+    assert np.array_equal(d, d_o) and np.array_equal(a, a_o)
+    obj, ds, un = s.objective()
+    obj_o, ds_o, un_o = oracle.objective(op_o, cost, client, d_o)
+    assert ds == ds_o and un == un_o
+    assert abs(obj - obj_o) <= RTOL * abs(obj_o)
+    st["mis"] = s.stats()
+    st["mis_log"] = s.mis_log()
+    st["n_open"] = nopen
     s.close()
     g.close()
     og.close()
@@ -136,6 +153,53 @@ def test_device_memory_inputs():
     h.close()
 
 
+@pytest.mark.parametrize("hi", [1, 3, 10])
+def test_chain_of_greedy_rounds(hi):
+    """A path whose costs grow along it: each facility's ball overlaps the
+    next one's, so the greedy decides a few facilities per round (about 30
+    rounds), each round's kill sweep deciding who drops out."""
+    n = 240
+    rowp, cols = brute.csr_from_edges(n, [(i, i + 1) for i in range(n - 1)])
+    w = flsynth.edge_weights(rowp, cols, 21, 1, hi)
+    cost = np.linspace(2.0, 8.0, n) * hi
+    client = np.ones(n, np.uint8)
+    st = _compare(rowp, cols, w, 4, 0, cost, client)
+    assert st["mis"]["mis_rounds"] >= (20 if hi == 1 else 2)
+    log = st["mis_log"]
+    tot = log[log[:, 1] == 3]
+    assert len(tot) == st["mis"]["mis_rounds"]
+    # every candidate is decided in exactly one greedy round
+    assert tot[:, 4].sum() == st["n_open"]
+    assert np.all(np.diff(tot[:, 3]) < 0)  # the undecided set shrinks every round
+
+
+def test_components_huge_radii_and_unserved_clients():
+    """Many small components (some without a facility: unserved clients,
+    assignment -1), costs up to 1e9 so that balls cover whole components and
+    the largest ball radius is far above every distance: the sweeps skip the
+    idle stretches between entry times."""
+    wl = flsynth.small_er(600, 1.2, 87)
+    w = flsynth.edge_weights(wl.rowp, wl.cols, 15)
+    fac = flsynth.bernoulli(wl.n, 40, 0.15)
+    cost = flsynth.loguniform(wl.n, 41, 1.0, 1.0e9, fac)
+    client = flsynth.bernoulli(wl.n, 42, 0.5)
+    _compare(wl.rowp, wl.cols, w, 8, 9, cost, client)
+
+
+def test_dense_conflicts_many_facilities():
+    """Erdos-Renyi with nearly every vertex a facility and a client, small
+    costs and lengths in [1, 10]: overlapping balls in every round."""
+    wl = flsynth.small_er(1200, 3.0, 89)
+    w = flsynth.edge_weights(wl.rowp, wl.cols, 17, 1, 10)
+    fac = flsynth.bernoulli(wl.n, 43, 0.9)
+    cost = flsynth.loguniform(wl.n, 44, 1.0, 30.0, fac)
+    client = flsynth.bernoulli(wl.n, 45, 0.9)
+    st = _compare(wl.rowp, wl.cols, w, 16, 10, cost, client)
+    log = st["mis_log"]
+    tot = log[log[:, 1] == 3]
+    assert tot[:, 4].sum() == st["n_open"]  # the rows count the facilities that joined
+
+
 def test_unbuilt_calls_and_bad_lengths():
     rowp, cols = brute.csr_from_edges(10, [(i, i + 1) for i in range(9)])
     n = len(rowp) - 1
@@ -145,7 +209,7 @@ def test_unbuilt_calls_and_bad_lengths():
     s = fl.Solve(g)
     cost, client = _inputs(n, 50)
     s.compute_radii(cost, client)
-    for call in (lambda: s.open_facilities(), lambda: s.open_facilities_eps(0.1, cost, client)):
+    for call in (lambda: s.open_facilities_eps(0.1, cost, client), lambda: s.compute_radii_exact(cost, client)):
         with pytest.raises(fl.FLError) as e:
             call()
         assert e.value.status == fl.FL_ESTATE
