@@ -978,6 +978,10 @@ def run_weighted(args):
         log = s.mis_log()
         out["largest_ball"] = int(log[log[:, 1] == 3][:, 2].max()) if len(log) else 0
         out["sweep_steps"] = int(log[log[:, 1] != 3][:, 3].sum()) if len(log) else 0
+        out["sweeps"] = {name: {"sweeps": int((log[:, 1] == kind).sum()),
+                                "steps": int(log[log[:, 1] == kind][:, 3].sum()),
+                                "host_ms": round(float(log[log[:, 1] == kind][:, 5].sum()) / 1e3, 3)}
+                         for name, kind in (("cover", 0), ("gather", 1), ("kill", 4))} if len(log) else {}
         s.close()
 
     for _ in range(args.warmup):
@@ -1025,6 +1029,7 @@ def run_weighted(args):
             "n_open": out["n_open"], "objective": out["objective"][0], "unserved": out["objective"][2],
             "mis_rounds": out["mis"]["mis_rounds"], "candidates": out["mis"]["candidates"],
             "largest_ball_radius": out["largest_ball"], "mis_sweep_steps": out["sweep_steps"],
+            "mis_sweeps": out["sweeps"],
             "phases_ms_per_step": {kk: v["ms"] / args.steps for kk, v in prof.items()},
             "gpu_launches": launches, "cpu_baseline": cpu, "clocks": clk}
     print(json.dumps(line), flush=True)

@@ -70,20 +70,42 @@ struct WSweep {
     uint32_t* dlab;             // smallest arrival up to the deadline
     int32_t* dist;              // first-arrival mode: arrival time
     uint8_t* past;              // first-arrival mode: 1 where a push went past the horizon
+    int32_t* ft;                // (cover) time of each vertex's first arrival, or NULL
+    const int32_t* fts;         // (gather, kill) the cover's first arrivals: prune by slack, or NULL
     int first;                  // 1: a vertex keeps its first arrival; 0: the minimum
 };
 
 // One arrival of x at v at time t; true when v joins the step's frontier.
 __device__ __forceinline__ bool arrive(const WSweep& a, int32_t v, uint32_t x, int64_t t) {
     if (a.dl && t <= (int64_t)a.dl[v] && x < a.dlab[v]) a.dlab[v] = x;
+    const uint32_t old = a.lab[v];
     if (a.first) {
-        if (a.lab[v] != kNone) return false;
+        if (old != kNone) return false;
         a.dist[v] = (int32_t)t;
-    } else if (x >= a.lab[v]) {
+    } else if (x >= old) {
         return false;
     }
+    if (a.ft && old == kNone) a.ft[v] = (int32_t)t;
     a.lab[v] = x;
     return true;
+}
+
+// First index i in [0, m) with bs[i] >= b (m when none), bs non-decreasing.
+// All 32 lanes call it and get the answer: each pass probes 32 evenly spaced
+// positions of the remaining range at once (log32 m dependent loads).
+__device__ int64_t warp_lower_bound(const int32_t* __restrict__ bs, int64_t m, int64_t b) {
+    int64_t lo = 0, hi = m;  // the answer lies in [lo, hi]
+    while (lo < hi) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t p = lo + step * lane_id();
+        const bool below = p < hi && (int64_t)bs[p] < b;
+        const int c = __popc(__ballot_sync(kFull, below));  // the probes below b are a prefix
+        if (c == 0) break;                                  // bs[lo] >= b
+        const int64_t first_not = lo + step * c;
+        lo += step * (c - 1) + 1;
+        hi = first_not < hi ? first_not : hi;
+    }
+    return lo;
 }
 
 // Appends the lanes' vertices with `want` to list (all 32 lanes call it).
@@ -121,20 +143,15 @@ __global__ void k_wdrain(WSweep a, int64_t t) {
 }
 
 // Step t, part 2 (cover): the undecided facilities with B_f = H - t enter.
-// Candidates in key order have non-decreasing B_f, so they are one range of
-// fac_by_ord, found by binary search; a candidate's value is its ordinal.
-__global__ void k_winject(WSweep a, const int32_t* __restrict__ fac_by_ord, const int32_t* __restrict__ bcap,
+// Candidates in key order have non-decreasing B_f (bsort[i] = B of the i-th),
+// so they are one range of fac_by_ord, found by search; a candidate's value
+// is its ordinal.
+__global__ void k_winject(WSweep a, const int32_t* __restrict__ fac_by_ord, const int32_t* __restrict__ bsort,
                           const uint8_t* __restrict__ state, int64_t m, int64_t H, int64_t t) {
     __shared__ int64_t range[2];
-    if (threadIdx.x < 2) {
-        const int64_t b = H - t + (int64_t)threadIdx.x;  // range[0]: first B >= H - t; range[1]: first B > H - t
-        int64_t lo = 0, hi = m;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if ((int64_t)bcap[fac_by_ord[mid]] < b) lo = mid + 1;
-            else hi = mid;
-        }
-        range[threadIdx.x] = lo;
+    if (threadIdx.x < 64) {  // warp 0: first B >= H - t; warp 1: first B > H - t
+        const int64_t at = warp_lower_bound(bsort, m, H - t + (int64_t)(threadIdx.x >> 5));
+        if (lane_id() == 0) range[threadIdx.x >> 5] = at;
     }
     __syncthreads();
     const int p = (int)(t & 1);
@@ -188,6 +205,10 @@ __global__ void __launch_bounds__(256) k_wpush(WSweep a, int64_t t, int64_t H) {
             const uint32_t lv = a.lab[v];
             if (a.first ? lv != kNone : lv <= x) continue;
             const int64_t t2 = t + a.wts[e];
+            if (a.fts) {  // v relays nothing useful after its slack H - (first cover arrival)
+                const int32_t fv = a.fts[v];
+                if (fv < 0 || t2 > H - (int64_t)fv) continue;
+            }
             if (t2 > H) {
                 if (a.first) a.past[v] = 1;
                 continue;
@@ -203,31 +224,27 @@ __global__ void __launch_bounds__(256) k_wpush(WSweep a, int64_t t, int64_t H) {
 }
 
 // The earliest time >= t at which a candidate enters the cover (H - B_f for
-// the largest B_f <= H - t, decided or not), or ~0 when none does.
-__global__ void k_wnext(const int32_t* __restrict__ fac_by_ord, const int32_t* __restrict__ bcap, int64_t m,
-                        int64_t H, int64_t t, unsigned long long* __restrict__ out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int64_t b = H - t + 1;
-    int64_t lo = 0, hi = m;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if ((int64_t)bcap[fac_by_ord[mid]] < b) lo = mid + 1;
-        else hi = mid;
-    }
-    *out = lo == 0 ? ~0ULL : (unsigned long long)(H - (int64_t)bcap[fac_by_ord[lo - 1]]);
+// the largest B_f <= H - t, decided or not), or ~0 when none does (one warp).
+__global__ void k_wnext(const int32_t* __restrict__ bsort, int64_t m, int64_t H, int64_t t,
+                        unsigned long long* __restrict__ out) {
+    const int64_t lo = warp_lower_bound(bsort, m, H - t + 1);
+    if (lane_id() == 0) *out = lo == 0 ? ~0ULL : (unsigned long long)(H - (int64_t)bsort[lo - 1]);
 }
 
 // Ordinals and ball radii of the sorted candidates: ord[f] = position in key
 // order, B_f = floor(r_f) (at most 2^31 - 1).
 __global__ void k_wordinals(const uint32_t* __restrict__ sorted_f, int64_t m, const double* __restrict__ r,
-                            uint32_t* __restrict__ ord, int32_t* __restrict__ fac_by_ord, int32_t* __restrict__ bcap) {
+                            uint32_t* __restrict__ ord, int32_t* __restrict__ fac_by_ord, int32_t* __restrict__ bcap,
+                            int32_t* __restrict__ bsort) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
         const int32_t f = (int32_t)sorted_f[i];
         ord[f] = (uint32_t)i;
         fac_by_ord[i] = f;
         const double fl = floor(r[f]);
-        bcap[f] = fl >= 2147483647.0 ? 2147483647 : (int32_t)fl;
+        const int32_t b = fl >= 2147483647.0 ? 2147483647 : (int32_t)fl;
+        bcap[f] = b;
+        bsort[i] = b;
     }
 }
 
@@ -376,6 +393,8 @@ struct WRing {
         a.dlab = nullptr;
         a.dist = nullptr;
         a.past = nullptr;
+        a.ft = nullptr;
+        a.fts = nullptr;
         a.first = 0;
         return a;
     }
@@ -392,7 +411,7 @@ struct WRing {
 // at time 0 through k_wseed).
 struct Entry {
     const int32_t* fac_by_ord;
-    const int32_t* bcap;
+    const int32_t* bsort;
     const uint8_t* state;
     int64_t m;
     int64_t t_last;  // no facility enters after this time
@@ -402,7 +421,7 @@ struct Entry {
 // chunks of steps the host reads the ring's counts: when nothing is pending
 // it jumps to the next entry time, or stops.  *t_end = the last step run,
 // *steps = the steps run.
-int run_sweep(fl_graph* g, WRing& ring, const WSweep& a, int64_t H, const Entry* entry, int64_t* t_end,
+int run_sweep(fl_graph* g, WRing& ring, const WSweep& a, int64_t H, const Entry* entry, int cls, int64_t* t_end,
               int64_t* steps) {
     cudaStream_t st = g->stream;
     const int R = ring.R;
@@ -413,19 +432,18 @@ int run_sweep(fl_graph* g, WRing& ring, const WSweep& a, int64_t H, const Entry*
     int64_t t = 0, ran = 0, last = 0;
     for (;;) {
         for (int j = 0; j < kChunk && t <= H; ++j, ++t) {
-            FL_LAUNCH(kProfMis, k_wdrain<<<gd, 256, 0, st>>>(a, t));
+            FL_LAUNCH(cls, k_wdrain<<<gd, 256, 0, st>>>(a, t));
             if (entry && t <= entry->t_last)
-                FL_LAUNCH(kProfMis, k_winject<<<gi, 256, 0, st>>>(a, entry->fac_by_ord, entry->bcap, entry->state,
-                                                                   entry->m, H, t));
-            FL_LAUNCH(kProfMis, k_wpush<<<gp, 256, 0, st>>>(a, t, H));
+                FL_LAUNCH(cls, k_winject<<<gi, 256, 0, st>>>(a, entry->fac_by_ord, entry->bsort, entry->state,
+                                                              entry->m, H, t));
+            FL_LAUNCH(cls, k_wpush<<<gp, 256, 0, st>>>(a, t, H));
             last = t;
             ++ran;
         }
         FL_CUDA(cudaGetLastError());
         if (t > H) break;
         if (entry && t <= entry->t_last)
-            FL_LAUNCH(kProfMis, k_wnext<<<1, 32, 0, st>>>(entry->fac_by_ord, entry->bcap, entry->m, H, t,
-                                                           ring.c + R + 3));
+            FL_LAUNCH(cls, k_wnext<<<1, 32, 0, st>>>(entry->bsort, entry->m, H, t, ring.c + R + 3));
         FL_CUDA(cudaMemcpyAsync(hc.data(), ring.c, (size_t)(R + 4) * 8, cudaMemcpyDeviceToHost, st));
         FL_CUDA(cudaStreamSynchronize(st));
         unsigned long long pending = 0;
@@ -460,10 +478,13 @@ int open_facilities_weighted(fl_solve* s) {
     FL_TRY(dalloc(s->claimed, (size_t)n));
     FL_TRY(dalloc(s->kill, (size_t)n));
     FL_TRY(dalloc(s->open, (size_t)n));
-    FL_TRY(dalloc(s->X, (size_t)n * 16));  // cover labels, sweep labels, deadline labels
+    FL_TRY(dalloc(s->X, (size_t)n * 16));  // cover labels, sweep labels, deadline labels, first arrivals
+    FL_TRY(dalloc(s->ubuck, (size_t)std::max<int64_t>(m, 1) * 4));
     uint32_t* cover = s->X.as<uint32_t>();
     uint32_t* lab = cover + n;
     uint32_t* dlab = cover + 2 * n;
+    int32_t* ft = reinterpret_cast<int32_t*>(cover + 3 * n);
+    int32_t* bsort = s->ubuck.as<int32_t>();
     int32_t* fac_by_ord = s->fac_by_ord.as<int32_t>();
     int32_t* bcap = s->bcap.as<int32_t>();
     uint8_t* state = s->state.as<uint8_t>();
@@ -472,7 +493,7 @@ int open_facilities_weighted(fl_solve* s) {
     if (m > 0)
         FL_LAUNCH(kProfKeys, k_wordinals<<<grid_for(m, 256), 256, 0, st>>>(s->key_val.as<uint32_t>(), m,
                                                                           s->radii.as<double>(), s->ord.as<uint32_t>(),
-                                                                          fac_by_ord, bcap));
+                                                                          fac_by_ord, bcap, bsort));
     FL_CUDA(cudaGetLastError());
     WRing ring;
     int rc = ring.alloc(g);
@@ -496,7 +517,7 @@ int open_facilities_weighted(fl_solve* s) {
         if (nu == 0) break;
         if (++rounds > m + 1) { rc = FL_ETIMEOUT; set_error(rc, "weighted MIS did not converge"); break; }
         const int64_t H = (int64_t)h[3];
-        Entry entry{fac_by_ord, bcap, state, m, H - (int64_t)h[4]};
+        Entry entry{fac_by_ord, bsort, state, m, H - (int64_t)h[4]};
         auto timed = [&](int kind, int64_t t_end, int64_t steps, clock::time_point t0) {
             const double us = std::chrono::duration<double, std::micro>(clock::now() - t0).count();
             s->mis_log.insert(s->mis_log.end(), {rounds, (int64_t)kind, t_end, steps, 0, (int64_t)us});
@@ -506,20 +527,24 @@ int open_facilities_weighted(fl_solve* s) {
         auto t0 = clock::now();
         WSweep a = ring.sweep(g);
         a.lab = cover;
+        a.ft = ft;
         e = cudaMemsetAsync(cover, 0xff, (size_t)n * 4, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ft, 0xff, (size_t)n * 4, st);
         if (e != cudaSuccess) { rc = status_of(e, "weighted MIS", __FILE__, __LINE__); break; }
-        if ((rc = ring.begin(st)) || (rc = run_sweep(g, ring, a, H, &entry, &t_end, &steps))) break;
+        if ((rc = ring.begin(st)) || (rc = run_sweep(g, ring, a, H, &entry, kProfMis, &t_end, &steps))) break;
         timed(0, t_end, steps, t0);
         // gather
         t0 = clock::now();
         a.lab = lab;
         a.dl = bcap;
         a.dlab = dlab;
+        a.ft = nullptr;
+        a.fts = ft;
         e = cudaMemsetAsync(lab, 0xff, (size_t)n * 8, st);  // lab and dlab
         if (e != cudaSuccess) { rc = status_of(e, "weighted MIS", __FILE__, __LINE__); break; }
         if ((rc = ring.begin(st))) break;
         FL_LAUNCH(kProfMis, k_wseed<<<grid_for(n, 256), 256, 0, st>>>(a, cover, s->client.as<uint8_t>()));
-        if ((rc = run_sweep(g, ring, a, H, nullptr, &t_end, &steps))) break;
+        if ((rc = run_sweep(g, ring, a, H, nullptr, kProfMis, &t_end, &steps))) break;
         timed(1, t_end, steps, t0);
         if (m > 0)
             FL_LAUNCH(kProfMis, k_wdecide<<<grid_for(m, 256), 256, 0, st>>>(fac_by_ord, m, dlab, state, c + R + 7,
@@ -539,7 +564,7 @@ int open_facilities_weighted(fl_solve* s) {
             if (e != cudaSuccess) { rc = status_of(e, "weighted MIS", __FILE__, __LINE__); break; }
             if ((rc = ring.begin(st))) break;
             FL_LAUNCH(kProfMis, k_wseed<<<grid_for(n, 256), 256, 0, st>>>(a, nullptr, s->kill.as<uint8_t>()));
-            if ((rc = run_sweep(g, ring, a, H, nullptr, &t_end, &steps))) break;
+            if ((rc = run_sweep(g, ring, a, H, nullptr, kProfMis, &t_end, &steps))) break;
             timed(4, t_end, steps, t0);
             FL_LAUNCH(kProfMis, k_wkill<<<grid_for(m, 256), 256, 0, st>>>(fac_by_ord, m, dlab, state));
         }
@@ -586,7 +611,7 @@ int assign_weighted(fl_solve* s) {
         rc = ring.begin(st);
         if (rc == FL_OK) {
             FL_LAUNCH(kProfBfs, k_wseed<<<grid_for(n, 256), 256, 0, st>>>(a, nullptr, s->open.as<uint8_t>()));
-            rc = run_sweep(g, ring, a, 2147483647LL, nullptr, &t_end, &steps);
+            rc = run_sweep(g, ring, a, 2147483647LL, nullptr, kProfBfs, &t_end, &steps);
         }
         unsigned long long err = 0;
         if (rc == FL_OK) {
