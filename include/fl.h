@@ -80,7 +80,9 @@ int fl_graph_create(int64_t n, const int64_t* row_off, const int32_t* cols, int6
  * Section 5 draws weights uniformly in [1, 100]).  Arguments as
  * fl_graph_create, plus
  *   lengths  int32[nnz] edge length of each CSR entry, an integer in
- *            [1, 65535], equal for (u, v) and (v, u) (same mem_kind).
+ *            [1, 65535], equal for (u, v) and (v, u) (same mem_kind): the
+ *            entries (u, v) and (v, u) of each length must be equally many
+ *            (FL_EINVAL otherwise); nnz < 2^32.
  * fl_build_sketches then builds the ADS in Dijkstra order: one group per
  * distance (the group's "hop" is the distance, at most 65535, else
  * FL_EINVAL), with the HIP weights and counted prefixes of the unweighted

@@ -33,7 +33,7 @@ int copy_out(void* dst, const void* src, size_t bytes, int mem_kind, cudaStream_
 
 void destroy_graph(fl_graph* g) {
     cudaStreamSynchronize(g->stream);  // its buffers go to the idle-block cache
-    DBuf* bufs[] = {&g->rowp, &g->cols, &g->wts, &g->low_list, &g->small_list, &g->mid_list, &g->hub_list, &g->hub_seg, &g->seg_hub, &g->part,
+    DBuf* bufs[] = {&g->rowp, &g->cols, &g->wts, &g->wrev, &g->low_list, &g->small_list, &g->mid_list, &g->hub_list, &g->hub_seg, &g->seg_hub, &g->part,
                     &g->S, &g->Scnt, &g->D[0], &g->D[1], &g->Dcnt[0], &g->Dcnt[1], &g->frontier[0],
                     &g->frontier[1], &g->stamp, &g->vg, &g->ve, &g->stg_ent, &g->stg_grp, &g->gofs, &g->eofs,
                     &g->ginfo, &g->gwt, &g->eid, &g->ecc_ub, &g->ctr, &g->scratch,
@@ -236,6 +236,7 @@ int fl_graph_create_weighted(int64_t n, const int64_t* row_off, const int32_t* c
         set_current_prof(&g->prof, g->stream);
         if ((rc = validate_csr(g))) break;
         if ((rc = check_weights(g))) break;
+        if ((rc = pair_reverse_edges(g))) break;
         // kept in the caller's numbering: the lengths stay aligned with the columns
     } while (0);
     if (rc != FL_OK) {

@@ -450,6 +450,7 @@ struct fl_graph {
     cudaStream_t stream = nullptr;
     fl::DBuf rowp, cols;           // int64[n+1], int32[nnz]
     fl::DBuf wts;                  // int32[nnz]: edge lengths of a weighted graph, else empty
+    fl::DBuf wrev;                 // uint32[nnz]: (weighted) the entry (v, u) paired with each entry (u, v)
     int max_w = 0;                 // largest edge length
     int64_t wlevels = 0;           // distance levels with active vertices in the last weighted build
     // static work lists: non-hub non-isolated vertices, hubs, hub segments
@@ -587,6 +588,7 @@ int build_work_lists(fl_graph* g);
 int build_sketches(fl_graph* g, int k, uint64_t seed);
 // weighted graphs (k_wsketch.cu): length check, and the build in Dijkstra order
 int check_weights(fl_graph* g);
+int pair_reverse_edges(fl_graph* g);
 int build_sketches_weighted(fl_graph* g, int k, uint64_t seed);
 int compute_ecc_bound(fl_graph* g);
 

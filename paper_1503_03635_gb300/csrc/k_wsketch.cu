@@ -12,8 +12,11 @@
 //
 // Level L: v is active when a neighbour u gained entries at distance
 // L - w(u, v); a ring of (largest length + 1) bitmaps holds the activations
-// of the coming levels.  An active v merges into its bottom-k sketch the
-// entries of each neighbour u at distance L - w(u, v); the ranks that enter
+// of the coming levels, and a second ring of bitmaps over the CSR entries
+// marks which entries (v, u) of an active v deliver at that level (u posts
+// to the entry of v's row paired with its own entry (u, v), so v reads only
+// the neighbours that gained).  An active v merges into its bottom-k sketch the
+// entries of each such neighbour u at distance L - w(u, v); the ranks that enter
 // form v's group at distance L, with the HIP weight and counted prefix of
 // the unweighted build (the sketch after the level, ties at one distance in
 // ascending rank).  A vertex's entries are kept in distance order in a
@@ -73,6 +76,9 @@ struct WArgs {
     uint32_t* ring;          // R bitmaps of `words` words
     int64_t words;
     int R;
+    const uint32_t* rev;     // nnz: the entry (v, u) paired with each entry (u, v)
+    uint32_t* marks;         // R bitmaps of `mwords` words over the CSR entries
+    int64_t mwords;
     unsigned long long* pend;  // R activation counts
     unsigned long long* err;   // 1: a row overflowed; 2: a distance above 65535; 4: the group log overflowed
 };
@@ -82,6 +88,15 @@ __device__ __forceinline__ void activate(const WArgs& a, int32_t u, int64_t leve
     const uint32_t bit = 1u << (u & 31);
     const uint32_t old = atomicOr(&a.ring[(int64_t)slot * a.words + (u >> 5)], bit);
     if (!(old & bit)) atomicAdd(&a.pend[slot], 1ULL);
+}
+
+// The source of CSR entry e = (u, v) gained entries that reach v at `level`:
+// mark v's paired entry (v, u) and activate v.
+__device__ __forceinline__ void post(const WArgs& a, int64_t e, int64_t level) {
+    const int slot = (int)(level % a.R);
+    const uint32_t re = a.rev[e];
+    atomicOr(&a.marks[(int64_t)slot * a.mwords + (re >> 5)], 1u << (re & 31));
+    activate(a, a.cols[e], level);
 }
 
 // Level 0: every vertex's own rank; its neighbours become active at the
@@ -108,7 +123,7 @@ __global__ void k_winit(WArgs a, int64_t n) {
         }
         for (int64_t e = a.rowp[v] + lane; e < a.rowp[v + 1]; e += 32) {
             a.cursor[e] = 0;
-            activate(a, a.cols[e], a.wts[e]);
+            post(a, e, a.wts[e]);
         }
     }
 }
@@ -144,10 +159,13 @@ __global__ void __launch_bounds__(256) k_wlevel(WArgs a, const int32_t* __restri
         int cnt = cnt_old;
         uint64_t kth = cnt == a.k ? __shfl_sync(kFull, s, a.k - 1) : kEmpty;
         const int64_t e0 = a.rowp[v], e1 = a.rowp[v + 1];
+        const uint32_t* mk = a.marks + (int64_t)(L % a.R) * a.mwords;
         for (int64_t eb = e0; eb < e1; eb += 32) {
             const int64_t e = eb + lane;
+            const bool marked = e < e1 && ((mk[e >> 5] >> (e & 31)) & 1u);
+            if (!__any_sync(kFull, marked)) continue;  // no neighbour of this chunk delivers
             int32_t u = 0, c0 = 0, c1 = 0;
-            if (e < e1) {
+            if (marked) {
                 u = a.cols[e];
                 const int32_t x = L - a.wts[e];
                 if (x >= 0) {
@@ -227,7 +245,7 @@ __global__ void __launch_bounds__(256) k_wlevel(WArgs a, const int32_t* __restri
         for (int64_t e = e0 + lane; e < e1; e += 32) {
             const int64_t lv = (int64_t)L + a.wts[e];
             if (lv > 65535) atomicOr(a.err, 2ULL);
-            else activate(a, a.cols[e], lv);
+            else post(a, e, lv);
         }
     }
 }
@@ -277,7 +295,115 @@ __global__ void k_wmaxlen(const int32_t* __restrict__ w, int64_t nnz, unsigned l
     if (__any_sync(kFull, neg) && lane_id() == 0) atomicOr(bad, 1ULL);
 }
 
+// Pairing keys of the CSR entries: (min(u, v), max(u, v)) and (length,
+// direction), the entry index as payload (a warp per source vertex u).
+__global__ void k_wrevkeys(const int64_t* __restrict__ rowp, const int32_t* __restrict__ cols,
+                           const int32_t* __restrict__ wts, int64_t n, uint64_t* __restrict__ hi,
+                           uint64_t* __restrict__ lo, uint32_t* __restrict__ val) {
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        for (int64_t e = rowp[u] + lane_id(); e < rowp[u + 1]; e += 32) {
+            const int64_t v = cols[e];
+            const uint64_t a = (uint64_t)(u < v ? u : v), b = (uint64_t)(u < v ? v : u);
+            hi[e] = (a << 32) | b;
+            lo[e] = ((uint64_t)(uint32_t)wts[e] << 1) | (u > v ? 1u : 0u);
+            val[e] = (uint32_t)e;
+        }
+    }
+}
+
+// First index of the sorted keys at or above (h, l).
+__device__ __forceinline__ int64_t key_lower_bound(const uint64_t* __restrict__ hi, const uint64_t* __restrict__ lo,
+                                                   int64_t m, uint64_t h, uint64_t l) {
+    int64_t a = 0, b = m;
+    while (a < b) {
+        const int64_t mid = (a + b) >> 1;
+        const uint64_t x = hi[mid];
+        if (x < h || (x == h && lo[mid] < l)) a = mid + 1;
+        else b = mid;
+    }
+    return a;
+}
+
+// After the sort, the entries of one edge and length form a group whose
+// first half runs min -> max and second half max -> min; the i-th of each
+// half pair up (a self-loop pairs with itself).  A group whose halves differ
+// means a length that is not the same in both directions (bad = 1).
+__global__ void k_wpair(const uint64_t* __restrict__ hi, const uint64_t* __restrict__ lo,
+                        const uint32_t* __restrict__ val, int64_t m, uint32_t* __restrict__ rev,
+                        unsigned long long* __restrict__ bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const uint64_t h = hi[i], l = lo[i];
+        if ((h >> 32) == (h & 0xffffffffULL)) {
+            rev[val[i]] = val[i];
+            continue;
+        }
+        const uint64_t l0 = l & ~1ULL;  // the group: keys (h, l0) and (h, l0 | 1)
+        const int64_t g0 = key_lower_bound(hi, lo, m, h, l0);
+        const int64_t g1 = key_lower_bound(hi, lo, m, h, l0 + 2);
+        const int64_t half = (g1 - g0) >> 1;
+        if (((g1 - g0) & 1) || half < 1 || lo[g0 + half - 1] != l0 || lo[g0 + half] != (l0 | 1u)) {
+            atomicOr(bad, 1ULL);
+            continue;
+        }
+        if (l & 1u) continue;  // the second half is written by its partners
+        const int64_t j = i + half;
+        rev[val[i]] = val[j];
+        rev[val[j]] = val[i];
+    }
+}
+
 }  // namespace
+
+// For every CSR entry (u, v) of a weighted graph, an entry (v, u) of the same
+// length, paired one to one (duplicates pair in order): the weighted build
+// marks the paired entry of v's row when u gains entries.  FL_EINVAL when an
+// edge's lengths differ between its two directions.
+int pair_reverse_edges(fl_graph* g) {
+    const int64_t n = g->n, nnz = g->nnz;
+    cudaStream_t st = g->stream;
+    if (nnz >= (1LL << 32)) FL_FAIL(FL_EINVAL, "a weighted graph holds fewer than 2^32 CSR entries");
+    FL_TRY(dalloc(g->wrev, (size_t)std::max<int64_t>(nnz, 1) * 4));
+    if (nnz == 0) return FL_OK;
+    DBuf hi, lo, val, flag;
+    int rc = FL_OK;
+    do {
+        if ((rc = dalloc(hi, (size_t)nnz * 8)) || (rc = dalloc(lo, (size_t)nnz * 8)) ||
+            (rc = dalloc(val, (size_t)nnz * 4)) || (rc = dalloc(flag, 16)))
+            break;
+        cudaError_t e = cudaMemsetAsync(flag.p, 0, 16, st);
+        if (e != cudaSuccess) { rc = status_of(e, "edge pairing", __FILE__, __LINE__); break; }
+        FL_LAUNCH(kProfOther, k_wrevkeys<<<grid_for(n * 32, 256), 256, 0, st>>>(
+                                  g->rowp.as<int64_t>(), g->cols.as<int32_t>(), g->wts.as<int32_t>(), n,
+                                  hi.as<uint64_t>(), lo.as<uint64_t>(), val.as<uint32_t>()));
+        // the digits that can vary: ids below n in both halves of hi, the
+        // length and the direction bit in lo
+        int nb = 1, wb = 1;
+        while (nb < 31 && (1LL << nb) < n) ++nb;
+        while (wb < 17 && (1 << wb) <= g->max_w) ++wb;
+        uint32_t digits = 0;
+        for (int d = 0; d * 4 < wb + 1; ++d) digits |= 1u << d;
+        for (int d = 0; d * 4 < nb; ++d) digits |= (1u << (16 + d)) | (1u << (24 + d));
+        if ((rc = sort_pairs_u128_digits(hi.as<uint64_t>(), lo.as<uint64_t>(), val.as<uint32_t>(), nnz, st,
+                                         g->scratch, kProfOther, digits)))
+            break;
+        FL_LAUNCH(kProfOther, k_wpair<<<grid_for(nnz, 256), 256, 0, st>>>(
+                                  hi.as<uint64_t>(), lo.as<uint64_t>(), val.as<uint32_t>(), nnz,
+                                  g->wrev.as<uint32_t>(), flag.as<unsigned long long>()));
+        unsigned long long h = 0;
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag.p, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { rc = status_of(e, "edge pairing", __FILE__, __LINE__); break; }
+        if (h) {
+            rc = FL_EINVAL;
+            set_error(rc, "an edge's length must be the same in both directions");
+        }
+    } while (0);
+    dfree_after(st, {&hi, &lo, &val, &flag});
+    return rc;
+}
 
 int check_weights(fl_graph* g) {
     cudaStream_t st = g->stream;
@@ -306,7 +432,8 @@ int build_sketches_weighted(fl_graph* g, int k, uint64_t seed) {
     // margin, at most n; doubled and rebuilt on overflow
     const double expect = (double)k * (1.0 + std::log(std::max(1.0, (double)n / k)));
     int64_t cap = std::min<int64_t>(n, (int64_t)(2.0 * expect) + 64);
-    DBuf ent, ecnt, ecnt_n, gcnt, cursor, glog, ring, pend, act, cnt;
+    const int64_t mwords = (nnz + 31) / 32;
+    DBuf ent, ecnt, ecnt_n, gcnt, cursor, glog, ring, pend, act, cnt, marks;
     int rc = FL_OK;
     for (;;) {
         const unsigned long long glog_cap = (unsigned long long)n * (unsigned long long)cap;
@@ -316,7 +443,8 @@ int build_sketches_weighted(fl_graph* g, int k, uint64_t seed) {
             (rc = dalloc(gcnt, (size_t)n * 4)) || (rc = dalloc(cursor, (size_t)std::max<int64_t>(nnz, 1) * 4)) ||
             (rc = dalloc(glog, (size_t)glog_cap * sizeof(WGroup))) ||
             (rc = dalloc(ring, (size_t)R * words * 4 + 16)) || (rc = dalloc(pend, (size_t)R * 8)) ||
-            (rc = dalloc(act, (size_t)n * 4)) || (rc = dalloc(cnt, 64)))
+            (rc = dalloc(act, (size_t)n * 4)) || (rc = dalloc(cnt, 64)) ||
+            (rc = dalloc(marks, (size_t)R * mwords * 4 + 16)))
             break;
         WArgs a;
         a.rowp = g->rowp.as<int64_t>();
@@ -341,7 +469,11 @@ int build_sketches_weighted(fl_graph* g, int k, uint64_t seed) {
         a.words = words;
         a.R = R;
         a.pend = pend.as<unsigned long long>();
+        a.rev = g->wrev.as<uint32_t>();
+        a.marks = marks.as<uint32_t>();
+        a.mwords = mwords;
         cudaError_t e = cudaMemsetAsync(ring.p, 0, (size_t)R * words * 4, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(marks.p, 0, (size_t)R * mwords * 4, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(pend.p, 0, (size_t)R * 8, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(cnt.p, 0, 64, st);
         if (e != cudaSuccess) { rc = status_of(e, "weighted build", __FILE__, __LINE__); break; }
@@ -378,6 +510,9 @@ int build_sketches_weighted(fl_graph* g, int k, uint64_t seed) {
                                                                                        (int32_t)L));
             FL_LAUNCH(kProfSketchMerge, k_wcommit<<<grid_for(n_act, 256), 256, 0, st>>>(
                                             act.as<int32_t>(), &c[2], a.ecnt_n, a.ecnt));
+            // the level's entry marks are read: the slot serves level L + R next
+            e = cudaMemsetAsync(a.marks + (int64_t)slot * mwords, 0, (size_t)mwords * 4, st);
+            if (e != cudaSuccess) { rc = status_of(e, "weighted build", __FILE__, __LINE__); break; }
             ++levels;
         }
         if (rc != FL_OK) break;
@@ -431,7 +566,7 @@ int build_sketches_weighted(fl_graph* g, int k, uint64_t seed) {
         g->wlevels = levels;
         break;
     }
-    dfree_after(st, {&ent, &ecnt, &ecnt_n, &gcnt, &cursor, &glog, &ring, &pend, &act, &cnt});
+    dfree_after(st, {&ent, &ecnt, &ecnt_n, &gcnt, &cursor, &glog, &ring, &pend, &act, &cnt, &marks});
     return rc;
 }
 

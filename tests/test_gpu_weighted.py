@@ -221,5 +221,11 @@ def test_unbuilt_calls_and_bad_lengths():
         with pytest.raises(fl.FLError) as e:
             fl.Graph(rowp, cols, lengths=wb)
         assert e.value.status == fl.FL_EINVAL
+    # a length that differs between the two directions of an edge
+    wb = w.copy()
+    wb[0] = w[0] % 100 + 1
+    with pytest.raises(fl.FLError) as e:
+        fl.Graph(rowp, cols, lengths=wb)
+    assert e.value.status == fl.FL_EINVAL
     with pytest.raises(ValueError):
         fl.Graph(rowp, cols, lengths=w[:-1])
