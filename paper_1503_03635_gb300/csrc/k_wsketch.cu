@@ -148,6 +148,7 @@ __global__ void k_wcollect(uint32_t* __restrict__ bm, int64_t words, int64_t n, 
 // One level: a warp per active vertex (see the file comment).
 __global__ void __launch_bounds__(256) k_wlevel(WArgs a, const int32_t* __restrict__ act,
                                                 const unsigned long long* __restrict__ n_act_d, int32_t L) {
+    __shared__ int32_t s_stage[8][1024];      // per warp: the delivering entries of 32 mark words
     const int64_t n_act = (int64_t)*n_act_d;  // the vertices the collect pass listed
     const int lane = lane_id();
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -160,44 +161,70 @@ __global__ void __launch_bounds__(256) k_wlevel(WArgs a, const int32_t* __restri
         uint64_t kth = cnt == a.k ? __shfl_sync(kFull, s, a.k - 1) : kEmpty;
         const int64_t e0 = a.rowp[v], e1 = a.rowp[v + 1];
         const uint32_t* mk = a.marks + (int64_t)(L % a.R) * a.mwords;
-        for (int64_t eb = e0; eb < e1; eb += 32) {
-            const int64_t e = eb + lane;
-            const bool marked = e < e1 && ((mk[e >> 5] >> (e & 31)) & 1u);
-            if (!__any_sync(kFull, marked)) continue;  // no neighbour of this chunk delivers
-            int32_t u = 0, c0 = 0, c1 = 0;
-            if (marked) {
-                u = a.cols[e];
-                const int32_t x = L - a.wts[e];
-                if (x >= 0) {
-                    const int32_t have = min(a.ecnt[u], a.cap);
-                    const WEnt* row = a.ent + (int64_t)u * a.cap;
-                    int32_t c = min(a.cursor[e], have);
-                    while (c < have && row[c].dist < x) ++c;
-                    c0 = c;
-                    while (c < have && row[c].dist == x) ++c;
-                    c1 = c;
-                    a.cursor[e] = c;  // later levels ask for larger distances
+        int32_t* stage = s_stage[threadIdx.x >> 5];
+        const int64_t w1 = (e1 + 31) >> 5;
+        for (int64_t wb = e0 >> 5; wb < w1; wb += 32) {
+            // 32 words of marks at once: their set bits inside [e0, e1) are the
+            // delivering entries, staged in row order (a hub's row holds
+            // thousands of entries, a few of which deliver at a level)
+            const int64_t wi = wb + lane;
+            uint32_t bits = 0;
+            if (wi < w1) {
+                bits = mk[wi];
+                const int64_t first = wi << 5;
+                if (first < e0) bits &= ~0u << (int)(e0 - first);
+                if (e1 - first < 32) bits &= (1u << (int)(e1 - first)) - 1u;
+            }
+            const int mine = __popc(bits);
+            int pre = mine;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, pre, o);
+                if (lane >= o) pre += y;
+            }
+            const int total = __shfl_sync(kFull, pre, 31);
+            if (total == 0) continue;
+            pre -= mine;
+            for (uint32_t b = bits; b; b &= b - 1u) stage[pre++] = (int32_t)((wi << 5) + (__ffs(b) - 1) - e0);
+            __syncwarp();
+            for (int cb = 0; cb < total; cb += 32) {
+                const int j = cb + lane;
+                int32_t u = 0, c0 = 0, c1 = 0;
+                if (j < total) {
+                    const int64_t e = e0 + stage[j];
+                    u = a.cols[e];
+                    const int32_t x = L - a.wts[e];
+                    if (x >= 0) {
+                        const int32_t have = min(a.ecnt[u], a.cap);
+                        const WEnt* row = a.ent + (int64_t)u * a.cap;
+                        int32_t c = min(a.cursor[e], have);
+                        while (c < have && row[c].dist < x) ++c;
+                        c0 = c;
+                        while (c < have && row[c].dist == x) ++c;
+                        c1 = c;
+                        a.cursor[e] = c;  // later levels ask for larger distances
+                    }
+                }
+                // each lane offers its entry's candidates one per round
+                while (__any_sync(kFull, c0 < c1)) {
+                    uint64_t r = kEmpty;
+                    if (c0 < c1) {
+                        r = vertex_rank(a.seed, a.ent[(int64_t)u * a.cap + c0].id);
+                        ++c0;
+                        if (r >= kth) r = kEmpty;  // cannot enter a full sketch
+                    }
+                    if (warp_member(s, r)) r = kEmpty;  // already held
+                    r = warp_sort(r);
+                    const uint64_t prev = __shfl_up_sync(kFull, r, 1);
+                    const bool keep = r != kEmpty && (lane == 0 || prev != r);
+                    r = warp_compact(r, __ballot_sync(kFull, keep), kEmpty);
+                    if (__ballot_sync(kFull, r != kEmpty) == 0) continue;
+                    s = warp_merge_low(s, r);
+                    if (lane >= a.k) s = kEmpty;
+                    cnt = __popc(__ballot_sync(kFull, s != kEmpty));
+                    kth = cnt == a.k ? __shfl_sync(kFull, s, a.k - 1) : kEmpty;
                 }
             }
-            // each lane offers its edge's candidates one per round
-            while (__any_sync(kFull, c0 < c1)) {
-                uint64_t r = kEmpty;
-                if (c0 < c1) {
-                    r = vertex_rank(a.seed, a.ent[(int64_t)u * a.cap + c0].id);
-                    ++c0;
-                    if (r >= kth) r = kEmpty;  // cannot enter a full sketch
-                }
-                if (warp_member(s, r)) r = kEmpty;  // already held
-                r = warp_sort(r);
-                const uint64_t prev = __shfl_up_sync(kFull, r, 1);
-                const bool keep = r != kEmpty && (lane == 0 || prev != r);
-                r = warp_compact(r, __ballot_sync(kFull, keep), kEmpty);
-                if (__ballot_sync(kFull, r != kEmpty) == 0) continue;
-                s = warp_merge_low(s, r);
-                if (lane >= a.k) s = kEmpty;
-                cnt = __popc(__ballot_sync(kFull, s != kEmpty));
-                kth = cnt == a.k ? __shfl_sync(kFull, s, a.k - 1) : kEmpty;
-            }
+            __syncwarp();
         }
         // the entries gained at distance L: in the new sketch, not in the old
         // (every lane takes part in the membership shuffles)
