@@ -230,6 +230,55 @@ def test_mis_on_weighted_balls_is_the_lexicographically_first(name):
         assert set(np.flatnonzero(op)) == S and nopen == len(S)
 
 
+@pytest.mark.parametrize("hi", [1, 3])
+def test_mis_chain_of_rounds_on_a_path(hi):
+    """A path whose costs grow along it, every vertex a client: each ball
+    overlaps the next one, so the lexicographically-first MIS is a long chain
+    of dependent decisions (the case where a parallel greedy needs many
+    rounds); against brute force on Floyd-Warshall distances."""
+    n = 80
+    rowp, cols = brute.csr_from_edges(n, [(i, i + 1) for i in range(n - 1)])
+    w = flsynth.edge_weights(rowp, cols, 21, 1, hi)
+    D = brute.apsp_weighted(rowp, cols, w)
+    cost = np.linspace(2.0, 8.0, n) * hi
+    client = np.ones(n, np.uint8)
+    g = oracle.Graph(rowp, cols)
+    g.set_weights(w)
+    g.build_sketches_weighted(4, 0)
+    r = g.radii(cost, client)
+    op, nopen = g.open_facilities_weighted(r, client, 0)
+    cand, balls, adj = brute.conflict_graph(D, r, client)
+    S = brute.lfmis(cand, adj, key=lambda f: (r[f], oracle.priority(0, f)))
+    assert set(np.flatnonzero(op)) == S and nopen == len(S)
+    assert 1 < len(S) < n
+
+
+def test_components_without_facilities_and_huge_costs():
+    """Small components, some without a facility (their clients stay
+    unassigned: -1, -1), opening costs up to 1e9 so that balls cover whole
+    components: selection and assignment against brute force."""
+    wl = flsynth.small_er(40, 1.2, 87)
+    n = wl.n
+    w = flsynth.edge_weights(wl.rowp, wl.cols, 15)
+    D = brute.apsp_weighted(wl.rowp, wl.cols, w)
+    fac = flsynth.bernoulli(n, 40, 0.3)
+    cost = flsynth.loguniform(n, 41, 1.0, 1.0e9, fac)
+    client = flsynth.bernoulli(n, 42, 0.5)
+    g = oracle.Graph(wl.rowp, wl.cols)
+    g.set_weights(w)
+    g.build_sketches_weighted(8, 9)
+    r = g.radii(cost, client)
+    op, nopen = g.open_facilities_weighted(r, client, 9)
+    cand, balls, adj = brute.conflict_graph(D, r, client)
+    S = brute.lfmis(cand, adj, key=lambda f: (r[f], oracle.priority(9, f)))
+    assert set(np.flatnonzero(op)) == S and nopen == len(S)
+    a, d = g.assign_weighted(op)
+    wa, wd = brute.nearest_assignment(D, S)
+    assert np.array_equal(a, wa) and np.array_equal(d, wd)
+    assert (d < 0).any() and (d > 0).any()
+    assert max(np.floor(r[f]) for f in cand) > 1.0e5  # balls far wider than any distance
+
+
 @pytest.mark.parametrize("name", sorted(GRAPHS))
 def test_weighted_assignment_is_the_nearest_open_facility(name):
     rowp, cols, w = _weighted(name, seed=23)
