@@ -467,7 +467,8 @@ int fl_hop_model(const fl_graph* g, int64_t cap, int64_t* n_hops, int64_t* edge_
  * device looks up that array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture on the device.  Every call
  * synchronises `stream` several times: after validating the CSR and once per
- * BFS level, to read the next frontier's size into host memory.  All calls
+ * BFS level, to read the next frontier's size into host memory, so no call
+ * can be captured into a CUDA graph.  All calls
  * share the array and each clears what must start at zero; calls that
  * overlap on the GPU race.
  */
